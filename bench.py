@@ -1,0 +1,448 @@
+"""Benchmark of the DiffWind hot path on GB300.
+
+Headline workload (one "step"): the flag-like sheet at full size - 400,040
+particles, 128^3 grid, Neo-Hookean E = 5e4, pinned edge, 32^3 x 16 Fourier
+wind field, dt = 5e-5 - advanced by 1000 MLS-MPM substeps with a re-sort of
+the particles by cell every 20 substeps, as one CUDA-graph replay. The metric
+is MPM particle-substeps per second over all ranks (weak scaling: every rank
+runs its own scene). Further measurements on the same run go into "metrics":
+the MPM forward+adjoint rollout with checkpointing (100k-particle sheet on
+64^3, 200 substeps, checkpoint every 20), the D3Q19 LBM step and its adjoint on
+a 128^3 lattice with a leaf-cluster obstacle (MLUPS).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
+the launching stream; a 512 MB buffer is written between timed steps to flush
+the 129 MB L2. `--impl reference` times the FP64 CPU oracle instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPM particle-substeps/s fwd+adj, LBM MLUPS; surrogate vs plain LBM at stated error"
+UNIT = "particle-substeps/s"
+WORKLOAD = "sheet400k_128^3_1000substeps_fwd"
+SORT_EVERY = 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--substeps", type=int, default=1000)
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [v for v in sm if smax and v >= 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- our arm ----
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2603_09668_gb300 import build as _build
+
+    _build.build_library()
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import inputs
+    from paper_2603_09668_gb300.rollout import Rollout
+
+    sc = inputs.sheet_scene(n_substeps=args.substeps, seed=rank, wind_seed=rank)
+    n = sc.n
+    mpm = B.MPM.from_params(sc.params(), max_particles=n)
+    wind = B.WindField(torch.from_numpy(sc.wind).to(dev), sc.t_total)
+    st0 = B.MpmState(*(torch.from_numpy(a).to(dev) for a in inputs.rest_state(sc.x)))
+    pin0 = torch.from_numpy(sc.pinned).to(dev)
+    ro = Rollout(mpm, n, wind, args.substeps, sort_every=SORT_EVERY, with_pins=True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ro.load(st0, pin0)
+        ro.run()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mpm.device_status()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: device time per step, L2 flushed between steps
+    times = []
+    barrier()
+    wall0 = time.perf_counter()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    mpm.device_status()
+    ms_step = sum(times) / len(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = t.item()
+    units = n * args.substeps * world
+    value = units / (ms_step * 1e-3)
+
+    # ---- end to end through the public API: pinned host in, result out
+    host_in = [a.cpu().pin_memory() for a in st0]
+    host_pin = pin0.cpu().pin_memory()
+    host_out = [torch.empty_like(a, device="cpu").pin_memory() for a in st0]
+    host_ids = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    dev_in = B.MpmState(*(torch.empty_like(a) for a in st0))
+    dev_pin = torch.empty_like(pin0)
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        dev_pin.copy_(host_pin, non_blocking=True)
+        ro.load(dev_in, dev_pin)
+        res, ids = ro.run()
+        for h, d in zip(host_out, res):
+            h.copy_(d, non_blocking=True)
+        host_ids.copy_(ids, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    h2d = sum(a.numel() * a.element_size() for a in host_in) + host_pin.numel()
+    d2h = sum(a.numel() * a.element_size() for a in host_out) + host_ids.numel() * 4
+
+    # ---- roofline of the dominant kernel: per-kernel CUDA events over one
+    # eager pass of the same rollout (same kernels, same inputs)
+    ro_eager = Rollout(mpm, n, wind, args.substeps, sort_every=SORT_EVERY, with_pins=True,
+                       use_graph=False)
+    mpm.profile_enable(4 * args.substeps + 64)
+    flush.fill_(1.0)
+    ro_eager.load(st0, pin0)
+    ro_eager.run()
+    prof = mpm.profile_read()
+    mpm.profile_enable(0)
+    active_nodes = estimate_active_nodes(ro_eager, sc)
+    roof = roofline(prof, n, active_nodes)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_gpu": n, "grid": sc.n_grid,
+                   "substeps_per_step": args.substeps, "sort_every": SORT_EVERY,
+                   "material": "neo-hookean E=5e4 nu=0.3", "wind": "32^3 x 16 Fourier",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": ro.kernel_launches * args.steps,
+        "clocks": clocks,
+        "roofline": roof,
+        "kernel_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
+        "wall_s_timed": wall,
+    }
+    if not args.no_extras:
+        result["metrics"] = extras(dev)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def estimate_active_nodes(ro, sc):
+    """Grid nodes inside the stencils of the final particle positions (for the
+    per-node part of the algorithmic bytes)."""
+    x = ro.result()[0].x.detach().cpu().numpy().astype(np.float64)
+    N = sc.n_grid
+    base = np.unique(np.floor(x * N - 0.5).astype(np.int64).T, axis=0)
+    offs = np.stack(np.meshgrid(*[np.arange(3)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    nodes = (base[:, None, :] + offs[None, :, :]).reshape(-1, 3)
+    lin = (nodes[:, 2] * N + nodes[:, 1]) * N + nodes[:, 0]
+    return int(np.unique(lin).size)
+
+
+def roofline(prof, n, active_nodes):
+    """Algorithmic bytes per launch of each substep kernel:
+      P2G  : x, v, C, F read (96 B / particle) + (m, p) written (16 B / node)
+      G2P  : x, F read (48 B / particle) + x, v, C, F written (96 B / particle)
+             + grid velocity read (16 B / node)
+      grid : (m, p) read, v written, (m, p) cleared (48 B / node of the grid)."""
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    per = {"p2g": 96 * n + 16 * active_nodes, "g2p": 144 * n + 16 * active_nodes}
+    best = None
+    for k in ("p2g", "g2p", "grid"):
+        ms, cnt = prof.get(k, (0.0, 0))
+        if cnt and (best is None or ms > best[1]):
+            best = (k, ms, cnt)
+    k, ms, cnt = best
+    avg_s = ms / cnt * 1e-3
+    if k in per:
+        traffic = per[k]
+    else:
+        traffic = None
+    achieved = traffic / avg_s / 1e9 if traffic else None
+    return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "algorithmic_bytes_per_launch": traffic, "avg_launch_us": avg_s * 1e6,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+
+
+def extras(dev):
+    import torch
+
+    from paper_2603_09668_gb300 import autograd as AG
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import inputs
+
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    # LBM 128^3 with the leaf-cluster obstacle
+    shape = (128, 128, 128)
+    pts = torch.from_numpy(inputs.ellipsoid_cluster()).to(dev)
+    solid = torch.empty((128, 128, 128), dtype=torch.uint8, device=dev)
+    B.voxelize_particles(pts, shape, 1.0 / 128, solid)
+    lbm = B.LBM(shape, 0.55, u_inlet=(0.05, 0.0, 0.0), bc_x=1, max_tape=20)
+    f = lbm.lattice(dev)
+    steps = 200
+    ms = timed(lambda: lbm.step(f, solid, steps))
+    cells = 128 ** 3
+    out["lbm_128_fwd_mlups"] = cells * steps / (ms * 1e-3) / 1e6
+    out["lbm_128_fwd_gbs"] = 152 * cells * steps / (ms * 1e-3) / 1e9
+    g = torch.randn_like(f)
+    ms = timed(lambda: lbm.step_adjoint(f, g, solid, 20))
+    out["lbm_128_adj_mlups"] = cells * 20 / (ms * 1e-3) / 1e6
+    lbm.close()
+
+    # MPM forward + adjoint with checkpointing (100k sheet, 64^3, 200 substeps)
+    sc = inputs.sheet_scene(nu=274, nv=183, n_grid=64, n_substeps=200, dt=5e-5, seed=0,
+                            wind_seed=0)
+    mpm = B.MPM.from_params(sc.params(), max_particles=sc.n)
+    st = B.MpmState(*(torch.from_numpy(a).to(dev) for a in inputs.rest_state(sc.x)))
+    pin = torch.from_numpy(sc.pinned).to(dev)
+    wv = torch.from_numpy(sc.wind).to(dev).requires_grad_(True)
+    E = torch.tensor(sc.E, device=dev, requires_grad=True)
+    target = torch.zeros((10, 3, sc.n), device=dev)
+
+    def fwd_adj():
+        X = AG.mpm_frames(mpm, st, wv, sc.t_total, E, 200, 20, pinned=pin)
+        loss = ((X - target) ** 2).sum() / sc.n
+        loss.backward()
+
+    ms = timed(fwd_adj, reps=2)
+    out["mpm_adj_sheet100k_64_ps_per_s"] = sc.n * 200 / (ms * 1e-3)
+    out["mpm_adj_note"] = "200 substeps forward + checkpointed adjoint (recompute + reverse)"
+    mpm.close()
+    return out
+
+
+def cpu_baseline(n_sub=30):
+    """The FP64 oracle on this host: n_sub substeps of the full 400k sheet."""
+    import oracle
+    from paper_2603_09668_gb300 import inputs
+
+    sc = inputs.sheet_scene()
+    st = tuple(a.astype(np.float64) for a in inputs.rest_state(sc.x))
+    t0 = time.perf_counter()
+    for k in range(n_sub):
+        st = oracle.mpm_substep(sc.params(), st, sc.wind_tuple(), k * sc.dt, sc.pinned)
+    dt = time.perf_counter() - t0
+    return {"value": sc.n * n_sub / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sub} substeps of the full 400,040-particle sheet on 128^3 (FP64, serial C)",
+            "seconds": dt}
+
+
+# ------------------------------------------------------- reference arm ----
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2603_09668_gb300 import inputs
+
+    oracle.build()
+    sc = inputs.sheet_scene()
+    n_sub = 3  # each step: 3 substeps of the full sheet (~1-2 s of FP64 CPU work)
+    st0 = tuple(a.astype(np.float64) for a in inputs.rest_state(sc.x))
+
+    def step():
+        st = st0
+        for k in range(n_sub):
+            st = oracle.mpm_substep(sc.params(), st, sc.wind_tuple(), k * sc.dt, sc.pinned)
+
+    for _ in range(args.warmup):
+        step()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        ts.append(time.perf_counter() - t0)
+    s_step = sum(ts) / len(ts)
+    value = sc.n * n_sub / s_step
+    sample = f"{n_sub} substeps of the full 400,040-particle sheet on 128^3 per step (FP64, serial C)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

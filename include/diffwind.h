@@ -1,0 +1,254 @@
+/*
+ * diffwind.h - C-ABI of the GB300 DiffWind hot path (libdiffwind.so).
+ *
+ * The library implements the data-parallel core of DiffWind (arXiv 2603.09668):
+ * the differentiable MLS-MPM substep that moves object particles under a
+ * spatio-temporal wind-force field (Sec. 3.3, Eq. simulation_mpm; App. A.3,
+ * Eqs. P2G, G2P, deformation_update, constitutive_model, young_poisson), the
+ * D3Q19 lattice Boltzmann step that supplies the wind-field physics
+ * constraint (Sec. 3.1, Eqs. lbe, lbm_sum_v2; Sec. 3.4), the particle-to-voxel
+ * obstacle mask (Sec. 3.4, Eq. point2voxel), and hand-written adjoints of
+ * each. All compute runs in CUDA kernels built for sm_103a.
+ *
+ * Conventions for every call:
+ *  - Pointers named as device pointers must point to device memory (cudaMalloc,
+ *    or a framework's device tensor); the caller owns them. The library owns
+ *    only the workspace it allocates in *_create and frees in *_destroy.
+ *  - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *    dw_stream; NULL is the legacy default stream). Host-visible status only
+ *    covers argument checks and launch errors; conditions found on the device
+ *    (a particle outside the grid, a non-finite value, an inverted element)
+ *    set a per-handle device status word read by *_device_status.
+ *  - Every call returns DW_OK or an error code; dw_last_error() returns a
+ *    message for the last failing call on the calling thread. No call aborts,
+ *    throws or traps.
+ *  - Floating point data is float32 (IEEE binary32). Particle arrays are
+ *    structure of arrays: x[3][n] means x[a*n + p] for axis a of particle p;
+ *    3x3 matrices are [9][n], row-major per particle: C[(3a+b)*n + p] = C_ab.
+ *  - A handle may be used from one stream at a time; calls on one handle that
+ *    overlap on the GPU race on its workspace.
+ */
+#ifndef DIFFWIND_H
+#define DIFFWIND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of this header are the library's only exported names. */
+#if defined(__GNUC__)
+#define DW_API __attribute__((visibility("default")))
+#else
+#define DW_API
+#endif
+
+typedef enum {
+    DW_OK = 0,
+    DW_ERR_ARG = 1,       /* bad argument: null pointer, size out of range, unsupported option */
+    DW_ERR_CUDA = 2,      /* a CUDA runtime call or kernel launch failed */
+    DW_ERR_OOM = 3,       /* a workspace allocation failed */
+    DW_ERR_NONFINITE = 4, /* device: a NaN or Inf was produced or read */
+    DW_ERR_DOMAIN = 5,    /* device: a particle's 3x3x3 stencil left the grid */
+    DW_ERR_TIMEOUT = 6,   /* device: a bounded wait gave up */
+    DW_ERR_INVERTED = 7   /* device: det F <= 0 where the constitutive model needs J > 0 */
+} dw_status;
+
+typedef void *dw_stream; /* cudaStream_t */
+
+/* Message of the last failing call on this thread ("" if none). */
+DW_API const char *dw_last_error(void);
+/* Library version string. */
+DW_API const char *dw_version(void);
+
+/* ===================================================================== wind
+ * Wind force field a_w(x, t) (Sec. 3: the wind is a grid field whose force
+ * property acts on the MPM background grid; Sec. 3.3: one field per time step).
+ * Nodes are node-centred on the unit cube: node j of nf sits at j / (nf - 1).
+ * Sampling is trilinear in space and linear in time between n_frames keyframes
+ * at k * t_total / (n_frames - 1); positions outside [0,1]^3 and times outside
+ * [0, t_total] are clamped. The value is a force per unit mass (N/kg).
+ */
+typedef struct {
+    const float *values; /* device [n_frames][nf][nf][nf][3], x index fastest */
+    int32_t nf;          /* nodes per axis, >= 2 (1 = spatially constant) */
+    int32_t n_frames;    /* keyframes, >= 1 */
+    float t_total;       /* time of the last keyframe; > 0 when n_frames > 1 */
+} dw_wind_field;
+
+/* out[3][n] = a_w(pos[:, p], t) for n positions pos[3][n] (device pointers).
+ * Errors: DW_ERR_ARG for null pointers with n > 0, nf < 1, n_frames < 1,
+ * t_total <= 0 with n_frames > 1. */
+DW_API dw_status wind_field_sample(const dw_wind_field *w, const float *pos, int64_t n, float t,
+                            float *out, dw_stream stream);
+
+/* Adjoint: g_values += S^T g_out, where S is the linear map values -> out of
+ * wind_field_sample at the same positions and time. g_values has the shape of
+ * w->values and is accumulated into (atomically). */
+DW_API dw_status wind_field_sample_adjoint(const dw_wind_field *w, const float *pos, int64_t n, float t,
+                                    const float *g_out, float *g_values, dw_stream stream);
+
+/* ====================================================================== MPM
+ * One MLS-MPM substep S (Eq. simulation_mpm): (x, v, F, C)^t -> (x, v, F, C)^{t+1}.
+ *   P2G (Eq. P2G) with quadratic B-spline weights on the 3x3x3 stencil, APIC
+ *   affine momentum and the MLS stress term -dt V0 (4/dx^2) P F^T (x_i - x_p);
+ *   grid update v_i = p_i/m_i + dt (g + a_w(x_i, t)) for nodes with m_i > 0,
+ *   v_i = 0 in a sticky band of bc_band nodes at each face;
+ *   G2P (Eq. G2P): v_p = sum w v_i, C_p = (4/dx^2) sum w v_i (x_i - x_p)^T,
+ *   x_p += dt v_p, F_p <- (I + dt C_p) F_p (Eq. deformation_update, with the C
+ *   of this G2P). Pinned particles keep v = 0, C = 0.
+ *   Stress P(F): Neo-Hookean mu (F - F^-T) + lam ln(J) F^-T (the gradient of
+ *   the energy of Eq. constitutive_model) or fixed-corotated
+ *   2 mu (F - R) + lam (J - 1) J F^-T; mu, lam from E, nu (Eq. young_poisson).
+ * The grid has n_grid^3 nodes on the unit cube, dx = 1 / n_grid, node (i,j,k)
+ * at (i, j, k) dx. A particle must keep floor(x / dx - 0.5) in [0, n_grid - 3]
+ * on every axis; otherwise DW_ERR_DOMAIN is raised on the device and the
+ * particle is left unchanged.
+ */
+enum { DW_NEOHOOKEAN = 0, DW_FIXED_COROTATED = 1 };
+enum { DW_P2G_AUTO = 0, DW_P2G_ATOMIC = 1, DW_P2G_WARP = 2, DW_P2G_TILE = 3 };
+
+typedef struct {
+    int32_t n_grid;        /* nodes per axis, 8 <= n_grid <= 512 */
+    float dt;              /* substep length (s) */
+    float gravity[3];      /* body acceleration (m/s^2) */
+    int32_t bc_band;       /* sticky wall band width in nodes, >= 0 */
+    int32_t material;      /* DW_NEOHOOKEAN or DW_FIXED_COROTATED */
+    float E, nu;           /* Young's modulus (Pa) and Poisson ratio, 0 <= nu < 0.5 */
+    float p_mass, p_vol;   /* particle mass m_p and rest volume V_p^0 */
+    int64_t max_particles; /* capacity of the per-particle workspace */
+    int32_t p2g_mode;      /* DW_P2G_*: P2G accumulation strategy (results agree to rounding) */
+} dw_mpm_desc;
+
+typedef struct {
+    float *x; /* device [3][n] positions */
+    float *v; /* device [3][n] velocities */
+    float *C; /* device [9][n] affine velocity matrices */
+    float *F; /* device [9][n] deformation gradients */
+    int64_t n;
+} dw_mpm_state;
+
+typedef struct dw_mpm_s *dw_mpm;
+
+/* Allocate a handle and its workspace (grid, adjoint grid, per-particle
+ * scratch for max_particles). Errors: DW_ERR_ARG, DW_ERR_OOM, DW_ERR_CUDA. */
+DW_API dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out);
+DW_API dw_status mpm_destroy(dw_mpm h);
+
+/* Change E and nu of an existing handle (takes effect for later calls). */
+DW_API dw_status mpm_set_material(dw_mpm h, float E, float nu);
+
+/* One substep at time t (the wind is sampled at t). `out` may be the same
+ * arrays as `in` (in place) but must not partially overlap them. pinned is a
+ * device uint8[n] (nonzero = pinned) or NULL. n <= max_particles. */
+DW_API dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
+                      const uint8_t *pinned, const dw_wind_field *wind, float t,
+                      dw_stream stream);
+
+/* Reverse mode of mpm_substep at the same input state, wind and time. Given
+ * g_out = dL/d(output state), writes g_in = dL/d(input state) (overwritten;
+ * may be the same arrays as g_out), and accumulates dL/d(wind values) into
+ * g_wind (device, shape of wind->values; NULL to skip) and dL/dE into *g_E
+ * (device float; NULL to skip). The forward grid is recomputed from `in`. */
+DW_API dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *g_out,
+                              const dw_mpm_state *g_in, const uint8_t *pinned,
+                              const dw_wind_field *wind, float t, float *g_wind, float *g_E,
+                              dw_stream stream);
+
+/* Reorder particles by grid cell (the cell of floor(x/dx - 0.5), cells
+ * grouped into 4^3 blocks) so that neighbouring P2G threads share stencils.
+ * Writes the permuted state into `out` (must not overlap `in`) and the
+ * permuted pin flags into pinned_out (when pinned_in is not NULL). With
+ * perm[k] the index in `in` of the particle now at k, ids_out[k] =
+ * ids_in[perm[k]] when ids_in (device int32[n]) is given, else perm[k]; so
+ * carrying ids through successive sorts tracks every particle's original
+ * index. The order of particles that share a cell is unspecified. */
+DW_API dw_status mpm_sort(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
+                          const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
+                          int32_t *ids_out, dw_stream stream);
+
+/* Waits for `stream`, returns the first device-side error recorded on this
+ * handle since the last call (DW_OK if none) and clears it. */
+DW_API dw_status mpm_device_status(dw_mpm h, dw_stream stream);
+
+/* Instrumentation (no counterpart in the paper): while enabled, every kernel
+ * the handle launches is bracketed by CUDA events recorded on the call's
+ * stream, up to `max_records` launches (events are created here, so enable
+ * before any stream capture; calls made while enabled must not be captured).
+ * mpm_profile_read waits for the recorded events and returns, per kernel id
+ * DW_K_*, the summed device milliseconds and the launch count since enable,
+ * then clears them. Arrays have DW_K_COUNT entries. */
+enum { DW_K_P2G = 0, DW_K_GRID = 1, DW_K_G2P = 2, DW_K_REV_G2P = 3, DW_K_REV_GRID = 4,
+       DW_K_REV_P2G = 5, DW_K_SORT = 6, DW_K_COUNT = 7 };
+DW_API dw_status mpm_profile_enable(dw_mpm h, int32_t max_records);
+DW_API dw_status mpm_profile_read(dw_mpm h, double *total_ms, int64_t *launches);
+
+/* ====================================================================== LBM
+ * D3Q19 lattice Boltzmann step (Eq. lbe) with the BGK collision
+ * f* = f - (f - f_eq)/tau (+ Guo forcing for a uniform body force F, with
+ * rho u = sum c f + F/2 as in Eq. lbm_sum_v2), f_eq = w rho (1 + 3 c.u +
+ * 4.5 (c.u)^2 - 1.5 u.u), then streaming f_i(x + c_i) = f*_i(x).
+ * Boundaries: halfway bounce-back on solid cells; y and z periodic; x periodic
+ * (bc_x = 0) or (bc_x = 1) an equilibrium inlet at x = 0 (populations entering
+ * through the x = 0 face are f_eq(1, u_inlet)) and a zero-gradient outlet at
+ * x = nx - 1 (populations entering through that face equal the cell's own
+ * post-collision populations of the same direction).
+ * Velocity order: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (+x+y),(-x-y),
+ * (+x+z),(-x-z),(+y+z),(-y-z),(+x-y),(-x+y),(+x-z),(-x+z),(+y-z),(-y+z);
+ * directions 2k-1 and 2k are opposite. Weights 1/3, 1/18, 1/36.
+ * Storage: f is device float [19][nz][ny][nx] (x fastest) holding the shifted
+ * populations f_i - w_i (deviation from the rest equilibrium, which keeps
+ * float32 resolution; a lattice at rest is all zeros). Solid cells' entries
+ * are never read or written. solid is device uint8 [nz][ny][nx] (nonzero =
+ * solid) or NULL (all fluid).
+ */
+typedef struct {
+    int32_t nx, ny, nz; /* lattice size, each >= 2; nx*ny*nz < 2^31 */
+    float tau;          /* BGK relaxation time, > 0.5 */
+    float u_inlet[3];   /* inlet velocity (lattice units), used when bc_x = 1 */
+    float force[3];     /* uniform body force density (lattice units) */
+    int32_t bc_x;       /* 0 periodic in x, 1 inlet/outlet in x */
+    int32_t max_tape;   /* lattices of workspace for lbm_step_adjoint (>= 1) */
+} dw_lbm_desc;
+
+typedef struct dw_lbm_s *dw_lbm;
+
+DW_API dw_status lbm_create(const dw_lbm_desc *desc, dw_lbm *out);
+DW_API dw_status lbm_destroy(dw_lbm h);
+
+/* Advance f in place by `steps` >= 0 lattice steps. Pairs of steps run as the
+ * in-place AA pattern (one collide-only kernel, one pull-collide-push kernel);
+ * an odd last step runs through the workspace. */
+DW_API dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t steps, dw_stream stream);
+
+/* Reverse mode of lbm_step(f_in, steps): on entry g_f = dL/df(t + steps), on
+ * return dL/df(t) (in place). f_in is the state the forward started from;
+ * the intermediate states are recomputed into the workspace, so steps must be
+ * <= max_tape. Gradients are taken with respect to the shifted populations,
+ * which equal those with respect to f. */
+DW_API dw_status lbm_step_adjoint(dw_lbm h, const float *f_in, float *g_f, const uint8_t *solid,
+                           int32_t steps, dw_stream stream);
+
+/* rho [nz][ny][nx] and u [3][nz][ny][nx] (Eq. lbm_sum_v2; rho u includes F/2).
+ * Either output may be NULL. Solid cells get rho = 0, u = 0. */
+DW_API dw_status lbm_macroscopic(dw_lbm h, const float *f, const uint8_t *solid, float *rho, float *u,
+                          dw_stream stream);
+
+/* Fill f with the shifted equilibrium f_eq(rho0, u0) - w at every cell. */
+DW_API dw_status lbm_init_equilibrium(dw_lbm h, float *f, float rho0, const float u0[3],
+                               dw_stream stream);
+
+/* Solid mask of Eq. point2voxel: solid[w] = 1 iff some particle lies in
+ * [x_w, x_w + dx)^3 with x_w = w dx, i.e. w = floor(x_p / dx); the mask is
+ * cleared first; particles outside the lattice are ignored. pos is device
+ * [3][n]. */
+DW_API dw_status voxelize_particles(const float *pos, int64_t n, int32_t nx, int32_t ny, int32_t nz,
+                             float dx, uint8_t *solid, dw_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFWIND_H */

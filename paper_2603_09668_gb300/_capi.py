@@ -1,0 +1,111 @@
+"""ctypes declarations of the libdiffwind C-ABI (include/diffwind.h).
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+from . import build as _build
+
+c_float_p = ct.POINTER(ct.c_float)
+
+
+class DwWindField(ct.Structure):
+    _fields_ = [("values", ct.c_void_p), ("nf", ct.c_int32), ("n_frames", ct.c_int32),
+                ("t_total", ct.c_float)]
+
+
+class DwMpmDesc(ct.Structure):
+    _fields_ = [("n_grid", ct.c_int32), ("dt", ct.c_float), ("gravity", ct.c_float * 3),
+                ("bc_band", ct.c_int32), ("material", ct.c_int32), ("E", ct.c_float),
+                ("nu", ct.c_float), ("p_mass", ct.c_float), ("p_vol", ct.c_float),
+                ("max_particles", ct.c_int64), ("p2g_mode", ct.c_int32)]
+
+
+class DwMpmState(ct.Structure):
+    _fields_ = [("x", ct.c_void_p), ("v", ct.c_void_p), ("C", ct.c_void_p), ("F", ct.c_void_p),
+                ("n", ct.c_int64)]
+
+
+class DwLbmDesc(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("tau", ct.c_float),
+                ("u_inlet", ct.c_float * 3), ("force", ct.c_float * 3), ("bc_x", ct.c_int32),
+                ("max_tape", ct.c_int32)]
+
+
+P = ct.POINTER
+VP = ct.c_void_p
+I32 = ct.c_int32
+I64 = ct.c_int64
+F32 = ct.c_float
+
+# name -> (restype, argtypes); every function returns dw_status (int) unless noted
+SIGNATURES = {
+    "dw_last_error": (ct.c_char_p, []),
+    "dw_version": (ct.c_char_p, []),
+    "wind_field_sample": (I32, [P(DwWindField), VP, I64, F32, VP, VP]),
+    "wind_field_sample_adjoint": (I32, [P(DwWindField), VP, I64, F32, VP, VP, VP]),
+    "mpm_create": (I32, [P(DwMpmDesc), P(VP)]),
+    "mpm_destroy": (I32, [VP]),
+    "mpm_set_material": (I32, [VP, F32, F32]),
+    "mpm_substep": (I32, [VP, P(DwMpmState), P(DwMpmState), VP, P(DwWindField), F32, VP]),
+    "mpm_substep_adjoint": (I32, [VP, P(DwMpmState), P(DwMpmState), P(DwMpmState), VP,
+                                  P(DwWindField), F32, VP, VP, VP]),
+    "mpm_sort": (I32, [VP, P(DwMpmState), P(DwMpmState), VP, VP, VP, VP, VP]),
+    "mpm_device_status": (I32, [VP, VP]),
+    "mpm_profile_enable": (I32, [VP, I32]),
+    "mpm_profile_read": (I32, [VP, P(ct.c_double), P(I64)]),
+    "lbm_create": (I32, [P(DwLbmDesc), P(VP)]),
+    "lbm_destroy": (I32, [VP]),
+    "lbm_step": (I32, [VP, VP, VP, I32, VP]),
+    "lbm_step_adjoint": (I32, [VP, VP, VP, VP, I32, VP]),
+    "lbm_macroscopic": (I32, [VP, VP, VP, VP, VP, VP]),
+    "lbm_init_equilibrium": (I32, [VP, VP, F32, P(F32 * 3), VP]),
+    "voxelize_particles": (I32, [VP, I64, I32, I32, I32, F32, VP, VP]),
+}
+
+STATUS = {0: "DW_OK", 1: "DW_ERR_ARG", 2: "DW_ERR_CUDA", 3: "DW_ERR_OOM", 4: "DW_ERR_NONFINITE",
+          5: "DW_ERR_DOMAIN", 6: "DW_ERR_TIMEOUT", 7: "DW_ERR_INVERTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DiffWindError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libdiffwind. Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"libdiffwind.so is not built ({path} missing); run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` first")
+            L = ct.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != 0:
+        msg = lib().dw_last_error().decode(errors="replace")
+        raise DiffWindError(status, msg)
+    return status

@@ -1,0 +1,330 @@
+"""Python binding of the libdiffwind C-ABI, one function per C entry point
+with the same name. Arguments are torch CUDA tensors (float32 / uint8 /
+int32, contiguous); the binding only checks and marshals them: every step of
+the computation runs in the library's CUDA kernels.
+
+Layouts follow include/diffwind.h: particle state x, v as [3, n], C, F as
+[9, n]; wind values [n_frames, nf, nf, nf, 3]; LBM populations [19, nz, ny, nx]
+(shifted, f - w); masks uint8 [nz, ny, nx].
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import NamedTuple, Optional
+
+import torch
+
+from ._capi import (DiffWindError, DwLbmDesc, DwMpmDesc, DwMpmState, DwWindField, check, lib)
+
+__all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
+           "wind_field_sample_adjoint", "mpm_create", "mpm_destroy", "mpm_set_material",
+           "mpm_substep", "mpm_substep_adjoint", "mpm_sort", "mpm_device_status",
+           "mpm_profile_enable", "mpm_profile_read", "lbm_create",
+           "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
+           "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM"]
+
+NEOHOOKEAN, FIXED_COROTATED = 0, 1
+P2G_AUTO, P2G_ATOMIC, P2G_WARP, P2G_TILE = 0, 1, 2, 3
+
+
+def _dev(t: Optional[torch.Tensor], dtype=torch.float32, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (libdiffwind has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+class MpmState(NamedTuple):
+    x: torch.Tensor  # [3, n]
+    v: torch.Tensor  # [3, n]
+    C: torch.Tensor  # [9, n]
+    F: torch.Tensor  # [9, n]
+
+    @property
+    def n(self):
+        return self.x.shape[1]
+
+    def to_c(self):
+        n = self.x.shape[1]
+        for name, t, rows in (("x", self.x, 3), ("v", self.v, 3), ("C", self.C, 9), ("F", self.F, 9)):
+            if t.dim() != 2 or t.shape[0] != rows or t.shape[1] != n:
+                raise ValueError(f"state.{name} must have shape [{rows}, {n}], got {tuple(t.shape)}")
+        return DwMpmState(_dev(self.x, name="x"), _dev(self.v, name="v"), _dev(self.C, name="C"),
+                          _dev(self.F, name="F"), n)
+
+    @staticmethod
+    def empty_like(s: "MpmState") -> "MpmState":
+        return MpmState(*(torch.empty_like(a) for a in s))
+
+    @staticmethod
+    def zeros_like(s: "MpmState") -> "MpmState":
+        return MpmState(*(torch.zeros_like(a) for a in s))
+
+    def clone(self) -> "MpmState":
+        return MpmState(*(a.clone() for a in self))
+
+
+class WindField(NamedTuple):
+    values: torch.Tensor  # [n_frames, nf, nf, nf, 3]
+    t_total: float
+
+    @property
+    def nf(self):
+        return self.values.shape[1]
+
+    @property
+    def n_frames(self):
+        return self.values.shape[0]
+
+    def to_c(self):
+        v = self.values
+        if v.dim() != 5 or v.shape[4] != 3 or not (v.shape[1] == v.shape[2] == v.shape[3]):
+            raise ValueError(f"wind values must be [n_frames, nf, nf, nf, 3], got {tuple(v.shape)}")
+        return DwWindField(_dev(v, name="wind.values"), v.shape[1], v.shape[0], float(self.t_total))
+
+
+# -------------------------------------------------------------------- wind --
+
+def wind_field_sample(wind: WindField, pos: torch.Tensor, t: float, out=None, stream=None):
+    n = pos.shape[1]
+    if out is None:
+        out = torch.empty((3, n), dtype=torch.float32, device=pos.device)
+    w = wind.to_c()
+    check(lib().wind_field_sample(ct.byref(w), _dev(pos, name="pos"), n, t, _dev(out, name="out"),
+                                  _stream(stream)))
+    return out
+
+
+def wind_field_sample_adjoint(wind: WindField, pos, t, g_out, g_values, stream=None):
+    w = wind.to_c()
+    check(lib().wind_field_sample_adjoint(ct.byref(w), _dev(pos, name="pos"), pos.shape[1], t,
+                                          _dev(g_out, name="g_out"), _dev(g_values, name="g_values"),
+                                          _stream(stream)))
+    return g_values
+
+
+# --------------------------------------------------------------------- MPM --
+
+def mpm_create(n_grid, dt, gravity=(0.0, -9.8, 0.0), bc_band=3, material=NEOHOOKEAN, E=1e4,
+               nu=0.3, p_mass=1.0, p_vol=1.0, max_particles=0, p2g_mode=P2G_AUTO):
+    d = DwMpmDesc(int(n_grid), float(dt), (ct.c_float * 3)(*gravity), int(bc_band), int(material),
+                  float(E), float(nu), float(p_mass), float(p_vol), int(max_particles), int(p2g_mode))
+    h = ct.c_void_p()
+    check(lib().mpm_create(ct.byref(d), ct.byref(h)))
+    return h
+
+
+def mpm_destroy(h):
+    check(lib().mpm_destroy(h))
+
+
+def mpm_set_material(h, E, nu):
+    check(lib().mpm_set_material(h, float(E), float(nu)))
+
+
+def _pin(pinned):
+    return _dev(pinned, torch.uint8, "pinned") if pinned is not None else None
+
+
+def mpm_substep(h, state_in: MpmState, state_out: MpmState, pinned, wind: WindField, t,
+                stream=None):
+    a, b, w = state_in.to_c(), state_out.to_c(), wind.to_c()
+    check(lib().mpm_substep(h, ct.byref(a), ct.byref(b), _pin(pinned), ct.byref(w), float(t),
+                            _stream(stream)))
+    return state_out
+
+
+def mpm_substep_adjoint(h, state_in: MpmState, g_out: MpmState, g_in: MpmState, pinned,
+                        wind: WindField, t, g_wind=None, g_E=None, stream=None):
+    a, go, gi, w = state_in.to_c(), g_out.to_c(), g_in.to_c(), wind.to_c()
+    check(lib().mpm_substep_adjoint(h, ct.byref(a), ct.byref(go), ct.byref(gi), _pin(pinned),
+                                    ct.byref(w), float(t), _dev(g_wind, name="g_wind"),
+                                    _dev(g_E, name="g_E"), _stream(stream)))
+    return g_in
+
+
+def mpm_sort(h, state_in: MpmState, state_out: MpmState, pinned_in, pinned_out, ids_in, ids_out,
+             stream=None):
+    a, b = state_in.to_c(), state_out.to_c()
+    check(lib().mpm_sort(h, ct.byref(a), ct.byref(b), _pin(pinned_in), _pin(pinned_out),
+                         _dev(ids_in, torch.int32, "ids_in"), _dev(ids_out, torch.int32, "ids_out"),
+                         _stream(stream)))
+    return state_out, pinned_out, ids_out
+
+
+def mpm_device_status(h, stream=None):
+    check(lib().mpm_device_status(h, _stream(stream)))
+
+
+KERNEL_NAMES = ["p2g", "grid", "g2p", "rev_g2p", "rev_grid", "rev_p2g", "sort"]
+
+
+def mpm_profile_enable(h, max_records):
+    check(lib().mpm_profile_enable(h, int(max_records)))
+
+
+def mpm_profile_read(h):
+    """{kernel name: (total device ms, launches)} since enable / the last read."""
+    ms = (ct.c_double * len(KERNEL_NAMES))()
+    cnt = (ct.c_int64 * len(KERNEL_NAMES))()
+    check(lib().mpm_profile_read(h, ms, cnt))
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_NAMES)}
+
+
+# --------------------------------------------------------------------- LBM --
+
+def lbm_create(shape, tau, u_inlet=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), bc_x=0, max_tape=2):
+    nx, ny, nz = shape
+    d = DwLbmDesc(int(nx), int(ny), int(nz), float(tau), (ct.c_float * 3)(*u_inlet),
+                  (ct.c_float * 3)(*force), int(bc_x), int(max_tape))
+    h = ct.c_void_p()
+    check(lib().lbm_create(ct.byref(d), ct.byref(h)))
+    return h
+
+
+def lbm_destroy(h):
+    check(lib().lbm_destroy(h))
+
+
+def _mask(solid):
+    return _dev(solid, torch.uint8, "solid") if solid is not None else None
+
+
+def lbm_step(h, f, solid, steps, stream=None):
+    check(lib().lbm_step(h, _dev(f, name="f"), _mask(solid), int(steps), _stream(stream)))
+    return f
+
+
+def lbm_step_adjoint(h, f_in, g_f, solid, steps, stream=None):
+    check(lib().lbm_step_adjoint(h, _dev(f_in, name="f_in"), _dev(g_f, name="g_f"), _mask(solid),
+                                 int(steps), _stream(stream)))
+    return g_f
+
+
+def lbm_macroscopic(h, f, solid, rho=None, u=None, stream=None):
+    check(lib().lbm_macroscopic(h, _dev(f, name="f"), _mask(solid), _dev(rho, name="rho"),
+                                _dev(u, name="u"), _stream(stream)))
+    return rho, u
+
+
+def lbm_init_equilibrium(h, f, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+    arr = (ct.c_float * 3)(*u0)
+    check(lib().lbm_init_equilibrium(h, _dev(f, name="f"), float(rho0), ct.byref(arr),
+                                     _stream(stream)))
+    return f
+
+
+def voxelize_particles(pos, shape, dx, solid, stream=None):
+    nx, ny, nz = shape
+    check(lib().voxelize_particles(_dev(pos, name="pos"), pos.shape[1], int(nx), int(ny), int(nz),
+                                   float(dx), _dev(solid, torch.uint8, "solid"), _stream(stream)))
+    return solid
+
+
+# ---------------------------------------------------------- owning handles --
+
+class MPM:
+    """Owns an MPM handle; the methods call the C-ABI functions above."""
+
+    def __init__(self, n_grid, dt, *, gravity=(0.0, -9.8, 0.0), bc_band=3, material=NEOHOOKEAN,
+                 E=1e4, nu=0.3, p_mass=1.0, p_vol=1.0, max_particles=0, p2g_mode=P2G_AUTO):
+        self.n_grid, self.dt = n_grid, dt
+        self.E, self.nu = E, nu
+        self.h = mpm_create(n_grid, dt, gravity, bc_band, material, E, nu, p_mass, p_vol,
+                            max_particles, p2g_mode)
+
+    @classmethod
+    def from_params(cls, params: dict, max_particles: int, p2g_mode=P2G_AUTO):
+        return cls(params["n_grid"], params["dt"], gravity=params["gravity"],
+                   bc_band=params["bc_band"], material=params["material"], E=params["E"],
+                   nu=params["nu"], p_mass=params["p_mass"], p_vol=params["p_vol"],
+                   max_particles=max_particles, p2g_mode=p2g_mode)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            mpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_material(self, E, nu):
+        mpm_set_material(self.h, E, nu)
+        self.E, self.nu = E, nu
+
+    def substep(self, state_in, state_out, pinned, wind, t, stream=None):
+        return mpm_substep(self.h, state_in, state_out, pinned, wind, t, stream)
+
+    def substep_adjoint(self, state_in, g_out, g_in, pinned, wind, t, g_wind=None, g_E=None,
+                        stream=None):
+        return mpm_substep_adjoint(self.h, state_in, g_out, g_in, pinned, wind, t, g_wind, g_E,
+                                   stream)
+
+    def sort(self, state_in, state_out, pinned_in, pinned_out, ids_in, ids_out, stream=None):
+        return mpm_sort(self.h, state_in, state_out, pinned_in, pinned_out, ids_in, ids_out, stream)
+
+    def device_status(self, stream=None):
+        mpm_device_status(self.h, stream)
+
+    def profile_enable(self, max_records):
+        mpm_profile_enable(self.h, max_records)
+
+    def profile_read(self):
+        return mpm_profile_read(self.h)
+
+
+class LBM:
+    """Owns an LBM handle; the methods call the C-ABI functions above."""
+
+    def __init__(self, shape, tau, *, u_inlet=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), bc_x=0,
+                 max_tape=2):
+        self.shape = tuple(shape)
+        self.tau = tau
+        self.force = force
+        self.h = lbm_create(shape, tau, u_inlet, force, bc_x, max_tape)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lattice(self, device="cuda"):
+        nx, ny, nz = self.shape
+        return torch.zeros((19, nz, ny, nx), dtype=torch.float32, device=device)
+
+    def step(self, f, solid, steps, stream=None):
+        return lbm_step(self.h, f, solid, steps, stream)
+
+    def step_adjoint(self, f_in, g_f, solid, steps, stream=None):
+        return lbm_step_adjoint(self.h, f_in, g_f, solid, steps, stream)
+
+    def macroscopic(self, f, solid, stream=None):
+        nx, ny, nz = self.shape
+        rho = torch.empty((nz, ny, nx), dtype=torch.float32, device=f.device)
+        u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=f.device)
+        lbm_macroscopic(self.h, f, solid, rho, u, stream)
+        return rho, u
+
+    def init_equilibrium(self, f, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+        return lbm_init_equilibrium(self.h, f, rho0, u0, stream)

@@ -1,0 +1,514 @@
+// D3Q19 BGK lattice Boltzmann step (Eq. lbe, moments of Eq. lbm_sum_v2), its
+// reverse mode, macroscopic fields and the particle-to-voxel mask
+// (Eq. point2voxel).
+//
+// Forward steps run in pairs as the in-place AA pattern on one lattice:
+//   even kernel: read the natural slots of the own cell, collide, write each
+//                post-collision population f*_i into the own cell's opposite
+//                slot (no neighbour access);
+//   odd kernel:  pull f_i from slot opp(i) of cell x - c_i, collide, push the
+//                result into slot i of cell x + c_i, which leaves the lattice
+//                in natural order again.
+// Every (cell, slot) pair read by the odd kernel is written only by the same
+// thread, which makes the update race-free in place. Boundary handling folded
+// into the two kernels:
+//   solid neighbour  -> halfway bounce-back (own cell's opposite population);
+//   beyond x = 0     -> inlet equilibrium f_eq(1, u_inlet) (bc_x = 1);
+//   beyond x = nx-1  -> the own post-collision population of the same
+//                       direction; the even kernel saves those five values of
+//                       the outlet face in a side buffer so that the odd kernel
+//                       does not read a slot its upstream neighbour pushes into.
+// Populations are stored shifted, f_i - w_i, for float32 resolution.
+#include <stdio.h>
+
+#include <new>
+
+#include "common.cuh"
+
+namespace dw {
+
+// D3Q19 velocity set; with the loops unrolled every lookup folds to a constant.
+struct D3Q19 {
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    __host__ __device__ static constexpr float w(int i) {
+        return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+};
+
+// Directions leaving through -x (c_x = -1) in slot order of the outlet side buffer.
+__host__ __device__ constexpr int outlet_slot(int i) {
+    return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 14 ? 3 : i == 16 ? 4 : -1;
+}
+
+struct LbmParams {
+    int nx, ny, nz;
+    int ncell;
+    float inv_tau;
+    float pre;         // 1 - 1/(2 tau), Guo forcing prefactor
+    float Fx, Fy, Fz;  // body force
+    int has_force;
+    int bc_x;
+    float feq_in[19];  // shifted inlet equilibrium f_eq(1, u_inlet) - w
+};
+
+// BGK collision (+ Guo forcing) of one node, shifted populations, in place.
+__device__ __forceinline__ void collide(const LbmParams &L, float f[19]) {
+    float rs = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        rs += f[i];
+        jx += (float)D3Q19::cx(i) * f[i];
+        jy += (float)D3Q19::cy(i) * f[i];
+        jz += (float)D3Q19::cz(i) * f[i];
+    }
+    float rho = 1.0f + rs;
+    float inv_rho = 1.0f / rho;
+    float ux = (jx + 0.5f * L.Fx) * inv_rho, uy = (jy + 0.5f * L.Fy) * inv_rho,
+          uz = (jz + 0.5f * L.Fz) * inv_rho;
+    float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float cu = (float)D3Q19::cx(i) * ux + (float)D3Q19::cy(i) * uy + (float)D3Q19::cz(i) * uz;
+        float feq = D3Q19::w(i) * (rs + rho * (3.0f * cu + 4.5f * cu * cu - uu));
+        float fi = f[i] - (f[i] - feq) * L.inv_tau;
+        if (L.has_force) {
+            float cF = (float)D3Q19::cx(i) * L.Fx + (float)D3Q19::cy(i) * L.Fy + (float)D3Q19::cz(i) * L.Fz;
+            float uF = ux * L.Fx + uy * L.Fy + uz * L.Fz;
+            fi += L.pre * D3Q19::w(i) * (3.0f * (cF - uF) + 9.0f * cu * cF);
+        }
+        f[i] = fi;
+    }
+}
+
+// Transposed collision Jacobian at state f: g <- (d f* / d f)^T g.
+__device__ __forceinline__ void collide_adjoint(const LbmParams &L, const float f[19], float g[19]) {
+    float rs = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        rs += f[i];
+        jx += (float)D3Q19::cx(i) * f[i];
+        jy += (float)D3Q19::cy(i) * f[i];
+        jz += (float)D3Q19::cz(i) * f[i];
+    }
+    float rho = 1.0f + rs;
+    float inv_rho = 1.0f / rho;
+    float u[3] = {(jx + 0.5f * L.Fx) * inv_rho, (jy + 0.5f * L.Fy) * inv_rho,
+                  (jz + 0.5f * L.Fz) * inv_rho};
+    float uu = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    float alpha = 0.0f, beta[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float c[3] = {(float)D3Q19::cx(i), (float)D3Q19::cy(i), (float)D3Q19::cz(i)};
+        float cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        float feq = D3Q19::w(i) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - uu);
+        alpha += g[i] * feq;
+        float cF = c[0] * L.Fx + c[1] * L.Fy + c[2] * L.Fz;
+        float F3[3] = {L.Fx, L.Fy, L.Fz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float dfeq = D3Q19::w(i) * rho * (3.0f * c[a] + 9.0f * cu * c[a] - 3.0f * u[a]);
+            float dsrc = L.pre * D3Q19::w(i) * (-3.0f * F3[a] + 9.0f * cF * c[a]);
+            beta[a] += g[i] * (dfeq * L.inv_tau + dsrc);
+        }
+    }
+    alpha *= L.inv_tau * inv_rho;
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+        float bc = beta[0] * ((float)D3Q19::cx(j) - u[0]) + beta[1] * ((float)D3Q19::cy(j) - u[1]) +
+                   beta[2] * ((float)D3Q19::cz(j) - u[2]);
+        g[j] = (1.0f - L.inv_tau) * g[j] + alpha + bc * inv_rho;
+    }
+}
+
+__device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ int cell_index(const LbmParams &L, int x, int y, int z) {
+    return (z * L.ny + y) * L.nx + x;
+}
+
+// ---------------------------------------------------------------- forward --
+
+__global__ void __launch_bounds__(256) k_lbm_aa_even(LbmParams L, float *f,
+                                                    const uint8_t *__restrict__ solid,
+                                                    float *__restrict__ outlet) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    if (solid && solid[cell]) return;
+    const size_t nc = (size_t)L.ncell;
+    float fl[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = f[i * nc + cell];
+    collide(L, fl);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[D3Q19::opp(i) * nc + cell] = fl[i];
+    if (L.bc_x == 1) {
+        int x = cell % L.nx;
+        if (x == L.nx - 1) {
+            int face = cell / L.nx;  // z * ny + y
+            int nface = L.ny * L.nz;
+#pragma unroll
+            for (int i = 0; i < 19; ++i)
+                if (outlet_slot(i) >= 0) outlet[outlet_slot(i) * nface + face] = fl[i];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lbm_aa_odd(LbmParams L, float *f,
+                                                   const uint8_t *__restrict__ solid,
+                                                   const float *__restrict__ outlet) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    if (solid && solid[cell]) return;
+    const size_t nc = (size_t)L.ncell;
+    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
+    const int nface = L.ny * L.nz, face = cell / L.nx;
+    float fl[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int sx = x - D3Q19::cx(i);
+        float val;
+        if (L.bc_x == 1 && sx < 0) {
+            val = L.feq_in[i];
+        } else if (L.bc_x == 1 && sx > L.nx - 1) {
+            val = outlet[outlet_slot(i) * nface + face];
+        } else {
+            int s = cell_index(L, wrapc(sx, L.nx), wrapc(y - D3Q19::cy(i), L.ny),
+                               wrapc(z - D3Q19::cz(i), L.nz));
+            if (solid && solid[s])
+                val = f[i * nc + cell];  // own f*_opp(i), stored in slot i by the even step
+            else
+                val = f[D3Q19::opp(i) * nc + s];
+        }
+        fl[i] = val;
+    }
+    collide(L, fl);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int tx = x + D3Q19::cx(i);
+        if (L.bc_x == 1 && (tx < 0 || tx > L.nx - 1)) continue;  // leaves the lattice
+        int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
+                           wrapc(z + D3Q19::cz(i), L.nz));
+        if (solid && solid[t])
+            f[D3Q19::opp(i) * nc + cell] = fl[i];
+        else
+            f[i * nc + t] = fl[i];
+    }
+    if (L.bc_x == 1) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            if (x == 0 && D3Q19::cx(i) == 1) f[i * nc + cell] = L.feq_in[i];
+            if (x == L.nx - 1 && D3Q19::cx(i) == -1) f[i * nc + cell] = fl[i];
+        }
+    }
+}
+
+// One collide + push step between two lattices in natural order. Solid cells
+// are copied so that fout holds a complete lattice.
+__global__ void __launch_bounds__(256) k_lbm_push(LbmParams L, const float *__restrict__ fin,
+                                                 float *__restrict__ fout,
+                                                 const uint8_t *__restrict__ solid) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const size_t nc = (size_t)L.ncell;
+    if (solid && solid[cell]) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) fout[i * nc + cell] = fin[i * nc + cell];
+        return;
+    }
+    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
+    float fl[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = fin[i * nc + cell];
+    collide(L, fl);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int tx = x + D3Q19::cx(i);
+        if (L.bc_x == 1 && (tx < 0 || tx > L.nx - 1)) continue;
+        int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
+                           wrapc(z + D3Q19::cz(i), L.nz));
+        if (solid && solid[t])
+            fout[D3Q19::opp(i) * nc + cell] = fl[i];
+        else
+            fout[i * nc + t] = fl[i];
+    }
+    if (L.bc_x == 1) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            if (x == 0 && D3Q19::cx(i) == 1) fout[i * nc + cell] = L.feq_in[i];
+            if (x == L.nx - 1 && D3Q19::cx(i) == -1) fout[i * nc + cell] = fl[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reverse --
+
+// One reverse step: g_prev = C^T S^T g_next at the pre-collision state f_t.
+__global__ void __launch_bounds__(256) k_lbm_adjoint(LbmParams L, const float *__restrict__ f_t,
+                                                    const float *__restrict__ g_next,
+                                                    float *__restrict__ g_prev,
+                                                    const uint8_t *__restrict__ solid) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const size_t nc = (size_t)L.ncell;
+    if (solid && solid[cell]) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) g_prev[i * nc + cell] = g_next[i * nc + cell];
+        return;
+    }
+    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
+    float g[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float acc = 0.0f;
+        int tx = x + D3Q19::cx(i);
+        if (!(L.bc_x == 1 && (tx < 0 || tx > L.nx - 1))) {
+            int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
+                               wrapc(z + D3Q19::cz(i), L.nz));
+            if (solid && solid[t])
+                acc += g_next[D3Q19::opp(i) * nc + cell];
+            else
+                acc += g_next[i * nc + t];
+        }
+        if (L.bc_x == 1 && x == L.nx - 1 && D3Q19::cx(i) == -1) acc += g_next[i * nc + cell];
+        g[i] = acc;
+    }
+    float fl[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = f_t[i * nc + cell];
+    collide_adjoint(L, fl, g);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) g_prev[i * nc + cell] = g[i];
+}
+
+// ------------------------------------------------------------ auxiliaries --
+
+__global__ void k_lbm_macroscopic(LbmParams L, const float *__restrict__ f,
+                                  const uint8_t *__restrict__ solid, float *__restrict__ rho,
+                                  float *__restrict__ u) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const size_t nc = (size_t)L.ncell;
+    float r = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f;
+    if (!(solid && solid[cell])) {
+        float rs = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            float fi = f[i * nc + cell];
+            rs += fi;
+            jx += (float)D3Q19::cx(i) * fi;
+            jy += (float)D3Q19::cy(i) * fi;
+            jz += (float)D3Q19::cz(i) * fi;
+        }
+        r = 1.0f + rs;
+        ux = (jx + 0.5f * L.Fx) / r;
+        uy = (jy + 0.5f * L.Fy) / r;
+        uz = (jz + 0.5f * L.Fz) / r;
+    }
+    if (rho) rho[cell] = r;
+    if (u) {
+        u[cell] = ux;
+        u[nc + cell] = uy;
+        u[2 * nc + cell] = uz;
+    }
+}
+
+__global__ void k_lbm_fill_eq(LbmParams L, float *__restrict__ f, float rho0, float ux, float uy,
+                              float uz) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const size_t nc = (size_t)L.ncell;
+    float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float cu = (float)D3Q19::cx(i) * ux + (float)D3Q19::cy(i) * uy + (float)D3Q19::cz(i) * uz;
+        f[i * nc + cell] = D3Q19::w(i) * ((rho0 - 1.0f) + rho0 * (3.0f * cu + 4.5f * cu * cu - uu));
+    }
+}
+
+__global__ void k_voxel_clear(uint8_t *__restrict__ solid, int64_t nbytes) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nbytes) solid[i] = 0;
+}
+
+// Eq. point2voxel: the node whose cell [x_w, x_w + dx)^3 holds the particle.
+__global__ void k_voxelize(const float *__restrict__ pos, int64_t n, int nx, int ny, int nz,
+                           float inv_dx, uint8_t *__restrict__ solid) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float sx = floorf(pos[p] * inv_dx), sy = floorf(pos[n + p] * inv_dx),
+          sz = floorf(pos[2 * n + p] * inv_dx);
+    if (!(sx >= 0.0f && sx < (float)nx && sy >= 0.0f && sy < (float)ny && sz >= 0.0f && sz < (float)nz))
+        return;
+    solid[((int64_t)sz * ny + (int64_t)sy) * nx + (int64_t)sx] = 1;
+}
+
+struct LbmHandle {
+    dw_lbm_desc desc;
+    LbmParams L;
+    float *outlet = nullptr;  // [5][ny*nz]
+    float *tape = nullptr;    // [max_tape][19][ncell]
+    float *gtmp = nullptr;    // [19][ncell]
+};
+
+static void fill_lbm_params(LbmHandle *h) {
+    const dw_lbm_desc &d = h->desc;
+    LbmParams &L = h->L;
+    L.nx = d.nx;
+    L.ny = d.ny;
+    L.nz = d.nz;
+    L.ncell = d.nx * d.ny * d.nz;
+    L.inv_tau = 1.0f / d.tau;
+    L.pre = 1.0f - 0.5f / d.tau;
+    L.Fx = d.force[0];
+    L.Fy = d.force[1];
+    L.Fz = d.force[2];
+    L.has_force = (d.force[0] != 0.0f || d.force[1] != 0.0f || d.force[2] != 0.0f) ? 1 : 0;
+    L.bc_x = d.bc_x;
+    double ux = d.u_inlet[0], uy = d.u_inlet[1], uz = d.u_inlet[2];
+    double uu = ux * ux + uy * uy + uz * uz;
+    for (int i = 0; i < 19; ++i) {
+        double cu = D3Q19::cx(i) * ux + D3Q19::cy(i) * uy + D3Q19::cz(i) * uz;
+        L.feq_in[i] = (float)(D3Q19::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    }
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+struct dw_lbm_s : LbmHandle {};
+
+extern "C" dw_status lbm_create(const dw_lbm_desc *desc, dw_lbm *out) {
+    DW_REQUIRE(desc && out, "desc/out must not be NULL");
+    *out = nullptr;
+    DW_REQUIRE(desc->nx >= 2 && desc->ny >= 2 && desc->nz >= 2, "lattice sizes must be >= 2");
+    DW_REQUIRE((int64_t)desc->nx * desc->ny * desc->nz < (1ll << 31), "lattice too large");
+    DW_REQUIRE(desc->tau > 0.5f, "tau must be > 0.5");
+    DW_REQUIRE(desc->bc_x == 0 || desc->bc_x == 1, "bc_x must be 0 or 1");
+    DW_REQUIRE(desc->max_tape >= 1 && desc->max_tape <= 4096, "max_tape must be in [1, 4096]");
+    dw_lbm h = new (std::nothrow) dw_lbm_s();
+    if (!h) {
+        set_error("out of host memory");
+        return DW_ERR_OOM;
+    }
+    h->desc = *desc;
+    fill_lbm_params(h);
+    size_t lat = sizeof(float) * 19 * (size_t)h->L.ncell;
+    cudaError_t e = cudaMalloc((void **)&h->outlet, sizeof(float) * 5 * (size_t)desc->ny * desc->nz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->tape, lat * (size_t)desc->max_tape);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->gtmp, lat);
+    if (e != cudaSuccess) {
+        dw_status st = cuda_fail(e, "lbm_create");
+        lbm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_destroy(dw_lbm h) {
+    if (!h) return DW_OK;
+    cudaFree(h->outlet);
+    cudaFree(h->tape);
+    cudaFree(h->gtmp);
+    delete h;
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t steps,
+                              dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(f, "f must not be NULL");
+    DW_REQUIRE(steps >= 0, "steps must be >= 0");
+    cudaStream_t s = as_stream(stream);
+    const LbmParams &L = h->L;
+    unsigned grid = grid_for(L.ncell, 256);
+    for (int k = 0; k + 1 < steps; k += 2) {
+        k_lbm_aa_even<<<grid, 256, 0, s>>>(L, f, solid, h->outlet);
+        k_lbm_aa_odd<<<grid, 256, 0, s>>>(L, f, solid, h->outlet);
+    }
+    if (steps & 1) {
+        k_lbm_push<<<grid, 256, 0, s>>>(L, f, h->tape, solid);
+        DW_CUDA(cudaMemcpyAsync(f, h->tape, sizeof(float) * 19 * (size_t)L.ncell,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    DW_LAUNCHED("lbm_step");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_step_adjoint(dw_lbm h, const float *f_in, float *g_f,
+                                      const uint8_t *solid, int32_t steps, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(f_in && g_f, "f_in/g_f must not be NULL");
+    DW_REQUIRE(steps >= 0 && steps <= h->desc.max_tape, "steps=%d must be in [0, max_tape=%d]",
+               steps, h->desc.max_tape);
+    if (steps == 0) return DW_OK;
+    cudaStream_t s = as_stream(stream);
+    const LbmParams &L = h->L;
+    const size_t lat = 19 * (size_t)L.ncell;
+    unsigned grid = grid_for(L.ncell, 256);
+    // states f(1) .. f(steps-1) into tape[0 .. steps-2]
+    for (int k = 1; k < steps; ++k) {
+        const float *src = k == 1 ? f_in : h->tape + (size_t)(k - 2) * lat;
+        k_lbm_push<<<grid, 256, 0, s>>>(L, src, h->tape + (size_t)(k - 1) * lat, solid);
+    }
+    float *cur = g_f, *other = h->gtmp;
+    for (int k = steps - 1; k >= 0; --k) {
+        const float *state = k == 0 ? f_in : h->tape + (size_t)(k - 1) * lat;
+        k_lbm_adjoint<<<grid, 256, 0, s>>>(L, state, cur, other, solid);
+        float *tmp = cur;
+        cur = other;
+        other = tmp;
+    }
+    if (cur != g_f)
+        DW_CUDA(cudaMemcpyAsync(g_f, cur, sizeof(float) * lat, cudaMemcpyDeviceToDevice, s));
+    DW_LAUNCHED("lbm_step_adjoint");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_macroscopic(dw_lbm h, const float *f, const uint8_t *solid, float *rho,
+                                     float *u, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(f, "f must not be NULL");
+    if (!rho && !u) return DW_OK;
+    k_lbm_macroscopic<<<grid_for(h->L.ncell, 256), 256, 0, as_stream(stream)>>>(h->L, f, solid, rho, u);
+    DW_LAUNCHED("k_lbm_macroscopic");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_init_equilibrium(dw_lbm h, float *f, float rho0, const float u0[3],
+                                          dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(f && u0, "f/u0 must not be NULL");
+    DW_REQUIRE(rho0 > 0.0f, "rho0 must be > 0");
+    k_lbm_fill_eq<<<grid_for(h->L.ncell, 256), 256, 0, as_stream(stream)>>>(h->L, f, rho0, u0[0],
+                                                                            u0[1], u0[2]);
+    DW_LAUNCHED("k_lbm_fill_eq");
+    return DW_OK;
+}
+
+extern "C" dw_status voxelize_particles(const float *pos, int64_t n, int32_t nx, int32_t ny,
+                                        int32_t nz, float dx, uint8_t *solid, dw_stream stream) {
+    DW_REQUIRE(solid, "solid must not be NULL");
+    DW_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1, "lattice sizes must be >= 1");
+    DW_REQUIRE(dx > 0.0f, "dx must be > 0");
+    DW_REQUIRE(n >= 0 && (n == 0 || pos), "pos must not be NULL with n > 0");
+    cudaStream_t s = as_stream(stream);
+    int64_t nb = (int64_t)nx * ny * nz;
+    k_voxel_clear<<<grid_for(nb, 256), 256, 0, s>>>(solid, nb);
+    if (n > 0) k_voxelize<<<grid_for(n, 256), 256, 0, s>>>(pos, n, nx, ny, nz, 1.0f / dx, solid);
+    DW_LAUNCHED("voxelize");
+    return DW_OK;
+}

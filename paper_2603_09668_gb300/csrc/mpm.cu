@@ -1,0 +1,837 @@
+// MLS-MPM substep S of Eq. simulation_mpm and its reverse mode, as a handle
+// with a persistent workspace (grid, adjoint grid, per-particle scratch).
+//
+// Kernels per forward substep: P2G (particles -> grid), grid update (nodes),
+// G2P (grid -> particles). Per adjoint substep: P2G + grid update recomputed
+// from the input state, then reverse G2P (scatter dL/dv_i to the grid),
+// reverse grid update (dL/dp_i, dL/dm_i, scatter into the wind-field
+// gradient) and reverse P2G (gather the grid adjoint to the particles).
+// Grid layout: float4 per node, node (i, j, k) at ((k N + j) N + i).
+#include <stdio.h>
+
+#include <new>
+#include <vector>
+#include <stdlib.h>
+
+#include "mpm_math.cuh"
+#include "mpm_p2g.cuh"
+#include "wind.cuh"
+
+namespace dw {
+
+struct MpmHandle {
+    dw_mpm_desc desc;
+    MpmParams P;
+    int64_t n_nodes;
+    float4 *grid_mp = nullptr;   // (m, p) after P2G; zero between calls
+    float4 *grid_v = nullptr;    // (v, m) after the grid update
+    float4 *grid_bv = nullptr;   // dL/dv_i during the adjoint; zero between calls
+    float4 *grid_bmp = nullptr;  // (dL/dm_i, dL/dp_i) during the adjoint
+    float *pscratch = nullptr;   // [12][max_particles]: partial dL/dx (3), dL/dF (9)
+    int *err = nullptr;          // device status bits
+    // sort workspace
+    int nb = 0;                  // 4^3 blocks per axis
+    int64_t n_keys = 0;
+    int *keys = nullptr;         // [max_particles]
+    int *perm = nullptr;         // [max_particles]
+    int *counts = nullptr;       // [n_keys + 1]
+    int *scan_tmp = nullptr;     // block sums for the exclusive scan
+    int64_t scan_tmp_len = 0;
+    // instrumentation: event pairs around kernel launches
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<int> ev_kernel;
+    int prof_used = 0;
+};
+
+// Brackets one kernel launch with events when profiling is enabled.
+struct ProfScope {
+    MpmHandle *h;
+    cudaStream_t s;
+    int slot = -1;
+    ProfScope(MpmHandle *h_, int kid, cudaStream_t s_) : h(h_), s(s_) {
+        if (h->prof_used < (int)h->ev_start.size()) {
+            slot = h->prof_used++;
+            h->ev_kernel[slot] = kid;
+            cudaEventRecord(h->ev_start[slot], s);
+        }
+    }
+    ~ProfScope() {
+        if (slot >= 0) cudaEventRecord(h->ev_stop[slot], s);
+    }
+};
+
+static void profile_free(MpmHandle *h) {
+    for (auto e : h->ev_start) cudaEventDestroy(e);
+    for (auto e : h->ev_stop) cudaEventDestroy(e);
+    h->ev_start.clear();
+    h->ev_stop.clear();
+    h->ev_kernel.clear();
+    h->prof_used = 0;
+}
+
+static void fill_params(MpmHandle *h) {
+    const dw_mpm_desc &d = h->desc;
+    MpmParams &P = h->P;
+    P.N = d.n_grid;
+    P.dx = 1.0f / (float)d.n_grid;
+    P.inv_dx = (float)d.n_grid;
+    P.dt = d.dt;
+    P.D = 4.0f * (float)d.n_grid * (float)d.n_grid;
+    P.gx = d.gravity[0];
+    P.gy = d.gravity[1];
+    P.gz = d.gravity[2];
+    P.band = d.bc_band;
+    P.material = d.material;
+    double E = d.E, nu = d.nu;
+    P.mu = (float)(E / (2.0 * (1.0 + nu)));                       // Eq. young_poisson
+    P.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    P.E = d.E;
+    P.p_mass = d.p_mass;
+    P.p_vol = d.p_vol;
+    P.kappa = d.dt * d.p_vol * P.D;
+}
+
+// --------------------------------------------------------------- forward --
+
+__global__ void k_grid_update(MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp,
+                              float4 *__restrict__ grid_v, int clear) {
+    int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nn = (int64_t)P.N * P.N * P.N;
+    if (node >= nn) return;
+    float4 mp = grid_mp[node];
+    float4 out = make_float4(0.f, 0.f, 0.f, mp.x);
+    if (mp.x > 0.0f) {
+        int i = (int)(node % P.N), j = (int)((node / P.N) % P.N), k = (int)(node / ((int64_t)P.N * P.N));
+        bool sticky = i < P.band || j < P.band || k < P.band || i > P.N - 1 - P.band ||
+                      j > P.N - 1 - P.band || k > P.N - 1 - P.band;
+        if (!sticky) {
+            float3 a = wind_sample_dev(wind, i * P.dx, j * P.dx, k * P.dx, t);
+            float inv_m = 1.0f / mp.x;
+            out.x = mp.y * inv_m + P.dt * (P.gx + a.x);
+            out.y = mp.z * inv_m + P.dt * (P.gy + a.y);
+            out.z = mp.w * inv_m + P.dt * (P.gz + a.z);
+        }
+    }
+    grid_v[node] = out;
+    if (clear) grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// x/xo and F/Fo may be the same arrays (in-place substep): every thread reads
+// its particle before writing it, so they carry no __restrict__.
+__global__ void k_g2p(MpmParams P, const float *x, const float *F,
+                      const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
+                      float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    float Fp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
+    Stencil s;
+    if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
+        // out of range: leave the particle as it was (P2G has flagged it)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xo[a * n + p] = xp[a];
+            vo[a * n + p] = 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Co[k * n + p] = 0.0f;
+            Fo[k * n + p] = Fp[k];
+        }
+        return;
+    }
+    float vn[3] = {0.f, 0.f, 0.f};
+    float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int N = P.N;
+#pragma unroll
+    for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+        for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+            for (int ok = 0; ok < 3; ++ok) {
+                float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
+                float d0 = ((float)oi - s.fx[0]) * P.dx, d1 = ((float)oj - s.fx[1]) * P.dx,
+                      d2 = ((float)ok - s.fx[2]) * P.dx;
+                int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
+                float4 gv = grid_v[id];
+                float wv[3] = {W * gv.x, W * gv.y, W * gv.z};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    vn[a] += wv[a];
+                    Cn[3 * a + 0] += wv[a] * d0;
+                    Cn[3 * a + 1] += wv[a] * d1;
+                    Cn[3 * a + 2] += wv[a] * d2;
+                }
+            }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Cn[k] *= P.D;
+    if (pinned && pinned[p]) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vn[a] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Cn[k] = 0.0f;
+    }
+    float M[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) M[k] = P.dt * Cn[k];
+    M[0] += 1.0f;
+    M[4] += 1.0f;
+    M[8] += 1.0f;
+    float Fn[9];
+    mul3(M, Fp, Fn);
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float xn = xp[a] + P.dt * vn[a];
+        fin = fin && isfinite(xn);
+        xo[a * n + p] = xn;
+        vo[a * n + p] = vn[a];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        Co[k * n + p] = Cn[k];
+        Fo[k * n + p] = Fn[k];
+    }
+    if (!fin || !finite9(Fn)) atomicOr(err, ERRBIT_NONFINITE);
+}
+
+// --------------------------------------------------------------- reverse --
+
+__device__ __forceinline__ void weight_grad(const MpmParams &P, const Stencil &s, int oi, int oj,
+                                            int ok, float g[3]) {
+    float wx = s.w[0][oi], wy = s.w[1][oj], wz = s.w[2][ok];
+    g[0] = s.dw[0][oi] * wy * wz * P.inv_dx;
+    g[1] = wx * s.dw[1][oj] * wz * P.inv_dx;
+    g[2] = wx * wy * s.dw[2][ok] * P.inv_dx;
+}
+
+// Reverse G2P: scatter dL/dv_i into grid_bv; write partial dL/dx_p, dL/dF_p.
+__global__ void k_rev_g2p(MpmParams P, const float *__restrict__ x, const float *__restrict__ F,
+                          const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
+                          const float *__restrict__ gxo, const float *__restrict__ gvo,
+                          const float *__restrict__ gCo, const float *__restrict__ gFo,
+                          float4 *__restrict__ grid_bv, float *__restrict__ scratch, int64_t n,
+                          int64_t cap) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float xp[3] = {x[p], x[n + p], x[2 * n + p]};
+    float Fp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
+    Stencil s;
+    float bxo[3] = {gxo[p], gxo[n + p], gxo[2 * n + p]};
+    if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) scratch[a * cap + p] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = 0.0f;
+        return;
+    }
+    const int N = P.N;
+    // recompute C' (v' is not needed: its adjoint only uses the weights)
+    float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool pin = pinned && pinned[p];
+    if (!pin) {
+#pragma unroll
+        for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+            for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+                for (int ok = 0; ok < 3; ++ok) {
+                    float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
+                    float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
+                                  ((float)ok - s.fx[2]) * P.dx};
+                    int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
+                    float4 gv = grid_v[id];
+                    float wv[3] = {W * gv.x, W * gv.y, W * gv.z};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) Cn[3 * a + b] += wv[a] * d[b];
+                }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Cn[k] *= P.D;
+    }
+    float bFo[9], bCo[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        bFo[k] = gFo[k * n + p];
+        bCo[k] = gCo[k * n + p];
+    }
+    // F' = (I + dt C') F  ->  bF_in = (I + dt C')^T bF', bC' += dt bF' F^T
+    float M[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) M[k] = P.dt * Cn[k];
+    M[0] += 1.0f;
+    M[4] += 1.0f;
+    M[8] += 1.0f;
+    float bFin[9], bFoFt[9];
+    mul3_atb(M, bFo, bFin);
+    mul3_abt(bFo, Fp, bFoFt);
+    float bC[9], bv[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) bC[k] = bCo[k] + P.dt * bFoFt[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bv[a] = gvo[a * n + p] + P.dt * bxo[a];
+    float bx[3] = {bxo[0], bxo[1], bxo[2]};
+    if (!pin) {
+#pragma unroll
+        for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+            for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+                for (int ok = 0; ok < 3; ++ok) {
+                    float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
+                    float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
+                                  ((float)ok - s.fx[2]) * P.dx};
+                    int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
+                    float4 gv = grid_v[id];
+                    float vi[3] = {gv.x, gv.y, gv.z};
+                    float Cd[3], CtV[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Cd[a] = bC[3 * a] * d[0] + bC[3 * a + 1] * d[1] + bC[3 * a + 2] * d[2];
+                        CtV[a] = bC[a] * vi[0] + bC[3 + a] * vi[1] + bC[6 + a] * vi[2];
+                    }
+                    float bW = 0.0f;
+                    float4 add;
+                    add.x = W * (bv[0] + P.D * Cd[0]);
+                    add.y = W * (bv[1] + P.D * Cd[1]);
+                    add.z = W * (bv[2] + P.D * Cd[2]);
+                    add.w = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) bW += vi[a] * (bv[a] + P.D * Cd[a]);
+                    atomicAdd(&grid_bv[id], add);
+                    float gW[3];
+                    weight_grad(P, s, oi, oj, ok, gW);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) bx[a] += -P.D * W * CtV[a] + bW * gW[a];
+                }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) scratch[a * cap + p] = bx[a];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = bFin[k];
+}
+
+// Reverse grid update: (dL/dm_i, dL/dp_i) into grid_bmp, wind gradient scatter,
+// and clearing of grid_mp and grid_bv for the next call.
+__global__ void k_rev_grid(MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp,
+                           float4 *__restrict__ grid_bv, float4 *__restrict__ grid_bmp,
+                           float *__restrict__ g_wind) {
+    int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nn = (int64_t)P.N * P.N * P.N;
+    if (node >= nn) return;
+    float4 mp = grid_mp[node];
+    float4 bmp = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mp.x > 0.0f) {
+        int i = (int)(node % P.N), j = (int)((node / P.N) % P.N), k = (int)(node / ((int64_t)P.N * P.N));
+        bool sticky = i < P.band || j < P.band || k < P.band || i > P.N - 1 - P.band ||
+                      j > P.N - 1 - P.band || k > P.N - 1 - P.band;
+        if (!sticky) {
+            float4 b = grid_bv[node];
+            float inv_m = 1.0f / mp.x;
+            bmp.y = b.x * inv_m;
+            bmp.z = b.y * inv_m;
+            bmp.w = b.z * inv_m;
+            bmp.x = -(mp.y * b.x + mp.z * b.y + mp.w * b.z) * inv_m * inv_m;
+            if (g_wind)
+                wind_sample_adjoint_dev(wind, i * P.dx, j * P.dx, k * P.dx, t,
+                                        make_float3(P.dt * b.x, P.dt * b.y, P.dt * b.z), g_wind);
+        }
+    }
+    grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    grid_bv[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    grid_bmp[node] = bmp;
+}
+
+__global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float *__restrict__ v,
+                          const float *__restrict__ C, const float *__restrict__ F,
+                          const float4 *__restrict__ grid_bmp, const float *__restrict__ scratch,
+                          float *__restrict__ gx, float *__restrict__ gv, float *__restrict__ gC,
+                          float *__restrict__ gF, float *__restrict__ g_E, int64_t n, int64_t cap) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float gE_local = 0.0f;
+    if (p < n) {
+        float xp[3] = {x[p], x[n + p], x[2 * n + p]};
+        float vp[3] = {v[p], v[n + p], v[2 * n + p]};
+        float Cp[9], Fp[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Cp[k] = C[k * n + p];
+            Fp[k] = F[k * n + p];
+        }
+        float bx[3] = {scratch[p], scratch[cap + p], scratch[2 * cap + p]};
+        float bF[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) bF[k] = scratch[(3 + k) * cap + p];
+        Stencil s;
+        float bA[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float bvp[3] = {0.f, 0.f, 0.f};
+        if (make_stencil(P, xp[0], xp[1], xp[2], s)) {
+            float Pk[9], PFt[9], A[9];
+            stress_P(P, Fp, Pk);
+            mul3_abt(Pk, Fp, PFt);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) A[k] = -P.kappa * PFt[k] + P.p_mass * Cp[k];
+            const int N = P.N;
+#pragma unroll
+            for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+                for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+                    for (int ok = 0; ok < 3; ++ok) {
+                        float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
+                        float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
+                                      ((float)ok - s.fx[2]) * P.dx};
+                        int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
+                        float4 g = grid_bmp[id];
+                        float bp[3] = {g.y, g.z, g.w};
+                        float bW = P.p_mass * g.x;
+                        float AtB[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float mom = P.p_mass * vp[c] + A[3 * c] * d[0] + A[3 * c + 1] * d[1] + A[3 * c + 2] * d[2];
+                            bW += bp[c] * mom;
+                            bvp[c] += W * P.p_mass * bp[c];
+#pragma unroll
+                            for (int b = 0; b < 3; ++b) {
+                                bA[3 * c + b] += W * bp[c] * d[b];
+                                AtB[b] += A[3 * c + b] * bp[c];
+                            }
+                        }
+                        float gW[3];
+                        weight_grad(P, s, oi, oj, ok, gW);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) bx[a] += -W * AtB[a] + bW * gW[a];
+                    }
+            // A = -kappa P F^T + m C
+            float bAF[9], bAtP[9], bP[9];
+            mul3(bA, Fp, bAF);
+            mul3_atb(bA, Pk, bAtP);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                bP[k] = -P.kappa * bAF[k];
+                bF[k] += -P.kappa * bAtP[k];
+            }
+            stress_P_adjoint(P, Fp, bP, bF);
+            float pp = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) pp += bP[k] * Pk[k];
+            gE_local = pp / P.E;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gx[a * n + p] = bx[a];
+            gv[a * n + p] = bvp[a];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            gC[k * n + p] = P.p_mass * bA[k];
+            gF[k * n + p] = bF[k];
+        }
+    }
+    if (g_E) {
+        // warp + block reduction, one atomic per block
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gE_local += __shfl_xor_sync(0xffffffffu, gE_local, o);
+        __shared__ float red[32];
+        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) red[wid] = gE_local;
+        __syncthreads();
+        if (wid == 0) {
+            float vsum = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+            if (lane == 0) atomicAdd(g_E, vsum);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ sort --
+
+__device__ __forceinline__ int cell_key(const MpmParams &P, int nb, float px, float py, float pz) {
+    float xs[3] = {px * P.inv_dx, py * P.inv_dx, pz * P.inv_dx};
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float b = floorf(xs[a] - 0.5f);
+        b = fminf(fmaxf(b, 0.0f), (float)(P.N - 1));  // NaN -> 0
+        c[a] = (int)b;
+    }
+    int blk = ((c[2] >> 2) * nb + (c[1] >> 2)) * nb + (c[0] >> 2);
+    int loc = ((c[2] & 3) * 4 + (c[1] & 3)) * 4 + (c[0] & 3);
+    return blk * 64 + loc;
+}
+
+__global__ void k_sort_keys(MpmParams P, int nb, const float *__restrict__ x, int64_t n,
+                            int *__restrict__ keys, int *__restrict__ counts) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int k = cell_key(P, nb, x[p], x[n + p], x[2 * n + p]);
+    keys[p] = k;
+    atomicAdd(&counts[k], 1);
+}
+
+// Exclusive scan, three phases: per-block scan with block totals, scan of the
+// totals (single block, loops over chunks), add-back.
+constexpr int SCAN_BLOCK = 1024;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) smem_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? smem_warp[lane] : 0;
+        int si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < nw) smem_warp[lane] = si - s;
+        if (lane == nw - 1) smem_warp[32] = si;
+    }
+    __syncthreads();
+    total = smem_warp[32];
+    int res = incl - v + smem_warp[wid];
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_blocks(int *__restrict__ data, int64_t len, int *__restrict__ block_sums) {
+    __shared__ int sw[33];
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    int v = i < len ? data[i] : 0;
+    int total;
+    int ex = block_exclusive_scan(v, sw, total);
+    if (i < len) data[i] = ex;
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int *__restrict__ sums, int64_t nblocks) {
+    __shared__ int sw[33];
+    int carry = 0;
+    for (int64_t base = 0; base < nblocks; base += SCAN_BLOCK) {
+        int64_t i = base + threadIdx.x;
+        int v = i < nblocks ? sums[i] : 0;
+        int total;
+        int ex = block_exclusive_scan(v, sw, total);
+        if (i < nblocks) sums[i] = ex + carry;
+        carry += total;
+    }
+}
+
+__global__ void k_scan_add(int *__restrict__ data, int64_t len, const int *__restrict__ sums) {
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    if (i < len) data[i] += sums[blockIdx.x];
+}
+
+__global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
+                               int *__restrict__ perm) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int pos = atomicAdd(&offsets[keys[p]], 1);
+    perm[pos] = (int)p;
+}
+
+__global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *__restrict__ x,
+                          const float *__restrict__ v, const float *__restrict__ C,
+                          const float *__restrict__ F, const uint8_t *__restrict__ pin_in,
+                          const int *__restrict__ ids_in, float *__restrict__ xo,
+                          float *__restrict__ vo, float *__restrict__ Co, float *__restrict__ Fo,
+                          uint8_t *__restrict__ pin_out, int *__restrict__ ids_out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int q = perm[k];
+    ids_out[k] = ids_in ? ids_in[q] : q;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xo[a * n + k] = x[a * n + q];
+        vo[a * n + k] = v[a * n + q];
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        Co[c * n + k] = C[c * n + q];
+        Fo[c * n + k] = F[c * n + q];
+    }
+    if (pin_in) pin_out[k] = pin_in[q];
+}
+
+static dw_status device_exclusive_scan(MpmHandle *h, int *data, int64_t len, cudaStream_t st) {
+    int64_t nblocks = (len + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nblocks > h->scan_tmp_len) {
+        set_error("scan workspace too small");
+        return DW_ERR_ARG;
+    }
+    k_scan_blocks<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, h->scan_tmp);
+    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(h->scan_tmp, nblocks);
+    k_scan_add<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, h->scan_tmp);
+    DW_LAUNCHED("exclusive scan");
+    return DW_OK;
+}
+
+// --------------------------------------------------------------- helpers --
+
+static dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *name) {
+    DW_REQUIRE(s != nullptr, "%s state is NULL", name);
+    DW_REQUIRE(s->n >= 0 && s->n <= h->desc.max_particles,
+               "%s state has n=%lld particles; the handle holds at most %lld", name,
+               (long long)s->n, (long long)h->desc.max_particles);
+    DW_REQUIRE(s->n == 0 || (s->x && s->v && s->C && s->F), "%s state has a NULL array", name);
+    return DW_OK;
+}
+
+static dw_status launch_grid_update(MpmHandle *h, const WindDev &wd, float t, int clear,
+                                    cudaStream_t st) {
+    ProfScope ps(h, DW_K_GRID, st);
+    k_grid_update<<<grid_for(h->n_nodes, 256), 256, 0, st>>>(h->P, wd, t, h->grid_mp, h->grid_v, clear);
+    DW_LAUNCHED("k_grid_update");
+    return DW_OK;
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+struct dw_mpm_s : MpmHandle {};
+
+extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
+    DW_REQUIRE(desc && out, "desc/out must not be NULL");
+    *out = nullptr;
+    DW_REQUIRE(desc->n_grid >= 8 && desc->n_grid <= 512, "n_grid=%d out of range [8, 512]", desc->n_grid);
+    DW_REQUIRE(desc->dt > 0.0f, "dt must be > 0");
+    DW_REQUIRE(desc->bc_band >= 0 && desc->bc_band < desc->n_grid / 2, "bc_band out of range");
+    DW_REQUIRE(desc->material == DW_NEOHOOKEAN || desc->material == DW_FIXED_COROTATED,
+               "unknown material %d", desc->material);
+    DW_REQUIRE(desc->E > 0.0f && desc->nu >= 0.0f && desc->nu < 0.5f, "need E > 0 and 0 <= nu < 0.5");
+    DW_REQUIRE(desc->p_mass > 0.0f && desc->p_vol > 0.0f, "p_mass and p_vol must be > 0");
+    DW_REQUIRE(desc->max_particles >= 0 && desc->max_particles < (1ll << 31),
+               "max_particles out of range");
+    DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_TILE, "unknown p2g_mode");
+    dw_mpm h = new (std::nothrow) dw_mpm_s();
+    if (!h) {
+        set_error("out of host memory");
+        return DW_ERR_OOM;
+    }
+    h->desc = *desc;
+    fill_params(h);
+    int N = desc->n_grid;
+    h->n_nodes = (int64_t)N * N * N;
+    h->nb = (N + 3) / 4;
+    h->n_keys = (int64_t)h->nb * h->nb * h->nb * 64;
+    h->scan_tmp_len = (h->n_keys + SCAN_BLOCK) / SCAN_BLOCK + 1;
+    int64_t cap = desc->max_particles > 0 ? desc->max_particles : 1;
+    cudaError_t e = cudaSuccess;
+    size_t gbytes = sizeof(float4) * (size_t)h->n_nodes;
+#define DW_ALLOC(ptr, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
+    DW_ALLOC(h->grid_mp, gbytes);
+    DW_ALLOC(h->grid_v, gbytes);
+    DW_ALLOC(h->grid_bv, gbytes);
+    DW_ALLOC(h->grid_bmp, gbytes);
+    DW_ALLOC(h->pscratch, sizeof(float) * 12 * (size_t)cap);
+    DW_ALLOC(h->err, sizeof(int));
+    DW_ALLOC(h->keys, sizeof(int) * (size_t)cap);
+    DW_ALLOC(h->perm, sizeof(int) * (size_t)cap);
+    DW_ALLOC(h->counts, sizeof(int) * (size_t)(h->n_keys + 1));
+    DW_ALLOC(h->scan_tmp, sizeof(int) * (size_t)h->scan_tmp_len);
+#undef DW_ALLOC
+    if (e == cudaSuccess) e = cudaMemset(h->grid_mp, 0, gbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->grid_bv, 0, gbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dw_status st = cuda_fail(e, "mpm_create");
+        mpm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_destroy(dw_mpm h) {
+    if (!h) return DW_OK;
+    cudaFree(h->grid_mp);
+    cudaFree(h->grid_v);
+    cudaFree(h->grid_bv);
+    cudaFree(h->grid_bmp);
+    cudaFree(h->pscratch);
+    cudaFree(h->err);
+    cudaFree(h->keys);
+    cudaFree(h->perm);
+    cudaFree(h->counts);
+    cudaFree(h->scan_tmp);
+    profile_free(h);
+    delete h;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_profile_enable(dw_mpm h, int32_t max_records) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(max_records >= 0 && max_records <= (1 << 20), "max_records out of range");
+    profile_free(h);
+    h->ev_start.resize(max_records);
+    h->ev_stop.resize(max_records);
+    h->ev_kernel.assign(max_records, 0);
+    for (int i = 0; i < max_records; ++i) {
+        DW_CUDA(cudaEventCreate(&h->ev_start[i]));
+        DW_CUDA(cudaEventCreate(&h->ev_stop[i]));
+    }
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_profile_read(dw_mpm h, double *total_ms, int64_t *launches) {
+    DW_REQUIRE(h && total_ms && launches, "arguments must not be NULL");
+    for (int k = 0; k < DW_K_COUNT; ++k) {
+        total_ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (int i = 0; i < h->prof_used; ++i) {
+        DW_CUDA(cudaEventSynchronize(h->ev_stop[i]));
+        float ms = 0.0f;
+        DW_CUDA(cudaEventElapsedTime(&ms, h->ev_start[i], h->ev_stop[i]));
+        total_ms[h->ev_kernel[i]] += ms;
+        launches[h->ev_kernel[i]] += 1;
+    }
+    h->prof_used = 0;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_set_material(dw_mpm h, float E, float nu) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(E > 0.0f && nu >= 0.0f && nu < 0.5f, "need E > 0 and 0 <= nu < 0.5");
+    h->desc.E = E;
+    h->desc.nu = nu;
+    fill_params(h);
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
+                                 const uint8_t *pinned, const dw_wind_field *wind, float t,
+                                 dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_state(h, in, "input");
+    if (st != DW_OK) return st;
+    st = check_state(h, out, "output");
+    if (st != DW_OK) return st;
+    DW_REQUIRE(in->n == out->n, "input and output particle counts differ");
+    WindDev wd;
+    st = wind_check(wind, &wd);
+    if (st != DW_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    int64_t n = in->n;
+    {
+        ProfScope ps(h, DW_K_P2G, s);
+        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err, s);
+    }
+    if (st != DW_OK) return st;
+    st = launch_grid_update(h, wd, t, 1, s);
+    if (st != DW_OK) return st;
+    if (n > 0) {
+        ProfScope ps(h, DW_K_G2P, s);
+        k_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v, out->x,
+                                               out->v, out->C, out->F, n, h->err);
+        DW_LAUNCHED("k_g2p");
+    }
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
+                                         const dw_mpm_state *g_out, const dw_mpm_state *g_in,
+                                         const uint8_t *pinned, const dw_wind_field *wind,
+                                         float t, float *g_wind, float *g_E, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_state(h, in, "input");
+    if (st != DW_OK) return st;
+    st = check_state(h, g_out, "g_out");
+    if (st != DW_OK) return st;
+    st = check_state(h, g_in, "g_in");
+    if (st != DW_OK) return st;
+    DW_REQUIRE(in->n == g_out->n && in->n == g_in->n, "particle counts differ");
+    WindDev wd;
+    st = wind_check(wind, &wd);
+    if (st != DW_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    int64_t n = in->n;
+    int64_t cap = h->desc.max_particles > 0 ? h->desc.max_particles : 1;
+    {
+        ProfScope ps(h, DW_K_P2G, s);
+        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err, s);
+    }
+    if (st != DW_OK) return st;
+    st = launch_grid_update(h, wd, t, 0, s);
+    if (st != DW_OK) return st;
+    if (n > 0) {
+        ProfScope ps(h, DW_K_REV_G2P, s);
+        k_rev_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v,
+                                                   g_out->x, g_out->v, g_out->C, g_out->F,
+                                                   h->grid_bv, h->pscratch, n, cap);
+        DW_LAUNCHED("k_rev_g2p");
+    }
+    {
+        ProfScope ps(h, DW_K_REV_GRID, s);
+        k_rev_grid<<<grid_for(h->n_nodes, 256), 256, 0, s>>>(h->P, wd, t, h->grid_mp, h->grid_bv,
+                                                              h->grid_bmp, g_wind);
+    }
+    DW_LAUNCHED("k_rev_grid");
+    if (n > 0) {
+        ProfScope ps(h, DW_K_REV_P2G, s);
+        k_rev_p2g<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->v, in->C, in->F, h->grid_bmp,
+                                                   h->pscratch, g_in->x, g_in->v, g_in->C,
+                                                   g_in->F, g_E, n, cap);
+        DW_LAUNCHED("k_rev_p2g");
+    }
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_sort(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
+                              const uint8_t *pinned_in, uint8_t *pinned_out,
+                              const int32_t *ids_in, int32_t *ids_out, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_state(h, in, "input");
+    if (st != DW_OK) return st;
+    st = check_state(h, out, "output");
+    if (st != DW_OK) return st;
+    DW_REQUIRE(in->n == out->n, "input and output particle counts differ");
+    DW_REQUIRE(in->n == 0 || in->x != out->x, "mpm_sort cannot run in place");
+    DW_REQUIRE(!pinned_in || pinned_out, "pinned_out must be given with pinned_in");
+    int64_t n = in->n;
+    if (n == 0) return DW_OK;
+    DW_REQUIRE(ids_out, "ids_out must not be NULL");
+    DW_REQUIRE(!ids_in || ids_in != ids_out, "ids_in and ids_out must differ");
+    cudaStream_t s = as_stream(stream);
+    ProfScope ps(h, DW_K_SORT, s);
+    DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
+    k_sort_keys<<<grid_for(n, 256), 256, 0, s>>>(h->P, h->nb, in->x, n, h->keys, h->counts);
+    DW_LAUNCHED("k_sort_keys");
+    st = device_exclusive_scan(h, h->counts, h->n_keys, s);
+    if (st != DW_OK) return st;
+    k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, h->perm);
+    DW_LAUNCHED("k_sort_scatter");
+    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in->x, in->v, in->C, in->F, pinned_in,
+                                               ids_in, out->x, out->v, out->C, out->F, pinned_out,
+                                               ids_out);
+    DW_LAUNCHED("k_permute");
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_device_status(dw_mpm h, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    int bits = 0;
+    cudaStream_t s = as_stream(stream);
+    DW_CUDA(cudaMemcpyAsync(&bits, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DW_CUDA(cudaStreamSynchronize(s));
+    DW_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    DW_CUDA(cudaStreamSynchronize(s));
+    return status_from_bits(bits);
+}

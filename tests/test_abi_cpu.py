@@ -1,0 +1,110 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads without a GPU,
+exports exactly the entry points include/*.h declares, and its ctypes layouts
+match the C structs. No compute call is made here."""
+import ctypes as ct
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names += re.findall(r"^DW_API\s+[\w\s\*]*?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2603_09668_gb300 import build
+
+    return build.build_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["mpm_create", "mpm_destroy", "mpm_substep", "mpm_substep_adjoint", "lbm_step",
+                     "lbm_step_adjoint", "wind_field_sample", "wind_field_sample_adjoint"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ct.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} is declared in include/ but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert exported == set(declared_functions()), exported ^ set(declared_functions())
+
+
+def test_ctypes_struct_layouts_match_c(libpath, tmp_path):
+    """Compile a tiny C program against the header that prints sizeof/offsetof."""
+    from paper_2603_09668_gb300 import _capi
+
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "diffwind.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(dw_mpm_desc), offsetof(dw_mpm_desc, max_particles),
+         offsetof(dw_mpm_desc, p2g_mode), offsetof(dw_mpm_desc, p_vol));
+  printf("%zu %zu\\n", sizeof(dw_mpm_state), offsetof(dw_mpm_state, n));
+  printf("%zu %zu\\n", sizeof(dw_wind_field), offsetof(dw_wind_field, t_total));
+  printf("%zu %zu %zu\\n", sizeof(dw_lbm_desc), offsetof(dw_lbm_desc, bc_x), offsetof(dw_lbm_desc, max_tape));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    d = _capi.DwMpmDesc
+    assert lines[0].split() == [str(ct.sizeof(d)), str(d.max_particles.offset), str(d.p2g_mode.offset),
+                                str(d.p_vol.offset)]
+    s = _capi.DwMpmState
+    assert lines[1].split() == [str(ct.sizeof(s)), str(s.n.offset)]
+    w = _capi.DwWindField
+    assert lines[2].split() == [str(ct.sizeof(w)), str(w.t_total.offset)]
+    lb = _capi.DwLbmDesc
+    assert lines[3].split() == [str(ct.sizeof(lb)), str(lb.bc_x.offset), str(lb.max_tape.offset)]
+
+
+def test_version_and_error_string_without_gpu(libpath):
+    from paper_2603_09668_gb300 import _capi
+
+    L = _capi.lib()
+    assert b"sm_103a" in L.dw_version()
+    assert L.dw_last_error() == b""
+
+
+def test_argument_errors_are_reported_without_touching_the_gpu(libpath):
+    """Host-side validation runs before any CUDA call, so it works on a CPU machine."""
+    from paper_2603_09668_gb300 import _capi
+
+    L = _capi.lib()
+    d = _capi.DwMpmDesc(4, 1e-4, (ct.c_float * 3)(0, -9.8, 0), 3, 0, 1e4, 0.3, 1.0, 1.0, 10, 0)
+    h = ct.c_void_p()
+    assert L.mpm_create(ct.byref(d), ct.byref(h)) == 1  # n_grid < 8
+    assert b"n_grid" in L.dw_last_error()
+    ld = _capi.DwLbmDesc(32, 32, 32, 0.4, (ct.c_float * 3)(), (ct.c_float * 3)(), 0, 1)
+    assert L.lbm_create(ct.byref(ld), ct.byref(h)) == 1  # tau <= 0.5
+    assert b"tau" in L.dw_last_error()
+    w = _capi.DwWindField(None, 8, 1, 1.0)
+    assert L.wind_field_sample(ct.byref(w), None, 0, 0.0, None, None) == 1
+    assert L.lbm_step(None, None, None, 2, None) == 1
+    assert L.mpm_substep(None, None, None, None, None, 0.0, None) == 1
+
+
+def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    from paper_2603_09668_gb300 import _capi
+
+    monkeypatch.setattr(_capi, "_lib", None)
+    monkeypatch.setattr(_capi, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _capi.lib()
