@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--substeps", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p2g-mode", type=int, default=0,
+                    help="P2G strategy: 0 auto, 1 global atomics, 2 warp-aggregated, 3 shared tile")
     return ap.parse_args()
 
 
@@ -153,7 +155,7 @@ def run_ours(args):
 
     sc = inputs.sheet_scene(n_substeps=args.substeps, seed=rank, wind_seed=rank)
     n = sc.n
-    mpm = B.MPM.from_params(sc.params(), max_particles=n)
+    mpm = B.MPM.from_params(sc.params(), max_particles=n, p2g_mode=args.p2g_mode)
     wind = B.WindField(torch.from_numpy(sc.wind).to(dev), sc.t_total)
     st0 = B.MpmState(*(torch.from_numpy(a).to(dev) for a in inputs.rest_state(sc.x)))
     pin0 = torch.from_numpy(sc.pinned).to(dev)
@@ -257,7 +259,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "particles_per_gpu": n, "grid": sc.n_grid,
                    "substeps_per_step": args.substeps, "sort_every": SORT_EVERY,
                    "material": "neo-hookean E=5e4 nu=0.3", "wind": "32^3 x 16 Fourier",
-                   "l2": "flushed between timed steps (512 MB write)",
+                   "l2": "flushed between timed steps (512 MB write)", "p2g_mode": args.p2g_mode,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
