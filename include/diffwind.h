@@ -185,6 +185,31 @@ enum { DW_K_P2G = 0, DW_K_GRID = 1, DW_K_G2P = 2, DW_K_REV_G2P = 3, DW_K_REV_GRI
 DW_API dw_status mpm_profile_enable(dw_mpm h, int32_t max_records);
 DW_API dw_status mpm_profile_read(dw_mpm h, double *total_ms, int64_t *launches);
 
+/* The same substep as mpm_substep for callers that cannot allocate device
+ * memory when they need it (for example code running inside an allocator
+ * callback or under its lock, a real-time loop that forbids allocation after
+ * start-up, or a host whose memory pool owns the whole device and only lends
+ * out buffers). The paper has no counterpart; this is a deployment variant.
+ * No handle is needed: the scratch grid is a fixed device array inside the
+ * library, sized for n_grid <= 64 (64^3 nodes, 8 MB, held on every GPU that
+ * loads the library until the process exits); a larger n_grid is rejected
+ * with DW_ERR_ARG. The call allocates nothing: no cudaMalloc, no cudaFree,
+ * no allocating library routine. desc->max_particles is ignored; in, out,
+ * pinned, wind and t are as in mpm_substep, and `out` may equal `in`.
+ * device_status is an optional caller-owned device int32 into which
+ * device-side error bits are OR-ed (DW_ERR_DOMAIN -> 2, DW_ERR_NONFINITE -> 1,
+ * DW_ERR_INVERTED -> 8); with NULL those conditions are not reported.
+ * The first call on a device looks up the array's device address with the
+ * calling thread's current device (cudaGetSymbolAddress); make that first
+ * call before any stream capture. Every call on a device shares the one
+ * array and the call zeroes the part it uses before P2G, so calls that
+ * overlap on the GPU (different streams, or threads without ordering) race
+ * and must be serialised by the caller. */
+DW_API dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_state *in,
+                                     const dw_mpm_state *out, const uint8_t *pinned,
+                                     const dw_wind_field *wind, float t,
+                                     int32_t *device_status, dw_stream stream);
+
 /* ====================================================================== LBM
  * D3Q19 lattice Boltzmann step (Eq. lbe) with the BGK collision
  * f* = f - (f - f_eq)/tau (+ Guo forcing for a uniform body force F, with

@@ -59,6 +59,8 @@ SIGNATURES = {
     "mpm_device_status": (I32, [VP, VP]),
     "mpm_profile_enable": (I32, [VP, I32]),
     "mpm_profile_read": (I32, [VP, P(ct.c_double), P(I64)]),
+    "mpm_substep_noalloc": (I32, [P(DwMpmDesc), P(DwMpmState), P(DwMpmState), VP,
+                                  P(DwWindField), F32, VP, VP]),
     "lbm_create": (I32, [P(DwLbmDesc), P(VP)]),
     "lbm_destroy": (I32, [VP]),
     "lbm_step": (I32, [VP, VP, VP, I32, VP]),

@@ -19,7 +19,7 @@ from ._capi import (DiffWindError, DwLbmDesc, DwMpmDesc, DwMpmState, DwWindField
 __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "wind_field_sample_adjoint", "mpm_create", "mpm_destroy", "mpm_set_material",
            "mpm_substep", "mpm_substep_adjoint", "mpm_sort", "mpm_device_status",
-           "mpm_profile_enable", "mpm_profile_read", "lbm_create",
+           "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM"]
 
@@ -166,6 +166,25 @@ def mpm_sort(h, state_in: MpmState, state_out: MpmState, pinned_in, pinned_out, 
 
 def mpm_device_status(h, stream=None):
     check(lib().mpm_device_status(h, _stream(stream)))
+
+
+def mpm_substep_noalloc(desc_params: dict, state_in: MpmState, state_out: MpmState, pinned,
+                        wind: WindField, t, device_status=None, p2g_mode=P2G_AUTO, stream=None):
+    """mpm_substep without a handle: the scratch grid is the library's fixed
+    device array (n_grid <= 64), for callers that cannot allocate device
+    memory at call time. desc_params holds the dw_mpm_desc fields (n_grid,
+    dt, gravity, bc_band, material, E, nu, p_mass, p_vol); device_status is an
+    optional device int32[1] that receives device-side error bits."""
+    p = desc_params
+    d = DwMpmDesc(int(p["n_grid"]), float(p["dt"]), (ct.c_float * 3)(*p["gravity"]),
+                  int(p["bc_band"]), int(p["material"]), float(p["E"]), float(p["nu"]),
+                  float(p["p_mass"]), float(p["p_vol"]), 0, int(p2g_mode))
+    a, b, w = state_in.to_c(), state_out.to_c(), wind.to_c()
+    check(lib().mpm_substep_noalloc(ct.byref(d), ct.byref(a), ct.byref(b), _pin(pinned),
+                                    ct.byref(w), float(t),
+                                    _dev(device_status, torch.int32, "device_status"),
+                                    _stream(stream)))
+    return state_out
 
 
 KERNEL_NAMES = ["p2g", "grid", "g2p", "rev_g2p", "rev_grid", "rev_p2g", "sort"]

@@ -9,6 +9,7 @@
 // Grid layout: float4 per node, node (i, j, k) at ((k N + j) N + i).
 #include <stdio.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 #include <stdlib.h>
@@ -834,4 +835,106 @@ extern "C" dw_status mpm_device_status(dw_mpm h, dw_stream stream) {
     DW_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), s));
     DW_CUDA(cudaStreamSynchronize(s));
     return status_from_bits(bits);
+}
+
+// ---------------------------------------------------------------------------
+// mpm_substep_noalloc: one substep whose scratch grid lives in fixed device
+// memory that is part of the loaded library, so the call allocates nothing.
+//
+// Who needs it: callers that may not allocate device memory at the moment
+// they want a substep - code running under a caching allocator's callback or
+// inside its lock, a real-time control loop whose rules forbid allocation
+// after start-up, or a host framework that has handed the whole device to its
+// own memory pool and only lends out input and output buffers. Such callers
+// cannot use mpm_create, whose workspace comes from cudaMalloc.
+//
+// The array below is sized for grids of up to NOALLOC_MAX_GRID^3 nodes and is
+// held by every GPU that loads the library until the process exits.
+namespace dw {
+
+constexpr int NOALLOC_MAX_GRID = 64;
+constexpr int64_t NOALLOC_MAX_NODES = (int64_t)NOALLOC_MAX_GRID * NOALLOC_MAX_GRID * NOALLOC_MAX_GRID;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// [0, N^3): (m, p) after P2G; [NOALLOC_MAX_NODES, + N^3): (v, m) after the grid update
+static __device__ __align__(256) float4 g_noalloc_grid[2 * NOALLOC_MAX_NODES];
+static __device__ __align__(256) int g_noalloc_status;
+
+struct NoallocAddr {
+    float4 *grid = nullptr;
+    int *status = nullptr;
+};
+static NoallocAddr g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+// Device addresses of the static arrays on the current device, looked up once
+// per device (host code cannot use the symbols' names as device addresses).
+static dw_status noalloc_addresses(NoallocAddr *out) {
+    int dev = 0;
+    DW_CUDA(cudaGetDevice(&dev));
+    DW_REQUIRE(dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device %d beyond the supported %d", dev,
+               NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocAddr &a = g_noalloc_addr[dev];
+    if (!a.grid) {
+        void *g = nullptr, *s = nullptr;
+        DW_CUDA(cudaGetSymbolAddress(&g, g_noalloc_grid));
+        DW_CUDA(cudaGetSymbolAddress(&s, g_noalloc_status));
+        a.grid = (float4 *)g;
+        a.status = (int *)s;
+    }
+    *out = a;
+    return DW_OK;
+}
+
+}  // namespace dw
+
+extern "C" dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_state *in,
+                                         const dw_mpm_state *out, const uint8_t *pinned,
+                                         const dw_wind_field *wind, float t,
+                                         int32_t *device_status, dw_stream stream) {
+    DW_REQUIRE(desc, "desc must not be NULL");
+    DW_REQUIRE(desc->n_grid >= 8 && desc->n_grid <= NOALLOC_MAX_GRID,
+               "mpm_substep_noalloc supports n_grid in [8, %d] (its fixed grid holds %lld "
+               "nodes); got n_grid=%d", NOALLOC_MAX_GRID, (long long)NOALLOC_MAX_NODES,
+               desc->n_grid);
+    DW_REQUIRE(desc->dt > 0.0f, "dt must be > 0");
+    DW_REQUIRE(desc->bc_band >= 0 && desc->bc_band < desc->n_grid / 2, "bc_band out of range");
+    DW_REQUIRE(desc->material == DW_NEOHOOKEAN || desc->material == DW_FIXED_COROTATED,
+               "unknown material %d", desc->material);
+    DW_REQUIRE(desc->E > 0.0f && desc->nu >= 0.0f && desc->nu < 0.5f, "need E > 0 and 0 <= nu < 0.5");
+    DW_REQUIRE(desc->p_mass > 0.0f && desc->p_vol > 0.0f, "p_mass and p_vol must be > 0");
+    DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_TILE, "unknown p2g_mode");
+    DW_REQUIRE(in && out, "in/out must not be NULL");
+    DW_REQUIRE(in->n >= 0 && in->n == out->n && in->n < (1ll << 31), "bad particle counts");
+    DW_REQUIRE(in->n == 0 || (in->x && in->v && in->C && in->F && out->x && out->v && out->C && out->F),
+               "state arrays must not be NULL");
+    WindDev wd;
+    dw_status st = wind_check(wind, &wd);
+    if (st != DW_OK) return st;
+    NoallocAddr a;
+    st = noalloc_addresses(&a);
+    if (st != DW_OK) return st;
+    MpmHandle tmp;  // host-side parameter holder only; no device memory
+    tmp.desc = *desc;
+    fill_params(&tmp);
+    const MpmParams P = tmp.P;
+    const int64_t nodes = (int64_t)desc->n_grid * desc->n_grid * desc->n_grid;
+    float4 *grid_mp = a.grid;
+    float4 *grid_v = a.grid + NOALLOC_MAX_NODES;
+    int *err = device_status ? (int *)device_status : a.status;
+    cudaStream_t s = as_stream(stream);
+    // the previous call left the array with its contents: P2G needs zeros
+    DW_CUDA(cudaMemsetAsync(grid_mp, 0, sizeof(float4) * (size_t)nodes, s));
+    int64_t n = in->n;
+    st = launch_p2g(desc->p2g_mode, P, in->x, in->v, in->C, in->F, n, grid_mp, err, s);
+    if (st != DW_OK) return st;
+    k_grid_update<<<grid_for(nodes, 256), 256, 0, s>>>(P, wd, t, grid_mp, grid_v, 1);
+    DW_LAUNCHED("k_grid_update");
+    if (n > 0) {
+        k_g2p<<<grid_for(n, 128), 128, 0, s>>>(P, in->x, in->F, pinned, grid_v, out->x, out->v,
+                                               out->C, out->F, n, err);
+        DW_LAUNCHED("k_g2p");
+    }
+    return DW_OK;
 }
