@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--substeps", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint"],
+                    help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
+                         "or the checkpointed MPM adjoint")
     ap.add_argument("--p2g-mode", type=int, default=0,
                     help="P2G strategy: 0 auto, 1 global atomics, 2 warp-aggregated, 3 shared tile")
     return ap.parse_args()
@@ -297,16 +300,19 @@ def estimate_active_nodes(ro, sc):
 
 def roofline(prof, n, active_nodes):
     """Algorithmic bytes per launch of each substep kernel:
-      P2G  : x, v, C, F read (96 B / particle) + (m, p) written (16 B / node)
-      G2P  : x, F read (48 B / particle) + x, v, C, F written (96 B / particle)
-             + grid velocity read (16 B / node)
-      grid : (m, p) read, v written, (m, p) cleared (48 B / node of the grid)."""
+      P2G   : x, v, C, F read (96 B / particle) + (m, p) written (16 B / node)
+      G2P   : x, F read (48 B / particle) + x, v, C, F written (96 B / particle)
+              + grid velocity read (16 B / node)
+      G2P2G : x, F read and written (96 B / particle) + grid velocity read and
+              (m, p) of the next substep written (32 B / node)
+      grid  : (m, p) read, v written, (m, p) cleared (48 B / active node)."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    per = {"p2g": 96 * n + 16 * active_nodes, "g2p": 144 * n + 16 * active_nodes}
+    per = {"p2g": 96 * n + 16 * active_nodes, "g2p": 144 * n + 16 * active_nodes,
+           "g2p2g": 96 * n + 32 * active_nodes, "grid": 48 * active_nodes}
     best = None
-    for k in ("p2g", "g2p", "grid"):
+    for k in ("p2g", "g2p", "grid", "g2p2g"):
         ms, cnt = prof.get(k, (0.0, 0))
         if cnt and (best is None or ms > best[1]):
             best = (k, ms, cnt)
@@ -323,48 +329,62 @@ def roofline(prof, n, active_nodes):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
 
 
-def extras(dev):
+def _timed(fn, reps=3):
+    import torch
+
+    stream = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return min(ts)
+
+
+def bench_lbm(dev, steps=200, adj_steps=20):
+    """D3Q19 step and adjoint on 128^3 with the leaf-cluster obstacle (200k
+    particles in 50 ellipsoids, voxelized by Eq. point2voxel), tau = 0.55,
+    inlet 0.05. Algorithmic bytes: 152 B per cell-step forward."""
+    import torch
+
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import inputs
+
+    out = {}
+    shape = (128, 128, 128)
+    pts = torch.from_numpy(inputs.ellipsoid_cluster()).to(dev)
+    solid = torch.empty((128, 128, 128), dtype=torch.uint8, device=dev)
+    B.voxelize_particles(pts, shape, 1.0 / 128, solid)
+    lbm = B.LBM(shape, 0.55, u_inlet=(0.05, 0.0, 0.0), bc_x=1, max_tape=max(adj_steps, 1))
+    f = lbm.lattice(dev)
+    ms = _timed(lambda: lbm.step(f, solid, steps))
+    cells = 128 ** 3
+    out["lbm_128_fwd_mlups"] = cells * steps / (ms * 1e-3) / 1e6
+    out["lbm_128_fwd_gbs"] = 152 * cells * steps / (ms * 1e-3) / 1e9
+    if adj_steps:
+        g = torch.randn_like(f)
+        ms = _timed(lambda: lbm.step_adjoint(f, g, solid, adj_steps))
+        out["lbm_128_adj_mlups"] = cells * adj_steps / (ms * 1e-3) / 1e6
+    lbm.close()
+    return out
+
+
+def bench_adjoint(dev):
+    """MPM forward + adjoint with checkpointing: the 100k-particle sheet on 64^3,
+    200 substeps, checkpoint every 20, loss on positions at the checkpoints,
+    gradients with respect to the 32^3 x 16 wind grid and E."""
     import torch
 
     from paper_2603_09668_gb300 import autograd as AG
     from paper_2603_09668_gb300 import binding as B
     from paper_2603_09668_gb300 import inputs
 
-    out = {}
-    stream = torch.cuda.current_stream()
-
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return min(ts)
-
-    # LBM 128^3 with the leaf-cluster obstacle
-    shape = (128, 128, 128)
-    pts = torch.from_numpy(inputs.ellipsoid_cluster()).to(dev)
-    solid = torch.empty((128, 128, 128), dtype=torch.uint8, device=dev)
-    B.voxelize_particles(pts, shape, 1.0 / 128, solid)
-    lbm = B.LBM(shape, 0.55, u_inlet=(0.05, 0.0, 0.0), bc_x=1, max_tape=20)
-    f = lbm.lattice(dev)
-    steps = 200
-    ms = timed(lambda: lbm.step(f, solid, steps))
-    cells = 128 ** 3
-    out["lbm_128_fwd_mlups"] = cells * steps / (ms * 1e-3) / 1e6
-    out["lbm_128_fwd_gbs"] = 152 * cells * steps / (ms * 1e-3) / 1e9
-    g = torch.randn_like(f)
-    ms = timed(lambda: lbm.step_adjoint(f, g, solid, 20))
-    out["lbm_128_adj_mlups"] = cells * 20 / (ms * 1e-3) / 1e6
-    lbm.close()
-
-    # MPM forward + adjoint with checkpointing (100k sheet, 64^3, 200 substeps)
     sc = inputs.sheet_scene(nu=274, nv=183, n_grid=64, n_substeps=200, dt=5e-5, seed=0,
                             wind_seed=0)
     mpm = B.MPM.from_params(sc.params(), max_particles=sc.n)
@@ -379,10 +399,15 @@ def extras(dev):
         loss = ((X - target) ** 2).sum() / sc.n
         loss.backward()
 
-    ms = timed(fwd_adj, reps=2)
-    out["mpm_adj_sheet100k_64_ps_per_s"] = sc.n * 200 / (ms * 1e-3)
-    out["mpm_adj_note"] = "200 substeps forward + checkpointed adjoint (recompute + reverse)"
+    ms = _timed(fwd_adj, reps=2)
     mpm.close()
+    return {"mpm_adj_sheet100k_64_ps_per_s": sc.n * 200 / (ms * 1e-3),
+            "mpm_adj_note": "200 substeps forward + checkpointed adjoint (recompute + reverse)"}
+
+
+def extras(dev):
+    out = bench_lbm(dev)
+    out.update(bench_adjoint(dev))
     return out
 
 
@@ -442,9 +467,26 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_only(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2603_09668_gb300 import build as _build
+
+    _build.build_library()
+    if args.only == "lbm":
+        res = bench_lbm(dev, steps=2 * max(args.steps, 1), adj_steps=2)
+    else:
+        res = bench_adjoint(dev)
+    print(json.dumps({"only": args.only, **res}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.only in ("lbm", "adjoint"):
+        run_only(a)
     else:
         run_ours(a)

@@ -169,6 +169,21 @@ DW_API dw_status mpm_sort(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *
                           const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
                           int32_t *ids_out, dw_stream stream);
 
+/* n_substeps substeps of mpm_substep at times t0, t0 + dt, ... applied in
+ * place to `state` (Eq. simulation_mpm iterated), the same arithmetic as
+ * calling mpm_substep n_substeps times. Every sort_every substeps (0 = never)
+ * the particles are re-sorted by cell as in mpm_sort, so on return the arrays
+ * hold the particles in a new order: `pinned` (device uint8[n] or NULL) is
+ * permuted along, and ids (device int32[n], required when sort_every > 0) is
+ * carried through the sorts (ids_out[k] = ids_in[perm[k]]), so filling it with
+ * 0..n-1 beforehand yields each particle's original index. Between sorts the
+ * G2P of one substep and the P2G of the next run fused in one kernel, which
+ * keeps v and C in registers; the state is complete at every sort and at the
+ * end. Uses the handle's second state buffer (max_particles). */
+DW_API dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *pinned, int32_t *ids,
+                             const dw_wind_field *wind, float t0, int32_t n_substeps,
+                             int32_t sort_every, dw_stream stream);
+
 /* Waits for `stream`, returns the first device-side error recorded on this
  * handle since the last call (DW_OK if none) and clears it. */
 DW_API dw_status mpm_device_status(dw_mpm h, dw_stream stream);
@@ -181,7 +196,7 @@ DW_API dw_status mpm_device_status(dw_mpm h, dw_stream stream);
  * DW_K_*, the summed device milliseconds and the launch count since enable,
  * then clears them. Arrays have DW_K_COUNT entries. */
 enum { DW_K_P2G = 0, DW_K_GRID = 1, DW_K_G2P = 2, DW_K_REV_G2P = 3, DW_K_REV_GRID = 4,
-       DW_K_REV_P2G = 5, DW_K_SORT = 6, DW_K_COUNT = 7 };
+       DW_K_REV_P2G = 5, DW_K_SORT = 6, DW_K_G2P2G = 7, DW_K_COUNT = 8 };
 DW_API dw_status mpm_profile_enable(dw_mpm h, int32_t max_records);
 DW_API dw_status mpm_profile_read(dw_mpm h, double *total_ms, int64_t *launches);
 

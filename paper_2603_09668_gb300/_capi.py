@@ -57,6 +57,7 @@ SIGNATURES = {
                                   P(DwWindField), F32, VP, VP, VP]),
     "mpm_sort": (I32, [VP, P(DwMpmState), P(DwMpmState), VP, VP, VP, VP, VP]),
     "mpm_device_status": (I32, [VP, VP]),
+    "mpm_rollout": (I32, [VP, P(DwMpmState), VP, VP, P(DwWindField), F32, I32, I32, VP]),
     "mpm_profile_enable": (I32, [VP, I32]),
     "mpm_profile_read": (I32, [VP, P(ct.c_double), P(I64)]),
     "mpm_substep_noalloc": (I32, [P(DwMpmDesc), P(DwMpmState), P(DwMpmState), VP,

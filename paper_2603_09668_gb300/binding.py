@@ -18,7 +18,7 @@ from ._capi import (DiffWindError, DwLbmDesc, DwMpmDesc, DwMpmState, DwWindField
 
 __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "wind_field_sample_adjoint", "mpm_create", "mpm_destroy", "mpm_set_material",
-           "mpm_substep", "mpm_substep_adjoint", "mpm_sort", "mpm_device_status",
+           "mpm_substep", "mpm_substep_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM"]
@@ -168,6 +168,15 @@ def mpm_device_status(h, stream=None):
     check(lib().mpm_device_status(h, _stream(stream)))
 
 
+def mpm_rollout(h, state: MpmState, pinned, ids, wind: WindField, t0, n_substeps, sort_every,
+                stream=None):
+    a, w = state.to_c(), wind.to_c()
+    check(lib().mpm_rollout(h, ct.byref(a), _pin(pinned), _dev(ids, torch.int32, "ids"),
+                            ct.byref(w), float(t0), int(n_substeps), int(sort_every),
+                            _stream(stream)))
+    return state
+
+
 def mpm_substep_noalloc(desc_params: dict, state_in: MpmState, state_out: MpmState, pinned,
                         wind: WindField, t, device_status=None, p2g_mode=P2G_AUTO, stream=None):
     """mpm_substep without a handle: the scratch grid is the library's fixed
@@ -187,7 +196,7 @@ def mpm_substep_noalloc(desc_params: dict, state_in: MpmState, state_out: MpmSta
     return state_out
 
 
-KERNEL_NAMES = ["p2g", "grid", "g2p", "rev_g2p", "rev_grid", "rev_p2g", "sort"]
+KERNEL_NAMES = ["p2g", "grid", "g2p", "rev_g2p", "rev_grid", "rev_p2g", "sort", "g2p2g"]
 
 
 def mpm_profile_enable(h, max_records):
@@ -299,6 +308,9 @@ class MPM:
 
     def device_status(self, stream=None):
         mpm_device_status(self.h, stream)
+
+    def rollout(self, state, pinned, ids, wind, t0, n_substeps, sort_every, stream=None):
+        return mpm_rollout(self.h, state, pinned, ids, wind, t0, n_substeps, sort_every, stream)
 
     def profile_enable(self, max_records):
         mpm_profile_enable(self.h, max_records)

@@ -140,7 +140,7 @@ __device__ __forceinline__ int cell_index(const LbmParams &L, int x, int y, int 
 
 // ---------------------------------------------------------------- forward --
 
-__global__ void __launch_bounds__(256) k_lbm_aa_even(LbmParams L, float *f,
+__global__ void __launch_bounds__(256, 4) k_lbm_aa_even(LbmParams L, float *f,
                                                     const uint8_t *__restrict__ solid,
                                                     float *__restrict__ outlet) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_lbm_aa_even(LbmParams L, float *f,
     }
 }
 
-__global__ void __launch_bounds__(256) k_lbm_aa_odd(LbmParams L, float *f,
+__global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
                                                    const uint8_t *__restrict__ solid,
                                                    const float *__restrict__ outlet) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_lbm_aa_odd(LbmParams L, float *f,
 
 // One collide + push step between two lattices in natural order. Solid cells
 // are copied so that fout holds a complete lattice.
-__global__ void __launch_bounds__(256) k_lbm_push(LbmParams L, const float *__restrict__ fin,
+__global__ void __launch_bounds__(256, 4) k_lbm_push(LbmParams L, const float *__restrict__ fin,
                                                  float *__restrict__ fout,
                                                  const uint8_t *__restrict__ solid) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) k_lbm_push(LbmParams L, const float *__re
 // ---------------------------------------------------------------- reverse --
 
 // One reverse step: g_prev = C^T S^T g_next at the pre-collision state f_t.
-__global__ void __launch_bounds__(256) k_lbm_adjoint(LbmParams L, const float *__restrict__ f_t,
+__global__ void __launch_bounds__(256, 4) k_lbm_adjoint(LbmParams L, const float *__restrict__ f_t,
                                                     const float *__restrict__ g_next,
                                                     float *__restrict__ g_prev,
                                                     const uint8_t *__restrict__ solid) {

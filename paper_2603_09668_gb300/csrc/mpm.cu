@@ -14,188 +14,102 @@
 #include <vector>
 #include <stdlib.h>
 
-#include "mpm_math.cuh"
-#include "mpm_p2g.cuh"
-#include "wind.cuh"
+#include "mpm_handle.cuh"
 
 namespace dw {
 
-struct MpmHandle {
-    dw_mpm_desc desc;
-    MpmParams P;
-    int64_t n_nodes;
-    float4 *grid_mp = nullptr;   // (m, p) after P2G; zero between calls
-    float4 *grid_v = nullptr;    // (v, m) after the grid update
-    float4 *grid_bv = nullptr;   // dL/dv_i during the adjoint; zero between calls
-    float4 *grid_bmp = nullptr;  // (dL/dm_i, dL/dp_i) during the adjoint
-    float *pscratch = nullptr;   // [12][max_particles]: partial dL/dx (3), dL/dF (9)
-    int *err = nullptr;          // device status bits
-    // sort workspace
-    int nb = 0;                  // 4^3 blocks per axis
-    int64_t n_keys = 0;
-    int *keys = nullptr;         // [max_particles]
-    int *perm = nullptr;         // [max_particles]
-    int *counts = nullptr;       // [n_keys + 1]
-    int *scan_tmp = nullptr;     // block sums for the exclusive scan
-    int64_t scan_tmp_len = 0;
-    // instrumentation: event pairs around kernel launches
-    std::vector<cudaEvent_t> ev_start, ev_stop;
-    std::vector<int> ev_kernel;
-    int prof_used = 0;
-};
-
-// Brackets one kernel launch with events when profiling is enabled.
-struct ProfScope {
-    MpmHandle *h;
-    cudaStream_t s;
-    int slot = -1;
-    ProfScope(MpmHandle *h_, int kid, cudaStream_t s_) : h(h_), s(s_) {
-        if (h->prof_used < (int)h->ev_start.size()) {
-            slot = h->prof_used++;
-            h->ev_kernel[slot] = kid;
-            cudaEventRecord(h->ev_start[slot], s);
-        }
-    }
-    ~ProfScope() {
-        if (slot >= 0) cudaEventRecord(h->ev_stop[slot], s);
-    }
-};
-
-static void profile_free(MpmHandle *h) {
-    for (auto e : h->ev_start) cudaEventDestroy(e);
-    for (auto e : h->ev_stop) cudaEventDestroy(e);
-    h->ev_start.clear();
-    h->ev_stop.clear();
-    h->ev_kernel.clear();
-    h->prof_used = 0;
-}
-
-static void fill_params(MpmHandle *h) {
-    const dw_mpm_desc &d = h->desc;
-    MpmParams &P = h->P;
-    P.N = d.n_grid;
-    P.dx = 1.0f / (float)d.n_grid;
-    P.inv_dx = (float)d.n_grid;
-    P.dt = d.dt;
-    P.D = 4.0f * (float)d.n_grid * (float)d.n_grid;
-    P.gx = d.gravity[0];
-    P.gy = d.gravity[1];
-    P.gz = d.gravity[2];
-    P.band = d.bc_band;
-    P.material = d.material;
-    double E = d.E, nu = d.nu;
-    P.mu = (float)(E / (2.0 * (1.0 + nu)));                       // Eq. young_poisson
-    P.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
-    P.E = d.E;
-    P.p_mass = d.p_mass;
-    P.p_vol = d.p_vol;
-    P.kappa = d.dt * d.p_vol * P.D;
-}
-
 // --------------------------------------------------------------- forward --
 
+__device__ __forceinline__ bool sticky_node(const MpmParams &P, int i, int j, int k) {
+    return i < P.band || j < P.band || k < P.band || i > P.N - 1 - P.band ||
+           j > P.N - 1 - P.band || k > P.N - 1 - P.band;
+}
+
+// Grid update of one node: v_i = p_i / m_i + dt (g + a_w(x_i, t)), zero in the
+// sticky band and at empty nodes; (v, m) goes to grid_v.
+__device__ __forceinline__ void grid_node_update(const MpmParams &P, const WindDev &wind, float t,
+                                                 int64_t node, int i, int j, int k,
+                                                 float4 *__restrict__ grid_mp,
+                                                 float4 *__restrict__ grid_v, int clear) {
+    float4 mp = grid_mp[node];
+    float4 out = make_float4(0.f, 0.f, 0.f, mp.x);
+    if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
+        float3 a = wind_sample_dev(wind, i * P.dx, j * P.dx, k * P.dx, t);
+        float inv_m = 1.0f / mp.x;
+        out.x = mp.y * inv_m + P.dt * (P.gx + a.x);
+        out.y = mp.z * inv_m + P.dt * (P.gy + a.y);
+        out.z = mp.w * inv_m + P.dt * (P.gz + a.z);
+    }
+    grid_v[node] = out;
+    if (clear) grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Dense grid update over every node (used without an active-block list).
 __global__ void k_grid_update(MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp,
                               float4 *__restrict__ grid_v, int clear) {
     int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nn = (int64_t)P.N * P.N * P.N;
     if (node >= nn) return;
-    float4 mp = grid_mp[node];
-    float4 out = make_float4(0.f, 0.f, 0.f, mp.x);
-    if (mp.x > 0.0f) {
-        int i = (int)(node % P.N), j = (int)((node / P.N) % P.N), k = (int)(node / ((int64_t)P.N * P.N));
-        bool sticky = i < P.band || j < P.band || k < P.band || i > P.N - 1 - P.band ||
-                      j > P.N - 1 - P.band || k > P.N - 1 - P.band;
-        if (!sticky) {
-            float3 a = wind_sample_dev(wind, i * P.dx, j * P.dx, k * P.dx, t);
-            float inv_m = 1.0f / mp.x;
-            out.x = mp.y * inv_m + P.dt * (P.gx + a.x);
-            out.y = mp.z * inv_m + P.dt * (P.gy + a.y);
-            out.z = mp.w * inv_m + P.dt * (P.gz + a.z);
+    int i = (int)(node % P.N), j = (int)((node / P.N) % P.N), k = (int)(node / ((int64_t)P.N * P.N));
+    grid_node_update(P, wind, t, node, i, j, k, grid_mp, grid_v, clear);
+}
+
+// Node (i, j, k) of thread t within active block b; false outside the grid.
+__device__ __forceinline__ bool active_node(const MpmParams &P, int nb, int b, int t, int &i,
+                                            int &j, int &k) {
+    int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+    i = bx * 4 + (t & 3);
+    j = by * 4 + ((t >> 2) & 3);
+    k = bz * 4 + (t >> 4);
+    return i < P.N && j < P.N && k < P.N;
+}
+
+// Grid update over the active blocks only; with clear, also zeroes (m, p)
+// and the block flags so that the grid is empty for the next P2G.
+__global__ void __launch_bounds__(GRID_THREADS) k_grid_update_active(
+    MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_v,
+    int clear, ActiveBlocks ab) {
+    const int count = *ab.count;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
+        int b = ab.list[e];
+        int i, j, k;
+        if (active_node(P, ab.nb, b, lt, i, j, k)) {
+            int64_t node = ((int64_t)k * P.N + j) * P.N + i;
+            grid_node_update(P, wind, t, node, i, j, k, grid_mp, grid_v, clear);
         }
+        if (clear && lt == 0) ab.flags[b] = 0;
     }
-    grid_v[node] = out;
-    if (clear) grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // x/xo and F/Fo may be the same arrays (in-place substep): every thread reads
 // its particle before writing it, so they carry no __restrict__.
 __global__ void k_g2p(MpmParams P, const float *x, const float *F,
                       const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
-                      float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err) {
+                      float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err,
+                      int *reset_count) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (reset_count && p == 0) *reset_count = 0;  // the grid update has consumed the list
     if (p >= n) return;
     float xp[3] = {x[p], x[n + p], x[2 * n + p]};
     float Fp[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
-    Stencil s;
-    if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
-        // out of range: leave the particle as it was (P2G has flagged it)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            xo[a * n + p] = xp[a];
-            vo[a * n + p] = 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            Co[k * n + p] = 0.0f;
-            Fo[k * n + p] = Fp[k];
-        }
-        return;
-    }
-    float vn[3] = {0.f, 0.f, 0.f};
-    float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const int N = P.N;
-#pragma unroll
-    for (int oi = 0; oi < 3; ++oi)
-#pragma unroll
-        for (int oj = 0; oj < 3; ++oj)
-#pragma unroll
-            for (int ok = 0; ok < 3; ++ok) {
-                float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
-                float d0 = ((float)oi - s.fx[0]) * P.dx, d1 = ((float)oj - s.fx[1]) * P.dx,
-                      d2 = ((float)ok - s.fx[2]) * P.dx;
-                int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
-                float4 gv = grid_v[id];
-                float wv[3] = {W * gv.x, W * gv.y, W * gv.z};
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    vn[a] += wv[a];
-                    Cn[3 * a + 0] += wv[a] * d0;
-                    Cn[3 * a + 1] += wv[a] * d1;
-                    Cn[3 * a + 2] += wv[a] * d2;
-                }
-            }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Cn[k] *= P.D;
-    if (pinned && pinned[p]) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) vn[a] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Cn[k] = 0.0f;
-    }
-    float M[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) M[k] = P.dt * Cn[k];
-    M[0] += 1.0f;
-    M[4] += 1.0f;
-    M[8] += 1.0f;
-    float Fn[9];
-    mul3(M, Fp, Fn);
+    float vn[3], Cn[9];
+    g2p_update(P, grid_v, pinned && pinned[p], xp, Fp, vn, Cn);  // out of range: unchanged
     bool fin = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float xn = xp[a] + P.dt * vn[a];
-        fin = fin && isfinite(xn);
-        xo[a * n + p] = xn;
+        fin = fin && isfinite(xp[a]);
+        xo[a * n + p] = xp[a];
         vo[a * n + p] = vn[a];
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         Co[k * n + p] = Cn[k];
-        Fo[k * n + p] = Fn[k];
+        Fo[k * n + p] = Fp[k];
     }
-    if (!fin || !finite9(Fn)) atomicOr(err, ERRBIT_NONFINITE);
+    if (!fin || !finite9(Fp)) atomicOr(err, ERRBIT_NONFINITE);
 }
 
 // --------------------------------------------------------------- reverse --
@@ -317,43 +231,56 @@ __global__ void k_rev_g2p(MpmParams P, const float *__restrict__ x, const float 
     for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = bFin[k];
 }
 
-// Reverse grid update: (dL/dm_i, dL/dp_i) into grid_bmp, wind gradient scatter,
-// and clearing of grid_mp and grid_bv for the next call.
-__global__ void k_rev_grid(MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp,
-                           float4 *__restrict__ grid_bv, float4 *__restrict__ grid_bmp,
-                           float *__restrict__ g_wind) {
-    int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nn = (int64_t)P.N * P.N * P.N;
-    if (node >= nn) return;
+// Reverse grid update of one node: (dL/dm_i, dL/dp_i) into grid_bmp, wind
+// gradient scatter, and clearing of grid_mp and grid_bv for the next call.
+__device__ __forceinline__ void rev_grid_node(const MpmParams &P, const WindDev &wind, float t,
+                                              int64_t node, int i, int j, int k,
+                                              float4 *__restrict__ grid_mp,
+                                              float4 *__restrict__ grid_bv,
+                                              float4 *__restrict__ grid_bmp,
+                                              float *__restrict__ g_wind) {
     float4 mp = grid_mp[node];
     float4 bmp = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (mp.x > 0.0f) {
-        int i = (int)(node % P.N), j = (int)((node / P.N) % P.N), k = (int)(node / ((int64_t)P.N * P.N));
-        bool sticky = i < P.band || j < P.band || k < P.band || i > P.N - 1 - P.band ||
-                      j > P.N - 1 - P.band || k > P.N - 1 - P.band;
-        if (!sticky) {
-            float4 b = grid_bv[node];
-            float inv_m = 1.0f / mp.x;
-            bmp.y = b.x * inv_m;
-            bmp.z = b.y * inv_m;
-            bmp.w = b.z * inv_m;
-            bmp.x = -(mp.y * b.x + mp.z * b.y + mp.w * b.z) * inv_m * inv_m;
-            if (g_wind)
-                wind_sample_adjoint_dev(wind, i * P.dx, j * P.dx, k * P.dx, t,
-                                        make_float3(P.dt * b.x, P.dt * b.y, P.dt * b.z), g_wind);
-        }
+    if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
+        float4 b = grid_bv[node];
+        float inv_m = 1.0f / mp.x;
+        bmp.y = b.x * inv_m;
+        bmp.z = b.y * inv_m;
+        bmp.w = b.z * inv_m;
+        bmp.x = -(mp.y * b.x + mp.z * b.y + mp.w * b.z) * inv_m * inv_m;
+        if (g_wind)
+            wind_sample_adjoint_dev(wind, i * P.dx, j * P.dx, k * P.dx, t,
+                                    make_float3(P.dt * b.x, P.dt * b.y, P.dt * b.z), g_wind);
     }
     grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     grid_bv[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     grid_bmp[node] = bmp;
 }
 
+__global__ void __launch_bounds__(GRID_THREADS) k_rev_grid_active(
+    MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_bv,
+    float4 *__restrict__ grid_bmp, float *__restrict__ g_wind, ActiveBlocks ab) {
+    const int count = *ab.count;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
+        int b = ab.list[e];
+        int i, j, k;
+        if (active_node(P, ab.nb, b, lt, i, j, k)) {
+            int64_t node = ((int64_t)k * P.N + j) * P.N + i;
+            rev_grid_node(P, wind, t, node, i, j, k, grid_mp, grid_bv, grid_bmp, g_wind);
+        }
+        if (lt == 0) ab.flags[b] = 0;
+    }
+}
+
 __global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float *__restrict__ v,
                           const float *__restrict__ C, const float *__restrict__ F,
                           const float4 *__restrict__ grid_bmp, const float *__restrict__ scratch,
                           float *__restrict__ gx, float *__restrict__ gv, float *__restrict__ gC,
-                          float *__restrict__ gF, float *__restrict__ g_E, int64_t n, int64_t cap) {
+                          float *__restrict__ gF, float *__restrict__ g_E, int64_t n, int64_t cap,
+                          int *reset_count) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (reset_count && p == 0) *reset_count = 0;  // the reverse grid update has consumed the list
     float gE_local = 0.0f;
     if (p < n) {
         float xp[3] = {x[p], x[n + p], x[2 * n + p]};
@@ -583,7 +510,7 @@ static dw_status device_exclusive_scan(MpmHandle *h, int *data, int64_t len, cud
 
 // --------------------------------------------------------------- helpers --
 
-static dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *name) {
+dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *name) {
     DW_REQUIRE(s != nullptr, "%s state is NULL", name);
     DW_REQUIRE(s->n >= 0 && s->n <= h->desc.max_particles,
                "%s state has n=%lld particles; the handle holds at most %lld", name,
@@ -595,8 +522,9 @@ static dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const ch
 static dw_status launch_grid_update(MpmHandle *h, const WindDev &wd, float t, int clear,
                                     cudaStream_t st) {
     ProfScope ps(h, DW_K_GRID, st);
-    k_grid_update<<<grid_for(h->n_nodes, 256), 256, 0, st>>>(h->P, wd, t, h->grid_mp, h->grid_v, clear);
-    DW_LAUNCHED("k_grid_update");
+    k_grid_update_active<<<GRID_CTAS, GRID_THREADS, 0, st>>>(h->P, wd, t, h->grid_mp, h->grid_v,
+                                                             clear, active_blocks(h));
+    DW_LAUNCHED("k_grid_update_active");
     return DW_OK;
 }
 
@@ -604,7 +532,6 @@ static dw_status launch_grid_update(MpmHandle *h, const WindDev &wd, float t, in
 
 using namespace dw;
 
-struct dw_mpm_s : MpmHandle {};
 
 extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
     DW_REQUIRE(desc && out, "desc/out must not be NULL");
@@ -646,10 +573,20 @@ extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
     DW_ALLOC(h->perm, sizeof(int) * (size_t)cap);
     DW_ALLOC(h->counts, sizeof(int) * (size_t)(h->n_keys + 1));
     DW_ALLOC(h->scan_tmp, sizeof(int) * (size_t)h->scan_tmp_len);
+    const size_t nblk = (size_t)h->nb * h->nb * h->nb;
+    h->nblk = (int64_t)nblk;
+    DW_ALLOC(h->block_flag, sizeof(int) * nblk);
+    DW_ALLOC(h->block_list, sizeof(int) * 2 * nblk);
+    DW_ALLOC(h->block_count, sizeof(int) * 2);
+    DW_ALLOC(h->roll_state, sizeof(float) * 24 * (size_t)cap);
+    DW_ALLOC(h->roll_pinned, (size_t)cap);
+    DW_ALLOC(h->roll_ids, sizeof(int32_t) * (size_t)cap);
 #undef DW_ALLOC
     if (e == cudaSuccess) e = cudaMemset(h->grid_mp, 0, gbytes);
     if (e == cudaSuccess) e = cudaMemset(h->grid_bv, 0, gbytes);
     if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->block_flag, 0, sizeof(int) * nblk);
+    if (e == cudaSuccess) e = cudaMemset(h->block_count, 0, sizeof(int) * 2);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dw_status st = cuda_fail(e, "mpm_create");
@@ -672,6 +609,12 @@ extern "C" dw_status mpm_destroy(dw_mpm h) {
     cudaFree(h->perm);
     cudaFree(h->counts);
     cudaFree(h->scan_tmp);
+    cudaFree(h->block_flag);
+    cudaFree(h->block_list);
+    cudaFree(h->block_count);
+    cudaFree(h->roll_state);
+    cudaFree(h->roll_pinned);
+    cudaFree(h->roll_ids);
     profile_free(h);
     delete h;
     return DW_OK;
@@ -733,7 +676,8 @@ extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_
     int64_t n = in->n;
     {
         ProfScope ps(h, DW_K_P2G, s);
-        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err, s);
+        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err,
+                        active_blocks(h), s);
     }
     if (st != DW_OK) return st;
     st = launch_grid_update(h, wd, t, 1, s);
@@ -741,7 +685,7 @@ extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_
     if (n > 0) {
         ProfScope ps(h, DW_K_G2P, s);
         k_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v, out->x,
-                                               out->v, out->C, out->F, n, h->err);
+                                               out->v, out->C, out->F, n, h->err, h->block_count);
         DW_LAUNCHED("k_g2p");
     }
     return DW_OK;
@@ -767,7 +711,8 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
     int64_t cap = h->desc.max_particles > 0 ? h->desc.max_particles : 1;
     {
         ProfScope ps(h, DW_K_P2G, s);
-        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err, s);
+        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err,
+                        active_blocks(h), s);
     }
     if (st != DW_OK) return st;
     st = launch_grid_update(h, wd, t, 0, s);
@@ -781,19 +726,43 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
     }
     {
         ProfScope ps(h, DW_K_REV_GRID, s);
-        k_rev_grid<<<grid_for(h->n_nodes, 256), 256, 0, s>>>(h->P, wd, t, h->grid_mp, h->grid_bv,
-                                                              h->grid_bmp, g_wind);
+        k_rev_grid_active<<<GRID_CTAS, GRID_THREADS, 0, s>>>(h->P, wd, t, h->grid_mp, h->grid_bv,
+                                                             h->grid_bmp, g_wind, active_blocks(h));
     }
-    DW_LAUNCHED("k_rev_grid");
+    DW_LAUNCHED("k_rev_grid_active");
     if (n > 0) {
         ProfScope ps(h, DW_K_REV_P2G, s);
         k_rev_p2g<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->v, in->C, in->F, h->grid_bmp,
                                                    h->pscratch, g_in->x, g_in->v, g_in->C,
-                                                   g_in->F, g_E, n, cap);
+                                                   g_in->F, g_E, n, cap, h->block_count);
         DW_LAUNCHED("k_rev_p2g");
     }
     return DW_OK;
 }
+
+namespace dw {
+
+dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_state *out,
+                         const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
+                         int32_t *ids_out, cudaStream_t s) {
+    int64_t n = in->n;
+    if (n == 0) return DW_OK;
+    ProfScope ps(h, DW_K_SORT, s);
+    DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
+    k_sort_keys<<<grid_for(n, 256), 256, 0, s>>>(h->P, h->nb, in->x, n, h->keys, h->counts);
+    DW_LAUNCHED("k_sort_keys");
+    dw_status st = device_exclusive_scan(h, h->counts, h->n_keys, s);
+    if (st != DW_OK) return st;
+    k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, h->perm);
+    DW_LAUNCHED("k_sort_scatter");
+    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in->x, in->v, in->C, in->F, pinned_in,
+                                               ids_in, out->x, out->v, out->C, out->F, pinned_out,
+                                               ids_out);
+    DW_LAUNCHED("k_permute");
+    return DW_OK;
+}
+
+}  // namespace dw
 
 extern "C" dw_status mpm_sort(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
                               const uint8_t *pinned_in, uint8_t *pinned_out,
@@ -806,24 +775,10 @@ extern "C" dw_status mpm_sort(dw_mpm h, const dw_mpm_state *in, const dw_mpm_sta
     DW_REQUIRE(in->n == out->n, "input and output particle counts differ");
     DW_REQUIRE(in->n == 0 || in->x != out->x, "mpm_sort cannot run in place");
     DW_REQUIRE(!pinned_in || pinned_out, "pinned_out must be given with pinned_in");
-    int64_t n = in->n;
-    if (n == 0) return DW_OK;
+    if (in->n == 0) return DW_OK;
     DW_REQUIRE(ids_out, "ids_out must not be NULL");
     DW_REQUIRE(!ids_in || ids_in != ids_out, "ids_in and ids_out must differ");
-    cudaStream_t s = as_stream(stream);
-    ProfScope ps(h, DW_K_SORT, s);
-    DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
-    k_sort_keys<<<grid_for(n, 256), 256, 0, s>>>(h->P, h->nb, in->x, n, h->keys, h->counts);
-    DW_LAUNCHED("k_sort_keys");
-    st = device_exclusive_scan(h, h->counts, h->n_keys, s);
-    if (st != DW_OK) return st;
-    k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, h->perm);
-    DW_LAUNCHED("k_sort_scatter");
-    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in->x, in->v, in->C, in->F, pinned_in,
-                                               ids_in, out->x, out->v, out->C, out->F, pinned_out,
-                                               ids_out);
-    DW_LAUNCHED("k_permute");
-    return DW_OK;
+    return sort_particles(h, in, out, pinned_in, pinned_out, ids_in, ids_out, as_stream(stream));
 }
 
 extern "C" dw_status mpm_device_status(dw_mpm h, dw_stream stream) {
@@ -927,13 +882,14 @@ extern "C" dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_s
     // the previous call left the array with its contents: P2G needs zeros
     DW_CUDA(cudaMemsetAsync(grid_mp, 0, sizeof(float4) * (size_t)nodes, s));
     int64_t n = in->n;
-    st = launch_p2g(desc->p2g_mode, P, in->x, in->v, in->C, in->F, n, grid_mp, err, s);
+    const ActiveBlocks dense{nullptr, nullptr, nullptr, 0};
+    st = launch_p2g(desc->p2g_mode, P, in->x, in->v, in->C, in->F, n, grid_mp, err, dense, s);
     if (st != DW_OK) return st;
     k_grid_update<<<grid_for(nodes, 256), 256, 0, s>>>(P, wd, t, grid_mp, grid_v, 1);
     DW_LAUNCHED("k_grid_update");
     if (n > 0) {
         k_g2p<<<grid_for(n, 128), 128, 0, s>>>(P, in->x, in->F, pinned, grid_v, out->x, out->v,
-                                               out->C, out->F, n, err);
+                                               out->C, out->F, n, err, nullptr);
         DW_LAUNCHED("k_g2p");
     }
     return DW_OK;

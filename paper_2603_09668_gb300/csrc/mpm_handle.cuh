@@ -1,0 +1,121 @@
+// Internal view of an MPM handle shared by the MPM translation units: the
+// workspace layout, launch instrumentation and the kernels and host helpers
+// one unit launches from another.
+#pragma once
+
+#include <vector>
+
+#include "mpm_g2p.cuh"
+#include "mpm_math.cuh"
+#include "mpm_p2g.cuh"
+#include "wind.cuh"
+
+namespace dw {
+
+struct MpmHandle {
+    dw_mpm_desc desc;
+    MpmParams P;
+    int64_t n_nodes;
+    float4 *grid_mp = nullptr;   // (m, p) after P2G; zero between calls
+    float4 *grid_v = nullptr;    // (v, m) after the grid update
+    float4 *grid_bv = nullptr;   // dL/dv_i during the adjoint; zero between calls
+    float4 *grid_bmp = nullptr;  // (dL/dm_i, dL/dp_i) during the adjoint
+    float *pscratch = nullptr;   // [12][max_particles]: partial dL/dx (3), dL/dF (9)
+    int *err = nullptr;          // device status bits
+    // active 4^3 blocks of the grid (built by P2G, consumed by the grid update)
+    int64_t nblk = 0;            // nb^3
+    int *block_flag = nullptr;   // [nblk]
+    int *block_list = nullptr;   // [2][nblk]: two lists so a fused kernel can fill one
+    int *block_count = nullptr;  // [2]      while the grid update consumes the other
+    // rollout workspace: the second state buffer of the sort ping-pong
+    float *roll_state = nullptr;     // [24][max_particles]
+    uint8_t *roll_pinned = nullptr;  // [max_particles]
+    int32_t *roll_ids = nullptr;     // [max_particles]
+    // sort workspace
+    int nb = 0;                  // 4^3 blocks per axis
+    int64_t n_keys = 0;
+    int *keys = nullptr;         // [max_particles]
+    int *perm = nullptr;         // [max_particles]
+    int *counts = nullptr;       // [n_keys + 1]
+    int *scan_tmp = nullptr;     // block sums for the exclusive scan
+    int64_t scan_tmp_len = 0;
+    // instrumentation: event pairs around kernel launches
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<int> ev_kernel;
+    int prof_used = 0;
+};
+
+// Brackets one kernel launch with events when profiling is enabled.
+struct ProfScope {
+    MpmHandle *h;
+    cudaStream_t s;
+    int slot = -1;
+    ProfScope(MpmHandle *h_, int kid, cudaStream_t s_) : h(h_), s(s_) {
+        if (h->prof_used < (int)h->ev_start.size()) {
+            slot = h->prof_used++;
+            h->ev_kernel[slot] = kid;
+            cudaEventRecord(h->ev_start[slot], s);
+        }
+    }
+    ~ProfScope() {
+        if (slot >= 0) cudaEventRecord(h->ev_stop[slot], s);
+    }
+};
+
+inline void profile_free(MpmHandle *h) {
+    for (auto e : h->ev_start) cudaEventDestroy(e);
+    for (auto e : h->ev_stop) cudaEventDestroy(e);
+    h->ev_start.clear();
+    h->ev_stop.clear();
+    h->ev_kernel.clear();
+    h->prof_used = 0;
+}
+
+inline void fill_params(MpmHandle *h) {
+    const dw_mpm_desc &d = h->desc;
+    MpmParams &P = h->P;
+    P.N = d.n_grid;
+    P.dx = 1.0f / (float)d.n_grid;
+    P.inv_dx = (float)d.n_grid;
+    P.dt = d.dt;
+    P.D = 4.0f * (float)d.n_grid * (float)d.n_grid;
+    P.gx = d.gravity[0];
+    P.gy = d.gravity[1];
+    P.gz = d.gravity[2];
+    P.band = d.bc_band;
+    P.material = d.material;
+    double E = d.E, nu = d.nu;
+    P.mu = (float)(E / (2.0 * (1.0 + nu)));                       // Eq. young_poisson
+    P.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    P.E = d.E;
+    P.p_mass = d.p_mass;
+    P.p_vol = d.p_vol;
+    P.kappa = d.dt * d.p_vol * P.D;
+}
+
+constexpr int GRID_THREADS = 256;  // four 4^3 blocks per CTA iteration
+constexpr int GRID_CTAS = 4 * 152;
+
+inline ActiveBlocks active_blocks(MpmHandle *h, int which = 0) {
+    return ActiveBlocks{h->block_flag, h->block_list + (size_t)which * h->nblk,
+                        h->block_count + which, h->nb};
+}
+
+// kernels of mpm.cu launched from other units
+__global__ void k_grid_update_active(MpmParams P, WindDev wind, float t,
+                                     float4 *__restrict__ grid_mp, float4 *__restrict__ grid_v,
+                                     int clear, ActiveBlocks ab);
+__global__ void k_g2p(MpmParams P, const float *x, const float *F,
+                      const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
+                      float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err,
+                      int *reset_count);
+
+// host helpers of mpm.cu
+dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *name);
+dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_state *out,
+                         const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
+                         int32_t *ids_out, cudaStream_t s);
+
+}  // namespace dw
+
+struct dw_mpm_s : dw::MpmHandle {};

@@ -1,0 +1,146 @@
+// mpm_rollout: many substeps of one scene in one call, with the G2P of
+// substep k and the P2G of substep k + 1 fused into one kernel.
+//
+// A substep is P2G -> grid update -> G2P (Eq. simulation_mpm). Inside a
+// rollout the particle state between two substeps is consumed only by the
+// next P2G, so k_g2p2g does, per particle: gather the grid velocities of
+// substep k (G2P), update x and F, then scatter the updated particle into the
+// zeroed grid of substep k + 1 (P2G) while v and C are still in registers.
+// Per inner substep the particle arrays see one read and one write of x and F
+// (96 B per particle) instead of the four arrays of the unfused kernels.
+// Every `sort_every` substeps the particles are re-sorted by cell; the state
+// is complete (x, v, C, F written) at those boundaries and at the end.
+#include "mpm_handle.cuh"
+
+namespace dw {
+
+template <bool STORE_VC>
+__global__ void __launch_bounds__(P2G_WARP_THREADS) k_g2p2g(
+    MpmParams P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
+    float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
+    float4 *__restrict__ grid_next, int64_t n, int *err, ActiveBlocks ab_next, int *reset_count) {
+    __shared__ float4 rows[P2G_WARP_THREADS / 32][32][P2G_ROW];
+    __shared__ int keys[P2G_WARP_THREADS / 32][32];
+    const int wid = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) *reset_count = 0;  // the grid update has consumed the current list
+    P2GParticle q;
+    q.valid = false;
+    if (p < n) {
+        float xp[3] = {x[p], x[n + p], x[2 * n + p]};
+        float Fp[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
+        float vn[3], Cn[9];
+        g2p_update(P, grid_v, pinned && pinned[p], xp, Fp, vn, Cn);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a * n + p] = xp[a];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) F[k * n + p] = Fp[k];
+        if (STORE_VC) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a * n + p] = vn[a];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) C[k * n + p] = Cn[k];
+        }
+        bool fin = isfinite(xp[0]) && isfinite(xp[1]) && isfinite(xp[2]) && finite9(Fp);
+        if (!fin) atomicOr(err, ERRBIT_NONFINITE);
+        if (make_stencil(P, xp[0], xp[1], xp[2], q.s)) {
+            if (!p2g_affine(P, Fp, Cn, q.A)) atomicOr(err, ERRBIT_INVERTED);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) q.mv[a] = P.p_mass * vn[a];
+            q.valid = true;
+        } else {
+            atomicOr(err, ERRBIT_DOMAIN);
+        }
+    }
+    p2g_warp_scatter(P, q, grid_next, ab_next, rows[wid], keys[wid]);
+}
+
+static dw_mpm_state view_of(float *base, int64_t n) {
+    dw_mpm_state s;
+    s.x = base;
+    s.v = base + 3 * n;
+    s.C = base + 6 * n;
+    s.F = base + 15 * n;
+    s.n = n;
+    return s;
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *pinned,
+                                 int32_t *ids, const dw_wind_field *wind, float t0,
+                                 int32_t n_substeps, int32_t sort_every, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_state(h, state, "state");
+    if (st != DW_OK) return st;
+    DW_REQUIRE(n_substeps >= 0, "n_substeps must be >= 0");
+    DW_REQUIRE(sort_every >= 0, "sort_every must be >= 0");
+    DW_REQUIRE(sort_every == 0 || ids, "ids must be given when sort_every > 0");
+    WindDev wd;
+    st = wind_check(wind, &wd);
+    if (st != DW_OK) return st;
+    const int64_t n = state->n;
+    if (n == 0 || n_substeps == 0) return DW_OK;
+    cudaStream_t s = as_stream(stream);
+    dw_mpm_state cur = *state, oth = view_of(h->roll_state, n);
+    uint8_t *cur_pin = pinned, *oth_pin = pinned ? h->roll_pinned : nullptr;
+    int32_t *cur_ids = ids, *oth_ids = h->roll_ids;
+    const int seg = sort_every > 0 ? sort_every : n_substeps;
+    const unsigned pgrid = grid_for(n, P2G_WARP_THREADS);
+    int L = 0;  // active list consumed by the next grid update
+    for (int k0 = 0; k0 < n_substeps; k0 += seg) {
+        const int len = min(seg, n_substeps - k0);
+        if (sort_every > 0) {
+            st = sort_particles(h, &cur, &oth, cur_pin, oth_pin, cur_ids, oth_ids, s);
+            if (st != DW_OK) return st;
+            std::swap(cur, oth);
+            std::swap(cur_pin, oth_pin);
+            std::swap(cur_ids, oth_ids);
+        }
+        {
+            ProfScope ps(h, DW_K_P2G, s);
+            st = launch_p2g(h->desc.p2g_mode, h->P, cur.x, cur.v, cur.C, cur.F, n, h->grid_mp,
+                            h->err, active_blocks(h, L), s);
+        }
+        if (st != DW_OK) return st;
+        for (int j = 0; j < len; ++j) {
+            const float t = t0 + (float)(k0 + j) * h->P.dt;
+            {
+                ProfScope ps(h, DW_K_GRID, s);
+                k_grid_update_active<<<GRID_CTAS, GRID_THREADS, 0, s>>>(
+                    h->P, wd, t, h->grid_mp, h->grid_v, 1, active_blocks(h, L));
+            }
+            DW_LAUNCHED("k_grid_update_active");
+            if (j + 1 < len) {
+                ProfScope ps(h, DW_K_G2P2G, s);
+                k_g2p2g<false><<<pgrid, P2G_WARP_THREADS, 0, s>>>(
+                    h->P, cur.x, cur.v, cur.C, cur.F, cur_pin, h->grid_v, h->grid_mp, n, h->err,
+                    active_blocks(h, 1 - L), h->block_count + L);
+                DW_LAUNCHED("k_g2p2g");
+                L = 1 - L;
+            } else {
+                ProfScope ps(h, DW_K_G2P, s);
+                k_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, cur.x, cur.F, cur_pin, h->grid_v,
+                                                       cur.x, cur.v, cur.C, cur.F, n, h->err,
+                                                       h->block_count + L);
+                DW_LAUNCHED("k_g2p");
+            }
+        }
+    }
+    if (cur.x != state->x) {  // an odd number of sorts: the result is in the workspace
+        const size_t b3 = sizeof(float) * 3 * (size_t)n, b9 = sizeof(float) * 9 * (size_t)n;
+        DW_CUDA(cudaMemcpyAsync(state->x, cur.x, b3, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(state->v, cur.v, b3, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(state->C, cur.C, b9, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(state->F, cur.F, b9, cudaMemcpyDeviceToDevice, s));
+        if (pinned)
+            DW_CUDA(cudaMemcpyAsync(pinned, cur_pin, (size_t)n, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(ids, cur_ids, sizeof(int32_t) * (size_t)n,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    return DW_OK;
+}

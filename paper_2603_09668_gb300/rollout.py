@@ -1,10 +1,9 @@
-"""Forward MPM rollouts: many substeps of one scene with periodic re-sorting of
-the particles by grid cell, recorded once as a CUDA graph and replayed.
+"""Forward MPM rollouts through mpm_rollout, recorded once as a CUDA graph.
 
-The graph holds, per segment of `sort_every` substeps, one mpm_sort (state
-ping-pong, particle ids carried along) followed by in-place mpm_substep calls
-at times t0 + k dt. Replaying it issues every kernel of the rollout with one
-launch from the host.
+mpm_rollout runs all substeps of a rollout in one library call (re-sorting
+the particles every `sort_every` substeps and fusing the G2P of each substep
+with the P2G of the next); this class owns the state buffers, records that
+call in a CUDA graph after a first eager run, and replays it.
 """
 from __future__ import annotations
 
@@ -19,40 +18,33 @@ class Rollout:
     def __init__(self, mpm: B.MPM, n: int, wind: B.WindField, n_substeps: int, *, t0: float = 0.0,
                  sort_every: int = 20, with_pins: bool = False, use_graph: bool = True,
                  device="cuda"):
-        if n_substeps < 1 or sort_every < 1:
-            raise ValueError("n_substeps and sort_every must be >= 1")
+        if n_substeps < 1 or sort_every < 0:
+            raise ValueError("n_substeps must be >= 1 and sort_every >= 0")
         self.mpm, self.n, self.wind = mpm, n, wind
         self.n_substeps, self.t0, self.sort_every = n_substeps, t0, sort_every
-        self.dt = mpm.dt
-        shapes = (3, 3, 9, 9)
-        self.bufs = [B.MpmState(*(torch.empty((r, n), dtype=torch.float32, device=device)
-                                  for r in shapes)) for _ in range(2)]
-        self.pins = [torch.zeros(n, dtype=torch.uint8, device=device) for _ in range(2)] \
-            if with_pins else [None, None]
-        self.ids = [torch.empty(n, dtype=torch.int32, device=device) for _ in range(2)]
-        self.n_sorts = (n_substeps + sort_every - 1) // sort_every
-        self.final = self.n_sorts % 2  # buffer holding the result
+        self.state = B.MpmState(*(torch.empty((r, n), dtype=torch.float32, device=device)
+                                  for r in (3, 3, 9, 9)))
+        self.pins = torch.zeros(n, dtype=torch.uint8, device=device) if with_pins else None
+        self.ids = torch.empty(n, dtype=torch.int32, device=device)
+        self.ids0 = torch.arange(n, dtype=torch.int32, device=device)
         self.use_graph = use_graph
         self.graph = None
 
-    # kernels per replay: the substeps (P2G, grid, G2P) and the sorts
-    # (keys, 3 scan kernels, scatter, permute)
     @property
     def kernel_launches(self):
-        return 3 * self.n_substeps + 6 * self.n_sorts
+        """Kernels of one run: per segment of L substeps a sort (6 kernels when
+        sorting), one P2G, L grid updates, L - 1 fused G2P+P2G and one G2P."""
+        seg = self.sort_every if self.sort_every > 0 else self.n_substeps
+        total, k0 = 0, 0
+        while k0 < self.n_substeps:
+            L = min(seg, self.n_substeps - k0)
+            total += (6 if self.sort_every > 0 else 0) + 2 * L + 1
+            k0 += seg
+        return total
 
     def _issue(self):
-        cur = 0
-        for k in range(self.n_substeps):
-            if k % self.sort_every == 0:
-                nxt = 1 - cur
-                ids_in = None if k == 0 else self.ids[cur]
-                self.mpm.sort(self.bufs[cur], self.bufs[nxt], self.pins[cur], self.pins[nxt],
-                              ids_in, self.ids[nxt])
-                cur = nxt
-            self.mpm.substep(self.bufs[cur], self.bufs[cur], self.pins[cur], self.wind,
-                             self.t0 + k * self.dt)
-        assert cur == self.final
+        self.mpm.rollout(self.state, self.pins, self.ids, self.wind, self.t0, self.n_substeps,
+                         self.sort_every)
 
     def _capture(self):
         s = torch.cuda.Stream()
@@ -63,14 +55,15 @@ class Rollout:
         torch.cuda.current_stream().wait_stream(s)
 
     def load(self, state: B.MpmState, pinned: Optional[torch.Tensor] = None):
-        """Copy an initial state (and pin flags) into the rollout's input buffer."""
-        for dst, src in zip(self.bufs[0], state):
+        """Copy an initial state (and pin flags) into the rollout's buffers."""
+        for dst, src in zip(self.state, state):
             dst.copy_(src, non_blocking=True)
-        if self.pins[0] is not None:
+        self.ids.copy_(self.ids0, non_blocking=True)
+        if self.pins is not None:
             if pinned is None:
-                self.pins[0].zero_()
+                self.pins.zero_()
             else:
-                self.pins[0].copy_(pinned, non_blocking=True)
+                self.pins.copy_(pinned, non_blocking=True)
 
     def run(self):
         """Advance the loaded state. The first call runs eagerly (which also
@@ -85,4 +78,4 @@ class Rollout:
 
     def result(self):
         """(final state in sorted order, ids: original index of each particle)."""
-        return self.bufs[self.final], self.ids[self.final]
+        return self.state, self.ids

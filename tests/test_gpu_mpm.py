@@ -279,3 +279,57 @@ def test_adjoint_accumulates_and_may_alias_g_out():
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * a.abs().max().item())
     assert torch.allclose(gw, 2 * gw1, rtol=1e-4, atol=1e-6 * gw1.abs().max().item())
     assert torch.allclose(gE, 2 * gE1, rtol=1e-4)
+
+
+# ---------------------------------------------------------------- rollout --
+
+@pytest.mark.parametrize("n_sub,sort_every", [(60, 20), (50, 20), (30, 0), (7, 3)])
+def test_rollout_matches_oracle_and_substep_loop(n_sub, sort_every):
+    """mpm_rollout (sorting + fused G2P/P2G) against the oracle and against the
+    plain substep loop; ids map the sorted particles back."""
+    sc = inputs.block_scene()
+    rng = np.random.default_rng(3)
+    st = inputs.perturbed_state(sc.x, v_scale=0.2, c_scale=2.0, f_scale=0.02, seed=5)
+    shuffle = rng.permutation(sc.n)
+    st = tuple(a[:, shuffle].copy() for a in st)
+    pinned = (rng.random(sc.n) < 0.05).astype(np.uint8)
+    vals = inputs.fourier_wind(8, 3, seed=4)
+    params = sc.params()
+    mpm = B.MPM.from_params(params, max_particles=sc.n)
+    w = wind_dev(vals, n_sub * sc.dt)
+    s = state_to_dev(st)
+    pin = to_dev(pinned)
+    ids = torch.arange(sc.n, dtype=torch.int32, device="cuda")
+    mpm.rollout(s, pin, ids, w, 0.0, n_sub, sort_every)
+    mpm.device_status()
+    idx = ids.cpu().numpy()
+    assert np.array_equal(np.sort(idx), np.arange(sc.n))
+    assert np.array_equal(pin.cpu().numpy(), pinned[idx])
+    ref = oracle.mpm_rollout(params, f64(st), wind_ref(vals, n_sub * sc.dt), 0.0, n_sub, pinned)
+    g = state_to_np(s)
+    assert np.abs(g[0] - ref[0][:, idx]).max() <= 1e-4
+    assert max_rel(g[3], ref[3][:, idx]) <= 1e-4
+    # the plain substep loop on the original order
+    loop = state_to_dev(st)
+    for k in range(n_sub):
+        mpm.substep(loop, loop, to_dev(pinned), w, k * sc.dt)
+    lp = state_to_np(loop)
+    assert np.abs(g[0] - lp[0][:, idx]).max() <= 1e-5
+    assert max_rel(g[1], lp[1][:, idx]) <= 1e-3
+
+
+def test_rollout_sheet_full_size_positions_within_1e4():
+    """The flag-like sheet at full size, 100 substeps through mpm_rollout with
+    re-sorting every 20, against the FP64 oracle on every particle."""
+    sc = inputs.sheet_scene(n_substeps=100)
+    params = sc.params()
+    st = inputs.rest_state(sc.x)
+    mpm = B.MPM.from_params(params, max_particles=sc.n)
+    s = state_to_dev(st)
+    pin = to_dev(sc.pinned)
+    ids = torch.arange(sc.n, dtype=torch.int32, device="cuda")
+    mpm.rollout(s, pin, ids, wind_dev(sc.wind, sc.t_total), 0.0, 100, 20)
+    mpm.device_status()
+    ref = oracle.mpm_rollout(params, f64(st), sc.wind_tuple(), 0.0, 100, sc.pinned)
+    idx = ids.cpu().numpy()
+    assert np.abs(s.x.cpu().numpy() - ref[0][:, idx]).max() <= 1e-4
