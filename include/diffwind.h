@@ -245,7 +245,7 @@ DW_API dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_state
  * solid) or NULL (all fluid).
  */
 typedef struct {
-    int32_t nx, ny, nz; /* lattice size, each >= 2; nx*ny*nz < 2^31 */
+    int32_t nx, ny, nz; /* lattice size, each >= 2; 19*nx*ny*nz < 2^31 */
     float tau;          /* BGK relaxation time, > 0.5 */
     float u_inlet[3];   /* inlet velocity (lattice units), used when bc_x = 1 */
     float force[3];     /* uniform body force density (lattice units) */

@@ -165,52 +165,102 @@ __global__ void __launch_bounds__(256, 4) k_lbm_aa_even(LbmParams L, float *f,
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
-                                                   const uint8_t *__restrict__ solid,
-                                                   const float *__restrict__ outlet) {
+// Per-cell link mask for the odd kernel: bit 0 = the cell is solid, bit i =
+// the neighbour x + c_i (after the periodic wraps) is solid. Built once per
+// lbm_step call so that the odd kernel reads 4 bytes instead of 18 masks.
+__global__ void k_lbm_links(LbmParams L, const uint8_t *__restrict__ solid,
+                            uint32_t *__restrict__ links) {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.ncell) return;
-    if (solid && solid[cell]) return;
-    const size_t nc = (size_t)L.ncell;
     const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
-    const int nface = L.ny * L.nz, face = cell / L.nx;
-    float fl[19];
+    uint32_t m = solid[cell] ? 1u : 0u;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        int sx = x - D3Q19::cx(i);
-        float val;
-        if (L.bc_x == 1 && sx < 0) {
-            val = L.feq_in[i];
-        } else if (L.bc_x == 1 && sx > L.nx - 1) {
-            val = outlet[outlet_slot(i) * nface + face];
-        } else {
-            int s = cell_index(L, wrapc(sx, L.nx), wrapc(y - D3Q19::cy(i), L.ny),
-                               wrapc(z - D3Q19::cz(i), L.nz));
-            if (solid && solid[s])
-                val = f[i * nc + cell];  // own f*_opp(i), stored in slot i by the even step
-            else
-                val = f[D3Q19::opp(i) * nc + s];
-        }
-        fl[i] = val;
-    }
-    collide(L, fl);
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
+    for (int i = 1; i < 19; ++i) {
         int tx = x + D3Q19::cx(i);
-        if (L.bc_x == 1 && (tx < 0 || tx > L.nx - 1)) continue;  // leaves the lattice
+        if (L.bc_x == 1 && (tx < 0 || tx > L.nx - 1)) continue;  // outside: no solid bit
         int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
                            wrapc(z + D3Q19::cz(i), L.nz));
-        if (solid && solid[t])
-            f[D3Q19::opp(i) * nc + cell] = fl[i];
-        else
-            f[i * nc + t] = fl[i];
+        if (solid[t]) m |= 1u << i;
+    }
+    links[cell] = m;
+}
+
+// Offsets of the neighbours with the periodic wraps folded in: the neighbour
+// x + c is cell + off(c) (m = -1 side, p = +1 side of each axis).
+struct NbrOffsets {
+    int xm, xp, ym, yp, zm, zp;
+    __device__ __forceinline__ int off(int cx, int cy, int cz) const {
+        return (cx < 0 ? xm : (cx > 0 ? xp : 0)) + (cy < 0 ? ym : (cy > 0 ? yp : 0)) +
+               (cz < 0 ? zm : (cz > 0 ? zp : 0));
+    }
+};
+
+__device__ __forceinline__ NbrOffsets nbr_offsets(const LbmParams &L, int x, int y, int z) {
+    NbrOffsets o;
+    const int sy = L.nx, sz = L.nx * L.ny;
+    o.xm = x == 0 ? L.nx - 1 : -1;
+    o.xp = x == L.nx - 1 ? -(L.nx - 1) : 1;
+    o.ym = y == 0 ? (L.ny - 1) * sy : -sy;
+    o.yp = y == L.ny - 1 ? -(L.ny - 1) * sy : sy;
+    o.zm = z == 0 ? (L.nz - 1) * sz : -sz;
+    o.zp = z == L.nz - 1 ? -(L.nz - 1) * sz : sz;
+    return o;
+}
+
+__global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
+                                                      const uint32_t *__restrict__ links,
+                                                      const float *__restrict__ outlet) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const uint32_t lk = links ? links[cell] : 0u;
+    if (lk & 1u) return;
+    const int nc = L.ncell;  // 19 * ncell < 2^31 is checked at create
+    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
+    const NbrOffsets o = nbr_offsets(L, x, y, z);
+    float fl[19];
+    fl[0] = f[cell];  // rest population: own slot 0 in both orders
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int j = D3Q19::opp(i);  // f_i arrives from x + c_j, stored in its slot j
+        const int idx = ((lk >> j) & 1u)
+                            ? i * nc + cell  // bounce-back: own f*_j, in slot i since the even step
+                            : j * nc + cell + o.off(D3Q19::cx(j), D3Q19::cy(j), D3Q19::cz(j));
+        fl[i] = f[idx];
     }
     if (L.bc_x == 1) {
+        const int nface = L.ny * L.nz, face = cell / L.nx;
+        if (x == 0) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            if (x == 0 && D3Q19::cx(i) == 1) f[i * nc + cell] = L.feq_in[i];
-            if (x == L.nx - 1 && D3Q19::cx(i) == -1) f[i * nc + cell] = fl[i];
+            for (int i = 1; i < 19; ++i)
+                if (D3Q19::cx(i) == 1) fl[i] = L.feq_in[i];
         }
+        if (x == L.nx - 1) {
+#pragma unroll
+            for (int i = 1; i < 19; ++i)
+                if (D3Q19::cx(i) == -1) fl[i] = outlet[outlet_slot(i) * nface + face];
+        }
+    }
+    collide(L, fl);
+    f[cell] = fl[0];
+    const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        if (inlet_face && D3Q19::cx(i) == -1) continue;   // leaves through x = 0
+        if (outlet_face && D3Q19::cx(i) == 1) continue;   // leaves through x = nx - 1
+        const int idx = ((lk >> i) & 1u)
+                            ? D3Q19::opp(i) * nc + cell
+                            : i * nc + cell + o.off(D3Q19::cx(i), D3Q19::cy(i), D3Q19::cz(i));
+        f[idx] = fl[i];
+    }
+    if (inlet_face) {
+#pragma unroll
+        for (int i = 1; i < 19; ++i)
+            if (D3Q19::cx(i) == 1) f[i * nc + cell] = L.feq_in[i];
+    }
+    if (outlet_face) {
+#pragma unroll
+        for (int i = 1; i < 19; ++i)
+            if (D3Q19::cx(i) == -1) f[i * nc + cell] = fl[i];
     }
 }
 
@@ -360,6 +410,7 @@ struct LbmHandle {
     float *outlet = nullptr;  // [5][ny*nz]
     float *tape = nullptr;    // [max_tape][19][ncell]
     float *gtmp = nullptr;    // [19][ncell]
+    uint32_t *links = nullptr;  // [ncell]
 };
 
 static void fill_lbm_params(LbmHandle *h) {
@@ -394,7 +445,7 @@ extern "C" dw_status lbm_create(const dw_lbm_desc *desc, dw_lbm *out) {
     DW_REQUIRE(desc && out, "desc/out must not be NULL");
     *out = nullptr;
     DW_REQUIRE(desc->nx >= 2 && desc->ny >= 2 && desc->nz >= 2, "lattice sizes must be >= 2");
-    DW_REQUIRE((int64_t)desc->nx * desc->ny * desc->nz < (1ll << 31), "lattice too large");
+    DW_REQUIRE(19ll * desc->nx * desc->ny * desc->nz < (1ll << 31), "lattice too large (19 nx ny nz must be < 2^31)");
     DW_REQUIRE(desc->tau > 0.5f, "tau must be > 0.5");
     DW_REQUIRE(desc->bc_x == 0 || desc->bc_x == 1, "bc_x must be 0 or 1");
     DW_REQUIRE(desc->max_tape >= 1 && desc->max_tape <= 4096, "max_tape must be in [1, 4096]");
@@ -409,6 +460,7 @@ extern "C" dw_status lbm_create(const dw_lbm_desc *desc, dw_lbm *out) {
     cudaError_t e = cudaMalloc((void **)&h->outlet, sizeof(float) * 5 * (size_t)desc->ny * desc->nz);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->tape, lat * (size_t)desc->max_tape);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->gtmp, lat);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->links, sizeof(uint32_t) * (size_t)h->L.ncell);
     if (e != cudaSuccess) {
         dw_status st = cuda_fail(e, "lbm_create");
         lbm_destroy(h);
@@ -423,6 +475,7 @@ extern "C" dw_status lbm_destroy(dw_lbm h) {
     cudaFree(h->outlet);
     cudaFree(h->tape);
     cudaFree(h->gtmp);
+    cudaFree(h->links);
     delete h;
     return DW_OK;
 }
@@ -435,9 +488,14 @@ extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t 
     cudaStream_t s = as_stream(stream);
     const LbmParams &L = h->L;
     unsigned grid = grid_for(L.ncell, 256);
+    const uint32_t *links = nullptr;
+    if (solid && steps >= 2) {
+        k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
+        links = h->links;
+    }
     for (int k = 0; k + 1 < steps; k += 2) {
         k_lbm_aa_even<<<grid, 256, 0, s>>>(L, f, solid, h->outlet);
-        k_lbm_aa_odd<<<grid, 256, 0, s>>>(L, f, solid, h->outlet);
+        k_lbm_aa_odd<<<grid, 256, 0, s>>>(L, f, links, h->outlet);
     }
     if (steps & 1) {
         k_lbm_push<<<grid, 256, 0, s>>>(L, f, h->tape, solid);

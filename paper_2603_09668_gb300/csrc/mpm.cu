@@ -69,6 +69,8 @@ __device__ __forceinline__ bool active_node(const MpmParams &P, int nb, int b, i
 __global__ void __launch_bounds__(GRID_THREADS) k_grid_update_active(
     MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_v,
     int clear, ActiveBlocks ab) {
+    pdl_wait();
+    pdl_trigger();
     const int count = *ab.count;
     const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
     for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
@@ -88,6 +90,8 @@ __global__ void k_g2p(MpmParams P, const float *x, const float *F,
                       const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
                       float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err,
                       int *reset_count) {
+    pdl_wait();
+    pdl_trigger();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (reset_count && p == 0) *reset_count = 0;  // the grid update has consumed the list
     if (p >= n) return;

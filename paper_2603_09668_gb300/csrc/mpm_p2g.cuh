@@ -119,16 +119,15 @@ __device__ __forceinline__ void p2g_scatter_global(const MpmParams &P, const P2G
 // Each warp reduces the contributions of lanes whose particles share a base
 // cell (runs of equal keys among consecutive lanes; after mpm_sort most warps
 // of a dense object are a single run) through a shared-memory transpose: every
-// lane writes its 27 node values (float4: m, p) into its own row, then lane L
-// walks the 32 rows of node L and issues one float4 atomic per run. The
-// stencil is processed in two halves (14 + 13 nodes) to halve the buffer.
+// lane writes its node values (float4: m, p) into its own row, then lane L
+// walks the 32 rows of node L and issues one float4 atomic per run. The 27
+// stencil nodes go in three passes of 9 to keep the buffer small; a row of 9
+// float4 (144 B) keeps the float4 row stores free of bank conflicts.
 
 constexpr int P2G_WARP_THREADS = 128;
-constexpr int P2G_HALF = 14;    // nodes per pass
-constexpr int P2G_ROW = 15;     // float4 per row: 15 * 16 B keeps float4 stores conflict-free
+constexpr int P2G_PASS = 9;  // nodes per pass
+constexpr int P2G_ROW = 9;   // float4 per row
 
-// Warp-cooperative scatter of one particle per lane (all 32 lanes call it;
-// invalid lanes contribute nothing). rows/keys are this warp's shared buffers.
 __device__ __forceinline__ void p2g_warp_scatter(const MpmParams &P, P2GParticle &q,
                                                  float4 *__restrict__ grid, const ActiveBlocks &ab,
                                                  float4 (*rows)[P2G_ROW], int *keys) {
@@ -151,41 +150,92 @@ __device__ __forceinline__ void p2g_warp_scatter(const MpmParams &P, P2GParticle
         for (int k = 0; k < 9; ++k) q.A[k] = 0.0f;
         q.mv[0] = q.mv[1] = q.mv[2] = 0.0f;
     }
-    // q' = m v - A fx dx, so that the node value is W (q' + dx A o)
-    float qp[3];
+    // node value = W_o (r0 + oi sx + oj sy + ok sz) with r0 = m v - A fx dx and
+    // s = dx times the columns of A; the mass part is W_o m
+    float r0[3], sx[3], sy[3], sz[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        qp[c] = q.mv[c] - (q.A[3 * c] * q.s.fx[0] + q.A[3 * c + 1] * q.s.fx[1] + q.A[3 * c + 2] * q.s.fx[2]) * P.dx;
+    for (int c = 0; c < 3; ++c) {
+        r0[c] = q.mv[c] - (q.A[3 * c] * q.s.fx[0] + q.A[3 * c + 1] * q.s.fx[1] + q.A[3 * c + 2] * q.s.fx[2]) * P.dx;
+        sx[c] = q.A[3 * c] * P.dx;
+        sy[c] = q.A[3 * c + 1] * P.dx;
+        sz[c] = q.A[3 * c + 2] * P.dx;
+    }
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int o0 = half * P2G_HALF;
-        const int cnt = half ? 27 - P2G_HALF : P2G_HALF;
+    for (int pass = 0; pass < 3; ++pass) {
+        // pass = ok: the 9 nodes of one z layer, line by line along x
+        const int ok = pass;
 #pragma unroll
-        for (int j = 0; j < (half ? 27 - P2G_HALF : P2G_HALF); ++j) {
-            const int o = o0 + j;
-            const int oi = o % 3, oj = (o / 3) % 3, ok = o / 9;
-            float W = q.s.w[0][oi] * q.s.w[1][oj] * q.s.w[2][ok];
-            float4 val;
-            val.x = W * P.p_mass;
-            val.y = W * (qp[0] + P.dx * (q.A[0] * oi + q.A[1] * oj + q.A[2] * ok));
-            val.z = W * (qp[1] + P.dx * (q.A[3] * oi + q.A[4] * oj + q.A[5] * ok));
-            val.w = W * (qp[2] + P.dx * (q.A[6] * oi + q.A[7] * oj + q.A[8] * ok));
-            rows[lane][j] = val;
+        for (int oj = 0; oj < 3; ++oj) {
+            const float wyz = q.s.w[1][oj] * q.s.w[2][ok];
+            float b[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float t = r0[c];
+                if (oj == 1) t += sy[c];
+                if (oj == 2) t += 2.0f * sy[c];
+                if (ok == 1) t += sz[c];
+                if (ok == 2) t += 2.0f * sz[c];
+                b[c] = t;
+            }
+#pragma unroll
+            for (int oi = 0; oi < 3; ++oi) {
+                const float W = q.s.w[0][oi] * wyz;
+                float4 val;
+                val.x = W * P.p_mass;
+                val.y = W * (oi == 0 ? b[0] : (oi == 1 ? b[0] + sx[0] : b[0] + 2.0f * sx[0]));
+                val.z = W * (oi == 0 ? b[1] : (oi == 1 ? b[1] + sx[1] : b[1] + 2.0f * sx[1]));
+                val.w = W * (oi == 0 ? b[2] : (oi == 1 ? b[2] + sx[2] : b[2] + 2.0f * sx[2]));
+                rows[lane][3 * oj + oi] = val;
+            }
         }
         __syncwarp();
-        if (lane < cnt) {
-            const int o = o0 + lane;
-            const int off = ((o / 9) * N + (o / 3) % 3) * N + o % 3;
+        if (ends == 0x80000000u) {
+            // The whole warp is one run (dense objects, sorted): lanes 9g + L
+            // (g = 0, 1, 2) sum rows 11g .. 11g + 10 of node L, then the three
+            // partial sums meet in lane L.
+            const int g = lane / 9, L = lane - 9 * g;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < 3) {
+                const int r0i = 11 * g, r1i = min(32, r0i + 11);
+#pragma unroll 4
+                for (int r = r0i; r < r1i; ++r) {
+                    const float4 t = rows[r][L];
+                    acc.x += t.x;
+                    acc.y += t.y;
+                    acc.z += t.z;
+                    acc.w += t.w;
+                }
+            }
 #pragma unroll
+            for (int d = 9; d <= 18; d += 9) {
+                const float ax = __shfl_down_sync(0xffffffffu, acc.x, d);
+                const float ay = __shfl_down_sync(0xffffffffu, acc.y, d);
+                const float az = __shfl_down_sync(0xffffffffu, acc.z, d);
+                const float aw = __shfl_down_sync(0xffffffffu, acc.w, d);
+                if (lane < 9 && lane + d < 27) {
+                    acc.x += ax;
+                    acc.y += ay;
+                    acc.z += az;
+                    acc.w += aw;
+                }
+            }
+            const int k = keys[0];
+            if (lane < 9 && k >= 0) {
+                const int off = (ok * N + lane / 3) * N + lane % 3;
+                atomicAdd(&grid[(int64_t)k + off], acc);
+            }
+        } else if (lane < P2G_PASS) {
+            const int off = (ok * N + lane / 3) * N + lane % 3;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
             for (int r = 0; r < 32; ++r) {
-                float4 t = rows[r][lane];
+                const float4 t = rows[r][lane];
                 acc.x += t.x;
                 acc.y += t.y;
                 acc.z += t.z;
                 acc.w += t.w;
                 if ((ends >> r) & 1u) {
-                    int k = keys[r];
+                    const int k = keys[r];
                     if (k >= 0) atomicAdd(&grid[(int64_t)k + off], acc);
                     acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 }

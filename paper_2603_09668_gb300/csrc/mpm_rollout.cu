@@ -14,6 +14,20 @@
 
 namespace dw {
 
+// Loads x and F of particle p through L2 (ld.global.cg).
+__device__ __forceinline__ void load_xF(const float *x, const float *F, int64_t n, int64_t p,
+                                        float xp[3], float Fp[9]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xp[a] = __ldcg(x + a * n + p);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fp[k] = __ldcg(F + k * n + p);
+}
+
+// One thread per particle. x and F are loaded before the programmatic-launch
+// wait: they were last written two launches back by a kernel that has
+// completed once this one runs (the grid update in between waits for it before
+// it lets this kernel start), and the loads go through L2; only grid_v, which
+// the grid update writes, is read after the wait.
 template <bool STORE_VC>
 __global__ void __launch_bounds__(P2G_WARP_THREADS) k_g2p2g(
     MpmParams P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
@@ -23,16 +37,20 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_g2p2g(
     __shared__ int keys[P2G_WARP_THREADS / 32][32];
     const int wid = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float xp[3] = {0.f, 0.f, 0.f}, Fp[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool pin = false;
+    if (p < n) {
+        load_xF(x, F, n, p, xp, Fp);
+        pin = pinned && pinned[p];
+    }
+    pdl_wait();
+    pdl_trigger();
     if (p == 0) *reset_count = 0;  // the grid update has consumed the current list
     P2GParticle q;
     q.valid = false;
     if (p < n) {
-        float xp[3] = {x[p], x[n + p], x[2 * n + p]};
-        float Fp[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
         float vn[3], Cn[9];
-        g2p_update(P, grid_v, pinned && pinned[p], xp, Fp, vn, Cn);
+        g2p_update(P, grid_v, pin, xp, Fp, vn, Cn);
 #pragma unroll
         for (int a = 0; a < 3; ++a) x[a * n + p] = xp[a];
 #pragma unroll
@@ -111,23 +129,22 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
             const float t = t0 + (float)(k0 + j) * h->P.dt;
             {
                 ProfScope ps(h, DW_K_GRID, s);
-                k_grid_update_active<<<GRID_CTAS, GRID_THREADS, 0, s>>>(
-                    h->P, wd, t, h->grid_mp, h->grid_v, 1, active_blocks(h, L));
+                DW_CUDA(launch_pdl(k_grid_update_active, GRID_CTAS, GRID_THREADS, s, h->P, wd, t,
+                                   h->grid_mp, h->grid_v, 1, active_blocks(h, L)));
             }
-            DW_LAUNCHED("k_grid_update_active");
             if (j + 1 < len) {
                 ProfScope ps(h, DW_K_G2P2G, s);
-                k_g2p2g<false><<<pgrid, P2G_WARP_THREADS, 0, s>>>(
-                    h->P, cur.x, cur.v, cur.C, cur.F, cur_pin, h->grid_v, h->grid_mp, n, h->err,
-                    active_blocks(h, 1 - L), h->block_count + L);
-                DW_LAUNCHED("k_g2p2g");
+                DW_CUDA(launch_pdl(k_g2p2g<false>, pgrid, P2G_WARP_THREADS, s, h->P, cur.x, cur.v,
+                                   cur.C, cur.F, (const uint8_t *)cur_pin,
+                                   (const float4 *)h->grid_v, h->grid_mp, n, h->err,
+                                   active_blocks(h, 1 - L), h->block_count + L));
                 L = 1 - L;
             } else {
                 ProfScope ps(h, DW_K_G2P, s);
-                k_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, cur.x, cur.F, cur_pin, h->grid_v,
-                                                       cur.x, cur.v, cur.C, cur.F, n, h->err,
-                                                       h->block_count + L);
-                DW_LAUNCHED("k_g2p");
+                DW_CUDA(launch_pdl(k_g2p, grid_for(n, 128), 128, s, h->P, (const float *)cur.x,
+                                   (const float *)cur.F, (const uint8_t *)cur_pin,
+                                   (const float4 *)h->grid_v, cur.x, cur.v, cur.C, cur.F, n,
+                                   h->err, h->block_count + L));
             }
         }
     }
