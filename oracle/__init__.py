@@ -1,5 +1,6 @@
 """FP64 CPU oracle for the DiffWind hot path (MLS-MPM substep, wind-force
-sample, D3Q19 BGK LBM step, obstacle voxelization) and their adjoints.
+sample, D3Q19 BGK LBM step, obstacle voxelization, the learned LBM surrogate)
+and their adjoints.
 
 TEST INFRASTRUCTURE ONLY. The oracle is the plain, slow, obviously correct
 restatement of the method that the CUDA path is checked against. Only
@@ -7,7 +8,8 @@ restatement of the method that the CUDA path is checked against. Only
 ``bench.py`` may import it. It shares no code with the CUDA library and never
 imports the product package.
 
-The arithmetic lives in plain C (``mpm_oracle.c``, ``lbm_oracle.c``), compiled
+The arithmetic lives in plain C (``mpm_oracle.c``, ``lbm_oracle.c``,
+``surrogate_oracle.c``), compiled
 with gcc into ``_build/liboracle.so``; this module only builds, loads and
 marshals numpy float64 arrays. Every function takes and returns
 structure-of-arrays data in the layouts the C files document.
@@ -24,7 +26,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = [os.path.join(_HERE, "mpm_oracle.c"), os.path.join(_HERE, "lbm_oracle.c")]
+_SOURCES = [os.path.join(_HERE, "mpm_oracle.c"), os.path.join(_HERE, "lbm_oracle.c"),
+            os.path.join(_HERE, "surrogate_oracle.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -98,6 +101,11 @@ def _declare(lib):
         "orc_lbm_step_adjoint": (i, [i, i, i, d, _dp, _dp, i, _u8p, _dp, _dp, i]),
         "orc_lbm_macroscopic": (None, [i, i, i, _dp, _u8p, _dp, _dp, _dp]),
         "orc_voxelize": (None, [_dp, i64, i, i, i, d, _u8p]),
+        "orc_surr_num_params": (i64, []),
+        "orc_surr_forward": (None, [i, _dp, _dp, _dp, _dp, _dp]),
+        "orc_surr_backward": (None, [i, _dp, _dp, _dp, _dp]),
+        "orc_surr_features": (None, [i, _dp, _u8p, _dp, _dp, _dp]),
+        "orc_surr_apply": (None, [i, _dp, _dp, _dp, _u8p, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -363,3 +371,69 @@ def voxelize(pos, shape, dx):
     solid = np.zeros(nx * ny * nz, dtype=np.uint8)
     _load().orc_voxelize(_ptr(pos), pos.shape[1], nx, ny, nz, float(dx), _u8ptr(solid))
     return solid
+
+
+# --------------------------------------------------------------- surrogate --
+
+SURR_CHANNELS = (16, 32, 32, 32, 16)
+
+
+def surr_num_params():
+    return int(_load().orc_surr_num_params())
+
+
+def surr_layer_slices():
+    """[(W slice, b slice, cin, cout)] into the packed parameter vector; W is
+    [27][cout][cin], tap = (dz+1)*9 + (dy+1)*3 + (dx+1)."""
+    out, o = [], 0
+    for l in range(4):
+        cin, cout = SURR_CHANNELS[l], SURR_CHANNELS[l + 1]
+        nw = 27 * cin * cout
+        out.append((slice(o, o + nw), slice(o + nw, o + nw + cout), cin, cout))
+        o += nw + cout
+    return out
+
+
+def surr_forward(n, params, feats, keep=False):
+    """feats [n^3][16] channels-last -> out [n^3][16] (and the hidden z, a)."""
+    params = _f64(params)
+    feats = _f64(feats)
+    nv = n ** 3
+    out = np.zeros((nv, 16))
+    z = np.zeros((3, nv, 32)) if keep else None
+    a = np.zeros((3, nv, 32)) if keep else None
+    _load().orc_surr_forward(n, _ptr(params), _ptr(feats), _ptr(z), _ptr(a), _ptr(out))
+    return (out, z, a) if keep else out
+
+
+def surr_backward(n, params, feats, g_out):
+    params = _f64(params)
+    feats = _f64(feats)
+    g_out = _f64(g_out)
+    g = np.zeros_like(params)
+    _load().orc_surr_backward(n, _ptr(params), _ptr(feats), _ptr(g_out), _ptr(g))
+    return g
+
+
+def surr_features(n, f, solid=None):
+    """Coarse features [n^3][16] of a fine (2n)^3 lattice of plain populations
+    f[19][cells], with the fine rho [cells] and u [3][cells]."""
+    f = _f64(f)
+    N3 = (2 * n) ** 3
+    feats = np.zeros((n ** 3, 16))
+    rho = np.zeros(N3)
+    u = np.zeros((3, N3))
+    m = _mask(solid, N3)
+    _load().orc_surr_features(n, _ptr(f), _u8ptr(m), _ptr(feats), _ptr(rho), _ptr(u))
+    return feats, rho, u
+
+
+def surr_apply(n, du, rho_fine, u_fine, f, solid=None):
+    """f (plain, [19][cells]) re-initialised to f_eq(rho, u + upsampled du)."""
+    du = _f64(du)
+    rho_fine = _f64(rho_fine)
+    u_fine = _f64(u_fine)
+    f = _f64(f).copy()
+    m = _mask(solid, (2 * n) ** 3)
+    _load().orc_surr_apply(n, _ptr(du), _ptr(rho_fine), _ptr(u_fine), _u8ptr(m), _ptr(f))
+    return f
