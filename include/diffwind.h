@@ -287,6 +287,66 @@ DW_API dw_status lbm_init_equilibrium(dw_lbm h, float *f, float rho0, const floa
 DW_API dw_status voxelize_particles(const float *pos, int64_t n, int32_t nx, int32_t ny, int32_t nz,
                              float dx, uint8_t *solid, dw_stream stream);
 
+/* ================================================================ surrogate
+ * Learned surrogate of the LBM wind constraint (no counterpart in the paper,
+ * which runs the LBM every time step, Sec. 3.4): a 4-layer 3D convolutional
+ * network on a coarse n^3 grid that maps the coarse state of a (2n)^3
+ * lattice to the change du of the coarse velocity over a block of lattice
+ * steps. Channels 16 -> 32 -> 32 -> 32 -> 16, kernel 3, zero padding, GELU
+ * after layers 1-3; inputs (rho - 1, ux, uy, uz, solid fraction, 0 ...) as
+ * 2x2x2 averages over fluid cells; outputs du in channels 0..2. BF16
+ * activations and weights on the tensor cores with FP32 accumulation; FP32
+ * master parameters packed layer by layer as W[tap][cout][cin] then b[cout],
+ * tap = (dz+1)*9 + (dy+1)*3 + (dx+1) (the input voxel is v + (dx,dy,dz)).
+ * Activations are channels-last [z][y][x][c]. Calls on one handle must not
+ * overlap on the GPU. */
+typedef struct dw_surr_s *dw_surr;
+
+/* n: coarse grid per axis, a multiple of 16 in [16, 256]; parameters start at 0. */
+DW_API dw_status surr_create(int32_t n, dw_surr *out);
+DW_API dw_status surr_destroy(dw_surr h);
+/* Number of FP32 parameters (83,056 for this architecture). */
+DW_API dw_status surr_num_params(dw_surr h, int64_t *count);
+/* Copy parameters in from a device FP32 array (and refresh the BF16 weights),
+ * or out to one; copy the accumulated gradients out; zero the gradients. */
+DW_API dw_status surr_set_params(dw_surr h, const float *src, dw_stream stream);
+DW_API dw_status surr_get_params(dw_surr h, float *dst, dw_stream stream);
+DW_API dw_status surr_get_grads(dw_surr h, float *dst, dw_stream stream);
+DW_API dw_status surr_zero_grads(dw_surr h, dw_stream stream);
+/* Coarse features from a shifted (2n)^3 lattice f [19][cells] and its mask;
+ * also keeps the fine rho and u for surr_apply. */
+DW_API dw_status surr_features(dw_surr h, const float *f, const uint8_t *solid, dw_stream stream);
+/* Set the coarse features directly from FP32 [n^3][16] (rounded to BF16). */
+DW_API dw_status surr_set_features(dw_surr h, const float *feats, dw_stream stream);
+/* Copy the current BF16 features [n^3][16] out. */
+DW_API dw_status surr_get_features(dw_surr h, void *feats_bf16, dw_stream stream);
+/* Network forward; keeps the activations for surr_backward; copies the FP32
+ * output [n^3][16] to out when out is not NULL. */
+DW_API dw_status surr_forward(dw_surr h, float *out, dw_stream stream);
+/* Mean squared error of output channels 0..2 against target [n^3][16] over the
+ * coarse voxels that are not fully solid; adds the loss to *loss (device
+ * float, may be NULL) and sets dL/d(output) for surr_backward. */
+DW_API dw_status surr_loss(dw_surr h, const float *target, float *loss, dw_stream stream);
+/* Set dL/d(output) [n^3][16] directly (FP32, rounded to BF16). */
+DW_API dw_status surr_set_output_grad(dw_surr h, const float *g_out, dw_stream stream);
+/* Reverse pass of the last surr_forward; accumulates into the gradients. */
+DW_API dw_status surr_backward(dw_surr h, dw_stream stream);
+/* Adam step (bias-corrected, step >= 1) on the parameters; zeroes the
+ * gradients and refreshes the BF16 weights. */
+DW_API dw_status surr_adam(dw_surr h, float lr, float beta1, float beta2, float eps, int32_t step,
+                           dw_stream stream);
+/* f = f_eq(rho, u + du) on the fluid cells of the shifted (2n)^3 lattice, with
+ * rho, u from the last surr_features and du the output (out [n^3][16], or the
+ * handle's last forward output when NULL) upsampled trilinearly from the
+ * cell-centred coarse grid (fine cell i at coarse coordinate i/2 - 1/4,
+ * clamped). Solid cells are not written. */
+DW_API dw_status surr_apply(dw_surr h, const float *out, const uint8_t *solid, float *f,
+                            dw_stream stream);
+/* sums[0] += sum |u_a - u_b|^2, sums[1] += sum |u_b|^2 over the fluid cells of
+ * two shifted lattices with ncell cells (device double[2]). */
+DW_API dw_status lbm_velocity_error(const float *fa, const float *fb, const uint8_t *solid,
+                                    int64_t ncell, double *sums, dw_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

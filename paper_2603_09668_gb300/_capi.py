@@ -69,6 +69,23 @@ SIGNATURES = {
     "lbm_macroscopic": (I32, [VP, VP, VP, VP, VP, VP]),
     "lbm_init_equilibrium": (I32, [VP, VP, F32, P(F32 * 3), VP]),
     "voxelize_particles": (I32, [VP, I64, I32, I32, I32, F32, VP, VP]),
+    "surr_create": (I32, [I32, P(VP)]),
+    "surr_destroy": (I32, [VP]),
+    "surr_num_params": (I32, [VP, P(I64)]),
+    "surr_set_params": (I32, [VP, VP, VP]),
+    "surr_get_params": (I32, [VP, VP, VP]),
+    "surr_get_grads": (I32, [VP, VP, VP]),
+    "surr_zero_grads": (I32, [VP, VP]),
+    "surr_features": (I32, [VP, VP, VP, VP]),
+    "surr_set_features": (I32, [VP, VP, VP]),
+    "surr_get_features": (I32, [VP, VP, VP]),
+    "surr_forward": (I32, [VP, VP, VP]),
+    "surr_loss": (I32, [VP, VP, VP, VP]),
+    "surr_set_output_grad": (I32, [VP, VP, VP]),
+    "surr_backward": (I32, [VP, VP]),
+    "surr_adam": (I32, [VP, F32, F32, F32, F32, I32, VP]),
+    "surr_apply": (I32, [VP, VP, VP, VP, VP]),
+    "lbm_velocity_error": (I32, [VP, VP, VP, I64, VP, VP]),
 }
 
 STATUS = {0: "DW_OK", 1: "DW_ERR_ARG", 2: "DW_ERR_CUDA", 3: "DW_ERR_OOM", 4: "DW_ERR_NONFINITE",

@@ -21,7 +21,11 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_substep", "mpm_substep_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
-           "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM"]
+           "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM", "surr_create",
+           "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
+           "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
+           "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
+           "surr_backward", "surr_adam", "surr_apply", "lbm_velocity_error", "Surrogate"]
 
 NEOHOOKEAN, FIXED_COROTATED = 0, 1
 P2G_AUTO, P2G_ATOMIC, P2G_WARP, P2G_TILE = 0, 1, 2, 3
@@ -359,3 +363,147 @@ class LBM:
 
     def init_equilibrium(self, f, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
         return lbm_init_equilibrium(self.h, f, rho0, u0, stream)
+
+
+# --------------------------------------------------------------- surrogate --
+
+def surr_create(n):
+    h = ct.c_void_p()
+    check(lib().surr_create(int(n), ct.byref(h)))
+    return h
+
+
+def surr_destroy(h):
+    check(lib().surr_destroy(h))
+
+
+def surr_num_params(h):
+    c = ct.c_int64()
+    check(lib().surr_num_params(h, ct.byref(c)))
+    return c.value
+
+
+def surr_set_params(h, src, stream=None):
+    check(lib().surr_set_params(h, _dev(src, name="params"), _stream(stream)))
+
+
+def surr_get_params(h, dst, stream=None):
+    check(lib().surr_get_params(h, _dev(dst, name="params"), _stream(stream)))
+    return dst
+
+
+def surr_get_grads(h, dst, stream=None):
+    check(lib().surr_get_grads(h, _dev(dst, name="grads"), _stream(stream)))
+    return dst
+
+
+def surr_zero_grads(h, stream=None):
+    check(lib().surr_zero_grads(h, _stream(stream)))
+
+
+def surr_features(h, f, solid, stream=None):
+    check(lib().surr_features(h, _dev(f, name="f"), _mask(solid), _stream(stream)))
+
+
+def surr_set_features(h, feats, stream=None):
+    check(lib().surr_set_features(h, _dev(feats, name="feats"), _stream(stream)))
+
+
+def surr_get_features(h, feats_bf16, stream=None):
+    check(lib().surr_get_features(h, _dev(feats_bf16, torch.bfloat16, "feats"), _stream(stream)))
+    return feats_bf16
+
+
+def surr_forward(h, out=None, stream=None):
+    check(lib().surr_forward(h, _dev(out, name="out"), _stream(stream)))
+    return out
+
+
+def surr_loss(h, target, loss=None, stream=None):
+    check(lib().surr_loss(h, _dev(target, name="target"), _dev(loss, name="loss"), _stream(stream)))
+
+
+def surr_set_output_grad(h, g_out, stream=None):
+    check(lib().surr_set_output_grad(h, _dev(g_out, name="g_out"), _stream(stream)))
+
+
+def surr_backward(h, stream=None):
+    check(lib().surr_backward(h, _stream(stream)))
+
+
+def surr_adam(h, lr, beta1, beta2, eps, step, stream=None):
+    check(lib().surr_adam(h, float(lr), float(beta1), float(beta2), float(eps), int(step),
+                          _stream(stream)))
+
+
+def surr_apply(h, out, solid, f, stream=None):
+    check(lib().surr_apply(h, _dev(out, name="out"), _mask(solid), _dev(f, name="f"),
+                           _stream(stream)))
+    return f
+
+
+def lbm_velocity_error(fa, fb, solid, sums, stream=None):
+    ncell = fa.numel() // 19
+    check(lib().lbm_velocity_error(_dev(fa, name="fa"), _dev(fb, name="fb"), _mask(solid), ncell,
+                                   _dev(sums, torch.float64, "sums"), _stream(stream)))
+    return sums
+
+
+class Surrogate:
+    """Owns a surrogate handle (coarse grid n per axis)."""
+
+    def __init__(self, n):
+        self.n = n
+        self.h = surr_create(n)
+        self.nparams = surr_num_params(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            surr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        surr_set_params(self.h, p)
+
+    def params(self, device="cuda"):
+        return surr_get_params(self.h, torch.empty(self.nparams, dtype=torch.float32, device=device))
+
+    def grads(self, device="cuda"):
+        return surr_get_grads(self.h, torch.empty(self.nparams, dtype=torch.float32, device=device))
+
+    def zero_grads(self):
+        surr_zero_grads(self.h)
+
+    def features(self, f, solid):
+        surr_features(self.h, f, solid)
+
+    def set_features(self, feats):
+        surr_set_features(self.h, feats)
+
+    def get_features(self):
+        out = torch.empty((self.n ** 3, 16), dtype=torch.bfloat16, device="cuda")
+        return surr_get_features(self.h, out)
+
+    def forward(self, out=None):
+        return surr_forward(self.h, out)
+
+    def loss(self, target, loss=None):
+        surr_loss(self.h, target, loss)
+
+    def set_output_grad(self, g):
+        surr_set_output_grad(self.h, g)
+
+    def backward(self):
+        surr_backward(self.h)
+
+    def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+        surr_adam(self.h, lr, beta1, beta2, eps, step)
+
+    def apply(self, solid, f, out=None):
+        return surr_apply(self.h, out, solid, f)

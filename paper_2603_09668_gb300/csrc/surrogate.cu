@@ -1,0 +1,557 @@
+// Learned surrogate of the LBM wind constraint: a 4-layer 3D conv network on
+// a coarse n^3 grid (channels 16 -> 32 -> 32 -> 32 -> 16, kernel 3, GELU after
+// layers 1-3) that maps the coarse state (rho - 1, u, solid fraction) of a
+// (2n)^3 lattice to the change du of the coarse velocity over a block of
+// lattice steps. Training and inference run in the library's kernels: BF16
+// tensor-core convolutions with FP32 accumulation (surrogate_conv.cuh), FP32
+// master weights and Adam. The paper has no learned component; Sec. 3.4 uses
+// the LBM velocity field as the guide that this network stands in for.
+#include <new>
+
+#include "surrogate_conv.cuh"
+
+namespace dw {
+
+static const int SCH[5] = {16, 32, 32, 32, 16};
+
+struct SurrHandle {
+    int n = 0;           // coarse grid per axis
+    int64_t nv = 0;      // n^3
+    int64_t nparams = 0;
+    int64_t off_w[4] = {0, 0, 0, 0}, off_b[4] = {0, 0, 0, 0};
+    float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    bf16 *wf = nullptr;  // forward weights, per layer [27][cout][cin]
+    bf16 *wd = nullptr;  // input-gradient weights, per layer [27][cin][cout], taps mirrored
+    int64_t woff[4] = {0, 0, 0, 0};
+    bf16 *feats = nullptr;          // [nv][16]
+    bf16 *z[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};  // [nv][32]
+    float *out = nullptr;           // [nv][16]
+    bf16 *g4 = nullptr;             // [nv][16]: dL/d(out)
+    bf16 *gz[3] = {nullptr, nullptr, nullptr};  // [nv][32]: dL/dz of layers 1..3
+    float *part = nullptr, *part_b = nullptr;   // weight-gradient partials
+    int nchunks = 0, tiles_per_chunk = 0;
+    float *fine = nullptr;          // [4][(2n)^3]: rho, ux, uy, uz of the last surr_features
+    double *red = nullptr;          // reduction scratch
+    int conv_ctas = 0;
+};
+
+// ------------------------------------------------------------- kernels ----
+
+__global__ void k_surr_weights(const float *__restrict__ params, bf16 *__restrict__ wf,
+                               bf16 *__restrict__ wd, int64_t off_w, int64_t woff, int cin,
+                               int cout) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t cnt = 27LL * cin * cout;
+    if (i >= cnt) return;
+    const int ci = (int)(i % cin), co = (int)((i / cin) % cout), t = (int)(i / ((int64_t)cin * cout));
+    const bf16 w = __float2bfloat16_rn(params[off_w + i]);
+    wf[woff + i] = w;
+    wd[woff + ((int64_t)(26 - t) * cin + ci) * cout + co] = w;
+}
+
+__device__ __constant__ int kCX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0};
+__device__ __constant__ int kCY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 1, -1};
+__device__ __constant__ int kCZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 1, -1, 1};
+
+// Fine rho and u of every cell of a shifted (2n)^3 lattice (solid: rho 1, u 0).
+__global__ void k_surr_fine(const float *__restrict__ f, const uint8_t *__restrict__ solid, int N,
+                            float *__restrict__ fine) {
+    const int64_t nc = (int64_t)N * N * N;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    float r = 1.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f;
+    if (!(solid && solid[c])) {
+        float rs = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const float fi = f[(size_t)i * nc + c];
+            rs += fi;
+            jx += (float)kCX[i] * fi;
+            jy += (float)kCY[i] * fi;
+            jz += (float)kCZ[i] * fi;
+        }
+        r = 1.0f + rs;
+        ux = jx / r;
+        uy = jy / r;
+        uz = jz / r;
+    }
+    fine[c] = r;
+    fine[nc + c] = ux;
+    fine[2 * nc + c] = uy;
+    fine[3 * nc + c] = uz;
+}
+
+// Coarse features: 2x2x2 averages over fluid cells of (rho - 1, u), solid fraction.
+__global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__restrict__ solid,
+                              int n, bf16 *__restrict__ feats) {
+    const int64_t nv = (int64_t)n * n * n;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int N = 2 * n;
+    const int64_t nc = (int64_t)N * N * N;
+    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((int64_t)n * n));
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int fluid = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int64_t c = ((int64_t)(2 * z + (k >> 2)) * N + (2 * y + ((k >> 1) & 1))) * N + 2 * x + (k & 1);
+        if (solid && solid[c]) continue;
+        ++fluid;
+        s[0] += fine[c] - 1.0f;
+        s[1] += fine[nc + c];
+        s[2] += fine[2 * nc + c];
+        s[3] += fine[3 * nc + c];
+    }
+    const float inv = fluid > 0 ? 1.0f / (float)fluid : 0.0f;
+    __align__(16) bf16 o[16];
+#pragma unroll
+    for (int ch = 0; ch < 16; ++ch) o[ch] = __float2bfloat16_rn(0.0f);
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * inv);
+    o[4] = __float2bfloat16_rn((8 - fluid) * 0.125f);
+    uint4 *dst = reinterpret_cast<uint4 *>(feats + v * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+}
+
+__global__ void k_f32_to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, int64_t cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Mean squared error over the coarse voxels that are not fully solid, on
+// channels 0..2: L = sum (out - target)^2 / (3 count); g4 = dL/d(out).
+__global__ void k_surr_loss(const float *__restrict__ out, const float *__restrict__ target,
+                            const bf16 *__restrict__ feats, int64_t nv, const int *__restrict__ count,
+                            bf16 *__restrict__ g4, float *__restrict__ loss) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float inv_norm = 1.0f / (3.0f * (float)max(*count, 1));
+    float l = 0.0f;
+    if (v < nv) {
+        const bool fluid = __bfloat162float(feats[v * 16 + 4]) < 1.0f;
+        __align__(16) bf16 g[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) g[c] = __float2bfloat16_rn(0.0f);
+        if (fluid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float d = out[v * 16 + c] - target[v * 16 + c];
+                l += d * d;
+                g[c] = __float2bfloat16_rn(2.0f * d * inv_norm);
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(g4 + v * 16);
+        dst[0] = reinterpret_cast<const uint4 *>(g)[0];
+        dst[1] = reinterpret_cast<const uint4 *>(g)[1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l * inv_norm);
+}
+
+__global__ void k_count_fluid(const bf16 *__restrict__ feats, int64_t nv, int *__restrict__ count) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = (v < nv && __bfloat162float(feats[v * 16 + 4]) < 1.0f) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+__global__ void k_wgrad_reduce(const float *__restrict__ part, const float *__restrict__ part_b,
+                               int nchunks, int64_t nw, int cout, float *__restrict__ gw,
+                               float *__restrict__ gb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nw) {
+        float s = 0.0f;
+        for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * nw + i];
+        gw[i] += s;
+    } else if (i < nw + cout) {
+        const int co = (int)(i - nw);
+        float s = 0.0f;
+        for (int c = 0; c < nchunks; ++c) s += part_b[(size_t)c * cout + co];
+        gb[co] += s;
+    }
+}
+
+__global__ void k_surr_adam(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t cnt, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    g[i] = 0.0f;
+}
+
+// f = f_eq(rho, u + du up-sampled) on fluid cells of the (2n)^3 lattice
+// (shifted populations), du trilinear from the cell-centred coarse grid.
+__global__ void k_surr_apply(const float *__restrict__ out, const float *__restrict__ fine,
+                             const uint8_t *__restrict__ solid, int n, float *__restrict__ f) {
+    const int N = 2 * n;
+    const int64_t nc = (int64_t)N * N * N;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    if (solid && solid[c]) return;
+    const int fi[3] = {(int)(c % N), (int)((c / N) % N), (int)(c / ((int64_t)N * N))};
+    int i0[3];
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float s = fminf(fmaxf(fi[a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
+        int i = min((int)floorf(s), n - 2);
+        i0[a] = i;
+        t[a] = s - (float)i;
+    }
+    float d[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int cx = k & 1, cy = (k >> 1) & 1, cz = k >> 2;
+        const float w = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+        const float *o = out + ((((int64_t)(i0[2] + cz)) * n + (i0[1] + cy)) * n + (i0[0] + cx)) * 16;
+        d[0] += w * o[0];
+        d[1] += w * o[1];
+        d[2] += w * o[2];
+    }
+    const float rho = fine[c];
+    const float ux = fine[nc + c] + d[0], uy = fine[2 * nc + c] + d[1], uz = fine[3 * nc + c] + d[2];
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const float cu = (float)kCX[i] * ux + (float)kCY[i] * uy + (float)kCZ[i] * uz;
+        const float w = i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+        f[(size_t)i * nc + c] = w * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - uu));
+    }
+}
+
+// sums over fluid cells of |u_a - u_b|^2 and |u_b|^2 (u from shifted lattices)
+__global__ void k_vel_err(const float *__restrict__ fa, const float *__restrict__ fb,
+                          const uint8_t *__restrict__ solid, int64_t nc, double *__restrict__ out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, r = 0.0;
+    if (c < nc && !(solid && solid[c])) {
+        float ua[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f}, ra = 1.0f, rb = 1.0f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const float a = fa[(size_t)i * nc + c], b = fb[(size_t)i * nc + c];
+            ra += a;
+            rb += b;
+            ua[0] += kCX[i] * a;
+            ua[1] += kCY[i] * a;
+            ua[2] += kCZ[i] * a;
+            ub[0] += kCX[i] * b;
+            ub[1] += kCY[i] * b;
+            ub[2] += kCZ[i] * b;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double da = ua[k] / ra - ub[k] / rb;
+            e += da * da;
+            r += (double)(ub[k] / rb) * (ub[k] / rb);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, e);
+        atomicAdd(out + 1, r);
+    }
+}
+
+// ----------------------------------------------------------- launching ----
+
+template <int CIN, int COUT, int EPI>
+static dw_status conv(SurrHandle *h, const bf16 *in, const bf16 *wt, const float *bias, bf16 *oz,
+                      bf16 *oa, float *of, const bf16 *zprev, cudaStream_t s) {
+    constexpr size_t smem = conv3_smem<CIN, COUT>();
+    static bool attr_set = false;  // one attribute per instantiation
+    if (!attr_set) {
+        DW_CUDA(cudaFuncSetAttribute(k_conv3<CIN, COUT, EPI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int ntiles = (h->n / CV_TX) * (h->n / CV_TY) * h->n;
+    const int grid = ntiles < h->conv_ctas ? ntiles : h->conv_ctas;
+    k_conv3<CIN, COUT, EPI><<<grid, CV_THREADS, smem, s>>>(in, wt, bias, h->n, oz, oa, of, zprev);
+    DW_LAUNCHED("k_conv3");
+    return DW_OK;
+}
+
+template <int CIN, int COUT>
+static dw_status wgrad(SurrHandle *h, const bf16 *in, const bf16 *g, int layer, cudaStream_t s) {
+    constexpr size_t smem = wgrad_smem<CIN, COUT>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        DW_CUDA(cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        attr_set = true;
+    }
+    k_wgrad<CIN, COUT><<<dim3(h->nchunks, 3), CV_THREADS, smem, s>>>(in, g, h->n, h->tiles_per_chunk,
+                                                                     h->part, h->part_b);
+    DW_LAUNCHED("k_wgrad");
+    const int64_t nw = 27LL * CIN * COUT;
+    k_wgrad_reduce<<<grid_for(nw + COUT, 256), 256, 0, s>>>(h->part, h->part_b, h->nchunks, nw, COUT,
+                                                            h->grads + h->off_w[layer],
+                                                            h->grads + h->off_b[layer]);
+    DW_LAUNCHED("k_wgrad_reduce");
+    return DW_OK;
+}
+
+static dw_status refresh_weights(SurrHandle *h, cudaStream_t s) {
+    for (int l = 0; l < 4; ++l) {
+        const int64_t cnt = 27LL * SCH[l] * SCH[l + 1];
+        k_surr_weights<<<grid_for(cnt, 256), 256, 0, s>>>(h->params, h->wf, h->wd, h->off_w[l],
+                                                          h->woff[l], SCH[l], SCH[l + 1]);
+    }
+    DW_LAUNCHED("k_surr_weights");
+    return DW_OK;
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+struct dw_surr_s : SurrHandle {};
+
+extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
+    DW_REQUIRE(out, "out must not be NULL");
+    *out = nullptr;
+    DW_REQUIRE(n >= 16 && n <= 256 && n % 16 == 0, "n=%d must be a multiple of 16 in [16, 256]", n);
+    dw_surr h = new (std::nothrow) dw_surr_s();
+    if (!h) {
+        set_error("out of host memory");
+        return DW_ERR_OOM;
+    }
+    h->n = n;
+    h->nv = (int64_t)n * n * n;
+    int64_t o = 0, wo = 0;
+    for (int l = 0; l < 4; ++l) {
+        h->off_w[l] = o;
+        h->woff[l] = wo;
+        o += 27LL * SCH[l] * SCH[l + 1];
+        wo += 27LL * SCH[l] * SCH[l + 1];
+        h->off_b[l] = o;
+        o += SCH[l + 1];
+    }
+    h->nparams = o;
+    const int ntiles = (n / CV_TX) * (n / CV_TY) * n;
+    h->tiles_per_chunk = 16;
+    h->nchunks = (ntiles + h->tiles_per_chunk - 1) / h->tiles_per_chunk;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    h->conv_ctas = 2 * (sms > 0 ? sms : 1);
+    const size_t nv = (size_t)h->nv, Nc = (size_t)8 * nv;
+#define DW_ALLOC(ptr, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
+    DW_ALLOC(h->params, sizeof(float) * o);
+    DW_ALLOC(h->grads, sizeof(float) * o);
+    DW_ALLOC(h->m, sizeof(float) * o);
+    DW_ALLOC(h->v, sizeof(float) * o);
+    DW_ALLOC(h->wf, sizeof(bf16) * wo);
+    DW_ALLOC(h->wd, sizeof(bf16) * wo);
+    DW_ALLOC(h->feats, sizeof(bf16) * nv * 16);
+    for (int l = 0; l < 3; ++l) {
+        DW_ALLOC(h->z[l], sizeof(bf16) * nv * 32);
+        DW_ALLOC(h->a[l], sizeof(bf16) * nv * 32);
+        DW_ALLOC(h->gz[l], sizeof(bf16) * nv * 32);
+    }
+    DW_ALLOC(h->out, sizeof(float) * nv * 16);
+    DW_ALLOC(h->g4, sizeof(bf16) * nv * 16);
+    DW_ALLOC(h->part, sizeof(float) * (size_t)h->nchunks * 27 * 32 * 32);
+    DW_ALLOC(h->part_b, sizeof(float) * (size_t)h->nchunks * 32);
+    DW_ALLOC(h->fine, sizeof(float) * 4 * Nc);
+    DW_ALLOC(h->red, sizeof(double) * 4);
+#undef DW_ALLOC
+    if (e == cudaSuccess) e = cudaMemset(h->params, 0, sizeof(float) * o);
+    if (e == cudaSuccess) e = cudaMemset(h->grads, 0, sizeof(float) * o);
+    if (e == cudaSuccess) e = cudaMemset(h->m, 0, sizeof(float) * o);
+    if (e == cudaSuccess) e = cudaMemset(h->v, 0, sizeof(float) * o);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dw_status st = cuda_fail(e, "surr_create");
+        surr_destroy(h);
+        return st;
+    }
+    *out = h;
+    return DW_OK;
+}
+
+extern "C" dw_status surr_destroy(dw_surr h) {
+    if (!h) return DW_OK;
+    cudaFree(h->params);
+    cudaFree(h->grads);
+    cudaFree(h->m);
+    cudaFree(h->v);
+    cudaFree(h->wf);
+    cudaFree(h->wd);
+    cudaFree(h->feats);
+    for (int l = 0; l < 3; ++l) {
+        cudaFree(h->z[l]);
+        cudaFree(h->a[l]);
+        cudaFree(h->gz[l]);
+    }
+    cudaFree(h->out);
+    cudaFree(h->g4);
+    cudaFree(h->part);
+    cudaFree(h->part_b);
+    cudaFree(h->fine);
+    cudaFree(h->red);
+    delete h;
+    return DW_OK;
+}
+
+extern "C" dw_status surr_num_params(dw_surr h, int64_t *count) {
+    DW_REQUIRE(h && count, "arguments must not be NULL");
+    *count = h->nparams;
+    return DW_OK;
+}
+
+extern "C" dw_status surr_set_params(dw_surr h, const float *src, dw_stream stream) {
+    DW_REQUIRE(h && src, "arguments must not be NULL");
+    cudaStream_t s = as_stream(stream);
+    DW_CUDA(cudaMemcpyAsync(h->params, src, sizeof(float) * h->nparams, cudaMemcpyDeviceToDevice, s));
+    return refresh_weights(h, s);
+}
+
+extern "C" dw_status surr_get_params(dw_surr h, float *dst, dw_stream stream) {
+    DW_REQUIRE(h && dst, "arguments must not be NULL");
+    DW_CUDA(cudaMemcpyAsync(dst, h->params, sizeof(float) * h->nparams, cudaMemcpyDeviceToDevice,
+                            as_stream(stream)));
+    return DW_OK;
+}
+
+extern "C" dw_status surr_get_grads(dw_surr h, float *dst, dw_stream stream) {
+    DW_REQUIRE(h && dst, "arguments must not be NULL");
+    DW_CUDA(cudaMemcpyAsync(dst, h->grads, sizeof(float) * h->nparams, cudaMemcpyDeviceToDevice,
+                            as_stream(stream)));
+    return DW_OK;
+}
+
+extern "C" dw_status surr_zero_grads(dw_surr h, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_CUDA(cudaMemsetAsync(h->grads, 0, sizeof(float) * h->nparams, as_stream(stream)));
+    return DW_OK;
+}
+
+extern "C" dw_status surr_features(dw_surr h, const float *f, const uint8_t *solid,
+                                   dw_stream stream) {
+    DW_REQUIRE(h && f, "handle and f must not be NULL");
+    cudaStream_t s = as_stream(stream);
+    const int N = 2 * h->n;
+    const int64_t nc = (int64_t)N * N * N;
+    k_surr_fine<<<grid_for(nc, 256), 256, 0, s>>>(f, solid, N, h->fine);
+    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, s>>>(h->fine, solid, h->n, h->feats);
+    DW_LAUNCHED("surr_features");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_set_features(dw_surr h, const float *feats, dw_stream stream) {
+    DW_REQUIRE(h && feats, "handle and feats must not be NULL");
+    k_f32_to_bf16<<<grid_for(h->nv * 16, 256), 256, 0, as_stream(stream)>>>(feats, h->feats, h->nv * 16);
+    DW_LAUNCHED("k_f32_to_bf16");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_get_features(dw_surr h, void *feats_bf16, dw_stream stream) {
+    DW_REQUIRE(h && feats_bf16, "handle and feats must not be NULL");
+    DW_CUDA(cudaMemcpyAsync(feats_bf16, h->feats, sizeof(bf16) * h->nv * 16, cudaMemcpyDeviceToDevice,
+                            as_stream(stream)));
+    return DW_OK;
+}
+
+extern "C" dw_status surr_forward(dw_surr h, float *out, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    cudaStream_t s = as_stream(stream);
+    dw_status st;
+    const float *P = h->params;
+    st = conv<16, 32, EPI_GELU>(h, h->feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s);
+    if (st != DW_OK) return st;
+    st = conv<32, 32, EPI_GELU>(h, h->a[0], h->wf + h->woff[1], P + h->off_b[1], h->z[1], h->a[1], nullptr, nullptr, s);
+    if (st != DW_OK) return st;
+    st = conv<32, 32, EPI_GELU>(h, h->a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
+    if (st != DW_OK) return st;
+    st = conv<32, 16, EPI_F32>(h, h->a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s);
+    if (st != DW_OK) return st;
+    if (out)
+        DW_CUDA(cudaMemcpyAsync(out, h->out, sizeof(float) * h->nv * 16, cudaMemcpyDeviceToDevice, s));
+    return DW_OK;
+}
+
+extern "C" dw_status surr_loss(dw_surr h, const float *target, float *loss, dw_stream stream) {
+    DW_REQUIRE(h && target, "handle and target must not be NULL");
+    cudaStream_t s = as_stream(stream);
+    int *cnt = reinterpret_cast<int *>(h->red);
+    DW_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    k_count_fluid<<<grid_for(h->nv, 256), 256, 0, s>>>(h->feats, h->nv, cnt);
+    k_surr_loss<<<grid_for(h->nv, 256), 256, 0, s>>>(h->out, target, h->feats, h->nv, cnt, h->g4, loss);
+    DW_LAUNCHED("k_surr_loss");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_set_output_grad(dw_surr h, const float *g_out, dw_stream stream) {
+    DW_REQUIRE(h && g_out, "handle and g_out must not be NULL");
+    k_f32_to_bf16<<<grid_for(h->nv * 16, 256), 256, 0, as_stream(stream)>>>(g_out, h->g4, h->nv * 16);
+    DW_LAUNCHED("k_f32_to_bf16");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_backward(dw_surr h, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    cudaStream_t s = as_stream(stream);
+    dw_status st;
+    // layer 4: dW from a3 and g4; dL/dz3 = (W4' * g4) GELU'(z3)
+    st = wgrad<32, 16>(h, h->a[2], h->g4, 3, s);
+    if (st != DW_OK) return st;
+    st = conv<16, 32, EPI_DGELU>(h, h->g4, h->wd + h->woff[3], nullptr, h->gz[2], nullptr, nullptr, h->z[2], s);
+    if (st != DW_OK) return st;
+    st = wgrad<32, 32>(h, h->a[1], h->gz[2], 2, s);
+    if (st != DW_OK) return st;
+    st = conv<32, 32, EPI_DGELU>(h, h->gz[2], h->wd + h->woff[2], nullptr, h->gz[1], nullptr, nullptr, h->z[1], s);
+    if (st != DW_OK) return st;
+    st = wgrad<32, 32>(h, h->a[0], h->gz[1], 1, s);
+    if (st != DW_OK) return st;
+    st = conv<32, 32, EPI_DGELU>(h, h->gz[1], h->wd + h->woff[1], nullptr, h->gz[0], nullptr, nullptr, h->z[0], s);
+    if (st != DW_OK) return st;
+    st = wgrad<16, 32>(h, h->feats, h->gz[0], 0, s);
+    return st;
+}
+
+extern "C" dw_status surr_adam(dw_surr h, float lr, float beta1, float beta2, float eps,
+                               int32_t step, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(step >= 1, "step counts from 1");
+    cudaStream_t s = as_stream(stream);
+    const float c1 = 1.0f / (1.0f - powf(beta1, (float)step));
+    const float c2 = 1.0f / (1.0f - powf(beta2, (float)step));
+    k_surr_adam<<<grid_for(h->nparams, 256), 256, 0, s>>>(h->params, h->grads, h->m, h->v, h->nparams,
+                                                          lr, beta1, beta2, eps, c1, c2);
+    DW_LAUNCHED("k_surr_adam");
+    return refresh_weights(h, s);
+}
+
+extern "C" dw_status surr_apply(dw_surr h, const float *out, const uint8_t *solid, float *f,
+                                dw_stream stream) {
+    DW_REQUIRE(h && f, "handle and f must not be NULL");
+    const int N = 2 * h->n;
+    const int64_t nc = (int64_t)N * N * N;
+    k_surr_apply<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(out ? out : h->out, h->fine, solid,
+                                                                   h->n, f);
+    DW_LAUNCHED("k_surr_apply");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_velocity_error(const float *fa, const float *fb, const uint8_t *solid,
+                                        int64_t ncell, double *sums, dw_stream stream) {
+    DW_REQUIRE(fa && fb && sums, "fa, fb and sums must not be NULL");
+    DW_REQUIRE(ncell > 0, "ncell must be > 0");
+    k_vel_err<<<grid_for(ncell, 256), 256, 0, as_stream(stream)>>>(fa, fb, solid, ncell, sums);
+    DW_LAUNCHED("k_vel_err");
+    return DW_OK;
+}

@@ -1,0 +1,274 @@
+// 3x3x3 convolutions of the surrogate network as implicit GEMMs on the tensor
+// cores (BF16 operands, FP32 accumulation), channels-last activations.
+//
+// Forward / input-gradient kernel k_conv3: out[v][co] = sum_{tap, ci}
+// W[tap][co][ci] in[v + d(tap)][ci] (zero outside the volume). A CTA computes
+// an output tile of 16 (x) x 8 (y) x 1 (z) voxels; warp w owns the 16 voxels of
+// row y0 + w, i.e. one M = 16 slice, and all COUT output channels. The input
+// halo (18 x 10 x 3 voxels) and the whole weight tensor live in shared memory;
+// A and B fragments come from ldmatrix with per-lane row addresses (the
+// implicit im2col), and mma.sync m16n8k16 accumulates in registers. CTAs are
+// persistent over tiles so the weights are loaded once per CTA.
+//
+// Weight-gradient kernel k_wgrad: dW[tap][co][ci] = sum_v g[v][co] in[v + d][ci]
+// per chunk of tiles, written as partial sums that k_wgrad_reduce adds up.
+//
+// Shared-memory rows (a voxel's or an output channel's CIN values) are stored
+// with their 16-byte chunks XOR-swizzled by the row index, so that the eight
+// rows an ldmatrix matrix reads hit distinct banks.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace dw {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int CV_TX = 16, CV_TY = 8;   // output tile
+constexpr int CV_HX = CV_TX + 2, CV_HY = CV_TY + 2, CV_HZ = 3;
+constexpr int CV_HALO = CV_HX * CV_HY * CV_HZ;  // 540 voxels
+constexpr int CV_THREADS = 256;
+
+enum { EPI_GELU = 0, EPI_F32 = 1, EPI_DGELU = 2 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of chunk c (16 B) of row r in a swizzled array with C channels
+template <int C>
+__device__ __forceinline__ uint32_t swz_off(int r, int c) {
+    constexpr int CPV = C / 8;
+    int cs = CPV == 4 ? (c ^ ((r >> 1) & 3)) : (c ^ ((r >> 2) & 1));
+    return (uint32_t)(r * C * 2 + cs * 16);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
+                                        uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
+                                          uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                          uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+           z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// Loads the 18 x 10 x 3 input halo of the tile at (x0, y0, z0) into smem.
+template <int C>
+__device__ __forceinline__ void load_halo(const bf16 *__restrict__ in, int n, int x0, int y0,
+                                          int z0, unsigned char *halo) {
+    constexpr int CPV = C / 8;
+    for (int idx = threadIdx.x; idx < CV_HALO * CPV; idx += blockDim.x) {
+        const int hr = idx / CPV, c = idx % CPV;
+        const int hx = hr % CV_HX, hy = (hr / CV_HX) % CV_HY, hz = hr / (CV_HX * CV_HY);
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gx >= 0 && gy >= 0 && gz >= 0 && gx < n && gy < n && gz < n)
+            v = *reinterpret_cast<const uint4 *>(in + (((size_t)gz * n + gy) * n + gx) * C + c * 8);
+        *reinterpret_cast<uint4 *>(halo + swz_off<C>(hr, c)) = v;
+    }
+}
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(CV_THREADS, 2) k_conv3(
+    const bf16 *__restrict__ in, const bf16 *__restrict__ wt, const float *__restrict__ bias,
+    int n, bf16 *__restrict__ out_z, bf16 *__restrict__ out_a, float *__restrict__ out_f,
+    const bf16 *__restrict__ zprev) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *wsm = smem;                                     // [27*COUT][CIN]
+    unsigned char *halo = smem + 27 * COUT * CIN * 2;              // [540][CIN]
+    constexpr int WCPV = CIN / 8;
+    for (int idx = threadIdx.x; idx < 27 * COUT * WCPV; idx += blockDim.x) {
+        const int row = idx / WCPV, c = idx % WCPV;
+        *reinterpret_cast<uint4 *>(wsm + swz_off<CIN>(row, c)) =
+            *reinterpret_cast<const uint4 *>(wt + (size_t)row * CIN + c * 8);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int tiles_x = n / CV_TX, tiles_y = n / CV_TY;
+    const int ntiles = tiles_x * tiles_y * n;
+    const uint32_t wbase = smem_u32(wsm), hbase = smem_u32(halo);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, z0 = tile / (tiles_x * tiles_y);
+        const int x0 = tx * CV_TX, y0 = ty * CV_TY;
+        __syncthreads();  // previous tile done with the halo (and the weights are in)
+        load_halo<CIN>(in, n, x0, y0, z0, halo);
+        __syncthreads();
+        float acc[COUT / 8][4];
+#pragma unroll
+        for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+        const int ar = lane & 15;  // A row (voxel) this lane addresses
+#pragma unroll 1
+        for (int t = 0; t < 27; ++t) {
+            const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+            const int hr = ((dz + 1) * CV_HY + (w + dy + 1)) * CV_HX + (ar + dx + 1);
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4(a0, a1, a2, a3, hbase + swz_off<CIN>(hr, 2 * kc + (lane >> 4)));
+#pragma unroll
+                for (int jj = 0; jj < COUT / 16; ++jj) {
+                    const int co = 16 * jj + ((lane >> 4) << 3) + (lane & 7);
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4(b0, b1, b2, b3,
+                            wbase + swz_off<CIN>(t * COUT + co, 2 * kc + ((lane >> 3) & 1)));
+                    mma_16816(acc[2 * jj], a0, a1, a2, a3, b0, b1);
+                    mma_16816(acc[2 * jj + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+        // epilogue: rows gid and gid + 8 of this warp's 16 voxels
+        const size_t vrow = ((size_t)z0 * n + (y0 + w)) * n + x0;
+#pragma unroll
+        for (int j = 0; j < COUT / 8; ++j) {
+            const int co = 8 * j + 2 * tig;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const size_t v = vrow + gid + 8 * h;
+                float z0v = acc[j][2 * h], z1v = acc[j][2 * h + 1];
+                if (EPI == EPI_GELU) {
+                    z0v += bias[co];
+                    z1v += bias[co + 1];
+                    *reinterpret_cast<__nv_bfloat162 *>(out_z + v * COUT + co) = __floats2bfloat162_rn(z0v, z1v);
+                    *reinterpret_cast<__nv_bfloat162 *>(out_a + v * COUT + co) =
+                        __floats2bfloat162_rn(gelu_f(z0v), gelu_f(z1v));
+                } else if (EPI == EPI_F32) {
+                    z0v += bias[co];
+                    z1v += bias[co + 1];
+                    *reinterpret_cast<float2 *>(out_f + v * COUT + co) = make_float2(z0v, z1v);
+                } else {
+                    const __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162 *>(zprev + v * COUT + co);
+                    const float g0 = z0v * gelu_grad_f(__bfloat162float(zp.x));
+                    const float g1 = z1v * gelu_grad_f(__bfloat162float(zp.y));
+                    *reinterpret_cast<__nv_bfloat162 *>(out_z + v * COUT + co) = __floats2bfloat162_rn(g0, g1);
+                }
+            }
+        }
+    }
+}
+
+template <int CIN, int COUT>
+constexpr size_t conv3_smem() {
+    return (size_t)27 * COUT * CIN * 2 + (size_t)CV_HALO * CIN * 2;
+}
+
+// Partial weight gradients of tap plane dz = blockIdx.y - 1 over the tiles of
+// chunk blockIdx.x: part[chunk][tap][co][ci] (taps of the plane only) and,
+// for blockIdx.y == 0, the bias-gradient partial part_b[chunk][co].
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(CV_THREADS) k_wgrad(const bf16 *__restrict__ in,
+                                                      const bf16 *__restrict__ g, int n,
+                                                      int tiles_per_chunk,
+                                                      float *__restrict__ part,
+                                                      float *__restrict__ part_b) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *gsm = smem;                       // [128][COUT]
+    unsigned char *halo = smem + 128 * COUT * 2;     // [540][CIN]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int dz = (int)blockIdx.y - 1;
+    const int tiles_x = n / CV_TX, tiles_y = n / CV_TY;
+    const int ntiles = tiles_x * tiles_y * n;
+    constexpr int MT = COUT / 16, NT = CIN / 8;
+    constexpr int ITEMS = 9 * MT;                      // (tap in plane, m tile)
+    constexpr int PER_WARP = (ITEMS + 7) / 8;
+    float acc[PER_WARP][NT][4];
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
+    float bsum = 0.0f;
+    const uint32_t gbase = smem_u32(gsm), hbase = smem_u32(halo);
+    const int t0 = blockIdx.x * tiles_per_chunk, t1 = min(ntiles, t0 + tiles_per_chunk);
+    for (int tile = t0; tile < t1; ++tile) {
+        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, z0 = tile / (tiles_x * tiles_y);
+        const int x0 = tx * CV_TX, y0 = ty * CV_TY;
+        __syncthreads();
+        load_halo<CIN>(in, n, x0, y0, z0, halo);
+        constexpr int GCPV = COUT / 8;
+        for (int idx = threadIdx.x; idx < 128 * GCPV; idx += blockDim.x) {
+            const int kv = idx / GCPV, c = idx % GCPV;
+            const size_t v = ((size_t)z0 * n + (y0 + kv / 16)) * n + x0 + kv % 16;
+            *reinterpret_cast<uint4 *>(gsm + swz_off<COUT>(kv, c)) =
+                *reinterpret_cast<const uint4 *>(g + v * COUT + c * 8);
+        }
+        __syncthreads();
+        if (blockIdx.y == 0 && threadIdx.x < COUT) {
+            for (int kv = 0; kv < 128; ++kv) {
+                const bf16 *row = reinterpret_cast<const bf16 *>(gsm + swz_off<COUT>(kv, threadIdx.x / 8));
+                bsum += __bfloat162float(row[threadIdx.x % 8]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PER_WARP; ++i) {
+            const int item = w + 8 * i;
+            if (item >= ITEMS) break;
+            const int tl = item / MT, mt = item % MT;  // tap in plane, m tile
+            const int dx = tl % 3 - 1, dy = tl / 3 - 1;
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+                uint32_t a0, a1, a2, a3;
+                {
+                    const int kv = ks * 16 + ((lane >> 4) << 3) + (lane & 7);
+                    ldsm_x4_t(a0, a1, a2, a3, gbase + swz_off<COUT>(kv, 2 * mt + ((lane >> 3) & 1)));
+                }
+                const int kvb = ks * 16 + (((lane >> 3) & 1) << 3) + (lane & 7);
+                const int hr = ((dz + 1) * CV_HY + (kvb / 16 + dy + 1)) * CV_HX + (kvb % 16 + dx + 1);
+#pragma unroll
+                for (int jj = 0; jj < NT / 2; ++jj) {
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_t(b0, b1, b2, b3, hbase + swz_off<CIN>(hr, 2 * jj + (lane >> 4)));
+                    mma_16816(acc[i][2 * jj], a0, a1, a2, a3, b0, b1);
+                    mma_16816(acc[i][2 * jj + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+    }
+    // write partials: row co = 16 mt + gid (+8), col ci = 8 j + 2 tig (+1)
+    float *pc = part + (size_t)blockIdx.x * 27 * COUT * CIN;
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) {
+        const int item = w + 8 * i;
+        if (item >= ITEMS) break;
+        const int tl = item / MT, mt = item % MT;
+        const int tap = (dz + 1) * 9 + tl;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int co = 16 * mt + gid + 8 * h, ci = 8 * j + 2 * tig;
+                *reinterpret_cast<float2 *>(pc + ((size_t)tap * COUT + co) * CIN + ci) =
+                    make_float2(acc[i][j][2 * h], acc[i][j][2 * h + 1]);
+            }
+    }
+    if (blockIdx.y == 0 && threadIdx.x < COUT) part_b[(size_t)blockIdx.x * COUT + threadIdx.x] = bsum;
+}
+
+template <int CIN, int COUT>
+constexpr size_t wgrad_smem() {
+    return (size_t)128 * COUT * 2 + (size_t)CV_HALO * CIN * 2;
+}
+
+}  // namespace dw

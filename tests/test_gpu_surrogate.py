@@ -1,0 +1,154 @@
+"""GPU parity of the surrogate network (BF16 tensor-core convolutions, FP32
+accumulation) against the FP64 oracle, through the C-ABI.
+
+The oracle receives the same BF16-rounded weights and features (as float64),
+so the differences come from the BF16 storage of the hidden activations and
+gradients: unit roundoff 2^-8 per stored value, a few roundings per layer,
+giving about 1% relative L2 at the output. Tolerances: forward 2e-2, weight
+gradients 5e-2 relative L2 per layer, features 1e-2 (one BF16 rounding),
+re-equilibrated populations 1e-6 absolute (FP32 arithmetic on exact inputs)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_09668_gb300 import binding as B
+from paper_2603_09668_gb300 import inputs
+
+from gpu_util import rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def random_params(seed=0, scale=1.0):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(oracle.surr_num_params(), np.float32)
+    for ws, bs, cin, cout in oracle.surr_layer_slices():
+        p[ws] = rng.standard_normal(ws.stop - ws.start) * scale * np.sqrt(2.0 / (27 * cin))
+        p[bs] = rng.standard_normal(cout) * 0.1
+    return p
+
+
+def oracle_params(p):
+    """BF16-rounded weights, FP32 biases: what the GPU computes with."""
+    q = np.asarray(p, np.float64).copy()
+    for ws, bs, cin, cout in oracle.surr_layer_slices():
+        q[ws] = bf16_round(p[ws])
+    return q
+
+
+def random_features(n, seed=1):
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n ** 3, 16), np.float32)
+    f[:, :5] = rng.standard_normal((n ** 3, 5)).astype(np.float32)
+    return f
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_forward_matches_oracle(n):
+    p = random_params(seed=n)
+    feats = random_features(n, seed=n + 1)
+    s = B.Surrogate(n)
+    s.set_params(to_dev(p))
+    s.set_features(to_dev(feats))
+    out = torch.empty((n ** 3, 16), device="cuda")
+    s.forward(out)
+    ref = oracle.surr_forward(n, oracle_params(p), bf16_round(feats))
+    assert rel_l2(out.cpu().numpy()[:, :3].astype(np.float64), ref[:, :3]) <= 2e-2
+    assert rel_l2(out.cpu().numpy().astype(np.float64), ref) <= 2e-2
+    s.close()
+
+
+def test_backward_matches_oracle():
+    n = 16
+    p = random_params(seed=3)
+    feats = random_features(n, seed=4)
+    g_out = np.zeros((n ** 3, 16), np.float32)
+    g_out[:, :3] = np.random.default_rng(5).standard_normal((n ** 3, 3)).astype(np.float32)
+    s = B.Surrogate(n)
+    s.set_params(to_dev(p))
+    s.set_features(to_dev(feats))
+    s.zero_grads()
+    s.forward()
+    s.set_output_grad(to_dev(g_out))
+    s.backward()
+    g = s.grads().cpu().numpy().astype(np.float64)
+    ref = oracle.surr_backward(n, oracle_params(p), bf16_round(feats), bf16_round(g_out))
+    for l, (ws, bs, cin, cout) in enumerate(oracle.surr_layer_slices()):
+        assert rel_l2(g[ws], ref[ws]) <= 5e-2, (l, "W", rel_l2(g[ws], ref[ws]))
+        assert rel_l2(g[bs], ref[bs]) <= 5e-2, (l, "b", rel_l2(g[bs], ref[bs]))
+    s.close()
+
+
+def test_features_and_apply_match_oracle():
+    n = 16
+    N = 2 * n
+    shape = (N, N, N)
+    c, w, _ = oracle.velocity_set()
+    solid = inputs.random_mask(shape, 0.1, seed=6)
+    rng = np.random.default_rng(7)
+    u0 = np.array([0.05, 0.01, -0.02])
+    feq = oracle.lbm_equilibrium(1.0, u0)
+    f_plain = feq[:, None] + rng.uniform(-2e-3, 2e-3, (19, N ** 3))
+    f_dev = to_dev((f_plain - w[:, None]).astype(np.float32).reshape(19, N, N, N))
+    s = B.Surrogate(n)
+    s.features(f_dev, to_dev(solid).reshape(N, N, N))
+    got = s.get_features().float().cpu().numpy().astype(np.float64)
+    ref, rho, u = oracle.surr_features(n, f_plain.astype(np.float32).astype(np.float64), solid)
+    assert np.abs(got - ref).max() <= 1e-2 * np.abs(ref).max()
+    assert np.array_equal(got[:, 4], ref[:, 4])  # solid fractions are exact in BF16
+    du = np.zeros((n ** 3, 16), np.float32)
+    du[:, :3] = rng.standard_normal((n ** 3, 3)).astype(np.float32) * 1e-3
+    f_out = f_dev.clone()
+    s.apply(to_dev(solid).reshape(N, N, N), f_out, to_dev(du))
+    f_ref = oracle.surr_apply(n, du, rho, u, f_plain, solid)
+    got_f = f_out.reshape(19, -1).cpu().numpy().astype(np.float64) + w[:, None]
+    fl = solid == 0
+    assert np.abs(got_f[:, fl] - f_ref[:, fl]).max() <= 1e-6
+    s.close()
+
+
+def test_velocity_error_reduction():
+    N = 24
+    c, w, _ = oracle.velocity_set()
+    rng = np.random.default_rng(8)
+    fa = rng.uniform(-1e-3, 1e-3, (19, N ** 3)).astype(np.float32)
+    fb = rng.uniform(-1e-3, 1e-3, (19, N ** 3)).astype(np.float32)
+    solid = inputs.random_mask((N, N, N), 0.2, seed=9)
+    sums = torch.zeros(2, dtype=torch.float64, device="cuda")
+    B.lbm_velocity_error(to_dev(fa), to_dev(fb), to_dev(solid), sums)
+    _, ua = oracle.lbm_macroscopic((N, N, N), fa.astype(np.float64) + w[:, None], solid=solid)
+    _, ub = oracle.lbm_macroscopic((N, N, N), fb.astype(np.float64) + w[:, None], solid=solid)
+    e = np.sum((ua - ub) ** 2)
+    r = np.sum(ub ** 2)
+    assert sums[0].item() == pytest.approx(e, rel=1e-4)
+    assert sums[1].item() == pytest.approx(r, rel=1e-4)
+
+
+def test_training_fits_a_teacher_network():
+    """Adam on the library's forward/backward kernels fits the outputs of a
+    random teacher network of the same architecture."""
+    n = 16
+    feats = random_features(n, seed=10)
+    teacher = random_params(seed=11, scale=0.5)
+    target = oracle.surr_forward(n, oracle_params(teacher), bf16_round(feats)).astype(np.float32)
+    s = B.Surrogate(n)
+    s.set_params(to_dev(random_params(seed=12, scale=0.5)))
+    s.set_features(to_dev(feats))
+    tgt = to_dev(target)
+    losses = []
+    loss = torch.zeros(1, device="cuda")
+    for step in range(1, 201):
+        loss.zero_()
+        s.forward()
+        s.loss(tgt, loss)
+        s.backward()
+        s.adam(3e-3, step)
+        if step in (1, 200):
+            losses.append(loss.item())
+    assert losses[1] < 0.1 * losses[0], losses
+    s.close()
