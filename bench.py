@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--substeps", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint"],
+    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch"],
                     help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
                          "or the checkpointed MPM adjoint")
     ap.add_argument("--p2g-mode", type=int, default=0,
@@ -405,9 +405,99 @@ def bench_adjoint(dev):
             "mpm_adj_note": "200 substeps forward + checkpointed adjoint (recompute + reverse)"}
 
 
+def bench_surrogate(dev, N=128, t_eval=1500, blocks=25):
+    """The learned LBM surrogate on a held-out leaf-cluster scene (128^3, tau
+    0.55, inlet 0.05 in a random direction): relative L2 velocity error of one
+    20-step block against the plain LBM from the same state (and of persistence,
+    du = 0, for comparison), times of a plain block and of a chained surrogate
+    block, and a run of `blocks` blocks with the plain-LBM check every 10."""
+    import math
+
+    import torch
+
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import surrogate as S
+
+    if not os.path.exists(S.weights_path(N)):
+        return {"surrogate": "no trained weights"}
+    rng = np.random.default_rng(987654)
+    d = S.inlet_direction(rng)
+    solid = S.leaf_mask(N, 424242, dev)
+    m = S.SurrogateLBM(N, u_inlet=tuple(S.U_REF * d))
+    f0 = m.lbm.lattice(dev)
+    m.lbm.step(f0, solid, t_eval)
+    ref = f0.clone()
+    m.plain_block(ref, solid)
+    err_persist = m.velocity_error(f0, ref, solid)
+    m.surr.features(f0, solid, S.IN_SCALE)
+    m.chained_block(solid)
+    err_net = m.fine_error(ref, solid)
+    f = f0.clone()
+    ms_plain = _timed(lambda: m.plain_block(f, solid), reps=5)
+    m.surr.features(f0, solid, S.IN_SCALE)
+    ms_surr = _timed(lambda: m.chained_block(solid), reps=5)
+    # longer run with checks against the plain LBM
+    f_plain = f0.clone()
+    m.lbm.step(f_plain, solid, 20 * blocks)
+    f_sur = f0.clone()
+    m.calls = 0
+    m.errors = []
+    used = m.advance(f_sur, solid, blocks)
+    err_run = m.velocity_error(f_sur, f_plain, solid)
+    m.close()
+    return {"surr_block_err": err_net, "persistence_err": err_persist,
+            "surr_block_ms": ms_surr, "plain_block_ms": ms_plain,
+            "surr_speedup": ms_plain / ms_surr, "surr_run_blocks": blocks,
+            "surr_run_used": used, "surr_run_check_errors": m.errors,
+            "surr_run_final_err": err_run}
+
+
+def bench_batch(dev, n_scenes=64, n_sub=500, sort_every=25, trial=10):
+    """64 uneven scenes (particle counts log-uniform 20k-400k, 64^3 / 128^3
+    grids, sheets and blocks, each with its own 16^3 x 8 wind) advanced by the
+    batched rollout: one launch per substep, replayed from a CUDA graph, launch
+    shape picked by the autotuner. Reported: whole-batch particle-substeps/s
+    over n_sub substeps with re-sorting every sort_every, and the tuner's
+    table (ms per substep per candidate)."""
+    import torch
+
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import inputs
+
+    scenes = inputs.batch_scenes(n_scenes=n_scenes, n_substeps=n_sub)
+    winds = [B.WindField(torch.from_numpy(sc.wind.astype(np.float32)).to(dev), sc.t_total)
+             for sc in scenes]
+    batch = B.MPMBatch([(sc.params(), sc.n, w) for sc, w in zip(scenes, winds)])
+    st = [np.concatenate([inputs.rest_state(sc.x)[i] for sc in scenes], axis=1) for i in range(4)]
+    pin = np.concatenate([sc.pinned if sc.pinned is not None else np.zeros(sc.n, np.uint8)
+                          for sc in scenes])
+    s0 = B.MpmState(*(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in st))
+    p0 = torch.from_numpy(pin).to(dev)
+    best, trials = batch.tune(s0, p0, n_trial_substeps=trial)
+    s = s0.clone()
+    p = p0.clone()
+    ids = torch.arange(batch.n, dtype=torch.int32, device=dev)
+
+    def run():
+        batch.rollout(s, p, ids, 0.0, n_sub, sort_every)
+
+    ms = _timed(run, reps=2)
+    batch.device_status()
+    cfg = batch.config()
+    batch.close()
+    n = int(batch.n)
+    return {"batch_scenes": n_scenes, "batch_particles": n, "batch_substeps": n_sub,
+            "batch_ps_per_s": n * n_sub / (ms * 1e-3), "batch_ms_per_substep": ms / n_sub,
+            "batch_config": cfg, "batch_tuner": [[t[0]["mode"], t[0]["threads"],
+                                                  t[0]["ctas_per_sm"], round(t[1], 4)]
+                                                 for t in trials]}
+
+
 def extras(dev):
     out = bench_lbm(dev)
     out.update(bench_adjoint(dev))
+    out.update(bench_surrogate(dev))
+    out.update(bench_batch(dev))
     return out
 
 
@@ -477,6 +567,10 @@ def run_only(args):
     _build.build_library()
     if args.only == "lbm":
         res = bench_lbm(dev, steps=2 * max(args.steps, 1), adj_steps=2)
+    elif args.only == "surrogate":
+        res = bench_surrogate(dev)
+    elif args.only == "batch":
+        res = bench_batch(dev)
     else:
         res = bench_adjoint(dev)
     print(json.dumps({"only": args.only, **res}), flush=True)
@@ -486,7 +580,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.only in ("lbm", "adjoint"):
+    elif a.only in ("lbm", "adjoint", "surrogate", "batch"):
         run_only(a)
     else:
         run_ours(a)

@@ -225,6 +225,110 @@ DW_API dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_state
                                      const dw_wind_field *wind, float t,
                                      int32_t *device_status, dw_stream stream);
 
+/* ============================================================ batched MPM
+ * Many independent scenes, each with its own grid size, material, time step,
+ * particle count and wind field, advanced by the same substep as mpm_rollout
+ * (Eq. simulation_mpm per scene; no data flows between scenes). The paper
+ * runs one scene at a time; batching is a throughput variant for ensembles
+ * such as several objects, wind candidates or optimisation restarts.
+ *
+ * Particle state of the batch: ONE concatenated structure-of-arrays state of
+ * n = sum n_particles particles (x[3][n], v[3][n], C[9][n], F[9][n], pinned
+ * uint8[n], ids int32[n]); scene s owns the particles [off_s, off_s + n_s)
+ * with off_s = n_0 + ... + n_(s-1), in the order the scenes were given. A
+ * particle never changes scene: sorting permutes within each scene's range.
+ *
+ * Launch shape (dw_batch_config): in DW_BATCH_PERSISTENT mode every substep
+ * is ONE cooperative kernel launch whose CTAs first run the grid update of the
+ * active 4^3 node blocks of all scenes, meet at a grid-wide barrier, then run
+ * G2P of the substep fused with the P2G of the next one over 128-particle
+ * work items (one scene per item). The barrier's wait is bounded: if it gives
+ * up, the device status becomes DW_ERR_TIMEOUT and later substeps of the
+ * batch do nothing until mpm_batch_device_status clears it. DW_BATCH_SPLIT
+ * runs the two phases as two launches (programmatic dependent launch). With
+ * use_graph, the whole launch sequence of a rollout is captured once per
+ * distinct (state pointers, n_substeps, sort_every, config) in a CUDA graph
+ * owned by the handle and replayed; if capture is not possible the sequence
+ * is launched directly (mpm_batch_get_config reports graph_active = 0).
+ */
+enum { DW_BATCH_PERSISTENT = 0, DW_BATCH_SPLIT = 1 };
+
+typedef struct {
+    dw_mpm_desc desc;      /* the scene's physics; desc.max_particles and desc.p2g_mode are ignored */
+    int64_t n_particles;   /* particles of the scene, >= 1 */
+    dw_wind_field wind;    /* the scene's wind field; its device values are read by every later
+                              rollout and must stay valid and unchanged while the handle lives */
+} dw_mpm_scene;
+
+typedef struct {
+    int32_t mode;          /* DW_BATCH_PERSISTENT or DW_BATCH_SPLIT */
+    int32_t threads;       /* CTA size, 128 or 256 (one or two 128-particle work items per CTA) */
+    int32_t ctas_per_sm;   /* PERSISTENT: resident CTAs per SM (>= 1, clamped to the occupancy
+                              limit); SPLIT: CTAs per SM of the grid-update launch */
+    int32_t use_graph;     /* nonzero: replay rollouts from a CUDA graph */
+    int32_t graph_active;  /* output of mpm_batch_get_config: the last rollout ran from a graph */
+} dw_batch_config;
+
+typedef struct {
+    dw_batch_config config;
+    float ms_per_substep;  /* measured device time of one substep with this configuration */
+} dw_batch_trial;
+
+typedef struct dw_mpm_batch_s *dw_mpm_batch;
+
+/* Allocate a batch for n_scenes scenes (1 <= n_scenes <= 2048): per-scene
+ * grids, active-block lists, the sort workspace and a second state buffer of
+ * n particles. Each desc is checked as in mpm_create; every scene's n_grid
+ * must be <= 400, and the sum of n_grid^3 over the scenes below 2^31. The
+ * initial configuration is PERSISTENT, 128 threads, the occupancy limit of
+ * CTAs per SM, graphs on. Errors: DW_ERR_ARG, DW_ERR_OOM, DW_ERR_CUDA. */
+DW_API dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scenes, dw_mpm_batch *out);
+DW_API dw_status mpm_batch_destroy(dw_mpm_batch h);
+
+/* Total particle count n of the batch and the first particle of each scene:
+ * offsets (host int64[n_scenes + 1] or NULL) receives off_0 .. off_n_scenes. */
+DW_API dw_status mpm_batch_layout(dw_mpm_batch h, int64_t *n_total, int64_t *offsets);
+
+/* n_substeps substeps of every scene, in place on the concatenated `state`
+ * (state->n must equal the batch's n): scene s runs mpm_rollout's arithmetic
+ * with its own desc and wind at times t0 + k dt_s, k = 0 .. n_substeps - 1.
+ * Every sort_every substeps (0 = never) each scene's particles are re-sorted
+ * by cell within the scene's range; pinned (device uint8[n] or NULL) is
+ * permuted along and ids (device int32[n], required when sort_every > 0) is
+ * carried through the sorts as in mpm_rollout. */
+DW_API dw_status mpm_batch_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint8_t *pinned,
+                                   int32_t *ids, float t0, int32_t n_substeps, int32_t sort_every,
+                                   dw_stream stream);
+
+DW_API dw_status mpm_batch_set_config(dw_mpm_batch h, const dw_batch_config *config);
+DW_API dw_status mpm_batch_get_config(dw_mpm_batch h, dw_batch_config *config);
+
+/* Autotuner: times every candidate launch shape (both modes, 128 and 256
+ * threads, each resident-CTA count up to the occupancy limit) on
+ * n_trial_substeps substeps of the batch started from `state` (copied into
+ * the handle's workspace; `state` and `pinned` are not modified), keeps the
+ * fastest as the handle's configuration (use_graph unchanged) and returns it
+ * in *best (may be NULL). trials (host, max_trials entries, or NULL) receives
+ * each candidate and its time; *n_trials (may be NULL) their number. The call
+ * waits for `stream`. */
+DW_API dw_status mpm_batch_tune(dw_mpm_batch h, const dw_mpm_state *state, const uint8_t *pinned,
+                                int32_t n_trial_substeps, dw_batch_config *best,
+                                dw_batch_trial *trials, int32_t max_trials, int32_t *n_trials,
+                                dw_stream stream);
+
+/* As mpm_device_status, for the batch (any scene). Also resets the barrier
+ * state, so a batch whose barrier gave up is usable again afterwards. */
+DW_API dw_status mpm_batch_device_status(dw_mpm_batch h, dw_stream stream);
+
+/* Failure-detection self-test of the persistent kernel's grid barrier: one
+ * cooperative launch of one CTA per SM runs the barrier alone, told to wait
+ * for missing_ctas (0..1024) more CTAs than were launched. With 0 it must
+ * pass (returns DW_OK); otherwise every CTA's bounded wait runs out (about a
+ * second) and the call returns DW_ERR_TIMEOUT. Waits for `stream` and clears
+ * the status like mpm_batch_device_status. */
+DW_API dw_status mpm_batch_barrier_selftest(dw_mpm_batch h, int32_t missing_ctas,
+                                            dw_stream stream);
+
 /* ====================================================================== LBM
  * D3Q19 lattice Boltzmann step (Eq. lbe) with the BGK collision
  * f* = f - (f - f_eq)/tau (+ Guo forcing for a uniform body force F, with
@@ -313,16 +417,20 @@ DW_API dw_status surr_set_params(dw_surr h, const float *src, dw_stream stream);
 DW_API dw_status surr_get_params(dw_surr h, float *dst, dw_stream stream);
 DW_API dw_status surr_get_grads(dw_surr h, float *dst, dw_stream stream);
 DW_API dw_status surr_zero_grads(dw_surr h, dw_stream stream);
-/* Coarse features from a shifted (2n)^3 lattice f [19][cells] and its mask;
- * also keeps the fine rho and u for surr_apply. */
-DW_API dw_status surr_features(dw_surr h, const float *f, const uint8_t *solid, dw_stream stream);
+/* Coarse features from a shifted (2n)^3 lattice f [19][cells] and its mask,
+ * channels (rho - 1, ux, uy, uz) multiplied by in_scale and the solid
+ * fraction; also keeps the fine rho and u for surr_apply. feats32 (device
+ * [n^3][16], may be NULL) receives the features in FP32 as well. */
+DW_API dw_status surr_features(dw_surr h, const float *f, const uint8_t *solid, float in_scale,
+                               float *feats32, dw_stream stream);
 /* Set the coarse features directly from FP32 [n^3][16] (rounded to BF16). */
 DW_API dw_status surr_set_features(dw_surr h, const float *feats, dw_stream stream);
 /* Copy the current BF16 features [n^3][16] out. */
 DW_API dw_status surr_get_features(dw_surr h, void *feats_bf16, dw_stream stream);
-/* Network forward; keeps the activations for surr_backward; copies the FP32
- * output [n^3][16] to out when out is not NULL. */
-DW_API dw_status surr_forward(dw_surr h, float *out, dw_stream stream);
+/* Network forward; with keep_activations != 0 keeps what surr_backward
+ * needs (training), otherwise stores only the layer outputs (inference);
+ * copies the FP32 output [n^3][16] to out when out is not NULL. */
+DW_API dw_status surr_forward(dw_surr h, float *out, int32_t keep_activations, dw_stream stream);
 /* Mean squared error of output channels 0..2 against target [n^3][16] over the
  * coarse voxels that are not fully solid; adds the loss to *loss (device
  * float, may be NULL) and sets dL/d(output) for surr_backward. */
@@ -336,12 +444,25 @@ DW_API dw_status surr_backward(dw_surr h, dw_stream stream);
 DW_API dw_status surr_adam(dw_surr h, float lr, float beta1, float beta2, float eps, int32_t step,
                            dw_stream stream);
 /* f = f_eq(rho, u + du) on the fluid cells of the shifted (2n)^3 lattice, with
- * rho, u from the last surr_features and du the output (out [n^3][16], or the
- * handle's last forward output when NULL) upsampled trilinearly from the
- * cell-centred coarse grid (fine cell i at coarse coordinate i/2 - 1/4,
- * clamped). Solid cells are not written. */
-DW_API dw_status surr_apply(dw_surr h, const float *out, const uint8_t *solid, float *f,
-                            dw_stream stream);
+ * rho, u from the last surr_features and du = out_scale times the output
+ * channels 0..2 (out [n^3][16], or the handle's last forward output when NULL)
+ * upsampled trilinearly from the cell-centred coarse grid (fine cell i at
+ * coarse coordinate i/2 - 1/4, clamped). Solid cells are not written. */
+DW_API dw_status surr_apply(dw_surr h, const float *out, float out_scale, const uint8_t *solid,
+                            float *f, dw_stream stream);
+/* Chained mode: the handle's fine (rho, u) state stands in for the lattice
+ * between surrogate calls. surr_features_fine takes the coarse features from
+ * it, surr_advance_fine adds out_scale times the upsampled output to its u,
+ * surr_write_lattice re-initialises f = f_eq(rho, u) on the fluid cells, and
+ * surr_fine_velocity_error adds sum |u_fine - u(f)|^2 and sum |u(f)|^2 over
+ * the fluid cells to sums (device double[2]). */
+DW_API dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float in_scale,
+                                    dw_stream stream);
+DW_API dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *solid,
+                                   dw_stream stream);
+DW_API dw_status surr_write_lattice(dw_surr h, const uint8_t *solid, float *f, dw_stream stream);
+DW_API dw_status surr_fine_velocity_error(dw_surr h, const float *f, const uint8_t *solid,
+                                          double *sums, dw_stream stream);
 /* sums[0] += sum |u_a - u_b|^2, sums[1] += sum |u_b|^2 over the fluid cells of
  * two shifted lattices with ncell cells (device double[2]). */
 DW_API dw_status lbm_velocity_error(const float *fa, const float *fb, const uint8_t *solid,

@@ -31,6 +31,19 @@ class DwMpmState(ct.Structure):
                 ("n", ct.c_int64)]
 
 
+class DwMpmScene(ct.Structure):
+    _fields_ = [("desc", DwMpmDesc), ("n_particles", ct.c_int64), ("wind", DwWindField)]
+
+
+class DwBatchConfig(ct.Structure):
+    _fields_ = [("mode", ct.c_int32), ("threads", ct.c_int32), ("ctas_per_sm", ct.c_int32),
+                ("use_graph", ct.c_int32), ("graph_active", ct.c_int32)]
+
+
+class DwBatchTrial(ct.Structure):
+    _fields_ = [("config", DwBatchConfig), ("ms_per_substep", ct.c_float)]
+
+
 class DwLbmDesc(ct.Structure):
     _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("tau", ct.c_float),
                 ("u_inlet", ct.c_float * 3), ("force", ct.c_float * 3), ("bc_x", ct.c_int32),
@@ -62,6 +75,16 @@ SIGNATURES = {
     "mpm_profile_read": (I32, [VP, P(ct.c_double), P(I64)]),
     "mpm_substep_noalloc": (I32, [P(DwMpmDesc), P(DwMpmState), P(DwMpmState), VP,
                                   P(DwWindField), F32, VP, VP]),
+    "mpm_batch_create": (I32, [P(DwMpmScene), I32, P(VP)]),
+    "mpm_batch_destroy": (I32, [VP]),
+    "mpm_batch_layout": (I32, [VP, P(I64), P(I64)]),
+    "mpm_batch_rollout": (I32, [VP, P(DwMpmState), VP, VP, F32, I32, I32, VP]),
+    "mpm_batch_set_config": (I32, [VP, P(DwBatchConfig)]),
+    "mpm_batch_get_config": (I32, [VP, P(DwBatchConfig)]),
+    "mpm_batch_tune": (I32, [VP, P(DwMpmState), VP, I32, P(DwBatchConfig), P(DwBatchTrial), I32,
+                             P(I32), VP]),
+    "mpm_batch_device_status": (I32, [VP, VP]),
+    "mpm_batch_barrier_selftest": (I32, [VP, I32, VP]),
     "lbm_create": (I32, [P(DwLbmDesc), P(VP)]),
     "lbm_destroy": (I32, [VP]),
     "lbm_step": (I32, [VP, VP, VP, I32, VP]),
@@ -76,15 +99,19 @@ SIGNATURES = {
     "surr_get_params": (I32, [VP, VP, VP]),
     "surr_get_grads": (I32, [VP, VP, VP]),
     "surr_zero_grads": (I32, [VP, VP]),
-    "surr_features": (I32, [VP, VP, VP, VP]),
+    "surr_features": (I32, [VP, VP, VP, F32, VP, VP]),
     "surr_set_features": (I32, [VP, VP, VP]),
     "surr_get_features": (I32, [VP, VP, VP]),
-    "surr_forward": (I32, [VP, VP, VP]),
+    "surr_forward": (I32, [VP, VP, I32, VP]),
+    "surr_features_fine": (I32, [VP, VP, F32, VP]),
+    "surr_advance_fine": (I32, [VP, F32, VP, VP]),
+    "surr_write_lattice": (I32, [VP, VP, VP, VP]),
+    "surr_fine_velocity_error": (I32, [VP, VP, VP, VP, VP]),
     "surr_loss": (I32, [VP, VP, VP, VP]),
     "surr_set_output_grad": (I32, [VP, VP, VP]),
     "surr_backward": (I32, [VP, VP]),
     "surr_adam": (I32, [VP, F32, F32, F32, F32, I32, VP]),
-    "surr_apply": (I32, [VP, VP, VP, VP, VP]),
+    "surr_apply": (I32, [VP, VP, F32, VP, VP, VP]),
     "lbm_velocity_error": (I32, [VP, VP, VP, I64, VP, VP]),
 }
 

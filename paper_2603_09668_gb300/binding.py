@@ -14,7 +14,8 @@ from typing import NamedTuple, Optional
 
 import torch
 
-from ._capi import (DiffWindError, DwLbmDesc, DwMpmDesc, DwMpmState, DwWindField, check, lib)
+from ._capi import (DiffWindError, DwBatchConfig, DwBatchTrial, DwLbmDesc, DwMpmDesc, DwMpmScene,
+                    DwMpmState, DwWindField, check, lib)
 
 __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "wind_field_sample_adjoint", "mpm_create", "mpm_destroy", "mpm_set_material",
@@ -25,9 +26,14 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
-           "surr_backward", "surr_adam", "surr_apply", "lbm_velocity_error", "Surrogate"]
+           "surr_backward", "surr_adam", "surr_apply", "lbm_velocity_error", "Surrogate",
+           "surr_features_fine", "surr_advance_fine", "surr_write_lattice",
+           "surr_fine_velocity_error", "mpm_batch_create", "mpm_batch_destroy",
+           "mpm_batch_layout", "mpm_batch_rollout", "mpm_batch_set_config",
+           "mpm_batch_get_config", "mpm_batch_tune", "mpm_batch_device_status", "mpm_batch_barrier_selftest", "MPMBatch"]
 
 NEOHOOKEAN, FIXED_COROTATED = 0, 1
+BATCH_PERSISTENT, BATCH_SPLIT = 0, 1
 P2G_AUTO, P2G_ATOMIC, P2G_WARP, P2G_TILE = 0, 1, 2, 3
 
 
@@ -215,6 +221,81 @@ def mpm_profile_read(h):
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_NAMES)}
 
 
+# ------------------------------------------------------------- batched MPM --
+
+def _desc_of(p: dict, max_particles=0, p2g_mode=P2G_AUTO):
+    return DwMpmDesc(int(p["n_grid"]), float(p["dt"]), (ct.c_float * 3)(*p["gravity"]),
+                     int(p["bc_band"]), int(p["material"]), float(p["E"]), float(p["nu"]),
+                     float(p["p_mass"]), float(p["p_vol"]), int(max_particles), int(p2g_mode))
+
+
+def mpm_batch_create(scenes):
+    """scenes: sequence of (params dict as for mpm_substep_noalloc, n_particles,
+    WindField). The wind tensors must outlive the handle."""
+    arr = (DwMpmScene * len(scenes))()
+    for i, (params, n, wind) in enumerate(scenes):
+        arr[i] = DwMpmScene(_desc_of(params), int(n), wind.to_c())
+    h = ct.c_void_p()
+    check(lib().mpm_batch_create(arr, len(scenes), ct.byref(h)))
+    return h
+
+
+def mpm_batch_destroy(h):
+    check(lib().mpm_batch_destroy(h))
+
+
+def mpm_batch_layout(h, n_scenes):
+    """(total particle count, [off_0, ..., off_n_scenes])."""
+    n = ct.c_int64()
+    offs = (ct.c_int64 * (n_scenes + 1))()
+    check(lib().mpm_batch_layout(h, ct.byref(n), offs))
+    return n.value, list(offs)
+
+
+def mpm_batch_rollout(h, state: MpmState, pinned, ids, t0, n_substeps, sort_every, stream=None):
+    a = state.to_c()
+    check(lib().mpm_batch_rollout(h, ct.byref(a), _pin(pinned), _dev(ids, torch.int32, "ids"),
+                                  float(t0), int(n_substeps), int(sort_every), _stream(stream)))
+    return state
+
+
+def _config_dict(c: DwBatchConfig):
+    return {"mode": c.mode, "threads": c.threads, "ctas_per_sm": c.ctas_per_sm,
+            "use_graph": c.use_graph, "graph_active": c.graph_active}
+
+
+def mpm_batch_set_config(h, mode, threads, ctas_per_sm, use_graph=1):
+    c = DwBatchConfig(int(mode), int(threads), int(ctas_per_sm), int(use_graph), 0)
+    check(lib().mpm_batch_set_config(h, ct.byref(c)))
+
+
+def mpm_batch_get_config(h):
+    c = DwBatchConfig()
+    check(lib().mpm_batch_get_config(h, ct.byref(c)))
+    return _config_dict(c)
+
+
+def mpm_batch_tune(h, state: MpmState, pinned, n_trial_substeps, max_trials=64, stream=None):
+    """(best configuration, [(configuration, ms per substep), ...])."""
+    a = state.to_c()
+    best = DwBatchConfig()
+    trials = (DwBatchTrial * max_trials)()
+    nt = ct.c_int32()
+    check(lib().mpm_batch_tune(h, ct.byref(a), _pin(pinned), int(n_trial_substeps),
+                               ct.byref(best), trials, int(max_trials), ct.byref(nt),
+                               _stream(stream)))
+    return _config_dict(best), [(_config_dict(trials[i].config), trials[i].ms_per_substep)
+                                for i in range(nt.value)]
+
+
+def mpm_batch_device_status(h, stream=None):
+    check(lib().mpm_batch_device_status(h, _stream(stream)))
+
+
+def mpm_batch_barrier_selftest(h, missing_ctas, stream=None):
+    check(lib().mpm_batch_barrier_selftest(h, int(missing_ctas), _stream(stream)))
+
+
 # --------------------------------------------------------------------- LBM --
 
 def lbm_create(shape, tau, u_inlet=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), bc_x=0, max_tape=2):
@@ -323,6 +404,51 @@ class MPM:
         return mpm_profile_read(self.h)
 
 
+class MPMBatch:
+    """Owns a batch of MPM scenes over one concatenated particle state.
+
+    scenes: sequence of (params dict, n_particles, WindField); scene s owns
+    the particles offsets[s]:offsets[s + 1] of the state."""
+
+    def __init__(self, scenes):
+        self._winds = [w for _, _, w in scenes]  # the handle reads them on every rollout
+        self.n_scenes = len(scenes)
+        self.h = mpm_batch_create(scenes)
+        self.n, self.offsets = mpm_batch_layout(self.h, self.n_scenes)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            mpm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rollout(self, state, pinned, ids, t0, n_substeps, sort_every, stream=None):
+        return mpm_batch_rollout(self.h, state, pinned, ids, t0, n_substeps, sort_every, stream)
+
+    def set_config(self, mode, threads, ctas_per_sm, use_graph=1):
+        mpm_batch_set_config(self.h, mode, threads, ctas_per_sm, use_graph)
+
+    def config(self):
+        return mpm_batch_get_config(self.h)
+
+    def tune(self, state, pinned, n_trial_substeps=10, stream=None):
+        return mpm_batch_tune(self.h, state, pinned, n_trial_substeps, stream=stream)
+
+    def device_status(self, stream=None):
+        mpm_batch_device_status(self.h, stream)
+
+    def barrier_selftest(self, missing_ctas, stream=None):
+        mpm_batch_barrier_selftest(self.h, missing_ctas, stream)
+
+    def scene_slice(self, s):
+        return slice(self.offsets[s], self.offsets[s + 1])
+
+
 class LBM:
     """Owns an LBM handle; the methods call the C-ABI functions above."""
 
@@ -401,8 +527,10 @@ def surr_zero_grads(h, stream=None):
     check(lib().surr_zero_grads(h, _stream(stream)))
 
 
-def surr_features(h, f, solid, stream=None):
-    check(lib().surr_features(h, _dev(f, name="f"), _mask(solid), _stream(stream)))
+def surr_features(h, f, solid, in_scale=1.0, feats32=None, stream=None):
+    check(lib().surr_features(h, _dev(f, name="f"), _mask(solid), float(in_scale),
+                              _dev(feats32, name="feats32"), _stream(stream)))
+    return feats32
 
 
 def surr_set_features(h, feats, stream=None):
@@ -414,9 +542,28 @@ def surr_get_features(h, feats_bf16, stream=None):
     return feats_bf16
 
 
-def surr_forward(h, out=None, stream=None):
-    check(lib().surr_forward(h, _dev(out, name="out"), _stream(stream)))
+def surr_forward(h, out=None, keep_activations=True, stream=None):
+    check(lib().surr_forward(h, _dev(out, name="out"), int(bool(keep_activations)), _stream(stream)))
     return out
+
+
+def surr_features_fine(h, solid, in_scale=1.0, stream=None):
+    check(lib().surr_features_fine(h, _mask(solid), float(in_scale), _stream(stream)))
+
+
+def surr_advance_fine(h, out_scale, solid, stream=None):
+    check(lib().surr_advance_fine(h, float(out_scale), _mask(solid), _stream(stream)))
+
+
+def surr_write_lattice(h, solid, f, stream=None):
+    check(lib().surr_write_lattice(h, _mask(solid), _dev(f, name="f"), _stream(stream)))
+    return f
+
+
+def surr_fine_velocity_error(h, f, solid, sums, stream=None):
+    check(lib().surr_fine_velocity_error(h, _dev(f, name="f"), _mask(solid),
+                                         _dev(sums, torch.float64, "sums"), _stream(stream)))
+    return sums
 
 
 def surr_loss(h, target, loss=None, stream=None):
@@ -436,9 +583,9 @@ def surr_adam(h, lr, beta1, beta2, eps, step, stream=None):
                           _stream(stream)))
 
 
-def surr_apply(h, out, solid, f, stream=None):
-    check(lib().surr_apply(h, _dev(out, name="out"), _mask(solid), _dev(f, name="f"),
-                           _stream(stream)))
+def surr_apply(h, out, solid, f, out_scale=1.0, stream=None):
+    check(lib().surr_apply(h, _dev(out, name="out"), float(out_scale), _mask(solid),
+                           _dev(f, name="f"), _stream(stream)))
     return f
 
 
@@ -480,8 +627,8 @@ class Surrogate:
     def zero_grads(self):
         surr_zero_grads(self.h)
 
-    def features(self, f, solid):
-        surr_features(self.h, f, solid)
+    def features(self, f, solid, in_scale=1.0, feats32=None):
+        return surr_features(self.h, f, solid, in_scale, feats32)
 
     def set_features(self, feats):
         surr_set_features(self.h, feats)
@@ -490,8 +637,20 @@ class Surrogate:
         out = torch.empty((self.n ** 3, 16), dtype=torch.bfloat16, device="cuda")
         return surr_get_features(self.h, out)
 
-    def forward(self, out=None):
-        return surr_forward(self.h, out)
+    def forward(self, out=None, keep_activations=True):
+        return surr_forward(self.h, out, keep_activations)
+
+    def features_fine(self, solid, in_scale=1.0):
+        surr_features_fine(self.h, solid, in_scale)
+
+    def advance_fine(self, out_scale, solid):
+        surr_advance_fine(self.h, out_scale, solid)
+
+    def write_lattice(self, solid, f):
+        return surr_write_lattice(self.h, solid, f)
+
+    def fine_velocity_error(self, f, solid, sums):
+        return surr_fine_velocity_error(self.h, f, solid, sums)
 
     def loss(self, target, loss=None):
         surr_loss(self.h, target, loss)
@@ -505,5 +664,5 @@ class Surrogate:
     def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         surr_adam(self.h, lr, beta1, beta2, eps, step)
 
-    def apply(self, solid, f, out=None):
-        return surr_apply(self.h, out, solid, f)
+    def apply(self, solid, f, out=None, out_scale=1.0):
+        return surr_apply(self.h, out, solid, f, out_scale)

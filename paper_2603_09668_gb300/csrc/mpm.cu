@@ -20,30 +20,6 @@ namespace dw {
 
 // --------------------------------------------------------------- forward --
 
-__device__ __forceinline__ bool sticky_node(const MpmParams &P, int i, int j, int k) {
-    return i < P.band || j < P.band || k < P.band || i > P.N - 1 - P.band ||
-           j > P.N - 1 - P.band || k > P.N - 1 - P.band;
-}
-
-// Grid update of one node: v_i = p_i / m_i + dt (g + a_w(x_i, t)), zero in the
-// sticky band and at empty nodes; (v, m) goes to grid_v.
-__device__ __forceinline__ void grid_node_update(const MpmParams &P, const WindDev &wind, float t,
-                                                 int64_t node, int i, int j, int k,
-                                                 float4 *__restrict__ grid_mp,
-                                                 float4 *__restrict__ grid_v, int clear) {
-    float4 mp = grid_mp[node];
-    float4 out = make_float4(0.f, 0.f, 0.f, mp.x);
-    if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
-        float3 a = wind_sample_dev(wind, i * P.dx, j * P.dx, k * P.dx, t);
-        float inv_m = 1.0f / mp.x;
-        out.x = mp.y * inv_m + P.dt * (P.gx + a.x);
-        out.y = mp.z * inv_m + P.dt * (P.gy + a.y);
-        out.z = mp.w * inv_m + P.dt * (P.gz + a.z);
-    }
-    grid_v[node] = out;
-    if (clear) grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
 // Dense grid update over every node (used without an active-block list).
 __global__ void k_grid_update(MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp,
                               float4 *__restrict__ grid_v, int clear) {
@@ -52,16 +28,6 @@ __global__ void k_grid_update(MpmParams P, WindDev wind, float t, float4 *__rest
     if (node >= nn) return;
     int i = (int)(node % P.N), j = (int)((node / P.N) % P.N), k = (int)(node / ((int64_t)P.N * P.N));
     grid_node_update(P, wind, t, node, i, j, k, grid_mp, grid_v, clear);
-}
-
-// Node (i, j, k) of thread t within active block b; false outside the grid.
-__device__ __forceinline__ bool active_node(const MpmParams &P, int nb, int b, int t, int &i,
-                                            int &j, int &k) {
-    int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
-    i = bx * 4 + (t & 3);
-    j = by * 4 + ((t >> 2) & 3);
-    k = bz * 4 + (t >> 4);
-    return i < P.N && j < P.N && k < P.N;
 }
 
 // Grid update over the active blocks only; with clear, also zeroes (m, p)
@@ -384,20 +350,6 @@ __global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float 
 
 // ------------------------------------------------------------------ sort --
 
-__device__ __forceinline__ int cell_key(const MpmParams &P, int nb, float px, float py, float pz) {
-    float xs[3] = {px * P.inv_dx, py * P.inv_dx, pz * P.inv_dx};
-    int c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float b = floorf(xs[a] - 0.5f);
-        b = fminf(fmaxf(b, 0.0f), (float)(P.N - 1));  // NaN -> 0
-        c[a] = (int)b;
-    }
-    int blk = ((c[2] >> 2) * nb + (c[1] >> 2)) * nb + (c[0] >> 2);
-    int loc = ((c[2] & 3) * 4 + (c[1] & 3)) * 4 + (c[0] & 3);
-    return blk * 64 + loc;
-}
-
 __global__ void k_sort_keys(MpmParams P, int nb, const float *__restrict__ x, int64_t n,
                             int *__restrict__ keys, int *__restrict__ counts) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -409,7 +361,6 @@ __global__ void k_sort_keys(MpmParams P, int nb, const float *__restrict__ x, in
 
 // Exclusive scan, three phases: per-block scan with block totals, scan of the
 // totals (single block, loops over chunks), add-back.
-constexpr int SCAN_BLOCK = 1024;
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &total) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -499,15 +450,15 @@ __global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *
     if (pin_in) pin_out[k] = pin_in[q];
 }
 
-static dw_status device_exclusive_scan(MpmHandle *h, int *data, int64_t len, cudaStream_t st) {
+dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cudaStream_t st) {
     int64_t nblocks = (len + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    if (nblocks > h->scan_tmp_len) {
+    if (nblocks > tmp_len) {
         set_error("scan workspace too small");
         return DW_ERR_ARG;
     }
-    k_scan_blocks<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, h->scan_tmp);
-    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(h->scan_tmp, nblocks);
-    k_scan_add<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, h->scan_tmp);
+    k_scan_blocks<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, tmp);
+    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(tmp, nblocks);
+    k_scan_add<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, tmp);
     DW_LAUNCHED("exclusive scan");
     return DW_OK;
 }
@@ -537,9 +488,9 @@ static dw_status launch_grid_update(MpmHandle *h, const WindDev &wd, float t, in
 using namespace dw;
 
 
-extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
-    DW_REQUIRE(desc && out, "desc/out must not be NULL");
-    *out = nullptr;
+namespace dw {
+
+dw_status validate_desc(const dw_mpm_desc *desc) {
     DW_REQUIRE(desc->n_grid >= 8 && desc->n_grid <= 512, "n_grid=%d out of range [8, 512]", desc->n_grid);
     DW_REQUIRE(desc->dt > 0.0f, "dt must be > 0");
     DW_REQUIRE(desc->bc_band >= 0 && desc->bc_band < desc->n_grid / 2, "bc_band out of range");
@@ -550,6 +501,16 @@ extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
     DW_REQUIRE(desc->max_particles >= 0 && desc->max_particles < (1ll << 31),
                "max_particles out of range");
     DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_TILE, "unknown p2g_mode");
+    return DW_OK;
+}
+
+}  // namespace dw
+
+extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
+    DW_REQUIRE(desc && out, "desc/out must not be NULL");
+    *out = nullptr;
+    dw_status st = validate_desc(desc);
+    if (st != DW_OK) return st;
     dw_mpm h = new (std::nothrow) dw_mpm_s();
     if (!h) {
         set_error("out of host memory");
@@ -755,7 +716,7 @@ dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_stat
     DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
     k_sort_keys<<<grid_for(n, 256), 256, 0, s>>>(h->P, h->nb, in->x, n, h->keys, h->counts);
     DW_LAUNCHED("k_sort_keys");
-    dw_status st = device_exclusive_scan(h, h->counts, h->n_keys, s);
+    dw_status st = exclusive_scan(h->counts, h->n_keys, h->scan_tmp, h->scan_tmp_len, s);
     if (st != DW_OK) return st;
     k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, h->perm);
     DW_LAUNCHED("k_sort_scatter");

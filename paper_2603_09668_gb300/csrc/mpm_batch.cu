@@ -1,0 +1,813 @@
+// mpm_batch: many independent MPM scenes advanced together, each substep one
+// launch over all of them.
+//
+// Every scene runs the substep of mpm_rollout (Eq. simulation_mpm: P2G, grid
+// update with gravity, wind (Sec. 3.3) and the sticky band, G2P with the F
+// update), with its own grid, parameters and wind field. The particles of all
+// scenes live in one concatenated SoA state; a static table splits it into
+// 128-particle work items that never straddle two scenes, and the active 4^3
+// node blocks of all scenes go into one list whose entries carry the scene
+// (scene << 20 | block).
+//
+// Persistent mode: one cooperative launch per substep k. Phase A: the CTAs
+// stride over the active-block list of substep k and update those nodes
+// (reading and clearing (m, p), writing (v, m)). A grid-wide barrier with a
+// bounded wait. Phase B: the CTAs stride over the work items; each particle
+// gathers the new grid velocities (G2P of substep k, loads through L2 because
+// other CTAs wrote them in phase A), updates x and F, and scatters itself into
+// its scene's cleared grid (P2G of substep k + 1), appending newly touched
+// blocks to the other list. The last substep before a sort (and of the
+// rollout) stores v and C instead of scattering. Split mode runs the phases
+// as two kernels with programmatic dependent launch.
+//
+// The sort is one counting sort over all scenes: scene s's keys are offset by
+// the number of keys of the scenes before it, so the sorted order keeps every
+// scene inside its own particle range.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "mpm_handle.cuh"
+
+namespace dw {
+
+constexpr int BATCH_ITEM = 128;         // particles per work item
+constexpr int BATCH_SCENE_SHIFT = 20;   // list entry = scene << 20 | block
+constexpr int BATCH_MAX_SCENES = 2048;  // scene < 2^11 keeps entries positive
+constexpr unsigned BATCH_SPIN_LIMIT = 1u << 20;  // about a second of polling
+
+struct BatchScene {
+    MpmParams P;
+    WindDev wind;
+    float4 *grid_mp;
+    float4 *grid_v;
+    int *flags;      // [nb^3]
+    int nb;
+    int key_offset;  // first sort key of the scene
+};
+
+// Arguments of one launch over the batch.
+struct BatchView {
+    const BatchScene *scenes;
+    const int4 *items;  // (scene, first particle, count, 0)
+    int n_items;
+    float *x, *v, *C, *F;  // concatenated state, stride n
+    const uint8_t *pinned;
+    int64_t n;
+    int *list;   // [2][list_cap]
+    int *count;  // [2]
+    int list_cap;
+    int *err;
+    unsigned *bar;      // grid barrier: arrivals, generation
+    const float *t0;    // time of substep 0 (device, set before each rollout)
+};
+
+__global__ void k_batch_set_time(float *t0, float value) { *t0 = value; }
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident) for
+// `expected` arriving CTAs (gridDim.x). Returns false when the wait gave up
+// (status bit ERRBIT_TIMEOUT set); then every CTA leaves.
+__device__ __forceinline__ bool batch_grid_sync(unsigned *bar, int *err, unsigned expected) {
+    __shared__ int gave_up;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gave_up = 0;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == expected) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            while (*gen == g0) {
+                if (++it > BATCH_SPIN_LIMIT) {
+                    atomicOr(err, ERRBIT_TIMEOUT);
+                    gave_up = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return gave_up == 0;
+}
+
+// Phase A: grid update of the blocks in list L at time t0 + k dt (per scene).
+template <int THREADS>
+__device__ __forceinline__ void batch_grid_phase(const BatchView &A, int k, int L) {
+    constexpr int SUBS = THREADS / 64;
+    const int count = A.count[L];
+    const int *list = A.list + (size_t)L * A.list_cap;
+    const float t0 = *A.t0;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * SUBS + sub; e < count; e += gridDim.x * SUBS) {
+        const int ent = list[e];
+        const BatchScene &S = A.scenes[ent >> BATCH_SCENE_SHIFT];
+        const int b = ent & ((1 << BATCH_SCENE_SHIFT) - 1);
+        const MpmParams P = S.P;
+        int i, j, kk;
+        if (active_node(P, S.nb, b, lt, i, j, kk)) {
+            const int64_t node = ((int64_t)kk * P.N + j) * P.N + i;
+            grid_node_update(P, S.wind, fmaf((float)k, P.dt, t0), node, i, j, kk, S.grid_mp,
+                             S.grid_v, 1);
+        }
+        if (lt == 0) S.flags[b] = 0;
+    }
+}
+
+// Phase B for one work item: G2P of the item's particles; unless FINAL, their
+// P2G into the scene's grid with the blocks appended to list Ln.
+template <bool FINAL, bool CG>
+__device__ __forceinline__ void batch_item(const BatchView &A, const int4 item,
+                                           const BatchScene &S, int slot, int Ln,
+                                           float4 (*rows)[P2G_ROW], int *keys) {
+    const MpmParams &P = S.P;  // read from shared memory where used
+    const int64_t n = A.n;
+    const int64_t p = (int64_t)item.y + slot;
+    P2GParticle q;
+    q.valid = false;
+    if (slot < item.z) {
+        float xp[3], Fp[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xp[a] = A.x[a * n + p];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Fp[c] = A.F[c * n + p];
+        const bool pin = A.pinned && A.pinned[p];
+        float vn[3], Cn[9];
+        g2p_update<CG>(P, S.grid_v, pin, xp, Fp, vn, Cn);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A.x[a * n + p] = xp[a];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) A.F[c * n + p] = Fp[c];
+        if (FINAL) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) A.v[a * n + p] = vn[a];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) A.C[c * n + p] = Cn[c];
+        }
+        const bool fin = isfinite(xp[0]) && isfinite(xp[1]) && isfinite(xp[2]) && finite9(Fp);
+        if (!fin) atomicOr(A.err, ERRBIT_NONFINITE);
+        if (!FINAL) {
+            if (make_stencil(P, xp[0], xp[1], xp[2], q.s)) {
+                if (!p2g_affine(P, Fp, Cn, q.A)) atomicOr(A.err, ERRBIT_INVERTED);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) q.mv[a] = P.p_mass * vn[a];
+                q.valid = true;
+            } else {
+                atomicOr(A.err, ERRBIT_DOMAIN);
+            }
+        }
+    }
+    if (!FINAL) {
+        const ActiveBlocks ab{S.flags, A.list + (size_t)Ln * A.list_cap, A.count + Ln, S.nb,
+                              item.x << BATCH_SCENE_SHIFT};
+        p2g_warp_scatter(P, q, S.grid_mp, ab, rows, keys);
+    }
+}
+
+// Phase B over the work items: each iteration the CTA stages the scene
+// records of its THREADS / 128 items in shared memory (so that the scene
+// parameters are shared-memory operands instead of registers), then every
+// 128-thread group runs one item.
+template <int THREADS, bool FINAL, bool CG>
+__device__ __forceinline__ void batch_items(const BatchView &A, int Ln,
+                                            float4 (*rows)[32][P2G_ROW], int (*keys)[32]) {
+    constexpr int PER = THREADS / BATCH_ITEM;
+    constexpr int WORDS = sizeof(BatchScene) / 4;
+    static_assert(sizeof(BatchScene) % 4 == 0, "scene record is not word-sized");
+    __shared__ BatchScene scene[PER];
+    __shared__ int4 item[PER];
+    const int wid = threadIdx.x >> 5, slot = threadIdx.x % BATCH_ITEM, sub = threadIdx.x / BATCH_ITEM;
+    for (int base = blockIdx.x * PER; base < A.n_items; base += gridDim.x * PER) {
+        __syncthreads();  // the previous items are done with the staged records
+        for (int w = threadIdx.x; w < PER * WORDS; w += THREADS) {
+            const int g = w / WORDS, o = w - g * WORDS;
+            if (base + g < A.n_items) {
+                const int4 it = A.items[base + g];
+                if (o == 0) item[g] = it;
+                reinterpret_cast<int *>(&scene[g])[o] =
+                    reinterpret_cast<const int *>(A.scenes + it.x)[o];
+            }
+        }
+        __syncthreads();
+        if (base + sub < A.n_items)
+            batch_item<FINAL, CG>(A, item[sub], scene[sub], slot, Ln, rows[wid], keys[wid]);
+    }
+}
+
+// One substep of every scene in one cooperative launch.
+template <int THREADS, bool FINAL>
+__global__ void __launch_bounds__(THREADS) k_batch_substep(BatchView A, int k, int L) {
+    __shared__ float4 rows[THREADS / 32][32][P2G_ROW];
+    __shared__ int keys[THREADS / 32][32];
+    // an earlier barrier gave up: do nothing (one read per CTA, shared by all its threads)
+    if (__syncthreads_or(threadIdx.x == 0 && (*(volatile int *)A.err & ERRBIT_TIMEOUT))) return;
+    batch_grid_phase<THREADS>(A, k, L);
+    if (!batch_grid_sync(A.bar, A.err, gridDim.x)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.count[L] = 0;  // list L is consumed
+    batch_items<THREADS, FINAL, true>(A, 1 - L, rows, keys);
+}
+
+// Barrier self-test: `expected` above gridDim.x stands for CTAs that never
+// arrive, so every CTA's wait runs out and the status becomes a timeout.
+__global__ void k_batch_barrier_probe(unsigned *bar, int *err, unsigned expected) {
+    batch_grid_sync(bar, err, expected);
+}
+
+// Split mode: the two phases as separate launches.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_batch_grid(BatchView A, int k, int L) {
+    pdl_wait();
+    pdl_trigger();
+    batch_grid_phase<THREADS>(A, k, L);
+}
+
+template <int THREADS, bool FINAL>
+__global__ void __launch_bounds__(THREADS) k_batch_particles(BatchView A, int L) {
+    __shared__ float4 rows[THREADS / 32][32][P2G_ROW];
+    __shared__ int keys[THREADS / 32][32];
+    pdl_wait();
+    pdl_trigger();
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.count[L] = 0;
+    batch_items<THREADS, FINAL, false>(A, 1 - L, rows, keys);
+}
+
+// P2G of every scene from a complete state (start of a segment), list L.
+__global__ void __launch_bounds__(BATCH_ITEM) k_batch_p2g(BatchView A, int L) {
+    __shared__ float4 rows[BATCH_ITEM / 32][32][P2G_ROW];
+    __shared__ int keys[BATCH_ITEM / 32][32];
+    const int wid = threadIdx.x >> 5;
+    const int4 item = A.items[blockIdx.x];
+    const BatchScene &S = A.scenes[item.x];
+    const MpmParams P = S.P;
+    P2GParticle q;
+    q.valid = false;
+    if ((int)threadIdx.x < item.z)
+        p2g_load(P, A.x, A.v, A.C, A.F, A.n, (int64_t)item.y + threadIdx.x, q, A.err);
+    const ActiveBlocks ab{S.flags, A.list + (size_t)L * A.list_cap, A.count + L, S.nb,
+                          item.x << BATCH_SCENE_SHIFT};
+    p2g_warp_scatter(P, q, S.grid_mp, ab, rows[wid], keys[wid]);
+}
+
+// Sort keys of every scene, offset per scene, counted into counts.
+__global__ void __launch_bounds__(BATCH_ITEM) k_batch_sort_keys(BatchView A, int *__restrict__ keys,
+                                                                int *__restrict__ counts) {
+    const int4 item = A.items[blockIdx.x];
+    if ((int)threadIdx.x >= item.z) return;
+    const BatchScene &S = A.scenes[item.x];
+    const int64_t p = (int64_t)item.y + threadIdx.x, n = A.n;
+    const int key = S.key_offset + cell_key(S.P, S.nb, A.x[p], A.x[n + p], A.x[2 * n + p]);
+    keys[p] = key;
+    atomicAdd(&counts[key], 1);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_coop(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                               cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+struct GraphKey {
+    const void *ptr[6];
+    int n_substeps, sort_every, mode, threads, ctas_per_sm;
+    bool operator==(const GraphKey &o) const {
+        for (int i = 0; i < 6; ++i)
+            if (ptr[i] != o.ptr[i]) return false;
+        return n_substeps == o.n_substeps && sort_every == o.sort_every && mode == o.mode &&
+               threads == o.threads && ctas_per_sm == o.ctas_per_sm;
+    }
+};
+
+}  // namespace dw
+
+struct dw_mpm_batch_s {
+    int n_scenes = 0;
+    std::vector<int64_t> offsets;  // [n_scenes + 1]
+    int64_t n_total = 0;
+    int64_t total_keys = 0;
+    int list_cap = 0;
+    int n_items = 0;
+    int num_sms = 0;
+    int occupancy[2][2] = {{0, 0}, {0, 0}};  // [threads == 256][final]: CTAs per SM
+    dw::BatchScene *scenes = nullptr;  // device table
+    int4 *items = nullptr;
+    float4 *grid_mp = nullptr, *grid_v = nullptr;
+    int *flags = nullptr, *list = nullptr, *count = nullptr, *err = nullptr;
+    unsigned *bar = nullptr;
+    float *t0 = nullptr;
+    int *keys = nullptr, *perm = nullptr, *key_counts = nullptr, *scan_tmp = nullptr;
+    int64_t scan_tmp_len = 0;
+    float *roll_state = nullptr;
+    uint8_t *roll_pinned = nullptr;
+    int32_t *roll_ids = nullptr;
+    dw_batch_config cfg = {};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    dw::GraphKey key = {};
+    bool graph_broken = false;  // capture failed once: launch directly from then on
+};
+
+namespace dw {
+
+static dw_mpm_state state_view(float *base, int64_t n) {
+    dw_mpm_state s;
+    s.x = base;
+    s.v = base + 3 * n;
+    s.C = base + 6 * n;
+    s.F = base + 15 * n;
+    s.n = n;
+    return s;
+}
+
+static BatchView view_of(dw_mpm_batch h, const dw_mpm_state &s, const uint8_t *pinned) {
+    BatchView A;
+    A.scenes = h->scenes;
+    A.items = h->items;
+    A.n_items = h->n_items;
+    A.x = s.x;
+    A.v = s.v;
+    A.C = s.C;
+    A.F = s.F;
+    A.pinned = pinned;
+    A.n = h->n_total;
+    A.list = h->list;
+    A.count = h->count;
+    A.list_cap = h->list_cap;
+    A.err = h->err;
+    A.bar = h->bar;
+    A.t0 = h->t0;
+    return A;
+}
+
+static dw_status batch_sort(dw_mpm_batch h, const dw_mpm_state &in, const dw_mpm_state &out,
+                            const uint8_t *pin_in, uint8_t *pin_out, const int32_t *ids_in,
+                            int32_t *ids_out, cudaStream_t s) {
+    const int64_t n = h->n_total;
+    DW_CUDA(cudaMemsetAsync(h->key_counts, 0, sizeof(int) * (size_t)(h->total_keys + 1), s));
+    k_batch_sort_keys<<<h->n_items, BATCH_ITEM, 0, s>>>(view_of(h, in, pin_in), h->keys,
+                                                        h->key_counts);
+    DW_LAUNCHED("k_batch_sort_keys");
+    dw_status st = exclusive_scan(h->key_counts, h->total_keys, h->scan_tmp, h->scan_tmp_len, s);
+    if (st != DW_OK) return st;
+    k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->key_counts, h->perm);
+    DW_LAUNCHED("k_sort_scatter");
+    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in.x, in.v, in.C, in.F, pin_in, ids_in,
+                                               out.x, out.v, out.C, out.F, pin_out, ids_out);
+    DW_LAUNCHED("k_permute");
+    return DW_OK;
+}
+
+static int occupancy_of(dw_mpm_batch h, int threads, bool final_) {
+    return h->occupancy[threads == 256 ? 1 : 0][final_ ? 1 : 0];
+}
+
+// One substep launch (or two in split mode).
+static dw_status launch_substep(dw_mpm_batch h, const BatchView &A, const dw_batch_config &c,
+                                int k, int L, bool final_, cudaStream_t s) {
+    const int T = c.threads;
+    if (c.mode == DW_BATCH_PERSISTENT) {
+        const int per_sm = std::min(c.ctas_per_sm, occupancy_of(h, T, final_));
+        const unsigned grid = (unsigned)(per_sm * h->num_sms);
+        if (T == 256)
+            DW_CUDA(final_ ? launch_coop(k_batch_substep<256, true>, grid, 256, s, A, k, L)
+                           : launch_coop(k_batch_substep<256, false>, grid, 256, s, A, k, L));
+        else
+            DW_CUDA(final_ ? launch_coop(k_batch_substep<128, true>, grid, 128, s, A, k, L)
+                           : launch_coop(k_batch_substep<128, false>, grid, 128, s, A, k, L));
+        return DW_OK;
+    }
+    const unsigned ggrid = (unsigned)(c.ctas_per_sm * h->num_sms);
+    const int per = T / BATCH_ITEM;
+    const unsigned pgrid = (unsigned)((h->n_items + per - 1) / per);
+    if (T == 256) {
+        DW_CUDA(launch_pdl(k_batch_grid<256>, ggrid, 256, s, A, k, L));
+        DW_CUDA(final_ ? launch_pdl(k_batch_particles<256, true>, pgrid, 256, s, A, L)
+                       : launch_pdl(k_batch_particles<256, false>, pgrid, 256, s, A, L));
+    } else {
+        DW_CUDA(launch_pdl(k_batch_grid<128>, ggrid, 128, s, A, k, L));
+        DW_CUDA(final_ ? launch_pdl(k_batch_particles<128, true>, pgrid, 128, s, A, L)
+                       : launch_pdl(k_batch_particles<128, false>, pgrid, 128, s, A, L));
+    }
+    return DW_OK;
+}
+
+// The launch sequence of a rollout (the time t0 is already on the device).
+static dw_status enqueue_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint8_t *pinned,
+                                 int32_t *ids, int n_substeps, int sort_every,
+                                 const dw_batch_config &c, cudaStream_t s) {
+    const int64_t n = h->n_total;
+    DW_CUDA(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), s));
+    dw_mpm_state cur = *state, oth = state_view(h->roll_state, n);
+    uint8_t *cur_pin = pinned, *oth_pin = pinned ? h->roll_pinned : nullptr;
+    int32_t *cur_ids = ids, *oth_ids = h->roll_ids;
+    const int seg = sort_every > 0 ? sort_every : n_substeps;
+    int L = 0;
+    for (int k0 = 0; k0 < n_substeps; k0 += seg) {
+        const int len = std::min(seg, n_substeps - k0);
+        if (sort_every > 0) {
+            dw_status st = batch_sort(h, cur, oth, cur_pin, oth_pin, cur_ids, oth_ids, s);
+            if (st != DW_OK) return st;
+            std::swap(cur, oth);
+            std::swap(cur_pin, oth_pin);
+            std::swap(cur_ids, oth_ids);
+        }
+        const BatchView A = view_of(h, cur, cur_pin);
+        k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, L);
+        DW_LAUNCHED("k_batch_p2g");
+        for (int j = 0; j < len; ++j) {
+            const bool final_ = j + 1 == len;
+            dw_status st = launch_substep(h, A, c, k0 + j, L, final_, s);
+            if (st != DW_OK) return st;
+            if (!final_) L = 1 - L;
+        }
+    }
+    if (cur.x != state->x) {  // an odd number of sorts: the result is in the workspace
+        const size_t b3 = sizeof(float) * 3 * (size_t)n, b9 = sizeof(float) * 9 * (size_t)n;
+        DW_CUDA(cudaMemcpyAsync(state->x, cur.x, b3, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(state->v, cur.v, b3, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(state->C, cur.C, b9, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(state->F, cur.F, b9, cudaMemcpyDeviceToDevice, s));
+        if (pinned)
+            DW_CUDA(cudaMemcpyAsync(pinned, cur_pin, (size_t)n, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(ids, cur_ids, sizeof(int32_t) * (size_t)n,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    return DW_OK;
+}
+
+static void drop_graph(dw_mpm_batch h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    h->exec = nullptr;
+}
+
+// Captures the launch sequence into h->exec; false (and no error left behind)
+// when this rollout cannot be captured.
+static bool capture_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint8_t *pinned,
+                            int32_t *ids, int n_substeps, int sort_every) {
+    drop_graph(h);
+    if (!h->cap_stream &&
+        cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    dw_status st = enqueue_rollout(h, state, pinned, ids, n_substeps, sort_every, h->cfg,
+                                   h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    bool ok = st == DW_OK && e == cudaSuccess && graph;
+    if (ok) ok = cudaGraphInstantiate(&h->exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (!ok) h->exec = nullptr;
+    return ok;
+}
+
+static dw_status check_batch_state(dw_mpm_batch h, const dw_mpm_state *s) {
+    DW_REQUIRE(s, "state is NULL");
+    DW_REQUIRE(s->n == h->n_total, "state has n=%lld particles; the batch has %lld",
+               (long long)s->n, (long long)h->n_total);
+    DW_REQUIRE(s->x && s->v && s->C && s->F, "state arrays must not be NULL");
+    return DW_OK;
+}
+
+static dw_status check_config(dw_mpm_batch h, const dw_batch_config *c) {
+    DW_REQUIRE(c, "config is NULL");
+    DW_REQUIRE(c->mode == DW_BATCH_PERSISTENT || c->mode == DW_BATCH_SPLIT, "unknown mode %d",
+               c->mode);
+    DW_REQUIRE(c->threads == 128 || c->threads == 256, "threads must be 128 or 256");
+    DW_REQUIRE(c->ctas_per_sm >= 1 && c->ctas_per_sm <= 64, "ctas_per_sm out of range [1, 64]");
+    if (c->mode == DW_BATCH_PERSISTENT)
+        DW_REQUIRE(occupancy_of(h, c->threads, false) >= 1 && occupancy_of(h, c->threads, true) >= 1,
+                   "the persistent kernel with %d threads cannot be resident", c->threads);
+    return DW_OK;
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scenes,
+                                      dw_mpm_batch *out) {
+    DW_REQUIRE(out, "out must not be NULL");
+    *out = nullptr;
+    DW_REQUIRE(scenes, "scenes must not be NULL");
+    DW_REQUIRE(n_scenes >= 1 && n_scenes <= BATCH_MAX_SCENES, "n_scenes=%d out of range [1, %d]",
+               n_scenes, BATCH_MAX_SCENES);
+    std::vector<BatchScene> tab(n_scenes);
+    std::vector<int64_t> offsets(n_scenes + 1, 0);
+    std::vector<int64_t> node_off(n_scenes + 1, 0), blk_off(n_scenes + 1, 0);
+    int64_t total_keys = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+        const dw_mpm_scene &sc = scenes[s];
+        dw_mpm_desc d = sc.desc;
+        d.max_particles = 0;
+        d.p2g_mode = DW_P2G_AUTO;
+        dw_status st = validate_desc(&d);
+        if (st != DW_OK) return st;
+        DW_REQUIRE(d.n_grid <= 400, "scene %d: n_grid=%d above the batch limit 400", s, d.n_grid);
+        DW_REQUIRE(sc.n_particles >= 1, "scene %d has no particles", s);
+        st = wind_check(&sc.wind, &tab[s].wind);
+        if (st != DW_OK) return st;
+        tab[s].P = params_of(d);
+        const int nb = (d.n_grid + 3) / 4;
+        tab[s].nb = nb;
+        tab[s].key_offset = (int)total_keys;
+        total_keys += (int64_t)nb * nb * nb * 64;
+        offsets[s + 1] = offsets[s] + sc.n_particles;
+        node_off[s + 1] = node_off[s] + (int64_t)d.n_grid * d.n_grid * d.n_grid;
+        blk_off[s + 1] = blk_off[s] + (int64_t)nb * nb * nb;
+        DW_REQUIRE(total_keys < (1ll << 31), "the scenes' grids are too large for one batch");
+        DW_REQUIRE(offsets[s + 1] < (1ll << 31), "more than 2^31 - 1 particles in the batch");
+    }
+    std::vector<int4> items;
+    for (int s = 0; s < n_scenes; ++s)
+        for (int64_t b = offsets[s]; b < offsets[s + 1]; b += BATCH_ITEM)
+            items.push_back(make_int4(s, (int)b, (int)std::min<int64_t>(BATCH_ITEM, offsets[s + 1] - b), 0));
+    DW_REQUIRE(items.size() < (1u << 31), "too many work items");
+
+    dw_mpm_batch h = new (std::nothrow) dw_mpm_batch_s();
+    if (!h) {
+        set_error("out of host memory");
+        return DW_ERR_OOM;
+    }
+    h->n_scenes = n_scenes;
+    h->offsets = offsets;
+    h->n_total = offsets[n_scenes];
+    h->total_keys = total_keys;
+    h->list_cap = (int)blk_off[n_scenes];
+    h->n_items = (int)items.size();
+    h->scan_tmp_len = (total_keys + SCAN_BLOCK) / SCAN_BLOCK + 1;
+    const int64_t n = h->n_total;
+    cudaError_t e = cudaSuccess;
+#define DW_ALLOC(ptr, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
+    DW_ALLOC(h->scenes, sizeof(BatchScene) * (size_t)n_scenes);
+    DW_ALLOC(h->items, sizeof(int4) * items.size());
+    DW_ALLOC(h->grid_mp, sizeof(float4) * (size_t)node_off[n_scenes]);
+    DW_ALLOC(h->grid_v, sizeof(float4) * (size_t)node_off[n_scenes]);
+    DW_ALLOC(h->flags, sizeof(int) * (size_t)blk_off[n_scenes]);
+    DW_ALLOC(h->list, sizeof(int) * 2 * (size_t)blk_off[n_scenes]);
+    DW_ALLOC(h->count, sizeof(int) * 2);
+    DW_ALLOC(h->err, sizeof(int));
+    DW_ALLOC(h->bar, sizeof(unsigned) * 2);
+    DW_ALLOC(h->t0, sizeof(float));
+    DW_ALLOC(h->keys, sizeof(int) * (size_t)n);
+    DW_ALLOC(h->perm, sizeof(int) * (size_t)n);
+    DW_ALLOC(h->key_counts, sizeof(int) * (size_t)(total_keys + 1));
+    DW_ALLOC(h->scan_tmp, sizeof(int) * (size_t)h->scan_tmp_len);
+    DW_ALLOC(h->roll_state, sizeof(float) * 24 * (size_t)n);
+    DW_ALLOC(h->roll_pinned, (size_t)n);
+    DW_ALLOC(h->roll_ids, sizeof(int32_t) * (size_t)n);
+#undef DW_ALLOC
+    if (e == cudaSuccess) {
+        for (int s = 0; s < n_scenes; ++s) {
+            tab[s].grid_mp = h->grid_mp + node_off[s];
+            tab[s].grid_v = h->grid_v + node_off[s];
+            tab[s].flags = h->flags + blk_off[s];
+        }
+        e = cudaMemcpy(h->scenes, tab.data(), sizeof(BatchScene) * tab.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->grid_mp, 0, sizeof(float4) * (size_t)node_off[n_scenes]);
+    if (e == cudaSuccess) e = cudaMemset(h->flags, 0, sizeof(int) * (size_t)blk_off[n_scenes]);
+    if (e == cudaSuccess) e = cudaMemset(h->count, 0, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->bar, 0, sizeof(unsigned) * 2);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy[0][0], k_batch_substep<128, false>, 128, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy[0][1], k_batch_substep<128, true>, 128, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy[1][0], k_batch_substep<256, false>, 256, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->occupancy[1][1], k_batch_substep<256, true>, 256, 0);
+    if (e != cudaSuccess) {
+        mpm_batch_destroy(h);
+        return e == cudaErrorMemoryAllocation ? (set_error("out of device memory"), DW_ERR_OOM)
+                                              : cuda_fail(e, "mpm_batch_create");
+    }
+    h->cfg.mode = DW_BATCH_PERSISTENT;
+    h->cfg.threads = 128;
+    h->cfg.ctas_per_sm = std::max(1, std::min(h->occupancy[0][0], h->occupancy[0][1]));
+    h->cfg.use_graph = 1;
+    h->cfg.graph_active = 0;
+    *out = h;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_batch_destroy(dw_mpm_batch h) {
+    if (!h) return DW_OK;
+    drop_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->scenes);
+    cudaFree(h->items);
+    cudaFree(h->grid_mp);
+    cudaFree(h->grid_v);
+    cudaFree(h->flags);
+    cudaFree(h->list);
+    cudaFree(h->count);
+    cudaFree(h->err);
+    cudaFree(h->bar);
+    cudaFree(h->t0);
+    cudaFree(h->keys);
+    cudaFree(h->perm);
+    cudaFree(h->key_counts);
+    cudaFree(h->scan_tmp);
+    cudaFree(h->roll_state);
+    cudaFree(h->roll_pinned);
+    cudaFree(h->roll_ids);
+    delete h;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_batch_layout(dw_mpm_batch h, int64_t *n_total, int64_t *offsets) {
+    DW_REQUIRE(h, "handle is NULL");
+    if (n_total) *n_total = h->n_total;
+    if (offsets)
+        for (int s = 0; s <= h->n_scenes; ++s) offsets[s] = h->offsets[s];
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_batch_set_config(dw_mpm_batch h, const dw_batch_config *config) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_config(h, config);
+    if (st != DW_OK) return st;
+    h->cfg = *config;
+    h->cfg.graph_active = 0;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_batch_get_config(dw_mpm_batch h, dw_batch_config *config) {
+    DW_REQUIRE(h && config, "handle and config must not be NULL");
+    *config = h->cfg;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_batch_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint8_t *pinned,
+                                       int32_t *ids, float t0, int32_t n_substeps,
+                                       int32_t sort_every, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_batch_state(h, state);
+    if (st != DW_OK) return st;
+    DW_REQUIRE(n_substeps >= 0, "n_substeps must be >= 0");
+    DW_REQUIRE(sort_every >= 0, "sort_every must be >= 0");
+    DW_REQUIRE(sort_every == 0 || ids, "ids must be given when sort_every > 0");
+    if (n_substeps == 0) return DW_OK;
+    cudaStream_t s = as_stream(stream);
+    k_batch_set_time<<<1, 1, 0, s>>>(h->t0, t0);
+    DW_LAUNCHED("k_batch_set_time");
+    if (h->cfg.use_graph && !h->graph_broken) {
+        GraphKey key = {{state->x, state->v, state->C, state->F, pinned, ids}, n_substeps,
+                        sort_every, h->cfg.mode, h->cfg.threads, h->cfg.ctas_per_sm};
+        if (!h->exec || !(key == h->key)) {
+            if (capture_rollout(h, state, pinned, ids, n_substeps, sort_every))
+                h->key = key;
+            else
+                h->graph_broken = true;
+        }
+        if (h->exec) {
+            DW_CUDA(cudaGraphLaunch(h->exec, s));
+            h->cfg.graph_active = 1;
+            return DW_OK;
+        }
+    }
+    h->cfg.graph_active = 0;
+    return enqueue_rollout(h, state, pinned, ids, n_substeps, sort_every, h->cfg, s);
+}
+
+extern "C" dw_status mpm_batch_device_status(dw_mpm_batch h, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    int bits = 0;
+    cudaStream_t s = as_stream(stream);
+    DW_CUDA(cudaMemcpyAsync(&bits, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DW_CUDA(cudaStreamSynchronize(s));
+    DW_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    DW_CUDA(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), s));
+    DW_CUDA(cudaStreamSynchronize(s));
+    return status_from_bits(bits);
+}
+
+extern "C" dw_status mpm_batch_barrier_selftest(dw_mpm_batch h, int32_t missing_ctas,
+                                                dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(missing_ctas >= 0 && missing_ctas <= 1024, "missing_ctas out of range [0, 1024]");
+    cudaStream_t s = as_stream(stream);
+    DW_CUDA(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), s));
+    const unsigned grid = (unsigned)h->num_sms;
+    DW_CUDA(launch_coop(k_batch_barrier_probe, grid, 128, s, h->bar, h->err,
+                        grid + (unsigned)missing_ctas));
+    return mpm_batch_device_status(h, stream);
+}
+
+extern "C" dw_status mpm_batch_tune(dw_mpm_batch h, const dw_mpm_state *state,
+                                    const uint8_t *pinned, int32_t n_trial_substeps,
+                                    dw_batch_config *best, dw_batch_trial *trials,
+                                    int32_t max_trials, int32_t *n_trials, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_batch_state(h, state);
+    if (st != DW_OK) return st;
+    DW_REQUIRE(n_trial_substeps >= 1, "n_trial_substeps must be >= 1");
+    DW_REQUIRE(max_trials >= 0, "max_trials must be >= 0");
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = h->n_total;
+    // candidates
+    std::vector<dw_batch_config> cand;
+    for (int T : {128, 256}) {
+        const int occ = std::min(occupancy_of(h, T, false), occupancy_of(h, T, true));
+        for (int c = 1; c <= occ; ++c)
+            cand.push_back(dw_batch_config{DW_BATCH_PERSISTENT, T, c, 0, 0});
+        for (int c : {2, 4})
+            cand.push_back(dw_batch_config{DW_BATCH_SPLIT, T, c, 0, 0});
+    }
+    // the trials run on a copy of the state in the workspace
+    const dw_mpm_state work = state_view(h->roll_state, n);
+    uint8_t *work_pin = pinned ? h->roll_pinned : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DW_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    dw_status result = DW_OK;
+    float best_ms = 0.0f;
+    int best_i = -1, recorded = 0;
+    k_batch_set_time<<<1, 1, 0, s>>>(h->t0, 0.0f);
+    DW_LAUNCHED("k_batch_set_time");
+    for (size_t i = 0; i < cand.size() && result == DW_OK; ++i) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && result == DW_OK; ++rep) {
+            cudaError_t e = cudaMemcpyAsync(work.x, state->x, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(work.v, state->v, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(work.C, state->C, sizeof(float) * 9 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(work.F, state->F, sizeof(float) * 9 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess && pinned) e = cudaMemcpyAsync(work_pin, pinned, (size_t)n, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            if (e != cudaSuccess) {
+                result = cuda_fail(e, "mpm_batch_tune");
+                break;
+            }
+            result = enqueue_rollout(h, &work, work_pin, nullptr, n_trial_substeps, 0, cand[i], s);
+            if (result != DW_OK) break;
+            e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) {
+                result = cuda_fail(e, "mpm_batch_tune");
+                break;
+            }
+            ms = rep == 0 ? t : std::min(ms, t);
+        }
+        if (result != DW_OK) break;
+        int bits = 0;
+        if (cudaMemcpy(&bits, h->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            result = cuda_fail(cudaGetLastError(), "mpm_batch_tune");
+            break;
+        }
+        if (bits) {  // a trial failed on the device: report it, keep the old configuration
+            result = mpm_batch_device_status(h, stream);
+            break;
+        }
+        const float per = ms / (float)n_trial_substeps;
+        if (trials && recorded < max_trials) trials[recorded++] = dw_batch_trial{cand[i], per};
+        if (best_i < 0 || per < best_ms) {
+            best_i = (int)i;
+            best_ms = per;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_trials) *n_trials = recorded;
+    if (result != DW_OK) return result;
+    const int use_graph = h->cfg.use_graph;
+    h->cfg = cand[best_i];
+    h->cfg.use_graph = use_graph;
+    h->cfg.graph_active = 0;
+    if (best) *best = h->cfg;
+    return DW_OK;
+}

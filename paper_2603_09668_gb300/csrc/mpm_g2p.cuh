@@ -7,8 +7,17 @@
 
 namespace dw {
 
+// Grid velocity load: through L2 only (CG) where the grid was written by
+// another CTA earlier in the same kernel, a plain load otherwise.
+template <bool CG>
+__device__ __forceinline__ float4 load_grid(const float4 *p) {
+    if (CG) return __ldcg(p);
+    return *p;
+}
+
 // Updates x and F in place and returns v and C. Returns false, leaving x and
 // F unchanged and v = C = 0, when the stencil leaves the grid.
+template <bool CG = false>
 __device__ __forceinline__ bool g2p_update(const MpmParams &P, const float4 *__restrict__ grid_v,
                                            bool pinned, float x[3], float F[9], float vn[3],
                                            float Cn[9]) {
@@ -35,7 +44,8 @@ __device__ __forceinline__ bool g2p_update(const MpmParams &P, const float4 *__r
         for (int oj = 0; oj < 3; ++oj) {
             const float wyz = s.w[1][oj] * s.w[2][ok];
             const int64_t row = base + ((int64_t)ok * N + oj) * N;
-            const float4 g0 = grid_v[row], g1 = grid_v[row + 1], g2 = grid_v[row + 2];
+            const float4 g0 = load_grid<CG>(grid_v + row), g1 = load_grid<CG>(grid_v + row + 1),
+                         g2 = load_grid<CG>(grid_v + row + 2);
             const float a[3] = {wx0 * g0.x + wx1 * g1.x + wx2 * g2.x,
                                 wx0 * g0.y + wx1 * g1.y + wx2 * g2.y,
                                 wx0 * g0.z + wx1 * g1.z + wx2 * g2.z};

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "mpm_g2p.cuh"
+#include "mpm_grid.cuh"
 #include "mpm_math.cuh"
 #include "mpm_p2g.cuh"
 #include "wind.cuh"
@@ -71,9 +72,8 @@ inline void profile_free(MpmHandle *h) {
     h->prof_used = 0;
 }
 
-inline void fill_params(MpmHandle *h) {
-    const dw_mpm_desc &d = h->desc;
-    MpmParams &P = h->P;
+inline MpmParams params_of(const dw_mpm_desc &d) {
+    MpmParams P;
     P.N = d.n_grid;
     P.dx = 1.0f / (float)d.n_grid;
     P.inv_dx = (float)d.n_grid;
@@ -91,14 +91,17 @@ inline void fill_params(MpmHandle *h) {
     P.p_mass = d.p_mass;
     P.p_vol = d.p_vol;
     P.kappa = d.dt * d.p_vol * P.D;
+    return P;
 }
+
+inline void fill_params(MpmHandle *h) { h->P = params_of(h->desc); }
 
 constexpr int GRID_THREADS = 256;  // four 4^3 blocks per CTA iteration
 constexpr int GRID_CTAS = 4 * 152;
 
 inline ActiveBlocks active_blocks(MpmHandle *h, int which = 0) {
     return ActiveBlocks{h->block_flag, h->block_list + (size_t)which * h->nblk,
-                        h->block_count + which, h->nb};
+                        h->block_count + which, h->nb, 0};
 }
 
 // kernels of mpm.cu launched from other units
@@ -110,7 +113,22 @@ __global__ void k_g2p(MpmParams P, const float *x, const float *F,
                       float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err,
                       int *reset_count);
 
+// particle sort (mpm.cu): counting sort by cell key, keys already counted
+constexpr int SCAN_BLOCK = 1024;
+__global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
+                               int *__restrict__ perm);
+__global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *__restrict__ x,
+                          const float *__restrict__ v, const float *__restrict__ C,
+                          const float *__restrict__ F, const uint8_t *__restrict__ pin_in,
+                          const int *__restrict__ ids_in, float *__restrict__ xo,
+                          float *__restrict__ vo, float *__restrict__ Co, float *__restrict__ Fo,
+                          uint8_t *__restrict__ pin_out, int *__restrict__ ids_out);
+// In-place exclusive prefix sum of data[0, len); tmp holds at least
+// len / SCAN_BLOCK + 1 ints.
+dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cudaStream_t st);
+
 // host helpers of mpm.cu
+dw_status validate_desc(const dw_mpm_desc *desc);
 dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *name);
 dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_state *out,
                          const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,

@@ -26,6 +26,7 @@ struct ActiveBlocks {
     int *list;   // [nb^3]
     int *count;  // [1], zero between substeps
     int nb;      // blocks per axis
+    int tag;     // or-ed into every list entry (the scene of a batched list)
 };
 
 __device__ __forceinline__ void mark_stencil_blocks(const ActiveBlocks &ab, const int base[3]) {
@@ -40,7 +41,7 @@ __device__ __forceinline__ void mark_stencil_blocks(const ActiveBlocks &ab, cons
             for (int bx = lo[0]; bx <= hi[0]; ++bx) {
                 int id = (bz * ab.nb + by) * ab.nb + bx;
                 if (*(volatile int *)&ab.flags[id] == 0 && atomicExch(&ab.flags[id], 1) == 0)
-                    ab.list[atomicAdd(ab.count, 1)] = id;
+                    ab.list[atomicAdd(ab.count, 1)] = ab.tag | id;
             }
 }
 

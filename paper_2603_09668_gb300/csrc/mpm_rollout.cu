@@ -10,6 +10,8 @@
 // (96 B per particle) instead of the four arrays of the unfused kernels.
 // Every `sort_every` substeps the particles are re-sorted by cell; the state
 // is complete (x, v, C, F written) at those boundaries and at the end.
+#include <math.h>
+
 #include "mpm_handle.cuh"
 
 namespace dw {
@@ -126,7 +128,7 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
         }
         if (st != DW_OK) return st;
         for (int j = 0; j < len; ++j) {
-            const float t = t0 + (float)(k0 + j) * h->P.dt;
+            const float t = fmaf((float)(k0 + j), h->P.dt, t0);  // as the batched kernels
             {
                 ProfScope ps(h, DW_K_GRID, s);
                 DW_CUDA(launch_pdl(k_grid_update_active, GRID_CTAS, GRID_THREADS, s, h->P, wd, t,

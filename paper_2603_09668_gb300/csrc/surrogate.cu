@@ -83,7 +83,8 @@ __global__ void k_surr_fine(const float *__restrict__ f, const uint8_t *__restri
 
 // Coarse features: 2x2x2 averages over fluid cells of (rho - 1, u), solid fraction.
 __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__restrict__ solid,
-                              int n, bf16 *__restrict__ feats) {
+                              int n, float in_scale, bf16 *__restrict__ feats,
+                              float *__restrict__ feats32) {
     const int64_t nv = (int64_t)n * n * n;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
@@ -102,7 +103,7 @@ __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__r
         s[2] += fine[2 * nc + c];
         s[3] += fine[3 * nc + c];
     }
-    const float inv = fluid > 0 ? 1.0f / (float)fluid : 0.0f;
+    const float inv = fluid > 0 ? in_scale / (float)fluid : 0.0f;
     __align__(16) bf16 o[16];
 #pragma unroll
     for (int ch = 0; ch < 16; ++ch) o[ch] = __float2bfloat16_rn(0.0f);
@@ -112,6 +113,13 @@ __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__r
     uint4 *dst = reinterpret_cast<uint4 *>(feats + v * 16);
     dst[0] = reinterpret_cast<const uint4 *>(o)[0];
     dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+    if (feats32) {
+        float4 *d32 = reinterpret_cast<float4 *>(feats32 + v * 16);
+        d32[0] = make_float4(s[0] * inv, s[1] * inv, s[2] * inv, s[3] * inv);
+        d32[1] = make_float4((8 - fluid) * 0.125f, 0.f, 0.f, 0.f);
+        d32[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d32[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 __global__ void k_f32_to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, int64_t cnt) {
@@ -189,8 +197,9 @@ __global__ void k_surr_adam(float *__restrict__ p, float *__restrict__ g, float 
 
 // f = f_eq(rho, u + du up-sampled) on fluid cells of the (2n)^3 lattice
 // (shifted populations), du trilinear from the cell-centred coarse grid.
-__global__ void k_surr_apply(const float *__restrict__ out, const float *__restrict__ fine,
-                             const uint8_t *__restrict__ solid, int n, float *__restrict__ f) {
+__global__ void k_surr_apply(const float *__restrict__ out, float out_scale,
+                             const float *__restrict__ fine, const uint8_t *__restrict__ solid,
+                             int n, float *__restrict__ f) {
     const int N = 2 * n;
     const int64_t nc = (int64_t)N * N * N;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,6 +225,9 @@ __global__ void k_surr_apply(const float *__restrict__ out, const float *__restr
         d[1] += w * o[1];
         d[2] += w * o[2];
     }
+    d[0] *= out_scale;
+    d[1] *= out_scale;
+    d[2] *= out_scale;
     const float rho = fine[c];
     const float ux = fine[nc + c] + d[0], uy = fine[2 * nc + c] + d[1], uz = fine[3 * nc + c] + d[2];
     const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
@@ -224,6 +236,91 @@ __global__ void k_surr_apply(const float *__restrict__ out, const float *__restr
         const float cu = (float)kCX[i] * ux + (float)kCY[i] * uy + (float)kCZ[i] * uz;
         const float w = i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
         f[(size_t)i * nc + c] = w * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - uu));
+    }
+}
+
+// Fine velocity update of the chained mode: u += out_scale * du upsampled
+// (same interpolation as k_surr_apply), rho kept; nothing written to a lattice.
+__global__ void k_surr_advance_fine(const float *__restrict__ out, float out_scale,
+                                    float *__restrict__ fine, const uint8_t *__restrict__ solid,
+                                    int n) {
+    const int N = 2 * n;
+    const int64_t nc = (int64_t)N * N * N;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    if (solid && solid[c]) return;
+    const int fi[3] = {(int)(c % N), (int)((c / N) % N), (int)(c / ((int64_t)N * N))};
+    int i0[3];
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float s = fminf(fmaxf(fi[a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
+        int i = min((int)floorf(s), n - 2);
+        i0[a] = i;
+        t[a] = s - (float)i;
+    }
+    float d[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int cx = k & 1, cy = (k >> 1) & 1, cz = k >> 2;
+        const float w = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+        const float *o = out + ((((int64_t)(i0[2] + cz)) * n + (i0[1] + cy)) * n + (i0[0] + cx)) * 16;
+        d[0] += w * o[0];
+        d[1] += w * o[1];
+        d[2] += w * o[2];
+    }
+    fine[nc + c] += out_scale * d[0];
+    fine[2 * nc + c] += out_scale * d[1];
+    fine[3 * nc + c] += out_scale * d[2];
+}
+
+// f = f_eq(rho, u) of the fine state on fluid cells (shifted populations).
+__global__ void k_surr_write_lattice(const float *__restrict__ fine, const uint8_t *__restrict__ solid,
+                                     int64_t nc, float *__restrict__ f) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    if (solid && solid[c]) return;
+    const float rho = fine[c], ux = fine[nc + c], uy = fine[2 * nc + c], uz = fine[3 * nc + c];
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const float cu = (float)kCX[i] * ux + (float)kCY[i] * uy + (float)kCZ[i] * uz;
+        const float w = i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+        f[(size_t)i * nc + c] = w * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - uu));
+    }
+}
+
+// sums over fluid cells of |u_fine - u(f)|^2 and |u(f)|^2
+__global__ void k_fine_vel_err(const float *__restrict__ fine, const float *__restrict__ f,
+                               const uint8_t *__restrict__ solid, int64_t nc, double *__restrict__ out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, r = 0.0;
+    if (c < nc && !(solid && solid[c])) {
+        float u[3] = {0.f, 0.f, 0.f}, rb = 1.0f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const float b = f[(size_t)i * nc + c];
+            rb += b;
+            u[0] += kCX[i] * b;
+            u[1] += kCY[i] * b;
+            u[2] += kCZ[i] * b;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double ub = u[k] / rb;
+            const double d = fine[(k + 1) * nc + c] - ub;
+            e += d * d;
+            r += ub * ub;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, e);
+        atomicAdd(out + 1, r);
     }
 }
 
@@ -441,13 +538,14 @@ extern "C" dw_status surr_zero_grads(dw_surr h, dw_stream stream) {
 }
 
 extern "C" dw_status surr_features(dw_surr h, const float *f, const uint8_t *solid,
-                                   dw_stream stream) {
+                                   float in_scale, float *feats32, dw_stream stream) {
     DW_REQUIRE(h && f, "handle and f must not be NULL");
     cudaStream_t s = as_stream(stream);
     const int N = 2 * h->n;
     const int64_t nc = (int64_t)N * N * N;
     k_surr_fine<<<grid_for(nc, 256), 256, 0, s>>>(f, solid, N, h->fine);
-    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, s>>>(h->fine, solid, h->n, h->feats);
+    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, s>>>(h->fine, solid, h->n, in_scale, h->feats,
+                                                       feats32);
     DW_LAUNCHED("surr_features");
     return DW_OK;
 }
@@ -466,17 +564,27 @@ extern "C" dw_status surr_get_features(dw_surr h, void *feats_bf16, dw_stream st
     return DW_OK;
 }
 
-extern "C" dw_status surr_forward(dw_surr h, float *out, dw_stream stream) {
+extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activations,
+                                  dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
     cudaStream_t s = as_stream(stream);
     dw_status st;
     const float *P = h->params;
-    st = conv<16, 32, EPI_GELU>(h, h->feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s);
-    if (st != DW_OK) return st;
-    st = conv<32, 32, EPI_GELU>(h, h->a[0], h->wf + h->woff[1], P + h->off_b[1], h->z[1], h->a[1], nullptr, nullptr, s);
-    if (st != DW_OK) return st;
-    st = conv<32, 32, EPI_GELU>(h, h->a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
-    if (st != DW_OK) return st;
+    if (keep_activations) {
+        st = conv<16, 32, EPI_GELU>(h, h->feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s);
+        if (st != DW_OK) return st;
+        st = conv<32, 32, EPI_GELU>(h, h->a[0], h->wf + h->woff[1], P + h->off_b[1], h->z[1], h->a[1], nullptr, nullptr, s);
+        if (st != DW_OK) return st;
+        st = conv<32, 32, EPI_GELU>(h, h->a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
+        if (st != DW_OK) return st;
+    } else {
+        st = conv<16, 32, EPI_GELU_ONLY>(h, h->feats, h->wf + h->woff[0], P + h->off_b[0], nullptr, h->a[0], nullptr, nullptr, s);
+        if (st != DW_OK) return st;
+        st = conv<32, 32, EPI_GELU_ONLY>(h, h->a[0], h->wf + h->woff[1], P + h->off_b[1], nullptr, h->a[1], nullptr, nullptr, s);
+        if (st != DW_OK) return st;
+        st = conv<32, 32, EPI_GELU_ONLY>(h, h->a[1], h->wf + h->woff[2], P + h->off_b[2], nullptr, h->a[2], nullptr, nullptr, s);
+        if (st != DW_OK) return st;
+    }
     st = conv<32, 16, EPI_F32>(h, h->a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s);
     if (st != DW_OK) return st;
     if (out)
@@ -536,13 +644,13 @@ extern "C" dw_status surr_adam(dw_surr h, float lr, float beta1, float beta2, fl
     return refresh_weights(h, s);
 }
 
-extern "C" dw_status surr_apply(dw_surr h, const float *out, const uint8_t *solid, float *f,
-                                dw_stream stream) {
+extern "C" dw_status surr_apply(dw_surr h, const float *out, float out_scale,
+                                const uint8_t *solid, float *f, dw_stream stream) {
     DW_REQUIRE(h && f, "handle and f must not be NULL");
     const int N = 2 * h->n;
     const int64_t nc = (int64_t)N * N * N;
-    k_surr_apply<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(out ? out : h->out, h->fine, solid,
-                                                                   h->n, f);
+    k_surr_apply<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(out ? out : h->out, out_scale,
+                                                                   h->fine, solid, h->n, f);
     DW_LAUNCHED("k_surr_apply");
     return DW_OK;
 }
@@ -553,5 +661,44 @@ extern "C" dw_status lbm_velocity_error(const float *fa, const float *fb, const 
     DW_REQUIRE(ncell > 0, "ncell must be > 0");
     k_vel_err<<<grid_for(ncell, 256), 256, 0, as_stream(stream)>>>(fa, fb, solid, ncell, sums);
     DW_LAUNCHED("k_vel_err");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float in_scale,
+                                        dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, as_stream(stream)>>>(h->fine, solid, h->n, in_scale,
+                                                                       h->feats, nullptr);
+    DW_LAUNCHED("k_surr_coarse");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *solid,
+                                       dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    const int N = 2 * h->n;
+    const int64_t nc = (int64_t)N * N * N;
+    k_surr_advance_fine<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(h->out, out_scale, h->fine,
+                                                                          solid, h->n);
+    DW_LAUNCHED("k_surr_advance_fine");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_write_lattice(dw_surr h, const uint8_t *solid, float *f, dw_stream stream) {
+    DW_REQUIRE(h && f, "handle and f must not be NULL");
+    const int N = 2 * h->n;
+    const int64_t nc = (int64_t)N * N * N;
+    k_surr_write_lattice<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(h->fine, solid, nc, f);
+    DW_LAUNCHED("k_surr_write_lattice");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_fine_velocity_error(dw_surr h, const float *f, const uint8_t *solid,
+                                              double *sums, dw_stream stream) {
+    DW_REQUIRE(h && f && sums, "arguments must not be NULL");
+    const int N = 2 * h->n;
+    const int64_t nc = (int64_t)N * N * N;
+    k_fine_vel_err<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(h->fine, f, solid, nc, sums);
+    DW_LAUNCHED("k_fine_vel_err");
     return DW_OK;
 }

@@ -31,7 +31,7 @@ constexpr int CV_HX = CV_TX + 2, CV_HY = CV_TY + 2, CV_HZ = 3;
 constexpr int CV_HALO = CV_HX * CV_HY * CV_HZ;  // 540 voxels
 constexpr int CV_THREADS = 256;
 
-enum { EPI_GELU = 0, EPI_F32 = 1, EPI_DGELU = 2 };
+enum { EPI_GELU = 0, EPI_F32 = 1, EPI_DGELU = 2, EPI_GELU_ONLY = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(CV_THREADS, 2) k_conv3(
             for (int h = 0; h < 2; ++h) {
                 const size_t v = vrow + gid + 8 * h;
                 float z0v = acc[j][2 * h], z1v = acc[j][2 * h + 1];
-                if (EPI == EPI_GELU) {
+                if (EPI == EPI_GELU || EPI == EPI_GELU_ONLY) {
                     z0v += bias[co];
                     z1v += bias[co + 1];
-                    *reinterpret_cast<__nv_bfloat162 *>(out_z + v * COUT + co) = __floats2bfloat162_rn(z0v, z1v);
+                    if (EPI == EPI_GELU)
+                        *reinterpret_cast<__nv_bfloat162 *>(out_z + v * COUT + co) = __floats2bfloat162_rn(z0v, z1v);
                     *reinterpret_cast<__nv_bfloat162 *>(out_a + v * COUT + co) =
                         __floats2bfloat162_rn(gelu_f(z0v), gelu_f(z1v));
                 } else if (EPI == EPI_F32) {

@@ -1,0 +1,225 @@
+"""Surrogate-accelerated LBM wind constraint.
+
+The plain D3Q19 LBM (lbm_step) advances the wind velocity field one lattice
+step at a time. The surrogate advances it by a block of `block` steps in one
+network call. The call reads the coarse features of the current lattice,
+runs the network, upsamples the predicted change of the coarse velocity,
+adds it to the fine velocity and re-initialises the populations at
+equilibrium. Training data come from the library's own LBM runs on lattices
+with random leaf-cluster obstacles and random inlet directions.
+
+`SurrogateLBM.advance` re-checks the surrogate against the plain LBM every
+`check_every` blocks: it runs both from the same state and compares the
+fluid velocities; the run continues from the plain result. If the relative
+L2 error exceeds `tol` (2%), the surrogate is switched off from then on.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import inputs
+
+U_REF = 0.05        # inlet speed (lattice units)
+IN_SCALE = 1.0 / U_REF
+OUT_SCALE = 1e-3    # network outputs du / OUT_SCALE
+BLOCK = 20          # lattice steps per surrogate call
+WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
+
+
+def inlet_direction(rng, cone_deg=30.0):
+    """Unit vector uniformly distributed in a cone of half-angle cone_deg about +x."""
+    cos_max = math.cos(math.radians(cone_deg))
+    c = rng.uniform(cos_max, 1.0)
+    phi = rng.uniform(0.0, 2.0 * math.pi)
+    s = math.sqrt(max(0.0, 1.0 - c * c))
+    return np.array([c, s * math.cos(phi), s * math.sin(phi)])
+
+
+def leaf_mask(N, seed, device="cuda"):
+    """Solid mask of the leaf cluster (50 ellipsoids, 200k particles) on N^3."""
+    pts = torch.from_numpy(inputs.ellipsoid_cluster(seed=seed)).to(device)
+    solid = torch.empty((N, N, N), dtype=torch.uint8, device=device)
+    B.voxelize_particles(pts, (N, N, N), 1.0 / N, solid)
+    return solid
+
+
+def generate_pairs(N, n_rollouts, t_lo, t_hi, seed=0, block=BLOCK, tau=0.55, device="cuda",
+                   keep_states=False):
+    """Training pairs from the plain LBM: per rollout a random obstacle and inlet
+    direction, a run from rest to a random time in [t_lo, t_hi), the coarse
+    features there (input) and the change of the coarse velocity over the next
+    `block` steps divided by OUT_SCALE (target, channels 0..2)."""
+    n = N // 2
+    rng = np.random.default_rng(seed)
+    surr = B.Surrogate(n)
+    xs, ys, states = [], [], []
+    fa = torch.empty((n ** 3, 16), dtype=torch.float32, device=device)
+    fb = torch.empty_like(fa)
+    for r in range(n_rollouts):
+        solid = leaf_mask(N, seed * 100003 + r, device)
+        d = inlet_direction(rng)
+        lbm = B.LBM((N, N, N), tau, u_inlet=tuple(U_REF * d), bc_x=1, max_tape=1)
+        f = lbm.lattice(device)
+        t0 = int(rng.integers(t_lo, t_hi)) // 2 * 2
+        lbm.step(f, solid, t0)
+        surr.features(f, solid, IN_SCALE, fa)
+        if keep_states:
+            states.append((f.clone(), solid, tuple(U_REF * d)))
+        lbm.step(f, solid, block)
+        surr.features(f, solid, IN_SCALE, fb)
+        y = torch.zeros_like(fa)
+        y[:, :3] = (fb[:, 1:4] - fa[:, 1:4]) / IN_SCALE / OUT_SCALE
+        xs.append(fa.clone())
+        ys.append(y)
+        lbm.close()
+    surr.close()
+    if keep_states:
+        return xs, ys, states
+    return xs, ys
+
+
+def init_params(nparams_slices, seed=0, device="cuda"):
+    """He-style initial weights, zero biases, in the library's packing."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    total = nparams_slices[-1][1].stop
+    p = torch.zeros(total, dtype=torch.float32)
+    for ws, bs, cin, cout in nparams_slices:
+        p[ws] = torch.randn(ws.stop - ws.start, generator=g) * math.sqrt(2.0 / (27 * cin))
+    return p.to(device)
+
+
+def layer_slices():
+    ch = (16, 32, 32, 32, 16)
+    out, o = [], 0
+    for l in range(4):
+        nw = 27 * ch[l] * ch[l + 1]
+        out.append((slice(o, o + nw), slice(o + nw, o + nw + ch[l + 1]), ch[l], ch[l + 1]))
+        o += nw + ch[l + 1]
+    return out
+
+
+def train(surr: B.Surrogate, xs, ys, steps, lr=1e-3, seed=0, log_every=0):
+    """Adam over random training pairs; returns the loss of each step."""
+    rng = np.random.default_rng(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for step in range(1, steps + 1):
+        i = int(rng.integers(len(xs)))
+        cur_lr = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps))  # cosine decay
+        loss.zero_()
+        surr.set_features(xs[i])
+        surr.forward()
+        surr.loss(ys[i], loss)
+        surr.backward()
+        surr.adam(cur_lr, step)
+        if log_every and step % log_every == 0:
+            hist.append((step, loss.item()))
+    return hist
+
+
+def weights_path(N):
+    return os.path.join(WEIGHTS_DIR, f"surrogate_lbm{N}.npy")
+
+
+def load_weights(surr: B.Surrogate, N, device="cuda"):
+    p = torch.from_numpy(np.load(weights_path(N)).astype(np.float32)).to(device)
+    surr.set_params(p)
+
+
+class SurrogateLBM:
+    """Plain LBM plus the surrogate for blocks of BLOCK steps, with the check.
+
+    Between surrogate calls the state is the fine (rho, u) field kept in the
+    surrogate handle (chained mode); the lattice is re-initialised from it,
+    f = f_eq(rho, u), only when the plain LBM takes over or at the end."""
+
+    def __init__(self, N, tau=0.55, u_inlet=(U_REF, 0.0, 0.0), check_every=10, tol=0.02,
+                 params=None, device="cuda"):
+        self.N = N
+        self.lbm = B.LBM((N, N, N), tau, u_inlet=u_inlet, bc_x=1, max_tape=1)
+        self.surr = B.Surrogate(N // 2)
+        if params is None:
+            load_weights(self.surr, N, device)
+        else:
+            self.surr.set_params(params)
+        self.check_every, self.tol = check_every, tol
+        self.calls = 0
+        self.fallback = False
+        self.errors = []
+        self._sums = torch.zeros(2, dtype=torch.float64, device=device)
+        self._shadow = None
+
+    # one block from a lattice (reads f, writes f)
+    def surrogate_block(self, f, solid):
+        """Advance f by BLOCK lattice steps with one network call (in place)."""
+        self.surr.features(f, solid, IN_SCALE)
+        self.surr.forward(keep_activations=False)
+        self.surr.apply(solid, f, None, OUT_SCALE)
+        return f
+
+    # one block of the chained mode (fine state in, fine state out)
+    def chained_block(self, solid):
+        self.surr.features_fine(solid, IN_SCALE)
+        self.surr.forward(keep_activations=False)
+        self.surr.advance_fine(OUT_SCALE, solid)
+
+    def plain_block(self, f, solid):
+        return self.lbm.step(f, solid, BLOCK)
+
+    def velocity_error(self, f, g, solid):
+        self._sums.zero_()
+        B.lbm_velocity_error(f, g, solid, self._sums)
+        e, r = self._sums.tolist()
+        return math.sqrt(e / max(r, 1e-300))
+
+    def fine_error(self, g, solid):
+        self._sums.zero_()
+        self.surr.fine_velocity_error(g, solid, self._sums)
+        e, r = self._sums.tolist()
+        return math.sqrt(e / max(r, 1e-300))
+
+    def advance(self, f, solid, n_blocks):
+        """n_blocks blocks of BLOCK steps on lattice f (in place); returns the
+        number of blocks the surrogate ran."""
+        used = 0
+        in_fine = False  # the current state is the handle's fine field, not f
+        for _ in range(n_blocks):
+            if self.fallback:
+                self.plain_block(f, solid)
+                continue
+            if not in_fine:
+                self.surr.features(f, solid, IN_SCALE)  # fine state from the lattice
+                in_fine = True
+            if self.calls % self.check_every == 0:
+                # check block: both runs from the same state; the run goes on
+                # from the plain result, which also re-anchors the chained
+                # state on the LBM trajectory
+                if self._shadow is None:
+                    self._shadow = torch.empty_like(f)
+                self.surr.write_lattice(solid, f)
+                self._shadow.copy_(f)
+                self.plain_block(self._shadow, solid)
+                self.chained_block(solid)
+                err = self.fine_error(self._shadow, solid)
+                self.errors.append(err)
+                f.copy_(self._shadow)
+                in_fine = False
+                if err > self.tol:
+                    self.fallback = True
+                    continue
+            else:
+                self.chained_block(solid)
+            self.calls += 1
+            used += 1
+        if in_fine:
+            self.surr.write_lattice(solid, f)
+        return used
+
+    def close(self):
+        self.lbm.close()
+        self.surr.close()

@@ -1,0 +1,231 @@
+"""GPU tests of the batched MPM (many scenes, one launch per substep) through
+the C-ABI.
+
+Parity: every scene of a batch must match the same scene run alone through
+mpm_rollout (same substeps, same re-sorting), particle by particle after the
+carried ids undo both sorts. Both runs sum the P2G contributions with float
+atomics in an unspecified order, so they agree to float32 rounding, not
+bitwise: positions within 1e-6 (absolute, of the unit domain), F within
+1e-6, v and C within 1e-4 of their largest magnitude. One small scene of the
+batch is also checked against the FP64 oracle (positions within 1e-4).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_09668_gb300 import binding as B
+from paper_2603_09668_gb300 import inputs
+
+from gpu_util import f64, max_rel, state_to_np, to_dev, wind_dev, wind_ref
+
+pytestmark = pytest.mark.gpu
+
+DT = 5e-5
+
+
+def small_scenes():
+    """Uneven scenes: grids 32^3 / 64^3, blocks (fixed-corotated) and sheets
+    (Neo-Hookean, pinned edge), 1 to ~13k particles (ragged last work item,
+    a one-particle scene), each with its own wind."""
+    out = []
+    specs = [("block", 32, 8, 2), ("sheet", 64, 110, 60), ("block", 64, 5, 1),
+             ("one", 32, 0, 0), ("sheet", 32, 40, 30), ("block", 32, 12, 3)]
+    for s, (kind, N, a, b) in enumerate(specs):
+        if kind == "block":
+            x = inputs.block_particles(sub=a, per_sub=b, seed=s)
+            pinned = np.zeros(x.shape[1], np.uint8)
+            mat, E, vol = 1, 1e4, 0.25 ** 3 / x.shape[1]
+        elif kind == "sheet":
+            x, pinned = inputs.sheet_particles(a, b, seed=s)
+            h = 0.6 / (a - 1)
+            mat, E, vol = 0, 5e4, 0.6 * 0.4 * 2 * h / x.shape[1]
+        else:
+            x = np.array([[0.5], [0.45], [0.52]], np.float32)
+            pinned = np.zeros(1, np.uint8)
+            mat, E, vol = 0, 1e4, 1e-6
+        st = inputs.perturbed_state(x, v_scale=0.1, c_scale=1.0, f_scale=0.01, seed=10 + s)
+        params = dict(n_grid=N, dt=DT, gravity=(0.0, -9.8, 0.0), bc_band=3, material=mat, E=E,
+                      nu=0.3, p_mass=1000.0 * vol, p_vol=vol)
+        wind = inputs.fourier_wind(16, 8, seed=100 + s)
+        out.append((params, st, pinned, wind))
+    return out
+
+
+def concat(scenes):
+    st = tuple(np.ascontiguousarray(np.concatenate([sc[1][i] for sc in scenes], axis=1))
+               for i in range(4))
+    pin = np.concatenate([sc[2] for sc in scenes])
+    return st, pin
+
+
+def make_batch(scenes, t_total):
+    winds = [wind_dev(sc[3], t_total) for sc in scenes]
+    return B.MPMBatch([(sc[0], sc[1][0].shape[1], w) for sc, w in zip(scenes, winds)])
+
+
+def dev_state(st):
+    return B.MpmState(*(to_dev(np.asarray(a, np.float32)) for a in st))
+
+
+def run_batch(scenes, n_sub, sort_every, config=None):
+    st, pin = concat(scenes)
+    batch = make_batch(scenes, n_sub * DT)
+    if config is not None:
+        batch.set_config(*config)
+    s = dev_state(st)
+    p = to_dev(pin)
+    ids = torch.arange(batch.n, dtype=torch.int32, device="cuda")
+    batch.rollout(s, p, ids, 0.0, n_sub, sort_every)
+    batch.device_status()
+    cfg = batch.config()
+    return batch, state_to_np(s), p.cpu().numpy(), ids.cpu().numpy(), cfg
+
+
+def unsort(arrs, idx):
+    """Arrays in sorted order -> original order, given the carried ids."""
+    out = []
+    for a in arrs:
+        b = np.empty_like(a)
+        b[..., idx] = a
+        out.append(b)
+    return out
+
+
+def assert_close(g, r, label):
+    dx = np.abs(g[0] - r[0]).max()
+    dF = np.abs(g[3] - r[3]).max()
+    assert dx <= 1e-6, (label, "x", dx)
+    assert dF <= 1e-6, (label, "F", dF)
+    assert max_rel(g[1], r[1]) <= 1e-4, (label, "v", max_rel(g[1], r[1]))
+    assert max_rel(g[2], r[2]) <= 1e-4, (label, "C", max_rel(g[2], r[2]))
+
+
+@pytest.mark.parametrize("sort_every", [0, 7])
+def test_each_scene_matches_the_scene_run_alone(sort_every):
+    scenes = small_scenes()
+    n_sub = 24
+    batch, g, gpin, gids, cfg = run_batch(scenes, n_sub, sort_every)
+    assert cfg["mode"] == B.BATCH_PERSISTENT
+    for s, (params, st, pinned, wind) in enumerate(scenes):
+        sl = batch.scene_slice(s)
+        n = st[0].shape[1]
+        local = gids[sl] - batch.offsets[s]
+        assert np.array_equal(np.sort(local), np.arange(n)), s  # a permutation within the scene
+        assert np.array_equal(gpin[sl], pinned[local])
+        mine = unsort([a[:, sl] for a in g], local)
+        mpm = B.MPM.from_params(params, max_particles=n)
+        a = dev_state(st)
+        ids = torch.arange(n, dtype=torch.int32, device="cuda")
+        mpm.rollout(a, to_dev(pinned), ids, wind_dev(wind, n_sub * DT), 0.0, n_sub, sort_every)
+        mpm.device_status()
+        alone = unsort(list(state_to_np(a)), ids.cpu().numpy())
+        assert_close(mine, alone, f"scene {s}")
+        mpm.close()
+    batch.close()
+
+
+def test_batch_scene_matches_oracle():
+    scenes = small_scenes()
+    n_sub = 20
+    batch, g, _, gids, _ = run_batch(scenes, n_sub, 10)
+    s = 0
+    params, st, pinned, wind = scenes[s]
+    sl = batch.scene_slice(s)
+    mine = unsort([a[:, sl] for a in g], gids[sl] - batch.offsets[s])
+    ref = oracle.mpm_rollout(params, f64(st), wind_ref(wind, n_sub * DT), 0.0, n_sub, pinned)
+    assert np.abs(mine[0] - ref[0]).max() <= 1e-4
+    assert np.abs(mine[3] - ref[3]).max() <= 1e-4
+    batch.close()
+
+
+@pytest.mark.parametrize("config", [(B.BATCH_PERSISTENT, 256, 1, 1), (B.BATCH_PERSISTENT, 128, 2, 0),
+                                    (B.BATCH_SPLIT, 128, 4, 1), (B.BATCH_SPLIT, 256, 2, 0)])
+def test_launch_shapes_agree(config):
+    scenes = small_scenes()
+    n_sub = 16
+    b0, g0, _, ids0, _ = run_batch(scenes, n_sub, 5)
+    b1, g1, _, ids1, cfg = run_batch(scenes, n_sub, 5, config)
+    assert cfg["mode"] == config[0] and cfg["threads"] == config[1]
+    assert_close(unsort(list(g1), ids1), unsort(list(g0), ids0), str(config))
+    b0.close()
+    b1.close()
+
+
+def test_graph_replay_repeats_and_time_advances():
+    """A graph is captured once per rollout shape: two rollouts of 8 substeps
+    from t0 = 0 and t0 = 8 dt equal one eager rollout of 16 (wind varies in
+    time, so a stale t0 would show)."""
+    scenes = small_scenes()
+    st, pin = concat(scenes)
+    batch = make_batch(scenes, 16 * DT)
+    s = dev_state(st)
+    p = to_dev(pin)
+    batch.rollout(s, p, None, 0.0, 8, 0)
+    batch.rollout(s, p, None, 8 * DT, 8, 0)
+    batch.device_status()
+    assert batch.config()["graph_active"] == 1
+    eager = make_batch(scenes, 16 * DT)
+    eager.set_config(B.BATCH_PERSISTENT, 128, 1, use_graph=0)
+    e = dev_state(st)
+    eager.rollout(e, to_dev(pin), None, 0.0, 16, 0)
+    eager.device_status()
+    assert eager.config()["graph_active"] == 0
+    assert_close(list(state_to_np(s)), list(state_to_np(e)), "graph vs eager")
+    batch.close()
+    eager.close()
+
+
+def test_autotuner_picks_a_measured_candidate_and_leaves_state():
+    scenes = small_scenes()
+    st, pin = concat(scenes)
+    batch = make_batch(scenes, 10 * DT)
+    s = dev_state(st)
+    p = to_dev(pin)
+    before = [a.clone() for a in s]
+    best, trials = batch.tune(s, p, n_trial_substeps=5)
+    assert len(trials) >= 4
+    assert {t[0]["mode"] for t in trials} == {B.BATCH_PERSISTENT, B.BATCH_SPLIT}
+    fastest = min(trials, key=lambda t: t[1])
+    assert {k: best[k] for k in ("mode", "threads", "ctas_per_sm")} == \
+        {k: fastest[0][k] for k in ("mode", "threads", "ctas_per_sm")}
+    assert all(t[1] > 0 for t in trials)
+    for a, b in zip(s, before):
+        assert torch.equal(a, b)
+    cfg = batch.config()
+    assert cfg["mode"] == best["mode"] and cfg["threads"] == best["threads"]
+    batch.rollout(s, p, None, 0.0, 4, 0)  # the tuned configuration runs
+    batch.device_status()
+    batch.close()
+
+
+def test_barrier_wait_is_bounded_and_reports_timeout():
+    """The grid barrier told to wait for CTAs that were never launched gives
+    up after its bounded wait and reports DW_ERR_TIMEOUT; the batch works
+    afterwards."""
+    scenes = small_scenes()[:2]
+    batch = make_batch(scenes, 4 * DT)
+    batch.barrier_selftest(0)
+    with pytest.raises(B.DiffWindError) as ei:
+        batch.barrier_selftest(1)
+    assert ei.value.status == 6  # DW_ERR_TIMEOUT
+    st, pin = concat(scenes)
+    s = dev_state(st)
+    batch.rollout(s, to_dev(pin), None, 0.0, 4, 0)
+    batch.device_status()
+    assert np.isfinite(state_to_np(s)[0]).all()
+    batch.close()
+
+
+def test_domain_error_is_reported_per_batch():
+    scenes = small_scenes()[:3]
+    scenes[1][1][0][:, 0] = (0.999, 0.5, 0.5)  # a particle outside the stencil range
+    st, pin = concat(scenes)
+    batch = make_batch(scenes, 2 * DT)
+    s = dev_state(st)
+    batch.rollout(s, to_dev(pin), None, 0.0, 2, 0)
+    with pytest.raises(B.DiffWindError) as ei:
+        batch.device_status()
+    assert ei.value.status == 5  # DW_ERR_DOMAIN
+    batch.device_status()  # cleared
+    batch.close()
