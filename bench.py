@@ -436,20 +436,28 @@ def bench_surrogate(dev, N=128, t_eval=1500, blocks=25):
     ms_plain = _timed(lambda: m.plain_block(f, solid), reps=5)
     m.surr.features(f0, solid, S.IN_SCALE)
     ms_surr = _timed(lambda: m.chained_block(solid), reps=5)
-    # longer run with checks against the plain LBM
+    # a run of `blocks` blocks with a plain-LBM check every 10 (the run goes on
+    # from the plain lattice after a check), timed against `blocks` plain blocks
     f_plain = f0.clone()
-    m.lbm.step(f_plain, solid, 20 * blocks)
+    ms_plain_run = _timed(lambda: (f_plain.copy_(f0), m.lbm.step(f_plain, solid, 20 * blocks)), reps=1)
     f_sur = f0.clone()
-    m.calls = 0
-    m.errors = []
-    used = m.advance(f_sur, solid, blocks)
+    runs = []
+
+    def run():
+        f_sur.copy_(f0)
+        m.calls, m.errors, m.fallback = 0, [], False
+        runs.append(m.advance(f_sur, solid, blocks))
+
+    ms_run = _timed(run, reps=1)
     err_run = m.velocity_error(f_sur, f_plain, solid)
     m.close()
     return {"surr_block_err": err_net, "persistence_err": err_persist,
             "surr_block_ms": ms_surr, "plain_block_ms": ms_plain,
             "surr_speedup": ms_plain / ms_surr, "surr_run_blocks": blocks,
-            "surr_run_used": used, "surr_run_check_errors": m.errors,
-            "surr_run_final_err": err_run}
+            "surr_run_used": runs[-1], "surr_run_check_errors": m.errors,
+            "surr_run_fallback": m.fallback, "surr_run_ms": ms_run,
+            "plain_run_ms": ms_plain_run, "surr_run_speedup": ms_plain_run / ms_run,
+            "surr_run_final_err_vs_plain_trajectory": err_run}
 
 
 def bench_batch(dev, n_scenes=64, n_sub=500, sort_every=25, trial=10):

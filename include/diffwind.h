@@ -431,6 +431,10 @@ DW_API dw_status surr_get_features(dw_surr h, void *feats_bf16, dw_stream stream
  * needs (training), otherwise stores only the layer outputs (inference);
  * copies the FP32 output [n^3][16] to out when out is not NULL. */
 DW_API dw_status surr_forward(dw_surr h, float *out, int32_t keep_activations, dw_stream stream);
+/* Waits for `stream`, returns the first device-side error of the handle's
+ * kernels since the last call (DW_ERR_TIMEOUT if a bounded wait inside a
+ * convolution gave up; DW_OK if none) and clears it. */
+DW_API dw_status surr_device_status(dw_surr h, dw_stream stream);
 /* Mean squared error of output channels 0..2 against target [n^3][16] over the
  * coarse voxels that are not fully solid; adds the loss to *loss (device
  * float, may be NULL) and sets dL/d(output) for surr_backward. */
@@ -452,14 +456,17 @@ DW_API dw_status surr_apply(dw_surr h, const float *out, float out_scale, const 
                             float *f, dw_stream stream);
 /* Chained mode: the handle's fine (rho, u) state stands in for the lattice
  * between surrogate calls. surr_features_fine takes the coarse features from
- * it, surr_advance_fine adds out_scale times the upsampled output to its u,
- * surr_write_lattice re-initialises f = f_eq(rho, u) on the fluid cells, and
+ * it; surr_advance_fine adds out_scale times the upsampled output to its u
+ * and then takes the coarse features of the updated state (scaled by
+ * in_scale, exactly as surr_features_fine would), so that chained calls
+ * alternate surr_forward and surr_advance_fine; surr_write_lattice
+ * re-initialises f = f_eq(rho, u) on the fluid cells, and
  * surr_fine_velocity_error adds sum |u_fine - u(f)|^2 and sum |u(f)|^2 over
  * the fluid cells to sums (device double[2]). */
 DW_API dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float in_scale,
                                     dw_stream stream);
 DW_API dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *solid,
-                                   dw_stream stream);
+                                   float in_scale, dw_stream stream);
 DW_API dw_status surr_write_lattice(dw_surr h, const uint8_t *solid, float *f, dw_stream stream);
 DW_API dw_status surr_fine_velocity_error(dw_surr h, const float *f, const uint8_t *solid,
                                           double *sums, dw_stream stream);

@@ -100,11 +100,12 @@ SIGNATURES = {
     "surr_get_grads": (I32, [VP, VP, VP]),
     "surr_zero_grads": (I32, [VP, VP]),
     "surr_features": (I32, [VP, VP, VP, F32, VP, VP]),
+    "surr_device_status": (I32, [VP, VP]),
     "surr_set_features": (I32, [VP, VP, VP]),
     "surr_get_features": (I32, [VP, VP, VP]),
     "surr_forward": (I32, [VP, VP, I32, VP]),
     "surr_features_fine": (I32, [VP, VP, F32, VP]),
-    "surr_advance_fine": (I32, [VP, F32, VP, VP]),
+    "surr_advance_fine": (I32, [VP, F32, VP, F32, VP]),
     "surr_write_lattice": (I32, [VP, VP, VP, VP]),
     "surr_fine_velocity_error": (I32, [VP, VP, VP, VP, VP]),
     "surr_loss": (I32, [VP, VP, VP, VP]),

@@ -26,7 +26,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
-           "surr_backward", "surr_adam", "surr_apply", "lbm_velocity_error", "Surrogate",
+           "surr_backward", "surr_device_status", "surr_adam", "surr_apply", "lbm_velocity_error", "Surrogate",
            "surr_features_fine", "surr_advance_fine", "surr_write_lattice",
            "surr_fine_velocity_error", "mpm_batch_create", "mpm_batch_destroy",
            "mpm_batch_layout", "mpm_batch_rollout", "mpm_batch_set_config",
@@ -551,8 +551,9 @@ def surr_features_fine(h, solid, in_scale=1.0, stream=None):
     check(lib().surr_features_fine(h, _mask(solid), float(in_scale), _stream(stream)))
 
 
-def surr_advance_fine(h, out_scale, solid, stream=None):
-    check(lib().surr_advance_fine(h, float(out_scale), _mask(solid), _stream(stream)))
+def surr_advance_fine(h, out_scale, solid, in_scale=1.0, stream=None):
+    check(lib().surr_advance_fine(h, float(out_scale), _mask(solid), float(in_scale),
+                                  _stream(stream)))
 
 
 def surr_write_lattice(h, solid, f, stream=None):
@@ -576,6 +577,10 @@ def surr_set_output_grad(h, g_out, stream=None):
 
 def surr_backward(h, stream=None):
     check(lib().surr_backward(h, _stream(stream)))
+
+
+def surr_device_status(h, stream=None):
+    check(lib().surr_device_status(h, _stream(stream)))
 
 
 def surr_adam(h, lr, beta1, beta2, eps, step, stream=None):
@@ -643,8 +648,8 @@ class Surrogate:
     def features_fine(self, solid, in_scale=1.0):
         surr_features_fine(self.h, solid, in_scale)
 
-    def advance_fine(self, out_scale, solid):
-        surr_advance_fine(self.h, out_scale, solid)
+    def advance_fine(self, out_scale, solid, in_scale=1.0):
+        surr_advance_fine(self.h, out_scale, solid, in_scale)
 
     def write_lattice(self, solid, f):
         return surr_write_lattice(self.h, solid, f)
@@ -660,6 +665,9 @@ class Surrogate:
 
     def backward(self):
         surr_backward(self.h)
+
+    def device_status(self):
+        surr_device_status(self.h)
 
     def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         surr_adam(self.h, lr, beta1, beta2, eps, step)

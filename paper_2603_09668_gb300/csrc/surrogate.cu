@@ -6,9 +6,11 @@
 // tensor-core convolutions with FP32 accumulation (surrogate_conv.cuh), FP32
 // master weights and Adam. The paper has no learned component; Sec. 3.4 uses
 // the LBM velocity field as the guide that this network stands in for.
+#include <cudaTypedefs.h>
+
 #include <new>
 
-#include "surrogate_conv.cuh"
+#include "surrogate_tc.cuh"
 
 namespace dw {
 
@@ -20,8 +22,8 @@ struct SurrHandle {
     int64_t nparams = 0;
     int64_t off_w[4] = {0, 0, 0, 0}, off_b[4] = {0, 0, 0, 0};
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *wf = nullptr;  // forward weights, per layer [27][cout][cin]
-    bf16 *wd = nullptr;  // input-gradient weights, per layer [27][cin][cout], taps mirrored
+    bf16 *wf = nullptr;  // forward weights, per layer [27][cin/8][cout][8]
+    bf16 *wd = nullptr;  // input-gradient weights, per layer [27][cout/8][cin][8], taps mirrored
     int64_t woff[4] = {0, 0, 0, 0};
     bf16 *feats = nullptr;          // [nv][16]
     bf16 *z[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};  // [nv][32]
@@ -32,11 +34,19 @@ struct SurrHandle {
     int nchunks = 0, tiles_per_chunk = 0;
     float *fine = nullptr;          // [4][(2n)^3]: rho, ux, uy, uz of the last surr_features
     double *red = nullptr;          // reduction scratch
+    int *err = nullptr;             // device status bits (bounded waits of the conv kernels)
     int conv_ctas = 0;
+    int sms = 0;
+    // TMA descriptors of the conv inputs: features, a1..a3, dL/d(out), dL/dz1..dz3
+    CUtensorMap tm_feats, tm_a[3], tm_g4, tm_gz[3];
 };
 
 // ------------------------------------------------------------- kernels ----
 
+// BF16 copies of the layer weights in the tensor-core operand layout
+// [tap][cin/8][cout][8] (core matrices of 8 output channels x 8 input
+// channels): wf for the forward convolution, wd for the input gradient (taps
+// mirrored, input and output channels swapped: [tap'][cout/8][cin][8]).
 __global__ void k_surr_weights(const float *__restrict__ params, bf16 *__restrict__ wf,
                                bf16 *__restrict__ wd, int64_t off_w, int64_t woff, int cin,
                                int cout) {
@@ -45,8 +55,8 @@ __global__ void k_surr_weights(const float *__restrict__ params, bf16 *__restric
     if (i >= cnt) return;
     const int ci = (int)(i % cin), co = (int)((i / cin) % cout), t = (int)(i / ((int64_t)cin * cout));
     const bf16 w = __float2bfloat16_rn(params[off_w + i]);
-    wf[woff + i] = w;
-    wd[woff + ((int64_t)(26 - t) * cin + ci) * cout + co] = w;
+    wf[woff + (((int64_t)t * (cin / 8) + ci / 8) * cout + co) * 8 + (ci & 7)] = w;
+    wd[woff + (((int64_t)(26 - t) * (cout / 8) + co / 8) * cin + ci) * 8 + (co & 7)] = w;
 }
 
 __device__ __constant__ int kCX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0};
@@ -110,9 +120,8 @@ __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__r
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * inv);
     o[4] = __float2bfloat16_rn((8 - fluid) * 0.125f);
-    uint4 *dst = reinterpret_cast<uint4 *>(feats + v * 16);
-    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
-    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+    reinterpret_cast<uint4 *>(feats)[v] = reinterpret_cast<const uint4 *>(o)[0];       // channels 0-7
+    reinterpret_cast<uint4 *>(feats)[nv + v] = reinterpret_cast<const uint4 *>(o)[1];  // channels 8-15
     if (feats32) {
         float4 *d32 = reinterpret_cast<float4 *>(feats32 + v * 16);
         d32[0] = make_float4(s[0] * inv, s[1] * inv, s[2] * inv, s[3] * inv);
@@ -122,9 +131,27 @@ __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__r
     }
 }
 
-__global__ void k_f32_to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, int64_t cnt) {
+// Channels-last FP32 [nv][16] -> planar BF16 [2][nv][8] (the layout of the
+// network's activations: 8-channel planes, see surrogate_tc.cuh).
+__global__ void k_cl16_to_planar(const float *__restrict__ src, bf16 *__restrict__ dst, int64_t nv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (chunk, voxel)
+    if (i >= 2 * nv) return;
+    const int64_t c = i / nv, v = i - c * nv;
+    const float4 a = *reinterpret_cast<const float4 *>(src + v * 16 + c * 8);
+    const float4 b = *reinterpret_cast<const float4 *>(src + v * 16 + c * 8 + 4);
+    __align__(16) bf16 o[8] = {__float2bfloat16_rn(a.x), __float2bfloat16_rn(a.y),
+                               __float2bfloat16_rn(a.z), __float2bfloat16_rn(a.w),
+                               __float2bfloat16_rn(b.x), __float2bfloat16_rn(b.y),
+                               __float2bfloat16_rn(b.z), __float2bfloat16_rn(b.w)};
+    reinterpret_cast<uint4 *>(dst)[i] = *reinterpret_cast<const uint4 *>(o);
+}
+
+// Planar BF16 [2][nv][8] -> channels-last BF16 [nv][16].
+__global__ void k_planar_to_cl16(const bf16 *__restrict__ src, bf16 *__restrict__ dst, int64_t nv) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < cnt) dst[i] = __float2bfloat16_rn(src[i]);
+    if (i >= 2 * nv) return;
+    const int64_t c = i / nv, v = i - c * nv;
+    reinterpret_cast<uint4 *>(dst)[v * 2 + c] = reinterpret_cast<const uint4 *>(src)[i];
 }
 
 // Mean squared error over the coarse voxels that are not fully solid, on
@@ -136,7 +163,7 @@ __global__ void k_surr_loss(const float *__restrict__ out, const float *__restri
     const float inv_norm = 1.0f / (3.0f * (float)max(*count, 1));
     float l = 0.0f;
     if (v < nv) {
-        const bool fluid = __bfloat162float(feats[v * 16 + 4]) < 1.0f;
+        const bool fluid = __bfloat162float(feats[v * 8 + 4]) < 1.0f;  // solid fraction, plane 0
         __align__(16) bf16 g[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) g[c] = __float2bfloat16_rn(0.0f);
@@ -148,9 +175,8 @@ __global__ void k_surr_loss(const float *__restrict__ out, const float *__restri
                 g[c] = __float2bfloat16_rn(2.0f * d * inv_norm);
             }
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(g4 + v * 16);
-        dst[0] = reinterpret_cast<const uint4 *>(g)[0];
-        dst[1] = reinterpret_cast<const uint4 *>(g)[1];
+        reinterpret_cast<uint4 *>(g4)[v] = reinterpret_cast<const uint4 *>(g)[0];
+        reinterpret_cast<uint4 *>(g4)[nv + v] = reinterpret_cast<const uint4 *>(g)[1];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
@@ -159,7 +185,7 @@ __global__ void k_surr_loss(const float *__restrict__ out, const float *__restri
 
 __global__ void k_count_fluid(const bf16 *__restrict__ feats, int64_t nv, int *__restrict__ count) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int c = (v < nv && __bfloat162float(feats[v * 16 + 4]) < 1.0f) ? 1 : 0;
+    int c = (v < nv && __bfloat162float(feats[v * 8 + 4]) < 1.0f) ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
@@ -239,39 +265,101 @@ __global__ void k_surr_apply(const float *__restrict__ out, float out_scale,
     }
 }
 
-// Fine velocity update of the chained mode: u += out_scale * du upsampled
-// (same interpolation as k_surr_apply), rho kept; nothing written to a lattice.
-__global__ void k_surr_advance_fine(const float *__restrict__ out, float out_scale,
-                                    float *__restrict__ fine, const uint8_t *__restrict__ solid,
-                                    int n) {
+// Chained-mode step after a network call: u += out_scale * du upsampled (the
+// interpolation of k_surr_apply; rho kept) on every fluid fine cell, then the
+// coarse features of the updated state (the arithmetic and summation order of
+// k_surr_coarse), so that the next network call can run directly.
+// A block of 128 threads covers 16 coarse voxels along x at one (y, z): warp
+// w = by + 2 bz takes fine row (2y + by, 2z + bz), lane l fine x = 2 x0 + l,
+// so every warp access is 32 consecutive cells. The 18 x 3 x 3 coarse outputs
+// the block interpolates from are staged in shared memory first.
+constexpr int ADV_VX = 16;  // coarse voxels per block along x
+__global__ void __launch_bounds__(128) k_surr_advance_fine(
+    const float *__restrict__ out, float out_scale, float *__restrict__ fine,
+    const uint8_t *__restrict__ solid, int n, float in_scale, bf16 *__restrict__ feats) {
+    __shared__ float du[3][3][ADV_VX + 2][3];  // coarse (z, y, x) around the block
+    __shared__ float part[8][ADV_VX][4];       // per fine cell k: (rho - 1, u) or 0
+    __shared__ int isf[8][ADV_VX];
+    const int bxs = n / ADV_VX;
+    const int x0 = (blockIdx.x % bxs) * ADV_VX;
+    const int y = (blockIdx.x / bxs) % n, z = blockIdx.x / (bxs * n);
+    for (int e = threadIdx.x; e < 3 * 3 * (ADV_VX + 2); e += blockDim.x) {
+        const int ex = e % (ADV_VX + 2), ey = (e / (ADV_VX + 2)) % 3, ez = e / (3 * (ADV_VX + 2));
+        const int cx = min(max(x0 - 1 + ex, 0), n - 1), cy = min(max(y - 1 + ey, 0), n - 1);
+        const int cz = min(max(z - 1 + ez, 0), n - 1);
+        const float *o = out + (((int64_t)cz * n + cy) * n + cx) * 16;
+        du[ez][ey][ex][0] = __ldg(o);
+        du[ez][ey][ex][1] = __ldg(o + 1);
+        du[ez][ey][ex][2] = __ldg(o + 2);
+    }
+    __syncthreads();
     const int N = 2 * n;
     const int64_t nc = (int64_t)N * N * N;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    if (solid && solid[c]) return;
-    const int fi[3] = {(int)(c % N), (int)((c / N) % N), (int)(c / ((int64_t)N * N))};
-    int i0[3];
-    float t[3];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int by = w & 1, bz = w >> 1, bx = lane & 1, vx = lane >> 1;
+    const int fi[3] = {2 * x0 + lane, 2 * y + by, 2 * z + bz};
+    const int64_t c = ((int64_t)fi[2] * N + fi[1]) * N + fi[0];
+    const int k = bx + 2 * by + 4 * bz;  // the cell's place in the coarse voxel
+    float contrib[4] = {0.f, 0.f, 0.f, 0.f};
+    int fl = 0;
+    if (!(solid && solid[c])) {
+        int i0[3];
+        float t[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float s = fminf(fmaxf(fi[a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
-        int i = min((int)floorf(s), n - 2);
-        i0[a] = i;
-        t[a] = s - (float)i;
-    }
-    float d[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < 3; ++a) {
+            float sa = fminf(fmaxf(fi[a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
+            int i = min((int)floorf(sa), n - 2);
+            i0[a] = i;
+            t[a] = sa - (float)i;
+        }
+        float d[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int cx = k & 1, cy = (k >> 1) & 1, cz = k >> 2;
-        const float w = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
-        const float *o = out + ((((int64_t)(i0[2] + cz)) * n + (i0[1] + cy)) * n + (i0[0] + cx)) * 16;
-        d[0] += w * o[0];
-        d[1] += w * o[1];
-        d[2] += w * o[2];
+        for (int q = 0; q < 8; ++q) {
+            const int cx = q & 1, cy = (q >> 1) & 1, cz = q >> 2;
+            const float wq = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
+            const float *o = du[i0[2] + cz - (z - 1)][i0[1] + cy - (y - 1)][i0[0] + cx - (x0 - 1)];
+            d[0] += wq * o[0];
+            d[1] += wq * o[1];
+            d[2] += wq * o[2];
+        }
+        const float ux = fine[nc + c] + out_scale * d[0];
+        const float uy = fine[2 * nc + c] + out_scale * d[1];
+        const float uz = fine[3 * nc + c] + out_scale * d[2];
+        fine[nc + c] = ux;
+        fine[2 * nc + c] = uy;
+        fine[3 * nc + c] = uz;
+        contrib[0] = fine[c] - 1.0f;
+        contrib[1] = ux;
+        contrib[2] = uy;
+        contrib[3] = uz;
+        fl = 1;
     }
-    fine[nc + c] += out_scale * d[0];
-    fine[2 * nc + c] += out_scale * d[1];
-    fine[3 * nc + c] += out_scale * d[2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) part[k][vx][a] = contrib[a];
+    isf[k][vx] = fl;
+    __syncthreads();
+    if (threadIdx.x < ADV_VX) {
+        const int v = threadIdx.x;
+        float sum[4] = {0.f, 0.f, 0.f, 0.f};
+        int fluid = 0;
+        for (int kk = 0; kk < 8; ++kk) {
+            if (!isf[kk][v]) continue;
+            ++fluid;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) sum[a] += part[kk][v][a];
+        }
+        const float inv = fluid > 0 ? in_scale / (float)fluid : 0.0f;
+        __align__(16) bf16 o8[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) o8[ch] = __float2bfloat16_rn(0.0f);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) o8[ch] = __float2bfloat16_rn(sum[ch] * inv);
+        o8[4] = __float2bfloat16_rn((8 - fluid) * 0.125f);
+        const int64_t nv = (int64_t)n * n * n;
+        const int64_t cv = ((int64_t)z * n + y) * n + x0 + v;
+        reinterpret_cast<uint4 *>(feats)[cv] = *reinterpret_cast<const uint4 *>(o8);   // channels 0-7
+        reinterpret_cast<uint4 *>(feats)[nv + cv] = make_uint4(0u, 0u, 0u, 0u);       // channels 8-15
+    }
 }
 
 // f = f_eq(rho, u) of the fine state on fluid cells (shifted populations).
@@ -363,20 +451,69 @@ __global__ void k_vel_err(const float *__restrict__ fa, const float *__restrict_
 
 // ----------------------------------------------------------- launching ----
 
+// pdl: launch with programmatic dependent launch (only where the weights
+// were not rewritten by the kernel just before: every layer but the first of
+// a forward pass).
 template <int CIN, int COUT, int EPI>
-static dw_status conv(SurrHandle *h, const bf16 *in, const bf16 *wt, const float *bias, bf16 *oz,
-                      bf16 *oa, float *of, const bf16 *zprev, cudaStream_t s) {
-    constexpr size_t smem = conv3_smem<CIN, COUT>();
-    static bool attr_set = false;  // one attribute per instantiation
-    if (!attr_set) {
-        DW_CUDA(cudaFuncSetAttribute(k_conv3<CIN, COUT, EPI>,
+static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, const float *bias,
+                      bf16 *oz, bf16 *oa, float *of, const bf16 *zprev, cudaStream_t s,
+                      bool pdl = true) {
+    constexpr size_t smem = tc_smem<CIN, COUT>();
+    static int per_sm = 0;  // resident CTAs per SM of this instantiation
+    if (per_sm == 0) {
+        DW_CUDA(cudaFuncSetAttribute(k_conv3_tc<CIN, COUT, EPI>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+        int occ = 0;
+        DW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3_tc<CIN, COUT, EPI>,
+                                                              TC_THREADS, smem));
+        per_sm = occ > 0 ? occ : 1;
     }
-    const int ntiles = (h->n / CV_TX) * (h->n / CV_TY) * h->n;
-    const int grid = ntiles < h->conv_ctas ? ntiles : h->conv_ctas;
-    k_conv3<CIN, COUT, EPI><<<grid, CV_THREADS, smem, s>>>(in, wt, bias, h->n, oz, oa, of, zprev);
-    DW_LAUNCHED("k_conv3");
+    const int ntiles = (h->n / TC_TX) * (h->n / TC_TY) * h->n;
+    const int ctas = per_sm * h->sms;  // one wave: every CTA is resident
+    const int grid = ntiles < ctas ? ntiles : ctas;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    DW_CUDA(cudaLaunchKernelEx(&cfg, k_conv3_tc<CIN, COUT, EPI>, tm_in, wt, bias, h->n, oz, oa, of,
+                               zprev, h->err));
+    return DW_OK;
+}
+
+// TMA descriptor of a planar [C/8][n][n][n][8] BF16 volume, box = one
+// 8-channel plane of a 10 x 18 x 3 halo, zero fill outside.
+static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        DW_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                 cudaEnableDefault, &q));
+        if (!fn || q != cudaDriverEntryPointSuccess) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return DW_ERR_CUDA;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t nn = (cuuint64_t)n;
+    const cuuint64_t dims[5] = {8, nn, nn, nn, (cuuint64_t)(C / 8)};
+    const cuuint64_t strides[4] = {16, 16 * nn, 16 * nn * nn, 16 * nn * nn * nn};
+    const cuuint32_t box[5] = {8, TC_HX, TC_HY, 3, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims,
+                              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return DW_ERR_CUDA;
+    }
     return DW_OK;
 }
 
@@ -444,6 +581,7 @@ extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     h->conv_ctas = 2 * (sms > 0 ? sms : 1);
+    h->sms = sms > 0 ? sms : 1;
     const size_t nv = (size_t)h->nv, Nc = (size_t)8 * nv;
 #define DW_ALLOC(ptr, bytes) \
     if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes))
@@ -465,14 +603,24 @@ extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
     DW_ALLOC(h->part_b, sizeof(float) * (size_t)h->nchunks * 32);
     DW_ALLOC(h->fine, sizeof(float) * 4 * Nc);
     DW_ALLOC(h->red, sizeof(double) * 4);
+    DW_ALLOC(h->err, sizeof(int));
 #undef DW_ALLOC
     if (e == cudaSuccess) e = cudaMemset(h->params, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->grads, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->m, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->v, 0, sizeof(float) * o);
+    if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dw_status st = cuda_fail(e, "surr_create");
+        surr_destroy(h);
+        return st;
+    }
+    dw_status st = make_halo_map(&h->tm_feats, h->feats, n, 16);
+    for (int l = 0; l < 3 && st == DW_OK; ++l) st = make_halo_map(&h->tm_a[l], h->a[l], n, 32);
+    if (st == DW_OK) st = make_halo_map(&h->tm_g4, h->g4, n, 16);
+    for (int l = 0; l < 3 && st == DW_OK; ++l) st = make_halo_map(&h->tm_gz[l], h->gz[l], n, 32);
+    if (st != DW_OK) {
         surr_destroy(h);
         return st;
     }
@@ -500,6 +648,7 @@ extern "C" dw_status surr_destroy(dw_surr h) {
     cudaFree(h->part_b);
     cudaFree(h->fine);
     cudaFree(h->red);
+    cudaFree(h->err);
     delete h;
     return DW_OK;
 }
@@ -552,15 +701,16 @@ extern "C" dw_status surr_features(dw_surr h, const float *f, const uint8_t *sol
 
 extern "C" dw_status surr_set_features(dw_surr h, const float *feats, dw_stream stream) {
     DW_REQUIRE(h && feats, "handle and feats must not be NULL");
-    k_f32_to_bf16<<<grid_for(h->nv * 16, 256), 256, 0, as_stream(stream)>>>(feats, h->feats, h->nv * 16);
-    DW_LAUNCHED("k_f32_to_bf16");
+    k_cl16_to_planar<<<grid_for(h->nv * 2, 256), 256, 0, as_stream(stream)>>>(feats, h->feats, h->nv);
+    DW_LAUNCHED("k_cl16_to_planar");
     return DW_OK;
 }
 
 extern "C" dw_status surr_get_features(dw_surr h, void *feats_bf16, dw_stream stream) {
     DW_REQUIRE(h && feats_bf16, "handle and feats must not be NULL");
-    DW_CUDA(cudaMemcpyAsync(feats_bf16, h->feats, sizeof(bf16) * h->nv * 16, cudaMemcpyDeviceToDevice,
-                            as_stream(stream)));
+    k_planar_to_cl16<<<grid_for(h->nv * 2, 256), 256, 0, as_stream(stream)>>>(
+        h->feats, static_cast<bf16 *>(feats_bf16), h->nv);
+    DW_LAUNCHED("k_planar_to_cl16");
     return DW_OK;
 }
 
@@ -571,25 +721,36 @@ extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activation
     dw_status st;
     const float *P = h->params;
     if (keep_activations) {
-        st = conv<16, 32, EPI_GELU>(h, h->feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s);
+        st = conv<16, 32, EPI_GELU>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s, false);
         if (st != DW_OK) return st;
-        st = conv<32, 32, EPI_GELU>(h, h->a[0], h->wf + h->woff[1], P + h->off_b[1], h->z[1], h->a[1], nullptr, nullptr, s);
+        st = conv<32, 32, EPI_GELU>(h, h->tm_a[0], h->wf + h->woff[1], P + h->off_b[1], h->z[1], h->a[1], nullptr, nullptr, s);
         if (st != DW_OK) return st;
-        st = conv<32, 32, EPI_GELU>(h, h->a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
+        st = conv<32, 32, EPI_GELU>(h, h->tm_a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
         if (st != DW_OK) return st;
     } else {
-        st = conv<16, 32, EPI_GELU_ONLY>(h, h->feats, h->wf + h->woff[0], P + h->off_b[0], nullptr, h->a[0], nullptr, nullptr, s);
+        st = conv<16, 32, EPI_GELU_ONLY>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], nullptr, h->a[0], nullptr, nullptr, s, false);
         if (st != DW_OK) return st;
-        st = conv<32, 32, EPI_GELU_ONLY>(h, h->a[0], h->wf + h->woff[1], P + h->off_b[1], nullptr, h->a[1], nullptr, nullptr, s);
+        st = conv<32, 32, EPI_GELU_ONLY>(h, h->tm_a[0], h->wf + h->woff[1], P + h->off_b[1], nullptr, h->a[1], nullptr, nullptr, s);
         if (st != DW_OK) return st;
-        st = conv<32, 32, EPI_GELU_ONLY>(h, h->a[1], h->wf + h->woff[2], P + h->off_b[2], nullptr, h->a[2], nullptr, nullptr, s);
+        st = conv<32, 32, EPI_GELU_ONLY>(h, h->tm_a[1], h->wf + h->woff[2], P + h->off_b[2], nullptr, h->a[2], nullptr, nullptr, s);
         if (st != DW_OK) return st;
     }
-    st = conv<32, 16, EPI_F32>(h, h->a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s);
+    st = conv<32, 16, EPI_F32>(h, h->tm_a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s);
     if (st != DW_OK) return st;
     if (out)
         DW_CUDA(cudaMemcpyAsync(out, h->out, sizeof(float) * h->nv * 16, cudaMemcpyDeviceToDevice, s));
     return DW_OK;
+}
+
+extern "C" dw_status surr_device_status(dw_surr h, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    int bits = 0;
+    cudaStream_t s = as_stream(stream);
+    DW_CUDA(cudaMemcpyAsync(&bits, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DW_CUDA(cudaStreamSynchronize(s));
+    DW_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    DW_CUDA(cudaStreamSynchronize(s));
+    return status_from_bits(bits);
 }
 
 extern "C" dw_status surr_loss(dw_surr h, const float *target, float *loss, dw_stream stream) {
@@ -605,8 +766,8 @@ extern "C" dw_status surr_loss(dw_surr h, const float *target, float *loss, dw_s
 
 extern "C" dw_status surr_set_output_grad(dw_surr h, const float *g_out, dw_stream stream) {
     DW_REQUIRE(h && g_out, "handle and g_out must not be NULL");
-    k_f32_to_bf16<<<grid_for(h->nv * 16, 256), 256, 0, as_stream(stream)>>>(g_out, h->g4, h->nv * 16);
-    DW_LAUNCHED("k_f32_to_bf16");
+    k_cl16_to_planar<<<grid_for(h->nv * 2, 256), 256, 0, as_stream(stream)>>>(g_out, h->g4, h->nv);
+    DW_LAUNCHED("k_cl16_to_planar");
     return DW_OK;
 }
 
@@ -617,15 +778,15 @@ extern "C" dw_status surr_backward(dw_surr h, dw_stream stream) {
     // layer 4: dW from a3 and g4; dL/dz3 = (W4' * g4) GELU'(z3)
     st = wgrad<32, 16>(h, h->a[2], h->g4, 3, s);
     if (st != DW_OK) return st;
-    st = conv<16, 32, EPI_DGELU>(h, h->g4, h->wd + h->woff[3], nullptr, h->gz[2], nullptr, nullptr, h->z[2], s);
+    st = conv<16, 32, EPI_DGELU>(h, h->tm_g4, h->wd + h->woff[3], nullptr, h->gz[2], nullptr, nullptr, h->z[2], s);
     if (st != DW_OK) return st;
     st = wgrad<32, 32>(h, h->a[1], h->gz[2], 2, s);
     if (st != DW_OK) return st;
-    st = conv<32, 32, EPI_DGELU>(h, h->gz[2], h->wd + h->woff[2], nullptr, h->gz[1], nullptr, nullptr, h->z[1], s);
+    st = conv<32, 32, EPI_DGELU>(h, h->tm_gz[2], h->wd + h->woff[2], nullptr, h->gz[1], nullptr, nullptr, h->z[1], s);
     if (st != DW_OK) return st;
     st = wgrad<32, 32>(h, h->a[0], h->gz[1], 1, s);
     if (st != DW_OK) return st;
-    st = conv<32, 32, EPI_DGELU>(h, h->gz[1], h->wd + h->woff[1], nullptr, h->gz[0], nullptr, nullptr, h->z[0], s);
+    st = conv<32, 32, EPI_DGELU>(h, h->tm_gz[1], h->wd + h->woff[1], nullptr, h->gz[0], nullptr, nullptr, h->z[0], s);
     if (st != DW_OK) return st;
     st = wgrad<16, 32>(h, h->feats, h->gz[0], 0, s);
     return st;
@@ -674,12 +835,10 @@ extern "C" dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float i
 }
 
 extern "C" dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *solid,
-                                       dw_stream stream) {
+                                       float in_scale, dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
-    const int N = 2 * h->n;
-    const int64_t nc = (int64_t)N * N * N;
-    k_surr_advance_fine<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(h->out, out_scale, h->fine,
-                                                                          solid, h->n);
+    k_surr_advance_fine<<<(unsigned)(h->nv / ADV_VX), 128, 0, as_stream(stream)>>>(
+        h->out, out_scale, h->fine, solid, h->n, in_scale, h->feats);
     DW_LAUNCHED("k_surr_advance_fine");
     return DW_OK;
 }

@@ -1,21 +1,15 @@
-// 3x3x3 convolutions of the surrogate network as implicit GEMMs on the tensor
-// cores (BF16 operands, FP32 accumulation), channels-last activations.
+// Weight gradients of the surrogate network's 3x3x3 convolutions on the
+// tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation), and the
+// helpers the convolution kernels share (GELU and its derivative).
 //
-// Forward / input-gradient kernel k_conv3: out[v][co] = sum_{tap, ci}
-// W[tap][co][ci] in[v + d(tap)][ci] (zero outside the volume). A CTA computes
-// an output tile of 16 (x) x 8 (y) x 1 (z) voxels; warp w owns the 16 voxels of
-// row y0 + w, i.e. one M = 16 slice, and all COUT output channels. The input
-// halo (18 x 10 x 3 voxels) and the whole weight tensor live in shared memory;
-// A and B fragments come from ldmatrix with per-lane row addresses (the
-// implicit im2col), and mma.sync m16n8k16 accumulates in registers. CTAs are
-// persistent over tiles so the weights are loaded once per CTA.
-//
-// Weight-gradient kernel k_wgrad: dW[tap][co][ci] = sum_v g[v][co] in[v + d][ci]
-// per chunk of tiles, written as partial sums that k_wgrad_reduce adds up.
-//
-// Shared-memory rows (a voxel's or an output channel's CIN values) are stored
-// with their 16-byte chunks XOR-swizzled by the row index, so that the eight
-// rows an ldmatrix matrix reads hit distinct banks.
+// k_wgrad: dW[tap][co][ci] = sum_v g[v][co] in[v + d(tap)][ci] over the
+// voxels of a chunk of output tiles of 16 (x) x 8 (y) x 1 (z), written as
+// partial sums that k_wgrad_reduce adds up. The GEMM runs over voxels (K),
+// which is why it stays on the warp-level MMA: the forward and input-gradient
+// convolutions (surrogate_tc.cuh) are the tcgen05 kernels. Activations are
+// planar, [C/8][n^3][8] BF16. Shared-memory rows (a voxel's or an output
+// channel's values) keep their 16-byte chunks XOR-swizzled by the row index,
+// so that the eight rows an ldmatrix matrix reads hit distinct banks.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -86,93 +80,10 @@ __device__ __forceinline__ void load_halo(const bf16 *__restrict__ in, int n, in
         const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (gx >= 0 && gy >= 0 && gz >= 0 && gx < n && gy < n && gz < n)
-            v = *reinterpret_cast<const uint4 *>(in + (((size_t)gz * n + gy) * n + gx) * C + c * 8);
+            v = *reinterpret_cast<const uint4 *>(
+                in + ((size_t)c * n * n * n + ((size_t)gz * n + gy) * n + gx) * 8);
         *reinterpret_cast<uint4 *>(halo + swz_off<C>(hr, c)) = v;
     }
-}
-
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(CV_THREADS, 2) k_conv3(
-    const bf16 *__restrict__ in, const bf16 *__restrict__ wt, const float *__restrict__ bias,
-    int n, bf16 *__restrict__ out_z, bf16 *__restrict__ out_a, float *__restrict__ out_f,
-    const bf16 *__restrict__ zprev) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *wsm = smem;                                     // [27*COUT][CIN]
-    unsigned char *halo = smem + 27 * COUT * CIN * 2;              // [540][CIN]
-    constexpr int WCPV = CIN / 8;
-    for (int idx = threadIdx.x; idx < 27 * COUT * WCPV; idx += blockDim.x) {
-        const int row = idx / WCPV, c = idx % WCPV;
-        *reinterpret_cast<uint4 *>(wsm + swz_off<CIN>(row, c)) =
-            *reinterpret_cast<const uint4 *>(wt + (size_t)row * CIN + c * 8);
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int tiles_x = n / CV_TX, tiles_y = n / CV_TY;
-    const int ntiles = tiles_x * tiles_y * n;
-    const uint32_t wbase = smem_u32(wsm), hbase = smem_u32(halo);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, z0 = tile / (tiles_x * tiles_y);
-        const int x0 = tx * CV_TX, y0 = ty * CV_TY;
-        __syncthreads();  // previous tile done with the halo (and the weights are in)
-        load_halo<CIN>(in, n, x0, y0, z0, halo);
-        __syncthreads();
-        float acc[COUT / 8][4];
-#pragma unroll
-        for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-        const int ar = lane & 15;  // A row (voxel) this lane addresses
-#pragma unroll 1
-        for (int t = 0; t < 27; ++t) {
-            const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-            const int hr = ((dz + 1) * CV_HY + (w + dy + 1)) * CV_HX + (ar + dx + 1);
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                uint32_t a0, a1, a2, a3;
-                ldsm_x4(a0, a1, a2, a3, hbase + swz_off<CIN>(hr, 2 * kc + (lane >> 4)));
-#pragma unroll
-                for (int jj = 0; jj < COUT / 16; ++jj) {
-                    const int co = 16 * jj + ((lane >> 4) << 3) + (lane & 7);
-                    uint32_t b0, b1, b2, b3;
-                    ldsm_x4(b0, b1, b2, b3,
-                            wbase + swz_off<CIN>(t * COUT + co, 2 * kc + ((lane >> 3) & 1)));
-                    mma_16816(acc[2 * jj], a0, a1, a2, a3, b0, b1);
-                    mma_16816(acc[2 * jj + 1], a0, a1, a2, a3, b2, b3);
-                }
-            }
-        }
-        // epilogue: rows gid and gid + 8 of this warp's 16 voxels
-        const size_t vrow = ((size_t)z0 * n + (y0 + w)) * n + x0;
-#pragma unroll
-        for (int j = 0; j < COUT / 8; ++j) {
-            const int co = 8 * j + 2 * tig;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const size_t v = vrow + gid + 8 * h;
-                float z0v = acc[j][2 * h], z1v = acc[j][2 * h + 1];
-                if (EPI == EPI_GELU || EPI == EPI_GELU_ONLY) {
-                    z0v += bias[co];
-                    z1v += bias[co + 1];
-                    if (EPI == EPI_GELU)
-                        *reinterpret_cast<__nv_bfloat162 *>(out_z + v * COUT + co) = __floats2bfloat162_rn(z0v, z1v);
-                    *reinterpret_cast<__nv_bfloat162 *>(out_a + v * COUT + co) =
-                        __floats2bfloat162_rn(gelu_f(z0v), gelu_f(z1v));
-                } else if (EPI == EPI_F32) {
-                    z0v += bias[co];
-                    z1v += bias[co + 1];
-                    *reinterpret_cast<float2 *>(out_f + v * COUT + co) = make_float2(z0v, z1v);
-                } else {
-                    const __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162 *>(zprev + v * COUT + co);
-                    const float g0 = z0v * gelu_grad_f(__bfloat162float(zp.x));
-                    const float g1 = z1v * gelu_grad_f(__bfloat162float(zp.y));
-                    *reinterpret_cast<__nv_bfloat162 *>(out_z + v * COUT + co) = __floats2bfloat162_rn(g0, g1);
-                }
-            }
-        }
-    }
-}
-
-template <int CIN, int COUT>
-constexpr size_t conv3_smem() {
-    return (size_t)27 * COUT * CIN * 2 + (size_t)CV_HALO * CIN * 2;
 }
 
 // Partial weight gradients of tap plane dz = blockIdx.y - 1 over the tiles of
@@ -213,7 +124,7 @@ __global__ void __launch_bounds__(CV_THREADS) k_wgrad(const bf16 *__restrict__ i
             const int kv = idx / GCPV, c = idx % GCPV;
             const size_t v = ((size_t)z0 * n + (y0 + kv / 16)) * n + x0 + kv % 16;
             *reinterpret_cast<uint4 *>(gsm + swz_off<COUT>(kv, c)) =
-                *reinterpret_cast<const uint4 *>(g + v * COUT + c * 8);
+                *reinterpret_cast<const uint4 *>(g + ((size_t)c * n * n * n + v) * 8);
         }
         __syncthreads();
         if (blockIdx.y == 0 && threadIdx.x < COUT) {

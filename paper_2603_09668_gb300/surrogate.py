@@ -9,7 +9,7 @@ equilibrium. Training data come from the library's own LBM runs on lattices
 with random leaf-cluster obstacles and random inlet directions.
 
 `SurrogateLBM.advance` re-checks the surrogate against the plain LBM every
-`check_every` blocks: it runs both from the same state and compares the
+`check_every` blocks: it runs both from the same lattice and compares the
 fluid velocities; the run continues from the plain result. If the relative
 L2 error exceeds `tol` (2%), the surrogate is switched off from then on.
 """
@@ -152,7 +152,6 @@ class SurrogateLBM:
         self.fallback = False
         self.errors = []
         self._sums = torch.zeros(2, dtype=torch.float64, device=device)
-        self._shadow = None
 
     # one block from a lattice (reads f, writes f)
     def surrogate_block(self, f, solid):
@@ -162,11 +161,13 @@ class SurrogateLBM:
         self.surr.apply(solid, f, None, OUT_SCALE)
         return f
 
-    # one block of the chained mode (fine state in, fine state out)
+    # one block of the chained mode: the coarse features of the current fine
+    # state are in the handle (from surr.features or the previous block);
+    # the network runs and the fine state advances, leaving the features of
+    # the new state for the next block
     def chained_block(self, solid):
-        self.surr.features_fine(solid, IN_SCALE)
         self.surr.forward(keep_activations=False)
-        self.surr.advance_fine(OUT_SCALE, solid)
+        self.surr.advance_fine(OUT_SCALE, solid, IN_SCALE)
 
     def plain_block(self, f, solid):
         return self.lbm.step(f, solid, BLOCK)
@@ -185,37 +186,38 @@ class SurrogateLBM:
 
     def advance(self, f, solid, n_blocks):
         """n_blocks blocks of BLOCK steps on lattice f (in place); returns the
-        number of blocks the surrogate ran."""
+        number of blocks whose result came from the surrogate.
+
+        Every check_every-th block is a check block: the fine state is taken
+        from the lattice, the plain LBM advances the lattice, the surrogate
+        advances the fine state, and the fluid velocities are compared; the
+        run continues from the plain lattice. Other blocks chain the
+        surrogate on the fine state; the lattice is rebuilt from it,
+        f = f_eq(rho, u), only before a check block or at the end."""
         used = 0
         in_fine = False  # the current state is the handle's fine field, not f
         for _ in range(n_blocks):
             if self.fallback:
                 self.plain_block(f, solid)
                 continue
-            if not in_fine:
-                self.surr.features(f, solid, IN_SCALE)  # fine state from the lattice
-                in_fine = True
             if self.calls % self.check_every == 0:
-                # check block: both runs from the same state; the run goes on
-                # from the plain result, which also re-anchors the chained
-                # state on the LBM trajectory
-                if self._shadow is None:
-                    self._shadow = torch.empty_like(f)
-                self.surr.write_lattice(solid, f)
-                self._shadow.copy_(f)
-                self.plain_block(self._shadow, solid)
+                if in_fine:
+                    self.surr.write_lattice(solid, f)
+                    in_fine = False
+                self.surr.features(f, solid, IN_SCALE)
+                self.plain_block(f, solid)
                 self.chained_block(solid)
-                err = self.fine_error(self._shadow, solid)
+                err = self.fine_error(f, solid)
                 self.errors.append(err)
-                f.copy_(self._shadow)
-                in_fine = False
                 if err > self.tol:
                     self.fallback = True
-                    continue
             else:
+                if not in_fine:
+                    self.surr.features(f, solid, IN_SCALE)
+                    in_fine = True
                 self.chained_block(solid)
+                used += 1
             self.calls += 1
-            used += 1
         if in_fine:
             self.surr.write_lattice(solid, f)
         return used

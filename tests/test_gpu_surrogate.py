@@ -152,3 +152,35 @@ def test_training_fits_a_teacher_network():
             losses.append(loss.item())
     assert losses[1] < 0.1 * losses[0], losses
     s.close()
+
+
+def test_chained_advance_matches_apply_and_features():
+    """surr_advance_fine (u += out_scale * upsampled output, then the coarse
+    features of the new state) against surr_apply (which re-equilibrates the
+    lattice from the same upsampled update) and surr_features_fine."""
+    n = 16
+    N = 2 * n
+    c, w, _ = oracle.velocity_set()
+    solid = inputs.random_mask((N, N, N), 0.1, seed=13)
+    rng = np.random.default_rng(14)
+    feq = oracle.lbm_equilibrium(1.0, np.array([0.04, -0.01, 0.02]))
+    f_plain = feq[:, None] + rng.uniform(-2e-3, 2e-3, (19, N ** 3))
+    f_dev = to_dev((f_plain - w[:, None]).astype(np.float32).reshape(19, N, N, N))
+    sol = to_dev(solid).reshape(N, N, N)
+    s = B.Surrogate(n)
+    s.set_params(to_dev(random_params(seed=15, scale=0.3)))
+    s.features(f_dev, sol, 20.0)
+    s.forward(keep_activations=False)  # the output the update upsamples
+    f_apply = f_dev.clone()
+    s.apply(sol, f_apply, None, 1e-3)
+    s.advance_fine(1e-3, sol, 20.0)
+    feats_adv = s.get_features().clone()
+    f_adv = f_dev.clone()
+    s.write_lattice(sol, f_adv)
+    fl = torch.from_numpy(solid == 0).to("cuda").reshape(-1)
+    d = (f_apply.reshape(19, -1)[:, fl] - f_adv.reshape(19, -1)[:, fl]).abs().max().item()
+    assert d <= 1e-7, d
+    s.features_fine(sol, 20.0)
+    assert torch.equal(s.get_features(), feats_adv)
+    s.device_status()
+    s.close()

@@ -1,0 +1,71 @@
+"""GPU tests of the learned wind-constraint surrogate as a whole: the trained
+128^3 network (weights/surrogate_lbm128.npy, trained by
+paper_2603_09668_gb300.train_surrogate with the library's own kernels) on a
+held-out leaf-cluster scene and inlet direction, against the plain LBM.
+
+What the network gains: over one 20-step block its velocity error against
+the plain LBM must be within 2% (relative L2 over fluid cells) and clearly
+below that of keeping the velocity unchanged (persistence, du = 0), the
+method without the network. The plain-LBM check must switch the surrogate
+off when its error exceeds the tolerance, after which the run is exactly the
+plain LBM."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_09668_gb300 import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+N = 128
+
+
+def held_out_scene(t_eval=1500):
+    if not os.path.exists(S.weights_path(N)):
+        pytest.fail("trained weights are missing: " + S.weights_path(N))
+    rng = np.random.default_rng(20241)
+    d = S.inlet_direction(rng)
+    solid = S.leaf_mask(N, 31337)
+    m = S.SurrogateLBM(N, u_inlet=tuple(S.U_REF * d))
+    f0 = m.lbm.lattice("cuda")
+    m.lbm.step(f0, solid, t_eval)
+    return m, f0, solid
+
+
+def test_trained_network_beats_persistence_within_2_percent():
+    m, f0, solid = held_out_scene()
+    ref = f0.clone()
+    m.plain_block(ref, solid)
+    err_persist = m.velocity_error(f0, ref, solid)
+    m.surr.features(f0, solid, S.IN_SCALE)
+    m.chained_block(solid)
+    err_net = m.fine_error(ref, solid)
+    m.surr.device_status()
+    assert err_net <= 0.02, err_net
+    assert err_net < 0.8 * err_persist, (err_net, err_persist)
+    m.close()
+
+
+def test_check_switches_to_plain_lbm_and_stays_exact():
+    m, f0, solid = held_out_scene()
+    m.tol = 1e-6  # every check fails
+    f = f0.clone()
+    used = m.advance(f, solid, 3)
+    assert used == 0 and m.fallback and len(m.errors) == 1
+    ref = f0.clone()
+    m.lbm.step(ref, solid, 3 * S.BLOCK)
+    assert torch.equal(f, ref)
+    m.close()
+
+
+def test_run_with_checks_uses_the_surrogate():
+    m, f0, solid = held_out_scene()
+    f = f0.clone()
+    used = m.advance(f, solid, 12)  # checks at blocks 0 and 10
+    assert not m.fallback
+    assert used == 10
+    assert len(m.errors) == 2 and max(m.errors) <= 0.02, m.errors
+    assert torch.isfinite(f).all()
+    m.close()
