@@ -157,6 +157,20 @@ DW_API dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in, const dw_
                               const dw_wind_field *wind, float t, float *g_wind, float *g_E,
                               dw_stream stream);
 
+/* Reverse mode of n_substeps substeps (a checkpointed segment) in one call:
+ * recomputes the states 1 .. n_substeps - 1 from `start` (state 0, at time
+ * t0) into `tape` (device float, (n_substeps - 1) * 24 * n floats, each state
+ * as x, v, C, F back to back; caller-owned, tape_floats its size), then runs
+ * mpm_substep_adjoint from the last substep back to the first at times
+ * t0 + j dt. g holds dL/d(state after the segment) on entry and is
+ * overwritten with dL/d(start); g_wind and g_E accumulate as in
+ * mpm_substep_adjoint. The substeps are those of mpm_substep (no sorting). */
+DW_API dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, float *tape,
+                                     int64_t tape_floats, const dw_mpm_state *g,
+                                     const uint8_t *pinned, const dw_wind_field *wind, float t0,
+                                     int32_t n_substeps, float *g_wind, float *g_E,
+                                     dw_stream stream);
+
 /* Reorder particles by grid cell (the cell of floor(x/dx - 0.5), cells
  * grouped into 4^3 blocks) so that neighbouring P2G threads share stencils.
  * Writes the permuted state into `out` (must not overlap `in`) and the

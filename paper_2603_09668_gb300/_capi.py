@@ -69,6 +69,8 @@ SIGNATURES = {
     "mpm_substep_adjoint": (I32, [VP, P(DwMpmState), P(DwMpmState), P(DwMpmState), VP,
                                   P(DwWindField), F32, VP, VP, VP]),
     "mpm_sort": (I32, [VP, P(DwMpmState), P(DwMpmState), VP, VP, VP, VP, VP]),
+    "mpm_segment_adjoint": (I32, [VP, P(DwMpmState), VP, I64, P(DwMpmState), VP, P(DwWindField),
+                                  F32, I32, VP, VP, VP]),
     "mpm_device_status": (I32, [VP, VP]),
     "mpm_rollout": (I32, [VP, P(DwMpmState), VP, VP, P(DwWindField), F32, I32, I32, VP]),
     "mpm_profile_enable": (I32, [VP, I32]),

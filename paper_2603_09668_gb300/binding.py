@@ -19,7 +19,7 @@ from ._capi import (DiffWindError, DwBatchConfig, DwBatchTrial, DwLbmDesc, DwMpm
 
 __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "wind_field_sample_adjoint", "mpm_create", "mpm_destroy", "mpm_set_material",
-           "mpm_substep", "mpm_substep_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
+           "mpm_substep", "mpm_substep_adjoint", "mpm_segment_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM", "surr_create",
@@ -163,6 +163,20 @@ def mpm_substep_adjoint(h, state_in: MpmState, g_out: MpmState, g_in: MpmState, 
                                     ct.byref(w), float(t), _dev(g_wind, name="g_wind"),
                                     _dev(g_E, name="g_E"), _stream(stream)))
     return g_in
+
+
+def mpm_segment_adjoint(h, start: MpmState, tape, g: MpmState, pinned, wind: WindField, t0,
+                        n_substeps, g_wind=None, g_E=None, stream=None):
+    """Reverse mode of a segment of n_substeps substeps from `start`; tape is a
+    device float32 tensor of at least (n_substeps - 1) * 24 * n elements."""
+    a, gg, w = start.to_c(), g.to_c(), wind.to_c()
+    tp = _dev(tape, name="tape") if tape is not None else None
+    nt = tape.numel() if tape is not None else 0
+    check(lib().mpm_segment_adjoint(h, ct.byref(a), tp, int(nt), ct.byref(gg), _pin(pinned),
+                                    ct.byref(w), float(t0), int(n_substeps),
+                                    _dev(g_wind, name="g_wind"), _dev(g_E, name="g_E"),
+                                    _stream(stream)))
+    return g
 
 
 def mpm_sort(h, state_in: MpmState, state_out: MpmState, pinned_in, pinned_out, ids_in, ids_out,
@@ -387,6 +401,11 @@ class MPM:
                         stream=None):
         return mpm_substep_adjoint(self.h, state_in, g_out, g_in, pinned, wind, t, g_wind, g_E,
                                    stream)
+
+    def segment_adjoint(self, start, tape, g, pinned, wind, t0, n_substeps, g_wind=None, g_E=None,
+                        stream=None):
+        return mpm_segment_adjoint(self.h, start, tape, g, pinned, wind, t0, n_substeps, g_wind,
+                                   g_E, stream)
 
     def sort(self, state_in, state_out, pinned_in, pinned_out, ids_in, ids_out, stream=None):
         return mpm_sort(self.h, state_in, state_out, pinned_in, pinned_out, ids_in, ids_out, stream)

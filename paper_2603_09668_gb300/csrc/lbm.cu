@@ -265,74 +265,84 @@ __global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
 }
 
 // One collide + push step between two lattices in natural order. Solid cells
-// are copied so that fout holds a complete lattice.
+// are copied so that fout holds a complete lattice. links (or NULL without a
+// mask) gives the solid neighbours, so every target index is computed without
+// a dependent load.
 __global__ void __launch_bounds__(256, 4) k_lbm_push(LbmParams L, const float *__restrict__ fin,
                                                  float *__restrict__ fout,
-                                                 const uint8_t *__restrict__ solid) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+                                                 const uint32_t *__restrict__ links) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.ncell) return;
-    const size_t nc = (size_t)L.ncell;
-    if (solid && solid[cell]) {
+    const int nc = L.ncell;  // 19 * ncell < 2^31 is checked at create
+    const uint32_t lk = links ? links[cell] : 0u;
+    if (lk & 1u) {
 #pragma unroll
         for (int i = 0; i < 19; ++i) fout[i * nc + cell] = fin[i * nc + cell];
         return;
     }
     const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
+    const NbrOffsets o = nbr_offsets(L, x, y, z);
     float fl[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) fl[i] = fin[i * nc + cell];
     collide(L, fl);
+    const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
+    fout[cell] = fl[0];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        int tx = x + D3Q19::cx(i);
-        if (L.bc_x == 1 && (tx < 0 || tx > L.nx - 1)) continue;
-        int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
-                           wrapc(z + D3Q19::cz(i), L.nz));
-        if (solid && solid[t])
-            fout[D3Q19::opp(i) * nc + cell] = fl[i];
-        else
-            fout[i * nc + t] = fl[i];
+    for (int i = 1; i < 19; ++i) {
+        if (inlet_face && D3Q19::cx(i) == -1) continue;   // leaves through x = 0
+        if (outlet_face && D3Q19::cx(i) == 1) continue;   // leaves through x = nx - 1
+        const int idx = ((lk >> i) & 1u)
+                            ? D3Q19::opp(i) * nc + cell
+                            : i * nc + cell + o.off(D3Q19::cx(i), D3Q19::cy(i), D3Q19::cz(i));
+        fout[idx] = fl[i];
     }
-    if (L.bc_x == 1) {
+    if (inlet_face) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            if (x == 0 && D3Q19::cx(i) == 1) fout[i * nc + cell] = L.feq_in[i];
-            if (x == L.nx - 1 && D3Q19::cx(i) == -1) fout[i * nc + cell] = fl[i];
-        }
+        for (int i = 1; i < 19; ++i)
+            if (D3Q19::cx(i) == 1) fout[i * nc + cell] = L.feq_in[i];
+    }
+    if (outlet_face) {
+#pragma unroll
+        for (int i = 1; i < 19; ++i)
+            if (D3Q19::cx(i) == -1) fout[i * nc + cell] = fl[i];
     }
 }
 
 // ---------------------------------------------------------------- reverse --
 
 // One reverse step: g_prev = C^T S^T g_next at the pre-collision state f_t.
+// The transposed streaming pulls g_next from where the forward pushed f*:
+// slot i of x + c_i, or slot opp(i) of x itself where x + c_i is solid
+// (bounce-back), nothing where the population leaves the domain, plus the
+// cell's own slot i at the outlet face for the populations it re-injects.
 __global__ void __launch_bounds__(256, 4) k_lbm_adjoint(LbmParams L, const float *__restrict__ f_t,
                                                     const float *__restrict__ g_next,
                                                     float *__restrict__ g_prev,
-                                                    const uint8_t *__restrict__ solid) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+                                                    const uint32_t *__restrict__ links) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= L.ncell) return;
-    const size_t nc = (size_t)L.ncell;
-    if (solid && solid[cell]) {
+    const int nc = L.ncell;
+    const uint32_t lk = links ? links[cell] : 0u;
+    if (lk & 1u) {
 #pragma unroll
         for (int i = 0; i < 19; ++i) g_prev[i * nc + cell] = g_next[i * nc + cell];
         return;
     }
     const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
+    const NbrOffsets o = nbr_offsets(L, x, y, z);
+    const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
     float g[19];
+    g[0] = g_next[cell];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        float acc = 0.0f;
-        int tx = x + D3Q19::cx(i);
-        if (!(L.bc_x == 1 && (tx < 0 || tx > L.nx - 1))) {
-            int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
-                               wrapc(z + D3Q19::cz(i), L.nz));
-            if (solid && solid[t])
-                acc += g_next[D3Q19::opp(i) * nc + cell];
-            else
-                acc += g_next[i * nc + t];
-        }
-        if (L.bc_x == 1 && x == L.nx - 1 && D3Q19::cx(i) == -1) acc += g_next[i * nc + cell];
-        g[i] = acc;
+    for (int i = 1; i < 19; ++i) {
+        const int idx = ((lk >> i) & 1u)
+                            ? D3Q19::opp(i) * nc + cell
+                            : i * nc + cell + o.off(D3Q19::cx(i), D3Q19::cy(i), D3Q19::cz(i));
+        float v = g_next[idx];
+        if ((inlet_face && D3Q19::cx(i) == -1) || (outlet_face && D3Q19::cx(i) == 1)) v = 0.0f;
+        if (outlet_face && D3Q19::cx(i) == -1) v += g_next[i * nc + cell];
+        g[i] = v;
     }
     float fl[19];
 #pragma unroll
@@ -489,7 +499,7 @@ extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t 
     const LbmParams &L = h->L;
     unsigned grid = grid_for(L.ncell, 256);
     const uint32_t *links = nullptr;
-    if (solid && steps >= 2) {
+    if (solid) {
         k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
         links = h->links;
     }
@@ -498,7 +508,7 @@ extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t 
         k_lbm_aa_odd<<<grid, 256, 0, s>>>(L, f, links, h->outlet);
     }
     if (steps & 1) {
-        k_lbm_push<<<grid, 256, 0, s>>>(L, f, h->tape, solid);
+        k_lbm_push<<<grid, 256, 0, s>>>(L, f, h->tape, links);
         DW_CUDA(cudaMemcpyAsync(f, h->tape, sizeof(float) * 19 * (size_t)L.ncell,
                                 cudaMemcpyDeviceToDevice, s));
     }
@@ -517,15 +527,20 @@ extern "C" dw_status lbm_step_adjoint(dw_lbm h, const float *f_in, float *g_f,
     const LbmParams &L = h->L;
     const size_t lat = 19 * (size_t)L.ncell;
     unsigned grid = grid_for(L.ncell, 256);
+    const uint32_t *links = nullptr;
+    if (solid) {
+        k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
+        links = h->links;
+    }
     // states f(1) .. f(steps-1) into tape[0 .. steps-2]
     for (int k = 1; k < steps; ++k) {
         const float *src = k == 1 ? f_in : h->tape + (size_t)(k - 2) * lat;
-        k_lbm_push<<<grid, 256, 0, s>>>(L, src, h->tape + (size_t)(k - 1) * lat, solid);
+        k_lbm_push<<<grid, 256, 0, s>>>(L, src, h->tape + (size_t)(k - 1) * lat, links);
     }
     float *cur = g_f, *other = h->gtmp;
     for (int k = steps - 1; k >= 0; --k) {
         const float *state = k == 0 ? f_in : h->tape + (size_t)(k - 1) * lat;
-        k_lbm_adjoint<<<grid, 256, 0, s>>>(L, state, cur, other, solid);
+        k_lbm_adjoint<<<grid, 256, 0, s>>>(L, state, cur, other, links);
         float *tmp = cur;
         cur = other;
         other = tmp;

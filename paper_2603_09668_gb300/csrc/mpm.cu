@@ -93,112 +93,125 @@ __device__ __forceinline__ void weight_grad(const MpmParams &P, const Stencil &s
 }
 
 // Reverse G2P: scatter dL/dv_i into grid_bv; write partial dL/dx_p, dL/dF_p.
-__global__ void k_rev_g2p(MpmParams P, const float *__restrict__ x, const float *__restrict__ F,
-                          const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
-                          const float *__restrict__ gxo, const float *__restrict__ gvo,
-                          const float *__restrict__ gCo, const float *__restrict__ gFo,
-                          float4 *__restrict__ grid_bv, float *__restrict__ scratch, int64_t n,
-                          int64_t cap) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    float xp[3] = {x[p], x[n + p], x[2 * n + p]};
-    float Fp[9];
+// The node value W_ip (bv_p + D bC_p (x_i - x_p)) has the form of a P2G value
+// (momentum m v + A (x_i - x_p) with m v -> bv, A -> D bC and no mass), so it
+// goes through the same warp-aggregated scatter; grid_bv holds (0, dL/dv_i).
+__global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
+    MpmParams P, const float *__restrict__ x, const float *__restrict__ F,
+    const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
+    const float *__restrict__ gxo, const float *__restrict__ gvo, const float *__restrict__ gCo,
+    const float *__restrict__ gFo, float4 *__restrict__ grid_bv, float *__restrict__ scratch,
+    int64_t n, int64_t cap) {
+    __shared__ float4 rows[P2G_WARP_THREADS / 32][32][P2G_ROW];
+    __shared__ int keys[P2G_WARP_THREADS / 32][32];
+    const int wid = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    P2GParticle q;
+    q.valid = false;
+    if (p < n) {
+        float xp[3] = {x[p], x[n + p], x[2 * n + p]};
+        float Fp[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
-    Stencil s;
-    float bxo[3] = {gxo[p], gxo[n + p], gxo[2 * n + p]};
-    if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
+        for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
+        float bxo[3] = {gxo[p], gxo[n + p], gxo[2 * n + p]};
+        Stencil s;
+        if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) scratch[a * cap + p] = 0.0f;
+            for (int a = 0; a < 3; ++a) scratch[a * cap + p] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = 0.0f;
-        return;
+            for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = 0.0f;
+        } else {
+            const int N = P.N;
+            // recompute C' (v' is not needed: its adjoint only uses the weights)
+            float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const bool pin = pinned && pinned[p];
+            if (!pin) {
+#pragma unroll
+                for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+                    for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+                        for (int ok = 0; ok < 3; ++ok) {
+                            float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
+                            float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
+                                          ((float)ok - s.fx[2]) * P.dx};
+                            int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
+                            float4 gv = grid_v[id];
+                            float wv[3] = {W * gv.x, W * gv.y, W * gv.z};
+#pragma unroll
+                            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                                for (int b = 0; b < 3; ++b) Cn[3 * a + b] += wv[a] * d[b];
+                        }
+#pragma unroll
+                for (int k = 0; k < 9; ++k) Cn[k] *= P.D;
+            }
+            float bFo[9], bCo[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                bFo[k] = gFo[k * n + p];
+                bCo[k] = gCo[k * n + p];
+            }
+            // F' = (I + dt C') F  ->  bF_in = (I + dt C')^T bF', bC' += dt bF' F^T
+            float M[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) M[k] = P.dt * Cn[k];
+            M[0] += 1.0f;
+            M[4] += 1.0f;
+            M[8] += 1.0f;
+            float bFin[9], bFoFt[9];
+            mul3_atb(M, bFo, bFin);
+            mul3_abt(bFo, Fp, bFoFt);
+            float bC[9], bv[3];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) bC[k] = bCo[k] + P.dt * bFoFt[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) bv[a] = gvo[a * n + p] + P.dt * bxo[a];
+            float bx[3] = {bxo[0], bxo[1], bxo[2]};
+            if (!pin) {
+#pragma unroll
+                for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+                    for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+                        for (int ok = 0; ok < 3; ++ok) {
+                            float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
+                            float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
+                                          ((float)ok - s.fx[2]) * P.dx};
+                            int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
+                            float4 gv = grid_v[id];
+                            float vi[3] = {gv.x, gv.y, gv.z};
+                            float Cd[3], CtV[3];
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                Cd[a] = bC[3 * a] * d[0] + bC[3 * a + 1] * d[1] + bC[3 * a + 2] * d[2];
+                                CtV[a] = bC[a] * vi[0] + bC[3 + a] * vi[1] + bC[6 + a] * vi[2];
+                            }
+                            float bW = 0.0f;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) bW += vi[a] * (bv[a] + P.D * Cd[a]);
+                            float gW[3];
+                            weight_grad(P, s, oi, oj, ok, gW);
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) bx[a] += -P.D * W * CtV[a] + bW * gW[a];
+                        }
+                q.s = s;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) q.mv[a] = bv[a];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) q.A[k] = P.D * bC[k];
+                q.valid = true;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) scratch[a * cap + p] = bx[a];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = bFin[k];
+        }
     }
-    const int N = P.N;
-    // recompute C' (v' is not needed: its adjoint only uses the weights)
-    float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool pin = pinned && pinned[p];
-    if (!pin) {
-#pragma unroll
-        for (int oi = 0; oi < 3; ++oi)
-#pragma unroll
-            for (int oj = 0; oj < 3; ++oj)
-#pragma unroll
-                for (int ok = 0; ok < 3; ++ok) {
-                    float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
-                    float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
-                                  ((float)ok - s.fx[2]) * P.dx};
-                    int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
-                    float4 gv = grid_v[id];
-                    float wv[3] = {W * gv.x, W * gv.y, W * gv.z};
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) Cn[3 * a + b] += wv[a] * d[b];
-                }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Cn[k] *= P.D;
-    }
-    float bFo[9], bCo[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        bFo[k] = gFo[k * n + p];
-        bCo[k] = gCo[k * n + p];
-    }
-    // F' = (I + dt C') F  ->  bF_in = (I + dt C')^T bF', bC' += dt bF' F^T
-    float M[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) M[k] = P.dt * Cn[k];
-    M[0] += 1.0f;
-    M[4] += 1.0f;
-    M[8] += 1.0f;
-    float bFin[9], bFoFt[9];
-    mul3_atb(M, bFo, bFin);
-    mul3_abt(bFo, Fp, bFoFt);
-    float bC[9], bv[3];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) bC[k] = bCo[k] + P.dt * bFoFt[k];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) bv[a] = gvo[a * n + p] + P.dt * bxo[a];
-    float bx[3] = {bxo[0], bxo[1], bxo[2]};
-    if (!pin) {
-#pragma unroll
-        for (int oi = 0; oi < 3; ++oi)
-#pragma unroll
-            for (int oj = 0; oj < 3; ++oj)
-#pragma unroll
-                for (int ok = 0; ok < 3; ++ok) {
-                    float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
-                    float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
-                                  ((float)ok - s.fx[2]) * P.dx};
-                    int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
-                    float4 gv = grid_v[id];
-                    float vi[3] = {gv.x, gv.y, gv.z};
-                    float Cd[3], CtV[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Cd[a] = bC[3 * a] * d[0] + bC[3 * a + 1] * d[1] + bC[3 * a + 2] * d[2];
-                        CtV[a] = bC[a] * vi[0] + bC[3 + a] * vi[1] + bC[6 + a] * vi[2];
-                    }
-                    float bW = 0.0f;
-                    float4 add;
-                    add.x = W * (bv[0] + P.D * Cd[0]);
-                    add.y = W * (bv[1] + P.D * Cd[1]);
-                    add.z = W * (bv[2] + P.D * Cd[2]);
-                    add.w = 0.0f;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) bW += vi[a] * (bv[a] + P.D * Cd[a]);
-                    atomicAdd(&grid_bv[id], add);
-                    float gW[3];
-                    weight_grad(P, s, oi, oj, ok, gW);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) bx[a] += -P.D * W * CtV[a] + bW * gW[a];
-                }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) scratch[a * cap + p] = bx[a];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = bFin[k];
+    MpmParams Pz = P;
+    Pz.p_mass = 0.0f;  // no mass channel: grid_bv = (0, dL/dv_i)
+    const ActiveBlocks none{nullptr, nullptr, nullptr, 0, 0};
+    p2g_warp_scatter(Pz, q, grid_bv, none, rows[wid], keys[wid]);
 }
 
 // Reverse grid update of one node: (dL/dm_i, dL/dp_i) into grid_bmp, wind
@@ -212,15 +225,16 @@ __device__ __forceinline__ void rev_grid_node(const MpmParams &P, const WindDev 
     float4 mp = grid_mp[node];
     float4 bmp = make_float4(0.f, 0.f, 0.f, 0.f);
     if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
-        float4 b = grid_bv[node];
+        const float4 b4 = grid_bv[node];  // (0, dL/dv_i)
+        const float b[3] = {b4.y, b4.z, b4.w};
         float inv_m = 1.0f / mp.x;
-        bmp.y = b.x * inv_m;
-        bmp.z = b.y * inv_m;
-        bmp.w = b.z * inv_m;
-        bmp.x = -(mp.y * b.x + mp.z * b.y + mp.w * b.z) * inv_m * inv_m;
+        bmp.y = b[0] * inv_m;
+        bmp.z = b[1] * inv_m;
+        bmp.w = b[2] * inv_m;
+        bmp.x = -(mp.y * b[0] + mp.z * b[1] + mp.w * b[2]) * inv_m * inv_m;
         if (g_wind)
             wind_sample_adjoint_dev(wind, i * P.dx, j * P.dx, k * P.dx, t,
-                                    make_float3(P.dt * b.x, P.dt * b.y, P.dt * b.z), g_wind);
+                                    make_float3(P.dt * b[0], P.dt * b[1], P.dt * b[2]), g_wind);
     }
     grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     grid_bv[node] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -684,7 +698,7 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
     if (st != DW_OK) return st;
     if (n > 0) {
         ProfScope ps(h, DW_K_REV_G2P, s);
-        k_rev_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v,
+        k_rev_g2p<<<grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v,
                                                    g_out->x, g_out->v, g_out->C, g_out->F,
                                                    h->grid_bv, h->pscratch, n, cap);
         DW_LAUNCHED("k_rev_g2p");
@@ -701,6 +715,49 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
                                                    h->pscratch, g_in->x, g_in->v, g_in->C,
                                                    g_in->F, g_E, n, cap, h->block_count);
         DW_LAUNCHED("k_rev_p2g");
+    }
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, float *tape,
+                                         int64_t tape_floats, const dw_mpm_state *g,
+                                         const uint8_t *pinned, const dw_wind_field *wind,
+                                         float t0, int32_t n_substeps, float *g_wind, float *g_E,
+                                         dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_state(h, start, "start");
+    if (st != DW_OK) return st;
+    st = check_state(h, g, "gradient");
+    if (st != DW_OK) return st;
+    DW_REQUIRE(start->n == g->n, "start and gradient particle counts differ");
+    DW_REQUIRE(n_substeps >= 0, "n_substeps must be >= 0");
+    const int64_t n = start->n;
+    if (n_substeps == 0) return DW_OK;
+    const int64_t need = (int64_t)(n_substeps - 1) * 24 * n;
+    DW_REQUIRE(n_substeps == 1 || (tape && tape_floats >= need),
+               "tape holds %lld floats; %d substeps of %lld particles need %lld",
+               (long long)tape_floats, n_substeps, (long long)n, (long long)need);
+    const float dt = h->P.dt;
+    auto slot = [&](int k) {  // state k (1 .. n_substeps - 1) in the tape
+        dw_mpm_state s;
+        float *b = tape + (size_t)(k - 1) * 24 * (size_t)n;
+        s.x = b;
+        s.v = b + 3 * n;
+        s.C = b + 6 * n;
+        s.F = b + 15 * n;
+        s.n = n;
+        return s;
+    };
+    for (int k = 1; k < n_substeps; ++k) {
+        const dw_mpm_state in = k == 1 ? *start : slot(k - 1), out = slot(k);
+        st = mpm_substep(h, &in, &out, pinned, wind, fmaf((float)(k - 1), dt, t0), stream);
+        if (st != DW_OK) return st;
+    }
+    for (int j = n_substeps - 1; j >= 0; --j) {
+        const dw_mpm_state in = j == 0 ? *start : slot(j);
+        st = mpm_substep_adjoint(h, &in, g, g, pinned, wind, fmaf((float)j, dt, t0), g_wind, g_E,
+                                 stream);
+        if (st != DW_OK) return st;
     }
     return DW_OK;
 }

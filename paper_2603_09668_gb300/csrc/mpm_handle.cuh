@@ -19,7 +19,7 @@ struct MpmHandle {
     int64_t n_nodes;
     float4 *grid_mp = nullptr;   // (m, p) after P2G; zero between calls
     float4 *grid_v = nullptr;    // (v, m) after the grid update
-    float4 *grid_bv = nullptr;   // dL/dv_i during the adjoint; zero between calls
+    float4 *grid_bv = nullptr;   // (0, dL/dv_i) during the adjoint; zero between calls
     float4 *grid_bmp = nullptr;  // (dL/dm_i, dL/dp_i) during the adjoint
     float *pscratch = nullptr;   // [12][max_particles]: partial dL/dx (3), dL/dF (9)
     int *err = nullptr;          // device status bits
