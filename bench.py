@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch"],
                     help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
                          "or the checkpointed MPM adjoint")
+    ap.add_argument("--batch-scenes", type=int, default=64,
+                    help="scenes of the batched workload (--only batch; 64 in the full run)")
     ap.add_argument("--p2g-mode", type=int, default=0,
                     help="P2G strategy: 0 auto, 1 global atomics, 2 warp-aggregated, 3 shared tile")
     return ap.parse_args()
@@ -298,6 +300,13 @@ def estimate_active_nodes(ro, sc):
     return int(np.unique(lin).size)
 
 
+# DRAM bytes (read + write) per launch of k_g2p2g on the 400,040-particle sheet
+# from one ncu capture of the current kernel (profiles/mpm_rollout_sheet400k.md,
+# "DRAM traffic of k_g2p2g"); to be re-measured whenever that kernel changes.
+G2P2G_DRAM_BYTES_SHEET400K = 20.07e6
+SHEET_PARTICLES = 400040
+
+
 def roofline(prof, n, active_nodes):
     """Algorithmic bytes per launch of each substep kernel:
       P2G   : x, v, C, F read (96 B / particle) + (m, p) written (16 B / node)
@@ -323,10 +332,13 @@ def roofline(prof, n, active_nodes):
     else:
         traffic = None
     achieved = traffic / avg_s / 1e9 if traffic else None
+    measured = G2P2G_DRAM_BYTES_SHEET400K if (k == "g2p2g" and n == SHEET_PARTICLES) else None
     return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": measured,
             "algorithmic_bytes_per_launch": traffic, "avg_launch_us": avg_s * 1e6,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                              "profiles/mpm_rollout_sheet400k.md" if measured else None}
 
 
 def _timed(fn, reps=3):
@@ -509,7 +521,7 @@ def extras(dev):
     return out
 
 
-def cpu_baseline(n_sub=30):
+def cpu_baseline(n_sub=75):
     """The FP64 oracle on this host: n_sub substeps of the full 400k sheet."""
     import oracle
     from paper_2603_09668_gb300 import inputs
@@ -578,7 +590,7 @@ def run_only(args):
     elif args.only == "surrogate":
         res = bench_surrogate(dev)
     elif args.only == "batch":
-        res = bench_batch(dev)
+        res = bench_batch(dev, n_scenes=args.batch_scenes)
     else:
         res = bench_adjoint(dev)
     print(json.dumps({"only": args.only, **res}), flush=True)
