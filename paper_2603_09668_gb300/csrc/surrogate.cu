@@ -269,84 +269,102 @@ __global__ void k_surr_apply(const float *__restrict__ out, float out_scale,
 // interpolation of k_surr_apply; rho kept) on every fluid fine cell, then the
 // coarse features of the updated state (the arithmetic and summation order of
 // k_surr_coarse), so that the next network call can run directly.
-// A block of 128 threads covers 16 coarse voxels along x at one (y, z): warp
-// w = by + 2 bz takes fine row (2y + by, 2z + bz), lane l fine x = 2 x0 + l,
-// so every warp access is 32 consecutive cells. The 18 x 3 x 3 coarse outputs
-// the block interpolates from are staged in shared memory first.
-constexpr int ADV_VX = 16;  // coarse voxels per block along x
-__global__ void __launch_bounds__(128) k_surr_advance_fine(
+// A block covers ADV_VX x ADV_VY x ADV_VZ coarse voxels; its threads are the
+// fine cells (x fastest: a warp is 32 consecutive cells of one fine row), and
+// the coarse outputs the block interpolates from, (ADV_VX + 2) x (ADV_VY + 2)
+// x (ADV_VZ + 2) voxels, are staged in shared memory first.
+constexpr int ADV_VX = 16, ADV_VY = 2, ADV_VZ = 2;
+constexpr int ADV_THREADS = 8 * ADV_VX * ADV_VY * ADV_VZ;  // 512 fine cells
+__global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
     const float *__restrict__ out, float out_scale, float *__restrict__ fine,
     const uint8_t *__restrict__ solid, int n, float in_scale, bf16 *__restrict__ feats) {
-    __shared__ float du[3][3][ADV_VX + 2][3];  // coarse (z, y, x) around the block
-    __shared__ float part[8][ADV_VX][4];       // per fine cell k: (rho - 1, u) or 0
-    __shared__ int isf[8][ADV_VX];
-    const int bxs = n / ADV_VX;
+    constexpr int SX = ADV_VX + 2, SY = ADV_VY + 2, SZ = ADV_VZ + 2;
+    constexpr int NV = ADV_VX * ADV_VY * ADV_VZ;
+    __shared__ float du[SZ][SY][SX][3];   // coarse (z, y, x) around the block
+    __shared__ float part[8][NV][4];      // per fine cell k of each voxel: (rho - 1, u) or 0
+    __shared__ int isf[8][NV];
+    const int bxs = n / ADV_VX, bys = n / ADV_VY;
     const int x0 = (blockIdx.x % bxs) * ADV_VX;
-    const int y = (blockIdx.x / bxs) % n, z = blockIdx.x / (bxs * n);
-    for (int e = threadIdx.x; e < 3 * 3 * (ADV_VX + 2); e += blockDim.x) {
-        const int ex = e % (ADV_VX + 2), ey = (e / (ADV_VX + 2)) % 3, ez = e / (3 * (ADV_VX + 2));
-        const int cx = min(max(x0 - 1 + ex, 0), n - 1), cy = min(max(y - 1 + ey, 0), n - 1);
-        const int cz = min(max(z - 1 + ez, 0), n - 1);
-        const float *o = out + (((int64_t)cz * n + cy) * n + cx) * 16;
-        du[ez][ey][ex][0] = __ldg(o);
-        du[ez][ey][ex][1] = __ldg(o + 1);
-        du[ez][ey][ex][2] = __ldg(o + 2);
-    }
-    __syncthreads();
+    const int y0 = ((blockIdx.x / bxs) % bys) * ADV_VY;
+    const int z0 = (blockIdx.x / (bxs * bys)) * ADV_VZ;
+    static_assert(SX * SY * SZ <= ADV_THREADS, "one staged voxel per thread");
     const int N = 2 * n;
     const int64_t nc = (int64_t)N * N * N;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int by = w & 1, bz = w >> 1, bx = lane & 1, vx = lane >> 1;
-    const int fi[3] = {2 * x0 + lane, 2 * y + by, 2 * z + bz};
+    // fine cell of this thread: (fx, fy, fz) within the block's 2 ADV_VX x 2 ADV_VY x 2 ADV_VZ
+    const int t = threadIdx.x;
+    const int lx = t % (2 * ADV_VX), ly = (t / (2 * ADV_VX)) % (2 * ADV_VY), lz = t / (4 * ADV_VX * ADV_VY);
+    const int fi[3] = {2 * x0 + lx, 2 * y0 + ly, 2 * z0 + lz};
     const int64_t c = ((int64_t)fi[2] * N + fi[1]) * N + fi[0];
-    const int k = bx + 2 * by + 4 * bz;  // the cell's place in the coarse voxel
+    // every load of the thread is issued before the first barrier: the staged
+    // coarse voxel, and the fine cell's rho, u and mask (solid cells hold
+    // rho = 1, u = 0 and are read but never written)
+    float st0 = 0.f, st1 = 0.f, st2 = 0.f;
+    if (t < SX * SY * SZ) {
+        const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
+        const int cx = min(max(x0 - 1 + ex, 0), n - 1), cy = min(max(y0 - 1 + ey, 0), n - 1);
+        const int cz = min(max(z0 - 1 + ez, 0), n - 1);
+        const float *o = out + (((int64_t)cz * n + cy) * n + cx) * 16;
+        st0 = __ldg(o);
+        st1 = __ldg(o + 1);
+        st2 = __ldg(o + 2);
+    }
+    const float rho = fine[c], u0 = fine[nc + c], u1 = fine[2 * nc + c], u2 = fine[3 * nc + c];
+    const bool is_solid = solid && solid[c];
+    if (t < SX * SY * SZ) {
+        const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
+        du[ez][ey][ex][0] = st0;
+        du[ez][ey][ex][1] = st1;
+        du[ez][ey][ex][2] = st2;
+    }
+    __syncthreads();
+    const int k = (lx & 1) + 2 * (ly & 1) + 4 * (lz & 1);  // the cell's place in its voxel
+    const int vl = ((lz >> 1) * ADV_VY + (ly >> 1)) * ADV_VX + (lx >> 1);  // voxel within block
     float contrib[4] = {0.f, 0.f, 0.f, 0.f};
     int fl = 0;
-    if (!(solid && solid[c])) {
+    if (!is_solid) {
         int i0[3];
-        float t[3];
+        float tt[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float sa = fminf(fmaxf(fi[a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
             int i = min((int)floorf(sa), n - 2);
             i0[a] = i;
-            t[a] = sa - (float)i;
+            tt[a] = sa - (float)i;
         }
         float d[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int cx = q & 1, cy = (q >> 1) & 1, cz = q >> 2;
-            const float wq = (cx ? t[0] : 1.f - t[0]) * (cy ? t[1] : 1.f - t[1]) * (cz ? t[2] : 1.f - t[2]);
-            const float *o = du[i0[2] + cz - (z - 1)][i0[1] + cy - (y - 1)][i0[0] + cx - (x0 - 1)];
+            const float wq = (cx ? tt[0] : 1.f - tt[0]) * (cy ? tt[1] : 1.f - tt[1]) * (cz ? tt[2] : 1.f - tt[2]);
+            const float *o = du[i0[2] + cz - (z0 - 1)][i0[1] + cy - (y0 - 1)][i0[0] + cx - (x0 - 1)];
             d[0] += wq * o[0];
             d[1] += wq * o[1];
             d[2] += wq * o[2];
         }
-        const float ux = fine[nc + c] + out_scale * d[0];
-        const float uy = fine[2 * nc + c] + out_scale * d[1];
-        const float uz = fine[3 * nc + c] + out_scale * d[2];
+        const float ux = u0 + out_scale * d[0];
+        const float uy = u1 + out_scale * d[1];
+        const float uz = u2 + out_scale * d[2];
         fine[nc + c] = ux;
         fine[2 * nc + c] = uy;
         fine[3 * nc + c] = uz;
-        contrib[0] = fine[c] - 1.0f;
+        contrib[0] = rho - 1.0f;
         contrib[1] = ux;
         contrib[2] = uy;
         contrib[3] = uz;
         fl = 1;
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) part[k][vx][a] = contrib[a];
-    isf[k][vx] = fl;
+    for (int a = 0; a < 4; ++a) part[k][vl][a] = contrib[a];
+    isf[k][vl] = fl;
     __syncthreads();
-    if (threadIdx.x < ADV_VX) {
-        const int v = threadIdx.x;
+    if (t < NV) {
         float sum[4] = {0.f, 0.f, 0.f, 0.f};
         int fluid = 0;
         for (int kk = 0; kk < 8; ++kk) {
-            if (!isf[kk][v]) continue;
+            if (!isf[kk][t]) continue;
             ++fluid;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) sum[a] += part[kk][v][a];
+            for (int a = 0; a < 4; ++a) sum[a] += part[kk][t][a];
         }
         const float inv = fluid > 0 ? in_scale / (float)fluid : 0.0f;
         __align__(16) bf16 o8[8];
@@ -356,7 +374,8 @@ __global__ void __launch_bounds__(128) k_surr_advance_fine(
         for (int ch = 0; ch < 4; ++ch) o8[ch] = __float2bfloat16_rn(sum[ch] * inv);
         o8[4] = __float2bfloat16_rn((8 - fluid) * 0.125f);
         const int64_t nv = (int64_t)n * n * n;
-        const int64_t cv = ((int64_t)z * n + y) * n + x0 + v;
+        const int vx = t % ADV_VX, vy = (t / ADV_VX) % ADV_VY, vz = t / (ADV_VX * ADV_VY);
+        const int64_t cv = ((int64_t)(z0 + vz) * n + (y0 + vy)) * n + x0 + vx;
         reinterpret_cast<uint4 *>(feats)[cv] = *reinterpret_cast<const uint4 *>(o8);   // channels 0-7
         reinterpret_cast<uint4 *>(feats)[nv + cv] = make_uint4(0u, 0u, 0u, 0u);       // channels 8-15
     }
@@ -837,7 +856,8 @@ extern "C" dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float i
 extern "C" dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *solid,
                                        float in_scale, dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
-    k_surr_advance_fine<<<(unsigned)(h->nv / ADV_VX), 128, 0, as_stream(stream)>>>(
+    k_surr_advance_fine<<<(unsigned)(h->nv / (ADV_VX * ADV_VY * ADV_VZ)), ADV_THREADS, 0,
+                          as_stream(stream)>>>(
         h->out, out_scale, h->fine, solid, h->n, in_scale, h->feats);
     DW_LAUNCHED("k_surr_advance_fine");
     return DW_OK;
