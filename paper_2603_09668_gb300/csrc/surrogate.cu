@@ -22,8 +22,8 @@ struct SurrHandle {
     int64_t nparams = 0;
     int64_t off_w[4] = {0, 0, 0, 0}, off_b[4] = {0, 0, 0, 0};
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *wf = nullptr;  // forward weights, per layer [27][cin/8][cout][8]
-    bf16 *wd = nullptr;  // input-gradient weights, per layer [27][cout/8][cin][8], taps mirrored
+    bf16 *wf = nullptr;  // forward weights, per layer [9][cin/8][3][cout][8]
+    bf16 *wd = nullptr;  // input-gradient weights, per layer [9][cout/8][3][cin][8], taps mirrored
     int64_t woff[4] = {0, 0, 0, 0};
     bf16 *feats = nullptr;          // [nv][16]
     bf16 *z[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};  // [nv][32]
@@ -44,9 +44,10 @@ struct SurrHandle {
 // ------------------------------------------------------------- kernels ----
 
 // BF16 copies of the layer weights in the tensor-core operand layout
-// [tap][cin/8][cout][8] (core matrices of 8 output channels x 8 input
-// channels): wf for the forward convolution, wd for the input gradient (taps
-// mirrored, input and output channels swapped: [tap'][cout/8][cin][8]).
+// [9 (dy, dx)][cin/8][3 (dz)][cout][8] (core matrices of 8 output channels x 8
+// input channels; the three dz taps of one (dx, dy) form one operand): wf for
+// the forward convolution, wd for the input gradient (taps mirrored, input
+// and output channels swapped).
 __global__ void k_surr_weights(const float *__restrict__ params, bf16 *__restrict__ wf,
                                bf16 *__restrict__ wd, int64_t off_w, int64_t woff, int cin,
                                int cout) {
@@ -55,8 +56,9 @@ __global__ void k_surr_weights(const float *__restrict__ params, bf16 *__restric
     if (i >= cnt) return;
     const int ci = (int)(i % cin), co = (int)((i / cin) % cout), t = (int)(i / ((int64_t)cin * cout));
     const bf16 w = __float2bfloat16_rn(params[off_w + i]);
-    wf[woff + (((int64_t)t * (cin / 8) + ci / 8) * cout + co) * 8 + (ci & 7)] = w;
-    wd[woff + (((int64_t)(26 - t) * (cout / 8) + co / 8) * cin + ci) * 8 + (co & 7)] = w;
+    const int t2 = 26 - t;  // tap of the input-gradient convolution
+    wf[woff + ((((int64_t)(t % 9) * (cin / 8) + ci / 8) * 3 + t / 9) * cout + co) * 8 + (ci & 7)] = w;
+    wd[woff + ((((int64_t)(t2 % 9) * (cout / 8) + co / 8) * 3 + t2 / 9) * cin + ci) * 8 + (co & 7)] = w;
 }
 
 __device__ __constant__ int kCX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0};
@@ -269,17 +271,20 @@ __global__ void k_surr_apply(const float *__restrict__ out, float out_scale,
 // interpolation of k_surr_apply; rho kept) on every fluid fine cell, then the
 // coarse features of the updated state (the arithmetic and summation order of
 // k_surr_coarse), so that the next network call can run directly.
-// A block covers ADV_VX x ADV_VY x ADV_VZ coarse voxels; its threads are the
-// fine cells (x fastest: a warp is 32 consecutive cells of one fine row), and
-// the coarse outputs the block interpolates from, (ADV_VX + 2) x (ADV_VY + 2)
-// x (ADV_VZ + 2) voxels, are staged in shared memory first.
-constexpr int ADV_VX = 16, ADV_VY = 2, ADV_VZ = 2;
-constexpr int ADV_THREADS = 8 * ADV_VX * ADV_VY * ADV_VZ;  // 512 fine cells
+// A block covers ADV_VX x ADV_VY x ADV_VZ coarse voxels; each thread takes two
+// of their fine cells, ADV_VZ fine slices apart (x fastest: a warp covers 32
+// consecutive cells of one fine row), so that every thread has two
+// independent sets of loads in flight; the coarse outputs the block
+// interpolates from, (ADV_VX + 2) x (ADV_VY + 2) x (ADV_VZ + 2) voxels, are
+// staged in shared memory first.
+constexpr int ADV_VX = 16, ADV_VY = 2, ADV_VZ = 4;
+constexpr int ADV_THREADS = 4 * ADV_VX * ADV_VY * ADV_VZ;  // two fine cells per thread
 __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
     const float *__restrict__ out, float out_scale, float *__restrict__ fine,
     const uint8_t *__restrict__ solid, int n, float in_scale, bf16 *__restrict__ feats) {
     constexpr int SX = ADV_VX + 2, SY = ADV_VY + 2, SZ = ADV_VZ + 2;
     constexpr int NV = ADV_VX * ADV_VY * ADV_VZ;
+    static_assert(SX * SY * SZ <= ADV_THREADS, "one staged voxel per thread");
     __shared__ float du[SZ][SY][SX][3];   // coarse (z, y, x) around the block
     __shared__ float part[8][NV][4];      // per fine cell k of each voxel: (rho - 1, u) or 0
     __shared__ int isf[8][NV];
@@ -287,17 +292,16 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
     const int x0 = (blockIdx.x % bxs) * ADV_VX;
     const int y0 = ((blockIdx.x / bxs) % bys) * ADV_VY;
     const int z0 = (blockIdx.x / (bxs * bys)) * ADV_VZ;
-    static_assert(SX * SY * SZ <= ADV_THREADS, "one staged voxel per thread");
     const int N = 2 * n;
     const int64_t nc = (int64_t)N * N * N;
-    // fine cell of this thread: (fx, fy, fz) within the block's 2 ADV_VX x 2 ADV_VY x 2 ADV_VZ
     const int t = threadIdx.x;
-    const int lx = t % (2 * ADV_VX), ly = (t / (2 * ADV_VX)) % (2 * ADV_VY), lz = t / (4 * ADV_VX * ADV_VY);
-    const int fi[3] = {2 * x0 + lx, 2 * y0 + ly, 2 * z0 + lz};
-    const int64_t c = ((int64_t)fi[2] * N + fi[1]) * N + fi[0];
-    // every load of the thread is issued before the first barrier: the staged
-    // coarse voxel, and the fine cell's rho, u and mask (solid cells hold
-    // rho = 1, u = 0 and are read but never written)
+    // the thread's two fine cells: (lx, ly, lz) and (lx, ly, lz + 2 ADV_VZ / 2) of the
+    // block's 2 ADV_VX x 2 ADV_VY x 2 ADV_VZ cells
+    const int lx = t % (2 * ADV_VX), ly = (t / (2 * ADV_VX)) % (2 * ADV_VY);
+    const int lzb = t / (4 * ADV_VX * ADV_VY);  // 0 .. ADV_VZ - 1
+    // every load is issued before the first barrier: the staged coarse voxel
+    // and both fine cells' rho, u and mask (solid cells hold rho = 1, u = 0 and
+    // are read but never written)
     float st0 = 0.f, st1 = 0.f, st2 = 0.f;
     if (t < SX * SY * SZ) {
         const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
@@ -308,8 +312,23 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
         st1 = __ldg(o + 1);
         st2 = __ldg(o + 2);
     }
-    const float rho = fine[c], u0 = fine[nc + c], u1 = fine[2 * nc + c], u2 = fine[3 * nc + c];
-    const bool is_solid = solid && solid[c];
+    int fi[2][3];
+    int64_t c[2];
+    float rho[2], u0[2], u1[2], u2[2];
+    bool is_solid[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int lz = lzb + h * ADV_VZ;
+        fi[h][0] = 2 * x0 + lx;
+        fi[h][1] = 2 * y0 + ly;
+        fi[h][2] = 2 * z0 + lz;
+        c[h] = ((int64_t)fi[h][2] * N + fi[h][1]) * N + fi[h][0];
+        rho[h] = fine[c[h]];
+        u0[h] = fine[nc + c[h]];
+        u1[h] = fine[2 * nc + c[h]];
+        u2[h] = fine[3 * nc + c[h]];
+        is_solid[h] = solid && solid[c[h]];
+    }
     if (t < SX * SY * SZ) {
         const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
         du[ez][ey][ex][0] = st0;
@@ -317,45 +336,49 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
         du[ez][ey][ex][2] = st2;
     }
     __syncthreads();
-    const int k = (lx & 1) + 2 * (ly & 1) + 4 * (lz & 1);  // the cell's place in its voxel
-    const int vl = ((lz >> 1) * ADV_VY + (ly >> 1)) * ADV_VX + (lx >> 1);  // voxel within block
-    float contrib[4] = {0.f, 0.f, 0.f, 0.f};
-    int fl = 0;
-    if (!is_solid) {
-        int i0[3];
-        float tt[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float sa = fminf(fmaxf(fi[a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
-            int i = min((int)floorf(sa), n - 2);
-            i0[a] = i;
-            tt[a] = sa - (float)i;
-        }
-        float d[3] = {0.f, 0.f, 0.f};
+    for (int h = 0; h < 2; ++h) {
+        const int lz = lzb + h * ADV_VZ;
+        const int k = (lx & 1) + 2 * (ly & 1) + 4 * (lz & 1);  // the cell's place in its voxel
+        const int vl = ((lz >> 1) * ADV_VY + (ly >> 1)) * ADV_VX + (lx >> 1);  // voxel within block
+        float contrib[4] = {0.f, 0.f, 0.f, 0.f};
+        int fl = 0;
+        if (!is_solid[h]) {
+            int i0[3];
+            float tt[3];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int cx = q & 1, cy = (q >> 1) & 1, cz = q >> 2;
-            const float wq = (cx ? tt[0] : 1.f - tt[0]) * (cy ? tt[1] : 1.f - tt[1]) * (cz ? tt[2] : 1.f - tt[2]);
-            const float *o = du[i0[2] + cz - (z0 - 1)][i0[1] + cy - (y0 - 1)][i0[0] + cx - (x0 - 1)];
-            d[0] += wq * o[0];
-            d[1] += wq * o[1];
-            d[2] += wq * o[2];
+            for (int a = 0; a < 3; ++a) {
+                float sa = fminf(fmaxf(fi[h][a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
+                int i = min((int)floorf(sa), n - 2);
+                i0[a] = i;
+                tt[a] = sa - (float)i;
+            }
+            float d[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int cx = q & 1, cy = (q >> 1) & 1, cz = q >> 2;
+                const float wq = (cx ? tt[0] : 1.f - tt[0]) * (cy ? tt[1] : 1.f - tt[1]) * (cz ? tt[2] : 1.f - tt[2]);
+                const float *o = du[i0[2] + cz - (z0 - 1)][i0[1] + cy - (y0 - 1)][i0[0] + cx - (x0 - 1)];
+                d[0] += wq * o[0];
+                d[1] += wq * o[1];
+                d[2] += wq * o[2];
+            }
+            const float ux = u0[h] + out_scale * d[0];
+            const float uy = u1[h] + out_scale * d[1];
+            const float uz = u2[h] + out_scale * d[2];
+            fine[nc + c[h]] = ux;
+            fine[2 * nc + c[h]] = uy;
+            fine[3 * nc + c[h]] = uz;
+            contrib[0] = rho[h] - 1.0f;
+            contrib[1] = ux;
+            contrib[2] = uy;
+            contrib[3] = uz;
+            fl = 1;
         }
-        const float ux = u0 + out_scale * d[0];
-        const float uy = u1 + out_scale * d[1];
-        const float uz = u2 + out_scale * d[2];
-        fine[nc + c] = ux;
-        fine[2 * nc + c] = uy;
-        fine[3 * nc + c] = uz;
-        contrib[0] = rho - 1.0f;
-        contrib[1] = ux;
-        contrib[2] = uy;
-        contrib[3] = uz;
-        fl = 1;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) part[k][vl][a] = contrib[a];
+        isf[k][vl] = fl;
     }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) part[k][vl][a] = contrib[a];
-    isf[k][vl] = fl;
     __syncthreads();
     if (t < NV) {
         float sum[4] = {0.f, 0.f, 0.f, 0.f};
@@ -477,19 +500,16 @@ template <int CIN, int COUT, int EPI>
 static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, const float *bias,
                       bf16 *oz, bf16 *oa, float *of, const bf16 *zprev, cudaStream_t s,
                       bool pdl = true) {
-    constexpr size_t smem = tc_smem<CIN, COUT>();
-    static int per_sm = 0;  // resident CTAs per SM of this instantiation
-    if (per_sm == 0) {
+    // The kernel allocates the whole tensor memory of its SM, so the shared
+    // memory request is raised above half an SM's to keep one CTA per SM.
+    constexpr size_t smem = tc_smem<CIN, COUT>() > 120 * 1024 ? tc_smem<CIN, COUT>() : 120 * 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
         DW_CUDA(cudaFuncSetAttribute(k_conv3_tc<CIN, COUT, EPI>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int occ = 0;
-        DW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3_tc<CIN, COUT, EPI>,
-                                                              TC_THREADS, smem));
-        per_sm = occ > 0 ? occ : 1;
+        attr_set = true;
     }
-    const int ntiles = (h->n / TC_TX) * (h->n / TC_TY) * h->n;
-    const int ctas = per_sm * h->sms;  // one wave: every CTA is resident
-    const int grid = ntiles < ctas ? ntiles : ctas;
+    const int grid = h->sms;  // one CTA per SM; each takes a contiguous range of output slices
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(TC_THREADS);
@@ -506,7 +526,7 @@ static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, c
 }
 
 // TMA descriptor of a planar [C/8][n][n][n][8] BF16 volume, box = one
-// 8-channel plane of a 10 x 18 x 3 halo, zero fill outside.
+// 8-channel plane of the 10 x 18 halo of one z slice, zero fill outside.
 static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -523,7 +543,7 @@ static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) 
     const cuuint64_t nn = (cuuint64_t)n;
     const cuuint64_t dims[5] = {8, nn, nn, nn, (cuuint64_t)(C / 8)};
     const cuuint64_t strides[4] = {16, 16 * nn, 16 * nn * nn, 16 * nn * nn * nn};
-    const cuuint32_t box[5] = {8, TC_HX, TC_HY, 3, 1};
+    const cuuint32_t box[5] = {8, TC_HX, TC_HY, 1, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims,
                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,

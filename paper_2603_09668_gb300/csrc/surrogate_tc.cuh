@@ -8,30 +8,22 @@
 // a tile's halo is one contiguous run of 16-byte voxel records.
 //
 // The convolution out[v][co] = sum_{tap, ci} W[tap][co][ci] in[v + d(tap)][ci]
-// (zero padding) is an implicit GEMM: for an output tile of 8 (x) x 16 (y) x
-// 1 (z) voxels, M = 128 voxels, N = COUT, K = 27 taps x CIN. The input halo
-// of the tile (10 x 18 x 3 voxels) is loaded by TMA, one box per 8-channel
-// plane (box {8 ch, 10, 18, 3, 1} of the 5D view [C/8][z][y][x][8], zero fill
-// outside the volume), so that each plane lands as 16-byte voxel rows ordered
-// (z, y, x). In that
-// "chunk plane" layout the A operand of every tap is a plain shared-memory
-// matrix descriptor without swizzling: the 8 x-voxels of one tile row form a
-// core matrix (8 rows x 16 B, contiguous), tile rows are 10 voxels (160 B)
-// apart (stride-dimension offset), and the next 8 channels are one plane
-// further (leading-dimension offset). Shifting the descriptor's start by the
-// tap's voxel offset selects the tap: no im2col copy exists anywhere.
-// The weights sit in shared memory as [tap][chunk][co][8 ci] (core matrices
-// of 8 output channels x 16 B).
-//
-// Per tile one thread waits for the halo, issues 27 x CIN/16 MMAs
-// (128 x COUT x 16 each) into a 32-column tensor-memory accumulator and
-// commits them to an mbarrier; when they complete, the halo of the next tile
-// is requested (overlapping the epilogue) and the four warps read their 32
-// accumulator lanes (one voxel per thread) with tcgen05.ld, add the bias,
-// apply the epilogue and store channels-last. Every wait is bounded; a wait
-// that runs out sets the error word, drains what is in flight (bounded) and
-// frees the tensor memory before the kernel returns.
+// (zero padding) is an implicit GEMM over output tiles of 8 (x) x 16 (y)
+// voxels (M = 128 rows). A CTA streams along z through the input slices of
+// its output range; for each slice the 10 x 18 halo is loaded by TMA, one box
+// per 8-channel plane (box {8 ch, 10, 18, 1, 1} of the 5D view
+// [C/8][z][y][x][8], zero fill outside the volume), so that each plane lands
+// as 16-byte voxel rows ordered (y, x). In that layout the A operand of every
+// (dx, dy) tap is a plain shared-memory matrix descriptor without swizzling:
+// the 8 x-voxels of one tile row form a core matrix (8 rows x 16 B,
+// contiguous), tile rows are 10 voxels (160 B) apart (stride-dimension
+// offset), and the next 8 channels are one plane further (leading-dimension
+// offset); shifting the descriptor's start selects the tap. The B operand
+// holds the weights of the three dz taps of that (dx, dy) together, so one
+// MMA has N = 3 COUT and delivers the slice's contributions to three output
+// slices at once (a 128 x 32 x 16 MMA costs nearly as much as 128 x 96 x 16).
 #pragma once
+
 
 #include <cuda.h>
 
@@ -41,8 +33,6 @@ namespace dw {
 
 constexpr int TC_TX = 8, TC_TY = 16;                 // output tile (x, y), z = 1
 constexpr int TC_HX = TC_TX + 2, TC_HY = TC_TY + 2;  // halo 10 x 18 x 3
-constexpr int TC_PLANE_BYTES = TC_HX * TC_HY * 3 * 16;   // 8640 B of one chunk
-constexpr int TC_PLANE = 8704;                        // plane stride, 128-B aligned
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     // shared-memory matrix descriptor: start, leading and stride byte offsets
@@ -93,23 +83,6 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// TMA loads of the halo planes of the tile at (x0, y0, z0), completing on bar.
-template <int CIN>
-__device__ __forceinline__ void tc_load_halo(const CUtensorMap *tm, uint32_t halo, uint32_t bar,
-                                             int x0, int y0, int z0) {
-    constexpr int KCH = CIN / 8;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"(KCH * TC_PLANE_BYTES) : "memory");
-#pragma unroll
-    for (int c = 0; c < KCH; ++c)
-        asm volatile(
-            "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-            :: "r"(halo + c * TC_PLANE), "l"((uint64_t)tm), "r"(0), "r"(x0 - 1), "r"(y0 - 1),
-               "r"(z0 - 1), "r"(c), "r"(bar)
-            : "memory");
-}
-
 // tcgen05.ld of N consecutive 32-bit accumulator columns of this warp's 32
 // lanes (one row per thread).
 template <int N>
@@ -128,6 +101,17 @@ __device__ __forceinline__ void tc_ld<16>(uint32_t taddr, float (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+template <>
+__device__ __forceinline__ void tc_ld<4>(uint32_t taddr, float (&r)[4]) {
+    uint32_t u[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = __uint_as_float(u[i]);
 }
 
 template <>
@@ -155,25 +139,86 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  :: "r"(bar) : "memory");
 }
 
-constexpr int TC_NST = 3;        // halo stages
+constexpr int TC_NST = 8;        // halo stages (one input slice each)
+constexpr int TC_LAG = 3;        // a stage is refilled once the MMAs of slice k - TC_LAG are done
 constexpr int TC_EPI_WARPS = 8;  // epilogue warps: lane quarter = warp & 3, column half = warp >> 2
 constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 1);  // + one producer / MMA warp
-constexpr int TC_TMEM_COLS = 64;                      // two 32-column accumulators
+constexpr int TC_TMEM_COLS = 512;                     // the whole tensor memory of the SM
+constexpr int TC_NWIN = 5;       // accumulator windows (one input slice each)
+constexpr int TC_RING = 8;       // slice-ready barrier ring (>= TC_NWIN + 2)
+constexpr int TC_SLICE_BYTES = TC_HX * TC_HY * 16;    // 2880 B: one plane of a 10 x 18 slice halo
+constexpr int TC_SLICE = 2944;                        // plane stride, 128-B aligned
 
 template <int CIN, int COUT>
 constexpr size_t tc_smem() {
-    return (size_t)TC_NST * (CIN / 8) * TC_PLANE + (size_t)27 * (CIN / 8) * COUT * 16 + 1024;
+    return (size_t)TC_NST * (CIN / 8) * TC_SLICE + (size_t)27 * (CIN / 8) * COUT * 16 + 1024;
+}
+
+// TMA loads of the halo planes of input slice z of the xy tile at (x0, y0).
+template <int CIN>
+__device__ __forceinline__ void tc_load_slice(const CUtensorMap *tm, uint32_t halo, uint32_t bar,
+                                              int x0, int y0, int z) {
+    constexpr int KCH = CIN / 8;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"(KCH * TC_SLICE_BYTES) : "memory");
+#pragma unroll
+    for (int c = 0; c < KCH; ++c)
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+            :: "r"(halo + c * TC_SLICE), "l"((uint64_t)tm), "r"(0), "r"(x0 - 1), "r"(y0 - 1),
+               "r"(z), "r"(c), "r"(bar)
+            : "memory");
+}
+
+// The CTA's output work as segments: output slices o0..o1 of one xy tile.
+struct TcSeg {
+    int xy, o0, o1;
+};
+
+// Segment j of the CTA's contiguous range of (xy tile, z) output units;
+// false past the end. Segments stop at xy boundaries.
+__device__ __forceinline__ bool tc_segment(int n, int nxy, int j, TcSeg &c) {
+    const int total = nxy * n;  // < 2^31: n <= 256
+    const int u0 = (int)((int64_t)total * blockIdx.x / gridDim.x);
+    const int u1 = (int)((int64_t)total * (blockIdx.x + 1) / gridDim.x);
+    int u = u0;
+    for (int i = 0;; ++i) {
+        if (u >= u1) return false;
+        const int xy = u / n, z = u % n;
+        const int cnt = min(u1 - u, n - z);
+        if (i == j) {
+            c.xy = xy;
+            c.o0 = z;
+            c.o1 = z + cnt - 1;
+            return true;
+        }
+        u += cnt;
+    }
 }
 
 // Epilogues: EPI_GELU (z and GELU(z) in BF16), EPI_GELU_ONLY (GELU(z)),
 // EPI_F32 (z in FP32), EPI_DGELU (acc * GELU'(zprev), BF16). wt holds the
-// weights in the operand layout [27][CIN/8][COUT][8].
+// weights as [9 (dy, dx)][CIN/8][3 (dz)][COUT][8].
 //
-// Roles: warp 8, lane 0 issues the weight copy and the halo loads (a ring of
-// TC_NST stages) and the MMAs of every tile into accumulator k % 2; warps 0-7
-// read accumulator k % 2, release it, and run the epilogue. mbarriers:
-// full[s] (halo landed), empty[s] (the MMAs that read stage s are done),
-// accf[a] (accumulator a complete), acce[a] (accumulator a read out).
+// z-streaming: the CTA walks the input z-slices of each segment once (slices
+// o0 - 1 .. o1 + 1, clipped to the volume). For each input slice and each of
+// its 9 (dx, dy) taps it issues MMAs with N = 3 COUT, the three dz taps at
+// once, into a fresh accumulator window of its own (a ring of TC_NWIN windows
+// of 3 COUT columns): block b of slice zi's window holds its contribution to
+// output slice zi + 1 - b. Output slice z is the sum of block 0 of slice
+// z - 1, block 1 of slice z and block 2 of slice z + 1 (missing slices
+// outside the volume contribute nothing), so it is finished once slice z + 1
+// is (slice n - 1 also finishes output n - 1), and the epilogue adds the
+// three blocks. Windows never overlap, so the MMAs of consecutive slices do
+// not wait on each other's accumulators.
+//
+// Roles: warp 8, lane 0 issues the weight copy, the halo loads (ring of
+// TC_NST slices) and the MMAs, committing each slice to ready[k % TC_RING];
+// warps 0-7 read the finished output slices (warp w: accumulator lanes
+// 32 (w % 4) .. + 31, column half w / 4) and arrive on wfree[w] once no
+// output needs window w any more, which the producer waits for before
+// reusing it.
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
     const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ wt,
@@ -181,12 +226,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
     float *__restrict__ out_f, const bf16 *__restrict__ zprev, int *err) {
     static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "unsupported shape");
     constexpr int KCH = CIN / 8;
-    constexpr int HBYTES = KCH * TC_PLANE;
+    constexpr int HBYTES = KCH * TC_SLICE;
     constexpr int WBYTES = 27 * KCH * COUT * 16;
-    constexpr int CPW = COUT / 2;  // accumulator columns per epilogue warp
-    constexpr uint32_t IDESC = tc_idesc(COUT);
+    constexpr int CPW = COUT / (TC_EPI_WARPS / 4);  // accumulator columns per epilogue warp
+    constexpr int NW = 3 * COUT;                    // MMA N: the three dz taps
+    static_assert(TC_NWIN * NW <= TC_TMEM_COLS && TC_RING >= TC_NWIN + 2, "tensor memory plan");
+    constexpr uint32_t IDESC = tc_idesc(NW);
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[TC_NST], empty[TC_NST], accf[2], acce[2], wbar;
+    __shared__ __align__(8) uint64_t full[TC_NST], empty[TC_NST], ready[TC_RING], wfree[TC_NWIN];
+    __shared__ __align__(8) uint64_t wbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -199,10 +247,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
             mbar_init(smem_u32(&full[i]), 1);
             mbar_init(smem_u32(&empty[i]), 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(smem_u32(&accf[i]), 1);
-            mbar_init(smem_u32(&acce[i]), TC_EPI_WARPS);
-        }
+        for (int i = 0; i < TC_RING; ++i) mbar_init(smem_u32(&ready[i]), 1);
+        for (int i = 0; i < TC_NWIN; ++i) mbar_init(smem_u32(&wfree[i]), TC_EPI_WARPS);
         mbar_init(smem_u32(&wbar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -216,24 +262,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
     tc_fence_after();
     const uint32_t taddr = tmem_base;
     const volatile int *abort_p = &abort_flag;
-
-    const int tiles_x = n / TC_TX, tiles_y = n / TC_TY;
-    const int ntiles = tiles_x * tiles_y * n;
-    const int K = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-
-    // Programmatic dependent launch: the next layer may be scheduled now (it
-    // gets an SM when a CTA of this grid exits); this grid's inputs (the
-    // previous layer's output) are read only after griddepcontrol.wait, while
-    // the weights, written before the first layer's launch, may be read before.
+    const int tiles_x = n / TC_TX, nxy = tiles_x * (n / TC_TY);
+    // Programmatic dependent launch: the next layer may be scheduled now; this
+    // grid's input (the previous layer's output) is read only after
+    // griddepcontrol.wait, the weights (written before the first layer) before.
     pdl_trigger();
+
     if (warp == TC_EPI_WARPS) {
         if (lane == 0) {
-            int issued = 0, consumed = 0, committed = 0;
-            auto load = [&](int k) {
-                const int t = blockIdx.x + k * gridDim.x;
-                tc_load_halo<CIN>(&tm_in, hbase + (k % TC_NST) * HBYTES,
-                                  smem_u32(&full[k % TC_NST]), (t % tiles_x) * TC_TX,
-                                  ((t / tiles_x) % tiles_y) * TC_TY, t / (tiles_x * tiles_y));
+            int issued = 0, consumed = 0;  // slices
+            bool ok = true;
+            // the slices of all segments in order, for the halo prefetch
+            int pf_seg = 0, pf_z = 0;
+            TcSeg pfc;
+            bool pf_more = tc_segment(n, nxy, 0, pfc);
+            if (pf_more) pf_z = max(pfc.o0 - 1, 0);
+            auto prefetch = [&]() {
+                if (!pf_more) return;
+                const int s = issued % TC_NST;
+                tc_load_slice<CIN>(&tm_in, hbase + s * HBYTES, smem_u32(&full[s]),
+                                   (pfc.xy % tiles_x) * TC_TX, (pfc.xy / tiles_x) * TC_TY, pf_z);
+                ++issued;
+                if (pf_z < min(pfc.o1 + 1, n - 1)) {
+                    ++pf_z;
+                } else {
+                    pf_more = tc_segment(n, nxy, ++pf_seg, pfc);
+                    if (pf_more) pf_z = max(pfc.o0 - 1, 0);
+                }
             };
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(smem_u32(&wbar)), "r"(WBYTES) : "memory");
@@ -241,118 +296,156 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                 :: "r"(wbase), "l"(wt), "r"(WBYTES), "r"(smem_u32(&wbar)) : "memory");
             pdl_wait();
-            for (; issued < TC_NST && issued < K; ++issued) load(issued);
-            bool ok = tc_wait(smem_u32(&wbar), 0, abort_p);
-            for (int k = 0; k < K && ok; ++k) {
-                const int s = k % TC_NST, a = k & 1;
-                ok = tc_wait(smem_u32(&full[s]), (k / TC_NST) & 1, abort_p);
-                if (!ok) break;
-                ++consumed;
-                ok = tc_wait(smem_u32(&acce[a]), ((k >> 1) & 1) ^ 1, abort_p);
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t d = taddr + a * 32;
-                // descriptors = stage / weight base + compile-time offsets (>> 4) of
-                // every (tap, k-step): the unrolled loop issues MMAs back to back
-                const uint64_t a0 = tc_desc(hbase + s * HBYTES, TC_PLANE, TC_HX * 16);
-                const uint64_t b0 = tc_desc(wbase, COUT * 16, 128);
-#pragma unroll
-                for (int t = 0; t < 27; ++t) {
-                    const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // offsets + 1
-#pragma unroll
-                    for (int kk = 0; kk < KCH / 2; ++kk) {
-                        const uint32_t a_off = ((dz * TC_HY + dy) * TC_HX + dx) * 16 + 2 * kk * TC_PLANE;
-                        const uint32_t b_off = ((t * KCH + 2 * kk) * COUT) * 16;
-                        const uint64_t ad = a0 + (a_off >> 4);
-                        const uint64_t bd = b0 + (b_off >> 4);
-                        const uint32_t acc = (t | kk) != 0;
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                            :: "r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-                            : "memory");
-                    }
-                }
-                tc_commit(smem_u32(&empty[s]));
-                tc_commit(smem_u32(&accf[a]));
-                ++committed;
-                // refill the stage of tile k - 1 (its MMAs were issued one tile earlier)
-                if (k >= 1 && issued < K) {
-                    const int k1 = k - 1;
-                    ok = tc_wait(smem_u32(&empty[k1 % TC_NST]), (k1 / TC_NST) & 1, abort_p);
+            while (issued < TC_NST && pf_more) prefetch();
+            ok = tc_wait(smem_u32(&wbar), 0, abort_p);
+            const uint64_t b0 = tc_desc(wbase, NW * 16, 128);
+            TcSeg c;
+            for (int j = 0; ok && tc_segment(n, nxy, j, c); ++j) {
+                const int i0 = max(c.o0 - 1, 0), i1 = min(c.o1 + 1, n - 1);
+                for (int zi = i0; zi <= i1; ++zi) {
+                    const int k = consumed, s = k % TC_NST, w = k % TC_NWIN;
+                    ok = tc_wait(smem_u32(&full[s]), (k / TC_NST) & 1, abort_p) &&
+                         tc_wait(smem_u32(&wfree[w]), ((k / TC_NWIN) & 1) ^ 1, abort_p);
                     if (!ok) break;
-                    load(issued++);
+                    ++consumed;
+                    tc_fence_after();
+                    const uint32_t d = taddr + (uint32_t)(w * NW);
+                    const uint64_t a0 = tc_desc(hbase + s * HBYTES, TC_SLICE, TC_HX * 16);
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) {
+                        const int dx = t % 3, dy = t / 3;  // offsets + 1
+#pragma unroll
+                        for (int kk = 0; kk < KCH / 2; ++kk) {
+                            const uint32_t a_off = (dy * TC_HX + dx) * 16 + 2 * kk * TC_SLICE;
+                            const uint32_t b_off = ((t * KCH + 2 * kk) * NW) * 16;
+                            const uint64_t ad = a0 + (a_off >> 4);
+                            const uint64_t bd = b0 + (b_off >> 4);
+                            const uint32_t acc = (t | kk) != 0;  // a fresh window per slice
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                :: "r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                                : "memory");
+                        }
+                    }
+                    tc_commit(smem_u32(&empty[s]));
+                    tc_commit(smem_u32(&ready[k % TC_RING]));
+                    // refill the stage of slice k - TC_LAG once its MMAs are done
+                    if (k >= TC_LAG && pf_more) {
+                        const int k1 = k - TC_LAG;
+                        ok = tc_wait(smem_u32(&empty[k1 % TC_NST]), (k1 / TC_NST) & 1, abort_p);
+                        if (!ok) break;
+                        prefetch();
+                    }
                 }
             }
             if (!ok) {
                 if (!abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
                 abort_flag = 1;
             }
-            // drain: halo loads still in flight and the last MMA batch (bounded)
+            // drain (bounded): halo loads still in flight, the last MMA batch
             for (int k = consumed; k < issued; ++k)
                 tc_wait(smem_u32(&full[k % TC_NST]), (k / TC_NST) & 1, nullptr);
-            if (committed > 0)
-                tc_wait(smem_u32(&empty[(committed - 1) % TC_NST]), ((committed - 1) / TC_NST) & 1, nullptr);
+            if (consumed > 0)
+                tc_wait(smem_u32(&empty[(consumed - 1) % TC_NST]), ((consumed - 1) / TC_NST) & 1, nullptr);
         }
-        __syncwarp();  // the warp reconverges before the final CTA barrier
+        __syncwarp();
     } else {
         const int q = warp & 3, hcol = warp >> 2;
         const int row = q * 32 + lane;  // accumulator lane = tile voxel (x = row & 7, y = row >> 3)
-        for (int k = 0; k < K; ++k) {
-            const int a = k & 1;
-            int ok = 1;  // lane 0 waits for the warp, so the warp stays converged
-            if (lane == 0) {
-                ok = tc_wait(smem_u32(&accf[a]), (k >> 1) & 1, abort_p);
-                if (!ok) {
-                    if (!abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
-                    abort_flag = 1;
-                }
-            }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            tc_fence_after();
-            float r[CPW];
-            tc_ld<CPW>(taddr + ((uint32_t)(q * 32) << 16) + a * 32 + hcol * CPW, r);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&acce[a]));
-            const int t = blockIdx.x + k * gridDim.x;
-            const int x0 = (t % tiles_x) * TC_TX, y0 = ((t / tiles_x) % tiles_y) * TC_TY;
-            const int z0 = t / (tiles_x * tiles_y);
-            const size_t v = ((size_t)z0 * n + (y0 + (row >> 3))) * n + x0 + (row & 7);
-            const size_t nv = (size_t)n * n * n;
-            const int c0 = hcol * CPW;
-            // planar BF16 outputs: channels c..c+7 of voxel v at ((c / 8) nv + v) * 8
-            auto plane = [&](int c) { return ((size_t)((c0 + c) >> 3) * nv + v) * 8; };
-            if (EPI == EPI_F32) {
-#pragma unroll
-                for (int c = 0; c < CPW; c += 4)
-                    *reinterpret_cast<float4 *>(out_f + v * COUT + c0 + c) =
-                        make_float4(r[c] + bias[c0 + c], r[c + 1] + bias[c0 + c + 1],
-                                    r[c + 2] + bias[c0 + c + 2], r[c + 3] + bias[c0 + c + 3]);
-            } else if (EPI == EPI_DGELU) {
-#pragma unroll
-                for (int c = 0; c < CPW; c += 8) {
-                    const uint4 zp = *reinterpret_cast<const uint4 *>(zprev + plane(c));
-                    const bf16 *zb = reinterpret_cast<const bf16 *>(&zp);
-                    __align__(16) bf16 o[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        o[j] = __float2bfloat16_rn(r[c + j] * gelu_grad_f(__bfloat162float(zb[j])));
-                    *reinterpret_cast<uint4 *>(out_z + plane(c)) = *reinterpret_cast<const uint4 *>(o);
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < CPW; c += 8) {
-                    __align__(16) bf16 oz[8], oa[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float z = r[c + j] + bias[c0 + c + j];
-                        oz[j] = __float2bfloat16_rn(z);
-                        oa[j] = __float2bfloat16_rn(gelu_f(z));
+        const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + hcol * CPW;
+        const size_t nv = (size_t)n * n * n;
+        int k = 0;  // slices seen
+        bool ok = true;
+        TcSeg c;
+        for (int j = 0; ok && tc_segment(n, nxy, j, c); ++j) {
+            const int i0 = max(c.o0 - 1, 0), i1 = min(c.o1 + 1, n - 1);
+            const int kb = k;  // global index of slice i0
+            const int x0 = (c.xy % tiles_x) * TC_TX, y0 = (c.xy / tiles_x) * TC_TY;
+            for (int zi = i0; zi <= i1; ++zi, ++k) {
+                int okw = 1;
+                if (lane == 0) {
+                    okw = tc_wait(smem_u32(&ready[k % TC_RING]), (k / TC_RING) & 1, abort_p);
+                    if (!okw) {
+                        if (!abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
+                        abort_flag = 1;
                     }
-                    if (EPI == EPI_GELU)
-                        *reinterpret_cast<uint4 *>(out_z + plane(c)) = *reinterpret_cast<const uint4 *>(oz);
-                    *reinterpret_cast<uint4 *>(out_a + plane(c)) = *reinterpret_cast<const uint4 *>(oa);
+                }
+                if (!__shfl_sync(0xffffffffu, okw, 0)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                // outputs finished by slice zi: zi - 1, and zi itself at the volume's end
+                const int zlo = max(zi - 1, c.o0), zhi = (zi == n - 1) ? min(zi, c.o1) : min(zi - 1, c.o1);
+                float r[2][CPW];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int z = zlo + m;
+                    if (z > zhi) break;
+#pragma unroll
+                    for (int cc = 0; cc < CPW; ++cc) r[m][cc] = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {  // block b of slice z - 1 + b
+                        const int zs = z - 1 + b;
+                        if (zs < i0 || zs > i1) continue;
+                        const int ks = kb + (zs - i0);
+                        float part[CPW];
+                        tc_ld<CPW>(tq + (uint32_t)((ks % TC_NWIN) * NW + b * COUT), part);
+#pragma unroll
+                        for (int cc = 0; cc < CPW; ++cc) r[m][cc] += part[cc];
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                // windows no longer needed: slice zi - 2 (its last output, zi - 1, is
+                // done), and at the segment's end the last two slices as well
+                if (lane == 0) {
+                    if (zi - 2 >= i0) mbar_arrive(smem_u32(&wfree[(k - 2) % TC_NWIN]));
+                    if (zi == i1) {
+                        if (zi - 1 >= i0) mbar_arrive(smem_u32(&wfree[(k - 1) % TC_NWIN]));
+                        mbar_arrive(smem_u32(&wfree[k % TC_NWIN]));
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    if (zlo + m > zhi) break;
+                    const int z = zlo + m;
+                    const size_t v = ((size_t)z * n + (y0 + (row >> 3))) * n + x0 + (row & 7);
+                    const int c0 = hcol * CPW;
+                    auto plane = [&](int cc) { return ((size_t)((c0 + cc) >> 3) * nv + v) * 8; };
+                    if (EPI == EPI_F32) {
+#pragma unroll
+                        for (int cc = 0; cc < CPW; cc += 4)
+                            *reinterpret_cast<float4 *>(out_f + v * COUT + c0 + cc) =
+                                make_float4(r[m][cc] + bias[c0 + cc], r[m][cc + 1] + bias[c0 + cc + 1],
+                                            r[m][cc + 2] + bias[c0 + cc + 2], r[m][cc + 3] + bias[c0 + cc + 3]);
+                    } else if (EPI == EPI_DGELU) {
+#pragma unroll
+                        for (int cc = 0; cc < CPW; cc += 8) {
+                            const uint4 zp = *reinterpret_cast<const uint4 *>(zprev + plane(cc));
+                            const bf16 *zb = reinterpret_cast<const bf16 *>(&zp);
+                            __align__(16) bf16 o[8];
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj)
+                                o[jj] = __float2bfloat16_rn(r[m][cc + jj] * gelu_grad_f(__bfloat162float(zb[jj])));
+                            *reinterpret_cast<uint4 *>(out_z + plane(cc)) = *reinterpret_cast<const uint4 *>(o);
+                        }
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < CPW; cc += 8) {
+                            __align__(16) bf16 oz[8], oa[8];
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                const float zz = r[m][cc + jj] + bias[c0 + cc + jj];
+                                oz[jj] = __float2bfloat16_rn(zz);
+                                oa[jj] = __float2bfloat16_rn(gelu_f(zz));
+                            }
+                            if (EPI == EPI_GELU)
+                                *reinterpret_cast<uint4 *>(out_z + plane(cc)) = *reinterpret_cast<const uint4 *>(oz);
+                            *reinterpret_cast<uint4 *>(out_a + plane(cc)) = *reinterpret_cast<const uint4 *>(oa);
+                        }
+                    }
                 }
             }
         }
