@@ -444,10 +444,18 @@ def bench_surrogate(dev, N=128, t_eval=1500, blocks=25):
     m.surr.features(f0, solid, S.IN_SCALE)
     m.chained_block(solid)
     err_net = m.fine_error(ref, solid)
+    # per-block times over runs of consecutive blocks (the steady state of a
+    # run; one event pair per run, so no per-block host gap is counted)
     f = f0.clone()
-    ms_plain = _timed(lambda: m.plain_block(f, solid), reps=5)
+    reps = 10
+    ms_plain = _timed(lambda: [m.plain_block(f, solid) for _ in range(reps)], reps=2) / reps
     m.surr.features(f0, solid, S.IN_SCALE)
-    ms_surr = _timed(lambda: m.chained_block(solid), reps=5)
+    m.chained_block(solid)  # first block eager, then the captured block
+    m.chained_block(solid)
+    ms_surr = _timed(lambda: [m.chained_block(solid) for _ in range(reps)], reps=2) / reps
+    m.use_graph = False
+    ms_surr_eager = _timed(lambda: [m.chained_block(solid) for _ in range(reps)], reps=2) / reps
+    m.use_graph = True
     # a run of `blocks` blocks with a plain-LBM check every 10 (the run goes on
     # from the plain lattice after a check), timed against `blocks` plain blocks
     f_plain = f0.clone()
@@ -464,8 +472,8 @@ def bench_surrogate(dev, N=128, t_eval=1500, blocks=25):
     err_run = m.velocity_error(f_sur, f_plain, solid)
     m.close()
     return {"surr_block_err": err_net, "persistence_err": err_persist,
-            "surr_block_ms": ms_surr, "plain_block_ms": ms_plain,
-            "surr_speedup": ms_plain / ms_surr, "surr_run_blocks": blocks,
+            "surr_block_ms": ms_surr, "surr_block_eager_ms": ms_surr_eager,
+            "plain_block_ms": ms_plain, "surr_speedup": ms_plain / ms_surr, "surr_run_blocks": blocks,
             "surr_run_used": runs[-1], "surr_run_check_errors": m.errors,
             "surr_run_fallback": m.fallback, "surr_run_ms": ms_run,
             "plain_run_ms": ms_plain_run, "surr_run_speedup": ms_plain_run / ms_run,

@@ -37,6 +37,9 @@ struct SurrHandle {
     int *err = nullptr;             // device status bits (bounded waits of the conv kernels)
     int conv_ctas = 0;
     int sms = 0;
+    // the BF16 weights were rewritten since the last forward: its first layer,
+    // which copies them before its dependency wait, is then launched normally
+    bool weights_dirty = true;
     // TMA descriptors of the conv inputs: features, a1..a3, dL/d(out), dL/dz1..dz3
     CUtensorMap tm_feats, tm_a[3], tm_g4, tm_gz[3];
 };
@@ -295,6 +298,8 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
     const int N = 2 * n;
     const int64_t nc = (int64_t)N * N * N;
     const int t = threadIdx.x;
+    pdl_wait();  // launched as a programmatic dependent of the network's last layer
+    pdl_trigger();
     // the thread's two fine cells: (lx, ly, lz) and (lx, ly, lz + 2 ADV_VZ / 2) of the
     // block's 2 ADV_VX x 2 ADV_VY x 2 ADV_VZ cells
     const int lx = t % (2 * ADV_VX), ly = (t / (2 * ADV_VX)) % (2 * ADV_VY);
@@ -344,14 +349,27 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
         float contrib[4] = {0.f, 0.f, 0.f, 0.f};
         int fl = 0;
         if (!is_solid[h]) {
+            // corner and weight of k_surr_apply's interpolation, in integers:
+            // fine cell 2v + b sits at coarse v - 1/4 (b = 0) or v + 1/4 (b = 1),
+            // so the lower corner is v - 1 + b with weight 0.25 + 0.5 b on the
+            // upper one, clamped at both ends of the axis
             int i0[3];
             float tt[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float sa = fminf(fmaxf(fi[h][a] * 0.5f - 0.25f, 0.0f), (float)(n - 1));
-                int i = min((int)floorf(sa), n - 2);
+                const int v = fi[h][a] >> 1, b = fi[h][a] & 1;
+                int i = v - 1 + b;
+                float t = b ? 0.25f : 0.75f;
+                if (v == 0 && b == 0) {
+                    i = 0;
+                    t = 0.0f;
+                }
+                if (v == n - 1 && b == 1) {
+                    i = n - 2;
+                    t = 1.0f;
+                }
                 i0[a] = i;
-                tt[a] = sa - (float)i;
+                tt[a] = t;
             }
             float d[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -493,9 +511,9 @@ __global__ void k_vel_err(const float *__restrict__ fa, const float *__restrict_
 
 // ----------------------------------------------------------- launching ----
 
-// pdl: launch with programmatic dependent launch (only where the weights
-// were not rewritten by the kernel just before: every layer but the first of
-// a forward pass).
+// pdl: launch with programmatic dependent launch. The kernel copies its
+// weights before its dependency wait, so this is off for the first layer of a
+// forward pass right after the weights were rewritten.
 template <int CIN, int COUT, int EPI>
 static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, const float *bias,
                       bf16 *oz, bf16 *oa, float *of, const bf16 *zprev, cudaStream_t s,
@@ -577,6 +595,7 @@ static dw_status wgrad(SurrHandle *h, const bf16 *in, const bf16 *g, int layer, 
 }
 
 static dw_status refresh_weights(SurrHandle *h, cudaStream_t s) {
+    h->weights_dirty = true;
     for (int l = 0; l < 4; ++l) {
         const int64_t cnt = 27LL * SCH[l] * SCH[l + 1];
         k_surr_weights<<<grid_for(cnt, 256), 256, 0, s>>>(h->params, h->wf, h->wd, h->off_w[l],
@@ -760,14 +779,14 @@ extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activation
     dw_status st;
     const float *P = h->params;
     if (keep_activations) {
-        st = conv<16, 32, EPI_GELU>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s, false);
+        st = conv<16, 32, EPI_GELU>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], h->z[0], h->a[0], nullptr, nullptr, s, !h->weights_dirty);
         if (st != DW_OK) return st;
         st = conv<32, 32, EPI_GELU>(h, h->tm_a[0], h->wf + h->woff[1], P + h->off_b[1], h->z[1], h->a[1], nullptr, nullptr, s);
         if (st != DW_OK) return st;
         st = conv<32, 32, EPI_GELU>(h, h->tm_a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
         if (st != DW_OK) return st;
     } else {
-        st = conv<16, 32, EPI_GELU_ONLY>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], nullptr, h->a[0], nullptr, nullptr, s, false);
+        st = conv<16, 32, EPI_GELU_ONLY>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], nullptr, h->a[0], nullptr, nullptr, s, !h->weights_dirty);
         if (st != DW_OK) return st;
         st = conv<32, 32, EPI_GELU_ONLY>(h, h->tm_a[0], h->wf + h->woff[1], P + h->off_b[1], nullptr, h->a[1], nullptr, nullptr, s);
         if (st != DW_OK) return st;
@@ -775,6 +794,7 @@ extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activation
         if (st != DW_OK) return st;
     }
     st = conv<32, 16, EPI_F32>(h, h->tm_a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s);
+    h->weights_dirty = false;
     if (st != DW_OK) return st;
     if (out)
         DW_CUDA(cudaMemcpyAsync(out, h->out, sizeof(float) * h->nv * 16, cudaMemcpyDeviceToDevice, s));
@@ -876,10 +896,9 @@ extern "C" dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float i
 extern "C" dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *solid,
                                        float in_scale, dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
-    k_surr_advance_fine<<<(unsigned)(h->nv / (ADV_VX * ADV_VY * ADV_VZ)), ADV_THREADS, 0,
-                          as_stream(stream)>>>(
-        h->out, out_scale, h->fine, solid, h->n, in_scale, h->feats);
-    DW_LAUNCHED("k_surr_advance_fine");
+    DW_CUDA(launch_pdl(k_surr_advance_fine, (unsigned)(h->nv / (ADV_VX * ADV_VY * ADV_VZ)),
+                       ADV_THREADS, as_stream(stream), (const float *)h->out, out_scale, h->fine,
+                       solid, h->n, in_scale, h->feats));
     return DW_OK;
 }
 

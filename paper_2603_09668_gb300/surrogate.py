@@ -139,7 +139,7 @@ class SurrogateLBM:
     f = f_eq(rho, u), only when the plain LBM takes over or at the end."""
 
     def __init__(self, N, tau=0.55, u_inlet=(U_REF, 0.0, 0.0), check_every=10, tol=0.02,
-                 params=None, device="cuda"):
+                 params=None, device="cuda", use_graph=True):
         self.N = N
         self.lbm = B.LBM((N, N, N), tau, u_inlet=u_inlet, bc_x=1, max_tape=1)
         self.surr = B.Surrogate(N // 2)
@@ -152,6 +152,9 @@ class SurrogateLBM:
         self.fallback = False
         self.errors = []
         self._sums = torch.zeros(2, dtype=torch.float64, device=device)
+        self.use_graph = use_graph
+        self._graphs = {}  # solid mask pointer -> CUDA graph of one chained block
+        self._warm = set()
 
     # one block from a lattice (reads f, writes f)
     def surrogate_block(self, f, solid):
@@ -166,6 +169,26 @@ class SurrogateLBM:
     # the network runs and the fine state advances, leaving the features of
     # the new state for the next block
     def chained_block(self, solid):
+        if not self.use_graph:
+            self._chained_eager(solid)
+            return
+        key = solid.data_ptr() if solid is not None else 0
+        g = self._graphs.get(key)
+        if g is None:
+            if key not in self._warm:
+                # the first block runs eagerly, which also sets the kernels'
+                # launch attributes outside any capture
+                self._warm.add(key)
+                self._chained_eager(solid)
+                return
+            # later blocks replay one captured block (capturing runs nothing)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._chained_eager(solid)
+            self._graphs[key] = g
+        g.replay()
+
+    def _chained_eager(self, solid):
         self.surr.forward(keep_activations=False)
         self.surr.advance_fine(OUT_SCALE, solid, IN_SCALE)
 

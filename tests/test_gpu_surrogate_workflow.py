@@ -69,3 +69,23 @@ def test_run_with_checks_uses_the_surrogate():
     assert len(m.errors) == 2 and max(m.errors) <= 0.02, m.errors
     assert torch.isfinite(f).all()
     m.close()
+
+
+def test_graph_replayed_blocks_equal_eager_blocks():
+    """Chained blocks replayed from the captured CUDA graph give the same
+    lattice, bit for bit, as the same blocks launched one by one (the kernels
+    have no atomics)."""
+    m, f0, solid = held_out_scene(t_eval=200)
+    outs = []
+    for use_graph in (True, False):
+        m.use_graph = use_graph
+        m.surr.features(f0, solid, S.IN_SCALE)
+        for _ in range(4):
+            m.chained_block(solid)
+        f = torch.empty_like(f0)
+        f.copy_(f0)
+        m.surr.write_lattice(solid, f)
+        outs.append(f)
+    assert len(m._graphs) == 1
+    assert torch.equal(outs[0], outs[1])
+    m.close()
