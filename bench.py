@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--substeps", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch"],
+    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch",
+                                                    "batch_adjoint"],
                     help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
                          "or the checkpointed MPM adjoint")
     ap.add_argument("--batch-scenes", type=int, default=64,
@@ -521,11 +522,82 @@ def bench_batch(dev, n_scenes=64, n_sub=500, sort_every=25, trial=10):
                                                  for t in trials]}
 
 
+def bench_batch_adjoint(dev, n_scenes=64, n_sub=500, ckpt=25, trial=10):
+    """Batched forward + adjoint of the 64-scene workload: the forward rollout
+    of n_sub substeps in segments of ckpt substeps, each segment's start state
+    stored as a checkpoint; then, from dL/d(final state) (a fixed seed
+    gradient), the reverse pass of every segment in reverse order by
+    mpm_batch_segment_adjoint (recomputing the segment's states into a tape),
+    accumulating each scene's wind and E gradients. Reported: whole-batch
+    particle-substeps/s of forward + adjoint together, and of the reverse
+    pass alone."""
+    import torch
+
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import inputs
+
+    scenes = inputs.batch_scenes(n_scenes=n_scenes, n_substeps=n_sub)
+    winds = [B.WindField(torch.from_numpy(sc.wind.astype(np.float32)).to(dev), sc.t_total)
+             for sc in scenes]
+    batch = B.MPMBatch([(sc.params(), sc.n, w) for sc, w in zip(scenes, winds)])
+    st = [np.concatenate([inputs.rest_state(sc.x)[i] for sc in scenes], axis=1) for i in range(4)]
+    pin = np.concatenate([sc.pinned if sc.pinned is not None else np.zeros(sc.n, np.uint8)
+                          for sc in scenes])
+    s0 = B.MpmState(*(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in st))
+    p = torch.from_numpy(pin).to(dev)
+    batch.tune(s0, p, n_trial_substeps=trial)
+    n = int(batch.n)
+    dt = scenes[0].dt
+    assert all(sc.dt == dt for sc in scenes)
+    n_seg = n_sub // ckpt
+    s = s0.clone()
+    ck = [B.MpmState.empty_like(s0) for _ in range(n_seg)]
+    tape = torch.empty((ckpt - 1) * 24 * n, dtype=torch.float32, device=dev)
+    g = B.MpmState.empty_like(s0)
+    g0 = B.MpmState.zeros_like(s0)
+    g0.x.fill_(1.0 / n)  # L = mean of the final positions' coordinates
+    nw, _ = batch.wind_layout()
+    g_wind = torch.zeros(nw, dtype=torch.float32, device=dev)
+    g_E = torch.zeros(n_scenes, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    marks = {}
+
+    def run():
+        for a, b in zip(s, s0):
+            a.copy_(b)
+        for i in range(n_seg):
+            for a, b in zip(ck[i], s):
+                a.copy_(b)
+            batch.rollout(s, p, None, i * ckpt * dt, ckpt, 0)
+        marks["mid"] = torch.cuda.Event(enable_timing=True)
+        marks["mid"].record(stream)
+        for a, b in zip(g, g0):
+            a.copy_(b)
+        for i in reversed(range(n_seg)):
+            batch.segment_adjoint(ck[i], tape, g, p, i * ckpt * dt, ckpt, g_wind, g_E)
+        marks["end"] = torch.cuda.Event(enable_timing=True)
+        marks["end"].record(stream)
+
+    ms = _timed(run, reps=1)
+    adj_ms = marks["mid"].elapsed_time(marks["end"])
+    batch.device_status()
+    finite = bool(torch.isfinite(g_wind).all().item() and torch.isfinite(g_E).all().item())
+    cfg = batch.config()
+    batch.close()
+    return {"batch_adj_scenes": n_scenes, "batch_adj_particles": n, "batch_adj_substeps": n_sub,
+            "batch_adj_checkpoint_every": ckpt,
+            "batch_fwd_adj_ps_per_s": n * n_sub / (ms * 1e-3),
+            "batch_adj_only_ps_per_s": n * n_sub / (adj_ms * 1e-3),
+            "batch_fwd_adj_ms": ms, "batch_adj_ms": adj_ms, "batch_adj_grads_finite": finite,
+            "batch_adj_config": cfg}
+
+
 def extras(dev):
     out = bench_lbm(dev)
     out.update(bench_adjoint(dev))
     out.update(bench_surrogate(dev))
     out.update(bench_batch(dev))
+    out.update(bench_batch_adjoint(dev))
     return out
 
 
@@ -599,6 +671,8 @@ def run_only(args):
         res = bench_surrogate(dev)
     elif args.only == "batch":
         res = bench_batch(dev, n_scenes=args.batch_scenes)
+    elif args.only == "batch_adjoint":
+        res = bench_batch_adjoint(dev, n_scenes=args.batch_scenes)
     else:
         res = bench_adjoint(dev)
     print(json.dumps({"only": args.only, **res}), flush=True)

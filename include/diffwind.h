@@ -334,6 +334,35 @@ DW_API dw_status mpm_batch_tune(dw_mpm_batch h, const dw_mpm_state *state, const
  * state, so a batch whose barrier gave up is usable again afterwards. */
 DW_API dw_status mpm_batch_device_status(dw_mpm_batch h, dw_stream stream);
 
+/* Size of the batch's concatenated wind gradient: scene s's block (shaped like
+ * its wind values, n_frames * nf^3 * 3 floats) starts at offsets[s] (host
+ * int64[n_scenes + 1] or NULL); *n_floats (may be NULL) is the total. */
+DW_API dw_status mpm_batch_wind_layout(dw_mpm_batch h, int64_t *n_floats, int64_t *offsets);
+
+/* Reverse mode of n_substeps batched substeps (a checkpointed segment of
+ * every scene at once; Eq. simulation_mpm differentiated as in
+ * mpm_segment_adjoint, scene by scene). Recomputes the states 1 ..
+ * n_substeps - 1 from `start` (state 0 of the concatenated batch, substep j
+ * of scene s at t0 + j dt_s) into `tape` (device float, (n_substeps - 1) *
+ * 24 * n floats, each state as x, v, C, F back to back; caller-owned,
+ * tape_floats its size) with the handle's launch configuration (without a
+ * graph), then runs the reverse substeps from the last to the first, each as
+ * five launches over all scenes. g (concatenated, n particles) holds
+ * dL/d(state after the segment) on entry and is overwritten with
+ * dL/d(start). g_wind (device, mpm_batch_wind_layout floats, or NULL)
+ * accumulates each scene's dL/d(wind values) at its offset; g_E (device
+ * float[n_scenes], or NULL) accumulates each scene's dL/dE. The substeps are
+ * those of mpm_batch_rollout without sorting. The first call allocates the
+ * reverse-mode workspace (two float4 per grid node of all scenes, 12 floats
+ * per particle), kept until mpm_batch_destroy. Errors: DW_ERR_ARG (state
+ * sizes, a missing or short tape), DW_ERR_OOM, DW_ERR_CUDA; device-side
+ * failures go to the batch's device status. */
+DW_API dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *start,
+                                           float *tape, int64_t tape_floats,
+                                           const dw_mpm_state *g, const uint8_t *pinned, float t0,
+                                           int32_t n_substeps, float *g_wind, float *g_E,
+                                           dw_stream stream);
+
 /* Failure-detection self-test of the persistent kernel's grid barrier: one
  * cooperative launch of one CTA per SM runs the barrier alone, told to wait
  * for missing_ctas (0..1024) more CTAs than were launched. With 0 it must

@@ -87,6 +87,9 @@ SIGNATURES = {
                              P(I32), VP]),
     "mpm_batch_device_status": (I32, [VP, VP]),
     "mpm_batch_barrier_selftest": (I32, [VP, I32, VP]),
+    "mpm_batch_wind_layout": (I32, [VP, P(I64), P(I64)]),
+    "mpm_batch_segment_adjoint": (I32, [VP, P(DwMpmState), VP, I64, P(DwMpmState), VP, F32, I32,
+                                        VP, VP, VP]),
     "lbm_create": (I32, [P(DwLbmDesc), P(VP)]),
     "lbm_destroy": (I32, [VP]),
     "lbm_step": (I32, [VP, VP, VP, I32, VP]),

@@ -30,7 +30,8 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "surr_features_fine", "surr_advance_fine", "surr_write_lattice",
            "surr_fine_velocity_error", "mpm_batch_create", "mpm_batch_destroy",
            "mpm_batch_layout", "mpm_batch_rollout", "mpm_batch_set_config",
-           "mpm_batch_get_config", "mpm_batch_tune", "mpm_batch_device_status", "mpm_batch_barrier_selftest", "MPMBatch"]
+           "mpm_batch_get_config", "mpm_batch_tune", "mpm_batch_device_status", "mpm_batch_barrier_selftest",
+           "mpm_batch_wind_layout", "mpm_batch_segment_adjoint", "MPMBatch"]
 
 NEOHOOKEAN, FIXED_COROTATED = 0, 1
 BATCH_PERSISTENT, BATCH_SPLIT = 0, 1
@@ -310,6 +311,28 @@ def mpm_batch_barrier_selftest(h, missing_ctas, stream=None):
     check(lib().mpm_batch_barrier_selftest(h, int(missing_ctas), _stream(stream)))
 
 
+def mpm_batch_wind_layout(h, n_scenes):
+    """(total floats of the concatenated wind gradient, [start of each scene's block, ..., total])."""
+    n = ct.c_int64()
+    offs = (ct.c_int64 * (n_scenes + 1))()
+    check(lib().mpm_batch_wind_layout(h, ct.byref(n), offs))
+    return n.value, list(offs)
+
+
+def mpm_batch_segment_adjoint(h, start: MpmState, tape, g: MpmState, pinned, t0, n_substeps,
+                              g_wind=None, g_E=None, stream=None):
+    """Reverse mode of n_substeps batched substeps from `start` (all scenes);
+    tape is a device float32 tensor of at least (n_substeps - 1) * 24 * n
+    elements, g_wind the concatenated wind gradient, g_E float32[n_scenes]."""
+    a, gg = start.to_c(), g.to_c()
+    tp = _dev(tape, name="tape") if tape is not None else None
+    nt = tape.numel() if tape is not None else 0
+    check(lib().mpm_batch_segment_adjoint(h, ct.byref(a), tp, int(nt), ct.byref(gg), _pin(pinned),
+                                          float(t0), int(n_substeps), _dev(g_wind, name="g_wind"),
+                                          _dev(g_E, name="g_E"), _stream(stream)))
+    return g
+
+
 # --------------------------------------------------------------------- LBM --
 
 def lbm_create(shape, tau, u_inlet=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), bc_x=0, max_tape=2):
@@ -466,6 +489,14 @@ class MPMBatch:
 
     def scene_slice(self, s):
         return slice(self.offsets[s], self.offsets[s + 1])
+
+    def wind_layout(self):
+        return mpm_batch_wind_layout(self.h, self.n_scenes)
+
+    def segment_adjoint(self, start, tape, g, pinned, t0, n_substeps, g_wind=None, g_E=None,
+                        stream=None):
+        return mpm_batch_segment_adjoint(self.h, start, tape, g, pinned, t0, n_substeps, g_wind,
+                                         g_E, stream)
 
 
 class LBM:

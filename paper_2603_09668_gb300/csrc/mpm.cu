@@ -14,6 +14,7 @@
 #include <vector>
 #include <stdlib.h>
 
+#include "mpm_adjoint.cuh"
 #include "mpm_handle.cuh"
 
 namespace dw {
@@ -84,14 +85,6 @@ __global__ void k_g2p(MpmParams P, const float *x, const float *F,
 
 // --------------------------------------------------------------- reverse --
 
-__device__ __forceinline__ void weight_grad(const MpmParams &P, const Stencil &s, int oi, int oj,
-                                            int ok, float g[3]) {
-    float wx = s.w[0][oi], wy = s.w[1][oj], wz = s.w[2][ok];
-    g[0] = s.dw[0][oi] * wy * wz * P.inv_dx;
-    g[1] = wx * s.dw[1][oj] * wz * P.inv_dx;
-    g[2] = wx * wy * s.dw[2][ok] * P.inv_dx;
-}
-
 // Reverse G2P: scatter dL/dv_i into grid_bv; write partial dL/dx_p, dL/dF_p.
 // The node value W_ip (bv_p + D bC_p (x_i - x_p)) has the form of a P2G value
 // (momentum m v + A (x_i - x_p) with m v -> bv, A -> D bC and no mass), so it
@@ -109,136 +102,29 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
     P2GParticle q;
     q.valid = false;
     if (p < n) {
-        float xp[3] = {x[p], x[n + p], x[2 * n + p]};
-        float Fp[9];
+        float xp[3], Fp[9], bxo[3], bvo[3], bCo[9], bFo[9], bx[3], bFin[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Fp[k] = F[k * n + p];
-        float bxo[3] = {gxo[p], gxo[n + p], gxo[2 * n + p]};
-        Stencil s;
-        if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) scratch[a * cap + p] = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = 0.0f;
-        } else {
-            const int N = P.N;
-            // recompute C' (v' is not needed: its adjoint only uses the weights)
-            float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const bool pin = pinned && pinned[p];
-            if (!pin) {
-#pragma unroll
-                for (int oi = 0; oi < 3; ++oi)
-#pragma unroll
-                    for (int oj = 0; oj < 3; ++oj)
-#pragma unroll
-                        for (int ok = 0; ok < 3; ++ok) {
-                            float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
-                            float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
-                                          ((float)ok - s.fx[2]) * P.dx};
-                            int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
-                            float4 gv = grid_v[id];
-                            float wv[3] = {W * gv.x, W * gv.y, W * gv.z};
-#pragma unroll
-                            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                                for (int b = 0; b < 3; ++b) Cn[3 * a + b] += wv[a] * d[b];
-                        }
-#pragma unroll
-                for (int k = 0; k < 9; ++k) Cn[k] *= P.D;
-            }
-            float bFo[9], bCo[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                bFo[k] = gFo[k * n + p];
-                bCo[k] = gCo[k * n + p];
-            }
-            // F' = (I + dt C') F  ->  bF_in = (I + dt C')^T bF', bC' += dt bF' F^T
-            float M[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) M[k] = P.dt * Cn[k];
-            M[0] += 1.0f;
-            M[4] += 1.0f;
-            M[8] += 1.0f;
-            float bFin[9], bFoFt[9];
-            mul3_atb(M, bFo, bFin);
-            mul3_abt(bFo, Fp, bFoFt);
-            float bC[9], bv[3];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) bC[k] = bCo[k] + P.dt * bFoFt[k];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) bv[a] = gvo[a * n + p] + P.dt * bxo[a];
-            float bx[3] = {bxo[0], bxo[1], bxo[2]};
-            if (!pin) {
-#pragma unroll
-                for (int oi = 0; oi < 3; ++oi)
-#pragma unroll
-                    for (int oj = 0; oj < 3; ++oj)
-#pragma unroll
-                        for (int ok = 0; ok < 3; ++ok) {
-                            float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
-                            float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
-                                          ((float)ok - s.fx[2]) * P.dx};
-                            int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
-                            float4 gv = grid_v[id];
-                            float vi[3] = {gv.x, gv.y, gv.z};
-                            float Cd[3], CtV[3];
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                Cd[a] = bC[3 * a] * d[0] + bC[3 * a + 1] * d[1] + bC[3 * a + 2] * d[2];
-                                CtV[a] = bC[a] * vi[0] + bC[3 + a] * vi[1] + bC[6 + a] * vi[2];
-                            }
-                            float bW = 0.0f;
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) bW += vi[a] * (bv[a] + P.D * Cd[a]);
-                            float gW[3];
-                            weight_grad(P, s, oi, oj, ok, gW);
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) bx[a] += -P.D * W * CtV[a] + bW * gW[a];
-                        }
-                q.s = s;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) q.mv[a] = bv[a];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) q.A[k] = P.D * bC[k];
-                q.valid = true;
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) scratch[a * cap + p] = bx[a];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = bFin[k];
+        for (int a = 0; a < 3; ++a) {
+            xp[a] = x[a * n + p];
+            bxo[a] = gxo[a * n + p];
+            bvo[a] = gvo[a * n + p];
         }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Fp[k] = F[k * n + p];
+            bCo[k] = gCo[k * n + p];
+            bFo[k] = gFo[k * n + p];
+        }
+        rev_g2p_particle(P, xp, Fp, pinned && pinned[p], grid_v, bxo, bvo, bCo, bFo, q, bx, bFin);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) scratch[a * cap + p] = bx[a];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) scratch[(3 + k) * cap + p] = bFin[k];
     }
     MpmParams Pz = P;
     Pz.p_mass = 0.0f;  // no mass channel: grid_bv = (0, dL/dv_i)
     const ActiveBlocks none{nullptr, nullptr, nullptr, 0, 0};
     p2g_warp_scatter(Pz, q, grid_bv, none, rows[wid], keys[wid]);
-}
-
-// Reverse grid update of one node: (dL/dm_i, dL/dp_i) into grid_bmp, wind
-// gradient scatter, and clearing of grid_mp and grid_bv for the next call.
-__device__ __forceinline__ void rev_grid_node(const MpmParams &P, const WindDev &wind, float t,
-                                              int64_t node, int i, int j, int k,
-                                              float4 *__restrict__ grid_mp,
-                                              float4 *__restrict__ grid_bv,
-                                              float4 *__restrict__ grid_bmp,
-                                              float *__restrict__ g_wind) {
-    float4 mp = grid_mp[node];
-    float4 bmp = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
-        const float4 b4 = grid_bv[node];  // (0, dL/dv_i)
-        const float b[3] = {b4.y, b4.z, b4.w};
-        float inv_m = 1.0f / mp.x;
-        bmp.y = b[0] * inv_m;
-        bmp.z = b[1] * inv_m;
-        bmp.w = b[2] * inv_m;
-        bmp.x = -(mp.y * b[0] + mp.z * b[1] + mp.w * b[2]) * inv_m * inv_m;
-        if (g_wind)
-            wind_sample_adjoint_dev(wind, i * P.dx, j * P.dx, k * P.dx, t,
-                                    make_float3(P.dt * b[0], P.dt * b[1], P.dt * b[2]), g_wind);
-    }
-    grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-    grid_bv[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-    grid_bmp[node] = bmp;
 }
 
 __global__ void __launch_bounds__(GRID_THREADS) k_rev_grid_active(
@@ -267,73 +153,20 @@ __global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float 
     if (reset_count && p == 0) *reset_count = 0;  // the reverse grid update has consumed the list
     float gE_local = 0.0f;
     if (p < n) {
-        float xp[3] = {x[p], x[n + p], x[2 * n + p]};
-        float vp[3] = {v[p], v[n + p], v[2 * n + p]};
-        float Cp[9], Fp[9];
+        float xp[3], vp[3], Cp[9], Fp[9], bx[3], bF[9], bvp[3], bC[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xp[a] = x[a * n + p];
+            vp[a] = v[a * n + p];
+            bx[a] = scratch[a * cap + p];
+        }
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             Cp[k] = C[k * n + p];
             Fp[k] = F[k * n + p];
+            bF[k] = scratch[(3 + k) * cap + p];
         }
-        float bx[3] = {scratch[p], scratch[cap + p], scratch[2 * cap + p]};
-        float bF[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) bF[k] = scratch[(3 + k) * cap + p];
-        Stencil s;
-        float bA[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float bvp[3] = {0.f, 0.f, 0.f};
-        if (make_stencil(P, xp[0], xp[1], xp[2], s)) {
-            float Pk[9], PFt[9], A[9];
-            stress_P(P, Fp, Pk);
-            mul3_abt(Pk, Fp, PFt);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) A[k] = -P.kappa * PFt[k] + P.p_mass * Cp[k];
-            const int N = P.N;
-#pragma unroll
-            for (int oi = 0; oi < 3; ++oi)
-#pragma unroll
-                for (int oj = 0; oj < 3; ++oj)
-#pragma unroll
-                    for (int ok = 0; ok < 3; ++ok) {
-                        float W = s.w[0][oi] * s.w[1][oj] * s.w[2][ok];
-                        float d[3] = {((float)oi - s.fx[0]) * P.dx, ((float)oj - s.fx[1]) * P.dx,
-                                      ((float)ok - s.fx[2]) * P.dx};
-                        int64_t id = ((int64_t)(s.base[2] + ok) * N + (s.base[1] + oj)) * N + (s.base[0] + oi);
-                        float4 g = grid_bmp[id];
-                        float bp[3] = {g.y, g.z, g.w};
-                        float bW = P.p_mass * g.x;
-                        float AtB[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            float mom = P.p_mass * vp[c] + A[3 * c] * d[0] + A[3 * c + 1] * d[1] + A[3 * c + 2] * d[2];
-                            bW += bp[c] * mom;
-                            bvp[c] += W * P.p_mass * bp[c];
-#pragma unroll
-                            for (int b = 0; b < 3; ++b) {
-                                bA[3 * c + b] += W * bp[c] * d[b];
-                                AtB[b] += A[3 * c + b] * bp[c];
-                            }
-                        }
-                        float gW[3];
-                        weight_grad(P, s, oi, oj, ok, gW);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) bx[a] += -W * AtB[a] + bW * gW[a];
-                    }
-            // A = -kappa P F^T + m C
-            float bAF[9], bAtP[9], bP[9];
-            mul3(bA, Fp, bAF);
-            mul3_atb(bA, Pk, bAtP);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                bP[k] = -P.kappa * bAF[k];
-                bF[k] += -P.kappa * bAtP[k];
-            }
-            stress_P_adjoint(P, Fp, bP, bF);
-            float pp = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) pp += bP[k] * Pk[k];
-            gE_local = pp / P.E;
-        }
+        rev_p2g_particle(P, xp, vp, Cp, Fp, grid_bmp, bx, bF, bvp, bC, gE_local);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             gx[a * n + p] = bx[a];
@@ -341,24 +174,13 @@ __global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float 
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            gC[k * n + p] = P.p_mass * bA[k];
+            gC[k * n + p] = bC[k];
             gF[k * n + p] = bF[k];
         }
     }
-    if (g_E) {
-        // warp + block reduction, one atomic per block
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gE_local += __shfl_xor_sync(0xffffffffu, gE_local, o);
-        __shared__ float red[32];
-        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) red[wid] = gE_local;
-        __syncthreads();
-        if (wid == 0) {
-            float vsum = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
-            if (lane == 0) atomicAdd(g_E, vsum);
-        }
+    if (g_E) {  // one atomic per block
+        const float sum = block_sum(gE_local);
+        if (threadIdx.x == 0) atomicAdd(g_E, sum);
     }
 }
 

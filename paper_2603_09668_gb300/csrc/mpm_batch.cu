@@ -23,12 +23,21 @@
 // The sort is one counting sort over all scenes: scene s's keys are offset by
 // the number of keys of the scenes before it, so the sorted order keeps every
 // scene inside its own particle range.
+//
+// Reverse mode (checkpointed segments): the states inside a segment are
+// recomputed one substep at a time into a caller-owned tape; each reverse
+// substep then runs over all scenes at once as five launches: P2G and the
+// grid update of the substep's input (the grid kept for the reverse pass),
+// reverse G2P (scatter of dL/dv_i into each scene's adjoint grid), reverse
+// grid update (dL/dm_i, dL/dp_i, the scene's wind gradient) and reverse P2G
+// (gather to the particles, per-scene dL/dE).
 #include <math.h>
 
 #include <algorithm>
 #include <new>
 #include <vector>
 
+#include "mpm_adjoint.cuh"
 #include "mpm_handle.cuh"
 
 namespace dw {
@@ -100,7 +109,9 @@ __device__ __forceinline__ bool batch_grid_sync(unsigned *bar, int *err, unsigne
 }
 
 // Phase A: grid update of the blocks in list L at time t0 + k dt (per scene).
-template <int THREADS>
+// CLEAR: also empty (m, p) and the block flags for the next P2G; without it
+// the grid and the list stay for a reverse pass.
+template <int THREADS, bool CLEAR = true>
 __device__ __forceinline__ void batch_grid_phase(const BatchView &A, int k, int L) {
     constexpr int SUBS = THREADS / 64;
     const int count = A.count[L];
@@ -116,9 +127,9 @@ __device__ __forceinline__ void batch_grid_phase(const BatchView &A, int k, int 
         if (active_node(P, S.nb, b, lt, i, j, kk)) {
             const int64_t node = ((int64_t)kk * P.N + j) * P.N + i;
             grid_node_update(P, S.wind, fmaf((float)k, P.dt, t0), node, i, j, kk, S.grid_mp,
-                             S.grid_v, 1);
+                             S.grid_v, CLEAR ? 1 : 0);
         }
-        if (lt == 0) S.flags[b] = 0;
+        if (CLEAR && lt == 0) S.flags[b] = 0;
     }
 }
 
@@ -268,6 +279,130 @@ __global__ void __launch_bounds__(BATCH_ITEM) k_batch_sort_keys(BatchView A, int
     atomicAdd(&counts[key], 1);
 }
 
+// ---------------------------------------------------------------- reverse --
+
+// Adjoint buffers of a reverse substep over the batch.
+struct BatchAdjView {
+    const int64_t *node_off;  // [n_scenes] first node of each scene in the batch grids
+    const int64_t *wind_off;  // [n_scenes] first float of each scene's wind gradient
+    float4 *grid_bv;          // (0, dL/dv_i), zero between calls
+    float4 *grid_bmp;         // (dL/dm_i, dL/dp_i)
+    float *scratch;           // [12][n]: partial dL/dx_p, dL/dF_p of the reverse G2P
+    float *gx, *gv, *gC, *gF; // dL/d(output state) in, dL/d(input state) out
+    float *g_wind;            // concatenated per-scene wind gradients, or NULL
+    float *g_E;               // [n_scenes], or NULL
+};
+
+// Grid update of list L at substep k keeping (m, p) and the list (the
+// recomputed forward grid of a reverse substep).
+__global__ void __launch_bounds__(256) k_batch_grid_keep(BatchView A, int k, int L) {
+    batch_grid_phase<256, false>(A, k, L);
+}
+
+// Reverse G2P of one work item per CTA: scatter into the scene's grid_bv.
+__global__ void __launch_bounds__(BATCH_ITEM) k_batch_rev_g2p(BatchView A, BatchAdjView R) {
+    __shared__ float4 rows[BATCH_ITEM / 32][32][P2G_ROW];
+    __shared__ int keys[BATCH_ITEM / 32][32];
+    const int wid = threadIdx.x >> 5;
+    const int4 item = A.items[blockIdx.x];
+    const BatchScene &S = A.scenes[item.x];
+    const MpmParams P = S.P;
+    const int64_t n = A.n, p = (int64_t)item.y + threadIdx.x;
+    P2GParticle q;
+    q.valid = false;
+    if ((int)threadIdx.x < item.z) {
+        float xp[3], Fp[9], bxo[3], bvo[3], bCo[9], bFo[9], bx[3], bFin[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xp[a] = A.x[a * n + p];
+            bxo[a] = R.gx[a * n + p];
+            bvo[a] = R.gv[a * n + p];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            Fp[c] = A.F[c * n + p];
+            bCo[c] = R.gC[c * n + p];
+            bFo[c] = R.gF[c * n + p];
+        }
+        rev_g2p_particle(P, xp, Fp, A.pinned && A.pinned[p], S.grid_v, bxo, bvo, bCo, bFo, q, bx,
+                         bFin);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) R.scratch[a * n + p] = bx[a];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) R.scratch[(3 + c) * n + p] = bFin[c];
+    }
+    MpmParams Pz = P;
+    Pz.p_mass = 0.0f;  // no mass channel: grid_bv = (0, dL/dv_i)
+    const ActiveBlocks none{nullptr, nullptr, nullptr, 0, 0};
+    p2g_warp_scatter(Pz, q, R.grid_bv + R.node_off[item.x], none, rows[wid], keys[wid]);
+}
+
+// Reverse grid update of the blocks in list L at substep k; clears the
+// scene's (m, p), grid_bv and block flags.
+__global__ void __launch_bounds__(256) k_batch_rev_grid(BatchView A, BatchAdjView R, int k, int L) {
+    constexpr int SUBS = 256 / 64;
+    const int count = A.count[L];
+    const int *list = A.list + (size_t)L * A.list_cap;
+    const float t0 = *A.t0;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * SUBS + sub; e < count; e += gridDim.x * SUBS) {
+        const int ent = list[e];
+        const int sc = ent >> BATCH_SCENE_SHIFT;
+        const BatchScene &S = A.scenes[sc];
+        const int b = ent & ((1 << BATCH_SCENE_SHIFT) - 1);
+        const MpmParams P = S.P;
+        int i, j, kk;
+        if (active_node(P, S.nb, b, lt, i, j, kk)) {
+            const int64_t node = ((int64_t)kk * P.N + j) * P.N + i;
+            const int64_t no = R.node_off[sc];
+            rev_grid_node(P, S.wind, fmaf((float)k, P.dt, t0), node, i, j, kk, S.grid_mp,
+                          R.grid_bv + no, R.grid_bmp + no,
+                          R.g_wind ? R.g_wind + R.wind_off[sc] : nullptr);
+        }
+        if (lt == 0) S.flags[b] = 0;
+    }
+}
+
+// Reverse P2G of one work item per CTA; one dL/dE atomic per item.
+__global__ void __launch_bounds__(BATCH_ITEM) k_batch_rev_p2g(BatchView A, BatchAdjView R, int L) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.count[L] = 0;  // the reverse grid consumed list L
+    const int4 item = A.items[blockIdx.x];
+    const BatchScene &S = A.scenes[item.x];
+    const MpmParams P = S.P;
+    const int64_t n = A.n, p = (int64_t)item.y + threadIdx.x;
+    float gE = 0.0f;
+    if ((int)threadIdx.x < item.z) {
+        float xp[3], vp[3], Cp[9], Fp[9], bx[3], bF[9], bvp[3], bC[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xp[a] = A.x[a * n + p];
+            vp[a] = A.v[a * n + p];
+            bx[a] = R.scratch[a * n + p];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            Cp[c] = A.C[c * n + p];
+            Fp[c] = A.F[c * n + p];
+            bF[c] = R.scratch[(3 + c) * n + p];
+        }
+        rev_p2g_particle(P, xp, vp, Cp, Fp, R.grid_bmp + R.node_off[item.x], bx, bF, bvp, bC, gE);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R.gx[a * n + p] = bx[a];
+            R.gv[a * n + p] = bvp[a];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            R.gC[c * n + p] = bC[c];
+            R.gF[c * n + p] = bF[c];
+        }
+    }
+    if (R.g_E) {
+        const float sum = block_sum(gE);
+        if (threadIdx.x == 0) atomicAdd(R.g_E + item.x, sum);
+    }
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_coop(void (*kernel)(KArgs...), unsigned grid, unsigned block,
                                cudaStream_t s, Args... args) {
@@ -317,6 +452,12 @@ struct dw_mpm_batch_s {
     float *roll_state = nullptr;
     uint8_t *roll_pinned = nullptr;
     int32_t *roll_ids = nullptr;
+    // reverse mode (allocated by the first mpm_batch_segment_adjoint)
+    std::vector<int64_t> wind_off;  // [n_scenes + 1] floats of the scenes' wind values
+    std::vector<int64_t> node_off;  // [n_scenes + 1]
+    int64_t *d_node_off = nullptr, *d_wind_off = nullptr;
+    float4 *grid_bv = nullptr, *grid_bmp = nullptr;
+    float *adj_scratch = nullptr;
     dw_batch_config cfg = {};
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -409,9 +550,10 @@ static dw_status launch_substep(dw_mpm_batch h, const BatchView &A, const dw_bat
 }
 
 // The launch sequence of a rollout (the time t0 is already on the device).
+// Substep k of the sequence runs at t0 + (k_base + k) dt.
 static dw_status enqueue_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint8_t *pinned,
                                  int32_t *ids, int n_substeps, int sort_every,
-                                 const dw_batch_config &c, cudaStream_t s) {
+                                 const dw_batch_config &c, cudaStream_t s, int k_base = 0) {
     const int64_t n = h->n_total;
     DW_CUDA(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), s));
     dw_mpm_state cur = *state, oth = state_view(h->roll_state, n);
@@ -433,7 +575,7 @@ static dw_status enqueue_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint
         DW_LAUNCHED("k_batch_p2g");
         for (int j = 0; j < len; ++j) {
             const bool final_ = j + 1 == len;
-            dw_status st = launch_substep(h, A, c, k0 + j, L, final_, s);
+            dw_status st = launch_substep(h, A, c, k_base + k0 + j, L, final_, s);
             if (st != DW_OK) return st;
             if (!final_) L = 1 - L;
         }
@@ -517,6 +659,7 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
     std::vector<BatchScene> tab(n_scenes);
     std::vector<int64_t> offsets(n_scenes + 1, 0);
     std::vector<int64_t> node_off(n_scenes + 1, 0), blk_off(n_scenes + 1, 0);
+    std::vector<int64_t> wind_off(n_scenes + 1, 0);
     int64_t total_keys = 0;
     for (int s = 0; s < n_scenes; ++s) {
         const dw_mpm_scene &sc = scenes[s];
@@ -537,6 +680,8 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
         offsets[s + 1] = offsets[s] + sc.n_particles;
         node_off[s + 1] = node_off[s] + (int64_t)d.n_grid * d.n_grid * d.n_grid;
         blk_off[s + 1] = blk_off[s] + (int64_t)nb * nb * nb;
+        wind_off[s + 1] = wind_off[s] + (int64_t)sc.wind.n_frames * sc.wind.nf * sc.wind.nf *
+                                            sc.wind.nf * 3;
         DW_REQUIRE(total_keys < (1ll << 31), "the scenes' grids are too large for one batch");
         DW_REQUIRE(offsets[s + 1] < (1ll << 31), "more than 2^31 - 1 particles in the batch");
     }
@@ -553,6 +698,8 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
     }
     h->n_scenes = n_scenes;
     h->offsets = offsets;
+    h->node_off = node_off;
+    h->wind_off = wind_off;
     h->n_total = offsets[n_scenes];
     h->total_keys = total_keys;
     h->list_cap = (int)blk_off[n_scenes];
@@ -641,6 +788,11 @@ extern "C" dw_status mpm_batch_destroy(dw_mpm_batch h) {
     cudaFree(h->roll_state);
     cudaFree(h->roll_pinned);
     cudaFree(h->roll_ids);
+    cudaFree(h->d_node_off);
+    cudaFree(h->d_wind_off);
+    cudaFree(h->grid_bv);
+    cudaFree(h->grid_bmp);
+    cudaFree(h->adj_scratch);
     delete h;
     return DW_OK;
 }
@@ -809,5 +961,121 @@ extern "C" dw_status mpm_batch_tune(dw_mpm_batch h, const dw_mpm_state *state,
     h->cfg.use_graph = use_graph;
     h->cfg.graph_active = 0;
     if (best) *best = h->cfg;
+    return DW_OK;
+}
+
+extern "C" dw_status mpm_batch_wind_layout(dw_mpm_batch h, int64_t *n_floats, int64_t *offsets) {
+    DW_REQUIRE(h, "handle is NULL");
+    if (n_floats) *n_floats = h->wind_off[h->n_scenes];
+    if (offsets)
+        for (int s = 0; s <= h->n_scenes; ++s) offsets[s] = h->wind_off[s];
+    return DW_OK;
+}
+
+namespace dw {
+
+// The reverse-mode workspace, allocated once per handle.
+static dw_status ensure_adjoint(dw_mpm_batch h) {
+    if (h->adj_scratch) return DW_OK;
+    const int64_t nodes = h->node_off[h->n_scenes], n = h->n_total;
+    cudaError_t e = cudaMalloc((void **)&h->grid_bv, sizeof(float4) * (size_t)nodes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->grid_bmp, sizeof(float4) * (size_t)nodes);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&h->d_node_off, sizeof(int64_t) * (size_t)h->n_scenes);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&h->d_wind_off, sizeof(int64_t) * (size_t)h->n_scenes);
+    if (e == cudaSuccess) e = cudaMemset(h->grid_bv, 0, sizeof(float4) * (size_t)nodes);
+    if (e == cudaSuccess) e = cudaMemset(h->grid_bmp, 0, sizeof(float4) * (size_t)nodes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_node_off, h->node_off.data(), sizeof(int64_t) * (size_t)h->n_scenes,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_wind_off, h->wind_off.data(), sizeof(int64_t) * (size_t)h->n_scenes,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->adj_scratch, sizeof(float) * 12 * (size_t)n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->grid_bv);
+        cudaFree(h->grid_bmp);
+        cudaFree(h->d_node_off);
+        cudaFree(h->d_wind_off);
+        cudaFree(h->adj_scratch);
+        h->grid_bv = h->grid_bmp = nullptr;
+        h->d_node_off = h->d_wind_off = nullptr;
+        h->adj_scratch = nullptr;
+        if (e == cudaErrorMemoryAllocation) {
+            set_error("out of device memory for the batch's reverse-mode workspace");
+            return DW_ERR_OOM;
+        }
+        return cuda_fail(e, "mpm_batch_segment_adjoint");
+    }
+    return DW_OK;
+}
+
+}  // namespace dw
+
+extern "C" dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *start,
+                                               float *tape, int64_t tape_floats,
+                                               const dw_mpm_state *g, const uint8_t *pinned,
+                                               float t0, int32_t n_substeps, float *g_wind,
+                                               float *g_E, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_batch_state(h, start);
+    if (st != DW_OK) return st;
+    st = check_batch_state(h, g);
+    if (st != DW_OK) return st;
+    DW_REQUIRE(n_substeps >= 0, "n_substeps must be >= 0");
+    if (n_substeps == 0) return DW_OK;
+    const int64_t n = h->n_total;
+    const int64_t need = (int64_t)(n_substeps - 1) * 24 * n;
+    DW_REQUIRE(n_substeps == 1 || (tape && tape_floats >= need),
+               "tape holds %lld floats; %d substeps of %lld particles need %lld",
+               (long long)tape_floats, n_substeps, (long long)n, (long long)need);
+    st = ensure_adjoint(h);
+    if (st != DW_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    k_batch_set_time<<<1, 1, 0, s>>>(h->t0, t0);
+    DW_LAUNCHED("k_batch_set_time");
+    auto slot = [&](int k) {  // state k (1 .. n_substeps - 1) in the tape
+        return state_view(tape + (size_t)(k - 1) * 24 * (size_t)n, n);
+    };
+    uint8_t *pin = const_cast<uint8_t *>(pinned);  // not written: the recompute never sorts
+    const size_t b3 = sizeof(float) * 3 * (size_t)n, b9 = sizeof(float) * 9 * (size_t)n;
+    for (int k = 1; k < n_substeps; ++k) {
+        const dw_mpm_state src = k == 1 ? *start : slot(k - 1), dst = slot(k);
+        DW_CUDA(cudaMemcpyAsync(dst.x, src.x, b3, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(dst.v, src.v, b3, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(dst.C, src.C, b9, cudaMemcpyDeviceToDevice, s));
+        DW_CUDA(cudaMemcpyAsync(dst.F, src.F, b9, cudaMemcpyDeviceToDevice, s));
+        st = enqueue_rollout(h, &dst, pin, nullptr, 1, 0, h->cfg, s, k - 1);
+        if (st != DW_OK) return st;
+    }
+    BatchAdjView R;
+    R.node_off = h->d_node_off;
+    R.wind_off = h->d_wind_off;
+    R.grid_bv = h->grid_bv;
+    R.grid_bmp = h->grid_bmp;
+    R.scratch = h->adj_scratch;
+    R.gx = g->x;
+    R.gv = g->v;
+    R.gC = g->C;
+    R.gF = g->F;
+    R.g_wind = g_wind;
+    R.g_E = g_E;
+    const unsigned ggrid = (unsigned)(8 * h->num_sms);
+    for (int j = n_substeps - 1; j >= 0; --j) {
+        const dw_mpm_state in = j == 0 ? *start : slot(j);
+        const BatchView A = view_of(h, in, pinned);
+        k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, 0);
+        DW_LAUNCHED("k_batch_p2g");
+        k_batch_grid_keep<<<ggrid, 256, 0, s>>>(A, j, 0);
+        DW_LAUNCHED("k_batch_grid_keep");
+        k_batch_rev_g2p<<<h->n_items, BATCH_ITEM, 0, s>>>(A, R);
+        DW_LAUNCHED("k_batch_rev_g2p");
+        k_batch_rev_grid<<<ggrid, 256, 0, s>>>(A, R, j, 0);
+        DW_LAUNCHED("k_batch_rev_grid");
+        k_batch_rev_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, R, 0);
+        DW_LAUNCHED("k_batch_rev_p2g");
+    }
     return DW_OK;
 }

@@ -17,7 +17,7 @@ import oracle
 from paper_2603_09668_gb300 import binding as B
 from paper_2603_09668_gb300 import inputs
 
-from gpu_util import f64, max_rel, state_to_np, to_dev, wind_dev, wind_ref
+from gpu_util import f64, max_rel, rel_l2, state_to_np, to_dev, wind_dev, wind_ref
 
 pytestmark = pytest.mark.gpu
 
@@ -228,4 +228,127 @@ def test_domain_error_is_reported_per_batch():
         batch.device_status()
     assert ei.value.status == 5  # DW_ERR_DOMAIN
     batch.device_status()  # cleared
+    batch.close()
+
+
+# ---------------------------------------------------------------- reverse --
+
+def batch_adjoint(scenes, n_sub, g_seed=4):
+    """mpm_batch_segment_adjoint over n_sub substeps from the scenes' states
+    with a random dL/d(final state): (batch, gradient state, g_wind, g_E,
+    the seed gradient, the tape)."""
+    st, pin = concat(scenes)
+    batch = make_batch(scenes, n_sub * DT)
+    rng = np.random.default_rng(g_seed)
+    g_out = tuple(rng.standard_normal(a.shape).astype(np.float32) for a in st)
+    g = dev_state(g_out)
+    nw, _ = batch.wind_layout()
+    g_wind = torch.zeros(nw, dtype=torch.float32, device="cuda")
+    g_E = torch.zeros(len(scenes), dtype=torch.float32, device="cuda")
+    tape = torch.empty(max(n_sub - 1, 1) * 24 * batch.n, dtype=torch.float32, device="cuda")
+    batch.segment_adjoint(dev_state(st), tape, g, to_dev(pin), 0.0, n_sub, g_wind, g_E)
+    batch.device_status()
+    return batch, state_to_np(g), g_wind.cpu().numpy(), g_E.cpu().numpy(), g_out, tape
+
+
+def test_wind_layout_concatenates_the_scenes_wind_values():
+    scenes = small_scenes()
+    batch = make_batch(scenes, DT)
+    total, offs = batch.wind_layout()
+    sizes = [sc[3].size for sc in scenes]
+    assert offs == [int(v) for v in np.concatenate([[0], np.cumsum(sizes)])]
+    assert total == sum(sizes)
+    batch.close()
+
+
+def test_batch_segment_adjoint_matches_each_scene_alone():
+    """Every scene's gradients (state, wind, E) from one batched segment
+    adjoint equal those of mpm_segment_adjoint on the scene alone, up to the
+    float atomics' summation order (relative L2 1e-4), and the batched tape
+    holds the same recomputed states."""
+    scenes = small_scenes()
+    n_sub = 10
+    batch, gb, gw, gE, g_out, tape = batch_adjoint(scenes, n_sub)
+    _, woff = batch.wind_layout()
+    n = batch.n
+    tape_np = tape.cpu().numpy()
+    for s, (params, st, pinned, wind) in enumerate(scenes):
+        sl = batch.scene_slice(s)
+        ns = st[0].shape[1]
+        mpm = B.MPM.from_params(params, max_particles=ns)
+        g = dev_state(tuple(a[:, sl] for a in g_out))
+        gw_s = torch.zeros(wind.size, dtype=torch.float32, device="cuda")
+        gE_s = torch.zeros(1, dtype=torch.float32, device="cuda")
+        tape_s = torch.empty((n_sub - 1) * 24 * ns, dtype=torch.float32, device="cuda")
+        mpm.segment_adjoint(dev_state(st), tape_s, g, to_dev(pinned), wind_dev(wind, n_sub * DT),
+                            0.0, n_sub, gw_s, gE_s)
+        mpm.device_status()
+        ref = state_to_np(g)
+        for name, a, b in zip("xvCF", gb, ref):
+            assert rel_l2(a[:, sl], b) <= 1e-4, (s, name, rel_l2(a[:, sl], b))
+        assert rel_l2(gw[woff[s]:woff[s + 1]], gw_s.cpu().numpy().ravel()) <= 1e-4, s
+        assert abs(gE[s] - gE_s.item()) <= 1e-4 * abs(gE_s.item()) + 1e-12, (s, gE[s], gE_s.item())
+        # the last recomputed state of the segment, scene s's columns
+        last = tape_np[(n_sub - 2) * 24 * n:(n_sub - 1) * 24 * n].reshape(24, n)[:, sl]
+        last_s = tape_s.cpu().numpy()[(n_sub - 2) * 24 * ns:].reshape(24, ns)
+        assert np.abs(last[0:3] - last_s[0:3]).max() <= 1e-6, s  # positions
+        mpm.close()
+    batch.close()
+
+
+def test_batch_segment_adjoint_matches_oracle():
+    """One block scene (fixed-corotated) and one pinned sheet scene
+    (Neo-Hookean) of the batch against the FP64 oracle's reverse mode of the
+    same 6 substeps (forward states recomputed by the oracle)."""
+    scenes = small_scenes()
+    n_sub = 6
+    batch, gb, gw, gE, g_out, _ = batch_adjoint(scenes, n_sub, g_seed=9)
+    _, woff = batch.wind_layout()
+    for s in (0, 4):
+        params, st, pinned, wind = scenes[s]
+        sl = batch.scene_slice(s)
+        w = wind_ref(wind, n_sub * DT)
+        states = [f64(st)]
+        for k in range(n_sub - 1):
+            states.append(oracle.mpm_substep(params, states[-1], w, k * DT, pinned))
+        g = tuple(np.asarray(a[:, sl], np.float64) for a in g_out)
+        g_wind = np.zeros(wind.shape)
+        g_E = 0.0
+        for k in reversed(range(n_sub)):
+            g, g_wind, e = oracle.mpm_substep_adjoint(params, states[k], w, k * DT, g, pinned,
+                                                      g_wind)
+            g_E += e
+        for name, a, b in zip("xvCF", gb, g):
+            assert rel_l2(a[:, sl], b) <= 1e-4, (s, name, rel_l2(a[:, sl], b))
+        assert rel_l2(gw[woff[s]:woff[s + 1]], g_wind.ravel()) <= 1e-4, s
+        assert abs(gE[s] - g_E) <= 1e-4 * abs(g_E), (s, gE[s], g_E)
+    batch.close()
+
+
+def test_batch_segment_adjoint_edge_cases():
+    """One substep needs no tape; a short tape is rejected before any launch;
+    gradients accumulate into g_wind and g_E across calls."""
+    scenes = small_scenes()[:3]
+    st, pin = concat(scenes)
+    batch = make_batch(scenes, 4 * DT)
+    nw, _ = batch.wind_layout()
+    g_wind = torch.zeros(nw, device="cuda")
+    g_E = torch.zeros(3, device="cuda")
+    rng = np.random.default_rng(1)
+    g_out = tuple(rng.standard_normal(a.shape).astype(np.float32) for a in st)
+    g1 = dev_state(g_out)
+    batch.segment_adjoint(dev_state(st), None, g1, to_dev(pin), 0.0, 1, g_wind, g_E)
+    batch.device_status()
+    gw1, gE1 = g_wind.clone(), g_E.clone()
+    g2 = dev_state(g_out)
+    batch.segment_adjoint(dev_state(st), None, g2, to_dev(pin), 0.0, 1, g_wind, g_E)
+    batch.device_status()
+    for a, b in zip(g1, g2):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * a.abs().max().item())
+    assert torch.allclose(g_wind, 2 * gw1, rtol=1e-4, atol=1e-6 * gw1.abs().max().item())
+    assert torch.allclose(g_E, 2 * gE1, rtol=1e-4, atol=1e-12)
+    short = torch.empty(24 * batch.n - 1, device="cuda")
+    with pytest.raises(B.DiffWindError) as ei:
+        batch.segment_adjoint(dev_state(st), short, dev_state(g_out), to_dev(pin), 0.0, 2)
+    assert ei.value.status == 1  # DW_ERR_ARG
     batch.close()
