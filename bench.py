@@ -682,7 +682,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.only in ("lbm", "adjoint", "surrogate", "batch"):
+    elif a.only in ("lbm", "adjoint", "surrogate", "batch", "batch_adjoint"):
         run_only(a)
     else:
         run_ours(a)
