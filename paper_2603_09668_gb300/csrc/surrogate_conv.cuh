@@ -62,11 +62,34 @@ __device__ __forceinline__ void mma_16816(float (&d)[4], uint32_t a0, uint32_t a
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z), evaluated in the tanh form of Hendrycks and Gimpel,
+// 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), with the hardware tanh
+// approximation. The tanh form is within 4.8e-4 (absolute, at z = 2.7) of
+// z Phi(z) for every z, and its derivative within 8.7e-4 of Phi(z) + z phi(z);
+// both stay below the BF16 rounding of the stored activations, and the form
+// costs about a quarter of the instructions of the erf form. gelu_grad_f is
+// the derivative of the same tanh form.
+constexpr float GELU_C = 0.7978845608028654f;  // sqrt(2/pi)
+constexpr float GELU_A = 0.044715f;
+
+__device__ __forceinline__ float tanh_approx(float u) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    return t;
+}
+
+__device__ __forceinline__ float gelu_f(float z) {
+    const float t = tanh_approx(z * fmaf(GELU_A * GELU_C, z * z, GELU_C));
+    const float hz = 0.5f * z;
+    return fmaf(hz, t, hz);
+}
 
 __device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-           z * 0.39894228040143268f * expf(-0.5f * z * z);
+    const float z2 = z * z;
+    const float t = tanh_approx(z * fmaf(GELU_A * GELU_C, z2, GELU_C));
+    // d/dz [0.5 z (1 + t)] = 0.5 (1 + t) + 0.5 z (1 - t^2) sqrt(2/pi) (1 + 3 a z^2)
+    const float du = fmaf(3.0f * GELU_A * GELU_C, z2, GELU_C);
+    return fmaf(0.5f * z * fmaf(-t, t, 1.0f), du, 0.5f * (1.0f + t));
 }
 
 // Loads the 18 x 10 x 3 input halo of the tile at (x0, y0, z0) into smem.
