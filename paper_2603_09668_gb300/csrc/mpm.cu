@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
     int64_t n, int64_t cap) {
     __shared__ float4 rows[P2G_WARP_THREADS / 32][32][P2G_ROW];
     __shared__ int keys[P2G_WARP_THREADS / 32][32];
+    pdl_wait();
+    pdl_trigger();
     const int wid = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     P2GParticle q;
@@ -130,6 +132,8 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
 __global__ void __launch_bounds__(GRID_THREADS) k_rev_grid_active(
     MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_bv,
     float4 *__restrict__ grid_bmp, float *__restrict__ g_wind, ActiveBlocks ab) {
+    pdl_wait();
+    pdl_trigger();
     const int count = *ab.count;
     const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
     for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
@@ -149,6 +153,8 @@ __global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float 
                           float *__restrict__ gx, float *__restrict__ gv, float *__restrict__ gC,
                           float *__restrict__ gF, float *__restrict__ g_E, int64_t n, int64_t cap,
                           int *reset_count) {
+    pdl_wait();
+    pdl_trigger();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (reset_count && p == 0) *reset_count = 0;  // the reverse grid update has consumed the list
     float gE_local = 0.0f;
@@ -313,9 +319,8 @@ dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *nam
 static dw_status launch_grid_update(MpmHandle *h, const WindDev &wd, float t, int clear,
                                     cudaStream_t st) {
     ProfScope ps(h, DW_K_GRID, st);
-    k_grid_update_active<<<GRID_CTAS, GRID_THREADS, 0, st>>>(h->P, wd, t, h->grid_mp, h->grid_v,
-                                                             clear, active_blocks(h));
-    DW_LAUNCHED("k_grid_update_active");
+    DW_CUDA(launch_pdl(k_grid_update_active, GRID_CTAS, GRID_THREADS, st, h->P, wd, t, h->grid_mp,
+                       h->grid_v, clear, active_blocks(h)));
     return DW_OK;
 }
 
@@ -485,9 +490,9 @@ extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_
     if (st != DW_OK) return st;
     if (n > 0) {
         ProfScope ps(h, DW_K_G2P, s);
-        k_g2p<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v, out->x,
-                                               out->v, out->C, out->F, n, h->err, h->block_count);
-        DW_LAUNCHED("k_g2p");
+        DW_CUDA(launch_pdl(k_g2p, grid_for(n, 128), 128, s, h->P, (const float *)in->x,
+                           (const float *)in->F, pinned, (const float4 *)h->grid_v, out->x, out->v,
+                           out->C, out->F, n, h->err, h->block_count));
     }
     return DW_OK;
 }
@@ -520,23 +525,20 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
     if (st != DW_OK) return st;
     if (n > 0) {
         ProfScope ps(h, DW_K_REV_G2P, s);
-        k_rev_g2p<<<grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, 0, s>>>(h->P, in->x, in->F, pinned, h->grid_v,
-                                                   g_out->x, g_out->v, g_out->C, g_out->F,
-                                                   h->grid_bv, h->pscratch, n, cap);
-        DW_LAUNCHED("k_rev_g2p");
+        DW_CUDA(launch_pdl(k_rev_g2p, grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, s, h->P,
+                           in->x, in->F, pinned, h->grid_v, g_out->x, g_out->v, g_out->C,
+                           g_out->F, h->grid_bv, h->pscratch, n, cap));
     }
     {
         ProfScope ps(h, DW_K_REV_GRID, s);
-        k_rev_grid_active<<<GRID_CTAS, GRID_THREADS, 0, s>>>(h->P, wd, t, h->grid_mp, h->grid_bv,
-                                                             h->grid_bmp, g_wind, active_blocks(h));
+        DW_CUDA(launch_pdl(k_rev_grid_active, GRID_CTAS, GRID_THREADS, s, h->P, wd, t, h->grid_mp,
+                           h->grid_bv, h->grid_bmp, g_wind, active_blocks(h)));
     }
-    DW_LAUNCHED("k_rev_grid_active");
     if (n > 0) {
         ProfScope ps(h, DW_K_REV_P2G, s);
-        k_rev_p2g<<<grid_for(n, 128), 128, 0, s>>>(h->P, in->x, in->v, in->C, in->F, h->grid_bmp,
-                                                   h->pscratch, g_in->x, g_in->v, g_in->C,
-                                                   g_in->F, g_E, n, cap, h->block_count);
-        DW_LAUNCHED("k_rev_p2g");
+        DW_CUDA(launch_pdl(k_rev_p2g, grid_for(n, 128), 128, s, h->P, in->x, in->v, in->C, in->F,
+                           h->grid_bmp, h->pscratch, g_in->x, g_in->v, g_in->C, g_in->F, g_E, n,
+                           cap, h->block_count));
     }
     return DW_OK;
 }

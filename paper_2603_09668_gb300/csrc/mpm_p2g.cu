@@ -10,6 +10,8 @@ __global__ void __launch_bounds__(128) k_p2g_atomic(MpmParams P, const float *__
                                                     const float *__restrict__ F, int64_t n,
                                                     float4 *__restrict__ grid, int *err,
                                                     ActiveBlocks ab) {
+    pdl_wait();
+    pdl_trigger();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     P2GParticle q;
     p2g_load(P, x, v, C, F, n, p, q, err);
@@ -28,6 +30,8 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_p2g_warp(MpmParams P,
                                                              int *err, ActiveBlocks ab) {
     __shared__ float4 rows[P2G_WARP_THREADS / 32][32][P2G_ROW];
     __shared__ int keys[P2G_WARP_THREADS / 32][32];
+    pdl_wait();
+    pdl_trigger();
     const int wid = threadIdx.x >> 5;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     P2GParticle q;
@@ -54,6 +58,8 @@ __global__ void __launch_bounds__(P2G_TILE_THREADS) k_p2g_tile(MpmParams P,
     __shared__ float tile[4][P2G_TILE_NODES];
     __shared__ int red_lo[3][P2G_TILE_THREADS / 32], red_hi[3][P2G_TILE_THREADS / 32];
     __shared__ int box[6];
+    pdl_wait();
+    pdl_trigger();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int64_t p = (int64_t)blockIdx.x * P2G_TILE_THREADS + tid;
     P2GParticle q;
@@ -134,13 +140,14 @@ dw_status launch_p2g(int mode, const MpmParams &P, const float *x, const float *
                             const ActiveBlocks &ab, cudaStream_t st) {
     if (n == 0) return DW_OK;
     if (mode == DW_P2G_ATOMIC) {
-        k_p2g_atomic<<<grid_for(n, 128), 128, 0, st>>>(P, x, v, C, F, n, grid, err, ab);
+        DW_CUDA(launch_pdl(k_p2g_atomic, grid_for(n, 128), 128, st, P, x, v, C, F, n, grid, err, ab));
     } else if (mode == DW_P2G_WARP || mode == DW_P2G_AUTO) {
-        k_p2g_warp<<<grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, 0, st>>>(P, x, v, C, F, n, grid, err, ab);
+        DW_CUDA(launch_pdl(k_p2g_warp, grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, st, P, x, v,
+                           C, F, n, grid, err, ab));
     } else {
-        k_p2g_tile<<<grid_for(n, P2G_TILE_THREADS), P2G_TILE_THREADS, 0, st>>>(P, x, v, C, F, n, grid, err, ab);
+        DW_CUDA(launch_pdl(k_p2g_tile, grid_for(n, P2G_TILE_THREADS), P2G_TILE_THREADS, st, P, x, v,
+                           C, F, n, grid, err, ab));
     }
-    DW_LAUNCHED("p2g");
     return DW_OK;
 }
 

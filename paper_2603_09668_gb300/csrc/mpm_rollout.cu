@@ -30,8 +30,10 @@ __device__ __forceinline__ void load_xF(const float *x, const float *F, int64_t 
 // completed once this one runs (the grid update in between waits for it before
 // it lets this kernel start), and the loads go through L2; only grid_v, which
 // the grid update writes, is read after the wait.
+// Ten resident CTAs per SM (48 registers, a few spilled) hide more of the
+// grid-velocity gather latency than the eight that 64 registers allow.
 template <bool STORE_VC>
-__global__ void __launch_bounds__(P2G_WARP_THREADS) k_g2p2g(
+__global__ void __launch_bounds__(P2G_WARP_THREADS, 10) k_g2p2g(
     MpmParams P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
     float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
     float4 *__restrict__ grid_next, int64_t n, int *err, ActiveBlocks ab_next, int *reset_count) {
