@@ -345,9 +345,14 @@ DW_API dw_status mpm_batch_wind_layout(dw_mpm_batch h, int64_t *n_floats, int64_
  * n_substeps - 1 from `start` (state 0 of the concatenated batch, substep j
  * of scene s at t0 + j dt_s) into `tape` (device float, (n_substeps - 1) *
  * 24 * n floats, each state as x, v, C, F back to back; caller-owned,
- * tape_floats its size) with the handle's launch configuration (without a
- * graph), then runs the reverse substeps from the last to the first, each as
- * five launches over all scenes. g (concatenated, n particles) holds
+ * tape_floats its size) with the handle's launch configuration, then runs
+ * the reverse substeps from the last to the first, each as five launches over
+ * all scenes. With use_graph the whole sequence is captured once per distinct
+ * (tape, g, pinned, g_wind, g_E, n_substeps, configuration) in a CUDA graph
+ * owned by the handle and replayed; `start` is first copied into the handle's
+ * workspace, so successive segments with different start states share one
+ * graph (the workspace is the one mpm_batch_rollout and mpm_batch_tune use;
+ * calls on one handle must not overlap). g (concatenated, n particles) holds
  * dL/d(state after the segment) on entry and is overwritten with
  * dL/d(start). g_wind (device, mpm_batch_wind_layout floats, or NULL)
  * accumulates each scene's dL/d(wind values) at its offset; g_E (device

@@ -430,6 +430,18 @@ struct GraphKey {
     }
 };
 
+// Pointers and shape a captured segment adjoint was recorded with.
+struct AdjKey {
+    const void *ptr[12];
+    int n_substeps, mode, threads, ctas_per_sm;
+    bool operator==(const AdjKey &o) const {
+        for (int i = 0; i < 12; ++i)
+            if (ptr[i] != o.ptr[i]) return false;
+        return n_substeps == o.n_substeps && mode == o.mode && threads == o.threads &&
+               ctas_per_sm == o.ctas_per_sm;
+    }
+};
+
 }  // namespace dw
 
 struct dw_mpm_batch_s {
@@ -458,6 +470,9 @@ struct dw_mpm_batch_s {
     int64_t *d_node_off = nullptr, *d_wind_off = nullptr;
     float4 *grid_bv = nullptr, *grid_bmp = nullptr;
     float *adj_scratch = nullptr;
+    cudaGraphExec_t adj_exec = nullptr;  // captured segment adjoint
+    dw::AdjKey adj_key = {};
+    bool adj_graph_broken = false;
     dw_batch_config cfg = {};
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -770,6 +785,7 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
 extern "C" dw_status mpm_batch_destroy(dw_mpm_batch h) {
     if (!h) return DW_OK;
     drop_graph(h);
+    if (h->adj_exec) cudaGraphExecDestroy(h->adj_exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->scenes);
     cudaFree(h->items);
@@ -1014,28 +1030,17 @@ static dw_status ensure_adjoint(dw_mpm_batch h) {
 
 }  // namespace dw
 
-extern "C" dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *start,
-                                               float *tape, int64_t tape_floats,
-                                               const dw_mpm_state *g, const uint8_t *pinned,
-                                               float t0, int32_t n_substeps, float *g_wind,
-                                               float *g_E, dw_stream stream) {
-    DW_REQUIRE(h, "handle is NULL");
-    dw_status st = check_batch_state(h, start);
-    if (st != DW_OK) return st;
-    st = check_batch_state(h, g);
-    if (st != DW_OK) return st;
-    DW_REQUIRE(n_substeps >= 0, "n_substeps must be >= 0");
-    if (n_substeps == 0) return DW_OK;
+namespace dw {
+
+// The launch sequence of a segment adjoint (the time t0 is already on the
+// device): the recompute of states 1 .. n_substeps - 1 into the tape, then
+// the reverse substeps.
+static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *start, float *tape,
+                                         const dw_mpm_state *g, const uint8_t *pinned,
+                                         int n_substeps, float *g_wind, float *g_E,
+                                         cudaStream_t s) {
     const int64_t n = h->n_total;
-    const int64_t need = (int64_t)(n_substeps - 1) * 24 * n;
-    DW_REQUIRE(n_substeps == 1 || (tape && tape_floats >= need),
-               "tape holds %lld floats; %d substeps of %lld particles need %lld",
-               (long long)tape_floats, n_substeps, (long long)n, (long long)need);
-    st = ensure_adjoint(h);
-    if (st != DW_OK) return st;
-    cudaStream_t s = as_stream(stream);
-    k_batch_set_time<<<1, 1, 0, s>>>(h->t0, t0);
-    DW_LAUNCHED("k_batch_set_time");
+    dw_status st = DW_OK;
     auto slot = [&](int k) {  // state k (1 .. n_substeps - 1) in the tape
         return state_view(tape + (size_t)(k - 1) * 24 * (size_t)n, n);
     };
@@ -1078,4 +1083,83 @@ extern "C" dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_stat
         DW_LAUNCHED("k_batch_rev_p2g");
     }
     return DW_OK;
+}
+
+// Captures the segment adjoint into h->adj_exec; false (and no error left
+// behind) when it cannot be captured.
+static bool capture_adjoint(dw_mpm_batch h, const dw_mpm_state *start, float *tape,
+                            const dw_mpm_state *g, const uint8_t *pinned, int n_substeps,
+                            float *g_wind, float *g_E) {
+    if (h->adj_exec) cudaGraphExecDestroy(h->adj_exec);
+    h->adj_exec = nullptr;
+    if (!h->cap_stream &&
+        cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    dw_status st = enqueue_segment_adjoint(h, start, tape, g, pinned, n_substeps, g_wind, g_E,
+                                           h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    bool ok = st == DW_OK && e == cudaSuccess && graph;
+    if (ok) ok = cudaGraphInstantiate(&h->adj_exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (!ok) h->adj_exec = nullptr;
+    return ok;
+}
+
+}  // namespace dw
+
+extern "C" dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *start,
+                                               float *tape, int64_t tape_floats,
+                                               const dw_mpm_state *g, const uint8_t *pinned,
+                                               float t0, int32_t n_substeps, float *g_wind,
+                                               float *g_E, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    dw_status st = check_batch_state(h, start);
+    if (st != DW_OK) return st;
+    st = check_batch_state(h, g);
+    if (st != DW_OK) return st;
+    DW_REQUIRE(n_substeps >= 0, "n_substeps must be >= 0");
+    if (n_substeps == 0) return DW_OK;
+    const int64_t n = h->n_total;
+    const int64_t need = (int64_t)(n_substeps - 1) * 24 * n;
+    DW_REQUIRE(n_substeps == 1 || (tape && tape_floats >= need),
+               "tape holds %lld floats; %d substeps of %lld particles need %lld",
+               (long long)tape_floats, n_substeps, (long long)n, (long long)need);
+    st = ensure_adjoint(h);
+    if (st != DW_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    k_batch_set_time<<<1, 1, 0, s>>>(h->t0, t0);
+    DW_LAUNCHED("k_batch_set_time");
+    if (h->cfg.use_graph && !h->adj_graph_broken) {
+        // The graph reads the start state from the workspace, so that one
+        // capture serves every segment of a rollout (each starts from its own
+        // checkpoint).
+        const dw_mpm_state ws = state_view(h->roll_state, n);
+        const AdjKey key = {{ws.x, nullptr, nullptr, nullptr, tape, g->x, g->v, g->C, g->F, pinned,
+                             g_wind, g_E},
+                            n_substeps, h->cfg.mode, h->cfg.threads, h->cfg.ctas_per_sm};
+        if (!h->adj_exec || !(key == h->adj_key)) {
+            if (capture_adjoint(h, &ws, tape, g, pinned, n_substeps, g_wind, g_E))
+                h->adj_key = key;
+            else
+                h->adj_graph_broken = true;
+        }
+        if (h->adj_exec) {
+            const size_t b3 = sizeof(float) * 3 * (size_t)n, b9 = sizeof(float) * 9 * (size_t)n;
+            DW_CUDA(cudaMemcpyAsync(ws.x, start->x, b3, cudaMemcpyDeviceToDevice, s));
+            DW_CUDA(cudaMemcpyAsync(ws.v, start->v, b3, cudaMemcpyDeviceToDevice, s));
+            DW_CUDA(cudaMemcpyAsync(ws.C, start->C, b9, cudaMemcpyDeviceToDevice, s));
+            DW_CUDA(cudaMemcpyAsync(ws.F, start->F, b9, cudaMemcpyDeviceToDevice, s));
+            DW_CUDA(cudaGraphLaunch(h->adj_exec, s));
+            return DW_OK;
+        }
+    }
+    return enqueue_segment_adjoint(h, start, tape, g, pinned, n_substeps, g_wind, g_E, s);
 }

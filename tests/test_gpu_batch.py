@@ -352,3 +352,36 @@ def test_batch_segment_adjoint_edge_cases():
         batch.segment_adjoint(dev_state(st), short, dev_state(g_out), to_dev(pin), 0.0, 2)
     assert ei.value.status == 1  # DW_ERR_ARG
     batch.close()
+
+
+def test_batch_segment_adjoint_graph_replay_equals_eager():
+    """Two segments with different start states through the captured graph
+    (the second a replay reading its start from the workspace) equal the
+    same two segments launched eagerly."""
+    scenes = small_scenes()[:4]
+    st, pin = concat(scenes)
+    st2 = tuple(a.copy() for a in st)
+    st2[0][:] += np.float32(1e-3)  # a shifted start state for the second segment
+    n_sub = 5
+    rng = np.random.default_rng(12)
+    g_out = tuple(rng.standard_normal(a.shape).astype(np.float32) for a in st)
+    results = []
+    for use_graph in (1, 0):
+        batch = make_batch(scenes, 2 * n_sub * DT)
+        batch.set_config(B.BATCH_PERSISTENT, 128, 1, use_graph)
+        nw, _ = batch.wind_layout()
+        g_wind = torch.zeros(nw, device="cuda")
+        g_E = torch.zeros(len(scenes), device="cuda")
+        tape = torch.empty((n_sub - 1) * 24 * batch.n, device="cuda")
+        g = dev_state(g_out)
+        p = to_dev(pin)
+        batch.segment_adjoint(dev_state(st2), tape, g, p, n_sub * DT, n_sub, g_wind, g_E)
+        batch.segment_adjoint(dev_state(st), tape, g, p, 0.0, n_sub, g_wind, g_E)
+        batch.device_status()
+        results.append((state_to_np(g), g_wind.cpu().numpy(), g_E.cpu().numpy()))
+        batch.close()
+    (ga, wa, ea), (gb, wb, eb) = results
+    for name, a, b in zip("xvCF", ga, gb):
+        assert rel_l2(a, b) <= 1e-5, (name, rel_l2(a, b))
+    assert rel_l2(wa, wb) <= 1e-5
+    assert np.allclose(ea, eb, rtol=1e-5, atol=1e-12)
