@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
     MpmParams Pz = P;
     Pz.p_mass = 0.0f;  // no mass channel: grid_bv = (0, dL/dv_i)
     const ActiveBlocks none{nullptr, nullptr, nullptr, 0, 0};
-    p2g_warp_scatter(Pz, q, grid_bv, none, rows[wid], keys[wid]);
+    p2g_warp_scatter<true>(Pz, q, grid_bv, none, rows[wid], keys[wid]);
 }
 
 __global__ void __launch_bounds__(GRID_THREADS) k_rev_grid_active(

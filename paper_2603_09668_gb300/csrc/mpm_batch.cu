@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(BATCH_ITEM) k_batch_p2g(BatchView A, int L) {
         p2g_load(P, A.x, A.v, A.C, A.F, A.n, (int64_t)item.y + threadIdx.x, q, A.err);
     const ActiveBlocks ab{S.flags, A.list + (size_t)L * A.list_cap, A.count + L, S.nb,
                           item.x << BATCH_SCENE_SHIFT};
-    p2g_warp_scatter(P, q, S.grid_mp, ab, rows[wid], keys[wid]);
+    p2g_warp_scatter<true>(P, q, S.grid_mp, ab, rows[wid], keys[wid]);
 }
 
 // Sort keys of every scene, offset per scene, counted into counts.
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(BATCH_ITEM) k_batch_rev_g2p(BatchView A, Batch
     MpmParams Pz = P;
     Pz.p_mass = 0.0f;  // no mass channel: grid_bv = (0, dL/dv_i)
     const ActiveBlocks none{nullptr, nullptr, nullptr, 0, 0};
-    p2g_warp_scatter(Pz, q, R.grid_bv + R.node_off[item.x], none, rows[wid], keys[wid]);
+    p2g_warp_scatter<true>(Pz, q, R.grid_bv + R.node_off[item.x], none, rows[wid], keys[wid]);
 }
 
 // Reverse grid update of the blocks in list L at substep k; clears the

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_p2g_warp(MpmParams P,
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     P2GParticle q;
     p2g_load(P, x, v, C, F, n, p, q, err);
-    p2g_warp_scatter(P, q, grid, ab, rows[wid], keys[wid]);
+    p2g_warp_scatter<true>(P, q, grid, ab, rows[wid], keys[wid]);
 }
 
 // --------------------------------------------------------------- tile ------

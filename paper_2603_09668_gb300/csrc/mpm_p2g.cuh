@@ -120,8 +120,10 @@ __device__ __forceinline__ void p2g_scatter_global(const MpmParams &P, const P2G
 // Each warp reduces the contributions of lanes whose particles share a base
 // cell (runs of equal keys among consecutive lanes; after mpm_sort most warps
 // of a dense object are a single run) through a shared-memory transpose: every
-// lane writes its node values (float4: m, p) into its own row, then lane L
-// walks the 32 rows of node L and issues one float4 atomic per run. The 27
+// lane writes its node values (float4: m, p) into its own row, then the rows
+// of each node are summed per run and one float4 atomic per node and run is
+// issued (27 lanes sum a single run or two runs; more runs: lane L walks the
+// 32 rows of node L). The 27
 // stencil nodes go in three passes of 9 to keep the buffer small; a row of 9
 // float4 (144 B) keeps the float4 row stores free of bank conflicts.
 
@@ -129,6 +131,10 @@ constexpr int P2G_WARP_THREADS = 128;
 constexpr int P2G_PASS = 9;  // nodes per pass
 constexpr int P2G_ROW = 9;   // float4 per row
 
+// TWO_RUN enables the 27-lane two-run reduction; it pays off in the
+// standalone scatter kernels, while the fused G2P/P2G kernel, already at its
+// register and instruction-cache limits, runs faster without it.
+template <bool TWO_RUN = false>
 __device__ __forceinline__ void p2g_warp_scatter(const MpmParams &P, P2GParticle &q,
                                                  float4 *__restrict__ grid, const ActiveBlocks &ab,
                                                  float4 (*rows)[P2G_ROW], int *keys) {
@@ -224,6 +230,56 @@ __device__ __forceinline__ void p2g_warp_scatter(const MpmParams &P, P2GParticle
             if (lane < 9 && k >= 0) {
                 const int off = (ok * N + lane / 3) * N + lane % 3;
                 atomicAdd(&grid[(int64_t)k + off], acc);
+            }
+        } else if (TWO_RUN && __popc(starts) == 2) {
+            // Two runs (a warp across one cell boundary, the common case
+            // after it in a dense object): as above, with one accumulator
+            // per run; rows b.. belong to the second run.
+            const int b = __ffs(starts & ~1u) - 1;
+            const int g = lane / 9, L = lane - 9 * g;
+            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+            if (g < 3) {
+                const int r0i = 11 * g, r1i = min(32, r0i + 11);
+#pragma unroll 4
+                for (int r = r0i; r < r1i; ++r) {
+                    const float4 t = rows[r][L];
+                    const float f0 = r < b ? 1.0f : 0.0f, f1 = 1.0f - f0;
+                    a0.x = fmaf(f0, t.x, a0.x);
+                    a0.y = fmaf(f0, t.y, a0.y);
+                    a0.z = fmaf(f0, t.z, a0.z);
+                    a0.w = fmaf(f0, t.w, a0.w);
+                    a1.x = fmaf(f1, t.x, a1.x);
+                    a1.y = fmaf(f1, t.y, a1.y);
+                    a1.z = fmaf(f1, t.z, a1.z);
+                    a1.w = fmaf(f1, t.w, a1.w);
+                }
+            }
+#pragma unroll
+            for (int d = 9; d <= 18; d += 9) {
+                const float x0 = __shfl_down_sync(0xffffffffu, a0.x, d);
+                const float y0 = __shfl_down_sync(0xffffffffu, a0.y, d);
+                const float z0 = __shfl_down_sync(0xffffffffu, a0.z, d);
+                const float w0 = __shfl_down_sync(0xffffffffu, a0.w, d);
+                const float x1 = __shfl_down_sync(0xffffffffu, a1.x, d);
+                const float y1 = __shfl_down_sync(0xffffffffu, a1.y, d);
+                const float z1 = __shfl_down_sync(0xffffffffu, a1.z, d);
+                const float w1 = __shfl_down_sync(0xffffffffu, a1.w, d);
+                if (lane < 9 && lane + d < 27) {
+                    a0.x += x0;
+                    a0.y += y0;
+                    a0.z += z0;
+                    a0.w += w0;
+                    a1.x += x1;
+                    a1.y += y1;
+                    a1.z += z1;
+                    a1.w += w1;
+                }
+            }
+            if (lane < 9) {
+                const int off = (ok * N + lane / 3) * N + lane % 3;
+                const int k0 = keys[0], k1 = keys[b];
+                if (k0 >= 0) atomicAdd(&grid[(int64_t)k0 + off], a0);
+                if (k1 >= 0) atomicAdd(&grid[(int64_t)k1 + off], a1);
             }
         } else if (lane < P2G_PASS) {
             const int off = (ok * N + lane / 3) * N + lane % 3;
