@@ -132,17 +132,24 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
 __global__ void __launch_bounds__(GRID_THREADS) k_rev_grid_active(
     MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_bv,
     float4 *__restrict__ grid_bmp, float *__restrict__ g_wind, ActiveBlocks ab) {
+    __shared__ float sbox[GRID_THREADS / 32][WIND_BOX];
     pdl_wait();
     pdl_trigger();
     const int count = *ab.count;
     const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    // every lane of a 64-thread group runs the same iterations (one block each)
     for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
         int b = ab.list[e];
-        int i, j, k;
+        int i = 0, j = 0, k = 0;
+        bool live = false;
+        float3 gw;
         if (active_node(P, ab.nb, b, lt, i, j, k)) {
             int64_t node = ((int64_t)k * P.N + j) * P.N + i;
-            rev_grid_node(P, wind, t, node, i, j, k, grid_mp, grid_bv, grid_bmp, g_wind);
+            live = rev_grid_node(P, node, i, j, k, grid_mp, grid_bv, grid_bmp, gw);
         }
+        if (g_wind)
+            wind_sample_adjoint_warp(wind, wind_scatter_coarse(P.N, wind.nf), live, i * P.dx,
+                                     j * P.dx, k * P.dx, t, gw, g_wind, sbox[threadIdx.x >> 5]);
         if (lt == 0) ab.flags[b] = 0;
     }
 }

@@ -121,16 +121,19 @@ __device__ __forceinline__ void rev_g2p_particle(const MpmParams &P, const float
     q.valid = true;
 }
 
-// Reverse grid update of one node: (dL/dm_i, dL/dp_i) into grid_bmp, wind
-// gradient scatter, and clearing of grid_mp and grid_bv for the next call.
-__device__ __forceinline__ void rev_grid_node(const MpmParams &P, const WindDev &wind, float t,
-                                              int64_t node, int i, int j, int k,
-                                              float4 *__restrict__ grid_mp,
+// Reverse grid update of one node: (dL/dm_i, dL/dp_i) into grid_bmp, and
+// clearing of grid_mp and grid_bv for the next call. Returns whether the node
+// took part in the grid update (m_i > 0, outside the sticky band); then gw is
+// dt dL/dv_i, the cotangent of the wind force sampled at the node, for
+// wind_sample_adjoint_warp.
+__device__ __forceinline__ bool rev_grid_node(const MpmParams &P, int64_t node, int i, int j,
+                                              int k, float4 *__restrict__ grid_mp,
                                               float4 *__restrict__ grid_bv,
-                                              float4 *__restrict__ grid_bmp,
-                                              float *__restrict__ g_wind) {
+                                              float4 *__restrict__ grid_bmp, float3 &gw) {
     float4 mp = grid_mp[node];
     float4 bmp = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool live = false;
+    gw = make_float3(0.f, 0.f, 0.f);
     if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
         const float4 b4 = grid_bv[node];  // (0, dL/dv_i)
         const float b[3] = {b4.y, b4.z, b4.w};
@@ -139,13 +142,13 @@ __device__ __forceinline__ void rev_grid_node(const MpmParams &P, const WindDev 
         bmp.z = b[1] * inv_m;
         bmp.w = b[2] * inv_m;
         bmp.x = -(mp.y * b[0] + mp.z * b[1] + mp.w * b[2]) * inv_m * inv_m;
-        if (g_wind)
-            wind_sample_adjoint_dev(wind, i * P.dx, j * P.dx, k * P.dx, t,
-                                    make_float3(P.dt * b[0], P.dt * b[1], P.dt * b[2]), g_wind);
+        gw = make_float3(P.dt * b[0], P.dt * b[1], P.dt * b[2]);
+        live = true;
     }
     grid_mp[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     grid_bv[node] = make_float4(0.f, 0.f, 0.f, 0.f);
     grid_bmp[node] = bmp;
+    return live;
 }
 
 // Reverse P2G of one particle at input state (xp, vp, Cp, Fp), gathering

@@ -341,24 +341,31 @@ __global__ void __launch_bounds__(BATCH_ITEM) k_batch_rev_g2p(BatchView A, Batch
 // scene's (m, p), grid_bv and block flags.
 __global__ void __launch_bounds__(256) k_batch_rev_grid(BatchView A, BatchAdjView R, int k, int L) {
     constexpr int SUBS = 256 / 64;
+    __shared__ float sbox[256 / 32][WIND_BOX];
     const int count = A.count[L];
     const int *list = A.list + (size_t)L * A.list_cap;
     const float t0 = *A.t0;
     const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    // every lane of a 64-thread group runs the same iterations (one block of
+    // one scene each), so the wind scatter below is warp-uniform
     for (int e = blockIdx.x * SUBS + sub; e < count; e += gridDim.x * SUBS) {
         const int ent = list[e];
         const int sc = ent >> BATCH_SCENE_SHIFT;
         const BatchScene &S = A.scenes[sc];
         const int b = ent & ((1 << BATCH_SCENE_SHIFT) - 1);
         const MpmParams P = S.P;
-        int i, j, kk;
+        int i = 0, j = 0, kk = 0;
+        bool live = false;
+        float3 gw;
         if (active_node(P, S.nb, b, lt, i, j, kk)) {
             const int64_t node = ((int64_t)kk * P.N + j) * P.N + i;
             const int64_t no = R.node_off[sc];
-            rev_grid_node(P, S.wind, fmaf((float)k, P.dt, t0), node, i, j, kk, S.grid_mp,
-                          R.grid_bv + no, R.grid_bmp + no,
-                          R.g_wind ? R.g_wind + R.wind_off[sc] : nullptr);
+            live = rev_grid_node(P, node, i, j, kk, S.grid_mp, R.grid_bv + no, R.grid_bmp + no, gw);
         }
+        if (R.g_wind)
+            wind_sample_adjoint_warp(S.wind, wind_scatter_coarse(P.N, S.wind.nf), live, i * P.dx,
+                                     j * P.dx, kk * P.dx, fmaf((float)k, P.dt, t0), gw,
+                                     R.g_wind + R.wind_off[sc], sbox[threadIdx.x >> 5]);
         if (lt == 0) S.flags[b] = 0;
     }
 }
