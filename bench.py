@@ -304,7 +304,7 @@ def estimate_active_nodes(ro, sc):
 # DRAM bytes (read + write) per launch of k_g2p2g on the 400,040-particle sheet
 # from one ncu capture of the current kernel (profiles/mpm_rollout_sheet400k.md,
 # "DRAM traffic of k_g2p2g"); to be re-measured whenever that kernel changes.
-G2P2G_DRAM_BYTES_SHEET400K = 20.07e6
+G2P2G_DRAM_BYTES_SHEET400K = 20.17e6
 SHEET_PARTICLES = 400040
 
 
