@@ -89,3 +89,92 @@ def test_sorted_and_unsorted_orders_agree():
     for k in ("wind", "x0", "F0"):
         assert rel_l2(a[k], b[k]) <= 1e-4, (k, rel_l2(a[k], b[k]))
     assert abs(a["E"] - b["E"]) <= 1e-4 * abs(b["E"])
+
+
+def test_checkpointed_wind_and_E_gradients_match_central_differences():
+    """The setting of the adjoint workload at a size the FP64 oracle finishes
+    in seconds: a pinned Neo-Hookean sheet (40 x 27 x 2 particles, 32^3 grid,
+    8^3 x 4 Fourier wind), 100 substeps with checkpoints every 25, loss
+    L = (1/N) sum over the checkpoint frames and particles of |x - x_target|^2
+    with the target trajectory driven by another wind field. The GPU
+    gradients (checkpointed forward + mpm_segment_adjoint through
+    autograd.mpm_frames) of 16 random wind entries among those the loss
+    depends on, and of E, against central differences of the oracle's loss
+    (eps = 1e-3 on a wind value, 1e-4 E on E): within 1e-2. The oracle's own
+    reverse pass meets these differences to 1e-6, so the check measures the
+    float32 path."""
+    n_sub, every = 100, 25
+    sc = inputs.sheet_scene(nu=40, nv=27, n_grid=32, n_substeps=n_sub, dt=1e-4, wind_nf=8,
+                            wind_frames=4, seed=0, wind_seed=0)
+    params, pinned = sc.params(), sc.pinned
+    st = inputs.rest_state(sc.x)
+    n = sc.n
+    w_true = inputs.fourier_wind(8, 4, seed=77)
+    t_total = n_sub * sc.dt
+
+    def oracle_frames(vals, p=params):
+        _, kept = oracle.mpm_rollout(p, f64(st), wind_ref(vals, t_total), 0.0, n_sub, pinned,
+                                     keep_every=every)
+        return np.stack([k[0] for k in kept[1:]])
+
+    target = oracle_frames(w_true)
+
+    def oracle_loss(vals, p=params):
+        return float(((oracle_frames(vals, p) - target) ** 2).sum() / n)
+
+    mpm = B.MPM.from_params(params, max_particles=n)
+    s0 = B.MpmState(*(to_dev(np.asarray(a, np.float32)) for a in st))
+    wv = to_dev(sc.wind.astype(np.float32)).requires_grad_(True)
+    E = torch.tensor(params["E"], device="cuda", requires_grad=True)
+    X = AG.mpm_frames(mpm, s0, wv, t_total, E, n_sub, every, pinned=to_dev(pinned))
+    loss = ((X - to_dev(target.astype(np.float32))) ** 2).sum() / n
+    loss.backward()
+    mpm.device_status()
+    g_wind = wv.grad.double().cpu().numpy().ravel()
+    g_E = float(E.grad)
+    mpm.close()
+
+    # entries the loss depends on: the oracle adjoint's nonzero wind gradient
+    ref = oracle_grads_loss(params, st, pinned, sc.wind, target, n_sub, every, t_total)
+    live = np.flatnonzero(np.abs(ref) > 1e-2 * np.abs(ref).max())
+    pick = np.random.default_rng(0).choice(live, size=16, replace=False)
+    eps = 1e-3
+    fd = []
+    for idx in pick:
+        vp = np.asarray(sc.wind, np.float64).copy().ravel()
+        vm = vp.copy()
+        vp[idx] += eps
+        vm[idx] -= eps
+        fd.append((oracle_loss(vp.reshape(sc.wind.shape)) - oracle_loss(vm.reshape(sc.wind.shape)))
+                  / (2 * eps))
+    fd = np.array(fd)
+    scale = np.abs(fd).max()
+    err = np.abs(g_wind[pick] - fd) / np.maximum(np.abs(fd), 0.1 * scale)
+    assert err.max() <= 1e-2, (err.max(), g_wind[pick], fd)
+    eE = 1e-4 * params["E"]
+    pp, pm = dict(params), dict(params)
+    pp["E"] += eE
+    pm["E"] -= eE
+    fd_E = (oracle_loss(sc.wind, pp) - oracle_loss(sc.wind, pm)) / (2 * eE)
+    assert abs(g_E - fd_E) <= 1e-2 * abs(fd_E), (g_E, fd_E)
+
+
+def oracle_grads_loss(params, st, pinned, vals, target, n_sub, every, t_total):
+    """dL/d(wind values) of the target-trajectory loss by the oracle's reverse
+    pass (flattened)."""
+    dt = params["dt"]
+    w = wind_ref(vals, t_total)
+    states = [f64(st)]
+    for k in range(n_sub):
+        states.append(oracle.mpm_substep(params, states[-1], w, k * dt, pinned))
+    n = states[0][0].shape[1]
+    g = [np.zeros_like(a) for a in states[0]]
+    g_wind = np.zeros(np.asarray(vals).shape)
+    for k in reversed(range(n_sub)):
+        if (k + 1) % every == 0:
+            f = (k + 1) // every - 1
+            g[0] = g[0] + 2.0 * (states[k + 1][0] - target[f]) / n
+        gi, g_wind, _ = oracle.mpm_substep_adjoint(params, states[k], w, k * dt, tuple(g), pinned,
+                                                   g_wind)
+        g = list(gi)
+    return g_wind.ravel()
