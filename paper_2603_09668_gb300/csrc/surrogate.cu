@@ -543,8 +543,9 @@ static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, c
     return DW_OK;
 }
 
-// TMA descriptor of a planar [C/8][n][n][n][8] BF16 volume, box = one
-// 8-channel plane of the 10 x 18 halo of one z slice, zero fill outside.
+// TMA descriptor of a planar [C/8][n][n][n][8] BF16 volume viewed as 4D
+// [C/8][z][y][x * 8]; box = the 10 x 18 halo of one z slice in all C/8
+// planes, zero fill outside.
 static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -559,11 +560,11 @@ static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) 
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const cuuint64_t nn = (cuuint64_t)n;
-    const cuuint64_t dims[5] = {8, nn, nn, nn, (cuuint64_t)(C / 8)};
-    const cuuint64_t strides[4] = {16, 16 * nn, 16 * nn * nn, 16 * nn * nn * nn};
-    const cuuint32_t box[5] = {8, TC_HX, TC_HY, 1, 1};
-    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims,
+    const cuuint64_t dims[4] = {8 * nn, nn, nn, (cuuint64_t)(C / 8)};
+    const cuuint64_t strides[3] = {16 * nn, 16 * nn * nn, 16 * nn * nn * nn};
+    const cuuint32_t box[4] = {8 * TC_HX, TC_HY, 1, (cuuint32_t)(C / 8)};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims,
                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

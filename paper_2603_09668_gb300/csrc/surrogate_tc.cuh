@@ -10,9 +10,9 @@
 // The convolution out[v][co] = sum_{tap, ci} W[tap][co][ci] in[v + d(tap)][ci]
 // (zero padding) is an implicit GEMM over output tiles of 8 (x) x 16 (y)
 // voxels (M = 128 rows). A CTA streams along z through the input slices of
-// its output range; for each slice the 10 x 18 halo is loaded by TMA, one box
-// per 8-channel plane (box {8 ch, 10, 18, 1, 1} of the 5D view
-// [C/8][z][y][x][8], zero fill outside the volume), so that each plane lands
+// its output range; for each slice the 10 x 18 halo of all 8-channel planes
+// is loaded by one TMA box ({80, 18, 1, C/8} of the 4D view
+// [C/8][z][y][x * 8], zero fill outside the volume), so that each plane lands
 // as 16-byte voxel rows ordered (y, x). In that layout the A operand of every
 // (dx, dy) tap is a plain shared-memory matrix descriptor without swizzling:
 // the 8 x-voxels of one tile row form a core matrix (8 rows x 16 B,
@@ -147,28 +147,30 @@ constexpr int TC_TMEM_COLS = 512;                     // the whole tensor memory
 constexpr int TC_NWIN = 5;       // accumulator windows (one input slice each)
 constexpr int TC_RING = 8;       // slice-ready barrier ring (>= TC_NWIN + 2)
 constexpr int TC_SLICE_BYTES = TC_HX * TC_HY * 16;    // 2880 B: one plane of a 10 x 18 slice halo
-constexpr int TC_SLICE = 2944;                        // plane stride, 128-B aligned
+constexpr int TC_SLICE = TC_SLICE_BYTES;              // plane stride: a slice's planes arrive as one box
 
 template <int CIN, int COUT>
 constexpr size_t tc_smem() {
     return (size_t)TC_NST * (CIN / 8) * TC_SLICE + (size_t)27 * (CIN / 8) * COUT * 16 + 1024;
 }
 
-// TMA loads of the halo planes of input slice z of the xy tile at (x0, y0).
+// TMA load of the halo of input slice z of the xy tile at (x0, y0): one box
+// {80 (10 voxels x 8 channels), 18, 1, CIN/8} of the 4D view
+// [C/8][z][y][x * 8] that lands as CIN/8 planes of 18 rows x 160 B, one
+// after the other (a single copy per slice instead of one per plane; the x
+// coordinate 8 (x0 - 1) elements is 16-byte aligned, the zero fill covers the
+// volume's faces).
 template <int CIN>
 __device__ __forceinline__ void tc_load_slice(const CUtensorMap *tm, uint32_t halo, uint32_t bar,
                                               int x0, int y0, int z) {
     constexpr int KCH = CIN / 8;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(bar), "r"(KCH * TC_SLICE_BYTES) : "memory");
-#pragma unroll
-    for (int c = 0; c < KCH; ++c)
-        asm volatile(
-            "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-            :: "r"(halo + c * TC_SLICE), "l"((uint64_t)tm), "r"(0), "r"(x0 - 1), "r"(y0 - 1),
-               "r"(z), "r"(c), "r"(bar)
-            : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        :: "r"(halo), "l"((uint64_t)tm), "r"(8 * (x0 - 1)), "r"(y0 - 1), "r"(z), "r"(0), "r"(bar)
+        : "memory");
 }
 
 // The CTA's output work as segments: output slices o0..o1 of one xy tile.
