@@ -23,6 +23,8 @@
 
 #include <new>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dw {
@@ -62,6 +64,17 @@ struct LbmParams {
     int bc_x;
     float feq_in[19];  // shifted inlet equilibrium f_eq(1, u_inlet) - w
 };
+
+// Cell of this thread in a lattice-row launch (lattice_launch): x from the
+// block's position along the row, y and z from the block indices, so that
+// no division is needed; false past the end of the row.
+__device__ __forceinline__ bool lattice_cell(const LbmParams &L, int &x, int &y, int &z, int &cell) {
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y;
+    z = blockIdx.z;
+    cell = (z * L.ny + y) * L.nx + x;
+    return x < L.nx;
+}
 
 // BGK collision (+ Guo forcing) of one node, shifted populations, in place.
 __device__ __forceinline__ void collide(const LbmParams &L, float f[19]) {
@@ -143,10 +156,12 @@ __device__ __forceinline__ int cell_index(const LbmParams &L, int x, int y, int 
 __global__ void __launch_bounds__(256, 4) k_lbm_aa_even(LbmParams L, float *f,
                                                     const uint8_t *__restrict__ solid,
                                                     float *__restrict__ outlet) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
+    pdl_wait();  // every thread, before anything of the previous step is touched
+    pdl_trigger();
+    int x, y, z, cell;
+    if (!lattice_cell(L, x, y, z, cell)) return;
     if (solid && solid[cell]) return;
-    const size_t nc = (size_t)L.ncell;
+    const int nc = L.ncell;  // 19 * ncell < 2^31 is checked at create
     float fl[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) fl[i] = f[i * nc + cell];
@@ -154,9 +169,8 @@ __global__ void __launch_bounds__(256, 4) k_lbm_aa_even(LbmParams L, float *f,
 #pragma unroll
     for (int i = 0; i < 19; ++i) f[D3Q19::opp(i) * nc + cell] = fl[i];
     if (L.bc_x == 1) {
-        int x = cell % L.nx;
         if (x == L.nx - 1) {
-            int face = cell / L.nx;  // z * ny + y
+            int face = z * L.ny + y;
             int nface = L.ny * L.nz;
 #pragma unroll
             for (int i = 0; i < 19; ++i)
@@ -210,12 +224,13 @@ __device__ __forceinline__ NbrOffsets nbr_offsets(const LbmParams &L, int x, int
 __global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
                                                       const uint32_t *__restrict__ links,
                                                       const float *__restrict__ outlet) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
+    pdl_wait();
+    pdl_trigger();
+    int x, y, z, cell;
+    if (!lattice_cell(L, x, y, z, cell)) return;
     const uint32_t lk = links ? links[cell] : 0u;
     if (lk & 1u) return;
     const int nc = L.ncell;  // 19 * ncell < 2^31 is checked at create
-    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
     const NbrOffsets o = nbr_offsets(L, x, y, z);
     float fl[19];
     fl[0] = f[cell];  // rest population: own slot 0 in both orders
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
         fl[i] = f[idx];
     }
     if (L.bc_x == 1) {
-        const int nface = L.ny * L.nz, face = cell / L.nx;
+        const int nface = L.ny * L.nz, face = z * L.ny + y;
         if (x == 0) {
 #pragma unroll
             for (int i = 1; i < 19; ++i)
@@ -271,8 +286,10 @@ __global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
 __global__ void __launch_bounds__(256, 4) k_lbm_push(LbmParams L, const float *__restrict__ fin,
                                                  float *__restrict__ fout,
                                                  const uint32_t *__restrict__ links) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
+    pdl_wait();
+    pdl_trigger();
+    int x, y, z, cell;
+    if (!lattice_cell(L, x, y, z, cell)) return;
     const int nc = L.ncell;  // 19 * ncell < 2^31 is checked at create
     const uint32_t lk = links ? links[cell] : 0u;
     if (lk & 1u) {
@@ -280,7 +297,6 @@ __global__ void __launch_bounds__(256, 4) k_lbm_push(LbmParams L, const float *_
         for (int i = 0; i < 19; ++i) fout[i * nc + cell] = fin[i * nc + cell];
         return;
     }
-    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
     const NbrOffsets o = nbr_offsets(L, x, y, z);
     float fl[19];
 #pragma unroll
@@ -320,8 +336,10 @@ __global__ void __launch_bounds__(256, 4) k_lbm_adjoint(LbmParams L, const float
                                                     const float *__restrict__ g_next,
                                                     float *__restrict__ g_prev,
                                                     const uint32_t *__restrict__ links) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
+    pdl_wait();
+    pdl_trigger();
+    int x, y, z, cell;
+    if (!lattice_cell(L, x, y, z, cell)) return;
     const int nc = L.ncell;
     const uint32_t lk = links ? links[cell] : 0u;
     if (lk & 1u) {
@@ -329,7 +347,6 @@ __global__ void __launch_bounds__(256, 4) k_lbm_adjoint(LbmParams L, const float
         for (int i = 0; i < 19; ++i) g_prev[i * nc + cell] = g_next[i * nc + cell];
         return;
     }
-    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
     const NbrOffsets o = nbr_offsets(L, x, y, z);
     const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
     float g[19];
@@ -456,6 +473,7 @@ extern "C" dw_status lbm_create(const dw_lbm_desc *desc, dw_lbm *out) {
     *out = nullptr;
     DW_REQUIRE(desc->nx >= 2 && desc->ny >= 2 && desc->nz >= 2, "lattice sizes must be >= 2");
     DW_REQUIRE(19ll * desc->nx * desc->ny * desc->nz < (1ll << 31), "lattice too large (19 nx ny nz must be < 2^31)");
+    DW_REQUIRE(desc->ny <= 65535 && desc->nz <= 65535, "ny and nz must be <= 65535");
     DW_REQUIRE(desc->tau > 0.5f, "tau must be > 0.5");
     DW_REQUIRE(desc->bc_x == 0 || desc->bc_x == 1, "bc_x must be 0 or 1");
     DW_REQUIRE(desc->max_tape >= 1 && desc->max_tape <= 4096, "max_tape must be in [1, 4096]");
@@ -490,6 +508,18 @@ extern "C" dw_status lbm_destroy(dw_lbm h) {
     return DW_OK;
 }
 
+namespace dw {
+
+// Launch shape of the lattice-row kernels (lattice_cell): one block row of up
+// to 256 threads along x per (y, z).
+static void lattice_launch(const LbmParams &L, dim3 &grid, dim3 &block) {
+    const int bx = std::min(256, (L.nx + 31) / 32 * 32);
+    block = dim3((unsigned)bx);
+    grid = dim3((unsigned)((L.nx + bx - 1) / bx), (unsigned)L.ny, (unsigned)L.nz);
+}
+
+}  // namespace dw
+
 extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t steps,
                               dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
@@ -503,12 +533,14 @@ extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t 
         k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
         links = h->links;
     }
+    dim3 rg, rb;
+    lattice_launch(L, rg, rb);
     for (int k = 0; k + 1 < steps; k += 2) {
-        k_lbm_aa_even<<<grid, 256, 0, s>>>(L, f, solid, h->outlet);
-        k_lbm_aa_odd<<<grid, 256, 0, s>>>(L, f, links, h->outlet);
+        DW_CUDA(launch_pdl3(k_lbm_aa_even, rg, rb, s, L, f, solid, h->outlet));
+        DW_CUDA(launch_pdl3(k_lbm_aa_odd, rg, rb, s, L, f, links, h->outlet));
     }
     if (steps & 1) {
-        k_lbm_push<<<grid, 256, 0, s>>>(L, f, h->tape, links);
+        DW_CUDA(launch_pdl3(k_lbm_push, rg, rb, s, L, (const float *)f, h->tape, links));
         DW_CUDA(cudaMemcpyAsync(f, h->tape, sizeof(float) * 19 * (size_t)L.ncell,
                                 cudaMemcpyDeviceToDevice, s));
     }
@@ -532,15 +564,17 @@ extern "C" dw_status lbm_step_adjoint(dw_lbm h, const float *f_in, float *g_f,
         k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
         links = h->links;
     }
+    dim3 rg, rb;
+    lattice_launch(L, rg, rb);
     // states f(1) .. f(steps-1) into tape[0 .. steps-2]
     for (int k = 1; k < steps; ++k) {
         const float *src = k == 1 ? f_in : h->tape + (size_t)(k - 2) * lat;
-        k_lbm_push<<<grid, 256, 0, s>>>(L, src, h->tape + (size_t)(k - 1) * lat, links);
+        DW_CUDA(launch_pdl3(k_lbm_push, rg, rb, s, L, src, h->tape + (size_t)(k - 1) * lat, links));
     }
     float *cur = g_f, *other = h->gtmp;
     for (int k = steps - 1; k >= 0; --k) {
         const float *state = k == 0 ? f_in : h->tape + (size_t)(k - 1) * lat;
-        k_lbm_adjoint<<<grid, 256, 0, s>>>(L, state, cur, other, links);
+        DW_CUDA(launch_pdl3(k_lbm_adjoint, rg, rb, s, L, state, (const float *)cur, other, links));
         float *tmp = cur;
         cur = other;
         other = tmp;
