@@ -153,7 +153,7 @@ __device__ __forceinline__ int cell_index(const LbmParams &L, int x, int y, int 
 
 // ---------------------------------------------------------------- forward --
 
-__global__ void __launch_bounds__(256, 4) k_lbm_aa_even(LbmParams L, float *f,
+__global__ void __launch_bounds__(256, 5) k_lbm_aa_even(LbmParams L, float *f,
                                                     const uint8_t *__restrict__ solid,
                                                     float *__restrict__ outlet) {
     pdl_wait();  // every thread, before anything of the previous step is touched
@@ -221,7 +221,7 @@ __device__ __forceinline__ NbrOffsets nbr_offsets(const LbmParams &L, int x, int
     return o;
 }
 
-__global__ void __launch_bounds__(256, 4) k_lbm_aa_odd(LbmParams L, float *f,
+__global__ void __launch_bounds__(256, 5) k_lbm_aa_odd(LbmParams L, float *f,
                                                       const uint32_t *__restrict__ links,
                                                       const float *__restrict__ outlet) {
     pdl_wait();
