@@ -35,6 +35,9 @@ struct SurrHandle {
     float *fine = nullptr;          // [4][(2n)^3]: rho, ux, uy, uz of the last surr_features
     double *red = nullptr;          // reduction scratch
     int *err = nullptr;             // device status bits (bounded waits of the conv kernels)
+    unsigned *gbar = nullptr;       // grid barrier of the one-launch forward (arrivals, generation)
+    bool fused = true;              // the one-launch forward can be launched (cooperatively)
+    bool fused_attr_set = false;
     int conv_ctas = 0;
     int sms = 0;
     // the BF16 weights were rewritten since the last forward: its first layer,
@@ -663,12 +666,14 @@ extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
     DW_ALLOC(h->fine, sizeof(float) * 4 * Nc);
     DW_ALLOC(h->red, sizeof(double) * 4);
     DW_ALLOC(h->err, sizeof(int));
+    DW_ALLOC(h->gbar, sizeof(unsigned) * 2);
 #undef DW_ALLOC
     if (e == cudaSuccess) e = cudaMemset(h->params, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->grads, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->m, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->v, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->gbar, 0, sizeof(unsigned) * 2);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         dw_status st = cuda_fail(e, "surr_create");
@@ -708,6 +713,7 @@ extern "C" dw_status surr_destroy(dw_surr h) {
     cudaFree(h->fine);
     cudaFree(h->red);
     cudaFree(h->err);
+    cudaFree(h->gbar);
     delete h;
     return DW_OK;
 }
@@ -786,6 +792,46 @@ extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activation
         if (st != DW_OK) return st;
         st = conv<32, 32, EPI_GELU>(h, h->tm_a[1], h->wf + h->woff[2], P + h->off_b[2], h->z[2], h->a[2], nullptr, nullptr, s);
         if (st != DW_OK) return st;
+    } else if (h->fused) {
+        // the whole inference pass in one cooperative launch
+        constexpr size_t smem = tc_forward_smem();
+        if (!h->fused_attr_set) {
+            DW_CUDA(cudaFuncSetAttribute(k_surr_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+            h->fused_attr_set = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)h->sms);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        // programmatic overlap with the previous kernel only while the weights
+        // (copied before the dependency wait) are unchanged
+        cfg.numAttrs = h->weights_dirty ? 1 : 2;
+        cudaError_t e = cudaLaunchKernelEx(
+            &cfg, k_surr_forward_tc, h->tm_feats, h->tm_a[0], h->tm_a[1], h->tm_a[2],
+            (const bf16 *)(h->wf + h->woff[0]), (const bf16 *)(h->wf + h->woff[1]),
+            (const bf16 *)(h->wf + h->woff[2]), (const bf16 *)(h->wf + h->woff[3]),
+            (const float *)(P + h->off_b[0]), (const float *)(P + h->off_b[1]),
+            (const float *)(P + h->off_b[2]), (const float *)(P + h->off_b[3]), h->a[0], h->a[1],
+            h->a[2], h->out, h->n, h->gbar, h->err);
+        if (e == cudaSuccess) {
+            h->weights_dirty = false;
+            if (out)
+                DW_CUDA(cudaMemcpyAsync(out, h->out, sizeof(float) * h->nv * 16,
+                                        cudaMemcpyDeviceToDevice, s));
+            return DW_OK;
+        }
+        // not launchable here (e.g. no cooperative launch): the per-layer kernels from now on
+        cudaGetLastError();
+        h->fused = false;
+        return surr_forward(h, out, keep_activations, stream);
     } else {
         st = conv<16, 32, EPI_GELU_ONLY>(h, h->tm_feats, h->wf + h->woff[0], P + h->off_b[0], nullptr, h->a[0], nullptr, nullptr, s, !h->weights_dirty);
         if (st != DW_OK) return st;
@@ -809,6 +855,7 @@ extern "C" dw_status surr_device_status(dw_surr h, dw_stream stream) {
     DW_CUDA(cudaMemcpyAsync(&bits, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     DW_CUDA(cudaStreamSynchronize(s));
     DW_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    DW_CUDA(cudaMemsetAsync(h->gbar, 0, sizeof(unsigned) * 2, s));  // a barrier that gave up
     DW_CUDA(cudaStreamSynchronize(s));
     return status_from_bits(bits);
 }

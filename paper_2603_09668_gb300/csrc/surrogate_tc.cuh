@@ -200,8 +200,8 @@ __device__ __forceinline__ bool tc_segment(int n, int nxy, int j, TcSeg &c) {
 }
 
 // Epilogues: EPI_GELU (z and GELU(z) in BF16), EPI_GELU_ONLY (GELU(z)),
-// EPI_F32 (z in FP32), EPI_DGELU (acc * GELU'(zprev), BF16). wt holds the
-// weights as [9 (dy, dx)][CIN/8][3 (dz)][COUT][8].
+// EPI_F32 (z in FP32), EPI_DGELU (acc * GELU'(zprev), BF16). Weights are
+// stored as [9 (dy, dx)][CIN/8][3 (dz)][COUT][8].
 //
 // z-streaming: the CTA walks the input z-slices of each segment once (slices
 // o0 - 1 .. o1 + 1, clipped to the volume). For each input slice and each of
@@ -215,64 +215,132 @@ __device__ __forceinline__ bool tc_segment(int n, int nxy, int j, TcSeg &c) {
 // three blocks. Windows never overlap, so the MMAs of consecutive slices do
 // not wait on each other's accumulators.
 //
-// Roles: warp 8, lane 0 issues the weight copy, the halo loads (ring of
+// Roles: warp 8, lane 0 issues the weight copies, the halo loads (ring of
 // TC_NST slices) and the MMAs, committing each slice to ready[k % TC_RING];
 // warps 0-7 read the finished output slices (warp w: accumulator lanes
 // 32 (w % 4) .. + 31, column half w / 4) and arrive on wfree[w] once no
 // output needs window w any more, which the producer waits for before
 // reusing it.
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
-    const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ wt,
-    const float *__restrict__ bias, int n, bf16 *__restrict__ out_z, bf16 *__restrict__ out_a,
-    float *__restrict__ out_f, const bf16 *__restrict__ zprev, int *err) {
-    static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "unsupported shape");
-    constexpr int KCH = CIN / 8;
-    constexpr int HBYTES = KCH * TC_SLICE;
-    constexpr int WBYTES = 27 * KCH * COUT * 16;
-    constexpr int CPW = COUT / (TC_EPI_WARPS / 4);  // accumulator columns per epilogue warp
-    constexpr int NW = 3 * COUT;                    // MMA N: the three dz taps
-    static_assert(TC_NWIN * NW <= TC_TMEM_COLS && TC_RING >= TC_NWIN + 2, "tensor memory plan");
-    constexpr uint32_t IDESC = tc_idesc(NW);
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[TC_NST], empty[TC_NST], ready[TC_RING], wfree[TC_NWIN];
-    __shared__ __align__(8) uint64_t wbar;
-    __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const uint32_t hbase = smem_u32(smem), wbase = hbase + TC_NST * HBYTES;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+// The pipeline's shared-memory state, kept across the layers of one launch:
+// the slice counter k runs on from layer to layer, so every mbarrier phase
+// and window index stays consistent without re-initialisation.
+struct TcPipe {
+    uint64_t full[TC_NST], empty[TC_NST], ready[TC_RING], wfree[TC_NWIN];
+    uint64_t wbar[2];  // weight buffers
+    uint32_t wbuf[2];  // their shared-memory addresses
+    int wcount[2];     // copies issued into each buffer (producer thread only)
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+constexpr int tc_wbytes(int cin, int cout) { return 27 * (cin / 8) * cout * 16; }
+constexpr int TC_WMAX = tc_wbytes(32, 32);  // largest layer's weights
+
+// Output buffers and bias of one layer.
+struct TcOut {
+    const float *bias;
+    bf16 *out_z, *out_a;
+    float *out_f;
+    const bf16 *zprev;
+};
+
+// What the producer does before the layer's first halo load.
+enum { TC_PRO_NONE = 0, TC_PRO_PDL = 1, TC_PRO_PROXY = 2 };
+
+// Barrier init and the TMEM allocation (all threads).
+__device__ __forceinline__ uint32_t tc_pipe_open(TcPipe &pp) {
+    const int tid = threadIdx.x;
     if (tid == 0) {
-        abort_flag = 0;
+        pp.abort_flag = 0;
         for (int i = 0; i < TC_NST; ++i) {
-            mbar_init(smem_u32(&full[i]), 1);
-            mbar_init(smem_u32(&empty[i]), 1);
+            mbar_init(smem_u32(&pp.full[i]), 1);
+            mbar_init(smem_u32(&pp.empty[i]), 1);
         }
-        for (int i = 0; i < TC_RING; ++i) mbar_init(smem_u32(&ready[i]), 1);
-        for (int i = 0; i < TC_NWIN; ++i) mbar_init(smem_u32(&wfree[i]), TC_EPI_WARPS);
-        mbar_init(smem_u32(&wbar), 1);
+        for (int i = 0; i < TC_RING; ++i) mbar_init(smem_u32(&pp.ready[i]), 1);
+        for (int i = 0; i < TC_NWIN; ++i) mbar_init(smem_u32(&pp.wfree[i]), TC_EPI_WARPS);
+        mbar_init(smem_u32(&pp.wbar[0]), 1);
+        mbar_init(smem_u32(&pp.wbar[1]), 1);
+        pp.wcount[0] = pp.wcount[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if ((tid >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(TC_TMEM_COLS));
+                     :: "r"(smem_u32(&pp.tmem_base)), "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t taddr = tmem_base;
-    const volatile int *abort_p = &abort_flag;
+    return pp.tmem_base;
+}
+
+// All threads: the TMEM release at the end; before it the producer waits
+// (bounded) for the last weight copy into each buffer, which an abort may
+// have left in flight.
+__device__ __forceinline__ void tc_pipe_close(TcPipe &pp, uint32_t taddr) {
+    if (threadIdx.x == 32 * TC_EPI_WARPS)
+        for (int b = 0; b < 2; ++b)
+            if (pp.wcount[b] > 0) tc_wait(smem_u32(&pp.wbar[b]), (pp.wcount[b] - 1) & 1, nullptr);
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(taddr), "r"(TC_TMEM_COLS));
+    }
+}
+
+// One bulk copy of a layer's weights into weight buffer b (producer thread).
+__device__ __forceinline__ void tc_copy_weights(TcPipe &pp, int b, const bf16 *wt, uint32_t bytes) {
+    const uint32_t bar = smem_u32(&pp.wbar[b]);
+    ++pp.wcount[b];
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(pp.wbuf[b]), "l"(wt), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Input slices of this CTA in one layer (the same for every layer).
+__device__ __forceinline__ int tc_slices(int n, int nxy) {
+    int cnt = 0;
+    TcSeg c;
+    for (int j = 0; tc_segment(n, nxy, j, c); ++j)
+        cnt += min(c.o1 + 1, n - 1) - max(c.o0 - 1, 0) + 1;
+    return cnt;
+}
+
+// One layer over the CTA's output range, called by all threads. Weight
+// buffer wb holds (or receives) this layer's weights: own_wt, when not NULL,
+// is copied there first by the producer. next_wt, when not NULL, is copied
+// into the other buffer at the start, the prefetch of the following layer's
+// weights (that buffer's previous layer has finished). k0 counts the slices
+// this CTA has gone through in earlier layers of the launch. fence_out: the
+// epilogue ends with a proxy fence, so that TMA reads of the output by other
+// CTAs after a grid barrier see it.
+template <int CIN, int COUT, int EPI>
+__device__ __forceinline__ void tc_layer(TcPipe &pp, uint32_t taddr, const CUtensorMap *tm_in,
+                                         const TcOut &o, int n, uint32_t hbase, int wb,
+                                         const bf16 *own_wt, const bf16 *next_wt,
+                                         uint32_t next_bytes, int k0, int prologue,
+                                         bool fence_out, int *err) {
+    static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "unsupported shape");
+    constexpr int KCH = CIN / 8;
+    constexpr int HBYTES = KCH * TC_SLICE;
+    constexpr int WBYTES = tc_wbytes(CIN, COUT);
+    constexpr int CPW = COUT / (TC_EPI_WARPS / 4);  // accumulator columns per epilogue warp
+    constexpr int NW = 3 * COUT;                    // MMA N: the three dz taps
+    static_assert(TC_NWIN * NW <= TC_TMEM_COLS && TC_RING >= TC_NWIN + 2, "tensor memory plan");
+    constexpr uint32_t IDESC = tc_idesc(NW);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const volatile int *abort_p = &pp.abort_flag;
     const int tiles_x = n / TC_TX, nxy = tiles_x * (n / TC_TY);
-    // Programmatic dependent launch: the next layer may be scheduled now; this
-    // grid's input (the previous layer's output) is read only after
-    // griddepcontrol.wait, the weights (written before the first layer) before.
-    pdl_trigger();
+    if (pp.abort_flag) return;  // an earlier layer gave up
 
     if (warp == TC_EPI_WARPS) {
         if (lane == 0) {
-            int issued = 0, consumed = 0;  // slices
+            int issued = k0, consumed = k0;  // slices
             bool ok = true;
             // the slices of all segments in order, for the halo prefetch
             int pf_seg = 0, pf_z = 0;
@@ -282,7 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
             auto prefetch = [&]() {
                 if (!pf_more) return;
                 const int s = issued % TC_NST;
-                tc_load_slice<CIN>(&tm_in, hbase + s * HBYTES, smem_u32(&full[s]),
+                tc_load_slice<CIN>(tm_in, hbase + s * HBYTES, smem_u32(&pp.full[s]),
                                    (pfc.xy % tiles_x) * TC_TX, (pfc.xy / tiles_x) * TC_TY, pf_z);
                 ++issued;
                 if (pf_z < min(pfc.o1 + 1, n - 1)) {
@@ -292,22 +360,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
                     if (pf_more) pf_z = max(pfc.o0 - 1, 0);
                 }
             };
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         :: "r"(smem_u32(&wbar)), "r"(WBYTES) : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                :: "r"(wbase), "l"(wt), "r"(WBYTES), "r"(smem_u32(&wbar)) : "memory");
-            pdl_wait();
-            while (issued < TC_NST && pf_more) prefetch();
-            ok = tc_wait(smem_u32(&wbar), 0, abort_p);
+            if (own_wt) tc_copy_weights(pp, wb, own_wt, WBYTES);
+            if (next_wt) tc_copy_weights(pp, 1 - wb, next_wt, next_bytes);
+            const uint32_t wbase = pp.wbuf[wb];
+            if (prologue == TC_PRO_PDL) pdl_wait();
+            if (prologue == TC_PRO_PROXY) asm volatile("fence.proxy.async.global;" ::: "memory");
+            while (issued - k0 < TC_NST && pf_more) prefetch();
+            ok = tc_wait(smem_u32(&pp.wbar[wb]), (pp.wcount[wb] - 1) & 1, abort_p);
             const uint64_t b0 = tc_desc(wbase, NW * 16, 128);
             TcSeg c;
             for (int j = 0; ok && tc_segment(n, nxy, j, c); ++j) {
                 const int i0 = max(c.o0 - 1, 0), i1 = min(c.o1 + 1, n - 1);
                 for (int zi = i0; zi <= i1; ++zi) {
                     const int k = consumed, s = k % TC_NST, w = k % TC_NWIN;
-                    ok = tc_wait(smem_u32(&full[s]), (k / TC_NST) & 1, abort_p) &&
-                         tc_wait(smem_u32(&wfree[w]), ((k / TC_NWIN) & 1) ^ 1, abort_p);
+                    ok = tc_wait(smem_u32(&pp.full[s]), (k / TC_NST) & 1, abort_p) &&
+                         tc_wait(smem_u32(&pp.wfree[w]), ((k / TC_NWIN) & 1) ^ 1, abort_p);
                     if (!ok) break;
                     ++consumed;
                     tc_fence_after();
@@ -330,26 +397,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
                                 : "memory");
                         }
                     }
-                    tc_commit(smem_u32(&empty[s]));
-                    tc_commit(smem_u32(&ready[k % TC_RING]));
+                    tc_commit(smem_u32(&pp.empty[s]));
+                    tc_commit(smem_u32(&pp.ready[k % TC_RING]));
                     // refill the stage of slice k - TC_LAG once its MMAs are done
-                    if (k >= TC_LAG && pf_more) {
+                    if (k - k0 >= TC_LAG && pf_more) {
                         const int k1 = k - TC_LAG;
-                        ok = tc_wait(smem_u32(&empty[k1 % TC_NST]), (k1 / TC_NST) & 1, abort_p);
+                        ok = tc_wait(smem_u32(&pp.empty[k1 % TC_NST]), (k1 / TC_NST) & 1, abort_p);
                         if (!ok) break;
                         prefetch();
                     }
                 }
             }
             if (!ok) {
-                if (!abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
-                abort_flag = 1;
+                if (!pp.abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
+                pp.abort_flag = 1;
             }
             // drain (bounded): halo loads still in flight, the last MMA batch
             for (int k = consumed; k < issued; ++k)
-                tc_wait(smem_u32(&full[k % TC_NST]), (k / TC_NST) & 1, nullptr);
-            if (consumed > 0)
-                tc_wait(smem_u32(&empty[(consumed - 1) % TC_NST]), ((consumed - 1) / TC_NST) & 1, nullptr);
+                tc_wait(smem_u32(&pp.full[k % TC_NST]), (k / TC_NST) & 1, nullptr);
+            if (consumed > k0)
+                tc_wait(smem_u32(&pp.empty[(consumed - 1) % TC_NST]), ((consumed - 1) / TC_NST) & 1, nullptr);
         }
         __syncwarp();
     } else {
@@ -357,7 +424,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
         const int row = q * 32 + lane;  // accumulator lane = tile voxel (x = row & 7, y = row >> 3)
         const uint32_t tq = taddr + ((uint32_t)(q * 32) << 16) + hcol * CPW;
         const size_t nv = (size_t)n * n * n;
-        int k = 0;  // slices seen
+        int k = k0;  // slices seen in this launch
         bool ok = true;
         TcSeg c;
         for (int j = 0; ok && tc_segment(n, nxy, j, c); ++j) {
@@ -367,10 +434,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
             for (int zi = i0; zi <= i1; ++zi, ++k) {
                 int okw = 1;
                 if (lane == 0) {
-                    okw = tc_wait(smem_u32(&ready[k % TC_RING]), (k / TC_RING) & 1, abort_p);
+                    okw = tc_wait(smem_u32(&pp.ready[k % TC_RING]), (k / TC_RING) & 1, abort_p);
                     if (!okw) {
-                        if (!abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
-                        abort_flag = 1;
+                        if (!pp.abort_flag) atomicOr(err, ERRBIT_TIMEOUT);
+                        pp.abort_flag = 1;
                     }
                 }
                 if (!__shfl_sync(0xffffffffu, okw, 0)) {
@@ -403,10 +470,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
                 // windows no longer needed: slice zi - 2 (its last output, zi - 1, is
                 // done), and at the segment's end the last two slices as well
                 if (lane == 0) {
-                    if (zi - 2 >= i0) mbar_arrive(smem_u32(&wfree[(k - 2) % TC_NWIN]));
+                    if (zi - 2 >= i0) mbar_arrive(smem_u32(&pp.wfree[(k - 2) % TC_NWIN]));
                     if (zi == i1) {
-                        if (zi - 1 >= i0) mbar_arrive(smem_u32(&wfree[(k - 1) % TC_NWIN]));
-                        mbar_arrive(smem_u32(&wfree[k % TC_NWIN]));
+                        if (zi - 1 >= i0) mbar_arrive(smem_u32(&pp.wfree[(k - 1) % TC_NWIN]));
+                        mbar_arrive(smem_u32(&pp.wfree[k % TC_NWIN]));
                     }
                 }
 #pragma unroll
@@ -419,19 +486,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
                     if (EPI == EPI_F32) {
 #pragma unroll
                         for (int cc = 0; cc < CPW; cc += 4)
-                            *reinterpret_cast<float4 *>(out_f + v * COUT + c0 + cc) =
-                                make_float4(r[m][cc] + bias[c0 + cc], r[m][cc + 1] + bias[c0 + cc + 1],
-                                            r[m][cc + 2] + bias[c0 + cc + 2], r[m][cc + 3] + bias[c0 + cc + 3]);
+                            *reinterpret_cast<float4 *>(o.out_f + v * COUT + c0 + cc) =
+                                make_float4(r[m][cc] + o.bias[c0 + cc], r[m][cc + 1] + o.bias[c0 + cc + 1],
+                                            r[m][cc + 2] + o.bias[c0 + cc + 2], r[m][cc + 3] + o.bias[c0 + cc + 3]);
                     } else if (EPI == EPI_DGELU) {
 #pragma unroll
                         for (int cc = 0; cc < CPW; cc += 8) {
-                            const uint4 zp = *reinterpret_cast<const uint4 *>(zprev + plane(cc));
+                            const uint4 zp = *reinterpret_cast<const uint4 *>(o.zprev + plane(cc));
                             const bf16 *zb = reinterpret_cast<const bf16 *>(&zp);
-                            __align__(16) bf16 o[8];
+                            __align__(16) bf16 od[8];
 #pragma unroll
                             for (int jj = 0; jj < 8; ++jj)
-                                o[jj] = __float2bfloat16_rn(r[m][cc + jj] * gelu_grad_f(__bfloat162float(zb[jj])));
-                            *reinterpret_cast<uint4 *>(out_z + plane(cc)) = *reinterpret_cast<const uint4 *>(o);
+                                od[jj] = __float2bfloat16_rn(r[m][cc + jj] * gelu_grad_f(__bfloat162float(zb[jj])));
+                            *reinterpret_cast<uint4 *>(o.out_z + plane(cc)) = *reinterpret_cast<const uint4 *>(od);
                         }
                     } else {
 #pragma unroll
@@ -439,26 +506,119 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
                             __align__(16) bf16 oz[8], oa[8];
 #pragma unroll
                             for (int jj = 0; jj < 8; ++jj) {
-                                const float zz = r[m][cc + jj] + bias[c0 + cc + jj];
+                                const float zz = r[m][cc + jj] + o.bias[c0 + cc + jj];
                                 oz[jj] = __float2bfloat16_rn(zz);
                                 oa[jj] = __float2bfloat16_rn(gelu_f(zz));
                             }
                             if (EPI == EPI_GELU)
-                                *reinterpret_cast<uint4 *>(out_z + plane(cc)) = *reinterpret_cast<const uint4 *>(oz);
-                            *reinterpret_cast<uint4 *>(out_a + plane(cc)) = *reinterpret_cast<const uint4 *>(oa);
+                                *reinterpret_cast<uint4 *>(o.out_z + plane(cc)) = *reinterpret_cast<const uint4 *>(oz);
+                            *reinterpret_cast<uint4 *>(o.out_a + plane(cc)) = *reinterpret_cast<const uint4 *>(oa);
                         }
                     }
                 }
             }
         }
+        if (fence_out) asm volatile("fence.proxy.async.global;" ::: "memory");
     }
-    tc_fence_before();
+}
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
+    const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ wt,
+    const float *__restrict__ bias, int n, bf16 *__restrict__ out_z, bf16 *__restrict__ out_a,
+    float *__restrict__ out_f, const bf16 *__restrict__ zprev, int *err) {
+    constexpr int HBYTES = (CIN / 8) * TC_SLICE;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TcPipe pp;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t hbase = smem_u32(smem);
+    if (threadIdx.x == 0) pp.wbuf[0] = pp.wbuf[1] = hbase + TC_NST * HBYTES;
+    const uint32_t taddr = tc_pipe_open(pp);
+    // Programmatic dependent launch: the next layer may be scheduled now; this
+    // grid's input (the previous layer's output) is read only after
+    // griddepcontrol.wait, the weights (written before the first layer) before.
+    pdl_trigger();
+    const TcOut o = {bias, out_z, out_a, out_f, zprev};
+    tc_layer<CIN, COUT, EPI>(pp, taddr, &tm_in, o, n, hbase, 0, wt, nullptr, 0, 0, TC_PRO_PDL,
+                             false, err);
+    tc_pipe_close(pp, taddr);
+}
+
+// Grid-wide barrier of a cooperative launch for `expected` CTAs (bar[0]
+// arrivals, bar[1] generation). Bounded: after about a second the CTA sets
+// ERRBIT_TIMEOUT and the abort flag and leaves; every later layer of the
+// launch then does nothing.
+__device__ __forceinline__ void tc_grid_sync(unsigned *bar, int *err, TcPipe &pp) {
     __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                     :: "r"(taddr), "r"(TC_TMEM_COLS));
+    if (threadIdx.x == 0 && !pp.abort_flag) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            for (unsigned it = 0; *gen == g0; ++it) {
+                if ((it & 1023u) == 0 && globaltimer_ns() - t0 > 1000000000ull) {
+                    atomicOr(err, ERRBIT_TIMEOUT);
+                    pp.abort_flag = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
     }
+    __syncthreads();
+}
+
+constexpr size_t tc_forward_smem() {
+    return (size_t)TC_NST * 4 * TC_SLICE + 2 * (size_t)TC_WMAX + 1024;
+}
+
+// The inference forward pass of the surrogate network in one cooperative
+// launch (one CTA per SM): layers 16 -> 32 -> 32 -> 32 (GELU) -> 16 (FP32),
+// a grid barrier between layers (each layer reads the previous one's output
+// around its own tiles), the TMEM allocation and the mbarriers kept across
+// layers, and the weights of layer l + 1 copied into the second weight
+// buffer while layer l runs.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_surr_forward_tc(
+    const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
+    const __grid_constant__ CUtensorMap tm2, const __grid_constant__ CUtensorMap tm3,
+    const bf16 *__restrict__ w0, const bf16 *__restrict__ w1, const bf16 *__restrict__ w2,
+    const bf16 *__restrict__ w3, const float *__restrict__ b0, const float *__restrict__ b1,
+    const float *__restrict__ b2, const float *__restrict__ b3, bf16 *__restrict__ a0,
+    bf16 *__restrict__ a1, bf16 *__restrict__ a2, float *__restrict__ out, int n, unsigned *bar,
+    int *err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TcPipe pp;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t hbase = smem_u32(smem);
+    if (threadIdx.x == 0) {
+        pp.wbuf[0] = hbase + TC_NST * 4 * TC_SLICE;
+        pp.wbuf[1] = pp.wbuf[0] + TC_WMAX;
+    }
+    const uint32_t taddr = tc_pipe_open(pp);
+    pdl_trigger();
+    const int per = tc_slices(n, (n / TC_TX) * (n / TC_TY));
+    tc_layer<16, 32, EPI_GELU_ONLY>(pp, taddr, &tm0, TcOut{b0, nullptr, a0, nullptr, nullptr}, n,
+                                    hbase, 0, w0, w1, tc_wbytes(32, 32), 0, TC_PRO_PDL, true, err);
+    tc_grid_sync(bar, err, pp);
+    tc_layer<32, 32, EPI_GELU_ONLY>(pp, taddr, &tm1, TcOut{b1, nullptr, a1, nullptr, nullptr}, n,
+                                    hbase, 1, nullptr, w2, tc_wbytes(32, 32), per, TC_PRO_PROXY,
+                                    true, err);
+    tc_grid_sync(bar, err, pp);
+    tc_layer<32, 32, EPI_GELU_ONLY>(pp, taddr, &tm2, TcOut{b2, nullptr, a2, nullptr, nullptr}, n,
+                                    hbase, 0, nullptr, w3, tc_wbytes(32, 16), 2 * per,
+                                    TC_PRO_PROXY, true, err);
+    tc_grid_sync(bar, err, pp);
+    tc_layer<32, 16, EPI_F32>(pp, taddr, &tm3, TcOut{b3, nullptr, nullptr, out, nullptr}, n, hbase,
+                              1, nullptr, nullptr, 0, 3 * per, TC_PRO_PROXY, false, err);
+    tc_pipe_close(pp, taddr);
 }
 
 }  // namespace dw
