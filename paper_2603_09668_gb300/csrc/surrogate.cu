@@ -28,6 +28,7 @@ struct SurrHandle {
     bf16 *feats = nullptr;          // [nv][16]
     bf16 *z[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};  // [nv][32]
     float *out = nullptr;           // [nv][16]
+    float *out4 = nullptr;          // [nv][4]: channels 0-3 of out (the chained update's input)
     bf16 *g4 = nullptr;             // [nv][16]: dL/d(out)
     bf16 *gz[3] = {nullptr, nullptr, nullptr};  // [nv][32]: dL/dz of layers 1..3
     float *part = nullptr, *part_b = nullptr;   // weight-gradient partials
@@ -286,7 +287,7 @@ __global__ void k_surr_apply(const float *__restrict__ out, float out_scale,
 constexpr int ADV_VX = 16, ADV_VY = 2, ADV_VZ = 4;
 constexpr int ADV_THREADS = 4 * ADV_VX * ADV_VY * ADV_VZ;  // two fine cells per thread
 __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
-    const float *__restrict__ out, float out_scale, float *__restrict__ fine,
+    const float *__restrict__ out4, float out_scale, float *__restrict__ fine,
     const uint8_t *__restrict__ solid, int n, float in_scale, bf16 *__restrict__ feats) {
     constexpr int SX = ADV_VX + 2, SY = ADV_VY + 2, SZ = ADV_VZ + 2;
     constexpr int NV = ADV_VX * ADV_VY * ADV_VZ;
@@ -315,10 +316,10 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
         const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
         const int cx = min(max(x0 - 1 + ex, 0), n - 1), cy = min(max(y0 - 1 + ey, 0), n - 1);
         const int cz = min(max(z0 - 1 + ez, 0), n - 1);
-        const float *o = out + (((int64_t)cz * n + cy) * n + cx) * 16;
-        st0 = __ldg(o);
-        st1 = __ldg(o + 1);
-        st2 = __ldg(o + 2);
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(out4) + ((int64_t)cz * n + cy) * n + cx);
+        st0 = q.x;
+        st1 = q.y;
+        st2 = q.z;
     }
     int fi[2][3];
     int64_t c[2];
@@ -520,7 +521,7 @@ __global__ void k_vel_err(const float *__restrict__ fa, const float *__restrict_
 template <int CIN, int COUT, int EPI>
 static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, const float *bias,
                       bf16 *oz, bf16 *oa, float *of, const bf16 *zprev, cudaStream_t s,
-                      bool pdl = true) {
+                      bool pdl = true, float *of4 = nullptr) {
     // The kernel allocates the whole tensor memory of its SM, so the shared
     // memory request is raised above half an SM's to keep one CTA per SM.
     constexpr size_t smem = tc_smem<CIN, COUT>() > 120 * 1024 ? tc_smem<CIN, COUT>() : 120 * 1024;
@@ -542,7 +543,7 @@ static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, c
     cfg.attrs = &attr;
     cfg.numAttrs = pdl ? 1 : 0;
     DW_CUDA(cudaLaunchKernelEx(&cfg, k_conv3_tc<CIN, COUT, EPI>, tm_in, wt, bias, h->n, oz, oa, of,
-                               zprev, h->err));
+                               zprev, of4, h->err));
     return DW_OK;
 }
 
@@ -660,6 +661,7 @@ extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
         DW_ALLOC(h->gz[l], sizeof(bf16) * nv * 32);
     }
     DW_ALLOC(h->out, sizeof(float) * nv * 16);
+    DW_ALLOC(h->out4, sizeof(float) * nv * 4);
     DW_ALLOC(h->g4, sizeof(bf16) * nv * 16);
     DW_ALLOC(h->part, sizeof(float) * (size_t)h->nchunks * 27 * 32 * 32);
     DW_ALLOC(h->part_b, sizeof(float) * (size_t)h->nchunks * 32);
@@ -707,6 +709,7 @@ extern "C" dw_status surr_destroy(dw_surr h) {
         cudaFree(h->gz[l]);
     }
     cudaFree(h->out);
+    cudaFree(h->out4);
     cudaFree(h->g4);
     cudaFree(h->part);
     cudaFree(h->part_b);
@@ -820,7 +823,7 @@ extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activation
             (const bf16 *)(h->wf + h->woff[2]), (const bf16 *)(h->wf + h->woff[3]),
             (const float *)(P + h->off_b[0]), (const float *)(P + h->off_b[1]),
             (const float *)(P + h->off_b[2]), (const float *)(P + h->off_b[3]), h->a[0], h->a[1],
-            h->a[2], h->out, h->n, h->gbar, h->err);
+            h->a[2], h->out, h->out4, h->n, h->gbar, h->err);
         if (e == cudaSuccess) {
             h->weights_dirty = false;
             if (out)
@@ -840,7 +843,7 @@ extern "C" dw_status surr_forward(dw_surr h, float *out, int32_t keep_activation
         st = conv<32, 32, EPI_GELU_ONLY>(h, h->tm_a[1], h->wf + h->woff[2], P + h->off_b[2], nullptr, h->a[2], nullptr, nullptr, s);
         if (st != DW_OK) return st;
     }
-    st = conv<32, 16, EPI_F32>(h, h->tm_a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s);
+    st = conv<32, 16, EPI_F32>(h, h->tm_a[2], h->wf + h->woff[3], P + h->off_b[3], nullptr, nullptr, h->out, nullptr, s, true, h->out4);
     h->weights_dirty = false;
     if (st != DW_OK) return st;
     if (out)
@@ -945,7 +948,7 @@ extern "C" dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t
                                        float in_scale, dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
     DW_CUDA(launch_pdl(k_surr_advance_fine, (unsigned)(h->nv / (ADV_VX * ADV_VY * ADV_VZ)),
-                       ADV_THREADS, as_stream(stream), (const float *)h->out, out_scale, h->fine,
+                       ADV_THREADS, as_stream(stream), (const float *)h->out4, out_scale, h->fine,
                        solid, h->n, in_scale, h->feats));
     return DW_OK;
 }

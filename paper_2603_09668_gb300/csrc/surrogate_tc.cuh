@@ -237,12 +237,15 @@ struct TcPipe {
 constexpr int tc_wbytes(int cin, int cout) { return 27 * (cin / 8) * cout * 16; }
 constexpr int TC_WMAX = tc_wbytes(32, 32);  // largest layer's weights
 
-// Output buffers and bias of one layer.
+// Output buffers and bias of one layer. out_f4 (EPI_F32, may be NULL) also
+// receives channels 0-3 of each voxel as one float4, the compact copy the
+// chained update reads.
 struct TcOut {
     const float *bias;
     bf16 *out_z, *out_a;
     float *out_f;
     const bf16 *zprev;
+    float *out_f4;
 };
 
 // What the producer does before the layer's first halo load.
@@ -485,10 +488,13 @@ __device__ __forceinline__ void tc_layer(TcPipe &pp, uint32_t taddr, const CUten
                     auto plane = [&](int cc) { return ((size_t)((c0 + cc) >> 3) * nv + v) * 8; };
                     if (EPI == EPI_F32) {
 #pragma unroll
-                        for (int cc = 0; cc < CPW; cc += 4)
-                            *reinterpret_cast<float4 *>(o.out_f + v * COUT + c0 + cc) =
+                        for (int cc = 0; cc < CPW; cc += 4) {
+                            const float4 q4 =
                                 make_float4(r[m][cc] + o.bias[c0 + cc], r[m][cc + 1] + o.bias[c0 + cc + 1],
                                             r[m][cc + 2] + o.bias[c0 + cc + 2], r[m][cc + 3] + o.bias[c0 + cc + 3]);
+                            *reinterpret_cast<float4 *>(o.out_f + v * COUT + c0 + cc) = q4;
+                            if (cc == 0 && c0 == 0 && o.out_f4) reinterpret_cast<float4 *>(o.out_f4)[v] = q4;
+                        }
                     } else if (EPI == EPI_DGELU) {
 #pragma unroll
                         for (int cc = 0; cc < CPW; cc += 8) {
@@ -526,7 +532,8 @@ template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
     const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ wt,
     const float *__restrict__ bias, int n, bf16 *__restrict__ out_z, bf16 *__restrict__ out_a,
-    float *__restrict__ out_f, const bf16 *__restrict__ zprev, int *err) {
+    float *__restrict__ out_f, const bf16 *__restrict__ zprev, float *__restrict__ out_f4,
+    int *err) {
     constexpr int HBYTES = (CIN / 8) * TC_SLICE;
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcPipe pp;
@@ -539,7 +546,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(
     // grid's input (the previous layer's output) is read only after
     // griddepcontrol.wait, the weights (written before the first layer) before.
     pdl_trigger();
-    const TcOut o = {bias, out_z, out_a, out_f, zprev};
+    const TcOut o = {bias, out_z, out_a, out_f, zprev, out_f4};
     tc_layer<CIN, COUT, EPI>(pp, taddr, &tm_in, o, n, hbase, 0, wt, nullptr, 0, 0, TC_PRO_PDL,
                              false, err);
     tc_pipe_close(pp, taddr);
@@ -591,8 +598,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_surr_forward_tc(
     const bf16 *__restrict__ w0, const bf16 *__restrict__ w1, const bf16 *__restrict__ w2,
     const bf16 *__restrict__ w3, const float *__restrict__ b0, const float *__restrict__ b1,
     const float *__restrict__ b2, const float *__restrict__ b3, bf16 *__restrict__ a0,
-    bf16 *__restrict__ a1, bf16 *__restrict__ a2, float *__restrict__ out, int n, unsigned *bar,
-    int *err) {
+    bf16 *__restrict__ a1, bf16 *__restrict__ a2, float *__restrict__ out, float *__restrict__ out4,
+    int n, unsigned *bar, int *err) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcPipe pp;
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -605,18 +612,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_surr_forward_tc(
     const uint32_t taddr = tc_pipe_open(pp);
     pdl_trigger();
     const int per = tc_slices(n, (n / TC_TX) * (n / TC_TY));
-    tc_layer<16, 32, EPI_GELU_ONLY>(pp, taddr, &tm0, TcOut{b0, nullptr, a0, nullptr, nullptr}, n,
+    tc_layer<16, 32, EPI_GELU_ONLY>(pp, taddr, &tm0, TcOut{b0, nullptr, a0, nullptr, nullptr, nullptr}, n,
                                     hbase, 0, w0, w1, tc_wbytes(32, 32), 0, TC_PRO_PDL, true, err);
     tc_grid_sync(bar, err, pp);
-    tc_layer<32, 32, EPI_GELU_ONLY>(pp, taddr, &tm1, TcOut{b1, nullptr, a1, nullptr, nullptr}, n,
+    tc_layer<32, 32, EPI_GELU_ONLY>(pp, taddr, &tm1, TcOut{b1, nullptr, a1, nullptr, nullptr, nullptr}, n,
                                     hbase, 1, nullptr, w2, tc_wbytes(32, 32), per, TC_PRO_PROXY,
                                     true, err);
     tc_grid_sync(bar, err, pp);
-    tc_layer<32, 32, EPI_GELU_ONLY>(pp, taddr, &tm2, TcOut{b2, nullptr, a2, nullptr, nullptr}, n,
+    tc_layer<32, 32, EPI_GELU_ONLY>(pp, taddr, &tm2, TcOut{b2, nullptr, a2, nullptr, nullptr, nullptr}, n,
                                     hbase, 0, nullptr, w3, tc_wbytes(32, 16), 2 * per,
                                     TC_PRO_PROXY, true, err);
     tc_grid_sync(bar, err, pp);
-    tc_layer<32, 16, EPI_F32>(pp, taddr, &tm3, TcOut{b3, nullptr, nullptr, out, nullptr}, n, hbase,
+    tc_layer<32, 16, EPI_F32>(pp, taddr, &tm3, TcOut{b3, nullptr, nullptr, out, nullptr, out4}, n, hbase,
                               1, nullptr, nullptr, 0, 3 * per, TC_PRO_PROXY, false, err);
     tc_pipe_close(pp, taddr);
 }
