@@ -136,10 +136,14 @@ class SurrogateLBM:
 
     Between surrogate calls the state is the fine (rho, u) field kept in the
     surrogate handle (chained mode); the lattice is re-initialised from it,
-    f = f_eq(rho, u), only when the plain LBM takes over or at the end."""
+    f = f_eq(rho, u), only when the plain LBM takes over or at the end.
+
+    use_graph replays each chained block from a CUDA graph; the default
+    launches eagerly, which chains every kernel to the previous one by
+    programmatic dependent launch, across blocks too."""
 
     def __init__(self, N, tau=0.55, u_inlet=(U_REF, 0.0, 0.0), check_every=10, tol=0.02,
-                 params=None, device="cuda", use_graph=True):
+                 params=None, device="cuda", use_graph=False):
         self.N = N
         self.lbm = B.LBM((N, N, N), tau, u_inlet=u_inlet, bc_x=1, max_tape=1)
         self.surr = B.Surrogate(N // 2)
