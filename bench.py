@@ -65,6 +65,33 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(x, device=None):
+    """Max of a per-rank float over all ranks (the job's time is its slowest
+    rank's); the value itself with one rank. device: where the reduction
+    tensor lives (the rank's GPU under NCCL, the CPU under gloo)."""
+    world, _, _ = dist_env()
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_step):
+    """Whole-job throughput: the units all ranks processed (replicas of the
+    same workload, weak scaling) over the slowest rank's time."""
+    return units_per_rank * world / (ms_step * 1e-3)
+
+
+def replica_seeds(rank):
+    """Seeds of rank r's replica: its own sheet jitter and wind field, the
+    same workload shape on every rank."""
+    return {"seed": rank, "wind_seed": rank}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -159,7 +186,7 @@ def run_ours(args):
     from paper_2603_09668_gb300 import inputs
     from paper_2603_09668_gb300.rollout import Rollout
 
-    sc = inputs.sheet_scene(n_substeps=args.substeps, seed=rank, wind_seed=rank)
+    sc = inputs.sheet_scene(n_substeps=args.substeps, **replica_seeds(rank))
     n = sc.n
     mpm = B.MPM.from_params(sc.params(), max_particles=n, p2g_mode=args.p2g_mode)
     wind = B.WindField(torch.from_numpy(sc.wind).to(dev), sc.t_total)
@@ -202,14 +229,9 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks = clk.summary()
     mpm.device_status()
-    ms_step = sum(times) / len(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = t.item()
+    ms_step = reduce_max(sum(times) / len(times), dev)
     units = n * args.substeps * world
-    value = units / (ms_step * 1e-3)
+    value = job_value(n * args.substeps, world, ms_step)
 
     # ---- end to end through the public API: pinned host in, result out
     host_in = [a.cpu().pin_memory() for a in st0]
@@ -236,12 +258,7 @@ def run_ours(args):
         e1.synchronize()
         if it >= args.warmup:
             e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = sum(e2e_times) / len(e2e_times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = reduce_max(sum(e2e_times) / len(e2e_times), dev)
     h2d = sum(a.numel() * a.element_size() for a in host_in) + host_pin.numel()
     d2h = sum(a.numel() * a.element_size() for a in host_out) + host_ids.numel() * 4
 
