@@ -63,6 +63,10 @@ struct BatchView {
     const int4 *items;  // (scene, first particle, count, 0)
     int n_items;
     float *x, *v, *C, *F;  // concatenated state, stride n
+    // when set, the substep writes its whole output state (x, v, C, F) here
+    // instead of updating x and F in place (the recompute of a reverse
+    // segment, state k in, state k + 1 out)
+    float *ox, *ov, *oC, *oF;
     const uint8_t *pinned;
     int64_t n;
     int *list;   // [2][list_cap]
@@ -153,15 +157,18 @@ __device__ __forceinline__ void batch_item(const BatchView &A, const int4 item,
         const bool pin = A.pinned && A.pinned[p];
         float vn[3], Cn[9];
         g2p_update<CG>(P, S.grid_v, pin, xp, Fp, vn, Cn);
+        const bool out = A.ox != nullptr;
+        float *xo = out ? A.ox : A.x, *Fo = out ? A.oF : A.F;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) A.x[a * n + p] = xp[a];
+        for (int a = 0; a < 3; ++a) xo[a * n + p] = xp[a];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) A.F[c * n + p] = Fp[c];
-        if (FINAL) {
+        for (int c = 0; c < 9; ++c) Fo[c * n + p] = Fp[c];
+        if (FINAL || out) {
+            float *vo = out ? A.ov : A.v, *Co = out ? A.oC : A.C;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) A.v[a * n + p] = vn[a];
+            for (int a = 0; a < 3; ++a) vo[a * n + p] = vn[a];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) A.C[c * n + p] = Cn[c];
+            for (int c = 0; c < 9; ++c) Co[c * n + p] = Cn[c];
         }
         const bool fin = isfinite(xp[0]) && isfinite(xp[1]) && isfinite(xp[2]) && finite9(Fp);
         if (!fin) atomicOr(A.err, ERRBIT_NONFINITE);
@@ -508,6 +515,7 @@ static BatchView view_of(dw_mpm_batch h, const dw_mpm_state &s, const uint8_t *p
     A.v = s.v;
     A.C = s.C;
     A.F = s.F;
+    A.ox = A.ov = A.oC = A.oF = nullptr;
     A.pinned = pinned;
     A.n = h->n_total;
     A.list = h->list;
@@ -1051,16 +1059,26 @@ static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *sta
     auto slot = [&](int k) {  // state k (1 .. n_substeps - 1) in the tape
         return state_view(tape + (size_t)(k - 1) * 24 * (size_t)n, n);
     };
-    uint8_t *pin = const_cast<uint8_t *>(pinned);  // not written: the recompute never sorts
-    const size_t b3 = sizeof(float) * 3 * (size_t)n, b9 = sizeof(float) * 9 * (size_t)n;
-    for (int k = 1; k < n_substeps; ++k) {
-        const dw_mpm_state src = k == 1 ? *start : slot(k - 1), dst = slot(k);
-        DW_CUDA(cudaMemcpyAsync(dst.x, src.x, b3, cudaMemcpyDeviceToDevice, s));
-        DW_CUDA(cudaMemcpyAsync(dst.v, src.v, b3, cudaMemcpyDeviceToDevice, s));
-        DW_CUDA(cudaMemcpyAsync(dst.C, src.C, b9, cudaMemcpyDeviceToDevice, s));
-        DW_CUDA(cudaMemcpyAsync(dst.F, src.F, b9, cudaMemcpyDeviceToDevice, s));
-        st = enqueue_rollout(h, &dst, pin, nullptr, 1, 0, h->cfg, s, k - 1);
-        if (st != DW_OK) return st;
+    // recompute: one P2G of the start state, then substeps k = 0 .. n - 2,
+    // each reading state k and writing state k + 1 whole into the tape while
+    // it scatters the P2G of substep k + 1 (the last one does not scatter)
+    if (n_substeps > 1) {
+        DW_CUDA(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), s));
+        k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(view_of(h, *start, pinned), 0);
+        DW_LAUNCHED("k_batch_p2g");
+        int L = 0;
+        for (int k = 0; k + 1 < n_substeps; ++k) {
+            BatchView A = view_of(h, k == 0 ? *start : slot(k), pinned);
+            const dw_mpm_state o = slot(k + 1);
+            A.ox = o.x;
+            A.ov = o.v;
+            A.oC = o.C;
+            A.oF = o.F;
+            const bool final_ = k + 2 == n_substeps;
+            st = launch_substep(h, A, h->cfg, k, L, final_, s);
+            if (st != DW_OK) return st;
+            if (!final_) L = 1 - L;
+        }
     }
     BatchAdjView R;
     R.node_off = h->d_node_off;
