@@ -1,0 +1,96 @@
+"""FP64 oracle of the physics-informed wind loss (Sec. 3.4) and of the pieces
+of the wind inversion loop around it.
+
+TEST INFRASTRUCTURE ONLY: the CUDA path is checked against these functions;
+only tests/, the smoke check in __graft_entry__.py and bench.py's reference
+leg may import this module. Nothing here is shared with the CUDA library.
+
+What it computes, in numpy float64:
+  - lbm_sample_velocity: the LBM macroscopic velocity (Eq. lbm_sum_v2, via
+    the lattice oracle's moments) trilinearly interpolated at arbitrary
+    points of the unit cube. Reading: lattice cell c spans [c/n, (c+1)/n)
+    (the cell of Eq. point2voxel with dx = 1/n), its velocity sits at the
+    cell centre (c + 1/2)/n; solid cells have u = 0; points are clamped to
+    the box of cell centres.
+  - phys_loss: Sec. 3.4's L_phys = |D_recon - (D_recon . D_guide) D_guide|^2
+    summed over the wind-grid nodes of one keyframe. Reading: D_recon is the
+    node's wind force, D_guide the unit direction of the LBM velocity there;
+    nodes where the flow is (almost) still, |u| <= eps, give no guidance and
+    add nothing. With P = I - d d^T (a projector for unit d) the term is
+    |P F|^2 and its gradient is 2 P F.
+  - adam_step: Adam (Kingma and Ba, 2015) with bias correction.
+  - cos_sim, nmse: the field scores of the evaluation (mean cosine similarity
+    of force vectors, normalised mean squared error).
+"""
+import numpy as np
+
+from . import lbm_macroscopic
+
+
+def lbm_sample_velocity(shape, f, pos, solid=None, force=(0.0, 0.0, 0.0)):
+    """u[3][m] at positions pos[3][m] of the unit cube, from populations f
+    (natural order, f[q][cell] unshifted, as the lattice oracle stores them)."""
+    nx, ny, nz = shape
+    rho, u = lbm_macroscopic(shape, f, force, solid)
+    u = u.reshape(3, nz, ny, nx)
+    pos = np.asarray(pos, np.float64)
+    m = pos.shape[1]
+    out = np.zeros((3, m))
+    dims = (nx, ny, nz)
+    for p in range(m):
+        i0, t = [0, 0, 0], [0.0, 0.0, 0.0]
+        for a in range(3):
+            n = dims[a]
+            s = min(max(pos[a, p] * n - 0.5, 0.0), n - 1.0)
+            i = min(int(np.floor(s)), n - 2)
+            i0[a], t[a] = i, s - i
+        for cz in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    w = ((t[0] if cx else 1 - t[0]) * (t[1] if cy else 1 - t[1]) *
+                         (t[2] if cz else 1 - t[2]))
+                    out[:, p] += w * u[:, i0[2] + cz, i0[1] + cy, i0[0] + cx]
+    return out
+
+
+def phys_loss(values, guide_u, eps=1e-6):
+    """(L_phys, dL/dvalues) of one keyframe: values [m][3] wind forces at the
+    nodes, guide_u [3][m] LBM velocities there."""
+    F = np.asarray(values, np.float64).reshape(-1, 3)
+    u = np.asarray(guide_u, np.float64).reshape(3, -1).T
+    loss = 0.0
+    g = np.zeros_like(F)
+    for k in range(F.shape[0]):
+        norm = np.sqrt(u[k] @ u[k])
+        if norm <= eps:
+            continue
+        d = u[k] / norm
+        r = F[k] - (F[k] @ d) * d
+        loss += r @ r
+        g[k] = 2.0 * r
+    return loss, g
+
+
+def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (step >= 1); returns (param, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** step)
+    vh = v / (1.0 - beta2 ** step)
+    return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def cos_sim(a, b, eps=1e-12):
+    """Mean cosine similarity of the 3-vectors of two fields [..., 3]."""
+    a = np.asarray(a, np.float64).reshape(-1, 3)
+    b = np.asarray(b, np.float64).reshape(-1, 3)
+    na, nb = np.linalg.norm(a, axis=1), np.linalg.norm(b, axis=1)
+    keep = (na > eps) & (nb > eps)
+    return float(np.mean(np.sum(a[keep] * b[keep], axis=1) / (na[keep] * nb[keep])))
+
+
+def nmse(a, ref):
+    """|a - ref|^2 / |ref|^2."""
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.sum((a - ref) ** 2) / np.sum(ref ** 2))

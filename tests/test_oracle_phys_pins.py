@@ -1,0 +1,135 @@
+"""Pins of the physics-informed wind loss oracle (oracle/phys.py) against
+what Sec. 3.4 and the mathematics fix: closed forms of L_phys (a force along
+the flow costs nothing, a force across it costs |F|^2), its invariance under
+rotations, its gradient by central differences; the guide velocity sampler
+against lattices whose velocity field is known in closed form (uniform and
+linear fields are reproduced exactly by trilinear interpolation, solid cells
+are at rest); Adam against torch.optim.Adam (an independent implementation)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import phys
+
+
+def eq_lattice(shape, ufun):
+    """Populations f_eq(1, u(cell centre)) of every cell (the lattice oracle's
+    natural order), so that the macroscopic velocity is u exactly."""
+    nx, ny, nz = shape
+    f = np.zeros((19, nz * ny * nx))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                c = (z * ny + y) * nx + x
+                u = ufun((x + 0.5) / nx, (y + 0.5) / ny, (z + 0.5) / nz)
+                f[:, c] = oracle.lbm_equilibrium(1.0, u)
+    return f
+
+
+def test_uniform_flow_is_sampled_exactly():
+    shape = (6, 5, 4)
+    u0 = np.array([0.03, -0.01, 0.02])
+    f = eq_lattice(shape, lambda x, y, z: u0)
+    pos = np.random.default_rng(0).random((3, 50))
+    u = phys.lbm_sample_velocity(shape, f, pos)
+    assert np.allclose(u, u0[:, None], atol=1e-15)
+
+
+def test_linear_field_is_reproduced_between_cell_centres():
+    shape = (8, 6, 5)
+    a = np.array([[0.02, -0.01, 0.005], [0.0, 0.015, -0.01], [0.01, 0.0, 0.02]])
+    b = np.array([0.01, -0.02, 0.005])
+    f = eq_lattice(shape, lambda x, y, z: b + a @ np.array([x, y, z]))
+    rng = np.random.default_rng(1)
+    # points inside the box of cell centres
+    lo = np.array([0.5 / shape[0], 0.5 / shape[1], 0.5 / shape[2]])
+    pos = lo[:, None] + rng.random((3, 40)) * (1 - 2 * lo)[:, None]
+    u = phys.lbm_sample_velocity(shape, f, pos)
+    assert np.allclose(u, b[:, None] + a @ pos, atol=1e-14)
+    # outside that box the point is clamped to the nearest centre
+    out = phys.lbm_sample_velocity(shape, f, np.array([[0.0], [0.0], [0.0]]))
+    assert np.allclose(out[:, 0], b + a @ lo, atol=1e-14)
+
+
+def test_solid_cells_are_at_rest():
+    shape = (4, 4, 4)
+    u0 = np.array([0.04, 0.0, 0.0])
+    f = eq_lattice(shape, lambda x, y, z: u0)
+    solid = np.zeros(64, np.uint8)
+    solid[(1 * 4 + 1) * 4 + 1] = 1  # cell (1, 1, 1)
+    # the centre of cell (1, 1, 1) samples that cell alone
+    u = phys.lbm_sample_velocity(shape, f, np.array([[1.5 / 4], [1.5 / 4], [1.5 / 4]]), solid)
+    assert np.allclose(u, 0.0)
+    # half way to cell (2, 1, 1): the mean of rest and u0
+    u = phys.lbm_sample_velocity(shape, f, np.array([[2.0 / 4], [1.5 / 4], [1.5 / 4]]), solid)
+    assert np.allclose(u[:, 0], 0.5 * u0)
+
+
+def test_phys_loss_closed_forms():
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal((3, 20))
+    d = u / np.linalg.norm(u, axis=0)
+    along = (3.0 * d).T
+    loss, g = phys.phys_loss(along, u)
+    assert loss == pytest.approx(0.0, abs=1e-24)
+    assert np.allclose(g, 0.0, atol=1e-12)
+    # a force across the flow costs all of its square
+    perp = np.cross(d.T, rng.standard_normal((20, 3)))
+    loss, g = phys.phys_loss(perp, u)
+    assert loss == pytest.approx(float(np.sum(perp ** 2)), rel=1e-12)
+    assert np.allclose(g, 2 * perp, atol=1e-12)
+    # still nodes give no guidance
+    loss, g = phys.phys_loss(perp, np.zeros((3, 20)))
+    assert loss == 0.0 and not g.any()
+
+
+def test_phys_loss_is_rotation_invariant():
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((30, 3))
+    u = rng.standard_normal((3, 30))
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    l0, g0 = phys.phys_loss(F, u)
+    l1, g1 = phys.phys_loss(F @ q.T, q @ u)
+    assert l1 == pytest.approx(l0, rel=1e-12)
+    assert np.allclose(g1, g0 @ q.T, atol=1e-12)
+
+
+def test_phys_loss_gradient_by_central_differences():
+    rng = np.random.default_rng(4)
+    F = rng.standard_normal((12, 3))
+    u = rng.standard_normal((3, 12))
+    u[:, 5] = 0.0  # a still node
+    _, g = phys.phys_loss(F, u)
+    eps = 1e-6
+    for k in range(12):
+        for c in range(3):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[k, c] += eps
+            Fm[k, c] -= eps
+            fd = (phys.phys_loss(Fp, u)[0] - phys.phys_loss(Fm, u)[0]) / (2 * eps)
+            assert g[k, c] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_adam_matches_torch():
+    rng = np.random.default_rng(5)
+    p0 = rng.standard_normal(17)
+    grads = [rng.standard_normal(17) for _ in range(6)]
+    p, m, v = p0.copy(), np.zeros(17), np.zeros(17)
+    t = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=0.05, betas=(0.9, 0.999), eps=1e-8)
+    for k, g in enumerate(grads, start=1):
+        p, m, v = phys.adam_step(p, g, m, v, k, 0.05)
+        opt.zero_grad()
+        t.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+    assert np.allclose(p, t.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_scores():
+    a = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    assert phys.cos_sim(a, a) == pytest.approx(1.0)
+    assert phys.cos_sim(a, -a) == pytest.approx(-1.0)
+    assert phys.cos_sim(a, np.array([[0.0, 1.0, 0.0], [3.0, 0.0, 0.0]])) == pytest.approx(0.0)
+    assert phys.nmse(a, a) == 0.0
+    assert phys.nmse(2 * a, a) == pytest.approx(1.0)
