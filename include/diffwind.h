@@ -239,6 +239,29 @@ DW_API dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_state
                                      const dw_wind_field *wind, float t,
                                      int32_t *device_status, dw_stream stream);
 
+/* ================================================ physics-informed wind loss
+ * Sec. 3.4: the LBM velocity D_guide steers the direction of the wind force
+ * D_recon through L_phys = |D_recon - (D_recon . D_guide) D_guide|^2. Read
+ * per wind-grid node of one keyframe, with d = u / |u| the unit direction of
+ * the LBM velocity u there: the term |F - (F.d) d|^2 is the square of the
+ * force component across the flow; nodes with |u| <= eps (still or solid)
+ * give no guidance and add nothing. Its gradient is 2 (F - (F.d) d).
+ */
+
+/* loss (device float, accumulated) += sum of the terms over the n nodes;
+ * g_values (device [n][3], accumulated, may be NULL) += their gradients.
+ * values [n][3] is one keyframe's slice of dw_wind_field.values, guide_u
+ * [3][n] the LBM velocity at the same nodes (lbm_sample_velocity). */
+DW_API dw_status wind_phys_loss(const float *values, const float *guide_u, int64_t n, float eps,
+                                float *loss, float *g_values, dw_stream stream);
+
+/* One Adam step (Kingma and Ba, with bias correction) on n parameters:
+ * m, v are the moment buffers (device, zero before step 1), step >= 1. The
+ * update of the wind inversion loop (per keyframe, Sec. 3.3). */
+DW_API dw_status adam_step(float *param, const float *grad, float *m, float *v, int64_t n,
+                           float lr, float beta1, float beta2, float eps, int32_t step,
+                           dw_stream stream);
+
 /* ============================================================ batched MPM
  * Many independent scenes, each with its own grid size, material, time step,
  * particle count and wind field, advanced by the same substep as mpm_rollout
@@ -427,6 +450,16 @@ DW_API dw_status lbm_step_adjoint(dw_lbm h, const float *f_in, float *g_f, const
  * Either output may be NULL. Solid cells get rho = 0, u = 0. */
 DW_API dw_status lbm_macroscopic(dw_lbm h, const float *f, const uint8_t *solid, float *rho, float *u,
                           dw_stream stream);
+
+/* The LBM wind velocity at points (the guide of the physics-informed loss,
+ * Sec. 3.4): u_out[3][n] = the velocity of Eq. lbm_sum_v2 interpolated
+ * trilinearly between cell centres (cell c of an axis with n_a cells spans
+ * [c/n_a, (c+1)/n_a), its centre (c + 1/2)/n_a; points are clamped to the box
+ * of centres), solid cells (solid may be NULL) counting as at rest. pos is
+ * device [3][n] in unit-cube coordinates; f the shifted lattice. Errors:
+ * DW_ERR_ARG for null pointers with n > 0. */
+DW_API dw_status lbm_sample_velocity(dw_lbm h, const float *f, const uint8_t *solid,
+                                     const float *pos, int64_t n, float *u_out, dw_stream stream);
 
 /* Fill f with the shifted equilibrium f_eq(rho0, u0) - w at every cell. */
 DW_API dw_status lbm_init_equilibrium(dw_lbm h, float *f, float rho0, const float u0[3],

@@ -19,8 +19,8 @@ What it computes, in numpy float64:
     add nothing. With P = I - d d^T (a projector for unit d) the term is
     |P F|^2 and its gradient is 2 P F.
   - adam_step: Adam (Kingma and Ba, 2015) with bias correction.
-  - cos_sim, nmse: the field scores of the evaluation (mean cosine similarity
-    of force vectors, normalised mean squared error).
+  - cos_sim, nmse: the scores of the wind-field evaluation (Sec. 4.4, Table
+    of CosSim / NMSE): both on force vectors normalised to unit length.
 """
 import numpy as np
 
@@ -80,17 +80,26 @@ def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def cos_sim(a, b, eps=1e-12):
-    """Mean cosine similarity of the 3-vectors of two fields [..., 3]."""
-    a = np.asarray(a, np.float64).reshape(-1, 3)
-    b = np.asarray(b, np.float64).reshape(-1, 3)
+def _unit_pairs(rec, gt, eps):
+    """Unit vectors of the locations where both fields have a direction."""
+    a = np.asarray(rec, np.float64).reshape(-1, 3)
+    b = np.asarray(gt, np.float64).reshape(-1, 3)
     na, nb = np.linalg.norm(a, axis=1), np.linalg.norm(b, axis=1)
     keep = (na > eps) & (nb > eps)
-    return float(np.mean(np.sum(a[keep] * b[keep], axis=1) / (na[keep] * nb[keep])))
+    return a[keep] / na[keep, None], b[keep] / nb[keep, None]
 
 
-def nmse(a, ref):
-    """|a - ref|^2 / |ref|^2."""
-    a = np.asarray(a, np.float64)
-    ref = np.asarray(ref, np.float64)
-    return float(np.sum((a - ref) ** 2) / np.sum(ref ** 2))
+def cos_sim(rec, gt, eps=1e-12):
+    """The evaluation's CosSim: the mean over grid locations (and time steps)
+    of F_gt^ . F_rec^, each force normalised to unit length. Reading: a
+    location where either force is zero has no direction and is left out."""
+    a, b = _unit_pairs(rec, gt, eps)
+    return float(np.mean(np.sum(a * b, axis=1)))
+
+
+def nmse(rec, gt, eps=1e-12):
+    """The evaluation's NMSE: the mean of |F_gt^ - F_rec^|^2 over the same
+    normalised vectors (range [0, 4]; for unit vectors it equals
+    2 - 2 CosSim)."""
+    a, b = _unit_pairs(rec, gt, eps)
+    return float(np.mean(np.sum((a - b) ** 2, axis=1)))

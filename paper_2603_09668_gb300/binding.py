@@ -22,7 +22,8 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_substep", "mpm_substep_adjoint", "mpm_segment_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
-           "lbm_init_equilibrium", "voxelize_particles", "MPM", "LBM", "surr_create",
+           "lbm_init_equilibrium", "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
+           "adam_step", "MPM", "LBM", "surr_create",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
@@ -376,6 +377,33 @@ def lbm_init_equilibrium(h, f, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
     return f
 
 
+def lbm_sample_velocity(h, f, solid, pos, u_out=None, stream=None):
+    """u[3][n] of the lattice f at points pos[3][n] (unit cube)."""
+    n = pos.shape[1]
+    if u_out is None:
+        u_out = torch.empty((3, n), dtype=torch.float32, device=pos.device)
+    check(lib().lbm_sample_velocity(h, _dev(f, name="f"), _mask(solid), _dev(pos, name="pos"),
+                                    int(n), _dev(u_out, name="u_out"), _stream(stream)))
+    return u_out
+
+
+def wind_phys_loss(values, guide_u, loss, g_values=None, eps=1e-6, stream=None):
+    """loss += L_phys of one keyframe (values [n][3], guide_u [3][n]);
+    g_values += its gradient (when given)."""
+    n = guide_u.shape[1]
+    check(lib().wind_phys_loss(_dev(values, name="values"), _dev(guide_u, name="guide_u"), int(n),
+                               float(eps), _dev(loss, name="loss"), _dev(g_values, name="g_values"),
+                               _stream(stream)))
+    return loss
+
+
+def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(lib().adam_step(_dev(param, name="param"), _dev(grad, name="grad"), _dev(m, name="m"),
+                          _dev(v, name="v"), int(param.numel()), float(lr), float(beta1),
+                          float(beta2), float(eps), int(step), _stream(stream)))
+    return param
+
+
 def voxelize_particles(pos, shape, dx, solid, stream=None):
     nx, ny, nz = shape
     check(lib().voxelize_particles(_dev(pos, name="pos"), pos.shape[1], int(nx), int(ny), int(nz),
@@ -529,6 +557,9 @@ class LBM:
 
     def step_adjoint(self, f_in, g_f, solid, steps, stream=None):
         return lbm_step_adjoint(self.h, f_in, g_f, solid, steps, stream)
+
+    def sample_velocity(self, f, solid, pos, u_out=None, stream=None):
+        return lbm_sample_velocity(self.h, f, solid, pos, u_out, stream)
 
     def macroscopic(self, f, solid, stream=None):
         nx, ny, nz = self.shape

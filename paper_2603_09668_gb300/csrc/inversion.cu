@@ -1,0 +1,95 @@
+// Pieces of the wind inversion loop around the MPM adjoint: the
+// physics-informed loss of Sec. 3.4 (the force component across the LBM flow
+// direction, squared, per wind-grid node) and an Adam step for the per-
+// keyframe optimisation of the wind force field (Sec. 3.3).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace dw {
+
+constexpr int PHYS_THREADS = 256;
+
+// One thread per node: r = F - (F.d) d with d = u / |u| (no term where
+// |u| <= eps); loss gets one atomic per block, g_values += 2 r.
+__global__ void __launch_bounds__(PHYS_THREADS) k_wind_phys_loss(
+    const float *__restrict__ values, const float *__restrict__ guide_u, int64_t n, float eps,
+    float *__restrict__ loss, float *__restrict__ g_values) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float term = 0.0f;
+    if (k < n) {
+        const float u0 = guide_u[k], u1 = guide_u[n + k], u2 = guide_u[2 * n + k];
+        const float norm = sqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+        if (norm > eps) {
+            const float d0 = u0 / norm, d1 = u1 / norm, d2 = u2 / norm;
+            const float F0 = values[3 * k], F1 = values[3 * k + 1], F2 = values[3 * k + 2];
+            const float fd = F0 * d0 + F1 * d1 + F2 * d2;
+            const float r0 = F0 - fd * d0, r1 = F1 - fd * d1, r2 = F2 - fd * d2;
+            term = r0 * r0 + r1 * r1 + r2 * r2;
+            if (g_values) {
+                g_values[3 * k] += 2.0f * r0;
+                g_values[3 * k + 1] += 2.0f * r1;
+                g_values[3 * k + 2] += 2.0f * r2;
+            }
+        }
+    }
+    // block sum, one atomic
+    __shared__ float red[PHYS_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = term;
+    __syncthreads();
+    if (wid == 0) {
+        float sum = lane < PHYS_THREADS / 32 ? red[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) atomicAdd(loss, sum);
+    }
+}
+
+__global__ void k_adam_step(float *__restrict__ param, const float *__restrict__ grad,
+                            float *__restrict__ m, float *__restrict__ v, int64_t n, float lr,
+                            float beta1, float beta2, float eps, float bc1, float bc2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float mi = beta1 * m[i] + (1.0f - beta1) * g;
+    const float vi = beta2 * v[i] + (1.0f - beta2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    param[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+extern "C" dw_status wind_phys_loss(const float *values, const float *guide_u, int64_t n,
+                                    float eps, float *loss, float *g_values, dw_stream stream) {
+    DW_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return DW_OK;
+    DW_REQUIRE(values && guide_u && loss, "values, guide_u and loss must not be NULL");
+    DW_REQUIRE(eps >= 0.0f, "eps must be >= 0");
+    k_wind_phys_loss<<<grid_for(n, PHYS_THREADS), PHYS_THREADS, 0, as_stream(stream)>>>(
+        values, guide_u, n, eps, loss, g_values);
+    DW_LAUNCHED("k_wind_phys_loss");
+    return DW_OK;
+}
+
+extern "C" dw_status adam_step(float *param, const float *grad, float *m, float *v, int64_t n,
+                               float lr, float beta1, float beta2, float eps, int32_t step,
+                               dw_stream stream) {
+    DW_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return DW_OK;
+    DW_REQUIRE(param && grad && m && v, "param, grad, m and v must not be NULL");
+    DW_REQUIRE(step >= 1, "step must be >= 1");
+    DW_REQUIRE(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f,
+               "betas must be in [0, 1)");
+    const float bc1 = 1.0f - (float)pow((double)beta1, (double)step);
+    const float bc2 = 1.0f - (float)pow((double)beta2, (double)step);
+    k_adam_step<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(param, grad, m, v, n, lr, beta1,
+                                                                  beta2, eps, bc1, bc2);
+    DW_LAUNCHED("k_adam_step");
+    return DW_OK;
+}

@@ -371,13 +371,13 @@ __global__ void __launch_bounds__(256, 4) k_lbm_adjoint(LbmParams L, const float
 
 // ------------------------------------------------------------ auxiliaries --
 
-__global__ void k_lbm_macroscopic(LbmParams L, const float *__restrict__ f,
-                                  const uint8_t *__restrict__ solid, float *__restrict__ rho,
-                                  float *__restrict__ u) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
+// rho and u of one cell by Eq. lbm_sum_v2 (shifted populations: rho = 1 +
+// sum f, rho u = sum c f + F/2); solid cells report rho = 0, u = 0.
+__device__ __forceinline__ void cell_moments(const LbmParams &L, const float *__restrict__ f,
+                                             const uint8_t *__restrict__ solid, int cell,
+                                             float &r, float &ux, float &uy, float &uz) {
     const size_t nc = (size_t)L.ncell;
-    float r = 0.0f, ux = 0.0f, uy = 0.0f, uz = 0.0f;
+    r = ux = uy = uz = 0.0f;
     if (!(solid && solid[cell])) {
         float rs = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
@@ -393,12 +393,59 @@ __global__ void k_lbm_macroscopic(LbmParams L, const float *__restrict__ f,
         uy = (jy + 0.5f * L.Fy) / r;
         uz = (jz + 0.5f * L.Fz) / r;
     }
+}
+
+__global__ void k_lbm_macroscopic(LbmParams L, const float *__restrict__ f,
+                                  const uint8_t *__restrict__ solid, float *__restrict__ rho,
+                                  float *__restrict__ u) {
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const size_t nc = (size_t)L.ncell;
+    float r, ux, uy, uz;
+    cell_moments(L, f, solid, cell, r, ux, uy, uz);
     if (rho) rho[cell] = r;
     if (u) {
         u[cell] = ux;
         u[nc + cell] = uy;
         u[2 * nc + cell] = uz;
     }
+}
+
+// The velocity at points pos[3][n] of the unit cube: trilinear between the
+// cell centres ((c + 1/2) / n per axis, clamped to their box) of the cells'
+// velocities (solid cells at rest).
+__global__ void k_lbm_sample_velocity(LbmParams L, const float *__restrict__ f,
+                                      const uint8_t *__restrict__ solid,
+                                      const float *__restrict__ pos, int64_t n,
+                                      float *__restrict__ u_out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int dims[3] = {L.nx, L.ny, L.nz};
+    int i0[3];
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float sc = pos[a * n + p] * (float)dims[a] - 0.5f;
+        sc = fminf(fmaxf(sc, 0.0f), (float)(dims[a] - 1));  // NaN -> 0
+        const int i = min((int)floorf(sc), dims[a] - 2);
+        i0[a] = i;
+        t[a] = sc - (float)i;
+    }
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int cx = q & 1, cy = (q >> 1) & 1, cz = q >> 2;
+        const float w = (cx ? t[0] : 1.0f - t[0]) * (cy ? t[1] : 1.0f - t[1]) *
+                        (cz ? t[2] : 1.0f - t[2]);
+        const int cell = ((i0[2] + cz) * L.ny + (i0[1] + cy)) * L.nx + (i0[0] + cx);
+        float r, ux, uy, uz;
+        cell_moments(L, f, solid, cell, r, ux, uy, uz);
+        acc[0] += w * ux;
+        acc[1] += w * uy;
+        acc[2] += w * uz;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u_out[a * n + p] = acc[a];
 }
 
 __global__ void k_lbm_fill_eq(LbmParams L, float *__restrict__ f, float rho0, float ux, float uy,
@@ -592,6 +639,19 @@ extern "C" dw_status lbm_macroscopic(dw_lbm h, const float *f, const uint8_t *so
     if (!rho && !u) return DW_OK;
     k_lbm_macroscopic<<<grid_for(h->L.ncell, 256), 256, 0, as_stream(stream)>>>(h->L, f, solid, rho, u);
     DW_LAUNCHED("k_lbm_macroscopic");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_sample_velocity(dw_lbm h, const float *f, const uint8_t *solid,
+                                         const float *pos, int64_t n, float *u_out,
+                                         dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return DW_OK;
+    DW_REQUIRE(f && pos && u_out, "f, pos and u_out must not be NULL");
+    k_lbm_sample_velocity<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(h->L, f, solid, pos, n,
+                                                                            u_out);
+    DW_LAUNCHED("k_lbm_sample_velocity");
     return DW_OK;
 }
 

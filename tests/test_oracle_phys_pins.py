@@ -132,4 +132,13 @@ def test_scores():
     assert phys.cos_sim(a, -a) == pytest.approx(-1.0)
     assert phys.cos_sim(a, np.array([[0.0, 1.0, 0.0], [3.0, 0.0, 0.0]])) == pytest.approx(0.0)
     assert phys.nmse(a, a) == 0.0
-    assert phys.nmse(2 * a, a) == pytest.approx(1.0)
+    assert phys.nmse(5 * a, a) == pytest.approx(0.0)  # directions only
+    assert phys.nmse(-a, a) == pytest.approx(4.0)
+    # unit vectors: |a^ - b^|^2 = 2 - 2 a^.b^, so NMSE = 2 - 2 CosSim
+    rng = np.random.default_rng(6)
+    x, y = rng.standard_normal((50, 3)), rng.standard_normal((50, 3))
+    assert phys.nmse(x, y) == pytest.approx(2 - 2 * phys.cos_sim(x, y), abs=1e-12)
+    # a location without a direction is left out
+    z = x.copy()
+    z[3] = 0.0
+    assert phys.cos_sim(z, y) == pytest.approx(phys.cos_sim(np.delete(x, 3, 0), np.delete(y, 3, 0)))
