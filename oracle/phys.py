@@ -19,8 +19,8 @@ What it computes, in numpy float64:
     add nothing. With P = I - d d^T (a projector for unit d) the term is
     |P F|^2 and its gradient is 2 P F.
   - adam_step: Adam (Kingma and Ba, 2015) with bias correction.
-  - cos_sim, nmse: the scores of the wind-field evaluation (Sec. 4.4, Table
-    of CosSim / NMSE): both on force vectors normalised to unit length.
+  - cos_sim, nmse: the scores of the wind-force-field evaluation (App. E.2,
+    the CosSim / NMSE table): both on force vectors normalised to unit length.
 """
 import numpy as np
 
