@@ -248,12 +248,39 @@ DW_API dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_state
  * give no guidance and add nothing. Its gradient is 2 (F - (F.d) d).
  */
 
-/* loss (device float, accumulated) += sum of the terms over the n nodes;
- * g_values (device [n][3], accumulated, may be NULL) += their gradients.
+/* loss (device float, accumulated) += weight * the sum of the terms over the
+ * n nodes; g_values (device [n][3], accumulated, may be NULL) += weight * their
+ * gradients (weight is the loss's factor in a weighted sum of losses).
  * values [n][3] is one keyframe's slice of dw_wind_field.values, guide_u
  * [3][n] the LBM velocity at the same nodes (lbm_sample_velocity). */
 DW_API dw_status wind_phys_loss(const float *values, const float *guide_u, int64_t n, float eps,
-                                float *loss, float *g_values, dw_stream stream);
+                                float weight, float *loss, float *g_values, dw_stream stream);
+
+/* Scores of a reconstructed wind force field against a reference one
+ * (App. E.2, the CosSim / NMSE evaluation): both forces at a location are
+ * normalised to unit length, a^ and b^. Over the n locations where both have
+ * |.| > eps, sums (device float[3], accumulated, so several keyframes add up)
+ * += {sum a^.b^, sum |a^ - b^|^2, number of such locations}; CosSim =
+ * sums[0] / sums[2] and NMSE = sums[1] / sums[2]. rec, gt are [n][3]. */
+DW_API dw_status wind_field_scores(const float *rec, const float *gt, int64_t n, float eps,
+                                   float *sums, dw_stream stream);
+
+/* The aerodynamic drag relation of Sec. 3.4, F_w = 1/2 rho_w C_D |v|^2 v/|v|,
+ * per node: values[k] = scale |u_k| u_k, with u [3][n] a wind velocity (e.g.
+ * lbm_sample_velocity at the wind-grid nodes) and values [n][3] one keyframe
+ * of dw_wind_field.values (overwritten). scale folds 1/2 rho_w C_D, the
+ * object's mass density and the lattice-to-physical velocity unit into one
+ * constant, so values is the wind acceleration the MPM grid update adds. */
+DW_API dw_status wind_drag_force(const float *u, int64_t n, float scale, float *values,
+                                 dw_stream stream);
+
+/* The trajectory term of the inversion loop: loss (device float, accumulated)
+ * += weight * sum_p |x_p - x_target_p|^2 over n particles, and g_x (device
+ * [3][n], accumulated, may be NULL) += 2 weight (x_p - x_target_p), the
+ * gradient an MPM adjoint takes as dL/dx of the final state. x and x_target
+ * are device [3][n]. */
+DW_API dw_status position_loss(const float *x, const float *x_target, int64_t n, float weight,
+                               float *loss, float *g_x, dw_stream stream);
 
 /* One Adam step (Kingma and Ba, with bias correction) on n parameters:
  * m, v are the moment buffers (device, zero before step 1), step >= 1. The

@@ -18,6 +18,10 @@ What it computes, in numpy float64:
     nodes where the flow is (almost) still, |u| <= eps, give no guidance and
     add nothing. With P = I - d d^T (a projector for unit d) the term is
     |P F|^2 and its gradient is 2 P F.
+  - drag_force: Sec. 3.4's drag relation F_w = 1/2 rho_w C_D |v|^2 v/|v|,
+    with all constants folded into one scale: F = scale |u| u.
+  - position_loss: the trajectory term weight * sum_p |x_p - x_p*|^2 and its
+    gradient 2 weight (x - x*).
   - adam_step: Adam (Kingma and Ba, 2015) with bias correction.
   - cos_sim, nmse: the scores of the wind-force-field evaluation (App. E.2,
     the CosSim / NMSE table): both on force vectors normalised to unit length.
@@ -69,6 +73,19 @@ def phys_loss(values, guide_u, eps=1e-6):
         loss += r @ r
         g[k] = 2.0 * r
     return loss, g
+
+
+def drag_force(u, scale):
+    """values [m][3] = scale |u| u for velocities u [3][m]."""
+    u = np.asarray(u, np.float64).reshape(3, -1).T
+    speed = np.sqrt(np.sum(u * u, axis=1))
+    return scale * speed[:, None] * u
+
+
+def position_loss(x, x_target, weight=1.0):
+    """(weight * sum |x - x*|^2, its gradient [3][n]) for x, x* [3][n]."""
+    d = np.asarray(x, np.float64) - np.asarray(x_target, np.float64)
+    return weight * float(np.sum(d * d)), 2.0 * weight * d
 
 
 def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -98,8 +98,11 @@ SIGNATURES = {
     "lbm_init_equilibrium": (I32, [VP, VP, F32, P(F32 * 3), VP]),
     "voxelize_particles": (I32, [VP, I64, I32, I32, I32, F32, VP, VP]),
     "lbm_sample_velocity": (I32, [VP, VP, VP, VP, I64, VP, VP]),
-    "wind_phys_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
+    "wind_phys_loss": (I32, [VP, VP, I64, F32, F32, VP, VP, VP]),
+    "wind_field_scores": (I32, [VP, VP, I64, F32, VP, VP]),
     "adam_step": (I32, [VP, VP, VP, VP, I64, F32, F32, F32, F32, I32, VP]),
+    "wind_drag_force": (I32, [VP, I64, F32, VP, VP]),
+    "position_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
     "surr_create": (I32, [I32, P(VP)]),
     "surr_destroy": (I32, [VP]),
     "surr_num_params": (I32, [VP, P(I64)]),

@@ -23,7 +23,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
-           "adam_step", "MPM", "LBM", "surr_create",
+           "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "MPM", "LBM", "surr_create",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
@@ -387,13 +387,44 @@ def lbm_sample_velocity(h, f, solid, pos, u_out=None, stream=None):
     return u_out
 
 
-def wind_phys_loss(values, guide_u, loss, g_values=None, eps=1e-6, stream=None):
-    """loss += L_phys of one keyframe (values [n][3], guide_u [3][n]);
-    g_values += its gradient (when given)."""
+def wind_phys_loss(values, guide_u, loss, g_values=None, eps=1e-6, weight=1.0, stream=None):
+    """loss += weight * L_phys of one keyframe (values [n][3], guide_u [3][n]);
+    g_values += weight * its gradient (when given)."""
     n = guide_u.shape[1]
     check(lib().wind_phys_loss(_dev(values, name="values"), _dev(guide_u, name="guide_u"), int(n),
-                               float(eps), _dev(loss, name="loss"), _dev(g_values, name="g_values"),
-                               _stream(stream)))
+                               float(eps), float(weight), _dev(loss, name="loss"),
+                               _dev(g_values, name="g_values"), _stream(stream)))
+    return loss
+
+
+def wind_field_scores(rec, gt, sums=None, eps=1e-12, stream=None):
+    """sums[3] += (sum of unit-vector cosines, sum of squared unit-vector
+    differences, count) over the locations of rec, gt [n][3] where both have a
+    direction; CosSim = sums[0] / sums[2], NMSE = sums[1] / sums[2]."""
+    if sums is None:
+        sums = torch.zeros(3, dtype=torch.float32, device=rec.device)
+    n = rec.numel() // 3
+    check(lib().wind_field_scores(_dev(rec, name="rec"), _dev(gt, name="gt"), int(n), float(eps),
+                                  _dev(sums, name="sums"), _stream(stream)))
+    return sums
+
+
+def wind_drag_force(u, scale, values=None, stream=None):
+    """values[n][3] = scale |u| u for velocities u[3][n] (the drag relation)."""
+    n = u.shape[1]
+    if values is None:
+        values = torch.empty((n, 3), dtype=torch.float32, device=u.device)
+    check(lib().wind_drag_force(_dev(u, name="u"), int(n), float(scale),
+                                _dev(values, name="values"), _stream(stream)))
+    return values
+
+
+def position_loss(x, x_target, loss, weight=1.0, g_x=None, stream=None):
+    """loss += weight sum |x - x_target|^2 (x, x_target [3][n]); g_x += its gradient."""
+    n = x.shape[1]
+    check(lib().position_loss(_dev(x, name="x"), _dev(x_target, name="x_target"), int(n),
+                              float(weight), _dev(loss, name="loss"), _dev(g_x, name="g_x"),
+                              _stream(stream)))
     return loss
 
 

@@ -140,6 +140,15 @@ def fourier_wind(nf, n_frames, mean=(10.0, 0.0, 0.0), amp=2.0, n_modes=8, kmax=3
     return np.ascontiguousarray(vals.astype(np.float32))
 
 
+def wind_node_positions(nf):
+    """Positions [3][nf^3] (float32, x index fastest) of the wind-grid nodes,
+    node (i, j, k) at (i, j, k) / (nf - 1): the node-centred grid spanning the
+    unit cube on which the wind keyframes are stored."""
+    grid = np.linspace(0.0, 1.0, nf) if nf > 1 else np.zeros(1)
+    Z, Y, X = np.meshgrid(grid, grid, grid, indexing="ij")
+    return np.ascontiguousarray(np.stack([X.ravel(), Y.ravel(), Z.ravel()]).astype(np.float32))
+
+
 # ------------------------------------------------------------------- LBM --
 
 def population_noise(shape, amplitude=1e-3, seed=0):
@@ -222,6 +231,25 @@ def sheet_scene(nu=548, nv=365, n_grid=128, n_substeps=1000, dt=5e-5, wind_nf=32
     wind = fourier_wind(wind_nf, wind_frames, seed=wind_seed)
     return Scene(f"sheet{n_grid}", n_grid, dt, 0, E, 0.3, 1000.0, vol / x.shape[1], x, pinned,
                  wind, t_total, n_substeps=n_substeps)
+
+
+def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=100, every=25,
+                   n_cells=32, lbm_steps=30, inlet_error_deg=10.0, seed=0):
+    """Synthetic wind-inversion case: the flag-like sheet (pinned edge, E=5e4)
+    on an n_grid^3 grid at dt=1e-4, n_intervals intervals of `substeps`
+    substeps (checkpoint every `every`), a wind grid of nf^3 nodes, and an
+    n_cells^3 lattice (tau 0.6) with an inlet of speed 0.05 along
+    (1, 0, 0.35) advanced lbm_steps steps per interval. The ground-truth force
+    follows the drag relation with scale 4000 (10 N/kg at the inlet speed);
+    the inversion's guide lattice assumes a wind-source direction off by
+    inlet_error_deg degrees about y."""
+    sc = sheet_scene(nu, nv, n_grid=n_grid, n_substeps=substeps, dt=1e-4, wind_nf=nf,
+                     wind_frames=1, seed=seed)
+    d = np.array([1.0, 0.0, 0.35])
+    u_in = tuple(float(c) for c in 0.05 * d / np.linalg.norm(d))
+    return dict(scene=sc, nf=nf, n_intervals=n_intervals, substeps=substeps, every=every,
+                n_cells=n_cells, tau=0.6, u_inlet=u_in, drag_scale=4000.0, lbm_steps=lbm_steps,
+                inlet_error_deg=inlet_error_deg)
 
 
 def batch_scenes(n_scenes=64, n_lo=20000, n_hi=400000, n_substeps=500, seed=0):

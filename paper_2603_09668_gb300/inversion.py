@@ -1,0 +1,234 @@
+"""The physics-informed wind inversion loop (Sec. 3.3 and 3.4) and the
+LBM-driven forward simulation it is scored against, run on the library's
+kernels; this module only orders the calls and owns the buffers.
+
+Forward simulation (Sec. 3.4, wind field evolution): per frame interval the
+particles are voxelized into the lattice's solid mask (Eq. point2voxel), the
+lattice advances, its velocity is sampled at the wind-grid nodes, the drag
+relation turns it into a wind acceleration (wind_drag_force), and the MPM
+runs the interval's substeps under that force, held constant over the
+interval (one keyframe).
+
+Inversion (Sec. 3.3): the intervals are solved one after another. For each,
+the force keyframe starts at zero and Adam minimises
+
+    w_data * sum_p |x_p(end) - x_p_observed|^2  +  lambda * L_phys,
+
+the first gradient coming from the checkpointed MPM adjoint
+(mpm_segment_adjoint, one call per checkpoint segment) and the second from
+wind_phys_loss against the lattice velocity of that interval (the guide, from
+a lattice whose inlet points along the assumed wind-source direction). The
+optimised force then advances the state, which starts the next interval.
+The observed positions stand in for the rendered views of L_render, which
+needs the Gaussian renderer.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .inputs import rest_state, wind_node_positions
+
+
+class LbmGuide:
+    """A lattice over the unit cube (nx = ny = nz, so one voxel size dx = 1/nx
+    serves Eq. point2voxel and the velocity sampler) with an inlet at x = 0,
+    evolved alongside the object, and its velocity at the nf^3 wind nodes."""
+
+    def __init__(self, n_cells: int, tau: float, u_inlet, nf: int, device="cuda"):
+        self.shape = (n_cells, n_cells, n_cells)
+        self.n_cells = n_cells
+        self.u_inlet = tuple(float(c) for c in u_inlet)
+        self.nf = nf
+        self.lbm = B.LBM(self.shape, tau, u_inlet=self.u_inlet, bc_x=1)
+        self.f = self.lbm.lattice(device)
+        self.lbm.init_equilibrium(self.f, 1.0, self.u_inlet)
+        self.solid = torch.zeros((n_cells, n_cells, n_cells), dtype=torch.uint8, device=device)
+        self.nodes = torch.from_numpy(wind_node_positions(nf)).to(device)
+        self.u = torch.empty((3, nf ** 3), dtype=torch.float32, device=device)
+
+    def advance(self, x: torch.Tensor, steps: int) -> torch.Tensor:
+        """Voxelize the particles x [3][n], run `steps` lattice steps and return
+        the velocity at the wind nodes [3][nf^3] (a view of the guide's buffer,
+        overwritten by the next call)."""
+        B.voxelize_particles(x, self.shape, 1.0 / self.n_cells, self.solid)
+        if steps > 0:
+            self.lbm.step(self.f, self.solid, steps)
+        self.lbm.sample_velocity(self.f, self.solid, self.nodes, self.u)
+        return self.u
+
+    def close(self):
+        self.lbm.close()
+
+
+def _wind(values: torch.Tensor) -> B.WindField:
+    # one keyframe: the force is constant over the interval
+    return B.WindField(values, 1.0)
+
+
+def simulate_wind_driven(mpm: B.MPM, guide: LbmGuide, state: B.MpmState, pinned, n_intervals: int,
+                         substeps: int, lbm_steps: int, drag_scale: float, t0: float = 0.0):
+    """Advance `state` in place through n_intervals intervals of `substeps`
+    substeps, each driven by the drag force of the guide lattice's velocity.
+    Returns (forces [n_intervals][nf^3][3], positions [n_intervals][3][n] at
+    the end of each interval)."""
+    nf = guide.nf
+    forces = torch.empty((n_intervals, nf ** 3, 3), dtype=torch.float32, device=state.x.device)
+    xs = torch.empty((n_intervals,) + tuple(state.x.shape), dtype=torch.float32,
+                     device=state.x.device)
+    t = t0
+    for k in range(n_intervals):
+        u = guide.advance(state.x, lbm_steps)
+        B.wind_drag_force(u, drag_scale, forces[k])
+        mpm.rollout(state, pinned, None, _wind(forces[k].view(1, nf, nf, nf, 3)), t, substeps, 0)
+        xs[k].copy_(state.x)
+        t += substeps * mpm.dt
+    return forces, xs
+
+
+@dataclass
+class InversionResult:
+    values: torch.Tensor   # [n_intervals][nf^3][3] reconstructed force per interval
+    history: torch.Tensor  # [n_intervals][iters][2]: (data term, lambda * L_phys) per iteration
+    x_end: torch.Tensor    # [n_intervals][3][n] positions after each committed interval
+    guides: torch.Tensor   # [n_intervals][3][nf^3] lattice velocity used as the guide
+
+
+class WindInversion:
+    """Sequential per-interval reconstruction of the wind force field.
+
+    iters Adam iterations per interval (learning rate lr), each one forward
+    pass of `substeps` substeps with a checkpoint every `every` substeps and
+    one reverse pass. w_data weights the position term (default 1 / (n h^2)
+    with h the grid spacing: the mean squared position error in grid cells);
+    lam_phys weights L_phys."""
+
+    def __init__(self, mpm: B.MPM, guide: LbmGuide, substeps: int, every: int, iters: int,
+                 lr: float, lam_phys: float, w_data: Optional[float] = None, eps_guide=1e-6):
+        if substeps < 1 or every < 1 or iters < 1:
+            raise ValueError("substeps, every and iters must be >= 1")
+        self.mpm, self.guide = mpm, guide
+        self.substeps, self.every, self.iters = substeps, every, iters
+        self.lr, self.lam_phys, self.w_data, self.eps_guide = lr, lam_phys, w_data, eps_guide
+
+    def reconstruct(self, state0: B.MpmState, pinned, x_observed: torch.Tensor,
+                    lbm_steps: int, t0: float = 0.0) -> InversionResult:
+        """x_observed [n_intervals][3][n]: the positions at the end of each
+        interval. state0 is not modified."""
+        mpm, guide, nf = self.mpm, self.guide, self.guide.nf
+        dev = state0.x.device
+        n, K, S, every = state0.n, x_observed.shape[0], self.substeps, self.every
+        w_data = self.w_data if self.w_data is not None else mpm.n_grid ** 2 / max(n, 1)
+        segs = [(k0, min(S, k0 + every)) for k0 in range(0, S, every)]
+
+        values = torch.zeros((K, nf ** 3, 3), dtype=torch.float32, device=dev)
+        history = torch.zeros((K, self.iters, 2), dtype=torch.float32, device=dev)
+        x_end = torch.empty((K, 3, n), dtype=torch.float32, device=dev)
+        guides = torch.empty((K, 3, nf ** 3), dtype=torch.float32, device=dev)
+        g_values = torch.empty((nf ** 3, 3), dtype=torch.float32, device=dev)
+        m_buf, v_buf = torch.empty_like(g_values), torch.empty_like(g_values)
+        state = state0.clone()
+        run = B.MpmState.empty_like(state0)
+        ckpts = [B.MpmState.empty_like(state0) for _ in segs]
+        g = B.MpmState.empty_like(state0)
+        tape = torch.empty(max(every - 1, 1) * 24 * max(n, 1), dtype=torch.float32, device=dev)
+
+        t = t0
+        for k in range(K):
+            guides[k].copy_(guide.advance(state.x, lbm_steps))
+            val = values[k]
+            wind = _wind(val.view(1, nf, nf, nf, 3))
+            m_buf.zero_()
+            v_buf.zero_()
+            for it in range(self.iters):
+                # forward with a checkpoint at the start of every segment
+                for c, a in zip(run, state):
+                    c.copy_(a)
+                for (k0, k1), ck in zip(segs, ckpts):
+                    for c, a in zip(ck, run):
+                        c.copy_(a)
+                    mpm.rollout(run, pinned, None, wind, t + k0 * mpm.dt, k1 - k0, 0)
+                # losses and the reverse pass
+                for a in g:
+                    a.zero_()
+                g_values.zero_()
+                B.position_loss(run.x, x_observed[k], history[k, it, 0:1], w_data, g.x)
+                for (k0, k1), ck in zip(reversed(segs), reversed(ckpts)):
+                    mpm.segment_adjoint(ck, tape, g, pinned, wind, t + k0 * mpm.dt, k1 - k0,
+                                        g_values.view(1, nf, nf, nf, 3))
+                if self.lam_phys > 0.0:
+                    B.wind_phys_loss(val, guides[k], history[k, it, 1:2], g_values,
+                                     self.eps_guide, self.lam_phys)
+                B.adam_step(val, g_values, m_buf, v_buf, it + 1, self.lr)
+            # commit the interval with the optimised force
+            mpm.rollout(state, pinned, None, wind, t, S, 0)
+            x_end[k].copy_(state.x)
+            t += S * mpm.dt
+        return InversionResult(values, history, x_end, guides)
+
+
+def field_scores(rec: torch.Tensor, gt: torch.Tensor, eps: float = 1e-12):
+    """(CosSim, NMSE) of rec against gt over all intervals and nodes where both
+    forces have a direction (App. E.2), from wind_field_scores."""
+    sums = B.wind_field_scores(rec.contiguous(), gt.contiguous(), eps=eps)
+    s = sums.cpu().numpy().astype(np.float64)
+    if s[2] == 0:
+        return float("nan"), float("nan")
+    return float(s[0] / s[2]), float(s[1] / s[2])
+
+
+def rotate_about_y(vec, degrees):
+    """vec rotated by `degrees` about the y axis (an assumed wind-source
+    direction that is off by that angle)."""
+    a = np.deg2rad(degrees)
+    x, y, z = vec
+    return (float(np.cos(a) * x + np.sin(a) * z), float(y), float(-np.sin(a) * x + np.cos(a) * z))
+
+
+@dataclass
+class SyntheticCase:
+    mpm: B.MPM
+    state0: B.MpmState
+    pinned: Optional[torch.Tensor]
+    gt_forces: torch.Tensor  # [n_intervals][nf^3][3]
+    x_obs: torch.Tensor      # [n_intervals][3][n]
+    guide: LbmGuide          # the inversion's guide lattice (assumed inlet)
+
+    def close(self):
+        self.guide.close()
+        self.mpm.close()
+
+
+def prepare_synthetic(case: dict, device="cuda") -> SyntheticCase:
+    """Ground truth of a synthetic case (inputs.inversion_case): the forward
+    simulation with the true inlet from the sheet at rest, and a fresh guide
+    lattice for the inversion whose inlet is rotated by the case's error."""
+    sc = case["scene"]
+    nf, K, S = case["nf"], case["n_intervals"], case["substeps"]
+    state0 = B.MpmState(*(torch.from_numpy(np.asarray(a, np.float32)).to(device)
+                          for a in rest_state(sc.x)))
+    pinned = torch.from_numpy(sc.pinned).to(device) if sc.pinned is not None else None
+    mpm = B.MPM.from_params(sc.params(), max_particles=sc.n)
+    gt_guide = LbmGuide(case["n_cells"], case["tau"], case["u_inlet"], nf, device)
+    gt_forces, x_obs = simulate_wind_driven(mpm, gt_guide, state0.clone(), pinned, K, S,
+                                            case["lbm_steps"], case["drag_scale"])
+    gt_guide.close()
+    guide = LbmGuide(case["n_cells"], case["tau"],
+                     rotate_about_y(case["u_inlet"], case["inlet_error_deg"]), nf, device)
+    return SyntheticCase(mpm, state0, pinned, gt_forces, x_obs, guide)
+
+
+def run_synthetic(case: dict, iters: int, lr: float, lam_phys: float, device="cuda"):
+    """prepare_synthetic, then the inversion from the same initial state.
+    Returns a dict with the ground truth, the InversionResult and the scores."""
+    syn = prepare_synthetic(case, device)
+    inv = WindInversion(syn.mpm, syn.guide, case["substeps"], case["every"], iters, lr, lam_phys)
+    res = inv.reconstruct(syn.state0, syn.pinned, syn.x_obs, case["lbm_steps"])
+    cos, nmse = field_scores(res.values, syn.gt_forces)
+    out = dict(gt_forces=syn.gt_forces, x_obs=syn.x_obs, result=res, cos_sim=cos, nmse=nmse)
+    syn.close()
+    return out

@@ -4,7 +4,9 @@ the flow costs nothing, a force across it costs |F|^2), its invariance under
 rotations, its gradient by central differences; the guide velocity sampler
 against lattices whose velocity field is known in closed form (uniform and
 linear fields are reproduced exactly by trilinear interpolation, solid cells
-are at rest); Adam against torch.optim.Adam (an independent implementation)."""
+are at rest); the drag relation by its closed form along an axis, its degree-2
+homogeneity and its direction; the trajectory term's gradient by central
+differences; Adam against torch.optim.Adam (an independent implementation)."""
 import numpy as np
 import pytest
 import torch
@@ -142,3 +144,36 @@ def test_scores():
     z = x.copy()
     z[3] = 0.0
     assert phys.cos_sim(z, y) == pytest.approx(phys.cos_sim(np.delete(x, 3, 0), np.delete(y, 3, 0)))
+
+
+def test_drag_force_closed_form_and_homogeneity():
+    # along +x: F = scale u^2, no other component; the sign follows u
+    F = phys.drag_force(np.array([[0.05, -0.05], [0.0, 0.0], [0.0, 0.0]]), 4000.0)
+    assert np.allclose(F, [[10.0, 0.0, 0.0], [-10.0, 0.0, 0.0]], atol=1e-12)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((3, 25))
+    F = phys.drag_force(u, 2.0)
+    # |F| = scale |u|^2, parallel to u, degree 2 in u
+    assert np.allclose(np.linalg.norm(F, axis=1), 2.0 * np.sum(u * u, axis=0), rtol=1e-12)
+    assert np.allclose(np.cross(F, u.T), 0.0, atol=1e-12)
+    assert np.all(np.sum(F * u.T, axis=1) >= 0)
+    assert np.allclose(phys.drag_force(3.0 * u, 2.0), 9.0 * F, rtol=1e-12)
+    assert not phys.drag_force(np.zeros((3, 4)), 2.0).any()
+
+
+def test_position_loss_closed_form_and_gradient():
+    x = np.array([[0.5, 0.2], [0.1, 0.3], [0.0, 0.4]])
+    t = np.array([[0.5, 0.0], [0.4, 0.3], [0.0, 0.0]])
+    loss, g = phys.position_loss(x, t, weight=2.0)
+    assert loss == pytest.approx(2.0 * (0.09 + 0.04 + 0.16))
+    rng = np.random.default_rng(8)
+    x, t = rng.random((3, 6)), rng.random((3, 6))
+    _, g = phys.position_loss(x, t, weight=0.7)
+    eps = 1e-6
+    for c in range(3):
+        for p in range(6):
+            xp, xm = x.copy(), x.copy()
+            xp[c, p] += eps
+            xm[c, p] -= eps
+            fd = (phys.position_loss(xp, t, 0.7)[0] - phys.position_loss(xm, t, 0.7)[0]) / (2 * eps)
+            assert g[c, p] == pytest.approx(fd, rel=1e-6)
