@@ -289,6 +289,17 @@ DW_API dw_status adam_step(float *param, const float *grad, float *m, float *v, 
                            float lr, float beta1, float beta2, float eps, int32_t step,
                            dw_stream stream);
 
+/* VectorAdam (Ling, Sharp and Jacobson, 2022) on n 3-vectors param [n][3]:
+ * m [n][3] is the first moment per component, v [n] the second moment of the
+ * squared norm |g|^2 of each vector's gradient (both zero before step 1);
+ * param -= lr * m^ / (sqrt(v^) + eps) with Adam's bias corrections. Unlike
+ * adam_step the update of a vector is a rotation of its gradient's history,
+ * so a rotated problem gives the rotated answer: the wind inversion uses it
+ * for the per-node force vectors. step >= 1. */
+DW_API dw_status vector_adam_step(float *param, const float *grad, float *m, float *v, int64_t n,
+                                  float lr, float beta1, float beta2, float eps, int32_t step,
+                                  dw_stream stream);
+
 /* ============================================================ batched MPM
  * Many independent scenes, each with its own grid size, material, time step,
  * particle count and wind field, advanced by the same substep as mpm_rollout

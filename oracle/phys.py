@@ -23,6 +23,8 @@ What it computes, in numpy float64:
   - position_loss: the trajectory term weight * sum_p |x_p - x_p*|^2 and its
     gradient 2 weight (x - x*).
   - adam_step: Adam (Kingma and Ba, 2015) with bias correction.
+  - vector_adam_step: VectorAdam (Ling, Sharp and Jacobson, 2022): Adam whose
+    second moment is taken on the squared norm of each 3-vector's gradient.
   - cos_sim, nmse: the scores of the wind-force-field evaluation (App. E.2,
     the CosSim / NMSE table): both on force vectors normalised to unit length.
 """
@@ -95,6 +97,17 @@ def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1.0 - beta1 ** step)
     vh = v / (1.0 - beta2 ** step)
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def vector_adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One VectorAdam update of param [n][3] (m [n][3], v [n]); returns
+    (param, m, v)."""
+    grad = np.asarray(grad, np.float64).reshape(-1, 3)
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * np.sum(grad * grad, axis=1)
+    mh = m / (1.0 - beta1 ** step)
+    vh = v / (1.0 - beta2 ** step)
+    return param - lr * mh / (np.sqrt(vh)[:, None] + eps), m, v
 
 
 def _unit_pairs(rec, gt, eps):

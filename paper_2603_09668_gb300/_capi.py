@@ -102,6 +102,7 @@ SIGNATURES = {
     "wind_field_scores": (I32, [VP, VP, I64, F32, VP, VP]),
     "adam_step": (I32, [VP, VP, VP, VP, I64, F32, F32, F32, F32, I32, VP]),
     "wind_drag_force": (I32, [VP, I64, F32, VP, VP]),
+    "vector_adam_step": (I32, [VP, VP, VP, VP, I64, F32, F32, F32, F32, I32, VP]),
     "position_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
     "surr_create": (I32, [I32, P(VP)]),
     "surr_destroy": (I32, [VP]),

@@ -23,7 +23,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
-           "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "MPM", "LBM", "surr_create",
+           "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "vector_adam_step", "MPM", "LBM", "surr_create",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
@@ -432,6 +432,18 @@ def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, str
     check(lib().adam_step(_dev(param, name="param"), _dev(grad, name="grad"), _dev(m, name="m"),
                           _dev(v, name="v"), int(param.numel()), float(lr), float(beta1),
                           float(beta2), float(eps), int(step), _stream(stream)))
+    return param
+
+
+def vector_adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """VectorAdam on param [n][3] (m [n][3], v [n])."""
+    n = param.numel() // 3
+    if m.numel() != 3 * n or v.numel() != n or grad.numel() != 3 * n:
+        raise ValueError("vector_adam_step: param, grad, m must be [n][3] and v [n]")
+    check(lib().vector_adam_step(_dev(param, name="param"), _dev(grad, name="grad"),
+                                 _dev(m, name="m"), _dev(v, name="v"), int(n), float(lr),
+                                 float(beta1), float(beta2), float(eps), int(step),
+                                 _stream(stream)))
     return param
 
 

@@ -123,6 +123,28 @@ __global__ void k_adam_step(float *__restrict__ param, const float *__restrict__
     param[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
+// VectorAdam (Ling, Sharp and Jacobson, 2022): one thread per 3-vector; the
+// first moment per component, the second moment on the squared norm of the
+// vector's gradient, so the step keeps the gradient's direction per node.
+__global__ void k_vector_adam_step(float *__restrict__ param, const float *__restrict__ grad,
+                                   float *__restrict__ m, float *__restrict__ v, int64_t n,
+                                   float lr, float beta1, float beta2, float eps, float bc1,
+                                   float bc2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g0 = grad[3 * i], g1 = grad[3 * i + 1], g2 = grad[3 * i + 2];
+    const float vi = beta2 * v[i] + (1.0f - beta2) * (g0 * g0 + g1 * g1 + g2 * g2);
+    v[i] = vi;
+    const float step = lr / (bc1 * (sqrtf(vi / bc2) + eps));
+    const float gs[3] = {g0, g1, g2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float mi = beta1 * m[3 * i + c] + (1.0f - beta1) * gs[c];
+        m[3 * i + c] = mi;
+        param[3 * i + c] -= step * mi;
+    }
+}
+
 }  // namespace dw
 
 using namespace dw;
@@ -187,5 +209,23 @@ extern "C" dw_status adam_step(float *param, const float *grad, float *m, float 
     k_adam_step<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(param, grad, m, v, n, lr, beta1,
                                                                   beta2, eps, bc1, bc2);
     DW_LAUNCHED("k_adam_step");
+    return DW_OK;
+}
+
+extern "C" dw_status vector_adam_step(float *param, const float *grad, float *m, float *v,
+                                      int64_t n, float lr, float beta1, float beta2, float eps,
+                                      int32_t step, dw_stream stream) {
+    DW_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return DW_OK;
+    DW_REQUIRE(param && grad && m && v, "param, grad, m and v must not be NULL");
+    DW_REQUIRE(step >= 1, "step must be >= 1");
+    DW_REQUIRE(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f,
+               "betas must be in [0, 1)");
+    const float bc1 = 1.0f - (float)pow((double)beta1, (double)step);
+    const float bc2 = 1.0f - (float)pow((double)beta2, (double)step);
+    k_vector_adam_step<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(param, grad, m, v, n, lr,
+                                                                         beta1, beta2, eps, bc1,
+                                                                         bc2);
+    DW_LAUNCHED("k_vector_adam_step");
     return DW_OK;
 }

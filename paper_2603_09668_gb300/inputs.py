@@ -233,17 +233,17 @@ def sheet_scene(nu=548, nv=365, n_grid=128, n_substeps=1000, dt=5e-5, wind_nf=32
                  wind, t_total, n_substeps=n_substeps)
 
 
-def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=100, every=25,
-                   n_cells=32, lbm_steps=30, inlet_error_deg=10.0, seed=0):
+def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, dt=2e-4,
+                   every=25, n_cells=32, lbm_steps=30, inlet_error_deg=10.0, seed=0):
     """Synthetic wind-inversion case: the flag-like sheet (pinned edge, E=5e4)
-    on an n_grid^3 grid at dt=1e-4, n_intervals intervals of `substeps`
-    substeps (checkpoint every `every`), a wind grid of nf^3 nodes, and an
-    n_cells^3 lattice (tau 0.6) with an inlet of speed 0.05 along
-    (1, 0, 0.35) advanced lbm_steps steps per interval. The ground-truth force
-    follows the drag relation with scale 4000 (10 N/kg at the inlet speed);
-    the inversion's guide lattice assumes a wind-source direction off by
-    inlet_error_deg degrees about y."""
-    sc = sheet_scene(nu, nv, n_grid=n_grid, n_substeps=substeps, dt=1e-4, wind_nf=nf,
+    on an n_grid^3 grid, n_intervals intervals of `substeps` substeps of dt
+    (0.04 s, a video frame interval; checkpoint every `every`), a wind grid of
+    nf^3 nodes, and an n_cells^3 lattice (tau 0.6) with an inlet of speed 0.05
+    along (1, 0, 0.35) advanced lbm_steps steps per interval. The ground-truth
+    force follows the drag relation with scale 4000 (10 N/kg at the inlet
+    speed); the inversion's guide lattice assumes a wind-source direction off
+    by inlet_error_deg degrees about y."""
+    sc = sheet_scene(nu, nv, n_grid=n_grid, n_substeps=substeps, dt=dt, wind_nf=nf,
                      wind_frames=1, seed=seed)
     d = np.array([1.0, 0.0, 0.35])
     u_in = tuple(float(c) for c in 0.05 * d / np.linalg.norm(d))

@@ -19,6 +19,10 @@ the first gradient coming from the checkpointed MPM adjoint
 wind_phys_loss against the lattice velocity of that interval (the guide, from
 a lattice whose inlet points along the assumed wind-source direction). The
 optimised force then advances the state, which starts the next interval.
+The update is VectorAdam by default: per-component Adam moves every
+component of every node by about the learning rate whatever its gradient's
+size, which scrambles the per-node directions the evaluation scores; plain
+Adam stays available (optimizer="adam").
 The observed positions stand in for the rendered views of L_render, which
 needs the Gaussian renderer.
 """
@@ -105,12 +109,16 @@ class WindInversion:
     pass of `substeps` substeps with a checkpoint every `every` substeps and
     one reverse pass. w_data weights the position term (default 1 / (n h^2)
     with h the grid spacing: the mean squared position error in grid cells);
-    lam_phys weights L_phys."""
+    lam_phys weights L_phys; optimizer is "vector_adam" or "adam"."""
 
     def __init__(self, mpm: B.MPM, guide: LbmGuide, substeps: int, every: int, iters: int,
-                 lr: float, lam_phys: float, w_data: Optional[float] = None, eps_guide=1e-6):
+                 lr: float, lam_phys: float, w_data: Optional[float] = None, eps_guide=1e-6,
+                 optimizer: str = "vector_adam"):
         if substeps < 1 or every < 1 or iters < 1:
             raise ValueError("substeps, every and iters must be >= 1")
+        if optimizer not in ("vector_adam", "adam"):
+            raise ValueError(f"unknown optimizer {optimizer!r}")
+        self.optimizer = optimizer
         self.mpm, self.guide = mpm, guide
         self.substeps, self.every, self.iters = substeps, every, iters
         self.lr, self.lam_phys, self.w_data, self.eps_guide = lr, lam_phys, w_data, eps_guide
@@ -130,7 +138,9 @@ class WindInversion:
         x_end = torch.empty((K, 3, n), dtype=torch.float32, device=dev)
         guides = torch.empty((K, 3, nf ** 3), dtype=torch.float32, device=dev)
         g_values = torch.empty((nf ** 3, 3), dtype=torch.float32, device=dev)
-        m_buf, v_buf = torch.empty_like(g_values), torch.empty_like(g_values)
+        m_buf = torch.empty_like(g_values)
+        vec = self.optimizer == "vector_adam"
+        v_buf = torch.empty(nf ** 3 if vec else (nf ** 3, 3), dtype=torch.float32, device=dev)
         state = state0.clone()
         run = B.MpmState.empty_like(state0)
         ckpts = [B.MpmState.empty_like(state0) for _ in segs]
@@ -163,7 +173,10 @@ class WindInversion:
                 if self.lam_phys > 0.0:
                     B.wind_phys_loss(val, guides[k], history[k, it, 1:2], g_values,
                                      self.eps_guide, self.lam_phys)
-                B.adam_step(val, g_values, m_buf, v_buf, it + 1, self.lr)
+                if vec:
+                    B.vector_adam_step(val, g_values, m_buf, v_buf, it + 1, self.lr)
+                else:
+                    B.adam_step(val, g_values, m_buf, v_buf, it + 1, self.lr)
             # commit the interval with the optimised force
             mpm.rollout(state, pinned, None, wind, t, S, 0)
             x_end[k].copy_(state.x)
@@ -222,11 +235,13 @@ def prepare_synthetic(case: dict, device="cuda") -> SyntheticCase:
     return SyntheticCase(mpm, state0, pinned, gt_forces, x_obs, guide)
 
 
-def run_synthetic(case: dict, iters: int, lr: float, lam_phys: float, device="cuda"):
+def run_synthetic(case: dict, iters: int, lr: float, lam_phys: float, device="cuda",
+                  optimizer="vector_adam"):
     """prepare_synthetic, then the inversion from the same initial state.
     Returns a dict with the ground truth, the InversionResult and the scores."""
     syn = prepare_synthetic(case, device)
-    inv = WindInversion(syn.mpm, syn.guide, case["substeps"], case["every"], iters, lr, lam_phys)
+    inv = WindInversion(syn.mpm, syn.guide, case["substeps"], case["every"], iters, lr, lam_phys,
+                        optimizer=optimizer)
     res = inv.reconstruct(syn.state0, syn.pinned, syn.x_obs, case["lbm_steps"])
     cos, nmse = field_scores(res.values, syn.gt_forces)
     out = dict(gt_forces=syn.gt_forces, x_obs=syn.x_obs, result=res, cos_sim=cos, nmse=nmse)

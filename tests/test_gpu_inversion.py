@@ -107,6 +107,20 @@ def test_adam_step_matches_oracle():
     assert max_rel(tp.cpu().numpy() - p0, p - p0) <= 1e-5
 
 
+def test_vector_adam_step_matches_oracle():
+    rng = np.random.default_rng(18)
+    n = 700
+    p0 = rng.standard_normal((n, 3)).astype(np.float32)
+    p, m, v = p0.astype(np.float64), np.zeros((n, 3)), np.zeros(n)
+    tp = to_dev(p0)
+    tm, tv = torch.zeros((n, 3), device="cuda"), torch.zeros(n, device="cuda")
+    for k in range(1, 6):
+        gr = rng.standard_normal((n, 3)).astype(np.float32)
+        p, m, v = phys.vector_adam_step(p, gr, m, v, k, 0.01)
+        B.vector_adam_step(tp, to_dev(gr), tm, tv, k, 0.01)
+    assert max_rel(tp.cpu().numpy() - p0, p - p0) <= 1e-5
+
+
 def test_empty_inputs_and_argument_errors():
     loss = torch.zeros(1, device="cuda")
     B.wind_phys_loss(torch.zeros((0, 3), device="cuda"), torch.zeros((3, 0), device="cuda"), loss)

@@ -6,7 +6,9 @@ against lattices whose velocity field is known in closed form (uniform and
 linear fields are reproduced exactly by trilinear interpolation, solid cells
 are at rest); the drag relation by its closed form along an axis, its degree-2
 homogeneity and its direction; the trajectory term's gradient by central
-differences; Adam against torch.optim.Adam (an independent implementation)."""
+differences; Adam against torch.optim.Adam (an independent implementation);
+VectorAdam against torch's Adam where each vector's gradient stays on one
+axis (the two then agree) and by its rotation equivariance."""
 import numpy as np
 import pytest
 import torch
@@ -177,3 +179,39 @@ def test_position_loss_closed_form_and_gradient():
             xm[c, p] -= eps
             fd = (phys.position_loss(xp, t, 0.7)[0] - phys.position_loss(xm, t, 0.7)[0]) / (2 * eps)
             assert g[c, p] == pytest.approx(fd, rel=1e-6)
+
+
+def test_vector_adam_reduces_to_adam_on_axis_aligned_gradients():
+    rng = np.random.default_rng(9)
+    n = 10
+    axis = rng.integers(0, 3, n)
+    p0 = rng.standard_normal((n, 3))
+    p, m, v = p0.copy(), np.zeros((n, 3)), np.zeros(n)
+    t = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=0.03)
+    for k in range(1, 7):
+        g = np.zeros((n, 3))
+        g[np.arange(n), axis] = rng.standard_normal(n)
+        p, m, v = phys.vector_adam_step(p, g, m, v, k, 0.03)
+        opt.zero_grad()
+        t.grad = torch.tensor(g)
+        opt.step()
+    # components that never saw a gradient stay put in both
+    assert np.allclose(p, t.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_vector_adam_is_rotation_equivariant():
+    rng = np.random.default_rng(10)
+    n = 8
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    p, m, v = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    pr, mr, vr = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    for k in range(1, 6):
+        g = rng.standard_normal((n, 3))
+        p, m, v = phys.vector_adam_step(p, g, m, v, k, 0.1)
+        pr, mr, vr = phys.vector_adam_step(pr, g @ q.T, mr, vr, k, 0.1)
+    assert np.allclose(pr, p @ q.T, atol=1e-12)
+    # the first step moves each vector by lr along -g/|g| (up to eps)
+    g = rng.standard_normal((n, 3))
+    p1, _, _ = phys.vector_adam_step(np.zeros((n, 3)), g, np.zeros((n, 3)), np.zeros(n), 1, 0.1)
+    assert np.allclose(p1, -0.1 * g / np.linalg.norm(g, axis=1)[:, None], atol=1e-9)
