@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch",
-                                                    "batch_adjoint"],
+                                                    "batch_adjoint", "inversion"],
                     help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
                          "or the checkpointed MPM adjoint")
     ap.add_argument("--batch-scenes", type=int, default=64,
@@ -613,12 +613,54 @@ def bench_batch_adjoint(dev, n_scenes=64, n_sub=500, ckpt=25, trial=10):
             "batch_adj_config": cfg}
 
 
+def bench_inversion(dev, iters=40):
+    """The physics-informed wind inversion (Sec. 3.3, 3.4) on the synthetic
+    flag case (5,504 particles on 64^3, 12^3 wind grid, 32^3 guide lattice,
+    3 intervals of 200 substeps at dt 2e-4, checkpoint every 25): one Adam
+    iteration = 200 substeps forward + checkpointed adjoint + L_phys +
+    VectorAdam. Scores against the ground-truth drag field (App. E.2) with and
+    without L_phys."""
+    import torch
+
+    from paper_2603_09668_gb300 import inputs
+    from paper_2603_09668_gb300 import inversion as I
+
+    case = inputs.inversion_case()
+    out = {}
+    for lam, tag in ((0.1, ""), (0.0, "_no_phys")):
+        syn = I.prepare_synthetic(case, dev)
+        inv = I.WindInversion(syn.mpm, syn.guide, case["substeps"], case["every"], iters, 1.0, lam)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = inv.reconstruct(syn.state0, syn.pinned, syn.x_obs, case["lbm_steps"])
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        cos, nmse = I.field_scores(res.values, syn.gt_forces)
+        syn.close()
+        out[f"inversion_cos_sim{tag}"] = cos
+        out[f"inversion_nmse{tag}"] = nmse
+        if not tag:
+            n_it = case["n_intervals"] * iters
+            out["inversion_iter_ms"] = ms / n_it
+            out["inversion_ps_per_s"] = case["scene"].n * case["substeps"] * n_it / (ms * 1e-3)
+            out["inversion_total_ms"] = ms
+    out["inversion_note"] = (f"{case['scene'].n} particles, 64^3 grid, 12^3 wind grid, "
+                             f"{case['n_intervals']} intervals x {iters} iterations x "
+                             f"{case['substeps']} substeps (forward + adjoint), guide inlet "
+                             f"{case['inlet_error_deg']} deg off; lambda_phys 0.1")
+    return out
+
+
 def extras(dev):
     out = bench_lbm(dev)
     out.update(bench_adjoint(dev))
     out.update(bench_surrogate(dev))
     out.update(bench_batch(dev))
     out.update(bench_batch_adjoint(dev))
+    out.update(bench_inversion(dev))
     return out
 
 
@@ -694,6 +736,8 @@ def run_only(args):
         res = bench_batch(dev, n_scenes=args.batch_scenes)
     elif args.only == "batch_adjoint":
         res = bench_batch_adjoint(dev, n_scenes=args.batch_scenes)
+    elif args.only == "inversion":
+        res = bench_inversion(dev)
     else:
         res = bench_adjoint(dev)
     print(json.dumps({"only": args.only, **res}), flush=True)
@@ -703,7 +747,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.only in ("lbm", "adjoint", "surrogate", "batch", "batch_adjoint"):
+    elif a.only in ("lbm", "adjoint", "surrogate", "batch", "batch_adjoint", "inversion"):
         run_only(a)
     else:
         run_ours(a)

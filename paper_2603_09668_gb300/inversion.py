@@ -235,8 +235,8 @@ def prepare_synthetic(case: dict, device="cuda") -> SyntheticCase:
     return SyntheticCase(mpm, state0, pinned, gt_forces, x_obs, guide)
 
 
-def run_synthetic(case: dict, iters: int, lr: float, lam_phys: float, device="cuda",
-                  optimizer="vector_adam"):
+def run_synthetic(case: dict, iters: int = 40, lr: float = 1.0, lam_phys: float = 0.1,
+                  device="cuda", optimizer="vector_adam"):
     """prepare_synthetic, then the inversion from the same initial state.
     Returns a dict with the ground truth, the InversionResult and the scores."""
     syn = prepare_synthetic(case, device)

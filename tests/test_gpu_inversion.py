@@ -132,15 +132,36 @@ def test_empty_inputs_and_argument_errors():
 
 
 def test_inversion_loop_recovers_the_wind_direction():
-    """The sequential per-interval inversion on the synthetic flag case: the
-    position term falls well below its value at the zero start in every
-    interval, the committed states track the observed ones, and the
-    reconstructed force points along the ground truth (App. E.2 scores)."""
+    """The sequential per-interval inversion on the synthetic flag case (drag
+    force of a lattice flow past the sheet; the guide lattice's inlet 10
+    degrees off): without L_phys the position term falls below 5% of its
+    zero-start value in every interval and the committed states track the
+    observed ones; L_phys (lambda 0.1) then turns the reconstructed forces
+    towards the ground truth: CosSim up by more than 0.03 and above 0.85
+    (measured on a GB300: 0.84 without, 0.92 with), NMSE = 2 - 2 CosSim."""
     from paper_2603_09668_gb300 import inversion as I
 
-    out = I.run_synthetic(inputs.inversion_case(), iters=30, lr=0.5, lam_phys=1e-4)
-    h = out["result"].history.cpu().numpy()
-    assert np.all(h[:, -1, 0] < 0.2 * h[:, 0, 0]), h[:, [0, -1], 0]
-    assert torch.isfinite(out["result"].values).all()
-    assert out["cos_sim"] > 0.5 and out["nmse"] < 1.0, (out["cos_sim"], out["nmse"])
-    assert abs(out["nmse"] - (2 - 2 * out["cos_sim"])) < 1e-4
+    case = inputs.inversion_case()
+    free = I.run_synthetic(case, iters=40, lr=1.0, lam_phys=0.0)
+    h = free["result"].history.cpu().numpy()
+    assert np.all(h[:, -1, 0] < 0.05 * h[:, 0, 0]), h[:, [0, -1], 0]
+    assert not h[:, :, 1].any()  # no L_phys term
+    cell = 1.0 / case["scene"].n_grid
+    assert (free["result"].x_end - free["x_obs"]).abs().max().item() < 0.05 * cell
+
+    guided = I.run_synthetic(case, iters=40, lr=1.0, lam_phys=0.1)
+    assert torch.isfinite(guided["result"].values).all()
+    assert (guided["result"].x_end - guided["x_obs"]).abs().max().item() < 0.5 * cell
+    assert guided["cos_sim"] > 0.85, guided["cos_sim"]
+    assert guided["cos_sim"] > free["cos_sim"] + 0.03, (free["cos_sim"], guided["cos_sim"])
+    for out in (free, guided):
+        assert abs(out["nmse"] - (2 - 2 * out["cos_sim"])) < 1e-4
+
+
+def test_inversion_argument_checks():
+    from paper_2603_09668_gb300 import inversion as I
+
+    with pytest.raises(ValueError):
+        I.WindInversion(None, None, 0, 25, 10, 1.0, 0.1)
+    with pytest.raises(ValueError):
+        I.WindInversion(None, None, 100, 25, 10, 1.0, 0.1, optimizer="sgd")
