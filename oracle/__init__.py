@@ -1,6 +1,6 @@
 """FP64 CPU oracle for the DiffWind hot path (MLS-MPM substep, wind-force
-sample, D3Q19 BGK LBM step, obstacle voxelization, the learned LBM surrogate)
-and their adjoints.
+sample, D3Q19 BGK LBM step, the moment-encoded HOME-LBM step, obstacle
+voxelization, the learned LBM surrogate) and their adjoints.
 
 TEST INFRASTRUCTURE ONLY. The oracle is the plain, slow, obviously correct
 restatement of the method that the CUDA path is checked against. Only
@@ -9,7 +9,7 @@ restatement of the method that the CUDA path is checked against. Only
 imports the product package.
 
 The arithmetic lives in plain C (``mpm_oracle.c``, ``lbm_oracle.c``,
-``surrogate_oracle.c``), compiled
+``home_oracle.c``, ``surrogate_oracle.c``), compiled
 with gcc into ``_build/liboracle.so``; this module only builds, loads and
 marshals numpy float64 arrays. Every function takes and returns
 structure-of-arrays data in the layouts the C files document.
@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SOURCES = [os.path.join(_HERE, "mpm_oracle.c"), os.path.join(_HERE, "lbm_oracle.c"),
-            os.path.join(_HERE, "surrogate_oracle.c")]
+            os.path.join(_HERE, "home_oracle.c"), os.path.join(_HERE, "surrogate_oracle.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -101,6 +101,11 @@ def _declare(lib):
         "orc_lbm_step_adjoint": (i, [i, i, i, d, _dp, _dp, i, _u8p, _dp, _dp, i]),
         "orc_lbm_macroscopic": (None, [i, i, i, _dp, _u8p, _dp, _dp, _dp]),
         "orc_voxelize": (None, [_dp, i64, i, i, i, d, _u8p]),
+        "orc_home_reconstruct": (None, [_dp, _dp]),
+        "orc_home_collide": (None, [_dp, d, _dp, _dp]),
+        "orc_home_init": (None, [i64, d, _dp, d, _dp, _dp]),
+        "orc_home_step": (i, [i, i, i, d, _dp, _dp, i, _u8p, _dp, i]),
+        "orc_home_macroscopic": (None, [i64, _dp, _u8p, _dp, _dp, _dp]),
         "orc_surr_num_params": (i64, []),
         "orc_surr_forward": (None, [i, _dp, _dp, _dp, _dp, _dp]),
         "orc_surr_backward": (None, [i, _dp, _dp, _dp, _dp]),
@@ -361,6 +366,64 @@ def lbm_macroscopic(shape, f, force=(0.0, 0.0, 0.0), solid=None):
     u = np.zeros((3, nc))
     m = _mask(solid, nc)
     _load().orc_lbm_macroscopic(nx, ny, nz, _ptr(force), _u8ptr(m), _ptr(f), _ptr(rho), _ptr(u))
+    return rho, u
+
+
+# ---------------------------------------------------------------- HOME-LBM --
+
+def home_reconstruct(m):
+    """The 19 populations of one cell's moments m[10] (rho, u, Sxx, Syy, Szz,
+    Sxy, Sxz, Syz)."""
+    m = _f64(m, (10,))
+    f = np.zeros(19)
+    _load().orc_home_reconstruct(_ptr(m), _ptr(f))
+    return f
+
+
+def home_collide(f, tau, force=(0.0, 0.0, 0.0)):
+    """The stored moments m[10] after the moment-space collision of one
+    cell's pre-collision populations f[19]."""
+    f = _f64(f, (19,))
+    force = _f64(force, (3,))
+    m = np.zeros(10)
+    _load().orc_home_collide(_ptr(f), float(tau), _ptr(force), _ptr(m))
+    return m
+
+
+def home_init(shape, rho0, u0, tau, force=(0.0, 0.0, 0.0)):
+    """m[10][nz*ny*nx]: every cell the collided equilibrium f_eq(rho0, u0)."""
+    nx, ny, nz = shape
+    nc = nx * ny * nz
+    u0 = _f64(u0, (3,))
+    force = _f64(force, (3,))
+    m = np.zeros((10, nc))
+    _load().orc_home_init(nc, float(rho0), _ptr(u0), float(tau), _ptr(force), _ptr(m))
+    return m
+
+
+def home_step(shape, tau, m, steps, u_in=(0.0, 0.0, 0.0), force=(0.0, 0.0, 0.0), bc_x=0,
+              solid=None):
+    """Advance moments m[10][nz*ny*nx] by `steps` HOME-LBM steps."""
+    nx, ny, nz = shape
+    m = _f64(m).copy()
+    u_in = _f64(u_in, (3,))
+    force = _f64(force, (3,))
+    mask = _mask(solid, nx * ny * nz)
+    st = _load().orc_home_step(nx, ny, nz, float(tau), _ptr(u_in), _ptr(force), bc_x,
+                               _u8ptr(mask), _ptr(m), steps)
+    _check(st, "home step")
+    return m
+
+
+def home_macroscopic(shape, m, force=(0.0, 0.0, 0.0), solid=None):
+    nx, ny, nz = shape
+    nc = nx * ny * nz
+    m = _f64(m)
+    force = _f64(force, (3,))
+    rho = np.zeros(nc)
+    u = np.zeros((3, nc))
+    mask = _mask(solid, nc)
+    _load().orc_home_macroscopic(nc, _ptr(force), _u8ptr(mask), _ptr(m), _ptr(rho), _ptr(u))
     return rho, u
 
 
