@@ -380,7 +380,9 @@ def _timed(fn, reps=3):
 def bench_lbm(dev, steps=200, adj_steps=20):
     """D3Q19 step and adjoint on 128^3 with the leaf-cluster obstacle (200k
     particles in 50 ellipsoids, voxelized by Eq. point2voxel), tau = 0.55,
-    inlet 0.05. Algorithmic bytes: 152 B per cell-step forward."""
+    inlet 0.05, and the HOME-LBM step on the same lattice. Algorithmic bytes:
+    152 B per cell-step forward (BGK, 19 populations in and out), 80 B
+    (HOME, 10 moments in and out)."""
     import torch
 
     from paper_2603_09668_gb300 import binding as B
@@ -401,6 +403,13 @@ def bench_lbm(dev, steps=200, adj_steps=20):
         g = torch.randn_like(f)
         ms = _timed(lambda: lbm.step_adjoint(f, g, solid, adj_steps))
         out["lbm_128_adj_mlups"] = cells * adj_steps / (ms * 1e-3) / 1e6
+    # HOME-LBM on the same lattice: ten moments per cell, 40 B read + 40 B written
+    m = lbm.moments(dev)
+    lbm.home_init(m, 1.0, (0.05, 0.0, 0.0))
+    home_steps = steps + (steps & 1)  # even: no copy back
+    ms = _timed(lambda: lbm.home_step(m, solid, home_steps))
+    out["lbm_128_home_mlups"] = cells * home_steps / (ms * 1e-3) / 1e6
+    out["lbm_128_home_gbs"] = 80 * cells * home_steps / (ms * 1e-3) / 1e9
     lbm.close()
     return out
 

@@ -503,6 +503,42 @@ DW_API dw_status lbm_sample_velocity(dw_lbm h, const float *f, const uint8_t *so
 DW_API dw_status lbm_init_equilibrium(dw_lbm h, float *f, float rho0, const float u0[3],
                                dw_stream stream);
 
+/* ====================================================== HOME-LBM (App. D)
+ * The moment-encoded variant of the step above (after Li et al. 2023): a
+ * cell stores ten moments of its post-collision populations, m = device float
+ * [10][nz][ny][nx] with planes 0: rho - 1, 1-3: u' (momentum over rho after
+ * the collision), 4-9: S_xx, S_yy, S_zz, S_xy, S_xz, S_yz with S = sum_i (c_i
+ * c_i - I/3) f_i / rho; 40 bytes per cell instead of 76. A step rebuilds
+ * every pulled population f_i(x) = f_i^post(x - c_i) from the source cell's
+ * moments by the Hermite series (second order in full, plus the six
+ * third-order terms H3_aab(c) = c_b (c_a^2 - 1/3) that D3Q19 carries, with
+ * the coefficient A_aab = u_b S_aa + 2 u_a S_ab - 2 u_a^2 u_b closed from
+ * the lower moments), with the boundaries of lbm_step (halfway bounce-back,
+ * the inlet rebuilt from rho = 1, u_inlet, S = u_inlet u_inlet, the
+ * zero-gradient outlet), then collides in moment space: with u = (j + F/2) /
+ * rho and N = Pi - rho (I/3 + u u), the deviatoric part of N decays by
+ * (1 - 1/tau), its trace is dropped (set to equilibrium), and the Guo forcing
+ * moment u F + F u enters with 1 - 1/(2 tau) (deviatoric) and 1/2 (trace);
+ * u' = u + F / (2 rho). It solves the same Navier-Stokes limit as lbm_step
+ * with the same shear viscosity (tau - 1/2) / 3. The handle's descriptor
+ * (tau, inlet, force, bc_x) applies; solid cells keep their moments. */
+
+/* Fill m with the collided equilibrium of rho0, u0 (the HOME counterpart of
+ * lbm_init_equilibrium: the state f_eq(rho0, u0) taken as pre-collision). */
+DW_API dw_status lbm_home_init(dw_lbm h, float *m, float rho0, const float u0[3],
+                               dw_stream stream);
+
+/* Advance m in place by `steps` HOME-LBM steps (pull streaming between m and
+ * the handle's tape in turn, so max_tape >= 1 suffices; an odd step count ends
+ * with one device copy back into m). solid as in lbm_step. */
+DW_API dw_status lbm_home_step(dw_lbm h, float *m, const uint8_t *solid, int32_t steps,
+                               dw_stream stream);
+
+/* rho [nz][ny][nx] and the macroscopic velocity u [3][nz][ny][nx] = u' -
+ * F / (2 rho) of the moments m; solid cells report 0. Either may be NULL. */
+DW_API dw_status lbm_home_macroscopic(dw_lbm h, const float *m, const uint8_t *solid, float *rho,
+                                      float *u, dw_stream stream);
+
 /* Solid mask of Eq. point2voxel: solid[w] = 1 iff some particle lies in
  * [x_w, x_w + dx)^3 with x_w = w dx, i.e. w = floor(x_p / dx); the mask is
  * cleared first; particles outside the lattice are ignored. pos is device

@@ -22,7 +22,8 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_substep", "mpm_substep_adjoint", "mpm_segment_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
-           "lbm_init_equilibrium", "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
+           "lbm_init_equilibrium", "lbm_home_init", "lbm_home_step", "lbm_home_macroscopic",
+           "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
            "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "vector_adam_step", "MPM", "LBM", "surr_create",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
@@ -377,6 +378,23 @@ def lbm_init_equilibrium(h, f, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
     return f
 
 
+def lbm_home_init(h, m, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+    arr = (ct.c_float * 3)(*u0)
+    check(lib().lbm_home_init(h, _dev(m, name="m"), float(rho0), ct.byref(arr), _stream(stream)))
+    return m
+
+
+def lbm_home_step(h, m, solid, steps, stream=None):
+    check(lib().lbm_home_step(h, _dev(m, name="m"), _mask(solid), int(steps), _stream(stream)))
+    return m
+
+
+def lbm_home_macroscopic(h, m, solid, rho=None, u=None, stream=None):
+    check(lib().lbm_home_macroscopic(h, _dev(m, name="m"), _mask(solid), _dev(rho, name="rho"),
+                                     _dev(u, name="u"), _stream(stream)))
+    return rho, u
+
+
 def lbm_sample_velocity(h, f, solid, pos, u_out=None, stream=None):
     """u[3][n] of the lattice f at points pos[3][n] (unit cube)."""
     n = pos.shape[1]
@@ -603,6 +621,24 @@ class LBM:
 
     def sample_velocity(self, f, solid, pos, u_out=None, stream=None):
         return lbm_sample_velocity(self.h, f, solid, pos, u_out, stream)
+
+    # HOME-LBM: ten moments per cell instead of nineteen populations
+    def moments(self, device="cuda"):
+        nx, ny, nz = self.shape
+        return torch.zeros((10, nz, ny, nx), dtype=torch.float32, device=device)
+
+    def home_init(self, m, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+        return lbm_home_init(self.h, m, rho0, u0, stream)
+
+    def home_step(self, m, solid, steps, stream=None):
+        return lbm_home_step(self.h, m, solid, steps, stream)
+
+    def home_macroscopic(self, m, solid, stream=None):
+        nx, ny, nz = self.shape
+        rho = torch.empty((nz, ny, nx), dtype=torch.float32, device=m.device)
+        u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=m.device)
+        lbm_home_macroscopic(self.h, m, solid, rho, u, stream)
+        return rho, u
 
     def macroscopic(self, f, solid, stream=None):
         nx, ny, nz = self.shape

@@ -679,3 +679,304 @@ extern "C" dw_status voxelize_particles(const float *pos, int64_t n, int32_t nx,
     DW_LAUNCHED("voxelize");
     return DW_OK;
 }
+
+// ================================================================ HOME-LBM
+// Moment-encoded lattice Boltzmann step (App. D, after Li et al. 2023): each
+// cell stores ten moments of its post-collision populations instead of the
+// nineteen populations, m = [10][ncell] with planes
+//   0: rho - 1, 1-3: u' (momentum / rho after the collision), 4-9: S (Sxx, Syy,
+//   Szz, Sxy, Sxz, Syz; S = sum H2(c_i) f_i / rho, H2 = c c - I/3).
+// A step pulls f_i(x) = f_i^post(x - c_i), each population rebuilt from the
+// source cell's moments by the Hermite series to second order plus the six
+// third-order terms D3Q19 carries (H3_aab(c) = c_b (c_a^2 - 1/3), coefficient
+// A_aab = u_b S_aa + 2 u_a S_ab - 2 u_a^2 u_b), with the same boundaries as the
+// BGK step (bounce-back from the own cell's opposite population, inlet, outlet),
+// then collides in moment space: the deviatoric part of the second moment
+// relaxes at 1/tau, its trace to equilibrium, Guo forcing per part. Arithmetic
+// on deviations (f_i - w_i) keeps float32 resolution. Two moment lattices are
+// used in turn (pull streaming is not in place); the handle's tape serves as
+// the second one.
+
+namespace dw {
+
+struct HomeParams {
+    float g_in[19];  // inlet populations (deviations): rebuilt from rho = 1, u_in, S = u_in u_in
+};
+
+// f_i - w_i rebuilt from one cell's moments (a[0] = rho - 1). Every velocity
+// component is a compile-time constant once the direction loop is unrolled,
+// and the guards drop the terms that vanish for it.
+__device__ __forceinline__ float home_rebuild(int i, const float a[10]) {
+    const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
+    const float ux = a[1], uy = a[2], uz = a[3];
+    const float sxx = a[4], syy = a[5], szz = a[6], sxy = a[7], sxz = a[8], syz = a[9];
+    float p = 0.0f;
+    if (cx) p += 3.0f * (float)cx * ux;
+    if (cy) p += 3.0f * (float)cy * uy;
+    if (cz) p += 3.0f * (float)cz * uz;
+    // 4.5 H2 : S
+    p += (cx ? 3.0f : -1.5f) * sxx;
+    p += (cy ? 3.0f : -1.5f) * syy;
+    p += (cz ? 3.0f : -1.5f) * szz;
+    if (cx && cy) p += 9.0f * (float)(cx * cy) * sxy;
+    if (cx && cz) p += 9.0f * (float)(cx * cz) * sxz;
+    if (cy && cz) p += 9.0f * (float)(cy * cz) * syz;
+    // 13.5 sum H3_aab A_aab, H3_aab = c_b (c_a^2 - 1/3): 13.5 * 2/3 = 9, 13.5 * -1/3 = -4.5
+    if (cy) p += (float)cy * (cx ? 9.0f : -4.5f) * (uy * sxx + 2.0f * ux * sxy - 2.0f * ux * ux * uy);
+    if (cz) p += (float)cz * (cx ? 9.0f : -4.5f) * (uz * sxx + 2.0f * ux * sxz - 2.0f * ux * ux * uz);
+    if (cx) p += (float)cx * (cy ? 9.0f : -4.5f) * (ux * syy + 2.0f * uy * sxy - 2.0f * uy * uy * ux);
+    if (cz) p += (float)cz * (cy ? 9.0f : -4.5f) * (uz * syy + 2.0f * uy * syz - 2.0f * uy * uy * uz);
+    if (cx) p += (float)cx * (cz ? 9.0f : -4.5f) * (ux * szz + 2.0f * uz * sxz - 2.0f * uz * uz * ux);
+    if (cy) p += (float)cy * (cz ? 9.0f : -4.5f) * (uy * szz + 2.0f * uz * syz - 2.0f * uz * uz * uy);
+    return D3Q19::w(i) * (a[0] + (1.0f + a[0]) * p);
+}
+
+// Moment-space collision from the pulled deviations' sums: dr = sum g,
+// j = sum c g, P = sum c c g (= Pi - I/3); writes the ten stored moments.
+__device__ __forceinline__ void home_collide(const LbmParams &L, float dr, const float j[3],
+                                             const float P[6], float out[10]) {
+    const float rho = 1.0f + dr, inv_rho = 1.0f / rho;
+    const float u[3] = {(j[0] + 0.5f * L.Fx) * inv_rho, (j[1] + 0.5f * L.Fy) * inv_rho,
+                        (j[2] + 0.5f * L.Fz) * inv_rho};
+    // N = Pi - rho (I/3 + u u) = P - dr/3 I - rho u u
+    const float third = 1.0f / 3.0f;
+    float N[6] = {P[0] - third * dr - rho * u[0] * u[0], P[1] - third * dr - rho * u[1] * u[1],
+                  P[2] - third * dr - rho * u[2] * u[2], P[3] - rho * u[0] * u[1],
+                  P[4] - rho * u[0] * u[2], P[5] - rho * u[1] * u[2]};
+    const float trN = third * (N[0] + N[1] + N[2]);
+    const float k = 1.0f - L.inv_tau;
+    float S[6];
+    S[0] = k * (N[0] - trN);
+    S[1] = k * (N[1] - trN);
+    S[2] = k * (N[2] - trN);
+    S[3] = k * N[3];
+    S[4] = k * N[4];
+    S[5] = k * N[5];
+    if (L.has_force) {
+        // Phi = u F + F u: deviatoric part with 1 - 1/(2 tau), trace part with 1/2
+        const float F[3] = {L.Fx, L.Fy, L.Fz};
+        const float pd[3] = {2.0f * u[0] * F[0], 2.0f * u[1] * F[1], 2.0f * u[2] * F[2]};
+        const float trP = third * (pd[0] + pd[1] + pd[2]);
+        S[0] += L.pre * (pd[0] - trP) + 0.5f * trP;
+        S[1] += L.pre * (pd[1] - trP) + 0.5f * trP;
+        S[2] += L.pre * (pd[2] - trP) + 0.5f * trP;
+        S[3] += L.pre * (u[0] * F[1] + F[0] * u[1]);
+        S[4] += L.pre * (u[0] * F[2] + F[0] * u[2]);
+        S[5] += L.pre * (u[1] * F[2] + F[1] * u[2]);
+    }
+    out[0] = dr;
+    out[1] = u[0] + 0.5f * L.Fx * inv_rho;
+    out[2] = u[1] + 0.5f * L.Fy * inv_rho;
+    out[3] = u[2] + 0.5f * L.Fz * inv_rho;
+    out[4] = u[0] * u[0] + S[0] * inv_rho;
+    out[5] = u[1] * u[1] + S[1] * inv_rho;
+    out[6] = u[2] * u[2] + S[2] * inv_rho;
+    out[7] = u[0] * u[1] + S[3] * inv_rho;
+    out[8] = u[0] * u[2] + S[4] * inv_rho;
+    out[9] = u[1] * u[2] + S[5] * inv_rho;
+}
+
+__device__ __forceinline__ void home_load(const float *__restrict__ m, int nc, int cell, float a[10]) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) a[k] = __ldg(m + k * nc + cell);
+}
+
+// One HOME-LBM step min -> mout (lattice-row launch). Solid cells are copied.
+__global__ void __launch_bounds__(256, 4) k_home_step(LbmParams L, HomeParams H,
+                                                  const float *__restrict__ min,
+                                                  float *__restrict__ mout,
+                                                  const uint32_t *__restrict__ links) {
+    pdl_wait();
+    pdl_trigger();
+    int x, y, z, cell;
+    if (!lattice_cell(L, x, y, z, cell)) return;
+    const int nc = L.ncell;
+    const uint32_t lk = links ? links[cell] : 0u;
+    float own[10];
+    home_load(min, nc, cell, own);
+    if (lk & 1u) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) mout[k * nc + cell] = own[k];
+        return;
+    }
+    const NbrOffsets o = nbr_offsets(L, x, y, z);
+    const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
+    float dr = 0.0f, j[3] = {0.0f, 0.0f, 0.0f}, P[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
+        const int jo = D3Q19::opp(i);  // the source x - c_i is the neighbour x + c_jo
+        float g;
+        if (i == 0) {
+            g = home_rebuild(0, own);
+        } else if (inlet_face && cx == 1) {
+            g = H.g_in[i];
+        } else if (outlet_face && cx == -1) {
+            g = home_rebuild(i, own);
+        } else if ((lk >> jo) & 1u) {
+            g = home_rebuild(jo, own);  // halfway bounce-back
+        } else {
+            float src[10];
+            home_load(min, nc, cell + o.off(-cx, -cy, -cz), src);
+            g = home_rebuild(i, src);
+        }
+        dr += g;
+        if (cx) j[0] += (float)cx * g;
+        if (cy) j[1] += (float)cy * g;
+        if (cz) j[2] += (float)cz * g;
+        if (cx) P[0] += g;
+        if (cy) P[1] += g;
+        if (cz) P[2] += g;
+        if (cx && cy) P[3] += (float)(cx * cy) * g;
+        if (cx && cz) P[4] += (float)(cx * cz) * g;
+        if (cy && cz) P[5] += (float)(cy * cz) * g;
+    }
+    float out[10];
+    home_collide(L, dr, j, P, out);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) mout[k * nc + cell] = out[k];
+}
+
+__global__ void k_home_fill(int nc, float *__restrict__ m, float v0, float v1,
+                            float v2, float v3, float v4, float v5, float v6, float v7, float v8,
+                            float v9) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nc) return;
+    const float v[10] = {v0, v1, v2, v3, v4, v5, v6, v7, v8, v9};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) m[k * nc + cell] = v[k];
+}
+
+__global__ void k_home_macroscopic(LbmParams L, const float *__restrict__ m,
+                                   const uint8_t *__restrict__ solid, float *__restrict__ rho,
+                                   float *__restrict__ u) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= L.ncell) return;
+    const int nc = L.ncell;
+    const bool sol = solid && solid[cell];
+    const float r = 1.0f + m[cell];
+    const float hr = 0.5f / r;
+    if (rho) rho[cell] = sol ? 0.0f : r;
+    if (u) {
+        u[cell] = sol ? 0.0f : m[nc + cell] - hr * L.Fx;
+        u[nc + cell] = sol ? 0.0f : m[2 * nc + cell] - hr * L.Fy;
+        u[2 * nc + cell] = sol ? 0.0f : m[3 * nc + cell] - hr * L.Fz;
+    }
+}
+
+// Host copy of the moment-space collision in double (inlet and fill values).
+static void home_collide_host(const dw_lbm_desc &d, double rho, const double j[3],
+                              const double Pi[3][3], double out[10]) {
+    const double F[3] = {d.force[0], d.force[1], d.force[2]}, tau = d.tau;
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
+    double N[3][3], Phi[3][3], trN = 0.0, trP = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            N[a][b] = Pi[a][b] - rho * ((a == b ? 1.0 / 3.0 : 0.0) + u[a] * u[b]);
+            Phi[a][b] = u[a] * F[b] + F[a] * u[b];
+        }
+    for (int a = 0; a < 3; ++a) {
+        trN += N[a][a] / 3.0;
+        trP += Phi[a][a] / 3.0;
+    }
+    double S[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double dl = a == b ? 1.0 : 0.0;
+            S[a][b] = u[a] * u[b] + ((1.0 - 1.0 / tau) * (N[a][b] - dl * trN) +
+                                     (1.0 - 0.5 / tau) * (Phi[a][b] - dl * trP) + 0.5 * dl * trP) /
+                                        rho;
+        }
+    out[0] = rho - 1.0;
+    for (int a = 0; a < 3; ++a) out[1 + a] = u[a] + 0.5 * F[a] / rho;
+    out[4] = S[0][0];
+    out[5] = S[1][1];
+    out[6] = S[2][2];
+    out[7] = S[0][1];
+    out[8] = S[0][2];
+    out[9] = S[1][2];
+}
+
+static HomeParams home_params(const dw_lbm_desc &d) {
+    HomeParams H;
+    const double u[3] = {d.u_inlet[0], d.u_inlet[1], d.u_inlet[2]};
+    const double S[3][3] = {{u[0] * u[0], u[0] * u[1], u[0] * u[2]},
+                            {u[1] * u[0], u[1] * u[1], u[1] * u[2]},
+                            {u[2] * u[0], u[2] * u[1], u[2] * u[2]}};
+    for (int i = 0; i < 19; ++i) {
+        const double c[3] = {(double)D3Q19::cx(i), (double)D3Q19::cy(i), (double)D3Q19::cz(i)};
+        double p = 0.0;
+        for (int a = 0; a < 3; ++a) p += 3.0 * c[a] * u[a];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                p += 4.5 * (c[a] * c[b] - (a == b ? 1.0 / 3.0 : 0.0)) * S[a][b];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                if (a == b) continue;
+                const double A = u[b] * S[a][a] + 2.0 * u[a] * S[a][b] - 2.0 * u[a] * u[a] * u[b];
+                p += 13.5 * c[b] * (c[a] * c[a] - 1.0 / 3.0) * A;
+            }
+        H.g_in[i] = (float)(D3Q19::w(i) * p);  // rho = 1: w (rho - 1) + w rho p
+    }
+    return H;
+}
+
+}  // namespace dw
+
+extern "C" dw_status lbm_home_init(dw_lbm h, float *m, float rho0, const float u0[3],
+                                   dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(m && u0, "m/u0 must not be NULL");
+    DW_REQUIRE(rho0 > 0.0f, "rho0 must be > 0");
+    const double r = rho0, u[3] = {u0[0], u0[1], u0[2]};
+    const double j[3] = {r * u[0], r * u[1], r * u[2]};
+    double Pi[3][3], v[10];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Pi[a][b] = r * ((a == b ? 1.0 / 3.0 : 0.0) + u[a] * u[b]);
+    home_collide_host(h->desc, r, j, Pi, v);
+    k_home_fill<<<grid_for(h->L.ncell, 256), 256, 0, as_stream(stream)>>>(
+        h->L.ncell, m, (float)v[0], (float)v[1], (float)v[2], (float)v[3], (float)v[4],
+        (float)v[5], (float)v[6], (float)v[7], (float)v[8], (float)v[9]);
+    DW_LAUNCHED("k_home_fill");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_home_step(dw_lbm h, float *m, const uint8_t *solid, int32_t steps,
+                                   dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(m, "m must not be NULL");
+    DW_REQUIRE(steps >= 0, "steps must be >= 0");
+    if (steps == 0) return DW_OK;
+    cudaStream_t s = as_stream(stream);
+    const LbmParams &L = h->L;
+    const HomeParams H = home_params(h->desc);
+    const uint32_t *links = nullptr;
+    if (solid) {
+        k_lbm_links<<<grid_for(L.ncell, 256), 256, 0, s>>>(L, solid, h->links);
+        links = h->links;
+    }
+    dim3 rg, rb;
+    lattice_launch(L, rg, rb);
+    float *a = m, *b = h->tape;  // the tape holds >= 19 ncell floats; 10 are used
+    for (int k = 0; k < steps; ++k) {
+        DW_CUDA(launch_pdl3(k_home_step, rg, rb, s, L, H, (const float *)a, b, links));
+        std::swap(a, b);
+    }
+    if (a != m)
+        DW_CUDA(cudaMemcpyAsync(m, a, sizeof(float) * 10 * (size_t)L.ncell,
+                                cudaMemcpyDeviceToDevice, s));
+    DW_LAUNCHED("lbm_home_step");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_home_macroscopic(dw_lbm h, const float *m, const uint8_t *solid,
+                                          float *rho, float *u, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(m, "m must not be NULL");
+    if (!rho && !u) return DW_OK;
+    k_home_macroscopic<<<grid_for(h->L.ncell, 256), 256, 0, as_stream(stream)>>>(h->L, m, solid,
+                                                                                 rho, u);
+    DW_LAUNCHED("k_home_macroscopic");
+    return DW_OK;
+}
