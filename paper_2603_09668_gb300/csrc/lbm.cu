@@ -485,6 +485,7 @@ struct LbmHandle {
     float *tape = nullptr;    // [max_tape][19][ncell]
     float *gtmp = nullptr;    // [19][ncell]
     uint32_t *links = nullptr;  // [ncell]
+    bool home_attr_set = false;  // k_home_step's shared-memory limit raised
 };
 
 static void fill_lbm_params(LbmHandle *h) {
@@ -706,7 +707,7 @@ struct HomeParams {
 // f_i - w_i rebuilt from one cell's moments (a[0] = rho - 1). Every velocity
 // component is a compile-time constant once the direction loop is unrolled,
 // and the guards drop the terms that vanish for it.
-__device__ __forceinline__ float home_rebuild(int i, const float a[10]) {
+__host__ __device__ __forceinline__ float home_rebuild(int i, const float a[10]) {
     const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
     const float ux = a[1], uy = a[2], uz = a[3];
     const float sxx = a[4], syy = a[5], szz = a[6], sxy = a[7], sxz = a[8], syz = a[9];
@@ -731,9 +732,65 @@ __device__ __forceinline__ float home_rebuild(int i, const float a[10]) {
     return D3Q19::w(i) * (a[0] + (1.0f + a[0]) * p);
 }
 
+// All nineteen f_i - w_i of one cell at once. Grouping each direction's terms
+// into an even part (shared by opposite directions) and odd parts makes the
+// closure coefficients A_aab count once per cell instead of once per
+// population; the result equals home_rebuild(i, a) for every i.
+__host__ __device__ __forceinline__ void home_rebuild_all(const float a[10], float g[19]) {
+    const float dr = a[0], rho = 1.0f + a[0];
+    const float ux = a[1], uy = a[2], uz = a[3];
+    const float sxx = a[4], syy = a[5], szz = a[6], sxy = a[7], sxz = a[8], syz = a[9];
+    const float Axxy = uy * sxx + 2.0f * ux * sxy - 2.0f * ux * ux * uy;
+    const float Axxz = uz * sxx + 2.0f * ux * sxz - 2.0f * ux * ux * uz;
+    const float Axyy = ux * syy + 2.0f * uy * sxy - 2.0f * uy * uy * ux;
+    const float Ayyz = uz * syy + 2.0f * uy * syz - 2.0f * uy * uy * uz;
+    const float Axzz = ux * szz + 2.0f * uz * sxz - 2.0f * uz * uz * ux;
+    const float Ayzz = uy * szz + 2.0f * uz * syz - 2.0f * uz * uz * uy;
+    const float w0 = 1.0f / 3.0f, w1 = 1.0f / 18.0f, w2 = 1.0f / 36.0f;
+    g[0] = w0 * (dr + rho * (-1.5f * (sxx + syy + szz)));
+    // axis directions: p = E_a +- O_a
+    const float Ex = 3.0f * sxx - 1.5f * (syy + szz), Ox = 3.0f * ux - 4.5f * (Axyy + Axzz);
+    const float Ey = 3.0f * syy - 1.5f * (sxx + szz), Oy = 3.0f * uy - 4.5f * (Axxy + Ayzz);
+    const float Ez = 3.0f * szz - 1.5f * (sxx + syy), Oz = 3.0f * uz - 4.5f * (Axxz + Ayyz);
+    g[1] = w1 * (dr + rho * (Ex + Ox));
+    g[2] = w1 * (dr + rho * (Ex - Ox));
+    g[3] = w1 * (dr + rho * (Ey + Oy));
+    g[4] = w1 * (dr + rho * (Ey - Oy));
+    g[5] = w1 * (dr + rho * (Ez + Oz));
+    g[6] = w1 * (dr + rho * (Ez - Oz));
+    // edge directions (s, t) in a plane: p = E + 9 s t S_ab + s P + t Q
+    {
+        const float E = 3.0f * (sxx + syy) - 1.5f * szz, D = 9.0f * sxy;
+        const float P = 3.0f * ux + 9.0f * Axyy - 4.5f * Axzz;
+        const float Q = 3.0f * uy + 9.0f * Axxy - 4.5f * Ayzz;
+        g[7] = w2 * (dr + rho * (E + D + P + Q));
+        g[8] = w2 * (dr + rho * (E + D - P - Q));
+        g[13] = w2 * (dr + rho * (E - D + P - Q));
+        g[14] = w2 * (dr + rho * (E - D - P + Q));
+    }
+    {
+        const float E = 3.0f * (sxx + szz) - 1.5f * syy, D = 9.0f * sxz;
+        const float P = 3.0f * ux + 9.0f * Axzz - 4.5f * Axyy;
+        const float Q = 3.0f * uz + 9.0f * Axxz - 4.5f * Ayyz;
+        g[9] = w2 * (dr + rho * (E + D + P + Q));
+        g[10] = w2 * (dr + rho * (E + D - P - Q));
+        g[15] = w2 * (dr + rho * (E - D + P - Q));
+        g[16] = w2 * (dr + rho * (E - D - P + Q));
+    }
+    {
+        const float E = 3.0f * (syy + szz) - 1.5f * sxx, D = 9.0f * syz;
+        const float P = 3.0f * uy + 9.0f * Ayzz - 4.5f * Axxy;
+        const float Q = 3.0f * uz + 9.0f * Ayyz - 4.5f * Axxz;
+        g[11] = w2 * (dr + rho * (E + D + P + Q));
+        g[12] = w2 * (dr + rho * (E + D - P - Q));
+        g[17] = w2 * (dr + rho * (E - D + P - Q));
+        g[18] = w2 * (dr + rho * (E - D - P + Q));
+    }
+}
+
 // Moment-space collision from the pulled deviations' sums: dr = sum g,
 // j = sum c g, P = sum c c g (= Pi - I/3); writes the ten stored moments.
-__device__ __forceinline__ void home_collide(const LbmParams &L, float dr, const float j[3],
+__host__ __device__ __forceinline__ void home_collide(const LbmParams &L, float dr, const float j[3],
                                              const float P[6], float out[10]) {
     const float rho = 1.0f + dr, inv_rho = 1.0f / rho;
     const float u[3] = {(j[0] + 0.5f * L.Fx) * inv_rho, (j[1] + 0.5f * L.Fy) * inv_rho,
@@ -776,49 +833,97 @@ __device__ __forceinline__ void home_collide(const LbmParams &L, float dr, const
     out[9] = u[1] * u[2] + S[5] * inv_rho;
 }
 
-__device__ __forceinline__ void home_load(const float *__restrict__ m, int nc, int cell, float a[10]) {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) a[k] = __ldg(m + k * nc + cell);
+// Tiles of the streaming HOME kernel: 32 x 8 cells of a z-plane per block
+// (one thread each), walking HOME_TZ planes along z. Each plane of the tile
+// plus a one-cell halo (34 x 10 = 340 cells) has its cells' nineteen
+// post-collision populations rebuilt once into a shared-memory ring of three
+// planes; every cell of the middle plane then pulls its populations from the
+// ring, so a cell's closure terms are evaluated about 1.5 times per step
+// (halo and the two extra planes of each z range) instead of once per pulling
+// neighbour, and its moments are read from global memory about as often.
+constexpr int HOME_TX = 32, HOME_TY = 8, HOME_TZ = 16;
+constexpr int HOME_HX = HOME_TX + 2, HOME_HY = HOME_TY + 2;
+constexpr int HOME_PLANE = HOME_HX * HOME_HY;          // 340 cells
+constexpr int HOME_SLOT = 19 * HOME_PLANE;             // floats per ring plane
+constexpr size_t HOME_SMEM = 3 * HOME_SLOT * sizeof(float);  // 77,520 bytes
+
+__host__ __device__ __forceinline__ int wrap_full(int v, int n) { return ((v % n) + n) % n; }
+
+__host__ __device__ __forceinline__ float ld_ro(const float *p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
 }
 
-// One HOME-LBM step min -> mout (lattice-row launch). Solid cells are copied.
-__global__ void __launch_bounds__(256, 4) k_home_step(LbmParams L, HomeParams H,
-                                                  const float *__restrict__ min,
-                                                  float *__restrict__ mout,
-                                                  const uint32_t *__restrict__ links) {
-    pdl_wait();
-    pdl_trigger();
-    int x, y, z, cell;
-    if (!lattice_cell(L, x, y, z, cell)) return;
+// Rebuild the populations of halo-plane cell c (0..339) of the tile at
+// (x0, y0) in plane zz (any integer; wrapped periodically) into slot[i * 340 + c].
+// Cells whose populations no fluid cell of the tile pulls are skipped: solid
+// cells (bounce-back uses the puller's own populations) and, with the x inlet
+// and outlet, cells beyond the x faces.
+__host__ __device__ __forceinline__ void home_tile_rebuild(const LbmParams &L,
+                                                           const float *__restrict__ m_in,
+                                                           const uint8_t *__restrict__ solid,
+                                                           float *slot, int x0, int y0, int zz,
+                                                           int c) {
+    const int hx = c % HOME_HX, hy = c / HOME_HX;
+    int gx = x0 + hx - 1;
+    if (gx < 0 || gx >= L.nx) {
+        if (L.bc_x == 1) return;
+        gx = wrap_full(gx, L.nx);
+    }
+    const int gy = wrap_full(y0 + hy - 1, L.ny), gz = wrap_full(zz, L.nz);
+    const int cell = (gz * L.ny + gy) * L.nx + gx;
+    if (solid && solid[cell]) return;
     const int nc = L.ncell;
-    const uint32_t lk = links ? links[cell] : 0u;
-    float own[10];
-    home_load(min, nc, cell, own);
-    if (lk & 1u) {
+    float a[10], g[19];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) mout[k * nc + cell] = own[k];
+    for (int k = 0; k < 10; ++k) a[k] = ld_ro(m_in + k * nc + cell);
+    home_rebuild_all(a, g);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) slot[i * HOME_PLANE + c] = g[i];
+}
+
+// Pull, collide and store cell (x0 + tx, y0 + ty, z) from the ring: planes
+// z - 1, z, z + 1 are in slots s_m, s_0, s_p of sm.
+__host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, const HomeParams &H,
+                                                        const float *__restrict__ m_in,
+                                                        float *__restrict__ mout,
+                                                        const uint32_t *__restrict__ links,
+                                                        const float *sm, int s_m, int s_0,
+                                                        int s_p, int x0, int y0, int z, int tx,
+                                                        int ty) {
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= L.nx || y >= L.ny) return;
+    const int nc = L.ncell;
+    const int cell = (z * L.ny + y) * L.nx + x;
+    const uint32_t lk = links ? links[cell] : 0u;
+    if (lk & 1u) {  // solid: keep the moments
+#pragma unroll
+        for (int k = 0; k < 10; ++k) mout[k * nc + cell] = ld_ro(m_in + k * nc + cell);
         return;
     }
-    const NbrOffsets o = nbr_offsets(L, x, y, z);
     const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
+    const int oc = (ty + 1) * HOME_HX + (tx + 1);
+    const float *own = sm + s_0 * HOME_SLOT;
     float dr = 0.0f, j[3] = {0.0f, 0.0f, 0.0f}, P[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
-        const int jo = D3Q19::opp(i);  // the source x - c_i is the neighbour x + c_jo
+        const int jo = D3Q19::opp(i);
         float g;
         if (i == 0) {
-            g = home_rebuild(0, own);
+            g = own[oc];
         } else if (inlet_face && cx == 1) {
             g = H.g_in[i];
         } else if (outlet_face && cx == -1) {
-            g = home_rebuild(i, own);
+            g = own[i * HOME_PLANE + oc];
         } else if ((lk >> jo) & 1u) {
-            g = home_rebuild(jo, own);  // halfway bounce-back
+            g = own[jo * HOME_PLANE + oc];  // halfway bounce-back
         } else {
-            float src[10];
-            home_load(min, nc, cell + o.off(-cx, -cy, -cz), src);
-            g = home_rebuild(i, src);
+            const int sl = cz == 1 ? s_m : (cz == -1 ? s_p : s_0);  // source plane z - c_z
+            g = sm[sl * HOME_SLOT + i * HOME_PLANE + oc - cy * HOME_HX - cx];
         }
         dr += g;
         if (cx) j[0] += (float)cx * g;
@@ -835,6 +940,34 @@ __global__ void __launch_bounds__(256, 4) k_home_step(LbmParams L, HomeParams H,
     home_collide(L, dr, j, P, out);
 #pragma unroll
     for (int k = 0; k < 10; ++k) mout[k * nc + cell] = out[k];
+}
+
+// One HOME-LBM step m_in -> mout. Grid (ceil(nx/32), ceil(ny/8),
+// ceil(nz/HOME_TZ)), 256 threads, HOME_SMEM bytes of dynamic shared memory.
+__global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
+                                                  const float *__restrict__ m_in,
+                                                  float *__restrict__ mout,
+                                                  const uint8_t *__restrict__ solid,
+                                                  const uint32_t *__restrict__ links) {
+    extern __shared__ float home_sm[];
+    pdl_wait();
+    pdl_trigger();
+    const int x0 = blockIdx.x * HOME_TX, y0 = blockIdx.y * HOME_TY, z0 = blockIdx.z * HOME_TZ;
+    const int z1 = min(z0 + HOME_TZ, L.nz);
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    for (int c = tid; c < HOME_PLANE; c += 256) {
+        home_tile_rebuild(L, m_in, solid, home_sm, x0, y0, z0 - 1, c);
+        home_tile_rebuild(L, m_in, solid, home_sm + HOME_SLOT, x0, y0, z0, c);
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int r = z - z0;
+        const int s_m = r % 3, s_0 = (r + 1) % 3, s_p = (r + 2) % 3;
+        for (int c = tid; c < HOME_PLANE; c += 256)
+            home_tile_rebuild(L, m_in, solid, home_sm + s_p * HOME_SLOT, x0, y0, z + 1, c);
+        __syncthreads();
+        home_tile_cell(L, H, m_in, mout, links, home_sm, s_m, s_0, s_p, x0, y0, z, tx, ty);
+        __syncthreads();
+    }
 }
 
 __global__ void k_home_fill(int nc, float *__restrict__ m, float v0, float v1,
@@ -956,11 +1089,18 @@ extern "C" dw_status lbm_home_step(dw_lbm h, float *m, const uint8_t *solid, int
         k_lbm_links<<<grid_for(L.ncell, 256), 256, 0, s>>>(L, solid, h->links);
         links = h->links;
     }
-    dim3 rg, rb;
-    lattice_launch(L, rg, rb);
+    if (!h->home_attr_set) {
+        DW_CUDA(cudaFuncSetAttribute(k_home_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)HOME_SMEM));
+        h->home_attr_set = true;
+    }
+    const dim3 grid((unsigned)((L.nx + HOME_TX - 1) / HOME_TX),
+                    (unsigned)((L.ny + HOME_TY - 1) / HOME_TY),
+                    (unsigned)((L.nz + HOME_TZ - 1) / HOME_TZ));
     float *a = m, *b = h->tape;  // the tape holds >= 19 ncell floats; 10 are used
     for (int k = 0; k < steps; ++k) {
-        DW_CUDA(launch_pdl3(k_home_step, rg, rb, s, L, H, (const float *)a, b, links));
+        DW_CUDA(launch_pdl_smem(k_home_step, grid, dim3(256), HOME_SMEM, s, L, H,
+                                (const float *)a, b, solid, links));
         std::swap(a, b);
     }
     if (a != m)
