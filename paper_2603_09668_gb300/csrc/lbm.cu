@@ -857,40 +857,54 @@ __host__ __device__ __forceinline__ float ld_ro(const float *p) {
 #endif
 }
 
-// Rebuild the populations of halo-plane cell c (0..339) of the tile at
-// (x0, y0) in plane zz (any integer; wrapped periodically) into slot[i * 340 + c].
-// Cells whose populations no fluid cell of the tile pulls are skipped: solid
+// The moments of halo-plane cell c (0..339) of the tile at (x0, y0) in plane
+// zz (any integer; wrapped periodically), loaded ahead of their use. ok is
+// false for cells whose populations no fluid cell of the tile pulls: solid
 // cells (bounce-back uses the puller's own populations) and, with the x inlet
-// and outlet, cells beyond the x faces.
-__host__ __device__ __forceinline__ void home_tile_rebuild(const LbmParams &L,
-                                                           const float *__restrict__ m_in,
-                                                           const uint8_t *__restrict__ solid,
-                                                           float *slot, int x0, int y0, int zz,
-                                                           int c) {
+// and outlet, cells beyond the x faces (nothing is loaded for those).
+struct HomeHalo {
+    float a[10];
+    bool ok;
+};
+
+__host__ __device__ __forceinline__ void home_halo_load(const LbmParams &L,
+                                                        const float *__restrict__ m_in,
+                                                        const uint8_t *__restrict__ solid,
+                                                        int x0, int y0, int zz, int c,
+                                                        HomeHalo &h) {
     const int hx = c % HOME_HX, hy = c / HOME_HX;
     int gx = x0 + hx - 1;
+    h.ok = true;
     if (gx < 0 || gx >= L.nx) {
-        if (L.bc_x == 1) return;
+        if (L.bc_x == 1) {
+            h.ok = false;
+            return;
+        }
         gx = wrap_full(gx, L.nx);
     }
     const int gy = wrap_full(y0 + hy - 1, L.ny), gz = wrap_full(zz, L.nz);
     const int cell = (gz * L.ny + gy) * L.nx + gx;
-    if (solid && solid[cell]) return;
     const int nc = L.ncell;
-    float a[10], g[19];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) a[k] = ld_ro(m_in + k * nc + cell);
-    home_rebuild_all(a, g);
+    for (int k = 0; k < 10; ++k) h.a[k] = ld_ro(m_in + k * nc + cell);
+    if (solid && solid[cell]) h.ok = false;
+}
+
+// Rebuild the nineteen populations of a loaded halo cell into slot[i * 340 + c].
+__host__ __device__ __forceinline__ void home_halo_store(const HomeHalo &h, float *slot, int c) {
+    if (!h.ok) return;
+    float g[19];
+    home_rebuild_all(h.a, g);
 #pragma unroll
     for (int i = 0; i < 19; ++i) slot[i * HOME_PLANE + c] = g[i];
 }
 
 // Pull, collide and store cell (x0 + tx, y0 + ty, z) from the ring: planes
-// z - 1, z, z + 1 are in slots s_m, s_0, s_p of sm.
+// z - 1, z, z + 1 are in slots s_m, s_0, s_p of sm; lk is the cell's link word
+// (bit 0 solid, bit i the neighbour x + c_i solid; 0 without a mask).
 __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, const HomeParams &H,
                                                         const float *__restrict__ m_in,
-                                                        float *__restrict__ mout,
-                                                        const uint32_t *__restrict__ links,
+                                                        float *__restrict__ mout, uint32_t lk,
                                                         const float *sm, int s_m, int s_0,
                                                         int s_p, int x0, int y0, int z, int tx,
                                                         int ty) {
@@ -898,7 +912,6 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
     if (x >= L.nx || y >= L.ny) return;
     const int nc = L.ncell;
     const int cell = (z * L.ny + y) * L.nx + x;
-    const uint32_t lk = links ? links[cell] : 0u;
     if (lk & 1u) {  // solid: keep the moments
 #pragma unroll
         for (int k = 0; k < 10; ++k) mout[k * nc + cell] = ld_ro(m_in + k * nc + cell);
@@ -944,6 +957,8 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
 
 // One HOME-LBM step m_in -> mout. Grid (ceil(nx/32), ceil(ny/8),
 // ceil(nz/HOME_TZ)), 256 threads, HOME_SMEM bytes of dynamic shared memory.
+// The moments of plane z + 2 and the link words of plane z + 1 are loaded
+// while plane z is pulled and collided, so their latency overlaps the work.
 __global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
                                                   const float *__restrict__ m_in,
                                                   float *__restrict__ mout,
@@ -955,17 +970,35 @@ __global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
     const int x0 = blockIdx.x * HOME_TX, y0 = blockIdx.y * HOME_TY, z0 = blockIdx.z * HOME_TZ;
     const int z1 = min(z0 + HOME_TZ, L.nz);
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    for (int c = tid; c < HOME_PLANE; c += 256) {
-        home_tile_rebuild(L, m_in, solid, home_sm, x0, y0, z0 - 1, c);
-        home_tile_rebuild(L, m_in, solid, home_sm + HOME_SLOT, x0, y0, z0, c);
-    }
+    const int c0 = tid, c1 = tid + 256;
+    const bool two = c1 < HOME_PLANE;
+    const bool inside = x0 + tx < L.nx && y0 + ty < L.ny;
+    const int col = (y0 + ty) * L.nx + (x0 + tx), plane = L.nx * L.ny;
+    HomeHalo h0, h1;
+    home_halo_load(L, m_in, solid, x0, y0, z0 - 1, c0, h0);
+    if (two) home_halo_load(L, m_in, solid, x0, y0, z0 - 1, c1, h1);
+    home_halo_store(h0, home_sm, c0);
+    if (two) home_halo_store(h1, home_sm, c1);
+    home_halo_load(L, m_in, solid, x0, y0, z0, c0, h0);
+    if (two) home_halo_load(L, m_in, solid, x0, y0, z0, c1, h1);
+    home_halo_store(h0, home_sm + HOME_SLOT, c0);
+    if (two) home_halo_store(h1, home_sm + HOME_SLOT, c1);
+    home_halo_load(L, m_in, solid, x0, y0, z0 + 1, c0, h0);
+    if (two) home_halo_load(L, m_in, solid, x0, y0, z0 + 1, c1, h1);
+    uint32_t lk_next = (links && inside) ? links[z0 * plane + col] : 0u;
     for (int z = z0; z < z1; ++z) {
         const int r = z - z0;
         const int s_m = r % 3, s_0 = (r + 1) % 3, s_p = (r + 2) % 3;
-        for (int c = tid; c < HOME_PLANE; c += 256)
-            home_tile_rebuild(L, m_in, solid, home_sm + s_p * HOME_SLOT, x0, y0, z + 1, c);
+        home_halo_store(h0, home_sm + s_p * HOME_SLOT, c0);
+        if (two) home_halo_store(h1, home_sm + s_p * HOME_SLOT, c1);
+        if (z + 1 < z1) {  // plane z + 2 is the next iteration's z + 1
+            home_halo_load(L, m_in, solid, x0, y0, z + 2, c0, h0);
+            if (two) home_halo_load(L, m_in, solid, x0, y0, z + 2, c1, h1);
+        }
+        const uint32_t lk = lk_next;
+        if (links && inside && z + 1 < z1) lk_next = links[(z + 1) * plane + col];
         __syncthreads();
-        home_tile_cell(L, H, m_in, mout, links, home_sm, s_m, s_0, s_p, x0, y0, z, tx, ty);
+        home_tile_cell(L, H, m_in, mout, lk, home_sm, s_m, s_0, s_p, x0, y0, z, tx, ty);
         __syncthreads();
     }
 }
