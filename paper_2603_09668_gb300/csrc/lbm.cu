@@ -920,34 +920,51 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
     const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
     const int oc = (ty + 1) * HOME_HX + (tx + 1);
     const float *own = sm + s_0 * HOME_SLOT;
-    float dr = 0.0f, j[3] = {0.0f, 0.0f, 0.0f}, P[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float g[19];
+    if (lk == 0u && !inlet_face && !outlet_face) {
+        // no solid neighbour, no open face: every population comes from the ring
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
-        const int jo = D3Q19::opp(i);
-        float g;
-        if (i == 0) {
-            g = own[oc];
-        } else if (inlet_face && cx == 1) {
-            g = H.g_in[i];
-        } else if (outlet_face && cx == -1) {
-            g = own[i * HOME_PLANE + oc];
-        } else if ((lk >> jo) & 1u) {
-            g = own[jo * HOME_PLANE + oc];  // halfway bounce-back
-        } else {
+        for (int i = 0; i < 19; ++i) {
+            const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
             const int sl = cz == 1 ? s_m : (cz == -1 ? s_p : s_0);  // source plane z - c_z
-            g = sm[sl * HOME_SLOT + i * HOME_PLANE + oc - cy * HOME_HX - cx];
+            g[i] = sm[sl * HOME_SLOT + i * HOME_PLANE + oc - cy * HOME_HX - cx];
         }
-        dr += g;
-        if (cx) j[0] += (float)cx * g;
-        if (cy) j[1] += (float)cy * g;
-        if (cz) j[2] += (float)cz * g;
-        if (cx) P[0] += g;
-        if (cy) P[1] += g;
-        if (cz) P[2] += g;
-        if (cx && cy) P[3] += (float)(cx * cy) * g;
-        if (cx && cz) P[4] += (float)(cx * cz) * g;
-        if (cy && cz) P[5] += (float)(cy * cz) * g;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
+            const int jo = D3Q19::opp(i);
+            if (i == 0) {
+                g[i] = own[oc];
+            } else if (inlet_face && cx == 1) {
+                g[i] = H.g_in[i];
+            } else if (outlet_face && cx == -1) {
+                g[i] = own[i * HOME_PLANE + oc];
+            } else if ((lk >> jo) & 1u) {
+                g[i] = own[jo * HOME_PLANE + oc];  // halfway bounce-back
+            } else {
+                const int sl = cz == 1 ? s_m : (cz == -1 ? s_p : s_0);
+                g[i] = sm[sl * HOME_SLOT + i * HOME_PLANE + oc - cy * HOME_HX - cx];
+            }
+        }
+    }
+    // moments over pairs of opposite directions (2k - 1, 2k): s = g + g_opp
+    // carries the even moments, d = g - g_opp the odd ones
+    float dr = g[0], j[3] = {0.0f, 0.0f, 0.0f}, P[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 1; i < 19; i += 2) {
+        const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
+        const float sp = g[i] + g[i + 1], dp = g[i] - g[i + 1];
+        dr += sp;
+        if (cx) j[0] += (float)cx * dp;
+        if (cy) j[1] += (float)cy * dp;
+        if (cz) j[2] += (float)cz * dp;
+        if (cx) P[0] += sp;
+        if (cy) P[1] += sp;
+        if (cz) P[2] += sp;
+        if (cx && cy) P[3] += (float)(cx * cy) * sp;
+        if (cx && cz) P[4] += (float)(cx * cz) * sp;
+        if (cy && cz) P[5] += (float)(cy * cz) * sp;
     }
     float out[10];
     home_collide(L, dr, j, P, out);
