@@ -24,6 +24,7 @@
 #include <new>
 
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -485,7 +486,8 @@ struct LbmHandle {
     float *tape = nullptr;    // [max_tape][19][ncell]
     float *gtmp = nullptr;    // [19][ncell]
     uint32_t *links = nullptr;  // [ncell]
-    bool home_attr_set = false;  // k_home_step's shared-memory limit raised
+    bool home_attr_set = false;  // k_home_step's shared-memory limit raised, tz chosen
+    int home_tz = 16;            // planes per block of k_home_step
 };
 
 static void fill_lbm_params(LbmHandle *h) {
@@ -834,14 +836,14 @@ __host__ __device__ __forceinline__ void home_collide(const LbmParams &L, float 
 }
 
 // Tiles of the streaming HOME kernel: 32 x 8 cells of a z-plane per block
-// (one thread each), walking HOME_TZ planes along z. Each plane of the tile
+// (one thread each), walking tz planes along z (chosen per lattice, below). Each plane of the tile
 // plus a one-cell halo (34 x 10 = 340 cells) has its cells' nineteen
 // post-collision populations rebuilt once into a shared-memory ring of three
 // planes; every cell of the middle plane then pulls its populations from the
 // ring, so a cell's closure terms are evaluated about 1.5 times per step
 // (halo and the two extra planes of each z range) instead of once per pulling
 // neighbour, and its moments are read from global memory about as often.
-constexpr int HOME_TX = 32, HOME_TY = 8, HOME_TZ = 16;
+constexpr int HOME_TX = 32, HOME_TY = 8;
 constexpr int HOME_HX = HOME_TX + 2, HOME_HY = HOME_TY + 2;
 constexpr int HOME_PLANE = HOME_HX * HOME_HY;          // 340 cells
 constexpr int HOME_SLOT = 19 * HOME_PLANE;             // floats per ring plane
@@ -857,37 +859,45 @@ __host__ __device__ __forceinline__ float ld_ro(const float *p) {
 #endif
 }
 
-// The moments of halo-plane cell c (0..339) of the tile at (x0, y0) in plane
-// zz (any integer; wrapped periodically), loaded ahead of their use. ok is
-// false for cells whose populations no fluid cell of the tile pulls: solid
-// cells (bounce-back uses the puller's own populations) and, with the x inlet
-// and outlet, cells beyond the x faces (nothing is loaded for those).
+// The moments of one halo-plane cell, loaded ahead of their use. ok is false
+// for cells whose populations no fluid cell of the tile pulls: solid cells
+// (bounce-back uses the puller's own populations) and, with the x inlet and
+// outlet, cells beyond the x faces (nothing is loaded for those).
 struct HomeHalo {
     float a[10];
     bool ok;
 };
 
-__host__ __device__ __forceinline__ void home_halo_load(const LbmParams &L,
-                                                        const float *__restrict__ m_in,
-                                                        const uint8_t *__restrict__ solid,
-                                                        int x0, int y0, int zz, int c,
-                                                        HomeHalo &h) {
+// Where halo-plane cell c (0..339) of the tile at (x0, y0) sits in every
+// plane: xy = y * nx + x after the periodic wraps, or -1 beyond an x face
+// with the inlet and outlet. Fixed for a thread, so computed once.
+__host__ __device__ __forceinline__ int home_halo_xy(const LbmParams &L, int x0, int y0, int c) {
     const int hx = c % HOME_HX, hy = c / HOME_HX;
     int gx = x0 + hx - 1;
-    h.ok = true;
     if (gx < 0 || gx >= L.nx) {
-        if (L.bc_x == 1) {
-            h.ok = false;
-            return;
-        }
+        if (L.bc_x == 1) return -1;
         gx = wrap_full(gx, L.nx);
     }
-    const int gy = wrap_full(y0 + hy - 1, L.ny), gz = wrap_full(zz, L.nz);
-    const int cell = (gz * L.ny + gy) * L.nx + gx;
+    return wrap_full(y0 + hy - 1, L.ny) * L.nx + gx;
+}
+
+// Load the moments of the halo cell at xy in plane gz (0 <= gz < nz).
+__host__ __device__ __forceinline__ void home_halo_load(const LbmParams &L,
+                                                        const float *__restrict__ m_in,
+                                                        const uint8_t *__restrict__ solid, int xy,
+                                                        int gz, HomeHalo &h) {
+    h.ok = xy >= 0;
+    if (!h.ok) return;
+    const int cell = gz * (L.nx * L.ny) + xy;
     const int nc = L.ncell;
 #pragma unroll
     for (int k = 0; k < 10; ++k) h.a[k] = ld_ro(m_in + k * nc + cell);
     if (solid && solid[cell]) h.ok = false;
+}
+
+// Plane z wrapped periodically for z in [-1, nz].
+__host__ __device__ __forceinline__ int home_wrap_z(const LbmParams &L, int z) {
+    return z < 0 ? z + L.nz : (z >= L.nz ? z - L.nz : z);
 }
 
 // Rebuild the nineteen populations of a loaded halo cell into slot[i * 340 + c].
@@ -973,35 +983,36 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
 }
 
 // One HOME-LBM step m_in -> mout. Grid (ceil(nx/32), ceil(ny/8),
-// ceil(nz/HOME_TZ)), 256 threads, HOME_SMEM bytes of dynamic shared memory.
+// ceil(nz/tz)), 256 threads, HOME_SMEM bytes of dynamic shared memory.
 // The moments of plane z + 2 and the link words of plane z + 1 are loaded
 // while plane z is pulled and collided, so their latency overlaps the work.
 __global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
                                                   const float *__restrict__ m_in,
                                                   float *__restrict__ mout,
                                                   const uint8_t *__restrict__ solid,
-                                                  const uint32_t *__restrict__ links) {
+                                                  const uint32_t *__restrict__ links, int tz) {
     extern __shared__ float home_sm[];
     pdl_wait();
     pdl_trigger();
-    const int x0 = blockIdx.x * HOME_TX, y0 = blockIdx.y * HOME_TY, z0 = blockIdx.z * HOME_TZ;
-    const int z1 = min(z0 + HOME_TZ, L.nz);
+    const int x0 = blockIdx.x * HOME_TX, y0 = blockIdx.y * HOME_TY, z0 = blockIdx.z * tz;
+    const int z1 = min(z0 + tz, L.nz);
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int c0 = tid, c1 = tid + 256;
     const bool two = c1 < HOME_PLANE;
     const bool inside = x0 + tx < L.nx && y0 + ty < L.ny;
     const int col = (y0 + ty) * L.nx + (x0 + tx), plane = L.nx * L.ny;
+    const int xy0 = home_halo_xy(L, x0, y0, c0), xy1 = two ? home_halo_xy(L, x0, y0, c1) : -1;
     HomeHalo h0, h1;
-    home_halo_load(L, m_in, solid, x0, y0, z0 - 1, c0, h0);
-    if (two) home_halo_load(L, m_in, solid, x0, y0, z0 - 1, c1, h1);
+    home_halo_load(L, m_in, solid, xy0, home_wrap_z(L, z0 - 1), h0);
+    if (two) home_halo_load(L, m_in, solid, xy1, home_wrap_z(L, z0 - 1), h1);
     home_halo_store(h0, home_sm, c0);
     if (two) home_halo_store(h1, home_sm, c1);
-    home_halo_load(L, m_in, solid, x0, y0, z0, c0, h0);
-    if (two) home_halo_load(L, m_in, solid, x0, y0, z0, c1, h1);
+    home_halo_load(L, m_in, solid, xy0, z0, h0);
+    if (two) home_halo_load(L, m_in, solid, xy1, z0, h1);
     home_halo_store(h0, home_sm + HOME_SLOT, c0);
     if (two) home_halo_store(h1, home_sm + HOME_SLOT, c1);
-    home_halo_load(L, m_in, solid, x0, y0, z0 + 1, c0, h0);
-    if (two) home_halo_load(L, m_in, solid, x0, y0, z0 + 1, c1, h1);
+    home_halo_load(L, m_in, solid, xy0, home_wrap_z(L, z0 + 1), h0);
+    if (two) home_halo_load(L, m_in, solid, xy1, home_wrap_z(L, z0 + 1), h1);
     uint32_t lk_next = (links && inside) ? links[z0 * plane + col] : 0u;
     for (int z = z0; z < z1; ++z) {
         const int r = z - z0;
@@ -1009,8 +1020,9 @@ __global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
         home_halo_store(h0, home_sm + s_p * HOME_SLOT, c0);
         if (two) home_halo_store(h1, home_sm + s_p * HOME_SLOT, c1);
         if (z + 1 < z1) {  // plane z + 2 is the next iteration's z + 1
-            home_halo_load(L, m_in, solid, x0, y0, z + 2, c0, h0);
-            if (two) home_halo_load(L, m_in, solid, x0, y0, z + 2, c1, h1);
+            const int gz = home_wrap_z(L, z + 2);
+            home_halo_load(L, m_in, solid, xy0, gz, h0);
+            if (two) home_halo_load(L, m_in, solid, xy1, gz, h1);
         }
         const uint32_t lk = lk_next;
         if (links && inside && z + 1 < z1) lk_next = links[(z + 1) * plane + col];
@@ -1105,6 +1117,26 @@ static HomeParams home_params(const dw_lbm_desc &d) {
     return H;
 }
 
+// Planes per block: each block also rebuilds the two planes beyond its z
+// range, so tall ranges waste less; the blocks run in waves of `slots`
+// (resident blocks on the GPU), so a block count just under a whole number of
+// waves wastes less. Take the tz in [8, 32] with the best product.
+static int home_pick_tz(const LbmParams &L, int slots) {
+    const long cols = (long)((L.nx + HOME_TX - 1) / HOME_TX) * ((L.ny + HOME_TY - 1) / HOME_TY);
+    int best = 16;
+    double best_eff = -1.0;
+    for (int tz = 8; tz <= 32; ++tz) {
+        const long blocks = cols * ((L.nz + tz - 1) / tz);
+        const double waves = (double)blocks / slots;
+        const double eff = waves / std::ceil(waves) * (double)tz / (tz + 2);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = tz;
+        }
+    }
+    return best;
+}
+
 }  // namespace dw
 
 extern "C" dw_status lbm_home_init(dw_lbm h, float *m, float rho0, const float u0[3],
@@ -1142,15 +1174,20 @@ extern "C" dw_status lbm_home_step(dw_lbm h, float *m, const uint8_t *solid, int
     if (!h->home_attr_set) {
         DW_CUDA(cudaFuncSetAttribute(k_home_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)HOME_SMEM));
+        int dev = 0, sms = 0, per_sm = 0;
+        DW_CUDA(cudaGetDevice(&dev));
+        DW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_home_step, 256, HOME_SMEM));
+        h->home_tz = home_pick_tz(L, std::max(1, sms * per_sm));
         h->home_attr_set = true;
     }
+    const int tz = h->home_tz;
     const dim3 grid((unsigned)((L.nx + HOME_TX - 1) / HOME_TX),
-                    (unsigned)((L.ny + HOME_TY - 1) / HOME_TY),
-                    (unsigned)((L.nz + HOME_TZ - 1) / HOME_TZ));
+                    (unsigned)((L.ny + HOME_TY - 1) / HOME_TY), (unsigned)((L.nz + tz - 1) / tz));
     float *a = m, *b = h->tape;  // the tape holds >= 19 ncell floats; 10 are used
     for (int k = 0; k < steps; ++k) {
         DW_CUDA(launch_pdl_smem(k_home_step, grid, dim3(256), HOME_SMEM, s, L, H,
-                                (const float *)a, b, solid, links));
+                                (const float *)a, b, solid, links, tz));
         std::swap(a, b);
     }
     if (a != m)
