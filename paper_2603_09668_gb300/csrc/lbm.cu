@@ -846,8 +846,25 @@ __host__ __device__ __forceinline__ void home_collide(const LbmParams &L, float 
 constexpr int HOME_TX = 32, HOME_TY = 8;
 constexpr int HOME_HX = HOME_TX + 2, HOME_HY = HOME_TY + 2;
 constexpr int HOME_PLANE = HOME_HX * HOME_HY;          // 340 cells
-constexpr int HOME_SLOT = 19 * HOME_PLANE;             // floats per ring plane
-constexpr size_t HOME_SMEM = 3 * HOME_SLOT * sizeof(float);  // 77,520 bytes
+// The ring keeps each plane's populations only as long as they are pulled:
+// in-plane directions (c_z = 0, nine of them) while the plane is the current
+// one, upward ones (c_z = +1, five) until the plane above is done, downward
+// ones (c_z = -1, five) from the plane below's step through the plane's own
+// (bounce-back reads them). Buffers, in units of 340 floats: in-plane
+// [2 planes][9] at 0, upward [3][5] at 18, downward [2][5] at 33.
+constexpr size_t HOME_SMEM = 43 * HOME_PLANE * sizeof(float);  // 58,480 bytes
+
+// Index of direction i within its group (in-plane 0 1 2 3 4 7 8 13 14,
+// upward 5 9 11 16 18, downward 6 10 12 15 17).
+__host__ __device__ constexpr int home_k(int i) {
+    constexpr int t[19] = {0, 1, 2, 3, 4, 0, 0, 5, 6, 1, 1, 2, 2, 7, 8, 3, 3, 4, 4};
+    return t[i];
+}
+// Ring offsets of plane q's group buffers (q counts the block's planes from
+// z0 - 1).
+__host__ __device__ __forceinline__ int home_in_base(int q) { return (q & 1) * 9 * HOME_PLANE; }
+__host__ __device__ __forceinline__ int home_up_base(int q) { return (18 + (q % 3) * 5) * HOME_PLANE; }
+__host__ __device__ __forceinline__ int home_dn_base(int q) { return (33 + (q & 1) * 5) * HOME_PLANE; }
 
 __host__ __device__ __forceinline__ int wrap_full(int v, int n) { return ((v % n) + n) % n; }
 
@@ -900,24 +917,28 @@ __host__ __device__ __forceinline__ int home_wrap_z(const LbmParams &L, int z) {
     return z < 0 ? z + L.nz : (z >= L.nz ? z - L.nz : z);
 }
 
-// Rebuild the nineteen populations of a loaded halo cell into slot[i * 340 + c].
-__host__ __device__ __forceinline__ void home_halo_store(const HomeHalo &h, float *slot, int c) {
+// Rebuild the nineteen populations of a loaded halo cell c of plane q into
+// the ring sm.
+__host__ __device__ __forceinline__ void home_halo_store(const HomeHalo &h, float *sm, int q, int c) {
     if (!h.ok) return;
     float g[19];
     home_rebuild_all(h.a, g);
+    const int bi = home_in_base(q) + c, bu = home_up_base(q) + c, bd = home_dn_base(q) + c;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) slot[i * HOME_PLANE + c] = g[i];
+    for (int i = 0; i < 19; ++i) {
+        const int cz = D3Q19::cz(i);
+        sm[(cz == 0 ? bi : (cz == 1 ? bu : bd)) + home_k(i) * HOME_PLANE] = g[i];
+    }
 }
 
-// Pull, collide and store cell (x0 + tx, y0 + ty, z) from the ring: planes
-// z - 1, z, z + 1 are in slots s_m, s_0, s_p of sm; lk is the cell's link word
-// (bit 0 solid, bit i the neighbour x + c_i solid; 0 without a mask).
+// Pull, collide and store cell (x0 + tx, y0 + ty, z) from the ring; z is the
+// block's plane q; lk is the cell's link word (bit 0 solid, bit i the
+// neighbour x + c_i solid; 0 without a mask).
 __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, const HomeParams &H,
                                                         const float *__restrict__ m_in,
                                                         float *__restrict__ mout, uint32_t lk,
-                                                        const float *sm, int s_m, int s_0,
-                                                        int s_p, int x0, int y0, int z, int tx,
-                                                        int ty) {
+                                                        const float *sm, int q, int x0, int y0,
+                                                        int z, int tx, int ty) {
     const int x = x0 + tx, y = y0 + ty;
     if (x >= L.nx || y >= L.ny) return;
     const int nc = L.ncell;
@@ -929,32 +950,38 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
     }
     const bool inlet_face = L.bc_x == 1 && x == 0, outlet_face = L.bc_x == 1 && x == L.nx - 1;
     const int oc = (ty + 1) * HOME_HX + (tx + 1);
-    const float *own = sm + s_0 * HOME_SLOT;
+    // pulled direction i comes from plane q - c_z; the own cell's from plane q
+    const int in_q = home_in_base(q) + oc, up_qm = home_up_base(q - 1) + oc,
+              dn_qp = home_dn_base(q + 1) + oc;
+    const int up_q = home_up_base(q) + oc, dn_q = home_dn_base(q) + oc;
     float g[19];
     if (lk == 0u && !inlet_face && !outlet_face) {
         // no solid neighbour, no open face: every population comes from the ring
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
-            const int sl = cz == 1 ? s_m : (cz == -1 ? s_p : s_0);  // source plane z - c_z
-            g[i] = sm[sl * HOME_SLOT + i * HOME_PLANE + oc - cy * HOME_HX - cx];
+            const int b = cz == 0 ? in_q : (cz == 1 ? up_qm : dn_qp);
+            g[i] = sm[b + home_k(i) * HOME_PLANE - cy * HOME_HX - cx];
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = D3Q19::cx(i), cy = D3Q19::cy(i), cz = D3Q19::cz(i);
-            const int jo = D3Q19::opp(i);
+            const int jo = D3Q19::opp(i), czo = D3Q19::cz(jo);
+            const int own_i = (cz == 0 ? in_q : (cz == 1 ? up_q : dn_q)) + home_k(i) * HOME_PLANE;
+            const int own_jo =
+                (czo == 0 ? in_q : (czo == 1 ? up_q : dn_q)) + home_k(jo) * HOME_PLANE;
             if (i == 0) {
-                g[i] = own[oc];
+                g[i] = sm[own_i];
             } else if (inlet_face && cx == 1) {
                 g[i] = H.g_in[i];
             } else if (outlet_face && cx == -1) {
-                g[i] = own[i * HOME_PLANE + oc];
+                g[i] = sm[own_i];
             } else if ((lk >> jo) & 1u) {
-                g[i] = own[jo * HOME_PLANE + oc];  // halfway bounce-back
+                g[i] = sm[own_jo];  // halfway bounce-back
             } else {
-                const int sl = cz == 1 ? s_m : (cz == -1 ? s_p : s_0);
-                g[i] = sm[sl * HOME_SLOT + i * HOME_PLANE + oc - cy * HOME_HX - cx];
+                const int b = cz == 0 ? in_q : (cz == 1 ? up_qm : dn_qp);
+                g[i] = sm[b + home_k(i) * HOME_PLANE - cy * HOME_HX - cx];
             }
         }
     }
@@ -986,7 +1013,7 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
 // ceil(nz/tz)), 256 threads, HOME_SMEM bytes of dynamic shared memory.
 // The moments of plane z + 2 and the link words of plane z + 1 are loaded
 // while plane z is pulled and collided, so their latency overlaps the work.
-__global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
+__global__ void __launch_bounds__(256, 3) k_home_step(LbmParams L, HomeParams H,
                                                   const float *__restrict__ m_in,
                                                   float *__restrict__ mout,
                                                   const uint8_t *__restrict__ solid,
@@ -1003,22 +1030,22 @@ __global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
     const int col = (y0 + ty) * L.nx + (x0 + tx), plane = L.nx * L.ny;
     const int xy0 = home_halo_xy(L, x0, y0, c0), xy1 = two ? home_halo_xy(L, x0, y0, c1) : -1;
     HomeHalo h0, h1;
+    // planes z0 - 1 and z0 (q = 0, 1), then plane z0 + 1 loaded ahead
     home_halo_load(L, m_in, solid, xy0, home_wrap_z(L, z0 - 1), h0);
     if (two) home_halo_load(L, m_in, solid, xy1, home_wrap_z(L, z0 - 1), h1);
-    home_halo_store(h0, home_sm, c0);
-    if (two) home_halo_store(h1, home_sm, c1);
+    home_halo_store(h0, home_sm, 0, c0);
+    if (two) home_halo_store(h1, home_sm, 0, c1);
     home_halo_load(L, m_in, solid, xy0, z0, h0);
     if (two) home_halo_load(L, m_in, solid, xy1, z0, h1);
-    home_halo_store(h0, home_sm + HOME_SLOT, c0);
-    if (two) home_halo_store(h1, home_sm + HOME_SLOT, c1);
+    home_halo_store(h0, home_sm, 1, c0);
+    if (two) home_halo_store(h1, home_sm, 1, c1);
     home_halo_load(L, m_in, solid, xy0, home_wrap_z(L, z0 + 1), h0);
     if (two) home_halo_load(L, m_in, solid, xy1, home_wrap_z(L, z0 + 1), h1);
     uint32_t lk_next = (links && inside) ? links[z0 * plane + col] : 0u;
     for (int z = z0; z < z1; ++z) {
-        const int r = z - z0;
-        const int s_m = r % 3, s_0 = (r + 1) % 3, s_p = (r + 2) % 3;
-        home_halo_store(h0, home_sm + s_p * HOME_SLOT, c0);
-        if (two) home_halo_store(h1, home_sm + s_p * HOME_SLOT, c1);
+        const int q = z - z0 + 1;
+        home_halo_store(h0, home_sm, q + 1, c0);
+        if (two) home_halo_store(h1, home_sm, q + 1, c1);
         if (z + 1 < z1) {  // plane z + 2 is the next iteration's z + 1
             const int gz = home_wrap_z(L, z + 2);
             home_halo_load(L, m_in, solid, xy0, gz, h0);
@@ -1027,7 +1054,7 @@ __global__ void __launch_bounds__(256, 2) k_home_step(LbmParams L, HomeParams H,
         const uint32_t lk = lk_next;
         if (links && inside && z + 1 < z1) lk_next = links[(z + 1) * plane + col];
         __syncthreads();
-        home_tile_cell(L, H, m_in, mout, lk, home_sm, s_m, s_0, s_p, x0, y0, z, tx, ty);
+        home_tile_cell(L, H, m_in, mout, lk, home_sm, q, x0, y0, z, tx, ty);
         __syncthreads();
     }
 }
