@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch",
-                                                    "batch_adjoint", "inversion"],
+                                                    "batch_adjoint", "inversion", "gsplat"],
                     help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
                          "or the checkpointed MPM adjoint")
     ap.add_argument("--batch-scenes", type=int, default=64,
@@ -663,6 +663,38 @@ def bench_inversion(dev, iters=40):
     return out
 
 
+def bench_gsplat(dev):
+    """Particle-bound Gaussian splatting: the 100,284-particle sheet (64^3
+    case) drawn at 512 x 512, forward (covariance update, projection, depth
+    sort, tile compositing) and reverse mode (down to dL/dx and dL/dF)."""
+    import torch
+
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300 import inputs
+
+    sc = inputs.sheet_scene(nu=274, nv=183, n_grid=64, n_substeps=1, seed=0)
+    n = sc.n
+    g = np.random.default_rng(7)
+    F = np.zeros((9, n), np.float32)
+    F[[0, 4, 8]] = 1.0
+    F += g.uniform(-0.05, 0.05, (9, n)).astype(np.float32)
+    s0 = np.zeros((6, n), np.float32)
+    s0[:3] = 0.003 ** 2
+    arrs = [torch.from_numpy(a).to(dev) for a in
+            (sc.x, F, s0, g.uniform(0, 1, (3, n)).astype(np.float32),
+             g.uniform(0.3, 0.9, n).astype(np.float32))]
+    cam = B.camera(np.eye(3), (-0.5, -0.6, 1.2), 600.0, 600.0, 256.0, 256.0, 512, 512)
+    r = B.GaussianRenderer(n, 512, 512)
+    img = torch.empty((3, 512, 512), device=dev)
+    g_img = torch.randn((3, 512, 512), device=dev)
+    g_x, g_F = torch.zeros_like(arrs[0]), torch.zeros_like(arrs[1])
+    fwd_ms = _timed(lambda: r.render(cam, *arrs, image=img))
+    bwd_ms = _timed(lambda: r.backward(cam, *arrs, g_img, g_x, g_F))
+    r.close()
+    return {"gs_sheet100k_512_fwd_ms": fwd_ms, "gs_sheet100k_512_bwd_ms": bwd_ms,
+            "gs_gaussians": n}
+
+
 def extras(dev):
     out = bench_lbm(dev)
     out.update(bench_adjoint(dev))
@@ -670,6 +702,7 @@ def extras(dev):
     out.update(bench_batch(dev))
     out.update(bench_batch_adjoint(dev))
     out.update(bench_inversion(dev))
+    out.update(bench_gsplat(dev))
     return out
 
 
@@ -747,6 +780,8 @@ def run_only(args):
         res = bench_batch_adjoint(dev, n_scenes=args.batch_scenes)
     elif args.only == "inversion":
         res = bench_inversion(dev)
+    elif args.only == "gsplat":
+        res = bench_gsplat(dev)
     else:
         res = bench_adjoint(dev)
     print(json.dumps({"only": args.only, **res}), flush=True)
@@ -756,7 +791,8 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.only in ("lbm", "adjoint", "surrogate", "batch", "batch_adjoint", "inversion"):
+    elif a.only in ("lbm", "adjoint", "surrogate", "batch", "batch_adjoint", "inversion",
+                    "gsplat"):
         run_only(a)
     else:
         run_ours(a)

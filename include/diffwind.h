@@ -300,6 +300,68 @@ DW_API dw_status vector_adam_step(float *param, const float *grad, float *m, flo
                                   float lr, float beta1, float beta2, float eps, int32_t step,
                                   dw_stream stream);
 
+/* ================================================ particle-bound Gaussians
+ * The object's 3D Gaussians ride on MPM particles (Sec. 3.2): the covariance
+ * of particle p follows its deformation gradient, Sigma_p(t) = F_p Sigma_p
+ * F_p^T, and the object is drawn by alpha-blended splatting (Sec. 3.3, Eq.
+ * rendering; the 3D Gaussian representation): with t = R x + T the camera-
+ * space centre, mu' = (fx t_x/t_z + cx, fy t_y/t_z + cy), J the Jacobian of
+ * that projection at t, Sigma' = J R Sigma R^T J^T, each pixel centre p
+ * (pixel (i, j) at (i + 1/2, j + 1/2)) gets C = sum_i T_i c_i alpha_i over the
+ * Gaussians in increasing t_z (ties by index), T_i = prod_{j<i} (1 -
+ * alpha_j), alpha_i = o_i exp(-q/2) for q = (p - mu')^T Sigma'^-1 (p - mu') <=
+ * 9 (three standard deviations) and 0 beyond; Gaussians with t_z <= near or
+ * a singular Sigma' are not drawn; no background term. Layouts: x [3][n], F
+ * [9][n] (row-major per particle, as dw_mpm_state), covariances [6][n] as
+ * (xx, yy, zz, xy, xz, yz), colours [3][n], opacities [n], images [3][H][W].
+ */
+typedef struct {
+    float R[9];     /* world -> camera rotation, row-major */
+    float T[3];     /* world -> camera translation */
+    float fx, fy;   /* focal lengths in pixels, > 0 */
+    float cx, cy;   /* principal point in pixels */
+    int32_t width, height;
+    float near_z;   /* Gaussians with t_z <= near_z are not drawn; > 0 */
+} dw_camera;
+
+typedef struct dw_gs_s *dw_gs;
+
+/* sigma [6][n] = F sigma0 F^T per particle (device arrays). */
+DW_API dw_status gs_covariance(const float *F, const float *sigma0, int64_t n, float *sigma,
+                               dw_stream stream);
+
+/* Renderer workspace for up to max_gaussians Gaussians and width x height
+ * images (about 100 bytes per Gaussian plus one image). */
+DW_API dw_status gs_create(int64_t max_gaussians, int32_t width, int32_t height, dw_gs *out);
+DW_API dw_status gs_destroy(dw_gs h);
+
+/* image (device [3][H][W], overwritten) of n Gaussians at the particles x
+ * with deformation gradients F and rest covariances sigma0. The handle keeps
+ * the projected Gaussians, their depth order and the image for
+ * gs_render_backward. cam's image size must be the handle's. */
+DW_API dw_status gs_render(dw_gs h, const dw_camera *cam, const float *x, const float *F,
+                           const float *sigma0, const float *color, const float *opacity,
+                           int64_t n, float *image, dw_stream stream);
+
+/* Reverse mode of the last gs_render, which must have drawn the same inputs:
+ * given g_image = dL/d(image), accumulates dL/dx into g_x [3][n] and dL/dF
+ * into g_F [9][n] (the MPM adjoint's inputs for the final state), and, when
+ * not NULL, dL/d(color) into g_color [3][n] and dL/d(opacity) into g_opacity
+ * [n]. The pixel rule q <= 9 makes the image piecewise smooth; the gradient
+ * is that of the smooth piece. DW_ERR_ARG when n differs from the last
+ * gs_render. */
+DW_API dw_status gs_render_backward(dw_gs h, const dw_camera *cam, const float *x, const float *F,
+                                    const float *sigma0, const float *color,
+                                    const float *opacity, int64_t n, const float *g_image,
+                                    float *g_x, float *g_F, float *g_color, float *g_opacity,
+                                    dw_stream stream);
+
+/* The L1 term of the photometric loss (Sec. 3.3): loss (device float,
+ * accumulated) += weight sum |image - target| over n values; g_image (device,
+ * accumulated, may be NULL) += weight sign(image - target). */
+DW_API dw_status image_l1_loss(const float *image, const float *target, int64_t n, float weight,
+                               float *loss, float *g_image, dw_stream stream);
+
 /* ============================================================ batched MPM
  * Many independent scenes, each with its own grid size, material, time step,
  * particle count and wind field, advanced by the same substep as mpm_rollout

@@ -65,7 +65,7 @@ def camera(R, T, fx, fy, cx, cy, width, height, near=0.01):
                 height=int(height), near=float(near))
 
 
-def _render(x, F, s0, color, opacity, cam):
+def _render(x, F, s0, color, opacity, cam, pixels=None, want_q=False):
     n = x.shape[1]
     R = torch.as_tensor(cam["R"], dtype=DT)
     T = torch.as_tensor(cam["T"], dtype=DT)
@@ -91,11 +91,17 @@ def _render(x, F, s0, color, opacity, cam):
     cc = S2[:, 0, 0] / dets
     mux = fx * tx / tzs + cx
     muy = fy * ty / tzs + cy
-    py, px = torch.meshgrid(torch.arange(H, dtype=DT) + 0.5, torch.arange(W, dtype=DT) + 0.5,
-                            indexing="ij")
+    if pixels is None:
+        py, px = torch.meshgrid(torch.arange(H, dtype=DT) + 0.5, torch.arange(W, dtype=DT) + 0.5,
+                                indexing="ij")
+    else:
+        pix = torch.as_tensor(np.asarray(pixels), dtype=DT)
+        px, py = pix[:, 0] + 0.5, pix[:, 1] + 0.5
     dx = px.reshape(-1, 1) - mux.reshape(1, -1)
     dy = py.reshape(-1, 1) - muy.reshape(1, -1)
     q = ca * dx * dx + 2 * cb * dx * dy + cc * dy * dy
+    if want_q:
+        return torch.where(vis.reshape(1, -1), q, torch.full_like(q, float("inf")))
     inside = ((q <= 9.0) & vis.reshape(1, -1)).detach()
     alpha = torch.where(inside, opacity.reshape(1, -1) * torch.exp(-0.5 * q),
                         torch.zeros_like(q))
@@ -105,7 +111,7 @@ def _render(x, F, s0, color, opacity, cam):
     trans = torch.cumprod(torch.cat([torch.ones(a.shape[0], 1, dtype=DT), 1 - a[:, :-1]], 1), 1)
     wgt = trans * a  # (HW, n)
     img = wgt @ color.T[order]  # (HW, 3)
-    return img.T.reshape(3, H, W)
+    return img.T.reshape(3, H, W) if pixels is None else img.T
 
 
 def _tensors(x, F, sigma0, color, opacity, grad=False):
@@ -113,11 +119,23 @@ def _tensors(x, F, sigma0, color, opacity, grad=False):
             for a in (x, F, sigma0, color, opacity)]
 
 
-def render(x, F, sigma0, color, opacity, cam):
+def render(x, F, sigma0, color, opacity, cam, pixels=None):
     """Image [3][H][W] of Gaussians at x [3][n] with F [9][n], rest
-    covariances sigma0 [6][n], colours [3][n] and opacities [n]."""
+    covariances sigma0 [6][n], colours [3][n] and opacities [n]; or, with
+    pixels (m, 2) integer (px, py), the colours [3][m] of those pixels."""
     with torch.no_grad():
-        return _render(*_tensors(x, F, sigma0, color, opacity), cam).numpy()
+        return _render(*_tensors(x, F, sigma0, color, opacity), cam, pixels).numpy()
+
+
+def near_cutoff(x, F, sigma0, cam, tol, pixels=None):
+    """Mask ([H*W] or [m]) of the pixels where some drawn Gaussian has its
+    Mahalanobis q within tol of the cut-off 9: there the in-or-out decision
+    depends on rounding, so a float32 renderer may decide otherwise."""
+    n = np.asarray(x).shape[1]
+    t = _tensors(x, F, sigma0, np.zeros((3, n)), np.zeros(n))
+    with torch.no_grad():
+        q = _render(*t, cam, pixels, want_q=True)
+    return (torch.abs(q - 9.0) < tol).any(dim=1).numpy()
 
 
 def render_grad(x, F, sigma0, color, opacity, cam, g_image):

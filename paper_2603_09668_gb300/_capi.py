@@ -50,6 +50,12 @@ class DwLbmDesc(ct.Structure):
                 ("max_tape", ct.c_int32)]
 
 
+class DwCamera(ct.Structure):
+    _fields_ = [("R", ct.c_float * 9), ("T", ct.c_float * 3), ("fx", ct.c_float),
+                ("fy", ct.c_float), ("cx", ct.c_float), ("cy", ct.c_float),
+                ("width", ct.c_int32), ("height", ct.c_int32), ("near_z", ct.c_float)]
+
+
 P = ct.POINTER
 VP = ct.c_void_p
 I32 = ct.c_int32
@@ -105,6 +111,13 @@ SIGNATURES = {
     "wind_field_scores": (I32, [VP, VP, I64, F32, VP, VP]),
     "adam_step": (I32, [VP, VP, VP, VP, I64, F32, F32, F32, F32, I32, VP]),
     "wind_drag_force": (I32, [VP, I64, F32, VP, VP]),
+    "gs_covariance": (I32, [VP, VP, I64, VP, VP]),
+    "gs_create": (I32, [I64, I32, I32, P(VP)]),
+    "gs_destroy": (I32, [VP]),
+    "gs_render": (I32, [VP, P(DwCamera), VP, VP, VP, VP, VP, I64, VP, VP]),
+    "gs_render_backward": (I32, [VP, P(DwCamera), VP, VP, VP, VP, VP, I64, VP, VP, VP, VP, VP,
+                                 VP]),
+    "image_l1_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
     "vector_adam_step": (I32, [VP, VP, VP, VP, I64, F32, F32, F32, F32, I32, VP]),
     "position_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
     "surr_create": (I32, [I32, P(VP)]),

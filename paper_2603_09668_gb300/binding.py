@@ -12,9 +12,10 @@ from __future__ import annotations
 import ctypes as ct
 from typing import NamedTuple, Optional
 
+import numpy as np
 import torch
 
-from ._capi import (DiffWindError, DwBatchConfig, DwBatchTrial, DwLbmDesc, DwMpmDesc, DwMpmScene,
+from ._capi import (DiffWindError, DwCamera, DwBatchConfig, DwBatchTrial, DwLbmDesc, DwMpmDesc, DwMpmScene,
                     DwMpmState, DwWindField, check, lib)
 
 __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
@@ -24,7 +25,8 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "lbm_home_init", "lbm_home_step", "lbm_home_macroscopic",
            "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
-           "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "vector_adam_step", "MPM", "LBM", "surr_create",
+           "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "vector_adam_step", "camera",
+           "gs_covariance", "image_l1_loss", "GaussianRenderer", "MPM", "LBM", "surr_create",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
@@ -463,6 +465,77 @@ def vector_adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e
                                  float(beta1), float(beta2), float(eps), int(step),
                                  _stream(stream)))
     return param
+
+
+# ---------------------------------------------------- particle-bound Gaussians --
+
+def camera(R, T, fx, fy, cx, cy, width, height, near=0.01) -> DwCamera:
+    """A pinhole camera: t = R x + T, pixel = (fx t_x/t_z + cx, fy t_y/t_z + cy)."""
+    R = [float(v) for v in np.asarray(R, np.float64).reshape(9)]
+    T = [float(v) for v in np.asarray(T, np.float64).reshape(3)]
+    return DwCamera((ct.c_float * 9)(*R), (ct.c_float * 3)(*T), float(fx), float(fy), float(cx),
+                    float(cy), int(width), int(height), float(near))
+
+
+def gs_covariance(F, sigma0, sigma=None, stream=None):
+    """sigma [6][n] = F sigma0 F^T (F [9][n], sigma0 [6][n])."""
+    n = F.shape[1]
+    if sigma is None:
+        sigma = torch.empty((6, n), dtype=torch.float32, device=F.device)
+    check(lib().gs_covariance(_dev(F, name="F"), _dev(sigma0, name="sigma0"), int(n),
+                              _dev(sigma, name="sigma"), _stream(stream)))
+    return sigma
+
+
+def image_l1_loss(image, target, loss, weight=1.0, g_image=None, stream=None):
+    """loss += weight sum |image - target|; g_image += weight sign(image - target)."""
+    check(lib().image_l1_loss(_dev(image, name="image"), _dev(target, name="target"),
+                              int(image.numel()), float(weight), _dev(loss, name="loss"),
+                              _dev(g_image, name="g_image"), _stream(stream)))
+    return loss
+
+
+class GaussianRenderer:
+    """Owns a gs handle: alpha-blended splatting of particle-bound Gaussians
+    and its reverse mode (gs_render, gs_render_backward)."""
+
+    def __init__(self, max_gaussians, width, height):
+        self.width, self.height = int(width), int(height)
+        h = ct.c_void_p()
+        check(lib().gs_create(int(max_gaussians), self.width, self.height, ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lib().gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, cam, x, F, sigma0, color, opacity, image=None, stream=None):
+        n = x.shape[1]
+        if image is None:
+            image = torch.empty((3, self.height, self.width), dtype=torch.float32, device=x.device)
+        check(lib().gs_render(self.h, ct.byref(cam), _dev(x, name="x"), _dev(F, name="F"),
+                              _dev(sigma0, name="sigma0"), _dev(color, name="color"),
+                              _dev(opacity, name="opacity"), int(n), _dev(image, name="image"),
+                              _stream(stream)))
+        return image
+
+    def backward(self, cam, x, F, sigma0, color, opacity, g_image, g_x, g_F, g_color=None,
+                 g_opacity=None, stream=None):
+        n = x.shape[1]
+        check(lib().gs_render_backward(self.h, ct.byref(cam), _dev(x, name="x"),
+                                       _dev(F, name="F"), _dev(sigma0, name="sigma0"),
+                                       _dev(color, name="color"), _dev(opacity, name="opacity"),
+                                       int(n), _dev(g_image, name="g_image"), _dev(g_x, name="g_x"),
+                                       _dev(g_F, name="g_F"), _dev(g_color, name="g_color"),
+                                       _dev(g_opacity, name="g_opacity"), _stream(stream)))
+        return g_x, g_F
 
 
 def voxelize_particles(pos, shape, dx, solid, stream=None):

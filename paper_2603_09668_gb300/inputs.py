@@ -252,6 +252,41 @@ def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, 
                 inlet_error_deg=inlet_error_deg)
 
 
+def gaussian_scene(n=300, width=61, height=47, depth_ties=False, seed=0):
+    """Particle-bound Gaussians for the renderer: centres uniform in a 0.8
+    box, deformation gradients I + U[-0.15, 0.15] per entry, rest covariances
+    with standard deviations in [0.01, 0.04] along random axes, colours U[0, 1],
+    opacities U[0.2, 0.95]. The camera looks at the box from 2.2 units,
+    rotated 0.3 rad about (0.2, 1, 0.1), focal length 0.9 width. With
+    depth_ties the camera is not rotated and every fourth Gaussian copies the
+    z of its predecessor, so that the depth keys tie exactly in any precision
+    (the order is then the index order). Returns (x, F, sigma0, color,
+    opacity, camera dict), arrays float32."""
+    g = rng(seed)
+    x = g.uniform(-0.4, 0.4, (3, n))
+    F = g.uniform(-0.15, 0.15, (9, n))
+    F[[0, 4, 8]] += 1.0
+    sig = np.zeros((6, n))
+    for p in range(n):
+        q, _ = np.linalg.qr(g.standard_normal((3, 3)))
+        S = q @ np.diag(g.uniform(0.01, 0.04, 3) ** 2) @ q.T
+        sig[:, p] = [S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[0, 2], S[1, 2]]
+    if depth_ties:
+        R = np.eye(3)
+        x[2, 4::4] = x[2, 3:-1:4][: len(x[2, 4::4])]
+    else:
+        a = np.array([0.2, 1.0, 0.1]) / np.linalg.norm([0.2, 1.0, 0.1])
+        K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        R = np.eye(3) + np.sin(0.3) * K + (1 - np.cos(0.3)) * K @ K
+    T = np.array([0.0, 0.0, 2.2])
+    color = g.uniform(0.0, 1.0, (3, n))
+    opacity = g.uniform(0.2, 0.95, n)
+    cam = dict(R=R, T=T, fx=0.9 * width, fy=0.9 * width, cx=width / 2, cy=height / 2,
+               width=width, height=height)
+    f32 = lambda a: np.ascontiguousarray(a.astype(np.float32))
+    return f32(x), f32(F), f32(sig), f32(color), f32(opacity), cam
+
+
 def batch_scenes(n_scenes=64, n_lo=20000, n_hi=400000, n_substeps=500, seed=0):
     """Uneven multi-scene batch: particle counts log-uniform in [n_lo, n_hi],
     grid 64^3 or 128^3, sheet or block, each with its own 16^3 x 8 wind."""

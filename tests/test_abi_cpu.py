@@ -58,6 +58,7 @@ int main(void) {
   printf("%zu %zu\\n", sizeof(dw_mpm_state), offsetof(dw_mpm_state, n));
   printf("%zu %zu\\n", sizeof(dw_wind_field), offsetof(dw_wind_field, t_total));
   printf("%zu %zu %zu\\n", sizeof(dw_lbm_desc), offsetof(dw_lbm_desc, bc_x), offsetof(dw_lbm_desc, max_tape));
+  printf("%zu %zu %zu\\n", sizeof(dw_camera), offsetof(dw_camera, width), offsetof(dw_camera, near_z));
   return 0;
 }
 """)
@@ -73,6 +74,8 @@ int main(void) {
     assert lines[2].split() == [str(ct.sizeof(w)), str(w.t_total.offset)]
     lb = _capi.DwLbmDesc
     assert lines[3].split() == [str(ct.sizeof(lb)), str(lb.bc_x.offset), str(lb.max_tape.offset)]
+    cm = _capi.DwCamera
+    assert lines[4].split() == [str(ct.sizeof(cm)), str(cm.width.offset), str(cm.near_z.offset)]
 
 
 def test_version_and_error_string_without_gpu(libpath):

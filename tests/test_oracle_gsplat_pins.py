@@ -97,6 +97,19 @@ def test_two_gaussians_composite_front_to_back():
     assert not back.any()
 
 
+def test_pixel_subset_matches_the_full_image():
+    rng = np.random.default_rng(2)
+    n, W, H = 7, 20, 14
+    cam = G.camera(np.eye(3), np.array([0.0, 0.0, 2.0]), 25.0, 25.0, 10, 7, W, H)
+    x = rng.uniform(-0.3, 0.3, (3, n))
+    s0 = iso6(n, 0.06 ** 2)
+    col, op = rng.uniform(0, 1, (3, n)), rng.uniform(0.2, 0.9, n)
+    img = G.render(x, eye9(n), s0, col, op, cam)
+    pix = np.stack([rng.integers(0, W, 30), rng.integers(0, H, 30)], 1)
+    sub = G.render(x, eye9(n), s0, col, op, cam, pixels=pix)
+    assert np.allclose(sub, img[:, pix[:, 1], pix[:, 0]], atol=1e-15)
+
+
 def test_l1_loss():
     a = np.array([[0.5, 0.25], [1.0, 0.0]])
     b = np.array([[0.0, 0.5], [1.0, 0.5]])
