@@ -117,7 +117,7 @@ def test_l1_loss_and_edge_cases():
     img = r.render(cam, e, torch.zeros((9, 0), device="cuda"), torch.zeros((6, 0), device="cuda"),
                    e, torch.zeros(0, device="cuda"))
     assert not img.any()
-    x = torch.tensor([[0.0], [0.0], [-1.0]], device="cuda")  # behind the camera
+    x = torch.tensor([[0.0], [0.0], [-3.0]], device="cuda")  # t_z = -1: behind the camera
     F = torch.eye(3, device="cuda").reshape(9, 1)
     s0 = torch.tensor([[0.01], [0.01], [0.01], [0.0], [0.0], [0.0]], device="cuda")
     c1, o1 = torch.ones((3, 1), device="cuda"), torch.ones(1, device="cuda")
