@@ -233,6 +233,16 @@ def sheet_scene(nu=548, nv=365, n_grid=128, n_substeps=1000, dt=5e-5, wind_nf=32
                  wind, t_total, n_substeps=n_substeps)
 
 
+def sheet_texture(x, cell=0.05):
+    """Colours [3][n] of a checkerboard of `cell`-sized squares over the rest
+    positions x [3][n] (x-y plane): 0.85 / 0.2 per square, a different tint
+    per channel."""
+    sq = (np.floor(x[0] / cell) + np.floor(x[1] / cell)).astype(np.int64) % 2
+    base = np.where(sq == 1, 0.85, 0.2)
+    tint = np.array([1.0, 0.8, 0.6])[:, None]
+    return np.ascontiguousarray((tint * base[None, :]).astype(np.float32))
+
+
 def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, dt=2e-4,
                    every=25, n_cells=32, lbm_steps=30, inlet_error_deg=10.0, seed=0):
     """Synthetic wind-inversion case: the flag-like sheet (pinned edge, E=5e4)
@@ -247,7 +257,7 @@ def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, 
                      wind_frames=1, seed=seed)
     d = np.array([1.0, 0.0, 0.35])
     u_in = tuple(float(c) for c in 0.05 * d / np.linalg.norm(d))
-    return dict(scene=sc, nf=nf, n_intervals=n_intervals, substeps=substeps, every=every,
+    return dict(scene=sc, nu=nu, nf=nf, n_intervals=n_intervals, substeps=substeps, every=every,
                 n_cells=n_cells, tau=0.6, u_inlet=u_in, drag_scale=4000.0, lbm_steps=lbm_steps,
                 inlet_error_deg=inlet_error_deg)
 

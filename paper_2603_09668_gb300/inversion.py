@@ -23,8 +23,11 @@ The update is VectorAdam by default: per-component Adam moves every
 component of every node by about the learning rate whatever its gradient's
 size, which scrambles the per-node directions the evaluation scores; plain
 Adam stays available (optimizer="adam").
-The observed positions stand in for the rendered views of L_render, which
-needs the Gaussian renderer.
+The data term is either the squared distance to observed particle positions
+or, with a Gaussian renderer and cameras (RenderObservation), L_render's L1
+term between the particle-bound Gaussians drawn from the simulated state
+and the observed images, its gradient taken through the renderer
+(gs_render_backward) into the MPM adjoint's dL/dx and dL/dF.
 """
 from __future__ import annotations
 
@@ -95,6 +98,38 @@ def simulate_wind_driven(mpm: B.MPM, guide: LbmGuide, state: B.MpmState, pinned,
 
 
 @dataclass
+class RenderObservation:
+    """Views of the particle-bound Gaussians: one renderer, its cameras, the
+    Gaussians' rest covariances [6][n], colours [3][n] and opacities [n]."""
+    renderer: B.GaussianRenderer
+    cameras: list
+    sigma0: torch.Tensor
+    color: torch.Tensor
+    opacity: torch.Tensor
+
+    def images(self, state: B.MpmState) -> torch.Tensor:
+        """[n_views][3][H][W] images of the state."""
+        r = self.renderer
+        out = torch.empty((len(self.cameras), 3, r.height, r.width), dtype=torch.float32,
+                          device=state.x.device)
+        for v, cam in enumerate(self.cameras):
+            r.render(cam, state.x, state.F, self.sigma0, self.color, self.opacity, out[v])
+        return out
+
+    def loss(self, state: B.MpmState, target: torch.Tensor, weight: float, loss: torch.Tensor,
+             g: B.MpmState, scratch: torch.Tensor):
+        """loss += weight sum over views of |image - target|; g.x and g.F +=
+        its gradient (each view drawn, then differentiated right away)."""
+        r = self.renderer
+        for v, cam in enumerate(self.cameras):
+            r.render(cam, state.x, state.F, self.sigma0, self.color, self.opacity, scratch[0])
+            scratch[1].zero_()
+            B.image_l1_loss(scratch[0], target[v], loss, weight, scratch[1])
+            r.backward(cam, state.x, state.F, self.sigma0, self.color, self.opacity, scratch[1],
+                       g.x, g.F)
+
+
+@dataclass
 class InversionResult:
     values: torch.Tensor   # [n_intervals][nf^3][3] reconstructed force per interval
     history: torch.Tensor  # [n_intervals][iters][2]: (data term, lambda * L_phys) per iteration
@@ -124,13 +159,21 @@ class WindInversion:
         self.lr, self.lam_phys, self.w_data, self.eps_guide = lr, lam_phys, w_data, eps_guide
 
     def reconstruct(self, state0: B.MpmState, pinned, x_observed: torch.Tensor,
-                    lbm_steps: int, t0: float = 0.0) -> InversionResult:
-        """x_observed [n_intervals][3][n]: the positions at the end of each
-        interval. state0 is not modified."""
+                    lbm_steps: int, t0: float = 0.0,
+                    views: Optional[RenderObservation] = None) -> InversionResult:
+        """x_observed: the observation at the end of each interval, positions
+        [n_intervals][3][n], or with views the images [n_intervals][n_views][3]
+        [H][W] (then w_data defaults to 1 / (3 H W), the mean L1 per view).
+        state0 is not modified."""
         mpm, guide, nf = self.mpm, self.guide, self.guide.nf
         dev = state0.x.device
         n, K, S, every = state0.n, x_observed.shape[0], self.substeps, self.every
-        w_data = self.w_data if self.w_data is not None else mpm.n_grid ** 2 / max(n, 1)
+        if views is None:
+            w_data = self.w_data if self.w_data is not None else mpm.n_grid ** 2 / max(n, 1)
+        else:
+            r = views.renderer
+            w_data = self.w_data if self.w_data is not None else 1.0 / (3 * r.width * r.height)
+            scratch = torch.empty((2, 3, r.height, r.width), dtype=torch.float32, device=dev)
         segs = [(k0, min(S, k0 + every)) for k0 in range(0, S, every)]
 
         values = torch.zeros((K, nf ** 3, 3), dtype=torch.float32, device=dev)
@@ -166,7 +209,10 @@ class WindInversion:
                 for a in g:
                     a.zero_()
                 g_values.zero_()
-                B.position_loss(run.x, x_observed[k], history[k, it, 0:1], w_data, g.x)
+                if views is None:
+                    B.position_loss(run.x, x_observed[k], history[k, it, 0:1], w_data, g.x)
+                else:
+                    views.loss(run, x_observed[k], w_data, history[k, it, 0:1], g, scratch)
                 for (k0, k1), ck in zip(reversed(segs), reversed(ckpts)):
                     mpm.segment_adjoint(ck, tape, g, pinned, wind, t + k0 * mpm.dt, k1 - k0,
                                         g_values.view(1, nf, nf, nf, 3))
@@ -235,14 +281,61 @@ def prepare_synthetic(case: dict, device="cuda") -> SyntheticCase:
     return SyntheticCase(mpm, state0, pinned, gt_forces, x_obs, guide)
 
 
+def sheet_views(case: dict, state0: B.MpmState, width: int = 128, height: int = 128):
+    """Two views of the case's sheet (front, and 0.6 rad about y) with
+    particle-bound Gaussians of the lattice spacing's size and a checkerboard
+    of colours over the rest positions (texture makes motion visible)."""
+    from .inputs import sheet_texture
+
+    sc = case["scene"]
+    dev = state0.x.device
+    h = 0.6 / (case["nu"] - 1)  # the sheet's lattice spacing
+    sigma0 = torch.zeros((6, sc.n), dtype=torch.float32, device=dev)
+    sigma0[:3] = h * h
+    color = torch.from_numpy(sheet_texture(sc.x)).to(dev)
+    opacity = torch.full((sc.n,), 0.9, dtype=torch.float32, device=dev)
+    centre = np.array([0.5, 0.6, 0.5])
+    f = 1.25 * width
+    cams = []
+    for ang in (0.0, 0.6):
+        R = np.array([[np.cos(ang), 0.0, np.sin(ang)], [0.0, 1.0, 0.0],
+                      [-np.sin(ang), 0.0, np.cos(ang)]])
+        T = np.array([0.0, 0.0, 1.5]) - R @ centre
+        cams.append(B.camera(R, T, f, f, width / 2, height / 2, width, height))
+    r = B.GaussianRenderer(sc.n, width, height)
+    return RenderObservation(r, cams, sigma0, color, opacity)
+
+
 def run_synthetic(case: dict, iters: int = 40, lr: float = 1.0, lam_phys: float = 0.1,
-                  device="cuda", optimizer="vector_adam"):
-    """prepare_synthetic, then the inversion from the same initial state.
-    Returns a dict with the ground truth, the InversionResult and the scores."""
+                  device="cuda", optimizer="vector_adam", observe: str = "positions",
+                  w_data: Optional[float] = None):
+    """prepare_synthetic, then the inversion from the same initial state,
+    observing the particle positions or (observe="render") two rendered
+    views of the ground-truth states. Returns a dict with the ground truth,
+    the InversionResult and the scores."""
     syn = prepare_synthetic(case, device)
     inv = WindInversion(syn.mpm, syn.guide, case["substeps"], case["every"], iters, lr, lam_phys,
-                        optimizer=optimizer)
-    res = inv.reconstruct(syn.state0, syn.pinned, syn.x_obs, case["lbm_steps"])
+                        w_data=w_data, optimizer=optimizer)
+    if observe == "render":
+        views = sheet_views(case, syn.state0)
+        K = syn.x_obs.shape[0]
+        obs = torch.empty((K, len(views.cameras), 3, views.renderer.height, views.renderer.width),
+                          dtype=torch.float32, device=syn.state0.x.device)
+        # the observed images: the ground-truth states at the interval ends (F from a re-run)
+        st = syn.state0.clone()
+        nf = syn.guide.nf
+        t = 0.0
+        for k in range(K):
+            wind = _wind(syn.gt_forces[k].view(1, nf, nf, nf, 3))
+            syn.mpm.rollout(st, syn.pinned, None, wind, t, case["substeps"], 0)
+            t += case["substeps"] * syn.mpm.dt
+            obs[k] = views.images(st)
+        res = inv.reconstruct(syn.state0, syn.pinned, obs, case["lbm_steps"], views=views)
+        views.renderer.close()
+    elif observe == "positions":
+        res = inv.reconstruct(syn.state0, syn.pinned, syn.x_obs, case["lbm_steps"])
+    else:
+        raise ValueError(f"unknown observation {observe!r}")
     cos, nmse = field_scores(res.values, syn.gt_forces)
     out = dict(gt_forces=syn.gt_forces, x_obs=syn.x_obs, result=res, cos_sim=cos, nmse=nmse)
     syn.close()
