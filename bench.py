@@ -656,10 +656,21 @@ def bench_inversion(dev, iters=40):
             out["inversion_iter_ms"] = ms / n_it
             out["inversion_ps_per_s"] = case["scene"].n * case["substeps"] * n_it / (ms * 1e-3)
             out["inversion_total_ms"] = ms
+    # observed through two rendered 128 x 128 views instead of the particle positions
+    for lam, tag in ((0.1, ""), (0.0, "_no_phys")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = I.run_synthetic(case, iters=iters, lr=1.0, lam_phys=lam, observe="render")
+        torch.cuda.synchronize()
+        out[f"inversion_render_cos_sim{tag}"] = res["cos_sim"]
+        out[f"inversion_render_nmse{tag}"] = res["nmse"]
+        if not tag:
+            out["inversion_render_wall_s"] = time.perf_counter() - t0
     out["inversion_note"] = (f"{case['scene'].n} particles, 64^3 grid, 12^3 wind grid, "
                              f"{case['n_intervals']} intervals x {iters} iterations x "
                              f"{case['substeps']} substeps (forward + adjoint), guide inlet "
-                             f"{case['inlet_error_deg']} deg off; lambda_phys 0.1")
+                             f"{case['inlet_error_deg']} deg off; lambda_phys 0.1; render: two 128 x 128 views, "
+                             f"L1, wall time includes the ground truth and its images")
     return out
 
 
