@@ -348,8 +348,9 @@ DW_API dw_status gs_render(dw_gs h, const dw_camera *cam, const float *x, const 
  * into g_F [9][n] (the MPM adjoint's inputs for the final state), and, when
  * not NULL, dL/d(color) into g_color [3][n] and dL/d(opacity) into g_opacity
  * [n]. The pixel rule q <= 9 makes the image piecewise smooth; the gradient
- * is that of the smooth piece. DW_ERR_ARG when n differs from the last
- * gs_render. */
+ * is that of the smooth piece. DW_ERR_ARG when n, an input pointer or the
+ * camera differs from the last gs_render (the arrays' contents must not have
+ * changed since; that is the caller's to keep). */
 DW_API dw_status gs_render_backward(dw_gs h, const dw_camera *cam, const float *x, const float *F,
                                     const float *sigma0, const float *color,
                                     const float *opacity, int64_t n, const float *g_image,

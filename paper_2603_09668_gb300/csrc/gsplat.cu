@@ -11,17 +11,23 @@
 //                    rectangle of the 3-sigma ellipse, depth key;
 //   radix sort       stable LSD sort of the depth keys (four 8-bit passes:
 //                    block histograms, one scan, order-keeping scatter);
-//   k_gs_render_fwd  one 16 x 16 pixel tile per block: the Gaussians are read
-//                    front to back in batches of 256, the batch's ones whose
-//                    rectangle meets the tile are compacted into shared
-//                    memory, then every pixel composites them.
-// gs_render_backward walks the same batches front to back again with the
+//   tile lists       in depth order, each Gaussian is listed once per 16 x 16
+//                    pixel tile its rectangle meets (counts, scan, copies);
+//                    a stable sort of the list by tile keeps the depth order
+//                    within each tile, and each tile's range is marked;
+//   k_gs_render_fwd  one tile per block: its Gaussians are read front to back
+//                    in batches of 256 into shared memory, then every pixel
+//                    composites them.
+// gs_render_backward walks the same ranges front to back again with the
 // final colour known (dC/dalpha_i = T_i c_i - (C - C_<=i) / (1 - alpha_i)),
 // reduces each Gaussian's pixel contributions per warp before one atomic,
 // and k_gs_preprocess_bwd carries the 2D gradients back to x and F.
 #include <math.h>
+#include <string.h>
 
 #include <new>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -285,67 +291,131 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t *__res
     }
 }
 
+// ------------------------------------------------------------ tile lists --
+
+// Tiles met by Gaussian order[k] (its pixel rectangle in 16 x 16 tiles).
+__global__ void k_gs_tile_count(const uint32_t *__restrict__ order, const int4 *__restrict__ rect,
+                                int n, uint32_t *__restrict__ cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int4 r = rect[order[k]];
+    uint32_t c = 0;
+    if (r.z >= r.x && r.w >= r.y)
+        c = (uint32_t)((r.z / GS_TILE - r.x / GS_TILE + 1) * (r.w / GS_TILE - r.y / GS_TILE + 1));
+    cnt[k] = c;
+}
+
+// Exclusive scan of 1024 values per block (256 threads x 4), block totals out.
+__global__ void __launch_bounds__(256) k_scan1024(const uint32_t *__restrict__ in, int n,
+                                                  uint32_t *__restrict__ out,
+                                                  uint32_t *__restrict__ sums) {
+    __shared__ uint32_t part[256];
+    const int base = blockIdx.x * 1024 + threadIdx.x * 4;
+    uint32_t v[4], t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = base + j < n ? in[base + j] : 0u;
+        t += v[j];
+    }
+    part[threadIdx.x] = t;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        const uint32_t a = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += a;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - t;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 255) sums[blockIdx.x] = part[255];
+}
+
+// out += the scanned block offsets; the total goes to *total.
+__global__ void k_scan_finish(uint32_t *__restrict__ out, const uint32_t *__restrict__ cnt, int n,
+                              const uint32_t *__restrict__ block_off, uint32_t *__restrict__ total) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t o = out[i] + block_off[i / 1024];
+    out[i] = o;
+    if (i == n - 1) *total = o + cnt[i];
+}
+
+// One entry (tile id, Gaussian) per tile met, written in depth order.
+__global__ void k_gs_duplicate(const uint32_t *__restrict__ order, const int4 *__restrict__ rect,
+                               const uint32_t *__restrict__ off, int n, int tiles_x,
+                               uint32_t *__restrict__ tile_key, uint32_t *__restrict__ gid) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t g = order[k];
+    const int4 r = rect[g];
+    if (!(r.z >= r.x && r.w >= r.y)) return;
+    uint32_t o = off[k];
+    for (int ty = r.y / GS_TILE; ty <= r.w / GS_TILE; ++ty)
+        for (int tx = r.x / GS_TILE; tx <= r.z / GS_TILE; ++tx) {
+            tile_key[o] = (uint32_t)(ty * tiles_x + tx);
+            gid[o] = g;
+            ++o;
+        }
+}
+
+// ranges[tile] = [first, last + 1) of the tile's entries in the sorted list.
+__global__ void k_gs_tile_ranges(const uint32_t *__restrict__ tile_key, int m,
+                                 int2 *__restrict__ ranges) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const uint32_t t = tile_key[p];
+    if (p == 0 || tile_key[p - 1] != t) ranges[t].x = p;
+    if (p == m - 1 || tile_key[p + 1] != t) ranges[t].y = p + 1;
+}
+
 // ---------------------------------------------------------------- render --
 
-// Load the batch [b0, b0 + 256) of the sorted Gaussians and keep, in order,
-// those whose rectangle meets the tile [tx0, tx1] x [ty0, ty1]; returns their
-// number. Compaction keeps the batch order (prefix over warps, then lanes).
-__device__ __forceinline__ int gs_gather_batch(int b0, int n, int tx0, int ty0, int tx1, int ty1,
-                                               const uint32_t *__restrict__ order,
-                                               const int4 *__restrict__ rect,
-                                               int *__restrict__ s_id, int *s_wsum) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k = b0 + threadIdx.x;
-    int g = -1;
-    if (k < n) {
-        const int gi = (int)order[k];
-        const int4 r = rect[gi];
-        if (r.z >= tx0 && r.x <= tx1 && r.w >= ty0 && r.y <= ty1) g = gi;
+// Load the batch [b0, b0 + 256) of the tile's range of the tile list into
+// shared memory (mu', conic, opacity, colour per Gaussian); returns its size.
+__device__ __forceinline__ int gs_load_batch(int b0, int end, int n,
+                                             const uint32_t *__restrict__ list,
+                                             const float *__restrict__ mu,
+                                             const float *__restrict__ conic,
+                                             const float *__restrict__ color,
+                                             const float *__restrict__ opacity, int *s_id,
+                                             float (*s_g)[9]) {
+    const int cnt = min(GS_THREADS, end - b0);
+    if ((int)threadIdx.x < cnt) {
+        const int g = (int)list[b0 + threadIdx.x];
+        float *r = s_g[threadIdx.x];
+        s_id[threadIdx.x] = g;
+        r[0] = mu[g];
+        r[1] = mu[n + g];
+        r[2] = conic[g];
+        r[3] = conic[n + g];
+        r[4] = conic[2 * n + g];
+        r[5] = opacity[g];
+        r[6] = color[g];
+        r[7] = color[n + g];
+        r[8] = color[2 * n + g];
     }
-    const unsigned m = __ballot_sync(0xffffffffu, g >= 0);
-    if (lane == 0) s_wsum[warp] = __popc(m);
     __syncthreads();
-    int off = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < GS_THREADS / 32; ++w) {
-        const int c = s_wsum[w];
-        off += w < warp ? c : 0;
-        total += c;
-    }
-    if (g >= 0) s_id[off + __popc(m & ((1u << lane) - 1u))] = g;
-    __syncthreads();
-    return total;
+    return cnt;
 }
 
 __global__ void __launch_bounds__(GS_THREADS) k_gs_render_fwd(
-    GsCam c, int n, const uint32_t *__restrict__ order, const int4 *__restrict__ rect,
+    GsCam c, int n, const uint32_t *__restrict__ list, const int2 *__restrict__ ranges,
     const float *__restrict__ mu, const float *__restrict__ conic,
     const float *__restrict__ color, const float *__restrict__ opacity,
     float *__restrict__ image, float *__restrict__ image_keep) {
     __shared__ int s_id[GS_THREADS];
-    __shared__ int s_wsum[GS_THREADS / 32];
     __shared__ float s_g[GS_THREADS][9];  // mu(2) conic(3) opacity color(3)
     const int tx0 = blockIdx.x * GS_TILE, ty0 = blockIdx.y * GS_TILE;
     const int px = tx0 + (threadIdx.x & (GS_TILE - 1)), py = ty0 + threadIdx.x / GS_TILE;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int2 rg = ranges[blockIdx.y * gridDim.x + blockIdx.x];
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    for (int b0 = 0; b0 < n; b0 += GS_THREADS) {
-        const int cnt = gs_gather_batch(b0, n, tx0, ty0, tx0 + GS_TILE - 1, ty0 + GS_TILE - 1,
-                                        order, rect, s_id, s_wsum);
-        if (threadIdx.x < cnt) {
-            const int g = s_id[threadIdx.x];
-            float *r = s_g[threadIdx.x];
-            r[0] = mu[g];
-            r[1] = mu[n + g];
-            r[2] = conic[g];
-            r[3] = conic[n + g];
-            r[4] = conic[2 * n + g];
-            r[5] = opacity[g];
-            r[6] = color[g];
-            r[7] = color[n + g];
-            r[8] = color[2 * n + g];
-        }
-        __syncthreads();
+    for (int b0 = rg.x; b0 < rg.y; b0 += GS_THREADS) {
+        const int cnt = gs_load_batch(b0, rg.y, n, list, mu, conic, color, opacity, s_id, s_g);
         for (int k = 0; k < cnt; ++k) {
             const float *r = s_g[k];
             const float dx = fx - r[0], dy = fy - r[1];
@@ -382,13 +452,12 @@ __device__ __forceinline__ float warp_sum(float v) {
 // (C - C_<=i) / (1 - alpha)), then dL/do, dL/dmu', dL/dconic; each Gaussian's
 // nine sums over a warp's pixels go to memory with one atomic each.
 __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
-    GsCam c, int n, const uint32_t *__restrict__ order, const int4 *__restrict__ rect,
+    GsCam c, int n, const uint32_t *__restrict__ list, const int2 *__restrict__ ranges,
     const float *__restrict__ mu, const float *__restrict__ conic,
     const float *__restrict__ color, const float *__restrict__ opacity,
     const float *__restrict__ image_keep, const float *__restrict__ g_image,
     float *__restrict__ g2d) {
     __shared__ int s_id[GS_THREADS];
-    __shared__ int s_wsum[GS_THREADS / 32];
     __shared__ float s_g[GS_THREADS][9];
     const int tx0 = blockIdx.x * GS_TILE, ty0 = blockIdx.y * GS_TILE;
     const int px = tx0 + (threadIdx.x & (GS_TILE - 1)), py = ty0 + threadIdx.x / GS_TILE;
@@ -405,23 +474,9 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
     }
     float T = 1.0f, Cl[3] = {0.0f, 0.0f, 0.0f};
     const int lane = threadIdx.x & 31;
-    for (int b0 = 0; b0 < n; b0 += GS_THREADS) {
-        const int cnt = gs_gather_batch(b0, n, tx0, ty0, tx0 + GS_TILE - 1, ty0 + GS_TILE - 1,
-                                        order, rect, s_id, s_wsum);
-        if (threadIdx.x < cnt) {
-            const int g = s_id[threadIdx.x];
-            float *r = s_g[threadIdx.x];
-            r[0] = mu[g];
-            r[1] = mu[n + g];
-            r[2] = conic[g];
-            r[3] = conic[n + g];
-            r[4] = conic[2 * n + g];
-            r[5] = opacity[g];
-            r[6] = color[g];
-            r[7] = color[n + g];
-            r[8] = color[2 * n + g];
-        }
-        __syncthreads();
+    const int2 rg = ranges[blockIdx.y * gridDim.x + blockIdx.x];
+    for (int b0 = rg.x; b0 < rg.y; b0 += GS_THREADS) {
+        const int cnt = gs_load_batch(b0, rg.y, n, list, mu, conic, color, opacity, s_id, s_g);
         for (int k = 0; k < cnt; ++k) {
             const float *r = s_g[k];
             const float dx = fx - r[0], dy = fy - r[1];
@@ -584,7 +639,18 @@ struct GsHandle {
     float *mu = nullptr, *conic = nullptr, *g2d = nullptr, *image = nullptr;
     int4 *rect = nullptr;
     uint32_t *key = nullptr, *idx = nullptr, *key2 = nullptr, *idx2 = nullptr, *counts = nullptr;
+    uint32_t *tcnt = nullptr, *toff = nullptr, *bsum = nullptr, *total = nullptr;
+    int2 *ranges = nullptr;  // [tiles]
+    // tile list: (tile key, Gaussian) entries and their sort buffers
+    int64_t list_cap = 0;
+    uint32_t *lkey = nullptr, *lgid = nullptr, *lkey2 = nullptr, *lgid2 = nullptr,
+             *lcounts = nullptr;
+    const uint32_t *list = nullptr;  // the sorted Gaussian column of the last gs_render
+    int tiles_x = 0, tiles_y = 0;
     int last_n = -1;  // Gaussians of the last gs_render
+    // inputs and camera of the last gs_render (the backward must see the same)
+    const void *last_in[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    dw_camera last_cam{};
 };
 
 static GsCam to_cam(const dw_camera &c) {
@@ -601,11 +667,49 @@ static GsCam to_cam(const dw_camera &c) {
     return g;
 }
 
+// Stable LSD radix sort of (k, v) by the low 8 * passes bits of k; the
+// result ends in (k, v) (the pointers are swapped as the passes alternate).
+static void radix_sort(uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2, int n,
+                       int passes, uint32_t *counts, cudaStream_t s) {
+    const int nb = (n + RS_TILE - 1) / RS_TILE;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_rs_hist<<<nb, RS_THREADS, 0, s>>>(k, n, shift, nb, counts);
+        k_rs_scan<<<1, 1024, 0, s>>>(counts, 256 * nb);
+        k_rs_scatter<<<nb, RS_THREADS, 0, s>>>(k, v, k2, v2, n, shift, nb, counts);
+        std::swap(k, k2);
+        std::swap(v, v2);
+    }
+}
+
 }  // namespace dw
 
 using namespace dw;
 
 struct dw_gs_s : GsHandle {};
+
+// Grow the tile-list buffers to hold m entries.
+static dw_status gs_list_reserve(dw_gs h, int64_t m) {
+    if (m <= h->list_cap) return DW_OK;
+    const int64_t cap = std::max<int64_t>(m, h->list_cap * 3 / 2);
+    DW_REQUIRE(cap < (1ll << 31), "tile list too long (Gaussians x tiles met >= 2^31)");
+    cudaFree(h->lkey);
+    cudaFree(h->lgid);
+    cudaFree(h->lkey2);
+    cudaFree(h->lgid2);
+    cudaFree(h->lcounts);
+    h->lkey = h->lgid = h->lkey2 = h->lgid2 = h->lcounts = nullptr;
+    h->list_cap = 0;
+    const size_t c = (size_t)cap, nb = (c + RS_TILE - 1) / RS_TILE;
+    cudaError_t e = cudaMalloc((void **)&h->lkey, sizeof(uint32_t) * c);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->lgid, sizeof(uint32_t) * c);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->lkey2, sizeof(uint32_t) * c);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->lgid2, sizeof(uint32_t) * c);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->lcounts, sizeof(uint32_t) * 256 * nb);
+    if (e != cudaSuccess) return cuda_fail(e, "gs_render (tile list)");
+    h->list_cap = cap;
+    return DW_OK;
+}
 
 extern "C" dw_status gs_create(int64_t max_gaussians, int32_t width, int32_t height, dw_gs *out) {
     DW_REQUIRE(out, "out must not be NULL");
@@ -633,6 +737,14 @@ extern "C" dw_status gs_create(int64_t max_gaussians, int32_t width, int32_t hei
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->counts, sizeof(uint32_t) * 256 * nb);
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&h->image, sizeof(float) * 3 * (size_t)width * height);
+    h->tiles_x = (width + GS_TILE - 1) / GS_TILE;
+    h->tiles_y = (height + GS_TILE - 1) / GS_TILE;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->tcnt, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->toff, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->bsum, sizeof(uint32_t) * ((n + 1023) / 1024));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->total, sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&h->ranges, sizeof(int2) * (size_t)h->tiles_x * h->tiles_y);
     if (e != cudaSuccess) {
         dw_status st = cuda_fail(e, "gs_create");
         gs_destroy(h);
@@ -654,6 +766,16 @@ extern "C" dw_status gs_destroy(dw_gs h) {
     cudaFree(h->idx2);
     cudaFree(h->counts);
     cudaFree(h->image);
+    cudaFree(h->tcnt);
+    cudaFree(h->toff);
+    cudaFree(h->bsum);
+    cudaFree(h->total);
+    cudaFree(h->ranges);
+    cudaFree(h->lkey);
+    cudaFree(h->lgid);
+    cudaFree(h->lkey2);
+    cudaFree(h->lgid2);
+    cudaFree(h->lcounts);
     delete h;
     return DW_OK;
 }
@@ -690,29 +812,43 @@ extern "C" dw_status gs_render(dw_gs h, const dw_camera *cam, const float *x, co
     cudaStream_t s = as_stream(stream);
     const GsCam c = to_cam(*cam);
     const int nn = (int)n;
+    const int ntiles = h->tiles_x * h->tiles_y;
+    DW_CUDA(cudaMemsetAsync(h->ranges, 0, sizeof(int2) * (size_t)ntiles, s));
+    h->list = h->lgid;
     if (nn > 0) {
         k_gs_preprocess<<<grid_for(nn, 256), 256, 0, s>>>(c, x, F, sigma0, nn, h->mu, h->conic,
                                                           h->rect, h->key, h->idx);
-        const int nb = (nn + RS_TILE - 1) / RS_TILE;
         uint32_t *ka = h->key, *va = h->idx, *kb = h->key2, *vb = h->idx2;
-        for (int shift = 0; shift < 32; shift += 8) {
-            k_rs_hist<<<nb, RS_THREADS, 0, s>>>(ka, nn, shift, nb, h->counts);
-            k_rs_scan<<<1, 1024, 0, s>>>(h->counts, 256 * nb);
-            k_rs_scatter<<<nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, nn, shift, nb, h->counts);
-            uint32_t *t = ka;
-            ka = kb;
-            kb = t;
-            t = va;
-            va = vb;
-            vb = t;
+        radix_sort(ka, va, kb, vb, nn, 4, h->counts, s);  // depth order in (ka, va)
+        // tile list: counts in depth order, offsets, total
+        k_gs_tile_count<<<grid_for(nn, 256), 256, 0, s>>>(va, h->rect, nn, h->tcnt);
+        const int nsb = (nn + 1023) / 1024;
+        k_scan1024<<<nsb, 256, 0, s>>>(h->tcnt, nn, h->toff, h->bsum);
+        k_rs_scan<<<1, 1024, 0, s>>>(h->bsum, nsb);
+        k_scan_finish<<<grid_for(nn, 256), 256, 0, s>>>(h->toff, h->tcnt, nn, h->bsum, h->total);
+        uint32_t m = 0;
+        DW_CUDA(cudaMemcpyAsync(&m, h->total, sizeof m, cudaMemcpyDeviceToHost, s));
+        DW_CUDA(cudaStreamSynchronize(s));
+        if (m > 0) {
+            dw_status st2 = gs_list_reserve(h, (int64_t)m);
+            if (st2 != DW_OK) return st2;
+            k_gs_duplicate<<<grid_for(nn, 256), 256, 0, s>>>(va, h->rect, h->toff, nn, h->tiles_x,
+                                                             h->lkey, h->lgid);
+            int bits = 1;
+            while ((1 << bits) < ntiles) ++bits;
+            uint32_t *lk = h->lkey, *lv = h->lgid, *lk2 = h->lkey2, *lv2 = h->lgid2;
+            radix_sort(lk, lv, lk2, lv2, (int)m, (bits + 7) / 8, h->lcounts, s);
+            k_gs_tile_ranges<<<grid_for(m, 256), 256, 0, s>>>(lk, (int)m, h->ranges);
+            h->list = lv;
         }
-        // four passes: the sorted order is back in (key, idx)
     }
-    const dim3 grid((unsigned)((h->width + GS_TILE - 1) / GS_TILE),
-                    (unsigned)((h->height + GS_TILE - 1) / GS_TILE));
-    k_gs_render_fwd<<<grid, GS_THREADS, 0, s>>>(c, nn, h->idx, h->rect, h->mu, h->conic, color,
+    const dim3 grid((unsigned)h->tiles_x, (unsigned)h->tiles_y);
+    k_gs_render_fwd<<<grid, GS_THREADS, 0, s>>>(c, nn, h->list, h->ranges, h->mu, h->conic, color,
                                                  opacity, image, h->image);
     h->last_n = nn;
+    const void *in[5] = {x, F, sigma0, color, opacity};
+    memcpy(h->last_in, in, sizeof in);
+    h->last_cam = *cam;
     DW_LAUNCHED("gs_render");
     return DW_OK;
 }
@@ -725,15 +861,17 @@ extern "C" dw_status gs_render_backward(dw_gs h, const dw_camera *cam, const flo
     dw_status st = gs_check(h, cam, x, F, sigma0, color, opacity, n);
     if (st != DW_OK) return st;
     DW_REQUIRE(g_image && g_x && g_F, "g_image, g_x and g_F must not be NULL");
-    DW_REQUIRE(h->last_n == (int)n, "gs_render_backward must follow gs_render of the same Gaussians");
+    const void *in[5] = {x, F, sigma0, color, opacity};
+    DW_REQUIRE(h->last_n == (int)n && memcmp(h->last_in, in, sizeof in) == 0 &&
+                   memcmp(&h->last_cam, cam, sizeof *cam) == 0,
+               "gs_render_backward must follow gs_render of the same Gaussians and camera");
     if (n == 0) return DW_OK;
     cudaStream_t s = as_stream(stream);
     const GsCam c = to_cam(*cam);
     const int nn = (int)n;
     DW_CUDA(cudaMemsetAsync(h->g2d, 0, sizeof(float) * 9 * (size_t)nn, s));
-    const dim3 grid((unsigned)((h->width + GS_TILE - 1) / GS_TILE),
-                    (unsigned)((h->height + GS_TILE - 1) / GS_TILE));
-    k_gs_render_bwd<<<grid, GS_THREADS, 0, s>>>(c, nn, h->idx, h->rect, h->mu, h->conic, color,
+    const dim3 grid((unsigned)h->tiles_x, (unsigned)h->tiles_y);
+    k_gs_render_bwd<<<grid, GS_THREADS, 0, s>>>(c, nn, h->list, h->ranges, h->mu, h->conic, color,
                                                  opacity, h->image, g_image, h->g2d);
     k_gs_preprocess_bwd<<<grid_for(nn, 256), 256, 0, s>>>(c, x, F, sigma0, nn, h->g2d, g_x, g_F,
                                                            g_color, g_opacity);
