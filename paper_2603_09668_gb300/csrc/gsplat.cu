@@ -20,8 +20,7 @@
 //                    composites them.
 // gs_render_backward walks the same ranges front to back again with the
 // final colour known (dC/dalpha_i = T_i c_i - (C - C_<=i) / (1 - alpha_i)),
-// reduces each Gaussian's pixel contributions per warp and then per tile
-// before one atomic per value,
+// reduces each Gaussian's pixel contributions per warp before one atomic,
 // and k_gs_preprocess_bwd carries the 2D gradients back to x and F.
 #include <math.h>
 #include <string.h>
@@ -451,8 +450,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Per pixel, front to back: w = T alpha, dL/dc += g w, dL/dalpha = g . (T c -
 // (C - C_<=i) / (1 - alpha)), then dL/do, dL/dmu', dL/dconic; each Gaussian's
-// nine sums over a warp's pixels are added in shared memory, and the tile's
-// sums go to memory with one atomic each.
+// nine sums over a warp's pixels go to memory with one atomic each.
 __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
     GsCam c, int n, const uint32_t *__restrict__ list, const int2 *__restrict__ ranges,
     const float *__restrict__ mu, const float *__restrict__ conic,
@@ -461,7 +459,6 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
     float *__restrict__ g2d) {
     __shared__ int s_id[GS_THREADS];
     __shared__ float s_g[GS_THREADS][9];
-    __shared__ float s_acc[GS_THREADS][9];  // the tile's sums per Gaussian of the batch
     const int tx0 = blockIdx.x * GS_TILE, ty0 = blockIdx.y * GS_TILE;
     const int px = tx0 + (threadIdx.x & (GS_TILE - 1)), py = ty0 + threadIdx.x / GS_TILE;
     const bool inside = px < c.width && py < c.height;
@@ -480,9 +477,6 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
     const int2 rg = ranges[blockIdx.y * gridDim.x + blockIdx.x];
     for (int b0 = rg.x; b0 < rg.y; b0 += GS_THREADS) {
         const int cnt = gs_load_batch(b0, rg.y, n, list, mu, conic, color, opacity, s_id, s_g);
-#pragma unroll
-        for (int j = 0; j < 9; ++j) s_acc[threadIdx.x][j] = 0.0f;
-        __syncthreads();
         for (int k = 0; k < cnt; ++k) {
             const float *r = s_g[k];
             const float dx = fx - r[0], dy = fy - r[1];
@@ -510,20 +504,12 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
                 T *= 1.0f - a;
             }
             if (__any_sync(0xffffffffu, hit)) {
+                const int g = s_id[k];
 #pragma unroll
                 for (int j = 0; j < 9; ++j) {
                     const float sj = warp_sum(v[j]);
-                    if (lane == 0 && sj != 0.0f) atomicAdd(&s_acc[k][j], sj);
+                    if (lane == 0 && sj != 0.0f) atomicAdd(&g2d[(int64_t)j * n + g], sj);
                 }
-            }
-        }
-        __syncthreads();
-        if ((int)threadIdx.x < cnt) {  // one global atomic per value, Gaussian and tile
-            const int g = s_id[threadIdx.x];
-#pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const float a = s_acc[threadIdx.x][j];
-                if (a != 0.0f) atomicAdd(&g2d[(int64_t)j * n + g], a);
             }
         }
         __syncthreads();
