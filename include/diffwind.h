@@ -602,6 +602,12 @@ DW_API dw_status lbm_home_step(dw_lbm h, float *m, const uint8_t *solid, int32_t
 DW_API dw_status lbm_home_macroscopic(dw_lbm h, const float *m, const uint8_t *solid, float *rho,
                                       float *u, dw_stream stream);
 
+/* lbm_sample_velocity for HOME-LBM moments m: the macroscopic velocity of
+ * lbm_home_macroscopic interpolated at points pos[3][n] the same way. */
+DW_API dw_status lbm_home_sample_velocity(dw_lbm h, const float *m, const uint8_t *solid,
+                                          const float *pos, int64_t n, float *u_out,
+                                          dw_stream stream);
+
 /* Solid mask of Eq. point2voxel: solid[w] = 1 iff some particle lies in
  * [x_w, x_w + dx)^3 with x_w = w dx, i.e. w = floor(x_p / dx); the mask is
  * cleared first; particles outside the lattice are ignored. pos is device

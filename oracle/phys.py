@@ -6,9 +6,10 @@ only tests/, the smoke check in __graft_entry__.py and bench.py's reference
 leg may import this module. Nothing here is shared with the CUDA library.
 
 What it computes, in numpy float64:
-  - lbm_sample_velocity: the LBM macroscopic velocity (Eq. lbm_sum_v2, via
-    the lattice oracle's moments) trilinearly interpolated at arbitrary
-    points of the unit cube. Reading: lattice cell c spans [c/n, (c+1)/n)
+  - lbm_sample_velocity / sample_velocity_field: the LBM macroscopic velocity
+    (Eq. lbm_sum_v2, via the lattice oracle's moments, or any cell field such
+    as the HOME-LBM oracle's) trilinearly interpolated at arbitrary points of
+    the unit cube. Reading: lattice cell c spans [c/n, (c+1)/n)
     (the cell of Eq. point2voxel with dx = 1/n), its velocity sits at the
     cell centre (c + 1/2)/n; solid cells have u = 0; points are clamped to
     the box of cell centres.
@@ -36,9 +37,16 @@ from . import lbm_macroscopic
 def lbm_sample_velocity(shape, f, pos, solid=None, force=(0.0, 0.0, 0.0)):
     """u[3][m] at positions pos[3][m] of the unit cube, from populations f
     (natural order, f[q][cell] unshifted, as the lattice oracle stores them)."""
+    _, u = lbm_macroscopic(shape, f, force, solid)
+    return sample_velocity_field(shape, u, pos)
+
+
+def sample_velocity_field(shape, u, pos):
+    """u[3][m] at positions pos[3][m] of a cell-centred velocity field u
+    [3][nz*ny*nx] (solid cells already at rest), trilinear between cell
+    centres, clamped to their box."""
     nx, ny, nz = shape
-    rho, u = lbm_macroscopic(shape, f, force, solid)
-    u = u.reshape(3, nz, ny, nx)
+    u = np.asarray(u, np.float64).reshape(3, nz, ny, nx)
     pos = np.asarray(pos, np.float64)
     m = pos.shape[1]
     out = np.zeros((3, m))

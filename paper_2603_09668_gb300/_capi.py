@@ -106,6 +106,7 @@ SIGNATURES = {
     "lbm_home_init": (I32, [VP, VP, F32, P(F32 * 3), VP]),
     "lbm_home_step": (I32, [VP, VP, VP, I32, VP]),
     "lbm_home_macroscopic": (I32, [VP, VP, VP, VP, VP, VP]),
+    "lbm_home_sample_velocity": (I32, [VP, VP, VP, VP, I64, VP, VP]),
     "lbm_sample_velocity": (I32, [VP, VP, VP, VP, I64, VP, VP]),
     "wind_phys_loss": (I32, [VP, VP, I64, F32, F32, VP, VP, VP]),
     "wind_field_scores": (I32, [VP, VP, I64, F32, VP, VP]),

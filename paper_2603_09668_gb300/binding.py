@@ -24,6 +24,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
            "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "lbm_home_init", "lbm_home_step", "lbm_home_macroscopic",
+           "lbm_home_sample_velocity",
            "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
            "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "vector_adam_step", "camera",
            "gs_covariance", "image_l1_loss", "GaussianRenderer", "MPM", "LBM", "surr_create",
@@ -397,6 +398,17 @@ def lbm_home_macroscopic(h, m, solid, rho=None, u=None, stream=None):
     return rho, u
 
 
+def lbm_home_sample_velocity(h, m, solid, pos, u_out=None, stream=None):
+    """u[3][n] of the HOME-LBM moments m at points pos[3][n] (unit cube)."""
+    n = pos.shape[1]
+    if u_out is None:
+        u_out = torch.empty((3, n), dtype=torch.float32, device=pos.device)
+    check(lib().lbm_home_sample_velocity(h, _dev(m, name="m"), _mask(solid),
+                                         _dev(pos, name="pos"), int(n),
+                                         _dev(u_out, name="u_out"), _stream(stream)))
+    return u_out
+
+
 def lbm_sample_velocity(h, f, solid, pos, u_out=None, stream=None):
     """u[3][n] of the lattice f at points pos[3][n] (unit cube)."""
     n = pos.shape[1]
@@ -705,6 +717,9 @@ class LBM:
 
     def home_step(self, m, solid, steps, stream=None):
         return lbm_home_step(self.h, m, solid, steps, stream)
+
+    def home_sample_velocity(self, m, solid, pos, u_out=None, stream=None):
+        return lbm_home_sample_velocity(self.h, m, solid, pos, u_out, stream)
 
     def home_macroscopic(self, m, solid, stream=None):
         nx, ny, nz = self.shape

@@ -396,6 +396,21 @@ __device__ __forceinline__ void cell_moments(const LbmParams &L, const float *__
     }
 }
 
+// The same from HOME-LBM moments m (planes rho - 1, u' = u + F/(2 rho), ...).
+__device__ __forceinline__ void home_cell_velocity(const LbmParams &L, const float *__restrict__ m,
+                                                   const uint8_t *__restrict__ solid, int cell,
+                                                   float &r, float &ux, float &uy, float &uz) {
+    const size_t nc = (size_t)L.ncell;
+    r = ux = uy = uz = 0.0f;
+    if (!(solid && solid[cell])) {
+        r = 1.0f + m[cell];
+        const float h = 0.5f / r;
+        ux = m[nc + cell] - h * L.Fx;
+        uy = m[2 * nc + cell] - h * L.Fy;
+        uz = m[3 * nc + cell] - h * L.Fz;
+    }
+}
+
 __global__ void k_lbm_macroscopic(LbmParams L, const float *__restrict__ f,
                                   const uint8_t *__restrict__ solid, float *__restrict__ rho,
                                   float *__restrict__ u) {
@@ -414,7 +429,9 @@ __global__ void k_lbm_macroscopic(LbmParams L, const float *__restrict__ f,
 
 // The velocity at points pos[3][n] of the unit cube: trilinear between the
 // cell centres ((c + 1/2) / n per axis, clamped to their box) of the cells'
-// velocities (solid cells at rest).
+// velocities (solid cells at rest); f holds populations or, with HOME, the
+// HOME-LBM moments.
+template <bool HOME>
 __global__ void k_lbm_sample_velocity(LbmParams L, const float *__restrict__ f,
                                       const uint8_t *__restrict__ solid,
                                       const float *__restrict__ pos, int64_t n,
@@ -440,7 +457,10 @@ __global__ void k_lbm_sample_velocity(LbmParams L, const float *__restrict__ f,
                         (cz ? t[2] : 1.0f - t[2]);
         const int cell = ((i0[2] + cz) * L.ny + (i0[1] + cy)) * L.nx + (i0[0] + cx);
         float r, ux, uy, uz;
-        cell_moments(L, f, solid, cell, r, ux, uy, uz);
+        if (HOME)
+            home_cell_velocity(L, f, solid, cell, r, ux, uy, uz);
+        else
+            cell_moments(L, f, solid, cell, r, ux, uy, uz);
         acc[0] += w * ux;
         acc[1] += w * uy;
         acc[2] += w * uz;
@@ -652,9 +672,22 @@ extern "C" dw_status lbm_sample_velocity(dw_lbm h, const float *f, const uint8_t
     DW_REQUIRE(n >= 0, "n must be >= 0");
     if (n == 0) return DW_OK;
     DW_REQUIRE(f && pos && u_out, "f, pos and u_out must not be NULL");
-    k_lbm_sample_velocity<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(h->L, f, solid, pos, n,
-                                                                            u_out);
+    k_lbm_sample_velocity<false><<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(
+        h->L, f, solid, pos, n, u_out);
     DW_LAUNCHED("k_lbm_sample_velocity");
+    return DW_OK;
+}
+
+extern "C" dw_status lbm_home_sample_velocity(dw_lbm h, const float *m, const uint8_t *solid,
+                                              const float *pos, int64_t n, float *u_out,
+                                              dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return DW_OK;
+    DW_REQUIRE(m && pos && u_out, "m, pos and u_out must not be NULL");
+    k_lbm_sample_velocity<true><<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(
+        h->L, m, solid, pos, n, u_out);
+    DW_LAUNCHED("k_lbm_sample_velocity<home>");
     return DW_OK;
 }
 

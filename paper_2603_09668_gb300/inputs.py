@@ -248,8 +248,9 @@ def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, 
     """Synthetic wind-inversion case: the flag-like sheet (pinned edge, E=5e4)
     on an n_grid^3 grid, n_intervals intervals of `substeps` substeps of dt
     (0.04 s, a video frame interval; checkpoint every `every`), a wind grid of
-    nf^3 nodes, and an n_cells^3 lattice (tau 0.6) with an inlet of speed 0.05
-    along (1, 0, 0.35) advanced lbm_steps steps per interval. The ground-truth
+    nf^3 nodes, and an n_cells^3 lattice (tau 0.6; HOME-LBM, or BGK with
+    lbm_model="bgk") with an inlet of speed 0.05 along (1, 0, 0.35) advanced
+    lbm_steps steps per interval. The ground-truth
     force follows the drag relation with scale 4000 (10 N/kg at the inlet
     speed); the inversion's guide lattice assumes a wind-source direction off
     by inlet_error_deg degrees about y."""
@@ -259,7 +260,7 @@ def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, 
     u_in = tuple(float(c) for c in 0.05 * d / np.linalg.norm(d))
     return dict(scene=sc, nu=nu, nf=nf, n_intervals=n_intervals, substeps=substeps, every=every,
                 n_cells=n_cells, tau=0.6, u_inlet=u_in, drag_scale=4000.0, lbm_steps=lbm_steps,
-                inlet_error_deg=inlet_error_deg)
+                inlet_error_deg=inlet_error_deg, lbm_model=lbm_model)
 
 
 def gaussian_scene(n=300, width=61, height=47, depth_ties=False, seed=0):

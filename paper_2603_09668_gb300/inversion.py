@@ -44,16 +44,26 @@ from .inputs import rest_state, wind_node_positions
 class LbmGuide:
     """A lattice over the unit cube (nx = ny = nz, so one voxel size dx = 1/nx
     serves Eq. point2voxel and the velocity sampler) with an inlet at x = 0,
-    evolved alongside the object, and its velocity at the nf^3 wind nodes."""
+    evolved alongside the object, and its velocity at the nf^3 wind nodes.
+    model "home" runs HOME-LBM (the paper's wind solver, Sec. 3.4), "bgk" the
+    BGK step."""
 
-    def __init__(self, n_cells: int, tau: float, u_inlet, nf: int, device="cuda"):
+    def __init__(self, n_cells: int, tau: float, u_inlet, nf: int, device="cuda",
+                 model: str = "home"):
+        if model not in ("home", "bgk"):
+            raise ValueError(f"unknown lattice model {model!r}")
         self.shape = (n_cells, n_cells, n_cells)
         self.n_cells = n_cells
         self.u_inlet = tuple(float(c) for c in u_inlet)
         self.nf = nf
+        self.model = model
         self.lbm = B.LBM(self.shape, tau, u_inlet=self.u_inlet, bc_x=1)
-        self.f = self.lbm.lattice(device)
-        self.lbm.init_equilibrium(self.f, 1.0, self.u_inlet)
+        if model == "home":
+            self.f = self.lbm.moments(device)
+            self.lbm.home_init(self.f, 1.0, self.u_inlet)
+        else:
+            self.f = self.lbm.lattice(device)
+            self.lbm.init_equilibrium(self.f, 1.0, self.u_inlet)
         self.solid = torch.zeros((n_cells, n_cells, n_cells), dtype=torch.uint8, device=device)
         self.nodes = torch.from_numpy(wind_node_positions(nf)).to(device)
         self.u = torch.empty((3, nf ** 3), dtype=torch.float32, device=device)
@@ -63,9 +73,14 @@ class LbmGuide:
         the velocity at the wind nodes [3][nf^3] (a view of the guide's buffer,
         overwritten by the next call)."""
         B.voxelize_particles(x, self.shape, 1.0 / self.n_cells, self.solid)
-        if steps > 0:
-            self.lbm.step(self.f, self.solid, steps)
-        self.lbm.sample_velocity(self.f, self.solid, self.nodes, self.u)
+        if self.model == "home":
+            if steps > 0:
+                self.lbm.home_step(self.f, self.solid, steps)
+            self.lbm.home_sample_velocity(self.f, self.solid, self.nodes, self.u)
+        else:
+            if steps > 0:
+                self.lbm.step(self.f, self.solid, steps)
+            self.lbm.sample_velocity(self.f, self.solid, self.nodes, self.u)
         return self.u
 
     def close(self):
@@ -272,12 +287,13 @@ def prepare_synthetic(case: dict, device="cuda") -> SyntheticCase:
                           for a in rest_state(sc.x)))
     pinned = torch.from_numpy(sc.pinned).to(device) if sc.pinned is not None else None
     mpm = B.MPM.from_params(sc.params(), max_particles=sc.n)
-    gt_guide = LbmGuide(case["n_cells"], case["tau"], case["u_inlet"], nf, device)
+    model = case.get("lbm_model", "home")
+    gt_guide = LbmGuide(case["n_cells"], case["tau"], case["u_inlet"], nf, device, model)
     gt_forces, x_obs = simulate_wind_driven(mpm, gt_guide, state0.clone(), pinned, K, S,
                                             case["lbm_steps"], case["drag_scale"])
     gt_guide.close()
     guide = LbmGuide(case["n_cells"], case["tau"],
-                     rotate_about_y(case["u_inlet"], case["inlet_error_deg"]), nf, device)
+                     rotate_about_y(case["u_inlet"], case["inlet_error_deg"]), nf, device, model)
     return SyntheticCase(mpm, state0, pinned, gt_forces, x_obs, guide)
 
 

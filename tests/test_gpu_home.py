@@ -96,6 +96,28 @@ def test_home_step_full_size_leaf_cluster():
     lbm.close()
 
 
+def test_home_sample_velocity_matches_oracle():
+    from oracle import phys
+
+    shape = (16, 12, 10)
+    tau, u_in = 0.6, (0.05, 0.02, 0.0)
+    solid_np = inputs.random_mask(shape, 0.1, seed=24)
+    m0, ref0 = start_moments(shape, tau, (0.04, 0.01, 0.0), (0.0, 0.0, 0.0), seed=25)
+    lbm = B.LBM(shape, tau, u_inlet=u_in, bc_x=1)
+    m = to_dev(m0).reshape(10, shape[2], shape[1], shape[0])
+    solid = to_dev(solid_np).reshape(shape[2], shape[1], shape[0])
+    lbm.home_step(m, solid, 5)
+    ref = oracle.home_step(shape, tau, ref0, 5, u_in=u_in, bc_x=1, solid=solid_np)
+    rng = np.random.default_rng(26)
+    pos = np.concatenate([rng.uniform(-0.05, 1.05, (3, 300)), inputs.wind_node_positions(8)],
+                         axis=1).astype(np.float32)
+    u = lbm.home_sample_velocity(m, solid, to_dev(pos)).cpu().numpy()
+    _, u_cells = oracle.home_macroscopic(shape, ref, solid=solid_np)
+    u_ref = phys.sample_velocity_field(shape, u_cells, pos.astype(np.float64))
+    assert rel_l2(u, u_ref) <= 1e-5, rel_l2(u, u_ref)
+    lbm.close()
+
+
 def test_home_init_matches_oracle_and_argument_errors():
     shape = (6, 5, 4)
     tau, force = 0.7, (2e-5, 0.0, -1e-5)
