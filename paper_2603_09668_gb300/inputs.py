@@ -244,7 +244,8 @@ def sheet_texture(x, cell=0.05):
 
 
 def inversion_case(nu=64, nv=43, n_grid=64, nf=12, n_intervals=3, substeps=200, dt=2e-4,
-                   every=25, n_cells=32, lbm_steps=30, inlet_error_deg=10.0, seed=0):
+                   every=25, n_cells=32, lbm_steps=30, inlet_error_deg=10.0, lbm_model="home",
+                   seed=0):
     """Synthetic wind-inversion case: the flag-like sheet (pinned edge, E=5e4)
     on an n_grid^3 grid, n_intervals intervals of `substeps` substeps of dt
     (0.04 s, a video frame interval; checkpoint every `every`), a wind grid of
