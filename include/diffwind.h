@@ -337,8 +337,10 @@ DW_API dw_status gs_destroy(dw_gs h);
 
 /* image (device [3][H][W], overwritten) of n Gaussians at the particles x
  * with deformation gradients F and rest covariances sigma0. The handle keeps
- * the projected Gaussians, their depth order and the image for
- * gs_render_backward. cam's image size must be the handle's. */
+ * the projected Gaussians, their depth order, the per-tile lists and the
+ * image for gs_render_backward. cam's image size must be the handle's. The
+ * call reads the tile-list length back to the host (4 bytes) to size the
+ * lists, so it waits for `stream` and cannot be captured in a CUDA graph. */
 DW_API dw_status gs_render(dw_gs h, const dw_camera *cam, const float *x, const float *F,
                            const float *sigma0, const float *color, const float *opacity,
                            int64_t n, float *image, dw_stream stream);
