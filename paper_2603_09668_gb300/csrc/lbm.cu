@@ -868,24 +868,24 @@ __host__ __device__ __forceinline__ void home_collide(const LbmParams &L, float 
     out[9] = u[1] * u[2] + S[5] * inv_rho;
 }
 
-// Tiles of the streaming HOME kernel: 32 x 8 cells of a z-plane per block
-// (one thread each), walking tz planes along z (chosen per lattice, below). Each plane of the tile
-// plus a one-cell halo (34 x 10 = 340 cells) has its cells' nineteen
+// Tiles of the streaming HOME kernel: 30 x 6 cells of a z-plane per block,
+// walking tz planes along z (chosen per lattice, below). Each plane of the
+// tile plus a one-cell halo (32 x 8 = 256 cells, one per thread) has its cells' nineteen
 // post-collision populations rebuilt once into a shared-memory ring of three
 // planes; every cell of the middle plane then pulls its populations from the
-// ring, so a cell's closure terms are evaluated about 1.5 times per step
+// ring, so a cell's closure terms are evaluated about 1.6 times per step
 // (halo and the two extra planes of each z range) instead of once per pulling
 // neighbour, and its moments are read from global memory about as often.
-constexpr int HOME_TX = 32, HOME_TY = 8;
+constexpr int HOME_TX = 30, HOME_TY = 6;
 constexpr int HOME_HX = HOME_TX + 2, HOME_HY = HOME_TY + 2;
-constexpr int HOME_PLANE = HOME_HX * HOME_HY;          // 340 cells
+constexpr int HOME_PLANE = HOME_HX * HOME_HY;          // 256 cells: one per thread
 // The ring keeps each plane's populations only as long as they are pulled:
 // in-plane directions (c_z = 0, nine of them) while the plane is the current
 // one, upward ones (c_z = +1, five) until the plane above is done, downward
 // ones (c_z = -1, five) from the plane below's step through the plane's own
 // (bounce-back reads them). Buffers, in units of 340 floats: in-plane
-// [2 planes][9] at 0, upward [3][5] at 18, downward [2][5] at 33.
-constexpr size_t HOME_SMEM = 43 * HOME_PLANE * sizeof(float);  // 58,480 bytes
+// [2 planes][9] at 0, upward [3][5] at 18, downward [2][5] at 33 (units of one plane).
+constexpr size_t HOME_SMEM = 43 * HOME_PLANE * sizeof(float);  // 44,032 bytes
 
 // Index of direction i within its group (in-plane 0 1 2 3 4 7 8 13 14,
 // upward 5 9 11 16 18, downward 6 10 12 15 17).
@@ -1046,7 +1046,14 @@ __host__ __device__ __forceinline__ void home_tile_cell(const LbmParams &L, cons
 // ceil(nz/tz)), 256 threads, HOME_SMEM bytes of dynamic shared memory.
 // The moments of plane z + 2 and the link words of plane z + 1 are loaded
 // while plane z is pulled and collided, so their latency overlaps the work.
-__global__ void __launch_bounds__(256, 3) k_home_step(LbmParams L, HomeParams H,
+// Interior cell of thread t (t < 180) of a tile: (t mod 30, t div 30).
+__host__ __device__ __forceinline__ bool home_interior(int t, int &ix, int &iy) {
+    ix = t % HOME_TX;
+    iy = t / HOME_TX;
+    return t < HOME_TX * HOME_TY;
+}
+
+__global__ void __launch_bounds__(256, 4) k_home_step(LbmParams L, HomeParams H,
                                                   const float *__restrict__ m_in,
                                                   float *__restrict__ mout,
                                                   const uint8_t *__restrict__ solid,
@@ -1056,38 +1063,28 @@ __global__ void __launch_bounds__(256, 3) k_home_step(LbmParams L, HomeParams H,
     pdl_trigger();
     const int x0 = blockIdx.x * HOME_TX, y0 = blockIdx.y * HOME_TY, z0 = blockIdx.z * tz;
     const int z1 = min(z0 + tz, L.nz);
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const int c0 = tid, c1 = tid + 256;
-    const bool two = c1 < HOME_PLANE;
-    const bool inside = x0 + tx < L.nx && y0 + ty < L.ny;
-    const int col = (y0 + ty) * L.nx + (x0 + tx), plane = L.nx * L.ny;
-    const int xy0 = home_halo_xy(L, x0, y0, c0), xy1 = two ? home_halo_xy(L, x0, y0, c1) : -1;
-    HomeHalo h0, h1;
+    const int tid = threadIdx.x;
+    int ix, iy;
+    const bool worker = home_interior(tid, ix, iy);
+    const bool inside = worker && x0 + ix < L.nx && y0 + iy < L.ny;
+    const int col = (y0 + iy) * L.nx + (x0 + ix), plane = L.nx * L.ny;
+    const int xy = home_halo_xy(L, x0, y0, tid);
+    HomeHalo h;
     // planes z0 - 1 and z0 (q = 0, 1), then plane z0 + 1 loaded ahead
-    home_halo_load(L, m_in, solid, xy0, home_wrap_z(L, z0 - 1), h0);
-    if (two) home_halo_load(L, m_in, solid, xy1, home_wrap_z(L, z0 - 1), h1);
-    home_halo_store(h0, home_sm, 0, c0);
-    if (two) home_halo_store(h1, home_sm, 0, c1);
-    home_halo_load(L, m_in, solid, xy0, z0, h0);
-    if (two) home_halo_load(L, m_in, solid, xy1, z0, h1);
-    home_halo_store(h0, home_sm, 1, c0);
-    if (two) home_halo_store(h1, home_sm, 1, c1);
-    home_halo_load(L, m_in, solid, xy0, home_wrap_z(L, z0 + 1), h0);
-    if (two) home_halo_load(L, m_in, solid, xy1, home_wrap_z(L, z0 + 1), h1);
+    home_halo_load(L, m_in, solid, xy, home_wrap_z(L, z0 - 1), h);
+    home_halo_store(h, home_sm, 0, tid);
+    home_halo_load(L, m_in, solid, xy, z0, h);
+    home_halo_store(h, home_sm, 1, tid);
+    home_halo_load(L, m_in, solid, xy, home_wrap_z(L, z0 + 1), h);
     uint32_t lk_next = (links && inside) ? links[z0 * plane + col] : 0u;
     for (int z = z0; z < z1; ++z) {
         const int q = z - z0 + 1;
-        home_halo_store(h0, home_sm, q + 1, c0);
-        if (two) home_halo_store(h1, home_sm, q + 1, c1);
-        if (z + 1 < z1) {  // plane z + 2 is the next iteration's z + 1
-            const int gz = home_wrap_z(L, z + 2);
-            home_halo_load(L, m_in, solid, xy0, gz, h0);
-            if (two) home_halo_load(L, m_in, solid, xy1, gz, h1);
-        }
+        home_halo_store(h, home_sm, q + 1, tid);
+        if (z + 1 < z1) home_halo_load(L, m_in, solid, xy, home_wrap_z(L, z + 2), h);
         const uint32_t lk = lk_next;
         if (links && inside && z + 1 < z1) lk_next = links[(z + 1) * plane + col];
         __syncthreads();
-        home_tile_cell(L, H, m_in, mout, lk, home_sm, q, x0, y0, z, tx, ty);
+        if (worker) home_tile_cell(L, H, m_in, mout, lk, home_sm, q, x0, y0, z, ix, iy);
         __syncthreads();
     }
 }
