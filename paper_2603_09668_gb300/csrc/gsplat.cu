@@ -450,7 +450,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Per pixel, front to back: w = T alpha, dL/dc += g w, dL/dalpha = g . (T c -
 // (C - C_<=i) / (1 - alpha)), then dL/do, dL/dmu', dL/dconic; each Gaussian's
-// nine sums over a warp's pixels go to memory with one atomic each.
+// nine sums over a warp's pixels go to memory from nine lanes at once.
 __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
     GsCam c, int n, const uint32_t *__restrict__ list, const int2 *__restrict__ ranges,
     const float *__restrict__ mu, const float *__restrict__ conic,
@@ -504,12 +504,14 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_render_bwd(
                 T *= 1.0f - a;
             }
             if (__any_sync(0xffffffffu, hit)) {
-                const int g = s_id[k];
+                // the xor sums leave all nine totals in every lane: lane j adds total j
+                float mine = 0.0f;
 #pragma unroll
                 for (int j = 0; j < 9; ++j) {
                     const float sj = warp_sum(v[j]);
-                    if (lane == 0 && sj != 0.0f) atomicAdd(&g2d[(int64_t)j * n + g], sj);
+                    mine = lane == j ? sj : mine;
                 }
+                if (lane < 9 && mine != 0.0f) atomicAdd(&g2d[(int64_t)lane * n + s_id[k]], mine);
             }
         }
         __syncthreads();
