@@ -159,20 +159,16 @@ class WindInversion:
     pass of `substeps` substeps with a checkpoint every `every` substeps and
     one reverse pass. w_data weights the position term (default 1 / (n h^2)
     with h the grid spacing: the mean squared position error in grid cells);
-    lam_phys weights L_phys; optimizer is "vector_adam" or "adam". With
-    use_graph (positions observed) the forward, losses and reverse pass of an
-    iteration (about two thousand small launches) are captured once per
-    interval in a CUDA graph and replayed; the optimiser step stays outside."""
+    lam_phys weights L_phys; optimizer is "vector_adam" or "adam"."""
 
     def __init__(self, mpm: B.MPM, guide: LbmGuide, substeps: int, every: int, iters: int,
                  lr: float, lam_phys: float, w_data: Optional[float] = None, eps_guide=1e-6,
-                 optimizer: str = "vector_adam", use_graph: bool = True):
+                 optimizer: str = "vector_adam"):
         if substeps < 1 or every < 1 or iters < 1:
             raise ValueError("substeps, every and iters must be >= 1")
         if optimizer not in ("vector_adam", "adam"):
             raise ValueError(f"unknown optimizer {optimizer!r}")
         self.optimizer = optimizer
-        self.use_graph = use_graph
         self.mpm, self.guide = mpm, guide
         self.substeps, self.every, self.iters = substeps, every, iters
         self.lr, self.lam_phys, self.w_data, self.eps_guide = lr, lam_phys, w_data, eps_guide
@@ -209,62 +205,39 @@ class WindInversion:
         g = B.MpmState.empty_like(state0)
         tape = torch.empty(max(every - 1, 1) * 24 * max(n, 1), dtype=torch.float32, device=dev)
 
-        # fixed buffers, so that one iteration's launches can be replayed
-        val_w = torch.zeros((nf ** 3, 3), dtype=torch.float32, device=dev)
-        guide_w = torch.empty((3, nf ** 3), dtype=torch.float32, device=dev)
-        target_w = torch.empty_like(x_observed[0])
-        loss_w = torch.zeros(2, dtype=torch.float32, device=dev)
-        wind = _wind(val_w.view(1, nf, nf, nf, 3))
-        g_wind = g_values.view(1, nf, nf, nf, 3)
-
-        def gradient(t_k):
-            """loss_w and g_values of the current force val_w (no host sync)."""
-            for c, a in zip(run, state):
-                c.copy_(a)
-            for (k0, k1), ck in zip(segs, ckpts):
-                for c, a in zip(ck, run):
-                    c.copy_(a)
-                mpm.rollout(run, pinned, None, wind, t_k + k0 * mpm.dt, k1 - k0, 0)
-            for a in g:
-                a.zero_()
-            g_values.zero_()
-            loss_w.zero_()
-            if views is None:
-                B.position_loss(run.x, target_w, loss_w[0:1], w_data, g.x)
-            else:
-                views.loss(run, target_w, w_data, loss_w[0:1], g, scratch)
-            for (k0, k1), ck in zip(reversed(segs), reversed(ckpts)):
-                mpm.segment_adjoint(ck, tape, g, pinned, wind, t_k + k0 * mpm.dt, k1 - k0, g_wind)
-            if self.lam_phys > 0.0:
-                B.wind_phys_loss(val_w, guide_w, loss_w[1:2], g_values, self.eps_guide,
-                                 self.lam_phys)
-
-        use_graph = self.use_graph and views is None
         t = t0
         for k in range(K):
-            guide_w.copy_(guide.advance(state.x, lbm_steps))
-            guides[k].copy_(guide_w)
-            target_w.copy_(x_observed[k])
-            val_w.zero_()
+            guides[k].copy_(guide.advance(state.x, lbm_steps))
+            val = values[k]
+            wind = _wind(val.view(1, nf, nf, nf, 3))
             m_buf.zero_()
             v_buf.zero_()
-            graph = None
             for it in range(self.iters):
-                if graph is None and use_graph and it >= 1:  # after one eager warm-up
-                    graph = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(graph):
-                        gradient(t)
-                if graph is not None:
-                    graph.replay()
+                # forward with a checkpoint at the start of every segment
+                for c, a in zip(run, state):
+                    c.copy_(a)
+                for (k0, k1), ck in zip(segs, ckpts):
+                    for c, a in zip(ck, run):
+                        c.copy_(a)
+                    mpm.rollout(run, pinned, None, wind, t + k0 * mpm.dt, k1 - k0, 0)
+                # losses and the reverse pass
+                for a in g:
+                    a.zero_()
+                g_values.zero_()
+                if views is None:
+                    B.position_loss(run.x, x_observed[k], history[k, it, 0:1], w_data, g.x)
                 else:
-                    gradient(t)
-                history[k, it].copy_(loss_w)
+                    views.loss(run, x_observed[k], w_data, history[k, it, 0:1], g, scratch)
+                for (k0, k1), ck in zip(reversed(segs), reversed(ckpts)):
+                    mpm.segment_adjoint(ck, tape, g, pinned, wind, t + k0 * mpm.dt, k1 - k0,
+                                        g_values.view(1, nf, nf, nf, 3))
+                if self.lam_phys > 0.0:
+                    B.wind_phys_loss(val, guides[k], history[k, it, 1:2], g_values,
+                                     self.eps_guide, self.lam_phys)
                 if vec:
-                    B.vector_adam_step(val_w, g_values, m_buf, v_buf, it + 1, self.lr)
+                    B.vector_adam_step(val, g_values, m_buf, v_buf, it + 1, self.lr)
                 else:
-                    B.adam_step(val_w, g_values, m_buf, v_buf, it + 1, self.lr)
-            del graph
-            values[k].copy_(val_w)
+                    B.adam_step(val, g_values, m_buf, v_buf, it + 1, self.lr)
             # commit the interval with the optimised force
             mpm.rollout(state, pinned, None, wind, t, S, 0)
             x_end[k].copy_(state.x)
