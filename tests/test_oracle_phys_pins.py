@@ -215,3 +215,23 @@ def test_vector_adam_is_rotation_equivariant():
     g = rng.standard_normal((n, 3))
     p1, _, _ = phys.vector_adam_step(np.zeros((n, 3)), g, np.zeros((n, 3)), np.zeros(n), 1, 0.1)
     assert np.allclose(p1, -0.1 * g / np.linalg.norm(g, axis=1)[:, None], atol=1e-9)
+
+
+def test_wind_node_positions_are_the_wind_field_nodes():
+    """The guide is sampled at inputs.wind_node_positions; sampling the wind
+    field there must return its node values exactly (same node order, x
+    fastest), so L_phys compares each node's force with the flow at that node."""
+    from paper_2603_09668_gb300 import inputs
+
+    nf = 5
+    vals = inputs.fourier_wind(nf, 1, seed=3).astype(np.float64)
+    pos = inputs.wind_node_positions(nf).astype(np.float64)
+    got = oracle.wind_sample(vals, nf, 1, 1.0, pos, 0.0)
+    assert np.allclose(got.T, vals[0].reshape(-1, 3), atol=1e-12)
+
+
+def test_gaussian_scene_ties_are_exact():
+    from paper_2603_09668_gb300 import inputs
+
+    x, *_ = inputs.gaussian_scene(n=40, depth_ties=True, seed=1)
+    assert np.array_equal(x[2, 4::4], x[2, 3:-1:4][: len(x[2, 4::4])])
