@@ -147,3 +147,33 @@ def test_gradient_by_central_differences():
             fd = (L(ap["x"], ap["F"], ap["color"], ap["opacity"]) -
                   L(am["x"], am["F"], am["color"], am["opacity"])) / (2 * eps)
             assert grads[name].reshape(-1)[k] == pytest.approx(fd, rel=1e-5, abs=1e-8), (name, k)
+
+
+def test_off_axis_shape_is_the_projected_covariance():
+    """An isotropic Gaussian off the axis projects to sigma^2 J J^T, J the
+    Jacobian of the pinhole projection at its centre (taken here by central
+    differences of the projection itself). The image's intensity covariance
+    equals that times the variance factor of a 2D Gaussian cut at Mahalanobis
+    radius 3, (1 - 5.5 e^-4.5) / (1 - e^-4.5)."""
+    W, H, f = 96, 96, 120.0
+    cam = G.camera(np.eye(3), np.zeros(3), f, f, 48.0, 48.0, W, H)
+    X = np.array([0.55, -0.4, 1.6])  # well off the axis: J couples z into x and y
+    sig = 0.03
+    img = G.render(X[:, None], eye9(1), iso6(1, sig ** 2), np.ones((3, 1)), np.array([0.5]), cam)
+
+    def proj(t):
+        return np.array([f * t[0] / t[2] + 48.0, f * t[1] / t[2] + 48.0])
+
+    J = np.zeros((2, 3))
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = 1e-6
+        J[:, a] = (proj(X + e) - proj(X - e)) / 2e-6
+    S2 = sig ** 2 * J @ J.T
+    py, px = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    w = img[0] / img[0].sum()
+    mx, my = np.sum(w * px), np.sum(w * py)
+    cov = np.array([[np.sum(w * (px - mx) ** 2), np.sum(w * (px - mx) * (py - my))],
+                    [np.sum(w * (px - mx) * (py - my)), np.sum(w * (py - my) ** 2)]])
+    k = (1 - 5.5 * np.exp(-4.5)) / (1 - np.exp(-4.5))
+    assert np.allclose(cov, k * S2, rtol=0.02, atol=0.02 * np.abs(S2).max())
