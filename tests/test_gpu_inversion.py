@@ -186,3 +186,87 @@ def test_inversion_argument_checks():
         I.WindInversion(None, None, 0, 25, 10, 1.0, 0.1)
     with pytest.raises(ValueError):
         I.WindInversion(None, None, 100, 25, 10, 1.0, 0.1, optimizer="sgd")
+
+
+def test_inversion_loop_matches_the_oracle_loop():
+    """The whole sequential inversion on a tiny case (192-particle sheet, 16^3
+    grid, 4^3 wind grid, 16^3 HOME-LBM lattices, two intervals of 10 substeps,
+    three VectorAdam iterations each): the GPU loop (float32, checkpointed
+    adjoint every 5 substeps) against the same loop written with the FP64
+    oracle's pieces. The observations come from the oracle's forward
+    simulation. Compared on the nodes whose first gradient is well above the
+    float32 noise, where the normalised step direction is determined."""
+    from oracle import phys
+    from paper_2603_09668_gb300 import inversion as I
+
+    sc = inputs.sheet_scene(nu=12, nv=8, n_grid=16, n_substeps=10, dt=2e-4, wind_nf=4,
+                            wind_frames=1, seed=0)
+    prm, n, dt = sc.params(), sc.n, sc.dt
+    nf, K, S, every, iters, lr, lam = 4, 2, 10, 5, 3, 1.0, 0.1
+    n_cells, tau, lbm_steps, scale = 16, 0.6, 5, 4000.0
+    shape = (n_cells,) * 3
+    d = np.array([1.0, 0.0, 0.35])
+    u_in = tuple(0.05 * d / np.linalg.norm(d))
+    u_guide = I.rotate_about_y(u_in, 10.0)
+    nodes = inputs.wind_node_positions(nf).astype(np.float64)
+    st0 = tuple(a.astype(np.float64) for a in inputs.rest_state(sc.x))
+
+    def guide_step(m, x, inlet):
+        solid = oracle.voxelize(x, shape, 1.0 / n_cells)
+        m = oracle.home_step(shape, tau, m, lbm_steps, u_in=inlet, bc_x=1, solid=solid)
+        _, u = oracle.home_macroscopic(shape, m, solid=solid)
+        return m, phys.sample_velocity_field(shape, u, nodes)
+
+    def wind_of(val):
+        return (val.reshape(1, nf, nf, nf, 3), nf, 1, 1.0)
+
+    # observations: the oracle's drag-driven forward simulation
+    m_gt, st, x_obs, t = oracle.home_init(shape, 1.0, u_in, tau), st0, [], 0.0
+    for k in range(K):
+        m_gt, ug = guide_step(m_gt, st[0], u_in)
+        w = wind_of(phys.drag_force(ug, scale))
+        for j in range(S):
+            st = oracle.mpm_substep(prm, st, w, t + j * dt, sc.pinned)
+        x_obs.append(st[0])
+        t += S * dt
+    # the oracle's inversion
+    w_data = prm["n_grid"] ** 2 / n
+    m_g, st, t = oracle.home_init(shape, 1.0, u_guide, tau), st0, 0.0
+    ref_vals, first_g = [], []
+    for k in range(K):
+        m_g, guide = guide_step(m_g, st[0], u_guide)
+        val, mm, vv = np.zeros((nf ** 3, 3)), np.zeros((nf ** 3, 3)), np.zeros(nf ** 3)
+        for it in range(iters):
+            states = [st]
+            for j in range(S):
+                states.append(oracle.mpm_substep(prm, states[-1], wind_of(val), t + j * dt,
+                                                 sc.pinned))
+            _, gx = phys.position_loss(states[-1][0], x_obs[k], w_data)
+            g = (gx, np.zeros((3, n)), np.zeros((9, n)), np.zeros((9, n)))
+            gw = np.zeros((1, nf, nf, nf, 3))
+            for j in reversed(range(S)):
+                g, gw, _ = oracle.mpm_substep_adjoint(prm, states[j], wind_of(val), t + j * dt, g,
+                                                      sc.pinned, gw)
+            gtot = gw.reshape(-1, 3) + lam * phys.phys_loss(val, guide)[1]
+            if it == 0:
+                first_g.append(np.linalg.norm(gtot, axis=1))
+            val, mm, vv = phys.vector_adam_step(val, gtot, mm, vv, it + 1, lr)
+        ref_vals.append(val)
+        for j in range(S):
+            st = oracle.mpm_substep(prm, st, wind_of(val), t + j * dt, sc.pinned)
+        t += S * dt
+    # the GPU loop on the same observations
+    mpm = B.MPM.from_params(prm, max_particles=n)
+    guide = I.LbmGuide(n_cells, tau, u_guide, nf, model="home")
+    inv = I.WindInversion(mpm, guide, S, every, iters, lr, lam)
+    state0 = B.MpmState(*(to_dev(a.astype(np.float32)) for a in st0))
+    obs = to_dev(np.stack(x_obs).astype(np.float32))
+    res = inv.reconstruct(state0, to_dev(sc.pinned), obs, lbm_steps)
+    got = res.values.cpu().numpy()
+    for k in range(K):
+        strong = first_g[k] > 1e-3 * first_g[k].max()
+        assert strong.sum() >= 8
+        e = rel_l2(got[k][strong], ref_vals[k][strong])
+        assert e <= 2e-3, (k, e, int(strong.sum()))
+    guide.close()
+    mpm.close()
