@@ -190,19 +190,21 @@ def test_inversion_argument_checks():
 
 def test_inversion_loop_matches_the_oracle_loop():
     """The whole sequential inversion on a tiny case (192-particle sheet, 16^3
-    grid, 4^3 wind grid, 16^3 HOME-LBM lattices, two intervals of 10 substeps,
-    three VectorAdam iterations each): the GPU loop (float32, checkpointed
-    adjoint every 5 substeps) against the same loop written with the FP64
-    oracle's pieces. The observations come from the oracle's forward
-    simulation. Compared on the nodes whose first gradient is well above the
+    grid, 4^3 wind grid, 16^3 HOME-LBM lattices, two intervals of 20 substeps
+    of 1 ms, three VectorAdam iterations each): the GPU loop (float32,
+    checkpointed adjoint every 5 substeps) against the same loop written with
+    the FP64 oracle's pieces. The observations come from the oracle's forward
+    simulation. The intervals are long enough that the particles move far
+    more than float32 resolves (the position term is a difference of nearby
+    positions). Compared on the nodes whose first gradient is well above the
     float32 noise, where the normalised step direction is determined."""
     from oracle import phys
     from paper_2603_09668_gb300 import inversion as I
 
-    sc = inputs.sheet_scene(nu=12, nv=8, n_grid=16, n_substeps=10, dt=2e-4, wind_nf=4,
+    sc = inputs.sheet_scene(nu=12, nv=8, n_grid=16, n_substeps=20, dt=1e-3, wind_nf=4,
                             wind_frames=1, seed=0)
     prm, n, dt = sc.params(), sc.n, sc.dt
-    nf, K, S, every, iters, lr, lam = 4, 2, 10, 5, 3, 1.0, 0.1
+    nf, K, S, every, iters, lr, lam = 4, 2, 20, 5, 3, 1.0, 0.1
     n_cells, tau, lbm_steps, scale = 16, 0.6, 5, 4000.0
     shape = (n_cells,) * 3
     d = np.array([1.0, 0.0, 0.35])
