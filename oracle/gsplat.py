@@ -27,6 +27,12 @@ Definitions (readings where the paper is silent are marked R):
   - C = sum_i T_i c_i alpha_i, T_i = prod_{j<i} (1 - alpha_j), the Gaussians
     in increasing t_z (ties by index); no background term (as printed).
   - Image layout [3][H][W].
+  - D-SSIM (the structural term of L_render, Sec. 3.3): 1 - mean over pixels
+    and channels of SSIM = ((2 mu_x mu_y + C1)(2 s_xy + C2)) / ((mu_x^2 +
+    mu_y^2 + C1)(s_x^2 + s_y^2 + C2)) with the local means and (co)variances
+    taken under an 11 x 11 Gaussian window of standard deviation 1.5, zero
+    outside the image, C1 = 0.01^2, C2 = 0.03^2 (R: the usual SSIM constants
+    and window, which the paper does not restate).
 """
 from __future__ import annotations
 
@@ -151,3 +157,35 @@ def l1_loss(image, target):
     """(mean |image - target|, its gradient) over all values."""
     d = np.asarray(image, np.float64) - np.asarray(target, np.float64)
     return float(np.mean(np.abs(d))), np.sign(d) / d.size
+
+
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+
+
+def _ssim_window():
+    k = torch.exp(-((torch.arange(11, dtype=DT) - 5.0) ** 2) / (2 * 1.5 ** 2))
+    k = k / k.sum()
+    return torch.outer(k, k)
+
+
+def _dssim(img, tgt):
+    """img, tgt (C, H, W) float64 tensors -> 1 - mean SSIM."""
+    C = img.shape[0]
+    w = _ssim_window().expand(C, 1, 11, 11).contiguous()
+    blur = lambda a: torch.nn.functional.conv2d(a[None], w, padding=5, groups=C)[0]
+    mx, my = blur(img), blur(tgt)
+    sxx = blur(img * img) - mx * mx
+    syy = blur(tgt * tgt) - my * my
+    sxy = blur(img * tgt) - mx * my
+    ssim = ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / (
+        (mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+    return 1.0 - ssim.mean()
+
+
+def dssim_loss(image, target):
+    """(1 - mean SSIM, its gradient with respect to image) for [C][H][W]."""
+    img = torch.tensor(np.ascontiguousarray(image, np.float64), requires_grad=True)
+    tgt = torch.tensor(np.ascontiguousarray(target, np.float64))
+    d = _dssim(img, tgt)
+    d.backward()
+    return float(d.detach()), img.grad.numpy()

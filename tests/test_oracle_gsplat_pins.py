@@ -110,6 +110,55 @@ def test_pixel_subset_matches_the_full_image():
     assert np.allclose(sub, img[:, pix[:, 1], pix[:, 0]], atol=1e-15)
 
 
+def test_dssim_identical_images_and_brute_force():
+    rng = np.random.default_rng(3)
+    a = rng.random((2, 13, 17))
+    d, g = G.dssim_loss(a, a)
+    assert d == pytest.approx(0.0, abs=1e-12)
+    assert np.abs(g).max() < 1e-12  # a minimum
+    # brute force on a tiny image: window sums written out pixel by pixel
+    b = rng.random((1, 7, 6))
+    c = rng.random((1, 7, 6))
+    k1 = np.exp(-((np.arange(11) - 5.0) ** 2) / (2 * 1.5 ** 2))
+    k1 /= k1.sum()
+    H, W = 7, 6
+    tot = 0.0
+    for yy in range(H):
+        for xx in range(W):
+            m = {"x": 0.0, "y": 0.0, "xx": 0.0, "yy": 0.0, "xy": 0.0}
+            for dy in range(-5, 6):
+                for dx in range(-5, 6):
+                    py_, px_ = yy + dy, xx + dx
+                    if 0 <= py_ < H and 0 <= px_ < W:
+                        wgt = k1[dy + 5] * k1[dx + 5]
+                        u, v = b[0, py_, px_], c[0, py_, px_]
+                        m["x"] += wgt * u
+                        m["y"] += wgt * v
+                        m["xx"] += wgt * u * u
+                        m["yy"] += wgt * v * v
+                        m["xy"] += wgt * u * v
+            sx = m["xx"] - m["x"] ** 2
+            sy = m["yy"] - m["y"] ** 2
+            sxy = m["xy"] - m["x"] * m["y"]
+            c1, c2 = 0.01 ** 2, 0.03 ** 2
+            tot += ((2 * m["x"] * m["y"] + c1) * (2 * sxy + c2)) / (
+                (m["x"] ** 2 + m["y"] ** 2 + c1) * (sx + sy + c2))
+    assert G.dssim_loss(b, c)[0] == pytest.approx(1.0 - tot / (H * W), abs=1e-12)
+
+
+def test_dssim_gradient_by_central_differences():
+    rng = np.random.default_rng(4)
+    a, b = rng.random((3, 9, 8)), rng.random((3, 9, 8))
+    _, g = G.dssim_loss(a, b)
+    eps = 1e-6
+    for k in rng.choice(a.size, 10, replace=False):
+        p_, m_ = a.copy(), a.copy()
+        p_.reshape(-1)[k] += eps
+        m_.reshape(-1)[k] -= eps
+        fd = (G.dssim_loss(p_, b)[0] - G.dssim_loss(m_, b)[0]) / (2 * eps)
+        assert g.reshape(-1)[k] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+
+
 def test_l1_loss():
     a = np.array([[0.5, 0.25], [1.0, 0.0]])
     b = np.array([[0.0, 0.5], [1.0, 0.5]])
