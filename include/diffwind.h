@@ -365,6 +365,18 @@ DW_API dw_status gs_render_backward(dw_gs h, const dw_camera *cam, const float *
 DW_API dw_status image_l1_loss(const float *image, const float *target, int64_t n, float weight,
                                float *loss, float *g_image, dw_stream stream);
 
+/* The structural term of L_render (Sec. 3.3): loss (device float,
+ * accumulated) += weight (1 - mean SSIM) over the channels x height x width
+ * values of image against target, SSIM = ((2 mu_x mu_y + C1)(2 s_xy + C2)) /
+ * ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)) with local means and
+ * (co)variances under an 11 x 11 Gaussian window (sigma 1.5, zero outside the
+ * image), C1 = 0.01^2, C2 = 0.03^2; g_image (may be NULL) += its gradient
+ * with respect to image. workspace: device, 10 x channels x height x width
+ * floats. Images are [channels][height][width]. */
+DW_API dw_status image_dssim_loss(const float *image, const float *target, int32_t channels,
+                                  int32_t height, int32_t width, float weight, float *loss,
+                                  float *g_image, float *workspace, dw_stream stream);
+
 /* ============================================================ batched MPM
  * Many independent scenes, each with its own grid size, material, time step,
  * particle count and wind field, advanced by the same substep as mpm_rollout

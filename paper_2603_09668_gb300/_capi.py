@@ -119,6 +119,7 @@ SIGNATURES = {
     "gs_render_backward": (I32, [VP, P(DwCamera), VP, VP, VP, VP, VP, I64, VP, VP, VP, VP, VP,
                                  VP]),
     "image_l1_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
+    "image_dssim_loss": (I32, [VP, VP, I32, I32, I32, F32, VP, VP, VP, VP]),
     "vector_adam_step": (I32, [VP, VP, VP, VP, I64, F32, F32, F32, F32, I32, VP]),
     "position_loss": (I32, [VP, VP, I64, F32, VP, VP, VP]),
     "surr_create": (I32, [I32, P(VP)]),

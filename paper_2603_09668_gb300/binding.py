@@ -27,7 +27,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "lbm_home_sample_velocity",
            "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
            "adam_step", "wind_drag_force", "position_loss", "wind_field_scores", "vector_adam_step", "camera",
-           "gs_covariance", "image_l1_loss", "GaussianRenderer", "MPM", "LBM", "surr_create",
+           "gs_covariance", "image_l1_loss", "image_dssim_loss", "GaussianRenderer", "MPM", "LBM", "surr_create",
            "surr_destroy", "surr_num_params", "surr_set_params", "surr_get_params",
            "surr_get_grads", "surr_zero_grads", "surr_features", "surr_set_features",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
@@ -504,6 +504,19 @@ def image_l1_loss(image, target, loss, weight=1.0, g_image=None, stream=None):
     check(lib().image_l1_loss(_dev(image, name="image"), _dev(target, name="target"),
                               int(image.numel()), float(weight), _dev(loss, name="loss"),
                               _dev(g_image, name="g_image"), _stream(stream)))
+    return loss
+
+
+def image_dssim_loss(image, target, loss, weight=1.0, g_image=None, workspace=None, stream=None):
+    """loss += weight (1 - mean SSIM) of image against target ([C][H][W]);
+    g_image += its gradient."""
+    C, H, W = image.shape
+    if workspace is None:
+        workspace = torch.empty(10 * C * H * W, dtype=torch.float32, device=image.device)
+    check(lib().image_dssim_loss(_dev(image, name="image"), _dev(target, name="target"), int(C),
+                                 int(H), int(W), float(weight), _dev(loss, name="loss"),
+                                 _dev(g_image, name="g_image"), _dev(workspace, name="workspace"),
+                                 _stream(stream)))
     return loss
 
 

@@ -635,6 +635,114 @@ __global__ void __launch_bounds__(256) k_image_l1(const float *__restrict__ img,
     }
 }
 
+// ----------------------------------------------------------------- D-SSIM --
+// The structural term of L_render: 1 - mean SSIM with local statistics under
+// an 11 x 11 Gaussian window (sigma 1.5, zero outside the image), computed as
+// separable blurs: horizontal sums of the five maps x, y, x^2, y^2, x y, then
+// vertical sums; the gradient blurs the per-pixel partials back the same way
+// (the window is symmetric, so the transposed blur is the blur).
+
+struct SsimWin {
+    float w[11];
+};
+
+__global__ void k_ssim_h5(const float *__restrict__ x, const float *__restrict__ y, int C, int H,
+                          int W, SsimWin k, float *__restrict__ out) {
+    const int64_t plane = (int64_t)C * H * W;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= plane) return;
+    const int px = (int)(i % W);
+    const int64_t row = i - px;
+    float s[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int d = -5; d <= 5; ++d) {
+        const int q = px + d;
+        if (q < 0 || q >= W) continue;
+        const float a = x[row + q], b = y[row + q], w = k.w[d + 5];
+        s[0] += w * a;
+        s[1] += w * b;
+        s[2] += w * a * a;
+        s[3] += w * b * b;
+        s[4] += w * a * b;
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) out[m * plane + i] = s[m];
+}
+
+// One-direction blur of `maps` planes of H x W (horizontal: dir 0, vertical: 1).
+__global__ void k_blur(const float *__restrict__ in, int64_t maps, int H, int W, int dir, SsimWin k,
+                       float *__restrict__ out) {
+    const int64_t total = maps * H * W;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int px = (int)(i % W), py = (int)((i / W) % H);
+    const int64_t base = i - px - (int64_t)py * W;  // start of this plane
+    float s = 0.0f;
+#pragma unroll
+    for (int d = -5; d <= 5; ++d) {
+        const int qx = dir == 0 ? px + d : px, qy = dir == 0 ? py : py + d;
+        if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+        s += k.w[d + 5] * in[base + (int64_t)qy * W + qx];
+    }
+    out[i] = s;
+}
+
+// SSIM per pixel from the blurred maps (mu_x, mu_y, <x^2>, <y^2>, <x y>);
+// loss += weight (1 - mean SSIM); part = weight * dD/d(mu_x, <x^2>, <x y>).
+__global__ void __launch_bounds__(256) k_ssim_map(const float *__restrict__ v5, int64_t n,
+                                                  float weight, float *__restrict__ loss,
+                                                  float *__restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    const float scale = -weight / (float)n;
+    float term = 0.0f;
+    if (i < n) {
+        const float A = v5[i], Ay = v5[n + i], B = v5[2 * n + i], Byy = v5[3 * n + i],
+                    Cxy = v5[4 * n + i];
+        const float n1 = 2.0f * A * Ay + C1, n2 = 2.0f * (Cxy - A * Ay) + C2;
+        const float d1 = A * A + Ay * Ay + C1, d2 = (B - A * A) + (Byy - Ay * Ay) + C2;
+        const float dd = d1 * d2;
+        const float S = n1 * n2 / dd;
+        term = S;
+        if (part) {
+            const float dA = 2.0f * Ay * (n2 - n1) / dd - 2.0f * A * n1 * n2 * (d2 - d1) / (dd * dd);
+            const float dB = -S / d2;
+            const float dC = 2.0f * n1 / dd;
+            part[i] = scale * dA;
+            part[n + i] = scale * dB;
+            part[2 * n + i] = scale * dC;
+        }
+    }
+    __shared__ float red[8];
+    term = warp_sum(term);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = term;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < 8 ? red[threadIdx.x] : 0.0f;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) atomicAdd(loss, scale * t + (blockIdx.x == 0 ? weight : 0.0f));
+    }
+}
+
+// g += blur(p_mu) + 2 x blur(p_xx) + y blur(p_xy)
+__global__ void k_ssim_grad(const float *__restrict__ x, const float *__restrict__ y,
+                            const float *__restrict__ bp, int64_t n, float *__restrict__ g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    g[i] += bp[i] + 2.0f * x[i] * bp[n + i] + y[i] * bp[2 * n + i];
+}
+
+static SsimWin ssim_window() {
+    SsimWin k;
+    double w[11], sum = 0.0;
+    for (int i = 0; i < 11; ++i) {
+        w[i] = exp(-((i - 5.0) * (i - 5.0)) / (2.0 * 1.5 * 1.5));
+        sum += w[i];
+    }
+    for (int i = 0; i < 11; ++i) k.w[i] = (float)(w[i] / sum);
+    return k;
+}
+
 struct GsHandle {
     int64_t cap = 0;
     int width = 0, height = 0;
@@ -889,5 +997,30 @@ extern "C" dw_status image_l1_loss(const float *image, const float *target, int6
     k_image_l1<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(image, target, n, weight, loss,
                                                                  g_image);
     DW_LAUNCHED("k_image_l1");
+    return DW_OK;
+}
+
+extern "C" dw_status image_dssim_loss(const float *image, const float *target, int32_t channels,
+                                      int32_t height, int32_t width, float weight, float *loss,
+                                      float *g_image, float *workspace, dw_stream stream) {
+    DW_REQUIRE(channels >= 1 && height >= 1 && width >= 1, "image sizes must be >= 1");
+    const int64_t n = (int64_t)channels * height * width;
+    DW_REQUIRE(10 * n < (1ll << 31), "image too large (10 C H W must be < 2^31)");
+    DW_REQUIRE(image && target && loss && workspace, "image, target, loss and workspace must not be NULL");
+    cudaStream_t s = as_stream(stream);
+    const SsimWin k = ssim_window();
+    float *h5 = workspace, *v5 = workspace + 5 * n;
+    k_ssim_h5<<<grid_for(n, 256), 256, 0, s>>>(image, target, channels, height, width, k, h5);
+    k_blur<<<grid_for(5 * n, 256), 256, 0, s>>>(h5, 5 * (int64_t)channels, height, width, 1, k, v5);
+    float *part = g_image ? workspace : nullptr;  // h5 is free again
+    k_ssim_map<<<grid_for(n, 256), 256, 0, s>>>(v5, n, weight, loss, part);
+    if (g_image) {
+        k_blur<<<grid_for(3 * n, 256), 256, 0, s>>>(part, 3 * (int64_t)channels, height, width, 0,
+                                                     k, v5);
+        k_blur<<<grid_for(3 * n, 256), 256, 0, s>>>(v5, 3 * (int64_t)channels, height, width, 1,
+                                                     k, part);
+        k_ssim_grad<<<grid_for(n, 256), 256, 0, s>>>(image, target, part, n, g_image);
+    }
+    DW_LAUNCHED("image_dssim_loss");
     return DW_OK;
 }

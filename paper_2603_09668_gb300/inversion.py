@@ -115,12 +115,15 @@ def simulate_wind_driven(mpm: B.MPM, guide: LbmGuide, state: B.MpmState, pinned,
 @dataclass
 class RenderObservation:
     """Views of the particle-bound Gaussians: one renderer, its cameras, the
-    Gaussians' rest covariances [6][n], colours [3][n] and opacities [n]."""
+    Gaussians' rest covariances [6][n], colours [3][n] and opacities [n].
+    The image term is L_render's per view, (1 - lambda_ssim) L1 + lambda_ssim
+    D-SSIM with lambda_ssim = 0.1 (Sec. 3.3)."""
     renderer: B.GaussianRenderer
     cameras: list
     sigma0: torch.Tensor
     color: torch.Tensor
     opacity: torch.Tensor
+    lambda_ssim: float = 0.1
 
     def images(self, state: B.MpmState) -> torch.Tensor:
         """[n_views][3][H][W] images of the state."""
@@ -132,14 +135,21 @@ class RenderObservation:
         return out
 
     def loss(self, state: B.MpmState, target: torch.Tensor, weight: float, loss: torch.Tensor,
-             g: B.MpmState, scratch: torch.Tensor):
-        """loss += weight sum over views of |image - target|; g.x and g.F +=
-        its gradient (each view drawn, then differentiated right away)."""
+             g: B.MpmState, scratch: torch.Tensor, workspace: torch.Tensor):
+        """loss += weight 3 H W times L_render summed over the views (with
+        weight = 1 / (3 H W): (1 - lambda) mean |image - target| + lambda
+        D-SSIM per view); g.x and g.F += its gradient (each view drawn, then
+        differentiated right away)."""
         r = self.renderer
+        lam = self.lambda_ssim
+        npix = 3 * r.height * r.width
         for v, cam in enumerate(self.cameras):
             r.render(cam, state.x, state.F, self.sigma0, self.color, self.opacity, scratch[0])
             scratch[1].zero_()
-            B.image_l1_loss(scratch[0], target[v], loss, weight, scratch[1])
+            B.image_l1_loss(scratch[0], target[v], loss, (1.0 - lam) * weight, scratch[1])
+            if lam > 0.0:
+                B.image_dssim_loss(scratch[0], target[v], loss, lam * weight * npix, scratch[1],
+                                   workspace)
             r.backward(cam, state.x, state.F, self.sigma0, self.color, self.opacity, scratch[1],
                        g.x, g.F)
 
@@ -189,6 +199,7 @@ class WindInversion:
             r = views.renderer
             w_data = self.w_data if self.w_data is not None else 1.0 / (3 * r.width * r.height)
             scratch = torch.empty((2, 3, r.height, r.width), dtype=torch.float32, device=dev)
+            ssim_ws = torch.empty(10 * 3 * r.height * r.width, dtype=torch.float32, device=dev)
         segs = [(k0, min(S, k0 + every)) for k0 in range(0, S, every)]
 
         values = torch.zeros((K, nf ** 3, 3), dtype=torch.float32, device=dev)
@@ -227,7 +238,8 @@ class WindInversion:
                 if views is None:
                     B.position_loss(run.x, x_observed[k], history[k, it, 0:1], w_data, g.x)
                 else:
-                    views.loss(run, x_observed[k], w_data, history[k, it, 0:1], g, scratch)
+                    views.loss(run, x_observed[k], w_data, history[k, it, 0:1], g, scratch,
+                               ssim_ws)
                 for (k0, k1), ck in zip(reversed(segs), reversed(ckpts)):
                     mpm.segment_adjoint(ck, tape, g, pinned, wind, t + k0 * mpm.dt, k1 - k0,
                                         g_values.view(1, nf, nf, nf, 3))

@@ -100,6 +100,22 @@ def test_full_size_render_on_sampled_pixels():
     r.close()
 
 
+def test_dssim_matches_oracle():
+    rng = np.random.default_rng(9)
+    a = rng.random((3, 37, 29)).astype(np.float32)  # no side a multiple of the window
+    b = np.clip(a + 0.1 * rng.standard_normal(a.shape), 0, 1).astype(np.float32)
+    ref_loss, ref_g = G.dssim_loss(a, b)
+    loss = torch.zeros(1, device="cuda")
+    g = torch.zeros((3, 37, 29), device="cuda")
+    B.image_dssim_loss(to_dev(a), to_dev(b), loss, 0.5, g)
+    assert loss.item() == pytest.approx(0.5 * ref_loss, rel=1e-4)
+    assert rel_l2(g.cpu().numpy(), 0.5 * ref_g) <= 1e-4
+    # identical images: zero loss
+    loss.zero_()
+    B.image_dssim_loss(to_dev(a), to_dev(a), loss)
+    assert abs(loss.item()) < 1e-5
+
+
 def test_l1_loss_and_edge_cases():
     rng = np.random.default_rng(8)
     a = rng.random((3, 17, 13)).astype(np.float32)
