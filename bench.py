@@ -670,7 +670,8 @@ def bench_inversion(dev, iters=40):
                              f"{case['n_intervals']} intervals x {iters} iterations x "
                              f"{case['substeps']} substeps (forward + adjoint), guide inlet "
                              f"{case['inlet_error_deg']} deg off; lambda_phys 0.1; render: two 128 x 128 views, "
-                             f"L1, wall time includes the ground truth and its images")
+                             f"0.9 L1 + 0.1 D-SSIM, wall time includes the ground truth and "
+                             f"its images")
     return out
 
 
