@@ -111,3 +111,10 @@ def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_capi, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _capi.lib()
+
+
+def test_every_declared_entry_point_has_a_ctypes_signature():
+    """The Python binding marshals every entry point include/*.h declares."""
+    src = open(os.path.join(ROOT, "paper_2603_09668_gb300", "_capi.py")).read()
+    missing = [n for n in declared_functions() if f'"{n}"' not in src]
+    assert not missing, missing
