@@ -180,26 +180,6 @@ __global__ void __launch_bounds__(256, 5) k_lbm_aa_even(LbmParams L, float *f,
     }
 }
 
-// Per-cell link mask for the odd kernel: bit 0 = the cell is solid, bit i =
-// the neighbour x + c_i (after the periodic wraps) is solid. Built once per
-// lbm_step call so that the odd kernel reads 4 bytes instead of 18 masks.
-__global__ void k_lbm_links(LbmParams L, const uint8_t *__restrict__ solid,
-                            uint32_t *__restrict__ links) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
-    const int x = cell % L.nx, y = (cell / L.nx) % L.ny, z = cell / (L.nx * L.ny);
-    uint32_t m = solid[cell] ? 1u : 0u;
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        int tx = x + D3Q19::cx(i);
-        if (L.bc_x == 1 && (tx < 0 || tx > L.nx - 1)) continue;  // outside: no solid bit
-        int t = cell_index(L, wrapc(tx, L.nx), wrapc(y + D3Q19::cy(i), L.ny),
-                           wrapc(z + D3Q19::cz(i), L.nz));
-        if (solid[t]) m |= 1u << i;
-    }
-    links[cell] = m;
-}
-
 // Offsets of the neighbours with the periodic wraps folded in: the neighbour
 // x + c is cell + off(c) (m = -1 side, p = +1 side of each axis).
 struct NbrOffsets {
@@ -220,6 +200,28 @@ __device__ __forceinline__ NbrOffsets nbr_offsets(const LbmParams &L, int x, int
     o.zm = z == 0 ? (L.nz - 1) * sz : -sz;
     o.zp = z == L.nz - 1 ? -(L.nz - 1) * sz : sz;
     return o;
+}
+
+// Per-cell link mask for the odd kernel: bit 0 = the cell is solid, bit i =
+// the neighbour x + c_i (after the periodic wraps) is solid, so that the
+// kernels read 4 bytes instead of 18 masks. Lattice-row launch: the 19 mask
+// bytes of a cell come from three rows of three planes, shared by the
+// neighbouring threads through L1.
+__global__ void __launch_bounds__(256) k_lbm_links(LbmParams L, const uint8_t *__restrict__ solid,
+                                                   uint32_t *__restrict__ links) {
+    pdl_wait();  // the mask may come from the previous kernel (voxelize)
+    pdl_trigger();
+    int x, y, z, cell;
+    if (!lattice_cell(L, x, y, z, cell)) return;
+    const NbrOffsets o = nbr_offsets(L, x, y, z);
+    uint32_t m = solid[cell] ? 1u : 0u;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int cx = D3Q19::cx(i);
+        if (L.bc_x == 1 && ((cx < 0 && x == 0) || (cx > 0 && x == L.nx - 1))) continue;  // no solid bit outside
+        if (solid[cell + o.off(cx, D3Q19::cy(i), D3Q19::cz(i))]) m |= 1u << i;
+    }
+    links[cell] = m;
 }
 
 __global__ void __launch_bounds__(256, 5) k_lbm_aa_odd(LbmParams L, float *f,
@@ -506,6 +508,7 @@ struct LbmHandle {
     float *tape = nullptr;    // [max_tape][19][ncell]
     float *gtmp = nullptr;    // [19][ncell]
     uint32_t *links = nullptr;  // [ncell]
+    const uint8_t *links_for = nullptr;  // mask whose link words lbm_cache_mask keeps in links
     bool home_attr_set = false;  // k_home_step's shared-memory limit raised, tz chosen
     int home_tz = 16;            // planes per block of k_home_step
 };
@@ -588,7 +591,36 @@ static void lattice_launch(const LbmParams &L, dim3 &grid, dim3 &block) {
     grid = dim3((unsigned)((L.nx + bx - 1) / bx), (unsigned)L.ny, (unsigned)L.nz);
 }
 
+// Link words for a call with mask `solid`: the cached words when the mask is
+// the one registered by lbm_cache_mask, else rebuilt into the handle's
+// buffer (which drops a registered mask). NULL without a mask.
+static dw_status links_for_call(LbmHandle *h, const uint8_t *solid, cudaStream_t s,
+                                const uint32_t **links) {
+    *links = nullptr;
+    if (!solid) return DW_OK;
+    if (solid != h->links_for) {
+        h->links_for = nullptr;
+        dim3 rg, rb;
+        lattice_launch(h->L, rg, rb);
+        DW_CUDA(launch_pdl3(k_lbm_links, rg, rb, s, h->L, solid, h->links));
+    }
+    *links = h->links;
+    return DW_OK;
+}
+
 }  // namespace dw
+
+extern "C" dw_status lbm_cache_mask(dw_lbm h, const uint8_t *solid, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    h->links_for = nullptr;
+    if (!solid) return DW_OK;
+    const uint32_t *links = nullptr;
+    dw_status st = links_for_call(h, solid, as_stream(stream), &links);
+    if (st != DW_OK) return st;
+    h->links_for = solid;
+    DW_LAUNCHED("lbm_cache_mask");
+    return DW_OK;
+}
 
 extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t steps,
                               dw_stream stream) {
@@ -597,12 +629,9 @@ extern "C" dw_status lbm_step(dw_lbm h, float *f, const uint8_t *solid, int32_t 
     DW_REQUIRE(steps >= 0, "steps must be >= 0");
     cudaStream_t s = as_stream(stream);
     const LbmParams &L = h->L;
-    unsigned grid = grid_for(L.ncell, 256);
     const uint32_t *links = nullptr;
-    if (solid) {
-        k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
-        links = h->links;
-    }
+    dw_status st = links_for_call(h, solid, s, &links);
+    if (st != DW_OK) return st;
     dim3 rg, rb;
     lattice_launch(L, rg, rb);
     for (int k = 0; k + 1 < steps; k += 2) {
@@ -628,12 +657,9 @@ extern "C" dw_status lbm_step_adjoint(dw_lbm h, const float *f_in, float *g_f,
     cudaStream_t s = as_stream(stream);
     const LbmParams &L = h->L;
     const size_t lat = 19 * (size_t)L.ncell;
-    unsigned grid = grid_for(L.ncell, 256);
     const uint32_t *links = nullptr;
-    if (solid) {
-        k_lbm_links<<<grid, 256, 0, s>>>(L, solid, h->links);
-        links = h->links;
-    }
+    dw_status st = links_for_call(h, solid, s, &links);
+    if (st != DW_OK) return st;
     dim3 rg, rb;
     lattice_launch(L, rg, rb);
     // states f(1) .. f(steps-1) into tape[0 .. steps-2]
@@ -1224,10 +1250,8 @@ extern "C" dw_status lbm_home_step(dw_lbm h, float *m, const uint8_t *solid, int
     const LbmParams &L = h->L;
     const HomeParams H = home_params(h->desc);
     const uint32_t *links = nullptr;
-    if (solid) {
-        k_lbm_links<<<grid_for(L.ncell, 256), 256, 0, s>>>(L, solid, h->links);
-        links = h->links;
-    }
+    dw_status st = links_for_call(h, solid, s, &links);
+    if (st != DW_OK) return st;
     if (!h->home_attr_set) {
         DW_CUDA(cudaFuncSetAttribute(k_home_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)HOME_SMEM));
