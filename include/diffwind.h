@@ -63,6 +63,17 @@ DW_API const char *dw_last_error(void);
 /* Library version string. */
 DW_API const char *dw_version(void);
 
+/* FP32 throughput probe (a measurement aid; the paper has no counterpart):
+ * launches `blocks` CTAs of 256 threads, each thread running `iters` x 128
+ * fused multiply-adds on 16 independent chains, as scalar FFMA (paired = 0)
+ * or as 64 float2 FFMA2 instructions (paired = 1). *flops receives the
+ * launch's floating-point operation count (2 per multiply-add); the caller
+ * times the launch on `stream` (asynchronous). out is a device float array
+ * of at least `blocks` entries that is written only to keep the chains live.
+ * Errors: DW_ERR_ARG for NULL pointers or counts < 1. */
+DW_API dw_status dw_fp32_probe(int32_t paired, int32_t iters, int32_t blocks, float *out,
+                               double *flops, dw_stream stream);
+
 /* ===================================================================== wind
  * Wind force field a_w(x, t) (Sec. 3: the wind is a grid field whose force
  * property acts on the MPM background grid; Sec. 3.3: one field per time step).
@@ -108,7 +119,14 @@ DW_API dw_status wind_field_sample_adjoint(const dw_wind_field *w, const float *
  * particle is left unchanged.
  */
 enum { DW_NEOHOOKEAN = 0, DW_FIXED_COROTATED = 1 };
-enum { DW_P2G_AUTO = 0, DW_P2G_ATOMIC = 1, DW_P2G_WARP = 2, DW_P2G_TILE = 3 };
+/* P2G accumulation strategies (results agree to float rounding): global float4
+ * atomics per particle and node (ATOMIC); per-warp sums of runs of particles
+ * that share a cell, one atomic per node and run (WARP); a CTA-wide shared
+ * tile (TILE). In mpm_rollout's fused G2P/P2G kernel, AUTO and PAIR run two
+ * particles per thread on paired float2 arithmetic with the warp sums; the
+ * other strategies run the one-particle-per-thread fused kernel. Outside
+ * mpm_rollout PAIR and AUTO use WARP. */
+enum { DW_P2G_AUTO = 0, DW_P2G_ATOMIC = 1, DW_P2G_WARP = 2, DW_P2G_TILE = 3, DW_P2G_PAIR = 4 };
 
 typedef struct {
     int32_t n_grid;        /* nodes per axis, 8 <= n_grid <= 512 */
@@ -547,6 +565,17 @@ typedef struct dw_lbm_s *dw_lbm;
 
 DW_API dw_status lbm_create(const dw_lbm_desc *desc, dw_lbm *out);
 DW_API dw_status lbm_destroy(dw_lbm h);
+
+/* Keep the link words of mask `solid` (per cell: which of its 18 neighbours
+ * are solid, with the periodic wraps and the x boundaries folded in) in the
+ * handle, so that the lattice calls given this same `solid` pointer skip
+ * rebuilding them. Without it every call with a mask rebuilds them (one
+ * launch over the lattice). The caller must not change the mask's contents
+ * while it is registered: register it again after a change. solid = NULL
+ * drops the registration; a call with another mask drops it too. Not in the
+ * paper: a property of this library's lattice kernels (Eq. lbe's bounce-back
+ * needs only "is the neighbour solid"). Errors: DW_ERR_ARG for a NULL handle. */
+DW_API dw_status lbm_cache_mask(dw_lbm h, const uint8_t *solid, dw_stream stream);
 
 /* Advance f in place by `steps` >= 0 lattice steps. Pairs of steps run as the
  * in-place AA pattern (one collide-only kernel, one pull-collide-push kernel);

@@ -66,6 +66,7 @@ F32 = ct.c_float
 SIGNATURES = {
     "dw_last_error": (ct.c_char_p, []),
     "dw_version": (ct.c_char_p, []),
+    "dw_fp32_probe": (I32, [I32, I32, I32, VP, P(ct.c_double), VP]),
     "wind_field_sample": (I32, [P(DwWindField), VP, I64, F32, VP, VP]),
     "wind_field_sample_adjoint": (I32, [P(DwWindField), VP, I64, F32, VP, VP, VP]),
     "mpm_create": (I32, [P(DwMpmDesc), P(VP)]),
@@ -99,6 +100,7 @@ SIGNATURES = {
     "lbm_create": (I32, [P(DwLbmDesc), P(VP)]),
     "lbm_destroy": (I32, [VP]),
     "lbm_step": (I32, [VP, VP, VP, I32, VP]),
+    "lbm_cache_mask": (I32, [VP, VP, VP]),
     "lbm_step_adjoint": (I32, [VP, VP, VP, VP, I32, VP]),
     "lbm_macroscopic": (I32, [VP, VP, VP, VP, VP, VP]),
     "lbm_init_equilibrium": (I32, [VP, VP, F32, P(F32 * 3), VP]),

@@ -22,7 +22,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "wind_field_sample_adjoint", "mpm_create", "mpm_destroy", "mpm_set_material",
            "mpm_substep", "mpm_substep_adjoint", "mpm_segment_adjoint", "mpm_sort", "mpm_device_status", "mpm_rollout",
            "mpm_profile_enable", "mpm_profile_read", "mpm_substep_noalloc", "lbm_create",
-           "lbm_destroy", "lbm_step", "lbm_step_adjoint", "lbm_macroscopic",
+           "lbm_destroy", "lbm_step", "lbm_cache_mask", "fp32_peak", "lbm_step_adjoint", "lbm_macroscopic",
            "lbm_init_equilibrium", "lbm_home_init", "lbm_home_step", "lbm_home_macroscopic",
            "lbm_home_sample_velocity",
            "voxelize_particles", "lbm_sample_velocity", "wind_phys_loss",
@@ -40,7 +40,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
 
 NEOHOOKEAN, FIXED_COROTATED = 0, 1
 BATCH_PERSISTENT, BATCH_SPLIT = 0, 1
-P2G_AUTO, P2G_ATOMIC, P2G_WARP, P2G_TILE = 0, 1, 2, 3
+P2G_AUTO, P2G_ATOMIC, P2G_WARP, P2G_TILE, P2G_PAIR = 0, 1, 2, 3, 4
 
 
 def _dev(t: Optional[torch.Tensor], dtype=torch.float32, name="tensor"):
@@ -360,6 +360,38 @@ def _mask(solid):
 def lbm_step(h, f, solid, steps, stream=None):
     check(lib().lbm_step(h, _dev(f, name="f"), _mask(solid), int(steps), _stream(stream)))
     return f
+
+
+def fp32_peak(paired, iters=4096, blocks_per_sm=8, reps=3):
+    """Measured FP32 throughput (FLOP/s) of the probe kernel: scalar FFMA
+    (paired=False) or paired FFMA2 (paired=True), best of `reps` launches on
+    the current stream, timed with CUDA events."""
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = blocks_per_sm * sms
+    out = torch.zeros(blocks, dtype=torch.float32, device=f"cuda:{dev}")
+    flops = ct.c_double(0.0)
+    stream = torch.cuda.current_stream()
+    best = None
+    for r in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        check(lib().dw_fp32_probe(int(bool(paired)), int(iters), int(blocks), _dev(out, name="out"),
+                                  ct.byref(flops), _stream(stream)))
+        e1.record(stream)
+        e1.synchronize()
+        if r == 0:
+            continue  # the first launch loads the module
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return flops.value / (best * 1e-3)
+
+
+def lbm_cache_mask(h, solid, stream=None):
+    """Registers `solid` so that calls with this tensor reuse its link words;
+    the mask must not change while registered (None drops it)."""
+    check(lib().lbm_cache_mask(h, _mask(solid), _stream(stream)))
 
 
 def lbm_step_adjoint(h, f_in, g_f, solid, steps, stream=None):
@@ -716,6 +748,9 @@ class LBM:
 
     def step_adjoint(self, f_in, g_f, solid, steps, stream=None):
         return lbm_step_adjoint(self.h, f_in, g_f, solid, steps, stream)
+
+    def cache_mask(self, solid, stream=None):
+        return lbm_cache_mask(self.h, solid, stream)
 
     def sample_velocity(self, f, solid, pos, u_out=None, stream=None):
         return lbm_sample_velocity(self.h, f, solid, pos, u_out, stream)

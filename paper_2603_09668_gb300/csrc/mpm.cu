@@ -348,7 +348,7 @@ dw_status validate_desc(const dw_mpm_desc *desc) {
     DW_REQUIRE(desc->p_mass > 0.0f && desc->p_vol > 0.0f, "p_mass and p_vol must be > 0");
     DW_REQUIRE(desc->max_particles >= 0 && desc->max_particles < (1ll << 31),
                "max_particles out of range");
-    DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_TILE, "unknown p2g_mode");
+    DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_PAIR, "unknown p2g_mode");
     return DW_OK;
 }
 
@@ -712,7 +712,7 @@ extern "C" dw_status mpm_substep_noalloc(const dw_mpm_desc *desc, const dw_mpm_s
                "unknown material %d", desc->material);
     DW_REQUIRE(desc->E > 0.0f && desc->nu >= 0.0f && desc->nu < 0.5f, "need E > 0 and 0 <= nu < 0.5");
     DW_REQUIRE(desc->p_mass > 0.0f && desc->p_vol > 0.0f, "p_mass and p_vol must be > 0");
-    DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_TILE, "unknown p2g_mode");
+    DW_REQUIRE(desc->p2g_mode >= DW_P2G_AUTO && desc->p2g_mode <= DW_P2G_PAIR, "unknown p2g_mode");
     DW_REQUIRE(in && out, "in/out must not be NULL");
     DW_REQUIRE(in->n >= 0 && in->n == out->n && in->n < (1ll << 31), "bad particle counts");
     DW_REQUIRE(in->n == 0 || (in->x && in->v && in->C && in->F && out->x && out->v && out->C && out->F),

@@ -141,7 +141,7 @@ dw_status launch_p2g(int mode, const MpmParams &P, const float *x, const float *
     if (n == 0) return DW_OK;
     if (mode == DW_P2G_ATOMIC) {
         DW_CUDA(launch_pdl(k_p2g_atomic, grid_for(n, 128), 128, st, P, x, v, C, F, n, grid, err, ab));
-    } else if (mode == DW_P2G_WARP || mode == DW_P2G_AUTO) {
+    } else if (mode == DW_P2G_WARP || mode == DW_P2G_AUTO || mode == DW_P2G_PAIR) {
         DW_CUDA(launch_pdl(k_p2g_warp, grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, st, P, x, v,
                            C, F, n, grid, err, ab));
     } else {

@@ -156,3 +156,47 @@ def test_voxelize_bit_exact():
         B.voxelize_particles(to_dev(pts), shape, dx, mask)
         ref = oracle.voxelize(pts, shape, dx)
         assert np.array_equal(mask.cpu().numpy().ravel(), ref)
+
+
+def test_cached_mask_link_words():
+    """lbm_cache_mask: steps, adjoint and HOME steps with the registered mask
+    equal those that rebuild the link words per call, bit for bit; after the
+    mask changes and is registered again the steps follow the new mask (a
+    stale cache would not)."""
+    shape = (24, 16, 12)
+    nx, ny, nz = shape
+    solid_a = to_dev(inputs.random_mask(shape, 0.1, seed=5)).reshape(nz, ny, nx)
+    solid_b = to_dev(inputs.random_mask(shape, 0.1, seed=6)).reshape(nz, ny, nx)
+    lbm = B.LBM(shape, 0.6, u_inlet=(0.05, 0.01, 0.0), bc_x=1, max_tape=4)
+    f0 = lbm.lattice()
+    lbm.init_equilibrium(f0, 1.0, (0.03, 0.0, 0.01))
+    ref = f0.clone()
+    lbm.step(ref, solid_a, 5)
+    g_ref = torch.linspace(-1, 1, f0.numel(), device=f0.device).reshape(f0.shape)
+    lbm.step_adjoint(f0, g_ref, solid_a, 4)
+    lbm.cache_mask(solid_a)
+    f = f0.clone()
+    lbm.step(f, solid_a, 5)
+    assert torch.equal(f, ref)
+    g = torch.linspace(-1, 1, f0.numel(), device=f0.device).reshape(f0.shape)
+    lbm.step_adjoint(f0, g, solid_a, 4)
+    assert torch.equal(g, g_ref)
+    # the mask changes in place: registering it again rebuilds the words
+    ref_b = f0.clone()
+    lbm.cache_mask(None)
+    lbm.step(ref_b, solid_b, 3)
+    solid_a.copy_(solid_b)
+    lbm.cache_mask(solid_a)
+    f = f0.clone()
+    lbm.step(f, solid_a, 3)
+    assert torch.equal(f, ref_b)
+    # HOME steps with the registered mask equal those without
+    m0 = lbm.moments()
+    lbm.home_init(m0, 1.0, (0.03, 0.0, 0.01))
+    m = m0.clone()
+    lbm.home_step(m, solid_a, 4)
+    lbm.cache_mask(None)
+    m_ref = m0.clone()
+    lbm.home_step(m_ref, solid_b, 4)
+    assert torch.equal(m, m_ref)
+    lbm.close()
