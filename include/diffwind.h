@@ -664,8 +664,9 @@ DW_API dw_status voxelize_particles(const float *pos, int64_t n, int32_t nx, int
  * network on a coarse n^3 grid that maps the coarse state of a (2n)^3
  * lattice to the change du of the coarse velocity over a block of lattice
  * steps. Channels 16 -> 32 -> 32 -> 32 -> 16, kernel 3, zero padding, GELU
- * after layers 1-3; inputs (rho - 1, ux, uy, uz, solid fraction, 0 ...) as
- * 2x2x2 averages over fluid cells; outputs du in channels 0..2. BF16
+ * after layers 1-3; inputs (rho - 1, u - u_ref, solid fraction, u_ref,
+ * 0 ...) with rho and u as 2x2x2 averages over fluid cells; outputs du in
+ * channels 0..2. BF16
  * activations and weights on the tensor cores with FP32 accumulation; FP32
  * master parameters packed layer by layer as W[tap][cout][cin] then b[cout],
  * tap = (dz+1)*9 + (dy+1)*3 + (dx+1) (the input voxel is v + (dx,dy,dz)).
@@ -684,10 +685,18 @@ DW_API dw_status surr_set_params(dw_surr h, const float *src, dw_stream stream);
 DW_API dw_status surr_get_params(dw_surr h, float *dst, dw_stream stream);
 DW_API dw_status surr_get_grads(dw_surr h, float *dst, dw_stream stream);
 DW_API dw_status surr_zero_grads(dw_surr h, dw_stream stream);
-/* Coarse features from a shifted (2n)^3 lattice f [19][cells] and its mask,
- * channels (rho - 1, ux, uy, uz) multiplied by in_scale and the solid
- * fraction; also keeps the fine rho and u for surr_apply. feats32 (device
- * [n^3][16], may be NULL) receives the features in FP32 as well. */
+/* Reference velocity of the features (host float[3], the lattice's inlet
+ * velocity; zero until set): the coarse features carry the fluid velocity
+ * relative to it (channels 1-3) and the reference itself (channels 5-7),
+ * both multiplied by in_scale, so that BF16 resolves the flow's departures
+ * from the free stream and the network knows the inlet. Not in the paper. */
+DW_API dw_status surr_set_inlet(dw_surr h, const float u[3]);
+/* Coarse features from a shifted (2n)^3 lattice f [19][cells] and its mask:
+ * per coarse voxel the 2x2x2 fluid averages of rho - 1 and of u - u_ref
+ * (0 without fluid), the solid fraction, and u_ref (surr_set_inlet), the
+ * velocities multiplied by in_scale; channels 8-15 are zero. Also keeps the
+ * fine rho and u for surr_apply. feats32 (device [n^3][16], may be NULL)
+ * receives the features in FP32 as well. */
 DW_API dw_status surr_features(dw_surr h, const float *f, const uint8_t *solid, float in_scale,
                                float *feats32, dw_stream stream);
 /* Set the coarse features directly from FP32 [n^3][16] (rounded to BF16). */
@@ -737,6 +746,20 @@ DW_API dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t *so
 DW_API dw_status surr_write_lattice(dw_surr h, const uint8_t *solid, float *f, dw_stream stream);
 DW_API dw_status surr_fine_velocity_error(dw_surr h, const float *f, const uint8_t *solid,
                                           double *sums, dw_stream stream);
+/* Defect correction of the chained mode (not in the paper; the plain LBM
+ * judges the surrogate, and its judgement is reused): mode 1 sets
+ * corr = u(f) - u_fine on the fluid cells (0 on solid cells), where f is the
+ * shifted lattice the plain LBM reached from the state the surrogate started
+ * from and u_fine the handle's fine velocity after the surrogate's block;
+ * mode 2 adds that difference to the current correction; mode 0 stops using
+ * it. While a correction is set, every surr_advance_fine adds corr to the
+ * fine velocity after the network's update, so that a slowly varying error
+ * of the network per block is cancelled instead of accumulated. The
+ * correction buffer (3 (2n)^3 floats) is allocated by the first call with
+ * mode 1. Errors: DW_ERR_ARG for a bad mode, mode 2 without a correction, or
+ * a NULL f with mode 1 or 2. */
+DW_API dw_status surr_set_correction(dw_surr h, const float *f, const uint8_t *solid, int32_t mode,
+                                     dw_stream stream);
 /* sums[0] += sum |u_a - u_b|^2, sums[1] += sum |u_b|^2 over the fluid cells of
  * two shifted lattices with ncell cells (device double[2]). */
 DW_API dw_status lbm_velocity_error(const float *fa, const float *fb, const uint8_t *solid,

@@ -109,7 +109,7 @@ def _declare(lib):
         "orc_surr_num_params": (i64, []),
         "orc_surr_forward": (None, [i, _dp, _dp, _dp, _dp, _dp]),
         "orc_surr_backward": (None, [i, _dp, _dp, _dp, _dp]),
-        "orc_surr_features": (None, [i, _dp, _u8p, _dp, _dp, _dp]),
+        "orc_surr_features": (None, [i, _dp, _u8p, _dp, _dp, _dp, _dp]),
         "orc_surr_apply": (None, [i, _dp, _dp, _dp, _u8p, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -478,16 +478,18 @@ def surr_backward(n, params, feats, g_out):
     return g
 
 
-def surr_features(n, f, solid=None):
+def surr_features(n, f, solid=None, u_ref=(0.0, 0.0, 0.0)):
     """Coarse features [n^3][16] of a fine (2n)^3 lattice of plain populations
-    f[19][cells], with the fine rho [cells] and u [3][cells]."""
+    f[19][cells] (velocities relative to u_ref, u_ref itself in channels 5-7),
+    with the fine rho [cells] and u [3][cells]."""
     f = _f64(f)
     N3 = (2 * n) ** 3
     feats = np.zeros((n ** 3, 16))
     rho = np.zeros(N3)
     u = np.zeros((3, N3))
     m = _mask(solid, N3)
-    _load().orc_surr_features(n, _ptr(f), _u8ptr(m), _ptr(feats), _ptr(rho), _ptr(u))
+    ur = np.ascontiguousarray(np.asarray(u_ref, np.float64))
+    _load().orc_surr_features(n, _ptr(f), _u8ptr(m), _ptr(ur), _ptr(feats), _ptr(rho), _ptr(u))
     return feats, rho, u
 
 

@@ -176,11 +176,13 @@ static const int CV[19][3] = {
     {-1, 1, 0}, {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}};
 
 /* Coarse features of a fine lattice of 2n^3 cells (plain populations f[19][cells]):
- * per coarse voxel, the 2x2x2 averages of (rho - 1, ux, uy, uz) over its fluid
- * cells and the solid fraction; channels 5..15 are zero. Also returns the
- * fine rho and u (solid cells: rho = 1, u = 0). */
-void orc_surr_features(int n, const double *f, const uint8_t *solid, double *feats,
-                       double *rho_fine, double *u_fine) {
+ * per coarse voxel, the 2x2x2 average of rho - 1 over its fluid cells, the
+ * average of u over its fluid cells minus the reference velocity uref
+ * (0 when the voxel has no fluid cell), the solid fraction, and uref itself
+ * in channels 5..7; channels 8..15 are zero. Also returns the fine rho and u
+ * (solid cells: rho = 1, u = 0). */
+void orc_surr_features(int n, const double *f, const uint8_t *solid, const double *uref,
+                       double *feats, double *rho_fine, double *u_fine) {
     int N = 2 * n;
     int64_t nc = (int64_t)N * N * N;
     for (int64_t c = 0; c < nc; ++c) {
@@ -213,9 +215,12 @@ void orc_surr_features(int n, const double *f, const uint8_t *solid, double *fea
                 }
                 double *o = feats + (((int64_t)z * n + y) * n + x) * 16;
                 for (int ch = 0; ch < 16; ++ch) o[ch] = 0.0;
-                if (fluid > 0)
-                    for (int ch = 0; ch < 4; ++ch) o[ch] = s[ch] / fluid;
+                if (fluid > 0) {
+                    o[0] = s[0] / fluid;
+                    for (int a = 0; a < 3; ++a) o[1 + a] = s[1 + a] / fluid - uref[a];
+                }
                 o[4] = (8 - fluid) / 8.0;
+                for (int a = 0; a < 3; ++a) o[5 + a] = uref[a];
             }
 }
 

@@ -139,6 +139,8 @@ SIGNATURES = {
     "surr_features_fine": (I32, [VP, VP, F32, VP]),
     "surr_advance_fine": (I32, [VP, F32, VP, F32, VP]),
     "surr_write_lattice": (I32, [VP, VP, VP, VP]),
+    "surr_set_inlet": (I32, [VP, P(F32)]),
+    "surr_set_correction": (I32, [VP, VP, VP, I32, VP]),
     "surr_fine_velocity_error": (I32, [VP, VP, VP, VP, VP]),
     "surr_loss": (I32, [VP, VP, VP, VP]),
     "surr_set_output_grad": (I32, [VP, VP, VP]),

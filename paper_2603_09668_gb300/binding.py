@@ -33,7 +33,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "surr_get_features", "surr_forward", "surr_loss", "surr_set_output_grad",
            "surr_backward", "surr_device_status", "surr_adam", "surr_apply", "lbm_velocity_error", "Surrogate",
            "surr_features_fine", "surr_advance_fine", "surr_write_lattice",
-           "surr_fine_velocity_error", "mpm_batch_create", "mpm_batch_destroy",
+           "surr_fine_velocity_error", "surr_set_correction", "surr_set_inlet", "mpm_batch_create", "mpm_batch_destroy",
            "mpm_batch_layout", "mpm_batch_rollout", "mpm_batch_set_config",
            "mpm_batch_get_config", "mpm_batch_tune", "mpm_batch_device_status", "mpm_batch_barrier_selftest",
            "mpm_batch_wind_layout", "mpm_batch_segment_adjoint", "MPMBatch"]
@@ -857,6 +857,19 @@ def surr_write_lattice(h, solid, f, stream=None):
     return f
 
 
+def surr_set_inlet(h, u):
+    """Reference (inlet) velocity of the surrogate's features."""
+    arr = (ct.c_float * 3)(*[float(a) for a in u])
+    check(lib().surr_set_inlet(h, arr))
+
+
+def surr_set_correction(h, f, solid, mode, stream=None):
+    """Chained-mode defect correction: mode 1 sets corr = u(f) - u_fine, mode 2
+    adds that difference, mode 0 stops using it."""
+    check(lib().surr_set_correction(h, _dev(f, name="f") if f is not None else None, _mask(solid),
+                                    int(mode), _stream(stream)))
+
+
 def surr_fine_velocity_error(h, f, solid, sums, stream=None):
     check(lib().surr_fine_velocity_error(h, _dev(f, name="f"), _mask(solid),
                                          _dev(sums, torch.float64, "sums"), _stream(stream)))
@@ -949,6 +962,12 @@ class Surrogate:
 
     def write_lattice(self, solid, f):
         return surr_write_lattice(self.h, solid, f)
+
+    def set_inlet(self, u):
+        surr_set_inlet(self.h, u)
+
+    def set_correction(self, f, solid, mode):
+        surr_set_correction(self.h, f, solid, mode)
 
     def fine_velocity_error(self, f, solid, sums):
         return surr_fine_velocity_error(self.h, f, solid, sums)

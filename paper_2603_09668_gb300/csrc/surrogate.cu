@@ -34,6 +34,9 @@ struct SurrHandle {
     float *part = nullptr, *part_b = nullptr;   // weight-gradient partials
     int nchunks = 0, tiles_per_chunk = 0;
     float *fine = nullptr;          // [4][(2n)^3]: rho, ux, uy, uz of the last surr_features
+    float *corr = nullptr;          // [3][(2n)^3] defect correction of the chained update
+    float uref[3] = {0.f, 0.f, 0.f};  // reference (inlet) velocity of the features
+    bool corr_on = false;           // corr is added by surr_advance_fine
     double *red = nullptr;          // reduction scratch
     int *err = nullptr;             // device status bits (bounded waits of the conv kernels)
     unsigned *gbar = nullptr;       // grid barrier of the one-launch forward (arrivals, generation)
@@ -102,7 +105,7 @@ __global__ void k_surr_fine(const float *__restrict__ f, const uint8_t *__restri
 
 // Coarse features: 2x2x2 averages over fluid cells of (rho - 1, u), solid fraction.
 __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__restrict__ solid,
-                              int n, float in_scale, bf16 *__restrict__ feats,
+                              int n, float in_scale, float3 uref, bf16 *__restrict__ feats,
                               float *__restrict__ feats32) {
     const int64_t nv = (int64_t)n * n * n;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,18 +126,28 @@ __global__ void k_surr_coarse(const float *__restrict__ fine, const uint8_t *__r
         s[3] += fine[3 * nc + c];
     }
     const float inv = fluid > 0 ? in_scale / (float)fluid : 0.0f;
+    // velocity relative to the reference velocity, which itself fills channels 5-7
+    const float r1 = fluid > 0 ? s[1] * inv - uref.x * in_scale : 0.0f;
+    const float r2 = fluid > 0 ? s[2] * inv - uref.y * in_scale : 0.0f;
+    const float r3 = fluid > 0 ? s[3] * inv - uref.z * in_scale : 0.0f;
     __align__(16) bf16 o[16];
 #pragma unroll
     for (int ch = 0; ch < 16; ++ch) o[ch] = __float2bfloat16_rn(0.0f);
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * inv);
+    o[0] = __float2bfloat16_rn(s[0] * inv);
+    o[1] = __float2bfloat16_rn(r1);
+    o[2] = __float2bfloat16_rn(r2);
+    o[3] = __float2bfloat16_rn(r3);
     o[4] = __float2bfloat16_rn((8 - fluid) * 0.125f);
+    o[5] = __float2bfloat16_rn(uref.x * in_scale);
+    o[6] = __float2bfloat16_rn(uref.y * in_scale);
+    o[7] = __float2bfloat16_rn(uref.z * in_scale);
     reinterpret_cast<uint4 *>(feats)[v] = reinterpret_cast<const uint4 *>(o)[0];       // channels 0-7
     reinterpret_cast<uint4 *>(feats)[nv + v] = reinterpret_cast<const uint4 *>(o)[1];  // channels 8-15
     if (feats32) {
         float4 *d32 = reinterpret_cast<float4 *>(feats32 + v * 16);
-        d32[0] = make_float4(s[0] * inv, s[1] * inv, s[2] * inv, s[3] * inv);
-        d32[1] = make_float4((8 - fluid) * 0.125f, 0.f, 0.f, 0.f);
+        d32[0] = make_float4(s[0] * inv, r1, r2, r3);
+        d32[1] = make_float4((8 - fluid) * 0.125f, uref.x * in_scale, uref.y * in_scale,
+                             uref.z * in_scale);
         d32[2] = make_float4(0.f, 0.f, 0.f, 0.f);
         d32[3] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -288,7 +301,8 @@ constexpr int ADV_VX = 16, ADV_VY = 2, ADV_VZ = 4;
 constexpr int ADV_THREADS = 4 * ADV_VX * ADV_VY * ADV_VZ;  // two fine cells per thread
 __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
     const float *__restrict__ out4, float out_scale, float *__restrict__ fine,
-    const uint8_t *__restrict__ solid, int n, float in_scale, bf16 *__restrict__ feats) {
+    const uint8_t *__restrict__ solid, int n, float in_scale, float3 uref,
+    bf16 *__restrict__ feats, const float *__restrict__ corr) {
     constexpr int SX = ADV_VX + 2, SY = ADV_VY + 2, SZ = ADV_VZ + 2;
     constexpr int NV = ADV_VX * ADV_VY * ADV_VZ;
     static_assert(SX * SY * SZ <= ADV_THREADS, "one staged voxel per thread");
@@ -311,15 +325,12 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
     // every load is issued before the first barrier: the staged coarse voxel
     // and both fine cells' rho, u and mask (solid cells hold rho = 1, u = 0 and
     // are read but never written)
-    float st0 = 0.f, st1 = 0.f, st2 = 0.f;
+    float4 st = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t < SX * SY * SZ) {
         const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
         const int cx = min(max(x0 - 1 + ex, 0), n - 1), cy = min(max(y0 - 1 + ey, 0), n - 1);
         const int cz = min(max(z0 - 1 + ez, 0), n - 1);
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(out4) + ((int64_t)cz * n + cy) * n + cx);
-        st0 = q.x;
-        st1 = q.y;
-        st2 = q.z;
+        st = __ldg(reinterpret_cast<const float4 *>(out4) + ((int64_t)cz * n + cy) * n + cx);
     }
     int fi[2][3];
     int64_t c[2];
@@ -336,13 +347,18 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
         u0[h] = fine[nc + c[h]];
         u1[h] = fine[2 * nc + c[h]];
         u2[h] = fine[3 * nc + c[h]];
+        if (corr) {  // the defect measured at the last check, added every block
+            u0[h] += corr[c[h]];
+            u1[h] += corr[nc + c[h]];
+            u2[h] += corr[2 * nc + c[h]];
+        }
         is_solid[h] = solid && solid[c[h]];
     }
     if (t < SX * SY * SZ) {
         const int ex = t % SX, ey = (t / SX) % SY, ez = t / (SX * SY);
-        du[ez][ey][ex][0] = st0;
-        du[ez][ey][ex][1] = st1;
-        du[ez][ey][ex][2] = st2;
+        du[ez][ey][ex][0] = st.x;
+        du[ez][ey][ex][1] = st.y;
+        du[ez][ey][ex][2] = st.z;
     }
     __syncthreads();
 #pragma unroll
@@ -413,11 +429,14 @@ __global__ void __launch_bounds__(ADV_THREADS) k_surr_advance_fine(
         }
         const float inv = fluid > 0 ? in_scale / (float)fluid : 0.0f;
         __align__(16) bf16 o8[8];
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) o8[ch] = __float2bfloat16_rn(0.0f);
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) o8[ch] = __float2bfloat16_rn(sum[ch] * inv);
+        o8[0] = __float2bfloat16_rn(sum[0] * inv);
+        o8[1] = __float2bfloat16_rn(fluid > 0 ? sum[1] * inv - uref.x * in_scale : 0.0f);
+        o8[2] = __float2bfloat16_rn(fluid > 0 ? sum[2] * inv - uref.y * in_scale : 0.0f);
+        o8[3] = __float2bfloat16_rn(fluid > 0 ? sum[3] * inv - uref.z * in_scale : 0.0f);
         o8[4] = __float2bfloat16_rn((8 - fluid) * 0.125f);
+        o8[5] = __float2bfloat16_rn(uref.x * in_scale);
+        o8[6] = __float2bfloat16_rn(uref.y * in_scale);
+        o8[7] = __float2bfloat16_rn(uref.z * in_scale);
         const int64_t nv = (int64_t)n * n * n;
         const int vx = t % ADV_VX, vy = (t / ADV_VX) % ADV_VY, vz = t / (ADV_VX * ADV_VY);
         const int64_t cv = ((int64_t)(z0 + vz) * n + (y0 + vy)) * n + x0 + vx;
@@ -440,6 +459,31 @@ __global__ void k_surr_write_lattice(const float *__restrict__ fine, const uint8
         const float w = i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
         f[(size_t)i * nc + c] = w * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - uu));
     }
+}
+
+// Defect of the chained update: corr (+)= u(f) - u_fine on fluid cells, 0 on
+// solid cells (u from the shifted lattice f of the plain LBM).
+__global__ void k_surr_correction(const float *__restrict__ fine, const float *__restrict__ f,
+                                  const uint8_t *__restrict__ solid, int64_t nc, int accumulate,
+                                  float *__restrict__ corr) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    float d[3] = {0.f, 0.f, 0.f};
+    if (!(solid && solid[c])) {
+        float u[3] = {0.f, 0.f, 0.f}, rb = 1.0f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const float b = f[(size_t)i * nc + c];
+            rb += b;
+            u[0] += kCX[i] * b;
+            u[1] += kCY[i] * b;
+            u[2] += kCZ[i] * b;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = u[k] / rb - fine[(k + 1) * nc + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) corr[k * nc + c] = accumulate ? corr[k * nc + c] + d[k] : d[k];
 }
 
 // sums over fluid cells of |u_fine - u(f)|^2 and |u(f)|^2
@@ -616,6 +660,17 @@ using namespace dw;
 
 struct dw_surr_s : SurrHandle {};
 
+static float3 uref_of(const SurrHandle *h) { return make_float3(h->uref[0], h->uref[1], h->uref[2]); }
+
+extern "C" dw_status surr_set_inlet(dw_surr h, const float u[3]) {
+    DW_REQUIRE(h && u, "handle and u must not be NULL");
+    for (int a = 0; a < 3; ++a) {
+        DW_REQUIRE(isfinite(u[a]), "u must be finite");
+        h->uref[a] = u[a];
+    }
+    return DW_OK;
+}
+
 extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
     DW_REQUIRE(out, "out must not be NULL");
     *out = nullptr;
@@ -714,6 +769,7 @@ extern "C" dw_status surr_destroy(dw_surr h) {
     cudaFree(h->part);
     cudaFree(h->part_b);
     cudaFree(h->fine);
+    cudaFree(h->corr);
     cudaFree(h->red);
     cudaFree(h->err);
     cudaFree(h->gbar);
@@ -761,8 +817,8 @@ extern "C" dw_status surr_features(dw_surr h, const float *f, const uint8_t *sol
     const int N = 2 * h->n;
     const int64_t nc = (int64_t)N * N * N;
     k_surr_fine<<<grid_for(nc, 256), 256, 0, s>>>(f, solid, N, h->fine);
-    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, s>>>(h->fine, solid, h->n, in_scale, h->feats,
-                                                       feats32);
+    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, s>>>(h->fine, solid, h->n, in_scale,
+                                                       uref_of(h), h->feats, feats32);
     DW_LAUNCHED("surr_features");
     return DW_OK;
 }
@@ -938,7 +994,7 @@ extern "C" dw_status lbm_velocity_error(const float *fa, const float *fb, const 
 extern "C" dw_status surr_features_fine(dw_surr h, const uint8_t *solid, float in_scale,
                                         dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
-    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, as_stream(stream)>>>(h->fine, solid, h->n, in_scale,
+    k_surr_coarse<<<grid_for(h->nv, 256), 256, 0, as_stream(stream)>>>(h->fine, solid, h->n, in_scale, uref_of(h),
                                                                        h->feats, nullptr);
     DW_LAUNCHED("k_surr_coarse");
     return DW_OK;
@@ -949,7 +1005,8 @@ extern "C" dw_status surr_advance_fine(dw_surr h, float out_scale, const uint8_t
     DW_REQUIRE(h, "handle is NULL");
     DW_CUDA(launch_pdl(k_surr_advance_fine, (unsigned)(h->nv / (ADV_VX * ADV_VY * ADV_VZ)),
                        ADV_THREADS, as_stream(stream), (const float *)h->out4, out_scale, h->fine,
-                       solid, h->n, in_scale, h->feats));
+                       solid, h->n, in_scale, uref_of(h), h->feats,
+                       (const float *)(h->corr_on ? h->corr : nullptr)));
     return DW_OK;
 }
 
@@ -959,6 +1016,26 @@ extern "C" dw_status surr_write_lattice(dw_surr h, const uint8_t *solid, float *
     const int64_t nc = (int64_t)N * N * N;
     k_surr_write_lattice<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(h->fine, solid, nc, f);
     DW_LAUNCHED("k_surr_write_lattice");
+    return DW_OK;
+}
+
+extern "C" dw_status surr_set_correction(dw_surr h, const float *f, const uint8_t *solid,
+                                        int32_t mode, dw_stream stream) {
+    DW_REQUIRE(h, "handle is NULL");
+    DW_REQUIRE(mode >= 0 && mode <= 2, "mode=%d must be 0, 1 or 2", mode);
+    if (mode == 0) {
+        h->corr_on = false;
+        return DW_OK;
+    }
+    DW_REQUIRE(f, "f must not be NULL");
+    DW_REQUIRE(mode == 1 || h->corr_on, "mode 2 accumulates into a correction that is not set");
+    const int N = 2 * h->n;
+    const int64_t nc = (int64_t)N * N * N;
+    if (!h->corr) DW_CUDA(cudaMalloc((void **)&h->corr, sizeof(float) * 3 * (size_t)nc));
+    k_surr_correction<<<grid_for(nc, 256), 256, 0, as_stream(stream)>>>(h->fine, f, solid, nc,
+                                                                        mode == 2 ? 1 : 0, h->corr);
+    DW_LAUNCHED("k_surr_correction");
+    h->corr_on = true;
     return DW_OK;
 }
 

@@ -48,12 +48,30 @@ def leaf_mask(N, seed, device="cuda"):
     return solid
 
 
+# channels of the features kept for training (the others are zero)
+X_CH = 8
+Y_CH = 3
+
+
+def turned(d, deg, rng):
+    """d rotated by `deg` degrees about a random axis normal to it."""
+    a = np.cross(d, rng.standard_normal(3))
+    a /= np.linalg.norm(a)
+    t = math.radians(deg)
+    return d * math.cos(t) + np.cross(a, d) * math.sin(t) + a * np.dot(a, d) * (1 - math.cos(t))
+
+
 def generate_pairs(N, n_rollouts, t_lo, t_hi, seed=0, block=BLOCK, tau=0.55, device="cuda",
-                   keep_states=False):
+                   keep_states=False, per_rollout=1, inlet_features=True, turn_frac=0.0,
+                   turn_deg=20.0, turn_window=300):
     """Training pairs from the plain LBM: per rollout a random obstacle and inlet
-    direction, a run from rest to a random time in [t_lo, t_hi), the coarse
-    features there (input) and the change of the coarse velocity over the next
-    `block` steps divided by OUT_SCALE (target, channels 0..2)."""
+    direction, a run from rest through `per_rollout` random times in
+    [t_lo, t_hi); at each, the coarse features (input, channels 0..X_CH-1) and
+    the change of the coarse velocity over the next `block` steps divided by
+    OUT_SCALE (target, channels 0..2). A fraction turn_frac of the rollouts turns the inlet
+    by turn_deg degrees at a time in [t_lo, t_hi) and samples its pairs in
+    the turn_window steps after the turn. Pairs are kept in these compact
+    channels (expand() restores the network's 16)."""
     n = N // 2
     rng = np.random.default_rng(seed)
     surr = B.Surrogate(n)
@@ -63,24 +81,47 @@ def generate_pairs(N, n_rollouts, t_lo, t_hi, seed=0, block=BLOCK, tau=0.55, dev
     for r in range(n_rollouts):
         solid = leaf_mask(N, seed * 100003 + r, device)
         d = inlet_direction(rng)
-        lbm = B.LBM((N, N, N), tau, u_inlet=tuple(U_REF * d), bc_x=1, max_tape=1)
+        u_in = tuple(U_REF * d)
+        surr.set_inlet(u_in if inlet_features else (0.0, 0.0, 0.0))
+        lbm = B.LBM((N, N, N), tau, u_inlet=u_in, bc_x=1, max_tape=1)
         f = lbm.lattice(device)
-        t0 = int(rng.integers(t_lo, t_hi)) // 2 * 2
-        lbm.step(f, solid, t0)
-        surr.features(f, solid, IN_SCALE, fa)
-        if keep_states:
-            states.append((f.clone(), solid, tuple(U_REF * d)))
-        lbm.step(f, solid, block)
-        surr.features(f, solid, IN_SCALE, fb)
-        y = torch.zeros_like(fa)
-        y[:, :3] = (fb[:, 1:4] - fa[:, 1:4]) / IN_SCALE / OUT_SCALE
-        xs.append(fa.clone())
-        ys.append(y)
+        t = 0
+        if rng.random() < turn_frac:
+            t_turn = int(rng.integers(t_lo, t_hi)) // 2 * 2
+            lbm.step(f, solid, t_turn)
+            lbm.close()
+            u_in = tuple(U_REF * turned(d, turn_deg, rng))
+            surr.set_inlet(u_in if inlet_features else (0.0, 0.0, 0.0))
+            lbm = B.LBM((N, N, N), tau, u_inlet=u_in, bc_x=1, max_tape=1)
+            t = t_turn
+            times = sorted(t_turn + int(x) // 2 * 2 for x in rng.integers(0, turn_window, per_rollout))
+        else:
+            times = sorted(int(x) // 2 * 2 for x in rng.integers(t_lo, t_hi, per_rollout))
+        for t0 in times:
+            if t0 < t:  # two draws closer than one block: skip the repeat
+                continue
+            lbm.step(f, solid, t0 - t)
+            surr.features(f, solid, IN_SCALE, fa)
+            if keep_states:
+                states.append((f.clone(), solid, u_in))
+            lbm.step(f, solid, block)
+            t = t0 + block
+            surr.features(f, solid, IN_SCALE, fb)
+            xs.append(fa[:, :X_CH].clone())
+            # du: channels 1-3 of the features (the reference velocity cancels)
+            ys.append(((fb[:, 1:4] - fa[:, 1:4]) / IN_SCALE / OUT_SCALE).contiguous())
         lbm.close()
     surr.close()
     if keep_states:
         return xs, ys, states
     return xs, ys
+
+
+def expand(a, width=16):
+    """A compact [nv][k] pair array padded with zero channels to [nv][width]."""
+    out = torch.zeros((a.shape[0], width), dtype=a.dtype, device=a.device)
+    out[:, :a.shape[1]] = a
+    return out
 
 
 def init_params(nparams_slices, seed=0, device="cuda"):
@@ -112,9 +153,9 @@ def train(surr: B.Surrogate, xs, ys, steps, lr=1e-3, seed=0, log_every=0):
         i = int(rng.integers(len(xs)))
         cur_lr = lr * 0.5 * (1.0 + math.cos(math.pi * step / steps))  # cosine decay
         loss.zero_()
-        surr.set_features(xs[i])
+        surr.set_features(expand(xs[i]) if xs[i].shape[1] < 16 else xs[i])
         surr.forward()
-        surr.loss(ys[i], loss)
+        surr.loss(expand(ys[i]) if ys[i].shape[1] < 16 else ys[i], loss)
         surr.backward()
         surr.adam(cur_lr, step)
         if log_every and step % log_every == 0:
@@ -138,15 +179,24 @@ class SurrogateLBM:
     surrogate handle (chained mode); the lattice is re-initialised from it,
     f = f_eq(rho, u), only when the plain LBM takes over or at the end.
 
+    inlet_features: give the network its features relative to the inlet
+    velocity (surr_set_inlet); the shipped 128^3 weights were trained without
+    (reference velocity zero). correct: add the last check's plain-minus-
+    surrogate difference to every later block (surr_set_correction; measured
+    to make the run worse, kept off by default). persistence: the scheme
+    without the network, for comparison.
+
     use_graph replays each chained block from a CUDA graph; the default
     launches eagerly, which chains every kernel to the previous one by
     programmatic dependent launch, across blocks too."""
 
     def __init__(self, N, tau=0.55, u_inlet=(U_REF, 0.0, 0.0), check_every=10, tol=0.02,
-                 params=None, device="cuda", use_graph=False):
+                 params=None, device="cuda", use_graph=False, correct=False,
+                 inlet_features=False, persistence=False):
         self.N = N
         self.lbm = B.LBM((N, N, N), tau, u_inlet=u_inlet, bc_x=1, max_tape=1)
         self.surr = B.Surrogate(N // 2)
+        self.surr.set_inlet(u_inlet if inlet_features else (0.0, 0.0, 0.0))
         if params is None:
             load_weights(self.surr, N, device)
         else:
@@ -157,6 +207,11 @@ class SurrogateLBM:
         self.errors = []
         self._sums = torch.zeros(2, dtype=torch.float64, device=device)
         self.use_graph = use_graph
+        self.correct = correct
+        # the same scheme without the network: every surrogate block keeps the
+        # velocity unchanged (du = 0), for comparison
+        self.persistence = persistence
+        self._corr_on = False
         self._graphs = {}  # solid mask pointer -> CUDA graph of one chained block
         self._warm = set()
 
@@ -173,6 +228,8 @@ class SurrogateLBM:
     # the network runs and the fine state advances, leaving the features of
     # the new state for the next block
     def chained_block(self, solid):
+        if self.persistence:
+            return
         if not self.use_graph:
             self._chained_eager(solid)
             return
@@ -238,6 +295,11 @@ class SurrogateLBM:
                 self.errors.append(err)
                 if err > self.tol:
                     self.fallback = True
+                elif self.correct:
+                    # the plain block's difference from the surrogate's block is
+                    # added to every later surrogate block (defect correction)
+                    self.surr.set_correction(f, solid, 2 if self._corr_on else 1)
+                    self._corr_on = True
             else:
                 if not in_fine:
                     self.surr.features(f, solid, IN_SCALE)
@@ -248,6 +310,13 @@ class SurrogateLBM:
         if in_fine:
             self.surr.write_lattice(solid, f)
         return used
+
+    def reset(self):
+        """Forget the check history and the correction (a new run)."""
+        self.calls, self.errors, self.fallback = 0, [], False
+        if self._corr_on:
+            self.surr.set_correction(None, None, 0)
+            self._corr_on = False
 
     def close(self):
         self.lbm.close()

@@ -93,7 +93,8 @@ def test_backward_matches_oracle():
     s.close()
 
 
-def test_features_and_apply_match_oracle():
+@pytest.mark.parametrize("u_ref", [(0.0, 0.0, 0.0), (0.045, 0.012, -0.018)])
+def test_features_and_apply_match_oracle(u_ref):
     n = 16
     N = 2 * n
     shape = (N, N, N)
@@ -105,9 +106,11 @@ def test_features_and_apply_match_oracle():
     f_plain = feq[:, None] + rng.uniform(-2e-3, 2e-3, (19, N ** 3))
     f_dev = to_dev((f_plain - w[:, None]).astype(np.float32).reshape(19, N, N, N))
     s = B.Surrogate(n)
+    s.set_inlet(u_ref)
     s.features(f_dev, to_dev(solid).reshape(N, N, N))
     got = s.get_features().float().cpu().numpy().astype(np.float64)
-    ref, rho, u = oracle.surr_features(n, f_plain.astype(np.float32).astype(np.float64), solid)
+    ref, rho, u = oracle.surr_features(n, f_plain.astype(np.float32).astype(np.float64), solid,
+                                       u_ref)
     assert np.abs(got - ref).max() <= 1e-2 * np.abs(ref).max()
     assert np.array_equal(got[:, 4], ref[:, 4])  # solid fractions are exact in BF16
     du = np.zeros((n ** 3, 16), np.float32)
@@ -192,4 +195,49 @@ def test_chained_advance_matches_apply_and_features():
     s.features_fine(sol, 20.0)
     assert torch.equal(s.get_features(), feats_adv)
     s.device_status()
+    s.close()
+
+
+def test_chained_correction_adds_the_plain_defect():
+    """surr_set_correction: with a network that predicts no change (zero
+    parameters), one chained block after setting the correction from a
+    lattice P reproduces P's velocity on every fluid cell (u_fine + (u(P) -
+    u_fine)); accumulating a second time from the same lattice changes
+    nothing further once u_fine equals u(P); mode 0 stops it."""
+    n = 16
+    N = 2 * n
+    c, w, _ = oracle.velocity_set()
+    rng = np.random.default_rng(12)
+    solid = to_dev(inputs.random_mask((N, N, N), 0.1, seed=13)).reshape(N, N, N)
+    feq = oracle.lbm_equilibrium(1.0, np.array([0.04, 0.0, 0.01]))
+    fa = to_dev((feq[:, None] + rng.uniform(-1e-3, 1e-3, (19, N ** 3)) - w[:, None])
+                .astype(np.float32).reshape(19, N, N, N))
+    fp = to_dev((feq[:, None] + rng.uniform(-1e-3, 1e-3, (19, N ** 3)) - w[:, None])
+                .astype(np.float32).reshape(19, N, N, N))
+    s = B.Surrogate(n)
+    s.set_params(torch.zeros(s.nparams, dtype=torch.float32, device="cuda"))
+    sums = torch.zeros(2, dtype=torch.float64, device="cuda")
+
+    def err_to(f):
+        sums.zero_()
+        s.fine_velocity_error(f, solid, sums)
+        e, r = sums.tolist()
+        return (e / r) ** 0.5
+
+    s.features(fa, solid, 20.0)
+    assert err_to(fp) > 1e-2
+    s.set_correction(fp, solid, 1)
+    s.forward(keep_activations=False)
+    s.advance_fine(1e-3, solid, 20.0)
+    assert err_to(fp) <= 1e-6
+    s.set_correction(fp, solid, 2)   # the defect is now zero: the correction stays
+    s.features(fa, solid, 20.0)
+    s.forward(keep_activations=False)
+    s.advance_fine(1e-3, solid, 20.0)
+    assert err_to(fp) <= 1e-6
+    s.set_correction(None, None, 0)
+    s.features(fa, solid, 20.0)
+    s.forward(keep_activations=False)
+    s.advance_fine(1e-3, solid, 20.0)
+    assert err_to(fp) > 1e-2
     s.close()

@@ -96,6 +96,15 @@ def test_features_closed_forms():
     assert np.allclose(fv[2, 3, 1, 0], 0.02) and np.allclose(fv[2, 3, 1, 1:4], u0)
     assert np.all(fv[..., 5:] == 0.0)
     assert np.allclose(rho.reshape(N, N, N)[solid == 0], 1.02)
+    # relative to a reference velocity: u - u_ref on voxels with fluid, 0 on a
+    # fully solid voxel, u_ref itself in channels 5-7 everywhere
+    u_ref = np.array([0.05, 0.01, -0.02])
+    feats_r, _, _ = oracle.surr_features(n, f, solid.ravel(), u_ref)
+    fr = feats_r.reshape(n, n, n, 16)
+    assert np.allclose(fr[2, 3, 1, 1:4], u0 - u_ref) and fr[2, 3, 1, 0] == pytest.approx(0.02)
+    assert np.allclose(fr[0, 0, 0, 1:4], 0.0)
+    assert np.allclose(fr[..., 5:8], u_ref) and np.all(fr[..., 8:] == 0.0)
+    assert np.allclose(fr[..., [0, 4]], fv[..., [0, 4]])
 
 
 def test_apply_upsampling_and_equilibrium():
