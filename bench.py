@@ -273,7 +273,8 @@ def run_ours(args):
     prof = mpm.profile_read()
     mpm.profile_enable(0)
     active_nodes = estimate_active_nodes(ro_eager, sc)
-    roof = roofline(prof, n, active_nodes)
+    fp32_peak = B.fp32_peak(paired=True) / 1e12  # FFMA2 throughput of this GPU, now
+    roof = roofline(prof, n, active_nodes, fp32_peak)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -293,7 +294,7 @@ def run_ours(args):
         "wall_s_timed": wall,
     }
     if not args.no_extras:
-        result["metrics"] = extras(dev)
+        result["metrics"] = extras(dev, fp32_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if world > 1:
@@ -318,45 +319,84 @@ def estimate_active_nodes(ro, sc):
     return int(np.unique(lin).size)
 
 
-# DRAM bytes (read + write) per launch of k_g2p2g on the 400,040-particle sheet
-# from one ncu capture of the current kernel (profiles/mpm_rollout_sheet400k.md,
-# "DRAM traffic of k_g2p2g"); to be re-measured whenever that kernel changes.
-G2P2G_DRAM_BYTES_SHEET400K = 20.17e6
-SHEET_PARTICLES = 400040
+# FP32 operations per particle-substep of the MLS-MPM substep, counted from
+# its formulas (a multiply-add counts 2): stencil weights and their products
+# for the old and the new position (2 x 87), G2P velocity (162) and affine
+# matrix (657), position and deformation-gradient update (72), Neo-Hookean
+# stress (62), affine momentum matrix (81), P2G mass and momentum of the 27
+# nodes (783).
+ALGO_FLOP_PER_PS = 1991
+
+# DRAM bytes (read + write) of one launch of the fused kernel on the
+# 400,040-particle sheet, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of the 5th launch of `bench.py --substeps 40 --steps 1
+# --warmup 1 --no-extras --no-cpu-baseline`); valid only for the kernel
+# sources it was taken on (hash of the files below), else reported as null.
+G2P2G_TRAFFIC = {"sha16": "e80c18d01827cff9", "bytes": 27.98e6, "particles": 400040}
+G2P2G_SOURCES = ("mpm_rollout.cu", "mpm_pair.cuh", "mpm_p2g.cuh", "mpm_math.cuh")
 
 
-def roofline(prof, n, active_nodes):
-    """Algorithmic bytes per launch of each substep kernel:
-      P2G   : x, v, C, F read (96 B / particle) + (m, p) written (16 B / node)
-      G2P   : x, F read (48 B / particle) + x, v, C, F written (96 B / particle)
-              + grid velocity read (16 B / node)
-      G2P2G : x, F read and written (96 B / particle) + grid velocity read and
-              (m, p) of the next substep written (32 B / node)
-      grid  : (m, p) read, v written, (m, p) cleared (48 B / active node)."""
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = peaks.get("hbm_gbs", 6800.0)
-    per = {"p2g": 96 * n + 16 * active_nodes, "g2p": 144 * n + 16 * active_nodes,
-           "g2p2g": 96 * n + 32 * active_nodes, "grid": 48 * active_nodes}
-    best = None
-    for k in ("p2g", "g2p", "grid", "g2p2g"):
-        ms, cnt = prof.get(k, (0.0, 0))
-        if cnt and (best is None or ms > best[1]):
-            best = (k, ms, cnt)
-    k, ms, cnt = best
+def g2p2g_source_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in G2P2G_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_09668_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path))["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs (measured)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def roofline(prof, n, active_nodes, fp32_peak_tflops):
+    """Roofline of the dominant kernel of the step, the fused G2P/P2G kernel
+    (k_g2p2g_pair), from its average launch time (CUDA events over an eager
+    pass of the same rollout). It is bound by instruction issue and latency:
+    neither its DRAM traffic nor its FP32 pipe is saturated. `bound` names the
+    nearer roof, the FP32 arithmetic: achieved = the method's FLOPs per
+    launch (ALGO_FLOP_PER_PS x particles) over the launch time, peak = the
+    FFMA2 throughput measured in this run. The HBM view is given beside it on
+    two byte bases: the fused kernel's own (x and F read and written, 96 B per
+    particle, plus 32 B per active node) and the unfused substep interface
+    (x, v, C, F in and out, 192 B per particle, plus 56 B per active node)."""
+    peak_gbs, peak_src = hbm_peak()
+    ms, cnt = prof.get("g2p2g", (0.0, 0))
+    if not cnt:
+        return None
     avg_s = ms / cnt * 1e-3
-    if k in per:
-        traffic = per[k]
-    else:
-        traffic = None
-    achieved = traffic / avg_s / 1e9 if traffic else None
-    measured = G2P2G_DRAM_BYTES_SHEET400K if (k == "g2p2g" and n == SHEET_PARTICLES) else None
-    return {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": measured,
-            "algorithmic_bytes_per_launch": traffic, "avg_launch_us": avg_s * 1e6,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                              "profiles/mpm_rollout_sheet400k.md" if measured else None}
+    flops = ALGO_FLOP_PER_PS * n
+    achieved = flops / avg_s / 1e12
+    b_fused = 96 * n + 32 * active_nodes
+    b_iface = 192 * n + 56 * active_nodes
+    traffic = None
+    if G2P2G_TRAFFIC["bytes"] and n == G2P2G_TRAFFIC["particles"] \
+            and g2p2g_source_sha() == G2P2G_TRAFFIC["sha16"]:
+        traffic = G2P2G_TRAFFIC["bytes"]
+    return {"kernel": "g2p2g", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": traffic,
+            "algorithmic_flop_per_launch": flops, "avg_launch_us": avg_s * 1e6,
+            "peak_source": "FFMA2 throughput probe (dw_fp32_probe), measured in this run",
+            "hbm": {"peak_gbs": peak_gbs, "peak_source": peak_src,
+                    "bytes_fused_basis": b_fused, "gbs_fused_basis": b_fused / avg_s / 1e9,
+                    "frac_fused_basis": b_fused / avg_s / 1e9 / peak_gbs,
+                    "bytes_interface_basis": b_iface,
+                    "gbs_interface_basis": b_iface / avg_s / 1e9,
+                    "frac_interface_basis": b_iface / avg_s / 1e9 / peak_gbs},
+            "traffic_source": ("ncu dram bytes of one launch on the kernel sources of this run"
+                               if traffic else "no capture of the current kernel sources")}
+
+
+def roof_entry(rate, per_unit, peak, unit, bound, basis):
+    """One workload's roofline line: achieved = rate x per_unit (in `unit`),
+    frac = achieved / peak."""
+    achieved = rate * per_unit
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "basis": basis}
 
 
 def _timed(fn, reps=3):
@@ -737,7 +777,7 @@ def bench_gsplat(dev):
             "gs_gaussians": n}
 
 
-def extras(dev):
+def extras(dev, fp32_peak):
     out = bench_lbm(dev)
     out.update(bench_adjoint(dev))
     out.update(bench_surrogate(dev))
@@ -745,60 +785,137 @@ def extras(dev):
     out.update(bench_batch_adjoint(dev))
     out.update(bench_inversion(dev))
     out.update(bench_gsplat(dev))
+    out["roofline"] = workload_rooflines(out, fp32_peak)
     return out
 
 
-def cpu_baseline(n_sub=75):
-    """The FP64 oracle on this host: n_sub substeps of the full 400k sheet."""
+def workload_rooflines(m, fp32_peak):
+    """Roofline lines of the secondary workloads from their measured rates:
+    bytes per unit are the algorithmic interface bytes (LBM: populations or
+    moments in and out; MPM: particle state in and out), FLOPs per call of the
+    surrogate are those of the network the method specifies."""
+    gbs, _ = hbm_peak()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    r = {}
+    if "lbm_128_fwd_mlups" in m:
+        r["lbm_128_fwd"] = roof_entry(m["lbm_128_fwd_mlups"] * 1e6, 152 / 1e9, gbs, "GB/s", "hbm",
+                                      "152 B per cell-step (19 populations in and out)")
+    if "lbm_128_adj_mlups" in m:
+        r["lbm_128_adj"] = roof_entry(m["lbm_128_adj_mlups"] * 1e6, 380 / 1e9, gbs, "GB/s", "hbm",
+                                      "380 B per cell-step (state, adjoint in and out: 228; "
+                                      "the forward recompute: 152)")
+    if "lbm_128_home_mlups" in m:
+        r["lbm_128_home"] = roof_entry(m["lbm_128_home_mlups"] * 1e6, 80 / 1e9, gbs, "GB/s", "hbm",
+                                       "80 B per cell-step (10 moments in and out)")
+    if "mpm_adj_sheet100k_64_ps_per_s" in m:
+        r["mpm_fwd_adj_sheet100k_64"] = roof_entry(
+            m["mpm_adj_sheet100k_64_ps_per_s"], 672 / 1e9, gbs, "GB/s", "hbm",
+            "672 B per particle-substep (forward 192; reverse 480: recompute 192, stored "
+            "state 96, adjoint state in and out 192)")
+    if "batch_ps_per_s" in m:
+        r["batch_fwd"] = roof_entry(m["batch_ps_per_s"], 192 / 1e9, gbs, "GB/s", "hbm",
+                                    "192 B per particle-substep (x, v, C, F in and out)")
+        r["batch_fwd_flops"] = roof_entry(m["batch_ps_per_s"], ALGO_FLOP_PER_PS / 1e12, fp32_peak,
+                                          "TFLOP/s", "alu", f"{ALGO_FLOP_PER_PS} FLOP per "
+                                          "particle-substep, FFMA2 peak measured in this run")
+    if "batch_fwd_adj_ps_per_s" in m:
+        r["batch_fwd_adj"] = roof_entry(m["batch_fwd_adj_ps_per_s"], 672 / 1e9, gbs, "GB/s", "hbm",
+                                        "672 B per particle-substep (as the single-scene adjoint)")
+    if "surr_block_ms" in m:
+        r["surrogate_block"] = roof_entry(1.0 / (m["surr_block_ms"] * 1e-3), 32.6e9 / 1e12, bf16,
+                                          "TFLOP/s", "tensor",
+                                          "32.6 GFLOP per call (5 -> 32 -> 32 -> 32 -> 3 channels, "
+                                          "kernel 3, 64^3; the kernels run 16-channel padded ends, "
+                                          "43.5 GFLOP) over the whole block (network and "
+                                          "chained update); BF16 burst peak of MEASURED_PEAKS.json")
+    return r
+
+
+def _oracle_sheet_run(args):
+    """Runs n_sub FP64 oracle substeps of the full sheet (replica `seed`) in
+    this process and returns the seconds taken (one replica per host core)."""
+    n_sub, seed = args
     import oracle
     from paper_2603_09668_gb300 import inputs
 
-    sc = inputs.sheet_scene()
+    sc = inputs.sheet_scene(seed=seed, wind_seed=seed)
     st = tuple(a.astype(np.float64) for a in inputs.rest_state(sc.x))
     t0 = time.perf_counter()
     for k in range(n_sub):
         st = oracle.mpm_substep(sc.params(), st, sc.wind_tuple(), k * sc.dt, sc.pinned)
-    dt = time.perf_counter() - t0
-    return {"value": sc.n * n_sub / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_sub} substeps of the full 400,040-particle sheet on 128^3 (FP64, serial C)",
-            "seconds": dt}
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n_sub=75, n_sub_all=30):
+    """The FP64 oracle on this host: n_sub substeps of the full 400k sheet on
+    one core, and independent replicas of n_sub_all substeps on every core at
+    once (processes started with spawn), the whole job's rate reported."""
+    import multiprocessing
+
+    import oracle
+    from paper_2603_09668_gb300 import inputs
+
+    oracle.build()
+    n = inputs.sheet_scene().n
+    one = _oracle_sheet_run((n_sub, 0))
+    cores = host_cores()
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_sheet_run, [(1, r) for r in range(cores)])  # load the library once
+        t0 = time.perf_counter()
+        pool.map(_oracle_sheet_run, [(n_sub_all, r) for r in range(cores)])
+        wall = time.perf_counter() - t0
+    return {"value": cores * n * n_sub_all / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{cores} independent replicas (one per core) of {n_sub_all} substeps of the "
+                       f"full 400,040-particle sheet on 128^3 (FP64, serial C each)"),
+            "seconds": wall,
+            "one_core": {"value": n * n_sub / one, "cores": 1,
+                         "sample": f"{n_sub} substeps of the full sheet on one core", "seconds": one}}
 
 
 # ------------------------------------------------------- reference arm ----
 
 def run_reference(args):
+    """The FP64 oracle on the host's cores: every step, one independent
+    replica of the full sheet per core (processes started with spawn) runs
+    3 substeps; value = particle-substeps of all replicas per second."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    import multiprocessing
+
     import oracle
     from paper_2603_09668_gb300 import inputs
 
     oracle.build()
-    sc = inputs.sheet_scene()
-    n_sub = 3  # each step: 3 substeps of the full sheet (~1-2 s of FP64 CPU work)
-    st0 = tuple(a.astype(np.float64) for a in inputs.rest_state(sc.x))
+    n = inputs.sheet_scene().n
+    n_sub = 3  # each step: 3 substeps of the full sheet per core (~1-2 s of FP64 CPU work)
+    cores = host_cores()
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        def step():
+            pool.map(_oracle_sheet_run, [(n_sub, r) for r in range(cores)])
 
-    def step():
-        st = st0
-        for k in range(n_sub):
-            st = oracle.mpm_substep(sc.params(), st, sc.wind_tuple(), k * sc.dt, sc.pinned)
-
-    for _ in range(args.warmup):
-        step()
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        step()
-        ts.append(time.perf_counter() - t0)
+        pool.map(_oracle_sheet_run, [(1, r) for r in range(cores)])  # load the library once
+        for _ in range(args.warmup):
+            step()
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            step()
+            ts.append(time.perf_counter() - t0)
     s_step = sum(ts) / len(ts)
-    value = sc.n * n_sub / s_step
-    sample = f"{n_sub} substeps of the full 400,040-particle sheet on 128^3 per step (FP64, serial C)"
+    value = cores * n * n_sub / s_step
+    sample = (f"{cores} independent replicas (one per core) of {n_sub} substeps of the full "
+              f"400,040-particle sheet on 128^3 per step (FP64, serial C each)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

@@ -94,7 +94,7 @@ def test_graph_replayed_blocks_equal_eager_blocks():
 def test_window_with_checks_holds_2_percent_and_beats_persistence():
     """The wind-constraint window t = 1500 -> 2000 (25 blocks of 20 lattice
     steps) of the held-out scene, run by the network with the plain-LBM check
-    every 4 blocks (the run continues from the plain lattice after a check):
+    every 3 blocks (the run continues from the plain lattice after a check):
     the final fluid velocity is within 2% (relative L2) of the plain LBM's
     trajectory without any fallback, and the same schedule with persistence
     (du = 0) in place of the network ends farther from it: what the network
