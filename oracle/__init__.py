@@ -73,6 +73,10 @@ class _MpmParams(ct.Structure):
                 ("nu", ct.c_double), ("p_mass", ct.c_double), ("p_vol", ct.c_double)]
 
 
+class _Wind(ct.Structure):
+    _fields_ = [("values", _dp), ("nf", ct.c_int), ("n_frames", ct.c_int), ("t_total", ct.c_double)]
+
+
 def _declare(lib):
     i64 = ct.c_int64
     d = ct.c_double
@@ -89,6 +93,8 @@ def _declare(lib):
         "orc_wind_sample": (None, [_dp, i, i, d, _dp, i64, d, _dp]),
         "orc_wind_sample_adjoint": (None, [_dp, i, i, d, _dp, i64, d, _dp, _dp]),
         "orc_mpm_p2g_grid": (i, [P, i64, _dp, _dp, _dp, _dp, _dp, _dp]),
+        "orc_mpm_grid_update": (i, [P, _dp, _dp, ct.POINTER(_Wind), d, _dp]),
+        "orc_mpm_g2p": (i, [P, i64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _dp]),
         "orc_mpm_substep": (i, [P, i64, _dp, _dp, _dp, _dp, _u8p, _dp, i, i, d, d,
                                 _dp, _dp, _dp, _dp]),
         "orc_mpm_substep_adjoint": (i, [P, i64, _dp, _dp, _dp, _dp, _u8p, _dp, i, i, d, d,
@@ -233,6 +239,35 @@ def mpm_p2g(params, x, v, C, F):
     _check(_load().orc_mpm_p2g_grid(ct.byref(pr), n, _ptr(x), _ptr(v), _ptr(C), _ptr(F),
                                     _ptr(gm), _ptr(gp)), "p2g")
     return gm, gp
+
+
+def mpm_grid_update(params, gm, gp, wind, t):
+    """Grid velocities v[3][N^3] from mass and momentum (Eq. grid update: the
+    momentum over the mass plus dt (gravity + wind force), zero on empty
+    nodes and in the sticky wall band)."""
+    gm, gp = _f64(gm), _f64(gp)
+    N = int(params["n_grid"])
+    values, nf, nfr, ttot = wind
+    values = _f64(values)
+    w = _Wind(_ptr(values), int(nf), int(nfr), float(ttot))
+    gv = np.zeros((3, N ** 3))
+    pr = _params(params)
+    _check(_load().orc_mpm_grid_update(ct.byref(pr), _ptr(gm), _ptr(gp), ct.byref(w), float(t),
+                                       _ptr(gv)), "grid update")
+    return gv
+
+
+def mpm_g2p(params, x, F, gv, pinned=None):
+    """G2P and the deformation update of particles at x with gradients F from
+    grid velocities gv[3][N^3]. Returns (x, v, C, F) after the substep."""
+    x, F, gv = _f64(x), _f64(F), _f64(gv)
+    n = x.shape[1]
+    out = (np.zeros((3, n)), np.zeros((3, n)), np.zeros((9, n)), np.zeros((9, n)))
+    pr = _params(params)
+    pin = _pinned(pinned, n)
+    _check(_load().orc_mpm_g2p(ct.byref(pr), n, _ptr(x), _ptr(F), _u8ptr(pin), _ptr(gv),
+                               *(_ptr(o) for o in out)), "g2p")
+    return out
 
 
 def mpm_substep(params, state, wind, t, pinned=None):
