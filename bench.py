@@ -333,7 +333,8 @@ ALGO_FLOP_PER_PS = 1991
 # --warmup 1 --no-extras --no-cpu-baseline`); valid only for the kernel
 # sources it was taken on (hash of the files below), else reported as null.
 G2P2G_TRAFFIC = {"sha16": "e80c18d01827cff9", "bytes": 27.98e6, "particles": 400040}
-G2P2G_SOURCES = ("mpm_rollout.cu", "mpm_pair.cuh", "mpm_p2g.cuh", "mpm_math.cuh")
+G2P2G_SOURCES = ("mpm_rollout.cu", "mpm_pair_warp.cuh", "mpm_pair.cuh", "mpm_p2g.cuh",
+                 "mpm_math.cuh")
 
 
 def g2p2g_source_sha():

@@ -415,13 +415,16 @@ DW_API dw_status image_dssim_loss(const float *image, const float *target, int32
  * work items (one scene per item). The barrier's wait is bounded: if it gives
  * up, the device status becomes DW_ERR_TIMEOUT and later substeps of the
  * batch do nothing until mpm_batch_device_status clears it. DW_BATCH_SPLIT
- * runs the two phases as two launches (programmatic dependent launch). With
+ * runs the two phases as two launches (programmatic dependent launch).
+ * DW_BATCH_PAIR is DW_BATCH_SPLIT with the fused phase of mpm_rollout's
+ * default kernel (two particles per thread on paired FP32 instructions, 64
+ * particles of one scene per warp); it is the default configuration. With
  * use_graph, the whole launch sequence of a rollout is captured once per
  * distinct (state pointers, n_substeps, sort_every, config) in a CUDA graph
  * owned by the handle and replayed; if capture is not possible the sequence
  * is launched directly (mpm_batch_get_config reports graph_active = 0).
  */
-enum { DW_BATCH_PERSISTENT = 0, DW_BATCH_SPLIT = 1 };
+enum { DW_BATCH_PERSISTENT = 0, DW_BATCH_SPLIT = 1, DW_BATCH_PAIR = 2 };
 
 typedef struct {
     dw_mpm_desc desc;      /* the scene's physics; desc.max_particles and desc.p2g_mode are ignored */
@@ -431,10 +434,11 @@ typedef struct {
 } dw_mpm_scene;
 
 typedef struct {
-    int32_t mode;          /* DW_BATCH_PERSISTENT or DW_BATCH_SPLIT */
-    int32_t threads;       /* CTA size, 128 or 256 (one or two 128-particle work items per CTA) */
+    int32_t mode;          /* DW_BATCH_PERSISTENT, DW_BATCH_SPLIT or DW_BATCH_PAIR */
+    int32_t threads;       /* CTA size, 128 or 256 (one or two 128-particle work items per CTA);
+                              PAIR: of the grid-update launch (the paired kernel has 128) */
     int32_t ctas_per_sm;   /* PERSISTENT: resident CTAs per SM (>= 1, clamped to the occupancy
-                              limit); SPLIT: CTAs per SM of the grid-update launch */
+                              limit); SPLIT, PAIR: CTAs per SM of the grid-update launch */
     int32_t use_graph;     /* nonzero: replay rollouts from a CUDA graph */
     int32_t graph_active;  /* output of mpm_batch_get_config: the last rollout ran from a graph */
 } dw_batch_config;
@@ -473,10 +477,11 @@ DW_API dw_status mpm_batch_rollout(dw_mpm_batch h, const dw_mpm_state *state, ui
 DW_API dw_status mpm_batch_set_config(dw_mpm_batch h, const dw_batch_config *config);
 DW_API dw_status mpm_batch_get_config(dw_mpm_batch h, dw_batch_config *config);
 
-/* Autotuner: times every candidate launch shape (both modes, 128 and 256
- * threads, each resident-CTA count up to the occupancy limit) on
- * n_trial_substeps substeps of the batch started from `state` (copied into
- * the handle's workspace; `state` and `pinned` are not modified), keeps the
+/* Autotuner: times every candidate launch shape (the three modes, 128 and
+ * 256 threads, each resident-CTA count up to the occupancy limit) on
+ * n_trial_substeps substeps of the batch started from `state` sorted by cell
+ * (as a rollout with re-sorting starts; the sorted copy goes into the
+ * handle's workspace, `state` and `pinned` are not modified), keeps the
  * fastest as the handle's configuration (use_graph unchanged) and returns it
  * in *best (may be NULL). trials (host, max_trials entries, or NULL) receives
  * each candidate and its time; *n_trials (may be NULL) their number. The call

@@ -39,7 +39,7 @@ __all__ = ["DiffWindError", "MpmState", "WindField", "wind_field_sample",
            "mpm_batch_wind_layout", "mpm_batch_segment_adjoint", "MPMBatch"]
 
 NEOHOOKEAN, FIXED_COROTATED = 0, 1
-BATCH_PERSISTENT, BATCH_SPLIT = 0, 1
+BATCH_PERSISTENT, BATCH_SPLIT, BATCH_PAIR = 0, 1, 2
 P2G_AUTO, P2G_ATOMIC, P2G_WARP, P2G_TILE, P2G_PAIR = 0, 1, 2, 3, 4
 
 

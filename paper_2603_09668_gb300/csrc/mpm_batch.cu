@@ -18,7 +18,11 @@
 // its scene's cleared grid (P2G of substep k + 1), appending newly touched
 // blocks to the other list. The last substep before a sort (and of the
 // rollout) stores v and C instead of scattering. Split mode runs the phases
-// as two kernels with programmatic dependent launch.
+// as two kernels with programmatic dependent launch. Pair mode is split mode
+// whose scattering phase B is the two-particles-per-thread body of
+// mpm_rollout (k_batch_pair: 64 particles of one scene per warp); the last
+// substep before a sort, and the recompute of a reverse segment, run the
+// split-mode kernels.
 //
 // The sort is one counting sort over all scenes: scene s's keys are offset by
 // the number of keys of the scenes before it, so the sorted order keeps every
@@ -39,6 +43,7 @@
 
 #include "mpm_adjoint.cuh"
 #include "mpm_handle.cuh"
+#include "mpm_pair_warp.cuh"
 
 namespace dw {
 
@@ -257,6 +262,34 @@ __global__ void __launch_bounds__(THREADS) k_batch_particles(BatchView A, int L)
     batch_items<THREADS, FINAL, false>(A, 1 - L, rows, keys);
 }
 
+// Pair mode, phase B of a substep that scatters: the paired body of
+// mpm_rollout (pair_warp, two particles per thread on FP32 pairs, box-staged
+// G2P, row-summed P2G). Warp w of CTA b takes half (b PAIR_WARPS + w) & 1 of
+// work item (b PAIR_WARPS + w) >> 1: up to 64 particles of one scene. Each
+// warp stages its scene record in shared memory, so that the scene's
+// parameters are shared-memory operands, and the material is chosen per warp.
+template <bool VEC>
+__global__ void __launch_bounds__(PAIR_THREADS, 5) k_batch_pair(BatchView A, int L) {
+    constexpr int WORDS = sizeof(BatchScene) / 4;
+    __shared__ PairWarpSmem smem[PAIR_WARPS];
+    __shared__ BatchScene scene[PAIR_WARPS];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int hw = blockIdx.x * PAIR_WARPS + wid;
+    if ((hw >> 1) >= A.n_items) return;
+    const int4 item = A.items[hw >> 1];
+    for (int w = lane; w < WORDS; w += 32)
+        reinterpret_cast<int *>(&scene[wid])[w] = reinterpret_cast<const int *>(A.scenes + item.x)[w];
+    __syncwarp();
+    const BatchScene &S = scene[wid];
+    const ActiveBlocks ab{S.flags, A.list + (size_t)(1 - L) * A.list_cap, A.count + (1 - L), S.nb,
+                          item.x << BATCH_SCENE_SHIFT};
+    const int64_t first = item.y;
+    pair_warp<-1, false, VEC>(S.P, A.x, A.v, A.C, A.F, A.pinned, S.grid_v, S.grid_mp, A.n,
+                              first + (hw & 1) * 64, first + item.z, A.err, ab,
+                              blockIdx.x == 0 && threadIdx.x == 0 ? A.count + L : nullptr,
+                              smem[wid]);
+}
+
 // P2G of every scene from a complete state (start of a segment), list L.
 __global__ void __launch_bounds__(BATCH_ITEM) k_batch_p2g(BatchView A, int L) {
     __shared__ float4 rows[BATCH_ITEM / 32][32][P2G_ROW];
@@ -465,6 +498,7 @@ struct dw_mpm_batch_s {
     int64_t total_keys = 0;
     int list_cap = 0;
     int n_items = 0;
+    bool items_aligned4 = false;  // n and every scene offset a multiple of 4
     int num_sms = 0;
     int occupancy[2][2] = {{0, 0}, {0, 0}};  // [threads == 256][final]: CTAs per SM
     dw::BatchScene *scenes = nullptr;  // device table
@@ -549,10 +583,22 @@ static int occupancy_of(dw_mpm_batch h, int threads, bool final_) {
     return h->occupancy[threads == 256 ? 1 : 0][final_ ? 1 : 0];
 }
 
-// One substep launch (or two in split mode).
+// One substep launch (or two in split and pair mode). vec: the pair kernel
+// may load x and F as float2 and 16-byte pieces.
 static dw_status launch_substep(dw_mpm_batch h, const BatchView &A, const dw_batch_config &c,
-                                int k, int L, bool final_, cudaStream_t s) {
+                                int k, int L, bool final_, cudaStream_t s, bool vec = false) {
     const int T = c.threads;
+    if (c.mode == DW_BATCH_PAIR && !final_ && !A.ox) {
+        const unsigned ggrid = (unsigned)(c.ctas_per_sm * h->num_sms);
+        const unsigned pgrid = (unsigned)((h->n_items + 1) / 2);
+        if (T == 256)
+            DW_CUDA(launch_pdl(k_batch_grid<256>, ggrid, 256, s, A, k, L));
+        else
+            DW_CUDA(launch_pdl(k_batch_grid<128>, ggrid, 128, s, A, k, L));
+        DW_CUDA(vec ? launch_pdl(k_batch_pair<true>, pgrid, PAIR_THREADS, s, A, L)
+                    : launch_pdl(k_batch_pair<false>, pgrid, PAIR_THREADS, s, A, L));
+        return DW_OK;
+    }
     if (c.mode == DW_BATCH_PERSISTENT) {
         const int per_sm = std::min(c.ctas_per_sm, occupancy_of(h, T, final_));
         const unsigned grid = (unsigned)(per_sm * h->num_sms);
@@ -601,11 +647,15 @@ static dw_status enqueue_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint
             std::swap(cur_ids, oth_ids);
         }
         const BatchView A = view_of(h, cur, cur_pin);
+        // pair kernel vector loads: every work item starts at a multiple of 4
+        // particles and the arrays are 16-byte aligned
+        const bool vec = h->items_aligned4 &&
+                         ((reinterpret_cast<uintptr_t>(cur.x) | reinterpret_cast<uintptr_t>(cur.F)) % 16 == 0);
         k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, L);
         DW_LAUNCHED("k_batch_p2g");
         for (int j = 0; j < len; ++j) {
             const bool final_ = j + 1 == len;
-            dw_status st = launch_substep(h, A, c, k_base + k0 + j, L, final_, s);
+            dw_status st = launch_substep(h, A, c, k_base + k0 + j, L, final_, s, vec);
             if (st != DW_OK) return st;
             if (!final_) L = 1 - L;
         }
@@ -665,8 +715,9 @@ static dw_status check_batch_state(dw_mpm_batch h, const dw_mpm_state *s) {
 
 static dw_status check_config(dw_mpm_batch h, const dw_batch_config *c) {
     DW_REQUIRE(c, "config is NULL");
-    DW_REQUIRE(c->mode == DW_BATCH_PERSISTENT || c->mode == DW_BATCH_SPLIT, "unknown mode %d",
-               c->mode);
+    DW_REQUIRE(c->mode == DW_BATCH_PERSISTENT || c->mode == DW_BATCH_SPLIT ||
+                   c->mode == DW_BATCH_PAIR,
+               "unknown mode %d", c->mode);
     DW_REQUIRE(c->threads == 128 || c->threads == 256, "threads must be 128 or 256");
     DW_REQUIRE(c->ctas_per_sm >= 1 && c->ctas_per_sm <= 64, "ctas_per_sm out of range [1, 64]");
     if (c->mode == DW_BATCH_PERSISTENT)
@@ -734,6 +785,8 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
     h->total_keys = total_keys;
     h->list_cap = (int)blk_off[n_scenes];
     h->n_items = (int)items.size();
+    h->items_aligned4 = true;
+    for (int s = 0; s <= n_scenes; ++s) h->items_aligned4 = h->items_aligned4 && offsets[s] % 4 == 0;
     h->scan_tmp_len = (total_keys + SCAN_BLOCK) / SCAN_BLOCK + 1;
     const int64_t n = h->n_total;
     cudaError_t e = cudaSuccess;
@@ -788,9 +841,9 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
         return e == cudaErrorMemoryAllocation ? (set_error("out of device memory"), DW_ERR_OOM)
                                               : cuda_fail(e, "mpm_batch_create");
     }
-    h->cfg.mode = DW_BATCH_PERSISTENT;
+    h->cfg.mode = DW_BATCH_PAIR;
     h->cfg.threads = 128;
-    h->cfg.ctas_per_sm = std::max(1, std::min(h->occupancy[0][0], h->occupancy[0][1]));
+    h->cfg.ctas_per_sm = 4;
     h->cfg.use_graph = 1;
     h->cfg.graph_active = 0;
     *out = h;
@@ -924,10 +977,12 @@ extern "C" dw_status mpm_batch_tune(dw_mpm_batch h, const dw_mpm_state *state,
         const int occ = std::min(occupancy_of(h, T, false), occupancy_of(h, T, true));
         for (int c = 1; c <= occ; ++c)
             cand.push_back(dw_batch_config{DW_BATCH_PERSISTENT, T, c, 0, 0});
-        for (int c : {2, 4})
+        for (int c : {2, 4}) {
             cand.push_back(dw_batch_config{DW_BATCH_SPLIT, T, c, 0, 0});
+            cand.push_back(dw_batch_config{DW_BATCH_PAIR, T, c, 0, 0});
+        }
     }
-    // the trials run on a copy of the state in the workspace
+    // the trials run on a copy of the state sorted by cell into the workspace
     const dw_mpm_state work = state_view(h->roll_state, n);
     uint8_t *work_pin = pinned ? h->roll_pinned : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -944,12 +999,9 @@ extern "C" dw_status mpm_batch_tune(dw_mpm_batch h, const dw_mpm_state *state,
     for (size_t i = 0; i < cand.size() && result == DW_OK; ++i) {
         float ms = 0.0f;
         for (int rep = 0; rep < 2 && result == DW_OK; ++rep) {
-            cudaError_t e = cudaMemcpyAsync(work.x, state->x, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(work.v, state->v, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(work.C, state->C, sizeof(float) * 9 * (size_t)n, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(work.F, state->F, sizeof(float) * 9 * (size_t)n, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess && pinned) e = cudaMemcpyAsync(work_pin, pinned, (size_t)n, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            result = batch_sort(h, *state, work, pinned, work_pin, nullptr, h->roll_ids, s);
+            if (result != DW_OK) break;
+            cudaError_t e = cudaEventRecord(e0, s);
             if (e != cudaSuccess) {
                 result = cuda_fail(e, "mpm_batch_tune");
                 break;

@@ -155,14 +155,15 @@ __device__ __forceinline__ void cof3_2(const float2 A[9], float2 K[9]) {
 
 // Affine momentum matrices A = -dt V0 (4/dx^2) P F^T + m C of both particles.
 // ok0 / ok1: det F > 0 (the stress is defined; P = 0 otherwise). The
-// fixed-corotated model (MAT = DW_FIXED_COROTATED) runs the scalar polar
-// iteration per particle (its Newton loop ends at a different step for each).
+// fixed-corotated model (MAT = DW_FIXED_COROTATED) runs the scalar affine
+// update of the one-particle kernels (p2g_affine) per particle: the polar
+// iteration's Newton loop ends at a different step for each.
+// MAT < 0: the material of P, chosen at run time.
 template <int MAT>
 __device__ __forceinline__ void affine2(const MpmParams &P, const float2 F[9], const float2 C[9],
                                        float2 A[9], bool &ok0, bool &ok1) {
-    float2 Pk[9];
-    if (MAT == DW_NEOHOOKEAN) {
-        float2 K[9];
+    if (MAT == DW_NEOHOOKEAN || (MAT < 0 && P.material == DW_NEOHOOKEAN)) {
+        float2 Pk[9], K[9];
         cof3_2(F, K);
         // det F = F0 K0 + F1 K1 + F2 K2 (expansion along the first row)
         const float2 J = fma(F[2], K[2], fma(F[1], K[1], mul(F[0], K[0])));
@@ -175,23 +176,31 @@ __device__ __forceinline__ void affine2(const MpmParams &P, const float2 F[9], c
         const float2 c = sub(mul(s2(P.lam), lnJ), mu);
 #pragma unroll
         for (int k = 0; k < 9; ++k) Pk[k] = fma(c, mul(K[k], inv), mul(mu, F[k]));
+        float2 PFt[9];
+        mul3_abt2(Pk, F, PFt);
+        const float2 mk = s2(-P.kappa), pm = s2(P.p_mass);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) A[k] = fma(mk, PFt[k], mul(pm, C[k]));
     } else {
-        float F0[9], F1[9], P0[9], P1[9];
+        // one particle after the other, each one's A finished before the
+        // other's polar iteration starts (fewer values live across the loop)
+        float Fq[9], Cq[9], Aq[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            F0[k] = F[k].x;
-            F1[k] = F[k].y;
+            Fq[k] = F[k].x;
+            Cq[k] = C[k].x;
         }
-        ok0 = stress_P(P, F0, P0);
-        ok1 = stress_P(P, F1, P1);
+        ok0 = p2g_affine(P, Fq, Cq, Aq);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Pk[k] = make_float2(P0[k], P1[k]);
+        for (int k = 0; k < 9; ++k) {
+            A[k].x = Aq[k];
+            Fq[k] = F[k].y;
+            Cq[k] = C[k].y;
+        }
+        ok1 = p2g_affine(P, Fq, Cq, Aq);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) A[k].y = Aq[k];
     }
-    float2 PFt[9];
-    mul3_abt2(Pk, F, PFt);
-    const float2 mk = s2(-P.kappa), pm = s2(P.p_mass);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) A[k] = fma(mk, PFt[k], mul(pm, C[k]));
 }
 
 // G2P sums of both particles from a box of staged grid velocities: planes

@@ -171,7 +171,13 @@ def test_inversion_from_rendered_views():
     case = inputs.inversion_case()
     free = I.run_synthetic(case, iters=40, lr=1.0, lam_phys=0.0, observe="render")
     h = free["result"].history.cpu().numpy()
+    print("image term per interval and iteration:", np.round(h[:, :, 0], 5).tolist())
     assert h[:, -1, 0].sum() < 0.8 * h[:, 0, 0].sum(), h[:, [0, -1], 0]
+    # every interval's optimisation lowers the image term well below its
+    # zero-start value (measured on a GB300: to 0.55, 0.50 and 0.37 of it);
+    # without L_phys the last iterate of the second interval drifts back up
+    # (0.0213 -> 0.0106 at iteration 8 -> 0.0214 at 40)
+    assert np.all(h[:, :, 0].min(axis=1) < 0.7 * h[:, 0, 0]), h[:, :, 0].min(axis=1) / h[:, 0, 0]
     guided = I.run_synthetic(case, iters=40, lr=1.0, lam_phys=0.1, observe="render")
     assert torch.isfinite(guided["result"].values).all()
     assert guided["cos_sim"] > 0.85, guided["cos_sim"]
@@ -271,5 +277,110 @@ def test_inversion_loop_matches_the_oracle_loop():
         assert strong.sum() >= 8
         e = rel_l2(got[k][strong], ref_vals[k][strong])
         assert e <= 2e-3, (k, e, int(strong.sum()))
+    guide.close()
+    mpm.close()
+
+
+def test_render_loop_matches_the_oracle_loop():
+    """One interval of the inversion observed through two rendered oblique
+    views on a tiny case (192-particle sheet, 16^3 grid, 4^3 wind grid, 20
+    substeps of 1 ms, 48 x 48 views, three VectorAdam iterations, no L_phys):
+    the GPU loop
+    (float32 render, 0.9 L1 + 0.1 D-SSIM, renderer backward, checkpointed MPM
+    adjoint every 5 substeps) against the same loop written with the FP64
+    oracle's renderer, image losses and MPM reverse pass. The observed images
+    are the oracle's renders of the oracle's forward run under a known wind.
+    Compared: the image loss of every iteration, and the wind values after
+    the three steps on the nodes whose first gradient is well above the
+    float32 noise (there the normalised step direction is determined)."""
+    from oracle import gsplat as G
+    from paper_2603_09668_gb300 import inversion as I
+
+    sc = inputs.sheet_scene(nu=12, nv=8, n_grid=16, n_substeps=20, dt=1e-3, wind_nf=4,
+                            wind_frames=1, seed=0)
+    prm, n, dt = sc.params(), sc.n, sc.dt
+    nf, S, every, iters, lr, lam_s = 4, 20, 5, 3, 1.0, 0.1
+    W = H = 48
+    st0 = tuple(a.astype(np.float64) for a in inputs.rest_state(sc.x))
+    h = 0.6 / (12 - 1)
+    sigma0 = np.zeros((6, n))
+    sigma0[:3] = h * h
+    color = inputs.sheet_texture(sc.x).astype(np.float64)
+    opacity = np.full(n, 0.9)
+    centre, f = np.array([0.5, 0.6, 0.5]), 1.25 * W
+    ocams, dcams = [], []
+    # oblique views (about y, then tilted about x): seen face-on, or turned
+    # about y alone, lattice neighbours of the flat sheet overlap at exactly
+    # equal depths, and their blending order (so the image) would follow
+    # rounding; here overlapping Gaussians differ in depth by > 5e-4
+    for a, b in ((0.45, 0.3), (-0.55, 0.35)):
+        Ry = np.array([[np.cos(a), 0.0, np.sin(a)], [0.0, 1.0, 0.0], [-np.sin(a), 0.0, np.cos(a)]])
+        Rx = np.array([[1.0, 0.0, 0.0], [0.0, np.cos(b), -np.sin(b)], [0.0, np.sin(b), np.cos(b)]])
+        R = Ry @ Rx
+        T = np.array([0.0, 0.0, 1.5]) - R @ centre
+        ocams.append(G.camera(R, T, f, f, W / 2, H / 2, W, H))
+        dcams.append(B.camera(R, T, f, f, W / 2, H / 2, W, H))
+
+    def wind_of(val):
+        return (val.reshape(1, nf, nf, nf, 3), nf, 1, 1.0)
+
+    # observations: the oracle's renders of its run under a known wind
+    w_true = inputs.fourier_wind(nf, 1, mean=(4.0, 0.0, 8.0), seed=3).reshape(-1, 3)
+    st = st0
+    for j in range(S):
+        st = oracle.mpm_substep(prm, st, wind_of(w_true), j * dt, sc.pinned)
+    targets = np.stack([G.render(st[0], st[3], sigma0, color, opacity, oc) for oc in ocams])
+    targets = targets.astype(np.float32)
+
+    # the oracle's loop
+    val, mm, vv = np.zeros((nf ** 3, 3)), np.zeros((nf ** 3, 3)), np.zeros(nf ** 3)
+    losses, first_g = [], None
+    for it in range(iters):
+        states = [st0]
+        for j in range(S):
+            states.append(oracle.mpm_substep(prm, states[-1], wind_of(val), j * dt, sc.pinned))
+        xe, Fe = states[-1][0], states[-1][3]
+        L, gx, gF = 0.0, np.zeros((3, n)), np.zeros((9, n))
+        for oc, tgt in zip(ocams, targets):
+            img = G.render(xe, Fe, sigma0, color, opacity, oc)
+            l1, g1 = G.l1_loss(img, tgt)
+            ds, g2 = G.dssim_loss(img, tgt)
+            L += (1.0 - lam_s) * l1 + lam_s * ds
+            gr = G.render_grad(xe, Fe, sigma0, color, opacity, oc, (1.0 - lam_s) * g1 + lam_s * g2)
+            gx += gr["x"]
+            gF += gr["F"]
+        losses.append(L)
+        g = (gx, np.zeros((3, n)), np.zeros((9, n)), gF)
+        gw = np.zeros((1, nf, nf, nf, 3))
+        for j in reversed(range(S)):
+            g, gw, _ = oracle.mpm_substep_adjoint(prm, states[j], wind_of(val), j * dt, g,
+                                                  sc.pinned, gw)
+        gtot = gw.reshape(-1, 3)
+        if it == 0:
+            first_g = np.linalg.norm(gtot, axis=1)
+        val, mm, vv = phys.vector_adam_step(val, gtot, mm, vv, it + 1, lr)
+
+    # the GPU loop on the same observations
+    mpm = B.MPM.from_params(prm, max_particles=n)
+    guide = I.LbmGuide(16, 0.6, (0.05, 0.0, 0.0), nf, model="home")
+    inv = I.WindInversion(mpm, guide, S, every, iters, lr, 0.0)
+    views = I.RenderObservation(B.GaussianRenderer(n, W, H), dcams,
+                                to_dev(sigma0.astype(np.float32)), to_dev(color.astype(np.float32)),
+                                to_dev(opacity.astype(np.float32)), lambda_ssim=lam_s)
+    state0 = B.MpmState(*(to_dev(a.astype(np.float32)) for a in st0))
+    res = inv.reconstruct(state0, to_dev(sc.pinned), to_dev(targets[None]), 5, views=views)
+    mpm.device_status()
+    got_L = res.history[0, :, 0].cpu().numpy()
+    got = res.values[0].cpu().numpy()
+    strong = first_g > 1e-3 * first_g.max()
+    e_val = rel_l2(got[strong], val[strong])
+    e_L = np.abs(got_L - np.array(losses)) / np.array(losses)
+    print("image loss GPU / oracle:", got_L.tolist(), losses, "value error", e_val,
+          "strong nodes", int(strong.sum()))
+    assert strong.sum() >= 8
+    # measured on a GB300: losses within 3e-5, values within 4.2e-4
+    assert e_L.max() <= 2e-4, (got_L, losses)
+    assert e_val <= 2e-3, e_val
+    views.renderer.close()
     guide.close()
     mpm.close()
