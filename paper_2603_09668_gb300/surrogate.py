@@ -11,7 +11,10 @@ with random leaf-cluster obstacles and random inlet directions.
 `SurrogateLBM.advance` re-checks the surrogate against the plain LBM every
 `check_every` blocks: it runs both from the same lattice and compares the
 fluid velocities; the run continues from the plain result. If the relative
-L2 error exceeds `tol` (2%), the surrogate is switched off from then on.
+L2 error exceeds `tol` (2%), the surrogate is switched off from then on. The
+default check interval, 3 blocks, is the one measured to keep a 25-block
+run within 2% of the plain LBM's own trajectory on held-out scenes; each
+block's error is far smaller (about 0.3%), but chained blocks drift.
 """
 from __future__ import annotations
 
@@ -190,7 +193,7 @@ class SurrogateLBM:
     launches eagerly, which chains every kernel to the previous one by
     programmatic dependent launch, across blocks too."""
 
-    def __init__(self, N, tau=0.55, u_inlet=(U_REF, 0.0, 0.0), check_every=10, tol=0.02,
+    def __init__(self, N, tau=0.55, u_inlet=(U_REF, 0.0, 0.0), check_every=3, tol=0.02,
                  params=None, device="cuda", use_graph=False, correct=False,
                  inlet_features=False, persistence=False):
         self.N = N

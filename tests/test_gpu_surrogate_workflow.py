@@ -63,10 +63,10 @@ def test_check_switches_to_plain_lbm_and_stays_exact():
 def test_run_with_checks_uses_the_surrogate():
     m, f0, solid = held_out_scene()
     f = f0.clone()
-    used = m.advance(f, solid, 12)  # checks at blocks 0 and 10
+    used = m.advance(f, solid, 12)  # checks at blocks 0, 3, 6 and 9
     assert not m.fallback
-    assert used == 10
-    assert len(m.errors) == 2 and max(m.errors) <= 0.02, m.errors
+    assert used == 8
+    assert len(m.errors) == 4 and max(m.errors) <= 0.02, m.errors
     assert torch.isfinite(f).all()
     m.close()
 
@@ -102,7 +102,7 @@ def test_window_with_checks_holds_2_percent_and_beats_persistence():
     m, f0, solid = held_out_scene()
     ref = f0.clone()
     m.lbm.step(ref, solid, 25 * S.BLOCK)
-    m.check_every = 3
+    assert m.check_every == 3  # the default
     res = {}
     for pers in (False, True):
         m.persistence = pers

@@ -212,6 +212,62 @@ def test_p2g_brute_force_over_all_nodes(material):
     assert np.allclose(gp, bp, rtol=1e-11, atol=1e-14)
 
 
+def test_grid_update_stage_against_the_formula():
+    """The grid-update stage (mpm_grid_update) on every node of a 12^3 grid:
+    v_i = p_i / m_i + dt (g + a_w(x_i, t)) where m_i > 0 outside the sticky
+    band, else 0, with the wind sampled by the (separately pinned) sampler."""
+    params, _ = small_scene(N=12)
+    N, dt, band = params["n_grid"], params["dt"], params["bc_band"]
+    rng = np.random.default_rng(21)
+    gm = np.where(rng.random(N ** 3) < 0.6, rng.uniform(0.1, 2.0, N ** 3), 0.0)
+    gp = rng.standard_normal((3, N ** 3))
+    wind = (inputs.fourier_wind(4, 3, seed=2), 4, 3, 0.05)
+    t = 0.017
+    gv = oracle.mpm_grid_update(params, gm, gp, wind, t)
+    idx = np.arange(N)
+    K, J, I = np.meshgrid(idx, idx, idx, indexing="ij")
+    ijk = np.stack([I.ravel(), J.ravel(), K.ravel()])
+    a = oracle.wind_sample(*wind, ijk / N, t)
+    inner = np.all((ijk >= band) & (ijk <= N - 1 - band), axis=0)
+    live = inner & (gm > 0)
+    ref = np.zeros((3, N ** 3))
+    g = np.asarray(params["gravity"])[:, None]
+    ref[:, live] = gp[:, live] / gm[live] + dt * (g + a[:, live])
+    assert live.sum() > 50 and (~live & (gm > 0)).sum() > 50
+    assert np.allclose(gv, ref, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_g2p_stage_brute_force_over_all_nodes(pinned):
+    """The G2P stage (mpm_g2p) against Eqs. G2P and deformation_update summed
+    over every node of an 8^3 grid with the kernel N((x_i - x_p)/dx):
+    v_p = sum w v_i, C_p = (4/dx^2) sum w v_i (x_i - x_p)^T, x_p + dt v_p,
+    (I + dt C_p) F_p; a pinned particle keeps v = C = 0."""
+    params, (x, _, _, F) = small_scene(n=5, N=8, seed=9)
+    N, dt = params["n_grid"], params["dt"]
+    dx = 1.0 / N
+    gv = np.random.default_rng(3).standard_normal((3, N ** 3))
+    pin = np.zeros(x.shape[1], np.uint8)
+    if pinned:
+        pin[[1, 3]] = 1
+    xo, vo, Co, Fo = oracle.mpm_g2p(params, x, F, gv, pin)
+    idx = np.arange(N)
+    K, J, I = np.meshgrid(idx, idx, idx, indexing="ij")
+    xi = np.stack([I.ravel(), J.ravel(), K.ravel()]) * dx
+    for p in range(x.shape[1]):
+        d = xi - x[:, p:p + 1]
+        W = bspline(d[0] / dx) * bspline(d[1] / dx) * bspline(d[2] / dx)
+        v = (W * gv).sum(axis=1)
+        Cm = 4.0 / dx ** 2 * (W * gv) @ d.T
+        if pin[p]:
+            v, Cm = np.zeros(3), np.zeros((3, 3))
+        assert np.allclose(vo[:, p], v, rtol=1e-12, atol=1e-14)
+        assert np.allclose(Co[:, p], Cm.ravel(), rtol=1e-11, atol=1e-12)
+        assert np.allclose(xo[:, p], x[:, p] + dt * v, rtol=1e-14, atol=1e-15)
+        Fn = (np.eye(3) + dt * Cm) @ F[:, p].reshape(3, 3)
+        assert np.allclose(Fo[:, p], Fn.ravel(), rtol=1e-13, atol=1e-14)
+
+
 # ---------------------------------------------------------------- substep --
 
 @pytest.mark.parametrize("material", [0, 1])
