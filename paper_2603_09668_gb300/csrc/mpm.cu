@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
     const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
     const float *__restrict__ gxo, const float *__restrict__ gvo, const float *__restrict__ gCo,
     const float *__restrict__ gFo, float4 *__restrict__ grid_bv, float *__restrict__ scratch,
-    int64_t n, int64_t cap) {
+    int64_t n, int64_t cap, const float *__restrict__ Cout) {
     __shared__ float4 rows[P2G_WARP_THREADS / 32][32][P2G_ROW];
     __shared__ int keys[P2G_WARP_THREADS / 32][32];
     pdl_wait();
@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS) k_rev_g2p(
             bCo[k] = gCo[k * n + p];
             bFo[k] = gFo[k * n + p];
         }
-        rev_g2p_particle(P, xp, Fp, pinned && pinned[p], grid_v, bxo, bvo, bCo, bFo, q, bx, bFin);
+        rev_g2p_particle(P, xp, Fp, pinned && pinned[p], grid_v, bxo, bvo, bCo, bFo, q, bx, bFin,
+                         Cout, n, p);
 #pragma unroll
         for (int a = 0; a < 3; ++a) scratch[a * cap + p] = bx[a];
 #pragma unroll
@@ -504,10 +505,12 @@ extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_
     return DW_OK;
 }
 
-extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
-                                         const dw_mpm_state *g_out, const dw_mpm_state *g_in,
-                                         const uint8_t *pinned, const dw_wind_field *wind,
-                                         float t, float *g_wind, float *g_E, dw_stream stream) {
+// The reverse substep; Cout (or NULL): C of the substep's output state, when
+// the caller kept it (a segment's recomputed states).
+static dw_status substep_adjoint(dw_mpm h, const dw_mpm_state *in, const float *Cout,
+                                 const dw_mpm_state *g_out, const dw_mpm_state *g_in,
+                                 const uint8_t *pinned, const dw_wind_field *wind, float t,
+                                 float *g_wind, float *g_E, dw_stream stream) {
     DW_REQUIRE(h, "handle is NULL");
     dw_status st = check_state(h, in, "input");
     if (st != DW_OK) return st;
@@ -534,7 +537,7 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
         ProfScope ps(h, DW_K_REV_G2P, s);
         DW_CUDA(launch_pdl(k_rev_g2p, grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, s, h->P,
                            in->x, in->F, pinned, h->grid_v, g_out->x, g_out->v, g_out->C,
-                           g_out->F, h->grid_bv, h->pscratch, n, cap));
+                           g_out->F, h->grid_bv, h->pscratch, n, cap, Cout));
     }
     {
         ProfScope ps(h, DW_K_REV_GRID, s);
@@ -548,6 +551,13 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
                            cap, h->block_count));
     }
     return DW_OK;
+}
+
+extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
+                                         const dw_mpm_state *g_out, const dw_mpm_state *g_in,
+                                         const uint8_t *pinned, const dw_wind_field *wind,
+                                         float t, float *g_wind, float *g_E, dw_stream stream) {
+    return substep_adjoint(h, in, nullptr, g_out, g_in, pinned, wind, t, g_wind, g_E, stream);
 }
 
 extern "C" dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, float *tape,
@@ -586,8 +596,10 @@ extern "C" dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, fl
     }
     for (int j = n_substeps - 1; j >= 0; --j) {
         const dw_mpm_state in = j == 0 ? *start : slot(j);
-        st = mpm_substep_adjoint(h, &in, g, g, pinned, wind, fmaf((float)j, dt, t0), g_wind, g_E,
-                                 stream);
+        // the output state j + 1 is in the tape for every substep but the last
+        const float *Cout = j + 1 < n_substeps ? slot(j + 1).C : nullptr;
+        st = substep_adjoint(h, &in, Cout, g, g, pinned, wind, fmaf((float)j, dt, t0), g_wind,
+                             g_E, stream);
         if (st != DW_OK) return st;
     }
     return DW_OK;

@@ -29,13 +29,17 @@ __device__ __forceinline__ void weight_grad(const MpmParams &P, const Stencil &s
 // W_ip (bv_p + D bC_p (x_i - x_p)), i.e. a P2G value with m v -> bv and
 // A -> D bC, to be scattered with the mass channel off), bx = partial dL/dx_p
 // and bFin = dL/dF_p through the F update. A particle outside the domain
-// gets bx = bFin = 0 and q.valid = false.
+// gets bx = bFin = 0 and q.valid = false. Cout (or NULL): the C array of the
+// substep's output state (row stride `stride`, particle p), when a recompute
+// kept it; then C' is read instead of gathered again from the grid.
 __device__ __forceinline__ void rev_g2p_particle(const MpmParams &P, const float xp[3],
                                                  const float Fp[9], bool pin,
                                                  const float4 *__restrict__ grid_v,
                                                  const float bxo[3], const float bvo[3],
                                                  const float bCo[9], const float bFo[9],
-                                                 P2GParticle &q, float bx[3], float bFin[9]) {
+                                                 P2GParticle &q, float bx[3], float bFin[9],
+                                                 const float *__restrict__ Cout = nullptr,
+                                                 int64_t stride = 0, int64_t p = 0) {
     q.valid = false;
     Stencil s;
     if (!make_stencil(P, xp[0], xp[1], xp[2], s)) {
@@ -46,9 +50,13 @@ __device__ __forceinline__ void rev_g2p_particle(const MpmParams &P, const float
         return;
     }
     const int N = P.N;
-    // recompute C' (v' is not needed: its adjoint only uses the weights)
+    // C' of the output state (v' is not needed: its adjoint only uses the
+    // weights): kept by the recompute, else gathered from the grid again
     float Cn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (!pin) {
+    if (Cout && !pin) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Cn[k] = Cout[k * stride + p];
+    } else if (!pin) {
 #pragma unroll
         for (int oi = 0; oi < 3; ++oi)
 #pragma unroll

@@ -331,6 +331,7 @@ struct BatchAdjView {
     float *gx, *gv, *gC, *gF; // dL/d(output state) in, dL/d(input state) out
     float *g_wind;            // concatenated per-scene wind gradients, or NULL
     float *g_E;               // [n_scenes], or NULL
+    const float *Cout;        // C of the reverse substep's output state (kept in the tape), or NULL
 };
 
 // Grid update of list L at substep k keeping (m, p) and the list (the
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(BATCH_ITEM) k_batch_rev_g2p(BatchView A, Batch
             bFo[c] = R.gF[c * n + p];
         }
         rev_g2p_particle(P, xp, Fp, A.pinned && A.pinned[p], S.grid_v, bxo, bvo, bCo, bFo, q, bx,
-                         bFin);
+                         bFin, R.Cout, n, p);
 #pragma unroll
         for (int a = 0; a < 3; ++a) R.scratch[a * n + p] = bx[a];
 #pragma unroll
@@ -1144,6 +1145,7 @@ static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *sta
     R.gF = g->F;
     R.g_wind = g_wind;
     R.g_E = g_E;
+    R.Cout = nullptr;
     const unsigned ggrid = (unsigned)(8 * h->num_sms);
     for (int j = n_substeps - 1; j >= 0; --j) {
         const dw_mpm_state in = j == 0 ? *start : slot(j);
@@ -1152,6 +1154,8 @@ static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *sta
         DW_LAUNCHED("k_batch_p2g");
         k_batch_grid_keep<<<ggrid, 256, 0, s>>>(A, j, 0);
         DW_LAUNCHED("k_batch_grid_keep");
+        // C of the output state j + 1, in the tape for every substep but the last
+        R.Cout = j + 1 < n_substeps ? slot(j + 1).C : nullptr;
         k_batch_rev_g2p<<<h->n_items, BATCH_ITEM, 0, s>>>(A, R);
         DW_LAUNCHED("k_batch_rev_g2p");
         k_batch_rev_grid<<<ggrid, 256, 0, s>>>(A, R, j, 0);
