@@ -53,7 +53,8 @@ typedef enum {
     DW_ERR_NONFINITE = 4, /* device: a NaN or Inf was produced or read */
     DW_ERR_DOMAIN = 5,    /* device: a particle's 3x3x3 stencil left the grid */
     DW_ERR_TIMEOUT = 6,   /* device: a bounded wait gave up */
-    DW_ERR_INVERTED = 7   /* device: det F <= 0 where the constitutive model needs J > 0 */
+    DW_ERR_INVERTED = 7,  /* device: det F <= 0 where the constitutive model needs J > 0 */
+    DW_ERR_IO = 8         /* host file: cannot be opened, read or written, or not the expected format */
 } dw_status;
 
 typedef void *dw_stream; /* cudaStream_t */
@@ -231,6 +232,33 @@ enum { DW_K_P2G = 0, DW_K_GRID = 1, DW_K_G2P = 2, DW_K_REV_G2P = 3, DW_K_REV_GRI
        DW_K_REV_P2G = 5, DW_K_SORT = 6, DW_K_G2P2G = 7, DW_K_COUNT = 8 };
 DW_API dw_status mpm_profile_enable(dw_mpm h, int32_t max_records);
 DW_API dw_status mpm_profile_read(dw_mpm h, double *total_ms, int64_t *launches);
+
+/* Host checkpoints of an MPM state, so that a rollout or an inversion can be
+ * resumed in another process from saved particles, time and substep counter
+ * (the checkpoints inside a rollout's adjoint stay in device memory).
+ * mpm_state_save copies `state` (device x, v, C, F of state->n particles)
+ * and, when not NULL, `pinned` (device uint8[n]) and `ids` (device int32[n])
+ * to the host on `stream`, waits for them, and writes the file `path`:
+ * the 8-byte tag "DWMPMST1", int64 n, float64 t, int64 substep, int32 flags
+ * (bit 0 pinned present, bit 1 ids present), int32 0, then the float32 rows
+ * x[3][n], v[3][n], C[9][n], F[9][n], then pinned and ids when present, in
+ * the host's byte order (little-endian on both supported hosts). The file is
+ * written to path + ".tmp" and renamed over `path` when complete, so an
+ * interrupted save keeps the previous checkpoint. mpm_state_peek reads only
+ * the header (n, flags, t, substep; each output may be NULL; no GPU needed),
+ * to size the buffers of a load. mpm_state_load reads the file into `state`
+ * (state->n must equal the file's n: DW_ERR_ARG otherwise) and, when not
+ * NULL, pinned and ids (DW_ERR_ARG if the file lacks them), and returns t and
+ * substep (may be NULL); it waits for its copies on `stream`. Errors: DW_ERR_IO
+ * for a file that cannot be opened, read or written, a wrong tag or header,
+ * or a size that does not match the header; DW_ERR_OOM when the host buffer
+ * cannot be allocated; DW_ERR_CUDA for a failed copy. */
+DW_API dw_status mpm_state_save(const char *path, const dw_mpm_state *state, const uint8_t *pinned,
+                                const int32_t *ids, double t, int64_t substep, dw_stream stream);
+DW_API dw_status mpm_state_peek(const char *path, int64_t *n, int32_t *flags, double *t,
+                                int64_t *substep);
+DW_API dw_status mpm_state_load(const char *path, const dw_mpm_state *state, uint8_t *pinned,
+                                int32_t *ids, double *t, int64_t *substep, dw_stream stream);
 
 /* The same substep as mpm_substep for callers that cannot allocate device
  * memory when they need it (for example code running inside an allocator

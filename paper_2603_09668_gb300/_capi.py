@@ -84,6 +84,9 @@ SIGNATURES = {
     "mpm_profile_read": (I32, [VP, P(ct.c_double), P(I64)]),
     "mpm_substep_noalloc": (I32, [P(DwMpmDesc), P(DwMpmState), P(DwMpmState), VP,
                                   P(DwWindField), F32, VP, VP]),
+    "mpm_state_save": (I32, [ct.c_char_p, P(DwMpmState), VP, VP, ct.c_double, I64, VP]),
+    "mpm_state_peek": (I32, [ct.c_char_p, P(I64), P(I32), P(ct.c_double), P(I64)]),
+    "mpm_state_load": (I32, [ct.c_char_p, P(DwMpmState), VP, VP, P(ct.c_double), P(I64), VP]),
     "mpm_batch_create": (I32, [P(DwMpmScene), I32, P(VP)]),
     "mpm_batch_destroy": (I32, [VP]),
     "mpm_batch_layout": (I32, [VP, P(I64), P(I64)]),
@@ -151,7 +154,7 @@ SIGNATURES = {
 }
 
 STATUS = {0: "DW_OK", 1: "DW_ERR_ARG", 2: "DW_ERR_CUDA", 3: "DW_ERR_OOM", 4: "DW_ERR_NONFINITE",
-          5: "DW_ERR_DOMAIN", 6: "DW_ERR_TIMEOUT", 7: "DW_ERR_INVERTED"}
+          5: "DW_ERR_DOMAIN", 6: "DW_ERR_TIMEOUT", 7: "DW_ERR_INVERTED", 8: "DW_ERR_IO"}
 
 _lock = threading.Lock()
 _lib = None

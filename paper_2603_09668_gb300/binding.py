@@ -10,6 +10,7 @@ Layouts follow include/diffwind.h: particle state x, v as [3, n], C, F as
 from __future__ import annotations
 
 import ctypes as ct
+import os
 from typing import NamedTuple, Optional
 
 import numpy as np
@@ -224,6 +225,33 @@ def mpm_substep_noalloc(desc_params: dict, state_in: MpmState, state_out: MpmSta
                                     _dev(device_status, torch.int32, "device_status"),
                                     _stream(stream)))
     return state_out
+
+
+def mpm_state_save(path, state: MpmState, pinned=None, ids=None, t=0.0, substep=0, stream=None):
+    """Host checkpoint of a state (and pinned, ids when given) to `path`."""
+    a = state.to_c()
+    check(lib().mpm_state_save(os.fsencode(path), ct.byref(a), _pin(pinned),
+                               _dev(ids, torch.int32, "ids"), float(t), int(substep),
+                               _stream(stream)))
+
+
+def mpm_state_peek(path):
+    """Header of a checkpoint: dict(n, has_pinned, has_ids, t, substep)."""
+    n, flags, t, k = ct.c_int64(), ct.c_int32(), ct.c_double(), ct.c_int64()
+    check(lib().mpm_state_peek(os.fsencode(path), ct.byref(n), ct.byref(flags), ct.byref(t),
+                               ct.byref(k)))
+    return dict(n=n.value, has_pinned=bool(flags.value & 1), has_ids=bool(flags.value & 2),
+                t=t.value, substep=k.value)
+
+
+def mpm_state_load(path, state: MpmState, pinned=None, ids=None, stream=None):
+    """Reads a checkpoint into `state` (and pinned, ids); returns (t, substep)."""
+    a = state.to_c()
+    t, k = ct.c_double(), ct.c_int64()
+    check(lib().mpm_state_load(os.fsencode(path), ct.byref(a), _pin(pinned),
+                               _dev(ids, torch.int32, "ids"), ct.byref(t), ct.byref(k),
+                               _stream(stream)))
+    return t.value, k.value
 
 
 KERNEL_NAMES = ["p2g", "grid", "g2p", "rev_g2p", "rev_grid", "rev_p2g", "sort", "g2p2g"]

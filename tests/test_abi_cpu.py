@@ -118,3 +118,43 @@ def test_every_declared_entry_point_has_a_ctypes_signature():
     src = open(os.path.join(ROOT, "paper_2603_09668_gb300", "_capi.py")).read()
     missing = [n for n in declared_functions() if f'"{n}"' not in src]
     assert not missing, missing
+
+
+def _write_state_file(path, n, t, substep, flags, rows=None, extra=b""):
+    """A checkpoint in the format include/diffwind.h documents for
+    mpm_state_save, written here with numpy (the header reader is host
+    code and needs no GPU)."""
+    import numpy as np
+
+    with open(path, "wb") as f:
+        f.write(b"DWMPMST1")
+        f.write(np.array([n], "<i8").tobytes() + np.array([t], "<f8").tobytes())
+        f.write(np.array([substep], "<i8").tobytes() + np.array([flags, 0], "<i4").tobytes())
+        rows = np.zeros((24, n), "<f4") if rows is None else rows
+        f.write(rows.tobytes())
+        if flags & 1:
+            f.write(np.zeros(n, np.uint8).tobytes())
+        if flags & 2:
+            f.write(np.arange(n, dtype="<i4").tobytes())
+        f.write(extra)
+
+
+def test_state_checkpoint_header_is_read_without_a_gpu(tmp_path, libpath):
+    from paper_2603_09668_gb300 import binding as B
+
+    p = tmp_path / "s.dwst"
+    _write_state_file(p, 7, 0.125, 2500, 3)
+    assert B.mpm_state_peek(str(p)) == dict(n=7, has_pinned=True, has_ids=True, t=0.125,
+                                            substep=2500)
+    _write_state_file(p, 5, 1.5, 3, 0)
+    h = B.mpm_state_peek(str(p))
+    assert (h["n"], h["has_pinned"], h["has_ids"], h["substep"]) == (5, False, False, 3)
+    bad = tmp_path / "bad.dwst"
+    bad.write_bytes(b"NOTSTATE" + bytes(32))
+    with pytest.raises(B.DiffWindError, match="DW_ERR_IO"):
+        B.mpm_state_peek(str(bad))
+    bad.write_bytes(b"DWMPM")  # short header
+    with pytest.raises(B.DiffWindError, match="DW_ERR_IO"):
+        B.mpm_state_peek(str(bad))
+    with pytest.raises(B.DiffWindError, match="DW_ERR_IO"):
+        B.mpm_state_peek(str(tmp_path / "missing.dwst"))
