@@ -29,12 +29,16 @@
 // scene inside its own particle range.
 //
 // Reverse mode (checkpointed segments): the states inside a segment are
-// recomputed one substep at a time into a caller-owned tape; each reverse
-// substep then runs over all scenes at once as five launches: P2G and the
-// grid update of the substep's input (the grid kept for the reverse pass),
-// reverse G2P (scatter of dL/dv_i into each scene's adjoint grid), reverse
-// grid update (dL/dm_i, dL/dp_i, the scene's wind gradient) and reverse P2G
-// (gather to the particles, per-scene dL/dE).
+// recomputed one substep at a time into a caller-owned tape, and the grid
+// phase of each recomputed substep keeps its active list and the listed
+// nodes' (m, p) in a handle-owned grid tape (when device memory allows).
+// Each reverse substep then runs over all scenes at once: the forward grid
+// of the substep restored from the grid tape with its grid update (or, for
+// the segment's last substep and without a grid tape, a P2G of the
+// substep's input and the grid update), reverse G2P (scatter of dL/dv_i into
+// each scene's adjoint grid), reverse grid update (dL/dm_i, dL/dp_i, the
+// scene's wind gradient) and reverse P2G (gather to the particles, per-scene
+// dL/dE).
 #include <math.h>
 
 #include <algorithm>
@@ -80,6 +84,12 @@ struct BatchView {
     int *err;
     unsigned *bar;      // grid barrier: arrivals, generation
     const float *t0;    // time of substep 0 (device, set before each rollout)
+    // when set (the recompute of a reverse segment), the grid phase also
+    // keeps the consumed list and each listed node's (m, p) in a grid tape
+    // slot: entry e's nodes at gtape[64 e + t], the list at gtape_list
+    float4 *gtape;
+    int *gtape_list;
+    int *gtape_count;
 };
 
 __global__ void k_batch_set_time(float *t0, float value) { *t0 = value; }
@@ -127,14 +137,17 @@ __device__ __forceinline__ void batch_grid_phase(const BatchView &A, int k, int 
     const int *list = A.list + (size_t)L * A.list_cap;
     const float t0 = *A.t0;
     const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    if (A.gtape && blockIdx.x == 0 && threadIdx.x == 0) *A.gtape_count = count;
     for (int e = blockIdx.x * SUBS + sub; e < count; e += gridDim.x * SUBS) {
         const int ent = list[e];
         const BatchScene &S = A.scenes[ent >> BATCH_SCENE_SHIFT];
         const int b = ent & ((1 << BATCH_SCENE_SHIFT) - 1);
         const MpmParams P = S.P;
+        if (A.gtape && lt == 0) A.gtape_list[e] = ent;
         int i, j, kk;
         if (active_node(P, S.nb, b, lt, i, j, kk)) {
             const int64_t node = ((int64_t)kk * P.N + j) * P.N + i;
+            if (A.gtape) A.gtape[(size_t)e * 64 + lt] = S.grid_mp[node];
             grid_node_update(P, S.wind, fmaf((float)k, P.dt, t0), node, i, j, kk, S.grid_mp,
                              S.grid_v, CLEAR ? 1 : 0);
         }
@@ -340,6 +353,35 @@ __global__ void __launch_bounds__(256) k_batch_grid_keep(BatchView A, int k, int
     batch_grid_phase<256, false>(A, k, L);
 }
 
+// The recomputed forward grid of reverse substep k from the grid tape: list
+// 0 and its count, each listed node's (m, p) written back into the scene's
+// grid and its grid update (grid kept), in place of a P2G of the substep's
+// input and k_batch_grid_keep.
+__global__ void __launch_bounds__(256) k_batch_grid_restore(BatchView A, int k,
+                                                            const float4 *__restrict__ gtape,
+                                                            const int *__restrict__ gtape_list,
+                                                            const int *__restrict__ gtape_count) {
+    constexpr int SUBS = 256 / 64;
+    const int count = *gtape_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.count[0] = count;
+    const float t0 = *A.t0;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * SUBS + sub; e < count; e += gridDim.x * SUBS) {
+        const int ent = gtape_list[e];
+        if (lt == 0) A.list[e] = ent;
+        const BatchScene &S = A.scenes[ent >> BATCH_SCENE_SHIFT];
+        const int b = ent & ((1 << BATCH_SCENE_SHIFT) - 1);
+        const MpmParams P = S.P;
+        int i, j, kk;
+        if (active_node(P, S.nb, b, lt, i, j, kk)) {
+            const int64_t node = ((int64_t)kk * P.N + j) * P.N + i;
+            S.grid_mp[node] = gtape[(size_t)e * 64 + lt];
+            grid_node_update(P, S.wind, fmaf((float)k, P.dt, t0), node, i, j, kk, S.grid_mp,
+                             S.grid_v, 0);
+        }
+    }
+}
+
 // Reverse G2P of one work item per CTA: scatter into the scene's grid_bv.
 __global__ void __launch_bounds__(BATCH_ITEM) k_batch_rev_g2p(BatchView A, BatchAdjView R) {
     __shared__ float4 rows[BATCH_ITEM / 32][32][P2G_ROW];
@@ -519,6 +561,12 @@ struct dw_mpm_batch_s {
     int64_t *d_node_off = nullptr, *d_wind_off = nullptr;
     float4 *grid_bv = nullptr, *grid_bmp = nullptr;
     float *adj_scratch = nullptr;
+    // grid tape of the segment recompute: gtape_slots substeps of list_cap
+    // entries (64 nodes' (m, p) each), their lists and counts
+    float4 *gtape = nullptr;
+    int *gtape_list = nullptr, *gtape_count = nullptr;
+    int gtape_slots = 0;
+    int gtape_refused = 0;  // slots a failed or oversized allocation was refused for
     cudaGraphExec_t adj_exec = nullptr;  // captured segment adjoint
     dw::AdjKey adj_key = {};
     bool adj_graph_broken = false;
@@ -559,6 +607,9 @@ static BatchView view_of(dw_mpm_batch h, const dw_mpm_state &s, const uint8_t *p
     A.err = h->err;
     A.bar = h->bar;
     A.t0 = h->t0;
+    A.gtape = nullptr;
+    A.gtape_list = nullptr;
+    A.gtape_count = nullptr;
     return A;
 }
 
@@ -877,6 +928,9 @@ extern "C" dw_status mpm_batch_destroy(dw_mpm_batch h) {
     cudaFree(h->d_wind_off);
     cudaFree(h->grid_bv);
     cudaFree(h->grid_bmp);
+    cudaFree(h->gtape);
+    cudaFree(h->gtape_list);
+    cudaFree(h->gtape_count);
     cudaFree(h->adj_scratch);
     delete h;
     return DW_OK;
@@ -1096,6 +1150,51 @@ static dw_status ensure_adjoint(dw_mpm_batch h) {
     return DW_OK;
 }
 
+// The grid tape for `slots` recompute substeps, grown on demand. It holds
+// every block of every scene per slot (list_cap x 1 KB), so it is taken only
+// while it leaves 8 GB of device memory free; without it the reverse pass
+// recomputes each substep's grid by a P2G of its input (same results up to
+// the float atomics' order). Returns whether the tape is there.
+static bool ensure_grid_tape(dw_mpm_batch h, int slots) {
+    if (slots <= 0) return false;
+    if (slots <= h->gtape_slots) return true;
+    if (h->gtape_refused && slots >= h->gtape_refused) return false;
+    const size_t per = (size_t)h->list_cap * 64 * sizeof(float4) + (size_t)h->list_cap * sizeof(int);
+    const size_t bytes = per * (size_t)slots + sizeof(int) * (size_t)slots;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || bytes + (8ull << 30) > free_b) {
+        cudaGetLastError();
+        h->gtape_refused = slots;
+        return false;
+    }
+    cudaFree(h->gtape);
+    cudaFree(h->gtape_list);
+    cudaFree(h->gtape_count);
+    h->gtape = nullptr;
+    h->gtape_list = h->gtape_count = nullptr;
+    h->gtape_slots = 0;
+    if (h->adj_exec) {  // a captured graph holds the old tape's addresses
+        cudaGraphExecDestroy(h->adj_exec);
+        h->adj_exec = nullptr;
+    }
+    cudaError_t e = cudaMalloc((void **)&h->gtape, (size_t)h->list_cap * 64 * sizeof(float4) * (size_t)slots);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&h->gtape_list, (size_t)h->list_cap * sizeof(int) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->gtape_count, sizeof(int) * (size_t)slots);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->gtape);
+        cudaFree(h->gtape_list);
+        cudaFree(h->gtape_count);
+        h->gtape = nullptr;
+        h->gtape_list = h->gtape_count = nullptr;
+        h->gtape_refused = slots;
+        return false;
+    }
+    h->gtape_slots = slots;
+    return true;
+}
+
 }  // namespace dw
 
 namespace dw {
@@ -1109,6 +1208,7 @@ static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *sta
                                          cudaStream_t s) {
     const int64_t n = h->n_total;
     dw_status st = DW_OK;
+    const bool gt = h->gtape_slots >= n_substeps - 1 && n_substeps > 1;
     auto slot = [&](int k) {  // state k (1 .. n_substeps - 1) in the tape
         return state_view(tape + (size_t)(k - 1) * 24 * (size_t)n, n);
     };
@@ -1127,6 +1227,11 @@ static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *sta
             A.ov = o.v;
             A.oC = o.C;
             A.oF = o.F;
+            if (gt) {  // the grid phase of substep k keeps its grid in tape slot k
+                A.gtape = h->gtape + (size_t)k * h->list_cap * 64;
+                A.gtape_list = h->gtape_list + (size_t)k * h->list_cap;
+                A.gtape_count = h->gtape_count + k;
+            }
             const bool final_ = k + 2 == n_substeps;
             st = launch_substep(h, A, h->cfg, k, L, final_, s);
             if (st != DW_OK) return st;
@@ -1150,10 +1255,17 @@ static dw_status enqueue_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *sta
     for (int j = n_substeps - 1; j >= 0; --j) {
         const dw_mpm_state in = j == 0 ? *start : slot(j);
         const BatchView A = view_of(h, in, pinned);
-        k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, 0);
-        DW_LAUNCHED("k_batch_p2g");
-        k_batch_grid_keep<<<ggrid, 256, 0, s>>>(A, j, 0);
-        DW_LAUNCHED("k_batch_grid_keep");
+        if (gt && j + 1 < n_substeps) {  // the recompute kept substep j's grid
+            k_batch_grid_restore<<<ggrid, 256, 0, s>>>(A, j, h->gtape + (size_t)j * h->list_cap * 64,
+                                                      h->gtape_list + (size_t)j * h->list_cap,
+                                                      h->gtape_count + j);
+            DW_LAUNCHED("k_batch_grid_restore");
+        } else {
+            k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, 0);
+            DW_LAUNCHED("k_batch_p2g");
+            k_batch_grid_keep<<<ggrid, 256, 0, s>>>(A, j, 0);
+            DW_LAUNCHED("k_batch_grid_keep");
+        }
         // C of the output state j + 1, in the tape for every substep but the last
         R.Cout = j + 1 < n_substeps ? slot(j + 1).C : nullptr;
         k_batch_rev_g2p<<<h->n_items, BATCH_ITEM, 0, s>>>(A, R);
@@ -1215,6 +1327,7 @@ extern "C" dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_stat
                (long long)tape_floats, n_substeps, (long long)n, (long long)need);
     st = ensure_adjoint(h);
     if (st != DW_OK) return st;
+    ensure_grid_tape(h, n_substeps - 1);
     cudaStream_t s = as_stream(stream);
     k_batch_set_time<<<1, 1, 0, s>>>(h->t0, t0);
     DW_LAUNCHED("k_batch_set_time");
