@@ -183,7 +183,14 @@ DW_API dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in, const dw_
  * mpm_substep_adjoint from the last substep back to the first at times
  * t0 + j dt. g holds dL/d(state after the segment) on entry and is
  * overwritten with dL/d(start); g_wind and g_E accumulate as in
- * mpm_substep_adjoint. The substeps are those of mpm_substep (no sorting). */
+ * mpm_substep_adjoint. The substeps are those of mpm_substep (no sorting).
+ * The recompute also keeps each substep's grid (the active blocks' mass and
+ * momentum) in a handle-owned grid tape, which the reverse substeps restore
+ * instead of repeating the P2G of their input; the tape grows on the first
+ * call with a longer segment (device allocation: make that call outside a
+ * stream capture) and is used only while it leaves 8 GB of device memory
+ * free, otherwise the grids are recomputed (results agree to the float
+ * atomics' order). */
 DW_API dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, float *tape,
                                      int64_t tape_floats, const dw_mpm_state *g,
                                      const uint8_t *pinned, const dw_wind_field *wind, float t0,
@@ -535,8 +542,13 @@ DW_API dw_status mpm_batch_wind_layout(dw_mpm_batch h, int64_t *n_floats, int64_
  * of scene s at t0 + j dt_s) into `tape` (device float, (n_substeps - 1) *
  * 24 * n floats, each state as x, v, C, F back to back; caller-owned,
  * tape_floats its size) with the handle's launch configuration, then runs
- * the reverse substeps from the last to the first, each as five launches over
- * all scenes. With use_graph the whole sequence is captured once per distinct
+ * the reverse substeps from the last to the first over all scenes. The
+ * recompute keeps each substep's grid in a handle-owned grid tape (every
+ * block of every scene per recomputed substep: 1 KB x the batch's blocks,
+ * grown on the first call with a longer segment and used only while it
+ * leaves 8 GB of device memory free), from which the reverse substeps
+ * restore their forward grids; without it they recompute them by a P2G of
+ * their input (results agree to the float atomics' order). With use_graph the whole sequence is captured once per distinct
  * (tape, g, pinned, g_wind, g_E, n_substeps, configuration) in a CUDA graph
  * owned by the handle and replayed; `start` is first copied into the handle's
  * workspace, so successive segments with different start states share one
@@ -548,7 +560,7 @@ DW_API dw_status mpm_batch_wind_layout(dw_mpm_batch h, int64_t *n_floats, int64_
  * float[n_scenes], or NULL) accumulates each scene's dL/dE. The substeps are
  * those of mpm_batch_rollout without sorting. The first call allocates the
  * reverse-mode workspace (two float4 per grid node of all scenes, 12 floats
- * per particle), kept until mpm_batch_destroy. Errors: DW_ERR_ARG (state
+ * per particle) and the grid tape, kept until mpm_batch_destroy. Errors: DW_ERR_ARG (state
  * sizes, a missing or short tape), DW_ERR_OOM, DW_ERR_CUDA; device-side
  * failures go to the batch's device status. */
 DW_API dw_status mpm_batch_segment_adjoint(dw_mpm_batch h, const dw_mpm_state *start,

@@ -51,6 +51,55 @@ __global__ void __launch_bounds__(GRID_THREADS) k_grid_update_active(
     }
 }
 
+// The grid update (clear on) of a segment adjoint's recompute, which also
+// keeps the consumed list and each listed node's (m, p) in a grid tape slot
+// (entry e's nodes at gtape[64 e + t]).
+__global__ void __launch_bounds__(GRID_THREADS) k_grid_update_tape(
+    MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_v,
+    ActiveBlocks ab, float4 *__restrict__ gtape, int *__restrict__ gtape_list,
+    int *__restrict__ gtape_count) {
+    pdl_wait();
+    pdl_trigger();
+    const int count = *ab.count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *gtape_count = count;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
+        const int b = ab.list[e];
+        if (lt == 0) gtape_list[e] = b;
+        int i, j, k;
+        if (active_node(P, ab.nb, b, lt, i, j, k)) {
+            const int64_t node = ((int64_t)k * P.N + j) * P.N + i;
+            gtape[(size_t)e * 64 + lt] = grid_mp[node];
+            grid_node_update(P, wind, t, node, i, j, k, grid_mp, grid_v, 1);
+        }
+        if (lt == 0) ab.flags[b] = 0;
+    }
+}
+
+// A reverse substep's forward grid from a grid tape slot: the list and its
+// count, the listed nodes' (m, p) written back and their grid update (grid
+// kept), in place of a P2G of the substep's input and the grid update.
+__global__ void __launch_bounds__(GRID_THREADS) k_grid_restore(
+    MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp, float4 *__restrict__ grid_v,
+    ActiveBlocks ab, const float4 *__restrict__ gtape, const int *__restrict__ gtape_list,
+    const int *__restrict__ gtape_count) {
+    pdl_wait();
+    pdl_trigger();
+    const int count = *gtape_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ab.count = count;
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
+    for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
+        const int b = gtape_list[e];
+        if (lt == 0) ab.list[e] = b;
+        int i, j, k;
+        if (active_node(P, ab.nb, b, lt, i, j, k)) {
+            const int64_t node = ((int64_t)k * P.N + j) * P.N + i;
+            grid_mp[node] = gtape[(size_t)e * 64 + lt];
+            grid_node_update(P, wind, t, node, i, j, k, grid_mp, grid_v, 0);
+        }
+    }
+}
+
 // x/xo and F/Fo may be the same arrays (in-place substep): every thread reads
 // its particle before writing it, so they carry no __restrict__.
 __global__ void k_g2p(MpmParams P, const float *x, const float *F,
@@ -429,6 +478,9 @@ extern "C" dw_status mpm_destroy(dw_mpm h) {
     cudaFree(h->roll_state);
     cudaFree(h->roll_pinned);
     cudaFree(h->roll_ids);
+    cudaFree(h->gtape);
+    cudaFree(h->gtape_list);
+    cudaFree(h->gtape_count);
     profile_free(h);
     delete h;
     return DW_OK;
@@ -474,9 +526,11 @@ extern "C" dw_status mpm_set_material(dw_mpm h, float E, float nu) {
     return DW_OK;
 }
 
-extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
-                                 const uint8_t *pinned, const dw_wind_field *wind, float t,
-                                 dw_stream stream) {
+// The substep; tape_slot >= 0 (a segment adjoint's recompute) also keeps
+// the grid in that slot of the handle's grid tape.
+static dw_status substep_impl(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
+                              const uint8_t *pinned, const dw_wind_field *wind, float t,
+                              dw_stream stream, int tape_slot) {
     DW_REQUIRE(h, "handle is NULL");
     dw_status st = check_state(h, in, "input");
     if (st != DW_OK) return st;
@@ -494,8 +548,15 @@ extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_
                         active_blocks(h), s);
     }
     if (st != DW_OK) return st;
-    st = launch_grid_update(h, wd, t, 1, s);
-    if (st != DW_OK) return st;
+    if (tape_slot >= 0) {
+        ProfScope ps(h, DW_K_GRID, s);
+        DW_CUDA(launch_pdl(k_grid_update_tape, GRID_CTAS, GRID_THREADS, s, h->P, wd, t, h->grid_mp,
+                           h->grid_v, active_blocks(h), h->gtape + (size_t)tape_slot * h->nblk * 64,
+                           h->gtape_list + (size_t)tape_slot * h->nblk, h->gtape_count + tape_slot));
+    } else {
+        st = launch_grid_update(h, wd, t, 1, s);
+        if (st != DW_OK) return st;
+    }
     if (n > 0) {
         ProfScope ps(h, DW_K_G2P, s);
         DW_CUDA(launch_pdl(k_g2p, grid_for(n, 128), 128, s, h->P, (const float *)in->x,
@@ -505,12 +566,19 @@ extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_
     return DW_OK;
 }
 
+extern "C" dw_status mpm_substep(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *out,
+                                 const uint8_t *pinned, const dw_wind_field *wind, float t,
+                                 dw_stream stream) {
+    return substep_impl(h, in, out, pinned, wind, t, stream, -1);
+}
+
 // The reverse substep; Cout (or NULL): C of the substep's output state, when
-// the caller kept it (a segment's recomputed states).
+// the caller kept it (a segment's recomputed states); tape_slot >= 0: the
+// substep's forward grid is in that slot of the handle's grid tape.
 static dw_status substep_adjoint(dw_mpm h, const dw_mpm_state *in, const float *Cout,
                                  const dw_mpm_state *g_out, const dw_mpm_state *g_in,
                                  const uint8_t *pinned, const dw_wind_field *wind, float t,
-                                 float *g_wind, float *g_E, dw_stream stream) {
+                                 float *g_wind, float *g_E, dw_stream stream, int tape_slot = -1) {
     DW_REQUIRE(h, "handle is NULL");
     dw_status st = check_state(h, in, "input");
     if (st != DW_OK) return st;
@@ -525,14 +593,21 @@ static dw_status substep_adjoint(dw_mpm h, const dw_mpm_state *in, const float *
     cudaStream_t s = as_stream(stream);
     int64_t n = in->n;
     int64_t cap = h->desc.max_particles > 0 ? h->desc.max_particles : 1;
-    {
-        ProfScope ps(h, DW_K_P2G, s);
-        st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp, h->err,
-                        active_blocks(h), s);
+    if (tape_slot >= 0) {
+        ProfScope ps(h, DW_K_GRID, s);
+        DW_CUDA(launch_pdl(k_grid_restore, GRID_CTAS, GRID_THREADS, s, h->P, wd, t, h->grid_mp,
+                           h->grid_v, active_blocks(h), h->gtape + (size_t)tape_slot * h->nblk * 64,
+                           h->gtape_list + (size_t)tape_slot * h->nblk, h->gtape_count + tape_slot));
+    } else {
+        {
+            ProfScope ps(h, DW_K_P2G, s);
+            st = launch_p2g(h->desc.p2g_mode, h->P, in->x, in->v, in->C, in->F, n, h->grid_mp,
+                            h->err, active_blocks(h), s);
+        }
+        if (st != DW_OK) return st;
+        st = launch_grid_update(h, wd, t, 0, s);
+        if (st != DW_OK) return st;
     }
-    if (st != DW_OK) return st;
-    st = launch_grid_update(h, wd, t, 0, s);
-    if (st != DW_OK) return st;
     if (n > 0) {
         ProfScope ps(h, DW_K_REV_G2P, s);
         DW_CUDA(launch_pdl(k_rev_g2p, grid_for(n, P2G_WARP_THREADS), P2G_WARP_THREADS, s, h->P,
@@ -558,6 +633,44 @@ extern "C" dw_status mpm_substep_adjoint(dw_mpm h, const dw_mpm_state *in,
                                          const uint8_t *pinned, const dw_wind_field *wind,
                                          float t, float *g_wind, float *g_E, dw_stream stream) {
     return substep_adjoint(h, in, nullptr, g_out, g_in, pinned, wind, t, g_wind, g_E, stream);
+}
+
+// The grid tape for `slots` recomputed substeps, grown on demand (nblk
+// entries of 64 nodes' (m, p) per slot: 4 MB at 64^3, 34 MB at 128^3); taken
+// only while it leaves 8 GB of device memory free. Returns whether it is
+// there; without it the reverse pass rebuilds each grid by a P2G.
+static bool ensure_grid_tape(MpmHandle *h, int slots) {
+    if (slots <= 0) return false;
+    if (slots <= h->gtape_slots) return true;
+    if (h->gtape_refused && slots >= h->gtape_refused) return false;
+    const size_t bytes = (size_t)slots * ((size_t)h->nblk * (64 * sizeof(float4) + sizeof(int)) + sizeof(int));
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || bytes + (8ull << 30) > free_b) {
+        cudaGetLastError();
+        h->gtape_refused = slots;
+        return false;
+    }
+    cudaFree(h->gtape);
+    cudaFree(h->gtape_list);
+    cudaFree(h->gtape_count);
+    h->gtape = nullptr;
+    h->gtape_list = h->gtape_count = nullptr;
+    h->gtape_slots = 0;
+    cudaError_t e = cudaMalloc((void **)&h->gtape, (size_t)slots * h->nblk * 64 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->gtape_list, (size_t)slots * h->nblk * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->gtape_count, (size_t)slots * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->gtape);
+        cudaFree(h->gtape_list);
+        cudaFree(h->gtape_count);
+        h->gtape = nullptr;
+        h->gtape_list = h->gtape_count = nullptr;
+        h->gtape_refused = slots;
+        return false;
+    }
+    h->gtape_slots = slots;
+    return true;
 }
 
 extern "C" dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, float *tape,
@@ -589,17 +702,20 @@ extern "C" dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, fl
         s.n = n;
         return s;
     };
+    // the recompute keeps each substep's grid when the grid tape fits
+    const bool gt = ensure_grid_tape(h, n_substeps - 1);
     for (int k = 1; k < n_substeps; ++k) {
         const dw_mpm_state in = k == 1 ? *start : slot(k - 1), out = slot(k);
-        st = mpm_substep(h, &in, &out, pinned, wind, fmaf((float)(k - 1), dt, t0), stream);
+        st = substep_impl(h, &in, &out, pinned, wind, fmaf((float)(k - 1), dt, t0), stream,
+                          gt ? k - 1 : -1);
         if (st != DW_OK) return st;
     }
     for (int j = n_substeps - 1; j >= 0; --j) {
         const dw_mpm_state in = j == 0 ? *start : slot(j);
-        // the output state j + 1 is in the tape for every substep but the last
-        const float *Cout = j + 1 < n_substeps ? slot(j + 1).C : nullptr;
-        st = substep_adjoint(h, &in, Cout, g, g, pinned, wind, fmaf((float)j, dt, t0), g_wind,
-                             g_E, stream);
+        // the output state j + 1 and substep j's grid are kept for every substep but the last
+        const bool kept = j + 1 < n_substeps;
+        st = substep_adjoint(h, &in, kept ? slot(j + 1).C : nullptr, g, g, pinned, wind,
+                             fmaf((float)j, dt, t0), g_wind, g_E, stream, kept && gt ? j : -1);
         if (st != DW_OK) return st;
     }
     return DW_OK;

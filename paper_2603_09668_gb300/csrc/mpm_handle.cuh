@@ -28,6 +28,12 @@ struct MpmHandle {
     int *block_flag = nullptr;   // [nblk]
     int *block_list = nullptr;   // [2][nblk]: two lists so a fused kernel can fill one
     int *block_count = nullptr;  // [2]      while the grid update consumes the other
+    // grid tape of a segment adjoint's recompute: per recomputed substep the
+    // consumed list and each listed node's (m, p) (nblk entries of 64 nodes)
+    float4 *gtape = nullptr;
+    int *gtape_list = nullptr, *gtape_count = nullptr;
+    int gtape_slots = 0;
+    int gtape_refused = 0;       // slots a failed or oversized allocation was refused for
     // rollout workspace: the second state buffer of the sort ping-pong
     float *roll_state = nullptr;     // [24][max_particles]
     uint8_t *roll_pinned = nullptr;  // [max_particles]
