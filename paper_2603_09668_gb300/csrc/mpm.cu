@@ -702,13 +702,22 @@ extern "C" dw_status mpm_segment_adjoint(dw_mpm h, const dw_mpm_state *start, fl
         s.n = n;
         return s;
     };
-    // the recompute keeps each substep's grid when the grid tape fits
+    // the recompute keeps each substep's grid when the grid tape fits; with
+    // the paired kernel it runs as one fused chain
     const bool gt = ensure_grid_tape(h, n_substeps - 1);
-    for (int k = 1; k < n_substeps; ++k) {
-        const dw_mpm_state in = k == 1 ? *start : slot(k - 1), out = slot(k);
-        st = substep_impl(h, &in, &out, pinned, wind, fmaf((float)(k - 1), dt, t0), stream,
-                          gt ? k - 1 : -1);
+    if (h->desc.p2g_mode == DW_P2G_AUTO || h->desc.p2g_mode == DW_P2G_PAIR) {
+        WindDev wd;
+        st = wind_check(wind, &wd);
         if (st != DW_OK) return st;
+        st = segment_recompute(h, start, tape, pinned, wd, t0, n_substeps, gt, as_stream(stream));
+        if (st != DW_OK) return st;
+    } else {
+        for (int k = 1; k < n_substeps; ++k) {
+            const dw_mpm_state in = k == 1 ? *start : slot(k - 1), out = slot(k);
+            st = substep_impl(h, &in, &out, pinned, wind, fmaf((float)(k - 1), dt, t0), stream,
+                              gt ? k - 1 : -1);
+            if (st != DW_OK) return st;
+        }
     }
     for (int j = n_substeps - 1; j >= 0; --j) {
         const dw_mpm_state in = j == 0 ? *start : slot(j);

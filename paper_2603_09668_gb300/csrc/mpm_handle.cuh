@@ -118,6 +118,19 @@ __global__ void k_g2p(MpmParams P, const float *x, const float *F,
                       const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
                       float *xo, float *vo, float *Co, float *Fo, int64_t n, int *err,
                       int *reset_count);
+__global__ void k_grid_update_tape(MpmParams P, WindDev wind, float t, float4 *__restrict__ grid_mp,
+                                   float4 *__restrict__ grid_v, ActiveBlocks ab,
+                                   float4 *__restrict__ gtape, int *__restrict__ gtape_list,
+                                   int *__restrict__ gtape_count);
+
+// The recompute of a segment adjoint (mpm_rollout.cu): states 1 .. n_substeps
+// - 1 from `start` into the tape slots, as one fused chain (the P2G of the
+// start state, then per substep the grid update, kept in grid tape slot k
+// when `keep_grid`, and the paired G2P/P2G kernel writing state k + 1 to its
+// slot). For p2g modes AUTO and PAIR.
+dw_status segment_recompute(MpmHandle *h, const dw_mpm_state *start, float *tape,
+                            const uint8_t *pinned, const WindDev &wd, float t0, int n_substeps,
+                            bool keep_grid, cudaStream_t s);
 
 // particle sort (mpm.cu): counting sort by cell key, keys already counted
 constexpr int SCAN_BLOCK = 1024;

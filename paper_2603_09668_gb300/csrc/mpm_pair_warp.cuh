@@ -157,16 +157,23 @@ __device__ __forceinline__ void g2p_direct(const MpmParams &P, const pr::Stencil
     for (int k = 0; k < 9; ++k) Cn[k] = c[k];
 }
 
+// Output arrays of a substep that writes its whole output state elsewhere
+// (the recompute of a reverse segment: state k in, state k + 1 out).
+struct PairOut {
+    float *x, *v, *C, *F;
+};
+
 // The substep body for one warp: particles wq .. min(wq + 64, wend) - 1 of
 // arrays with row stride n. MAT < 0 takes the material from P at run time
 // (warp-uniform). reset_count, when not NULL, is cleared after the
-// dependency wait (the active list the grid update has consumed).
-template <int MAT, bool STORE_VC, bool VEC>
+// dependency wait (the active list the grid update has consumed). With OUT
+// the updated x, v, C and F go to `out` (x and F are not updated in place).
+template <int MAT, bool STORE_VC, bool VEC, bool OUT = false>
 __device__ __forceinline__ void pair_warp(
     const MpmParams &P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
     float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
     float4 *__restrict__ grid_next, int64_t n, int64_t wq, int64_t wend, int *err,
-    const ActiveBlocks &ab_next, int *reset_count, PairWarpSmem &ws) {
+    const ActiveBlocks &ab_next, int *reset_count, PairWarpSmem &ws, PairOut out = {}) {
     using namespace pr;
     const int lane = threadIdx.x & 31;
     const int64_t q = wq + 2 * lane;
@@ -277,14 +284,14 @@ __device__ __forceinline__ void pair_warp(
     }
     if (v0) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) st_pair<VEC>(x + a * n, q, xp[a], v1);
+        for (int a = 0; a < 3; ++a) st_pair<VEC>((OUT ? out.x : x) + a * n, q, xp[a], v1);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) st_pair<VEC>(F + k * n, q, Fn[k], v1);
-        if (STORE_VC) {
+        for (int k = 0; k < 9; ++k) st_pair<VEC>((OUT ? out.F : F) + k * n, q, Fn[k], v1);
+        if (STORE_VC || OUT) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) st_pair<VEC>(v + a * n, q, vn[a], v1);
+            for (int a = 0; a < 3; ++a) st_pair<VEC>((OUT ? out.v : v) + a * n, q, vn[a], v1);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) st_pair<VEC>(C + k * n, q, Cn[k], v1);
+            for (int k = 0; k < 9; ++k) st_pair<VEC>((OUT ? out.C : C) + k * n, q, Cn[k], v1);
         }
         // one non-finite entry makes the sum non-finite
         float2 sum = add(add(xp[0], xp[1]), xp[2]);

@@ -85,17 +85,84 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS, 10) k_g2p2g(
 //
 // k_g2p2g_pair: the body of k_g2p2g with two particles per thread on paired
 // FP32 instructions (pair_warp, mpm_pair_warp.cuh).
-template <int MAT, bool STORE_VC, bool VEC>
+// With OUT the output state goes to `out` (the recompute of a reverse segment).
+template <int MAT, bool STORE_VC, bool VEC, bool OUT = false>
 __global__ void __launch_bounds__(PAIR_THREADS, 5) k_g2p2g_pair(
     MpmParams P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
     float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
-    float4 *__restrict__ grid_next, int64_t n, int *err, ActiveBlocks ab_next, int *reset_count) {
+    float4 *__restrict__ grid_next, int64_t n, int *err, ActiveBlocks ab_next, int *reset_count,
+    PairOut out) {
     __shared__ PairWarpSmem smem[PAIR_WARPS];
     const int wid = threadIdx.x >> 5;
     const int64_t wq = ((int64_t)blockIdx.x * PAIR_THREADS + wid * 32) * 2;  // the warp's first particle
-    pair_warp<MAT, STORE_VC, VEC>(P, x, v, C, F, pinned, grid_v, grid_next, n, wq, n, err, ab_next,
-                                  blockIdx.x == 0 && threadIdx.x == 0 ? reset_count : nullptr,
-                                  smem[wid]);
+    pair_warp<MAT, STORE_VC, VEC, OUT>(P, x, v, C, F, pinned, grid_v, grid_next, n, wq, n, err,
+                                       ab_next,
+                                       blockIdx.x == 0 && threadIdx.x == 0 ? reset_count : nullptr,
+                                       smem[wid], out);
+}
+
+dw_status segment_recompute(MpmHandle *h, const dw_mpm_state *start, float *tape,
+                            const uint8_t *pinned, const WindDev &wd, float t0, int n_substeps,
+                            bool keep_grid, cudaStream_t s) {
+    const int64_t n = start->n;
+    if (n_substeps < 2 || n == 0) return DW_OK;
+    auto slot = [&](int k) {  // state k (1 .. n_substeps - 1) in the tape
+        dw_mpm_state st;
+        float *b = tape + (size_t)(k - 1) * 24 * (size_t)n;
+        st.x = b;
+        st.v = b + 3 * n;
+        st.C = b + 6 * n;
+        st.F = b + 15 * n;
+        st.n = n;
+        return st;
+    };
+    dw_status st;
+    {
+        ProfScope ps(h, DW_K_P2G, s);
+        st = launch_p2g(h->desc.p2g_mode, h->P, start->x, start->v, start->C, start->F, n,
+                        h->grid_mp, h->err, active_blocks(h, 0), s);
+    }
+    if (st != DW_OK) return st;
+    const unsigned pair_grid = grid_for(n, 2 * PAIR_THREADS);
+    int L = 0;  // list consumed by the next grid update
+    for (int k = 0; k + 1 < n_substeps; ++k) {
+        const float t = fmaf((float)k, h->P.dt, t0);
+        {
+            ProfScope ps(h, DW_K_GRID, s);
+            if (keep_grid)
+                DW_CUDA(launch_pdl(k_grid_update_tape, GRID_CTAS, GRID_THREADS, s, h->P, wd, t,
+                                   h->grid_mp, h->grid_v, active_blocks(h, L),
+                                   h->gtape + (size_t)k * h->nblk * 64,
+                                   h->gtape_list + (size_t)k * h->nblk, h->gtape_count + k));
+            else
+                DW_CUDA(launch_pdl(k_grid_update_active, GRID_CTAS, GRID_THREADS, s, h->P, wd, t,
+                                   h->grid_mp, h->grid_v, 1, active_blocks(h, L)));
+        }
+        const dw_mpm_state in = k == 0 ? *start : slot(k), out = slot(k + 1);
+        if (k + 2 < n_substeps) {  // state k + 1 is scattered for substep k + 1's grid
+            ProfScope ps(h, DW_K_G2P2G, s);
+            const bool vec = n % 4 == 0 &&
+                             ((reinterpret_cast<uintptr_t>(in.x) | reinterpret_cast<uintptr_t>(in.F) |
+                               reinterpret_cast<uintptr_t>(out.x) | reinterpret_cast<uintptr_t>(out.F)) %
+                                  16 == 0);
+            auto kern = h->P.material == DW_NEOHOOKEAN
+                            ? (vec ? k_g2p2g_pair<DW_NEOHOOKEAN, false, true, true>
+                                   : k_g2p2g_pair<DW_NEOHOOKEAN, false, false, true>)
+                            : (vec ? k_g2p2g_pair<DW_FIXED_COROTATED, false, true, true>
+                                   : k_g2p2g_pair<DW_FIXED_COROTATED, false, false, true>);
+            DW_CUDA(launch_pdl(kern, pair_grid, PAIR_THREADS, s, h->P, in.x, in.v, in.C, in.F,
+                               pinned, (const float4 *)h->grid_v, h->grid_mp, n, h->err,
+                               active_blocks(h, 1 - L), h->block_count + L,
+                               PairOut{out.x, out.v, out.C, out.F}));
+            L = 1 - L;
+        } else {
+            ProfScope ps(h, DW_K_G2P, s);
+            DW_CUDA(launch_pdl(k_g2p, grid_for(n, 128), 128, s, h->P, (const float *)in.x,
+                               (const float *)in.F, pinned, (const float4 *)h->grid_v, out.x,
+                               out.v, out.C, out.F, n, h->err, h->block_count + L));
+        }
+    }
+    return DW_OK;
 }
 
 static dw_mpm_state view_of(float *base, int64_t n) {
@@ -173,7 +240,7 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
                     DW_CUDA(launch_pdl(kern, pair_grid, PAIR_THREADS, s, h->P, cur.x, cur.v, cur.C,
                                        cur.F, (const uint8_t *)cur_pin, (const float4 *)h->grid_v,
                                        h->grid_mp, n, h->err, active_blocks(h, 1 - L),
-                                       h->block_count + L));
+                                       h->block_count + L, PairOut{}));
                 } else {
                     DW_CUDA(launch_pdl(k_g2p2g<false>, pgrid, P2G_WARP_THREADS, s, h->P, cur.x,
                                        cur.v, cur.C, cur.F, (const uint8_t *)cur_pin,
