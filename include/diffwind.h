@@ -764,6 +764,21 @@ DW_API dw_status surr_loss(dw_surr h, const float *target, float *loss, dw_strea
 DW_API dw_status surr_set_output_grad(dw_surr h, const float *g_out, dw_stream stream);
 /* Reverse pass of the last surr_forward; accumulates into the gradients. */
 DW_API dw_status surr_backward(dw_surr h, dw_stream stream);
+
+/* One layer's weight and bias gradients from given operands, the step that
+ * surr_backward runs for each layer: gw[27][cout][cin] += sum over voxels v
+ * of g[v][co] in[v + d(tap)][ci] (zero padding; tap = 9 (dz + 1) + 3 (dy + 1)
+ * + (dx + 1)) and gb[cout] += sum_v g[v][co]. in (cin channels) and g (cout
+ * channels) are device BF16 volumes of the handle's n^3 coarse voxels in the
+ * planar layout [C/8][n^3][8]; gw and gb are device FP32. (cin, cout) must be
+ * a layer shape of the network: (16, 32), (32, 32) or (32, 16). impl 0 runs
+ * the tcgen05 kernel surr_backward uses (TMA-loaded operands, FP32 sums in
+ * tensor memory), impl 1 the warp-level mma.sync kernel it replaced; the two
+ * agree up to the order of the FP32 sums. Uses the handle's partial-sum
+ * workspace (calls on one handle must not overlap). */
+DW_API dw_status surr_weight_grad(dw_surr h, int32_t cin, int32_t cout, const void *in,
+                                  const void *g, float *gw, float *gb, int32_t impl,
+                                  dw_stream stream);
 /* Adam step (bias-corrected, step >= 1) on the parameters; zeroes the
  * gradients and refreshes the BF16 weights. */
 DW_API dw_status surr_adam(dw_surr h, float lr, float beta1, float beta2, float eps, int32_t step,

@@ -148,6 +148,7 @@ SIGNATURES = {
     "surr_loss": (I32, [VP, VP, VP, VP]),
     "surr_set_output_grad": (I32, [VP, VP, VP]),
     "surr_backward": (I32, [VP, VP]),
+    "surr_weight_grad": (I32, [VP, I32, I32, VP, VP, VP, VP, I32, VP]),
     "surr_adam": (I32, [VP, F32, F32, F32, F32, I32, VP]),
     "surr_apply": (I32, [VP, VP, F32, VP, VP, VP]),
     "lbm_velocity_error": (I32, [VP, VP, VP, I64, VP, VP]),

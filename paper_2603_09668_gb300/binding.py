@@ -1009,6 +1009,17 @@ class Surrogate:
     def backward(self):
         surr_backward(self.h)
 
+    def weight_grad(self, cin, cout, x, g, gw, gb, impl=0, stream=None):
+        """gw [27][cout][cin] += dW, gb [cout] += db of one layer from BF16
+        planar volumes x (cin channels) and g (cout channels) of n^3 voxels
+        (uint8 or bfloat16 tensors); impl 0 tcgen05, 1 mma.sync."""
+        for t, name in ((x, "x"), (g, "g")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        check(lib().surr_weight_grad(self.h, int(cin), int(cout), x.data_ptr(), g.data_ptr(),
+                                     _dev(gw, name="gw"), _dev(gb, name="gb"), int(impl),
+                                     _stream(stream)))
+
     def device_status(self):
         surr_device_status(self.h)
 

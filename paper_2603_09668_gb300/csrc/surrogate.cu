@@ -8,9 +8,11 @@
 // the LBM velocity field as the guide that this network stands in for.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <new>
 
 #include "surrogate_tc.cuh"
+#include "surrogate_wgrad_tc.cuh"
 
 namespace dw {
 
@@ -49,6 +51,10 @@ struct SurrHandle {
     bool weights_dirty = true;
     // TMA descriptors of the conv inputs: features, a1..a3, dL/d(out), dL/dz1..dz3
     CUtensorMap tm_feats, tm_a[3], tm_g4, tm_gz[3];
+    // and of the weight-gradient kernel's operands: layer l's input (features,
+    // a1..a3) and its output gradient (dL/dz1..dz3, dL/d(out))
+    CUtensorMap tmw_in[4], tmw_g[4];
+    int part_chunks = 0;            // capacity of part / part_b in CTA partials
 };
 
 // ------------------------------------------------------------- kernels ----
@@ -592,9 +598,10 @@ static dw_status conv(SurrHandle *h, const CUtensorMap &tm_in, const bf16 *wt, c
 }
 
 // TMA descriptor of a planar [C/8][n][n][n][8] BF16 volume viewed as 4D
-// [C/8][z][y][x * 8]; box = the 10 x 18 halo of one z slice in all C/8
+// [C/8][z][y][x * 8]; box = bx voxels x by rows x bz slices in all C/8
 // planes, zero fill outside.
-static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) {
+static dw_status make_box_map(CUtensorMap *tm, const bf16 *base, int n, int C, int bx, int by,
+                              int bz) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -610,7 +617,7 @@ static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) 
     const cuuint64_t nn = (cuuint64_t)n;
     const cuuint64_t dims[4] = {8 * nn, nn, nn, (cuuint64_t)(C / 8)};
     const cuuint64_t strides[3] = {16 * nn, 16 * nn * nn, 16 * nn * nn * nn};
-    const cuuint32_t box[4] = {8 * TC_HX, TC_HY, 1, (cuuint32_t)(C / 8)};
+    const cuuint32_t box[4] = {(cuuint32_t)(8 * bx), (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)(C / 8)};
     const cuuint32_t es[4] = {1, 1, 1, 1};
     const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims,
                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -623,8 +630,48 @@ static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) 
     return DW_OK;
 }
 
+// The conv kernels' box: the 10 x 18 halo of one z slice.
+static dw_status make_halo_map(CUtensorMap *tm, const bf16 *base, int n, int C) {
+    return make_box_map(tm, base, n, C, TC_HX, TC_HY, 1);
+}
+
+// The weight-gradient kernel's boxes: an input tile's halo (16 voxels x 6
+// rows x 3 slices) and an output-gradient tile (16 x 4 x 1).
+static dw_status make_wgrad_maps(CUtensorMap *tm_in, CUtensorMap *tm_g, const bf16 *in, int cin,
+                                 const bf16 *g, int cout, int n) {
+    dw_status st = make_box_map(tm_in, in, n, cin, WG_TX, WG_HY, 3);
+    if (st == DW_OK) st = make_box_map(tm_g, g, n, cout, WG_TX, WG_TY, 1);
+    return st;
+}
+
+// Weight and bias gradients of one layer on tcgen05: gw += dW, gb += db.
 template <int CIN, int COUT>
-static dw_status wgrad(SurrHandle *h, const bf16 *in, const bf16 *g, int layer, cudaStream_t s) {
+static dw_status wgrad_tc(SurrHandle *h, const CUtensorMap &tm_in, const CUtensorMap &tm_g,
+                          const bf16 *g, float *gw, float *gb, cudaStream_t s) {
+    constexpr size_t smem = wg_smem<CIN, COUT>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        DW_CUDA(cudaFuncSetAttribute(k_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        attr_set = true;
+    }
+    const int ntiles = (h->n / WG_TX) * (h->n / WG_TY) * h->n;
+    const int grid = std::min(std::min(h->sms, h->part_chunks), ntiles);
+    k_wgrad_tc<CIN, COUT><<<grid, WG_THREADS, smem, s>>>(tm_in, tm_g, h->n, h->part, h->err);
+    DW_LAUNCHED("k_wgrad_tc");
+    k_bias_grad<COUT><<<grid, 256, 0, s>>>(g, h->nv, h->part_b);
+    DW_LAUNCHED("k_bias_grad");
+    const int64_t nw = 27LL * CIN * COUT;
+    k_wgrad_reduce<<<grid_for(nw + COUT, 256), 256, 0, s>>>(h->part, h->part_b, grid, nw, COUT, gw, gb);
+    DW_LAUNCHED("k_wgrad_reduce");
+    return DW_OK;
+}
+
+// The same on the warp-level MMA (mma.sync): kept as a second implementation
+// that surr_weight_grad exposes for comparison.
+template <int CIN, int COUT>
+static dw_status wgrad(SurrHandle *h, const bf16 *in, const bf16 *g, float *gw, float *gb,
+                       cudaStream_t s) {
     constexpr size_t smem = wgrad_smem<CIN, COUT>();
     static bool attr_set = false;
     if (!attr_set) {
@@ -637,8 +684,7 @@ static dw_status wgrad(SurrHandle *h, const bf16 *in, const bf16 *g, int layer, 
     DW_LAUNCHED("k_wgrad");
     const int64_t nw = 27LL * CIN * COUT;
     k_wgrad_reduce<<<grid_for(nw + COUT, 256), 256, 0, s>>>(h->part, h->part_b, h->nchunks, nw, COUT,
-                                                            h->grads + h->off_w[layer],
-                                                            h->grads + h->off_b[layer]);
+                                                            gw, gb);
     DW_LAUNCHED("k_wgrad_reduce");
     return DW_OK;
 }
@@ -718,8 +764,9 @@ extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
     DW_ALLOC(h->out, sizeof(float) * nv * 16);
     DW_ALLOC(h->out4, sizeof(float) * nv * 4);
     DW_ALLOC(h->g4, sizeof(bf16) * nv * 16);
-    DW_ALLOC(h->part, sizeof(float) * (size_t)h->nchunks * 27 * 32 * 32);
-    DW_ALLOC(h->part_b, sizeof(float) * (size_t)h->nchunks * 32);
+    h->part_chunks = std::max(h->nchunks, h->sms);
+    DW_ALLOC(h->part, sizeof(float) * (size_t)h->part_chunks * 27 * 32 * 32);
+    DW_ALLOC(h->part_b, sizeof(float) * (size_t)h->part_chunks * 32);
     DW_ALLOC(h->fine, sizeof(float) * 4 * Nc);
     DW_ALLOC(h->red, sizeof(double) * 4);
     DW_ALLOC(h->err, sizeof(int));
@@ -741,6 +788,10 @@ extern "C" dw_status surr_create(int32_t n, dw_surr *out) {
     for (int l = 0; l < 3 && st == DW_OK; ++l) st = make_halo_map(&h->tm_a[l], h->a[l], n, 32);
     if (st == DW_OK) st = make_halo_map(&h->tm_g4, h->g4, n, 16);
     for (int l = 0; l < 3 && st == DW_OK; ++l) st = make_halo_map(&h->tm_gz[l], h->gz[l], n, 32);
+    if (st == DW_OK) st = make_wgrad_maps(&h->tmw_in[0], &h->tmw_g[0], h->feats, 16, h->gz[0], 32, n);
+    for (int l = 1; l < 3 && st == DW_OK; ++l)
+        st = make_wgrad_maps(&h->tmw_in[l], &h->tmw_g[l], h->a[l - 1], 32, h->gz[l], 32, n);
+    if (st == DW_OK) st = make_wgrad_maps(&h->tmw_in[3], &h->tmw_g[3], h->a[2], 32, h->g4, 16, n);
     if (st != DW_OK) {
         surr_destroy(h);
         return st;
@@ -942,20 +993,46 @@ extern "C" dw_status surr_backward(dw_surr h, dw_stream stream) {
     cudaStream_t s = as_stream(stream);
     dw_status st;
     // layer 4: dW from a3 and g4; dL/dz3 = (W4' * g4) GELU'(z3)
-    st = wgrad<32, 16>(h, h->a[2], h->g4, 3, s);
+    st = wgrad_tc<32, 16>(h, h->tmw_in[3], h->tmw_g[3], h->g4, h->grads + h->off_w[3],
+                          h->grads + h->off_b[3], s);
     if (st != DW_OK) return st;
     st = conv<16, 32, EPI_DGELU>(h, h->tm_g4, h->wd + h->woff[3], nullptr, h->gz[2], nullptr, nullptr, h->z[2], s);
     if (st != DW_OK) return st;
-    st = wgrad<32, 32>(h, h->a[1], h->gz[2], 2, s);
+    st = wgrad_tc<32, 32>(h, h->tmw_in[2], h->tmw_g[2], h->gz[2], h->grads + h->off_w[2],
+                          h->grads + h->off_b[2], s);
     if (st != DW_OK) return st;
     st = conv<32, 32, EPI_DGELU>(h, h->tm_gz[2], h->wd + h->woff[2], nullptr, h->gz[1], nullptr, nullptr, h->z[1], s);
     if (st != DW_OK) return st;
-    st = wgrad<32, 32>(h, h->a[0], h->gz[1], 1, s);
+    st = wgrad_tc<32, 32>(h, h->tmw_in[1], h->tmw_g[1], h->gz[1], h->grads + h->off_w[1],
+                          h->grads + h->off_b[1], s);
     if (st != DW_OK) return st;
     st = conv<32, 32, EPI_DGELU>(h, h->tm_gz[1], h->wd + h->woff[1], nullptr, h->gz[0], nullptr, nullptr, h->z[0], s);
     if (st != DW_OK) return st;
-    st = wgrad<16, 32>(h, h->feats, h->gz[0], 0, s);
+    st = wgrad_tc<16, 32>(h, h->tmw_in[0], h->tmw_g[0], h->gz[0], h->grads + h->off_w[0],
+                          h->grads + h->off_b[0], s);
     return st;
+}
+
+extern "C" dw_status surr_weight_grad(dw_surr h, int32_t cin, int32_t cout, const void *in,
+                                      const void *g, float *gw, float *gb, int32_t impl,
+                                      dw_stream stream) {
+    DW_REQUIRE(h && in && g && gw && gb, "handle and arrays must not be NULL");
+    DW_REQUIRE((cin == 16 && cout == 32) || (cin == 32 && cout == 32) || (cin == 32 && cout == 16),
+               "(cin, cout) = (%d, %d) is not a layer shape of the network", cin, cout);
+    DW_REQUIRE(impl == 0 || impl == 1, "impl must be 0 (tcgen05) or 1 (mma.sync)");
+    cudaStream_t s = as_stream(stream);
+    const bf16 *bi = static_cast<const bf16 *>(in), *bg = static_cast<const bf16 *>(g);
+    if (impl == 1) {
+        if (cin == 16) return wgrad<16, 32>(h, bi, bg, gw, gb, s);
+        if (cout == 32) return wgrad<32, 32>(h, bi, bg, gw, gb, s);
+        return wgrad<32, 16>(h, bi, bg, gw, gb, s);
+    }
+    CUtensorMap tm_in, tm_g;
+    dw_status st = make_wgrad_maps(&tm_in, &tm_g, bi, cin, bg, cout, h->n);
+    if (st != DW_OK) return st;
+    if (cin == 16) return wgrad_tc<16, 32>(h, tm_in, tm_g, bg, gw, gb, s);
+    if (cout == 32) return wgrad_tc<32, 32>(h, tm_in, tm_g, bg, gw, gb, s);
+    return wgrad_tc<32, 16>(h, tm_in, tm_g, bg, gw, gb, s);
 }
 
 extern "C" dw_status surr_adam(dw_surr h, float lr, float beta1, float beta2, float eps,

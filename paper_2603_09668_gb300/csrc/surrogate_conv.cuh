@@ -4,9 +4,9 @@
 //
 // k_wgrad: dW[tap][co][ci] = sum_v g[v][co] in[v + d(tap)][ci] over the
 // voxels of a chunk of output tiles of 16 (x) x 8 (y) x 1 (z), written as
-// partial sums that k_wgrad_reduce adds up. The GEMM runs over voxels (K),
-// which is why it stays on the warp-level MMA: the forward and input-gradient
-// convolutions (surrogate_tc.cuh) are the tcgen05 kernels. Activations are
+// partial sums that k_wgrad_reduce adds up. The training backward pass runs
+// the tcgen05 version (surrogate_wgrad_tc.cuh); this warp-level MMA kernel is
+// kept as the second implementation surr_weight_grad offers. Activations are
 // planar, [C/8][n^3][8] BF16. Shared-memory rows (a voxel's or an output
 // channel's values) keep their 16-byte chunks XOR-swizzled by the row index,
 // so that the eight rows an ldmatrix matrix reads hit distinct banks.

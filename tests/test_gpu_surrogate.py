@@ -241,3 +241,52 @@ def test_chained_correction_adds_the_plain_defect():
     s.advance_fine(1e-3, solid, 20.0)
     assert err_to(fp) > 1e-2
     s.close()
+
+
+def _planar_bf16(n, c, seed):
+    """A random BF16 volume in the planar layout [c/8][n^3][8] (device) and
+    the same values as float64 [c][z][y][x] (host)."""
+    rng = np.random.default_rng(seed)
+    v = torch.tensor(rng.standard_normal((c // 8, n ** 3, 8)).astype(np.float32)).to(torch.bfloat16)
+    ref = v.to(torch.float64).numpy().reshape(c // 8, n, n, n, 8)
+    ref = np.moveaxis(ref, 4, 1).reshape(c, n, n, n)
+    return v.cuda().contiguous(), ref
+
+
+@pytest.mark.parametrize("n", [16, 64])
+@pytest.mark.parametrize("shape", [(16, 32), (32, 32), (32, 16)])
+def test_weight_gradient_kernels_match_the_sum(n, shape):
+    """surr_weight_grad, both implementations (tcgen05 with TMA-loaded MN-major
+    operands, the one surr_backward runs; and the mma.sync kernel), against
+    the definition dW[tap][co][ci] = sum_v g[v][co] in[v + d(tap)][ci] with
+    zero padding, summed in float64 from the same BF16 values, for every layer
+    shape; the bias gradient sum_v g[v][co]; a second call accumulates. Both
+    sum in FP32: relative L2 2e-5 at 16^3 voxels, 1e-4 at 64^3."""
+    cin, cout = shape
+    x, X = _planar_bf16(n, cin, seed=cin + 7 * n)
+    g, G = _planar_bf16(n, cout, seed=cout + 11 * n)
+    Xp = np.pad(X, ((0, 0), (1, 1), (1, 1), (1, 1)))
+    ref = np.zeros((27, cout, cin))
+    Gm = G.reshape(cout, -1)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                sh = Xp[:, dz:dz + n, dy:dy + n, dx:dx + n].reshape(cin, -1)
+                ref[9 * dz + 3 * dy + dx] = Gm @ sh.T
+    ref_b = Gm.sum(axis=1)
+    tol = 2e-5 if n == 16 else 1e-4
+    s = B.Surrogate(n)
+    got = {}
+    for impl in (0, 1):
+        gw = torch.zeros(27 * cout * cin, device="cuda")
+        gb = torch.zeros(cout, device="cuda")
+        s.weight_grad(cin, cout, x, g, gw, gb, impl=impl)
+        s.device_status()
+        w = gw.double().cpu().numpy().reshape(27, cout, cin)
+        assert rel_l2(w, ref) <= tol, (impl, rel_l2(w, ref))
+        assert rel_l2(gb.double().cpu().numpy(), ref_b) <= tol, impl
+        got[impl] = w
+        s.weight_grad(cin, cout, x, g, gw, gb, impl=impl)  # accumulates
+        assert rel_l2(gw.double().cpu().numpy().reshape(27, cout, cin), 2 * ref) <= tol
+    assert rel_l2(got[0], got[1]) <= tol
+    s.close()
