@@ -283,6 +283,7 @@ class SurrogateLBM:
         f = f_eq(rho, u), only before a check block or at the end."""
         used = 0
         in_fine = False  # the current state is the handle's fine field, not f
+        self.lbm.cache_mask(solid)  # the plain blocks share the mask's link words
         for _ in range(n_blocks):
             if self.fallback:
                 self.plain_block(f, solid)
