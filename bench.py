@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--substeps", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate", "batch",
+    ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate",
+                                                    "surrogate_train", "batch",
                                                     "batch_adjoint", "inversion", "gsplat"],
                     help="run one part alone (for profiling): the sheet rollout, the 128^3 LBM "
                          "or the checkpointed MPM adjoint")
@@ -778,10 +779,57 @@ def bench_gsplat(dev):
             "gs_gaussians": n}
 
 
+def bench_surrogate_train(dev, n=64, reps=10):
+    """One training step of the surrogate network at 64^3 coarse voxels
+    (forward keeping the activations, MSE loss, reverse pass, Adam), its
+    reverse pass alone, and each layer shape's weight-gradient kernel on
+    tcgen05 and on mma.sync (surr_weight_grad), with their FLOP rates
+    (2 x 27 x cin x cout per voxel)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_09668_gb300 import binding as B
+
+    s = B.Surrogate(n)
+    rng = np.random.default_rng(0)
+    s.set_params(torch.tensor(rng.standard_normal(s.nparams).astype(np.float32) * 0.05).to(dev))
+    s.set_features(torch.tensor(rng.standard_normal((n ** 3, 16)).astype(np.float32)).to(dev))
+    out = torch.empty((n ** 3, 16), device=dev)
+    target = torch.tensor(rng.standard_normal((n ** 3, 16)).astype(np.float32) * 0.1).to(dev)
+    loss = torch.zeros(1, device=dev)
+    step = [0]
+
+    def train_step():
+        step[0] += 1
+        s.zero_grads()
+        s.forward(out, keep_activations=True)
+        s.loss(target, loss)
+        s.backward()
+        s.adam(1e-4, step=step[0])
+
+    res = {"surr_train_step_ms": _timed(train_step, reps), "surr_backward_ms": _timed(s.backward, reps)}
+    for cin, cout in ((16, 32), (32, 32), (32, 16)):
+        x = torch.randn((cin // 8, n ** 3, 8), device=dev).to(torch.bfloat16).contiguous()
+        g = torch.randn((cout // 8, n ** 3, 8), device=dev).to(torch.bfloat16).contiguous()
+        gw = torch.zeros(27 * cin * cout, device=dev)
+        gb = torch.zeros(cout, device=dev)
+        flop = 2 * 27 * cin * cout * n ** 3
+        for impl, name in ((0, "tc"), (1, "mma")):
+            ms = _timed(lambda: s.weight_grad(cin, cout, x, g, gw, gb, impl=impl), reps)
+            res[f"surr_wgrad_{cin}_{cout}_{name}_us"] = ms * 1e3
+            res[f"surr_wgrad_{cin}_{cout}_{name}_tflops"] = flop / ms / 1e9
+    s.device_status()
+    s.close()
+    res["surr_train_note"] = ("64^3 coarse voxels; wgrad: one layer's weight and bias gradients, "
+                              "tc = tcgen05 (the kernel the reverse pass runs), mma = mma.sync")
+    return res
+
+
 def extras(dev, fp32_peak):
     out = bench_lbm(dev)
     out.update(bench_adjoint(dev))
     out.update(bench_surrogate(dev))
+    out.update(bench_surrogate_train(dev))
     out.update(bench_batch(dev))
     out.update(bench_batch_adjoint(dev))
     out.update(bench_inversion(dev))
@@ -831,6 +879,13 @@ def workload_rooflines(m, fp32_peak):
                                           "kernel 3, 64^3; the kernels run 16-channel padded ends, "
                                           "43.5 GFLOP) over the whole block (network and "
                                           "chained update); BF16 burst peak of MEASURED_PEAKS.json")
+    if "surr_wgrad_32_32_tc_us" in m:
+        r["surrogate_wgrad_32_32"] = roof_entry(1.0 / (m["surr_wgrad_32_32_tc_us"] * 1e-6),
+                                                2 * 27 * 32 * 32 * 64 ** 3 / 1e12, bf16, "TFLOP/s",
+                                                "tensor",
+                                                "one 32 -> 32 layer's weight gradient at 64^3 "
+                                                "(14.5 GFLOP, tcgen05, bias and partial-sum "
+                                                "reduction included); BF16 burst peak")
     return r
 
 
@@ -934,6 +989,8 @@ def run_only(args):
         res = bench_lbm(dev, steps=2 * max(args.steps, 1), adj_steps=2)
     elif args.only == "surrogate":
         res = bench_surrogate(dev)
+    elif args.only == "surrogate_train":
+        res = bench_surrogate_train(dev)
     elif args.only == "batch":
         res = bench_batch(dev, n_scenes=args.batch_scenes)
     elif args.only == "batch_adjoint":
@@ -951,8 +1008,8 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.only in ("lbm", "adjoint", "surrogate", "batch", "batch_adjoint", "inversion",
-                    "gsplat"):
+    elif a.only in ("lbm", "adjoint", "surrogate", "surrogate_train", "batch", "batch_adjoint",
+                    "inversion", "gsplat"):
         run_only(a)
     else:
         run_ours(a)
