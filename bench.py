@@ -904,10 +904,28 @@ def _oracle_sheet_run(args):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(n_sub=75, n_sub_all=30):
+def _oracle_lbm_run(args):
+    """Runs `steps` FP64 oracle BGK steps of the 128^3 leaf-cluster lattice
+    (tau 0.55, inlet 0.05 along x) in this process; returns the seconds."""
+    steps, seed = args
+    import oracle
+    from paper_2603_09668_gb300 import inputs
+
+    shape = (128, 128, 128)
+    solid = oracle.voxelize(inputs.ellipsoid_cluster(seed=seed), shape, 1.0 / 128)
+    _, w, _ = oracle.velocity_set()
+    f = np.repeat(w[:, None], 128 ** 3, axis=1)
+    t0 = time.perf_counter()
+    oracle.lbm_step(shape, 0.55, f, steps, u_in=(0.05, 0.0, 0.0), bc_x=1, solid=solid)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n_sub=75, n_sub_all=30, lbm_steps=4):
     """The FP64 oracle on this host: n_sub substeps of the full 400k sheet on
     one core, and independent replicas of n_sub_all substeps on every core at
-    once (processes started with spawn), the whole job's rate reported."""
+    once (processes started with spawn), the whole job's rate reported; and
+    lbm_steps BGK steps of the 128^3 leaf-cluster lattice the same two ways,
+    in MLUPS."""
     import multiprocessing
 
     import oracle
@@ -923,12 +941,22 @@ def cpu_baseline(n_sub=75, n_sub_all=30):
         t0 = time.perf_counter()
         pool.map(_oracle_sheet_run, [(n_sub_all, r) for r in range(cores)])
         wall = time.perf_counter() - t0
+        # the LBM step: one core, then one replica per core
+        lbm_one = _oracle_lbm_run((lbm_steps, 0))
+        t0 = time.perf_counter()
+        pool.map(_oracle_lbm_run, [(lbm_steps, r) for r in range(cores)])
+        lbm_wall = time.perf_counter() - t0
+    cells = 128 ** 3
     return {"value": cores * n * n_sub_all / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"{cores} independent replicas (one per core) of {n_sub_all} substeps of the "
                        f"full 400,040-particle sheet on 128^3 (FP64, serial C each)"),
             "seconds": wall,
             "one_core": {"value": n * n_sub / one, "cores": 1,
-                         "sample": f"{n_sub} substeps of the full sheet on one core", "seconds": one}}
+                         "sample": f"{n_sub} substeps of the full sheet on one core", "seconds": one},
+            "lbm_128": {"unit": "MLUPS", "one_core": cells * lbm_steps / lbm_one / 1e6,
+                        "all_cores": cores * cells * lbm_steps / lbm_wall / 1e6, "cores": cores,
+                        "sample": (f"{lbm_steps} FP64 oracle BGK steps of the 128^3 leaf-cluster "
+                                   f"lattice on one core, then one replica per core")}}
 
 
 # ------------------------------------------------------- reference arm ----
