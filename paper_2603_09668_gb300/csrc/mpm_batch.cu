@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(THREADS) k_batch_particles(BatchView A, int L)
 // warp stages its scene record in shared memory, so that the scene's
 // parameters are shared-memory operands, and the material is chosen per warp.
 template <bool VEC>
-__global__ void __launch_bounds__(PAIR_THREADS, 5) k_batch_pair(BatchView A, int L) {
+__global__ void __launch_bounds__(PAIR_THREADS, PAIR_MIN_CTAS) k_batch_pair(BatchView A, int L) {
     constexpr int WORDS = sizeof(BatchScene) / 4;
     __shared__ PairWarpSmem smem[PAIR_WARPS];
     __shared__ BatchScene scene[PAIR_WARPS];
@@ -642,7 +642,8 @@ static dw_status launch_substep(dw_mpm_batch h, const BatchView &A, const dw_bat
     const int T = c.threads;
     if (c.mode == DW_BATCH_PAIR && !final_ && !A.ox) {
         const unsigned ggrid = (unsigned)(c.ctas_per_sm * h->num_sms);
-        const unsigned pgrid = (unsigned)((h->n_items + 1) / 2);
+        // PAIR_WARPS halves of 128-particle work items per CTA
+        const unsigned pgrid = (unsigned)((2 * h->n_items + PAIR_WARPS - 1) / PAIR_WARPS);
         if (T == 256)
             DW_CUDA(launch_pdl(k_batch_grid<256>, ggrid, 256, s, A, k, L));
         else

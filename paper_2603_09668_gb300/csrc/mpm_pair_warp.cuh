@@ -28,6 +28,8 @@ namespace dw {
 //   the passes and tested after them.
 constexpr int PAIR_THREADS = 128;
 constexpr int PAIR_WARPS = PAIR_THREADS / 32;
+// resident CTAs per SM the launch bounds ask for: 96 registers per thread
+constexpr int PAIR_MIN_CTAS = 65536 / (96 * PAIR_THREADS);
 constexpr unsigned FULL = 0xffffffffu;
 
 template <bool VEC>

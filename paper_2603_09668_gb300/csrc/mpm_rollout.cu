@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS, 10) k_g2p2g(
 // FP32 instructions (pair_warp, mpm_pair_warp.cuh).
 // With OUT the output state goes to `out` (the recompute of a reverse segment).
 template <int MAT, bool STORE_VC, bool VEC, bool OUT = false>
-__global__ void __launch_bounds__(PAIR_THREADS, 5) k_g2p2g_pair(
+__global__ void __launch_bounds__(PAIR_THREADS, PAIR_MIN_CTAS) k_g2p2g_pair(
     MpmParams P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
     float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
     float4 *__restrict__ grid_next, int64_t n, int *err, ActiveBlocks ab_next, int *reset_count,
