@@ -293,11 +293,19 @@ def test_wind_layout_concatenates_the_scenes_wind_values():
     batch.close()
 
 
-def test_batch_segment_adjoint_matches_each_scene_alone():
+@pytest.mark.parametrize("p2g_mode", [B.P2G_WARP, B.P2G_AUTO])
+def test_batch_segment_adjoint_matches_each_scene_alone(p2g_mode):
     """Every scene's gradients (state, wind, E) from one batched segment
-    adjoint equal those of mpm_segment_adjoint on the scene alone, up to the
-    float atomics' summation order (relative L2 1e-4), and the batched tape
-    holds the same recomputed states."""
+    adjoint equal those of mpm_segment_adjoint on the scene alone, and the
+    batched tape holds the same recomputed states. The batched recompute runs
+    the one-particle-per-thread substep kernels: against the single-scene
+    adjoint with the same kernels (P2G_WARP) the results agree up to the
+    float atomics' summation order (relative L2 1e-4); against the
+    single-scene default (P2G_AUTO: the recompute on the paired kernel, whose
+    FFMA2 products round differently) the 10 recomputed substeps differ by
+    the cross-kernel rounding of the forward tests (1e-5 in x), which the
+    reverse pass carries into the gradients at up to a few 1e-4 (bound 1e-3)."""
+    tol = 1e-4 if p2g_mode == B.P2G_WARP else 1e-3
     scenes = small_scenes()
     n_sub = 10
     batch, gb, gw, gE, g_out, tape = batch_adjoint(scenes, n_sub)
@@ -307,7 +315,7 @@ def test_batch_segment_adjoint_matches_each_scene_alone():
     for s, (params, st, pinned, wind) in enumerate(scenes):
         sl = batch.scene_slice(s)
         ns = st[0].shape[1]
-        mpm = B.MPM.from_params(params, max_particles=ns)
+        mpm = B.MPM.from_params(params, max_particles=ns, p2g_mode=p2g_mode)
         g = dev_state(tuple(a[:, sl] for a in g_out))
         gw_s = torch.zeros(wind.size, dtype=torch.float32, device="cuda")
         gE_s = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -317,13 +325,14 @@ def test_batch_segment_adjoint_matches_each_scene_alone():
         mpm.device_status()
         ref = state_to_np(g)
         for name, a, b in zip("xvCF", gb, ref):
-            assert rel_l2(a[:, sl], b) <= 1e-4, (s, name, rel_l2(a[:, sl], b))
-        assert rel_l2(gw[woff[s]:woff[s + 1]], gw_s.cpu().numpy().ravel()) <= 1e-4, s
-        assert abs(gE[s] - gE_s.item()) <= 1e-4 * abs(gE_s.item()) + 1e-12, (s, gE[s], gE_s.item())
+            assert rel_l2(a[:, sl], b) <= tol, (s, name, rel_l2(a[:, sl], b))
+        assert rel_l2(gw[woff[s]:woff[s + 1]], gw_s.cpu().numpy().ravel()) <= tol, s
+        assert abs(gE[s] - gE_s.item()) <= tol * abs(gE_s.item()) + 1e-12, (s, gE[s], gE_s.item())
         # the last recomputed state of the segment, scene s's columns
         last = tape_np[(n_sub - 2) * 24 * n:(n_sub - 1) * 24 * n].reshape(24, n)[:, sl]
         last_s = tape_s.cpu().numpy()[(n_sub - 2) * 24 * ns:].reshape(24, ns)
-        assert np.abs(last[0:3] - last_s[0:3]).max() <= 1e-6, s  # positions
+        x_tol = 1e-6 if p2g_mode == B.P2G_WARP else CROSS["tol_xF"]
+        assert np.abs(last[0:3] - last_s[0:3]).max() <= x_tol, s  # positions
         mpm.close()
     batch.close()
 
