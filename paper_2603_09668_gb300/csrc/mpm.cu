@@ -38,16 +38,22 @@ __global__ void __launch_bounds__(GRID_THREADS) k_grid_update_active(
     int clear, ActiveBlocks ab) {
     pdl_wait();
     pdl_trigger();
+    const int nblk = ab.nb * ab.nb * ab.nb;  // entries of the list
+    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63, stride = gridDim.x * 4;
+    int e = blockIdx.x * 4 + sub;
+    // the first entry is read together with the count, not after it (an
+    // entry past the count is read but not used)
+    int b = e < nblk ? ab.list[e] : 0;
     const int count = *ab.count;
-    const int sub = threadIdx.x >> 6, lt = threadIdx.x & 63;
-    for (int e = blockIdx.x * 4 + sub; e < count; e += gridDim.x * 4) {
-        int b = ab.list[e];
+    for (; e < count; e += stride) {
+        const int bn = e + stride < count ? ab.list[e + stride] : 0;  // the next entry
         int i, j, k;
         if (active_node(P, ab.nb, b, lt, i, j, k)) {
             int64_t node = ((int64_t)k * P.N + j) * P.N + i;
             grid_node_update(P, wind, t, node, i, j, k, grid_mp, grid_v, clear);
         }
         if (clear && lt == 0) ab.flags[b] = 0;
+        b = bn;
     }
 }
 

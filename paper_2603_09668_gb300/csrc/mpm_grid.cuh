@@ -20,9 +20,10 @@ __device__ __forceinline__ void grid_node_update(const MpmParams &P, const WindD
                                                  float4 *__restrict__ grid_mp,
                                                  float4 *__restrict__ grid_v, int clear) {
     float4 mp = grid_mp[node];
+    // the wind taps are loaded together with (m, p), not after the test on m
+    const float3 a = wind_sample_dev(wind, i * P.dx, j * P.dx, k * P.dx, t);
     float4 out = make_float4(0.f, 0.f, 0.f, mp.x);
     if (mp.x > 0.0f && !sticky_node(P, i, j, k)) {
-        float3 a = wind_sample_dev(wind, i * P.dx, j * P.dx, k * P.dx, t);
         float inv_m = 1.0f / mp.x;
         out.x = mp.y * inv_m + P.dt * (P.gx + a.x);
         out.y = mp.z * inv_m + P.dt * (P.gy + a.y);

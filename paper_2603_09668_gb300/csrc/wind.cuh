@@ -78,7 +78,9 @@ __device__ __forceinline__ float3 wind_sample_dev(const WindDev &w, float px, fl
             int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
             float wt = wt_t * (cx ? tp.fr[0] : 1.0f - tp.fr[0]) *
                        (cy ? tp.fr[1] : 1.0f - tp.fr[1]) * (cz ? tp.fr[2] : 1.0f - tp.fr[2]);
-            if (wt == 0.0f) continue;
+            // every tap lies inside the field (wind_taps clamps the corner),
+            // so all 48 loads are issued without a branch; a zero weight adds
+            // a signed zero, which leaves the (never negative-zero) sum as it is
             int node = tp.base + dk * tp.st + cx * tp.sx + cy * tp.sy + cz * tp.sz;
             const float *v = w.values + 3 * (size_t)node;
             acc.x += wt * __ldg(v + 0);
