@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--substeps", type=int, default=1000)
+    ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
+                    help="substeps between particle re-sorts in the headline rollout")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["mpm", "lbm", "adjoint", "surrogate",
@@ -193,7 +195,7 @@ def run_ours(args):
     wind = B.WindField(torch.from_numpy(sc.wind).to(dev), sc.t_total)
     st0 = B.MpmState(*(torch.from_numpy(a).to(dev) for a in inputs.rest_state(sc.x)))
     pin0 = torch.from_numpy(sc.pinned).to(dev)
-    ro = Rollout(mpm, n, wind, args.substeps, sort_every=SORT_EVERY, with_pins=True)
+    ro = Rollout(mpm, n, wind, args.substeps, sort_every=args.sort_every, with_pins=True)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -265,7 +267,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel: per-kernel CUDA events over one
     # eager pass of the same rollout (same kernels, same inputs)
-    ro_eager = Rollout(mpm, n, wind, args.substeps, sort_every=SORT_EVERY, with_pins=True,
+    ro_eager = Rollout(mpm, n, wind, args.substeps, sort_every=args.sort_every, with_pins=True,
                        use_graph=False)
     mpm.profile_enable(4 * args.substeps + 64)
     flush.fill_(1.0)
@@ -282,7 +284,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles_per_gpu": n, "grid": sc.n_grid,
-                   "substeps_per_step": args.substeps, "sort_every": SORT_EVERY,
+                   "substeps_per_step": args.substeps, "sort_every": args.sort_every,
                    "material": "neo-hookean E=5e4 nu=0.3", "wind": "32^3 x 16 Fourier",
                    "l2": "flushed between timed steps (512 MB write)", "p2g_mode": args.p2g_mode,
                    "parallelism": f"replicas x{world}"},

@@ -216,10 +216,12 @@ DW_API dw_status mpm_sort(dw_mpm h, const dw_mpm_state *in, const dw_mpm_state *
  * hold the particles in a new order: `pinned` (device uint8[n] or NULL) is
  * permuted along, and ids (device int32[n], required when sort_every > 0) is
  * carried through the sorts (ids_out[k] = ids_in[perm[k]]), so filling it with
- * 0..n-1 beforehand yields each particle's original index. Between sorts the
- * G2P of one substep and the P2G of the next run fused in one kernel, which
- * keeps v and C in registers; the state is complete at every sort and at the
- * end. Uses the handle's second state buffer (max_particles). */
+ * 0..n-1 beforehand yields each particle's original index. The G2P of one
+ * substep and the P2G of the next run fused in one kernel, which keeps v and
+ * C in registers (the arrays v and C are written only by the last substep's
+ * G2P); a re-sort runs between two fused launches, after the P2G of the
+ * substep that follows it. The state is complete at the end. Uses the
+ * handle's second state buffer (max_particles). */
 DW_API dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *pinned, int32_t *ids,
                              const dw_wind_field *wind, float t0, int32_t n_substeps,
                              int32_t sort_every, dw_stream stream);

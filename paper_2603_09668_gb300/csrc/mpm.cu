@@ -343,14 +343,14 @@ __global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *
     int q = perm[k];
     ids_out[k] = ids_in ? ids_in[q] : q;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        xo[a * n + k] = x[a * n + q];
-        vo[a * n + k] = v[a * n + q];
-    }
+    for (int a = 0; a < 3; ++a) xo[a * n + k] = x[a * n + q];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        Co[c * n + k] = C[c * n + q];
-        Fo[c * n + k] = F[c * n + q];
+    for (int c = 0; c < 9; ++c) Fo[c * n + k] = F[c * n + q];
+    if (v) {  // v and C may be left out (NULL)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vo[a * n + k] = v[a * n + q];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Co[c * n + k] = C[c * n + q];
     }
     if (pin_in) pin_out[k] = pin_in[q];
 }
@@ -740,7 +740,7 @@ namespace dw {
 
 dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_state *out,
                          const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
-                         int32_t *ids_out, cudaStream_t s) {
+                         int32_t *ids_out, cudaStream_t s, bool with_vc) {
     int64_t n = in->n;
     if (n == 0) return DW_OK;
     ProfScope ps(h, DW_K_SORT, s);
@@ -751,9 +751,9 @@ dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_stat
     if (st != DW_OK) return st;
     k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, h->perm);
     DW_LAUNCHED("k_sort_scatter");
-    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in->x, in->v, in->C, in->F, pinned_in,
-                                               ids_in, out->x, out->v, out->C, out->F, pinned_out,
-                                               ids_out);
+    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in->x, with_vc ? in->v : nullptr,
+                                               with_vc ? in->C : nullptr, in->F, pinned_in, ids_in,
+                                               out->x, out->v, out->C, out->F, pinned_out, ids_out);
     DW_LAUNCHED("k_permute");
     return DW_OK;
 }

@@ -16,12 +16,13 @@
 // gathers the new grid velocities (G2P of substep k, loads through L2 because
 // other CTAs wrote them in phase A), updates x and F, and scatters itself into
 // its scene's cleared grid (P2G of substep k + 1), appending newly touched
-// blocks to the other list. The last substep before a sort (and of the
-// rollout) stores v and C instead of scattering. Split mode runs the phases
-// as two kernels with programmatic dependent launch. Pair mode is split mode
-// whose scattering phase B is the two-particles-per-thread body of
+// blocks to the other list. The last substep of the rollout stores v and C
+// instead of scattering; a re-sort runs between two launches (after the P2G
+// of the substep that follows it, v and C not kept). Split mode runs the
+// phases as two kernels with programmatic dependent launch. Pair mode is
+// split mode whose scattering phase B is the two-particles-per-thread body of
 // mpm_rollout (k_batch_pair: 64 particles of one scene per warp); the last
-// substep before a sort, and the recompute of a reverse segment, run the
+// substep of the rollout, and the recompute of a reverse segment, run the
 // split-mode kernels.
 //
 // The sort is one counting sort over all scenes: scene s's keys are offset by
@@ -613,9 +614,11 @@ static BatchView view_of(dw_mpm_batch h, const dw_mpm_state &s, const uint8_t *p
     return A;
 }
 
+// with_vc = false leaves v and C of `out` unwritten (a rollout between fused
+// launches, where v and C are not kept).
 static dw_status batch_sort(dw_mpm_batch h, const dw_mpm_state &in, const dw_mpm_state &out,
                             const uint8_t *pin_in, uint8_t *pin_out, const int32_t *ids_in,
-                            int32_t *ids_out, cudaStream_t s) {
+                            int32_t *ids_out, cudaStream_t s, bool with_vc = true) {
     const int64_t n = h->n_total;
     DW_CUDA(cudaMemsetAsync(h->key_counts, 0, sizeof(int) * (size_t)(h->total_keys + 1), s));
     k_batch_sort_keys<<<h->n_items, BATCH_ITEM, 0, s>>>(view_of(h, in, pin_in), h->keys,
@@ -625,7 +628,8 @@ static dw_status batch_sort(dw_mpm_batch h, const dw_mpm_state &in, const dw_mpm
     if (st != DW_OK) return st;
     k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->key_counts, h->perm);
     DW_LAUNCHED("k_sort_scatter");
-    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in.x, in.v, in.C, in.F, pin_in, ids_in,
+    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in.x, with_vc ? in.v : nullptr,
+                                               with_vc ? in.C : nullptr, in.F, pin_in, ids_in,
                                                out.x, out.v, out.C, out.F, pin_out, ids_out);
     DW_LAUNCHED("k_permute");
     return DW_OK;
@@ -688,29 +692,41 @@ static dw_status enqueue_rollout(dw_mpm_batch h, const dw_mpm_state *state, uint
     dw_mpm_state cur = *state, oth = state_view(h->roll_state, n);
     uint8_t *cur_pin = pinned, *oth_pin = pinned ? h->roll_pinned : nullptr;
     int32_t *cur_ids = ids, *oth_ids = h->roll_ids;
-    const int seg = sort_every > 0 ? sort_every : n_substeps;
+    auto resort = [&](bool with_vc) {
+        dw_status r = batch_sort(h, cur, oth, cur_pin, oth_pin, cur_ids, oth_ids, s, with_vc);
+        std::swap(cur, oth);
+        std::swap(cur_pin, oth_pin);
+        std::swap(cur_ids, oth_ids);
+        return r;
+    };
+    // pair kernel vector loads: every work item starts at a multiple of 4
+    // particles and the arrays are 16-byte aligned
+    auto vec_of = [&](const dw_mpm_state &q) {
+        return h->items_aligned4 &&
+               ((reinterpret_cast<uintptr_t>(q.x) | reinterpret_cast<uintptr_t>(q.F)) % 16 == 0);
+    };
+    if (sort_every > 0) {
+        dw_status st = resort(true);  // the input state's v and C feed the first P2G
+        if (st != DW_OK) return st;
+    }
+    BatchView A = view_of(h, cur, cur_pin);
+    bool vec = vec_of(cur);
     int L = 0;
-    for (int k0 = 0; k0 < n_substeps; k0 += seg) {
-        const int len = std::min(seg, n_substeps - k0);
-        if (sort_every > 0) {
-            dw_status st = batch_sort(h, cur, oth, cur_pin, oth_pin, cur_ids, oth_ids, s);
+    k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, L);
+    DW_LAUNCHED("k_batch_p2g");
+    for (int k = 0; k < n_substeps; ++k) {
+        const bool final_ = k + 1 == n_substeps;
+        dw_status st = launch_substep(h, A, c, k_base + k, L, final_, s, vec);
+        if (st != DW_OK) return st;
+        if (final_) break;
+        L = 1 - L;
+        // re-sort between two fused launches (the P2G of substep k + 1 has
+        // run in the old order; v and C are not kept between them)
+        if (sort_every > 0 && (k + 1) % sort_every == 0) {
+            st = resort(false);
             if (st != DW_OK) return st;
-            std::swap(cur, oth);
-            std::swap(cur_pin, oth_pin);
-            std::swap(cur_ids, oth_ids);
-        }
-        const BatchView A = view_of(h, cur, cur_pin);
-        // pair kernel vector loads: every work item starts at a multiple of 4
-        // particles and the arrays are 16-byte aligned
-        const bool vec = h->items_aligned4 &&
-                         ((reinterpret_cast<uintptr_t>(cur.x) | reinterpret_cast<uintptr_t>(cur.F)) % 16 == 0);
-        k_batch_p2g<<<h->n_items, BATCH_ITEM, 0, s>>>(A, L);
-        DW_LAUNCHED("k_batch_p2g");
-        for (int j = 0; j < len; ++j) {
-            const bool final_ = j + 1 == len;
-            dw_status st = launch_substep(h, A, c, k_base + k0 + j, L, final_, s, vec);
-            if (st != DW_OK) return st;
-            if (!final_) L = 1 - L;
+            A = view_of(h, cur, cur_pin);
+            vec = vec_of(cur);
         }
     }
     if (cur.x != state->x) {  // an odd number of sorts: the result is in the workspace

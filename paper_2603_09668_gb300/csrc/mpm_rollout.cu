@@ -197,64 +197,74 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
     dw_mpm_state cur = *state, oth = view_of(h->roll_state, n);
     uint8_t *cur_pin = pinned, *oth_pin = pinned ? h->roll_pinned : nullptr;
     int32_t *cur_ids = ids, *oth_ids = h->roll_ids;
-    const int seg = sort_every > 0 ? sort_every : n_substeps;
     const unsigned pgrid = grid_for(n, P2G_WARP_THREADS);
     // the fused kernel: two particles per thread (AUTO, PAIR) or one (the other strategies)
     const bool pair = h->desc.p2g_mode == DW_P2G_AUTO || h->desc.p2g_mode == DW_P2G_PAIR;
     const unsigned pair_grid = grid_for(n, 2 * PAIR_THREADS);
     int L = 0;  // active list consumed by the next grid update
-    for (int k0 = 0; k0 < n_substeps; k0 += seg) {
-        const int len = min(seg, n_substeps - k0);
-        if (sort_every > 0) {
-            st = sort_particles(h, &cur, &oth, cur_pin, oth_pin, cur_ids, oth_ids, s);
-            if (st != DW_OK) return st;
-            std::swap(cur, oth);
-            std::swap(cur_pin, oth_pin);
-            std::swap(cur_ids, oth_ids);
-        }
-        // vector paths: float2 pairs of x and F, 16-byte pieces of F (n a
-        // multiple of 4, 16-byte aligned arrays)
-        const bool pair_vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cur.x) |
-                                                reinterpret_cast<uintptr_t>(cur.F)) % 16 == 0);
-        {
-            ProfScope ps(h, DW_K_P2G, s);
-            st = launch_p2g(h->desc.p2g_mode, h->P, cur.x, cur.v, cur.C, cur.F, n, h->grid_mp,
-                            h->err, active_blocks(h, L), s);
-        }
+    auto resort = [&](bool with_vc) {
+        dw_status r = sort_particles(h, &cur, &oth, cur_pin, oth_pin, cur_ids, oth_ids, s, with_vc);
+        std::swap(cur, oth);
+        std::swap(cur_pin, oth_pin);
+        std::swap(cur_ids, oth_ids);
+        return r;
+    };
+    if (sort_every > 0) {
+        st = resort(true);  // the input state's v and C feed the first P2G
         if (st != DW_OK) return st;
-        for (int j = 0; j < len; ++j) {
-            const float t = fmaf((float)(k0 + j), h->P.dt, t0);  // as the batched kernels
-            {
-                ProfScope ps(h, DW_K_GRID, s);
-                DW_CUDA(launch_pdl(k_grid_update_active, GRID_CTAS, GRID_THREADS, s, h->P, wd, t,
-                                   h->grid_mp, h->grid_v, 1, active_blocks(h, L)));
-            }
-            if (j + 1 < len) {
-                ProfScope ps(h, DW_K_G2P2G, s);
-                if (pair) {
-                    auto kern = h->P.material == DW_NEOHOOKEAN
-                                    ? (pair_vec ? k_g2p2g_pair<DW_NEOHOOKEAN, false, true>
-                                                : k_g2p2g_pair<DW_NEOHOOKEAN, false, false>)
-                                    : (pair_vec ? k_g2p2g_pair<DW_FIXED_COROTATED, false, true>
-                                                : k_g2p2g_pair<DW_FIXED_COROTATED, false, false>);
-                    DW_CUDA(launch_pdl(kern, pair_grid, PAIR_THREADS, s, h->P, cur.x, cur.v, cur.C,
-                                       cur.F, (const uint8_t *)cur_pin, (const float4 *)h->grid_v,
-                                       h->grid_mp, n, h->err, active_blocks(h, 1 - L),
-                                       h->block_count + L, PairOut{}));
-                } else {
-                    DW_CUDA(launch_pdl(k_g2p2g<false>, pgrid, P2G_WARP_THREADS, s, h->P, cur.x,
-                                       cur.v, cur.C, cur.F, (const uint8_t *)cur_pin,
-                                       (const float4 *)h->grid_v, h->grid_mp, n, h->err,
-                                       active_blocks(h, 1 - L), h->block_count + L));
-                }
-                L = 1 - L;
+    }
+    {
+        ProfScope ps(h, DW_K_P2G, s);
+        st = launch_p2g(h->desc.p2g_mode, h->P, cur.x, cur.v, cur.C, cur.F, n, h->grid_mp, h->err,
+                        active_blocks(h, L), s);
+    }
+    if (st != DW_OK) return st;
+    for (int k = 0; k < n_substeps; ++k) {
+        const float t = fmaf((float)k, h->P.dt, t0);  // as the batched kernels
+        {
+            ProfScope ps(h, DW_K_GRID, s);
+            DW_CUDA(launch_pdl(k_grid_update_active, GRID_CTAS, GRID_THREADS, s, h->P, wd, t,
+                               h->grid_mp, h->grid_v, 1, active_blocks(h, L)));
+        }
+        if (k + 1 == n_substeps) {
+            ProfScope ps(h, DW_K_G2P, s);
+            DW_CUDA(launch_pdl(k_g2p, grid_for(n, 128), 128, s, h->P, (const float *)cur.x,
+                               (const float *)cur.F, (const uint8_t *)cur_pin,
+                               (const float4 *)h->grid_v, cur.x, cur.v, cur.C, cur.F, n, h->err,
+                               h->block_count + L));
+            break;
+        }
+        {
+            ProfScope ps(h, DW_K_G2P2G, s);
+            if (pair) {
+                // vector paths: float2 pairs of x and F, 16-byte pieces of F (n a
+                // multiple of 4, 16-byte aligned arrays)
+                const bool pair_vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cur.x) |
+                                                        reinterpret_cast<uintptr_t>(cur.F)) % 16 == 0);
+                auto kern = h->P.material == DW_NEOHOOKEAN
+                                ? (pair_vec ? k_g2p2g_pair<DW_NEOHOOKEAN, false, true>
+                                            : k_g2p2g_pair<DW_NEOHOOKEAN, false, false>)
+                                : (pair_vec ? k_g2p2g_pair<DW_FIXED_COROTATED, false, true>
+                                            : k_g2p2g_pair<DW_FIXED_COROTATED, false, false>);
+                DW_CUDA(launch_pdl(kern, pair_grid, PAIR_THREADS, s, h->P, cur.x, cur.v, cur.C,
+                                   cur.F, (const uint8_t *)cur_pin, (const float4 *)h->grid_v,
+                                   h->grid_mp, n, h->err, active_blocks(h, 1 - L),
+                                   h->block_count + L, PairOut{}));
             } else {
-                ProfScope ps(h, DW_K_G2P, s);
-                DW_CUDA(launch_pdl(k_g2p, grid_for(n, 128), 128, s, h->P, (const float *)cur.x,
-                                   (const float *)cur.F, (const uint8_t *)cur_pin,
-                                   (const float4 *)h->grid_v, cur.x, cur.v, cur.C, cur.F, n,
-                                   h->err, h->block_count + L));
+                DW_CUDA(launch_pdl(k_g2p2g<false>, pgrid, P2G_WARP_THREADS, s, h->P, cur.x,
+                                   cur.v, cur.C, cur.F, (const uint8_t *)cur_pin,
+                                   (const float4 *)h->grid_v, h->grid_mp, n, h->err,
+                                   active_blocks(h, 1 - L), h->block_count + L));
             }
+        }
+        L = 1 - L;
+        // Re-sort between two fused launches: the P2G of substep k + 1 has
+        // already run (in the old order; the grid does not depend on it), so
+        // the sorted order serves the G2P of k + 1 and every P2G after it.
+        // v and C are not kept between fused launches, so none is lost.
+        if (sort_every > 0 && (k + 1) % sort_every == 0) {
+            st = resort(false);
+            if (st != DW_OK) return st;
         }
     }
     if (cur.x != state->x) {  // an odd number of sorts: the result is in the workspace

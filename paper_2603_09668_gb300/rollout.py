@@ -32,15 +32,13 @@ class Rollout:
 
     @property
     def kernel_launches(self):
-        """Kernels of one run: per segment of L substeps a sort (6 kernels when
-        sorting), one P2G, L grid updates, L - 1 fused G2P+P2G and one G2P."""
-        seg = self.sort_every if self.sort_every > 0 else self.n_substeps
-        total, k0 = 0, 0
-        while k0 < self.n_substeps:
-            L = min(seg, self.n_substeps - k0)
-            total += (6 if self.sort_every > 0 else 0) + 2 * L + 1
-            k0 += seg
-        return total
+        """Kernels of one run: one P2G, a grid update per substep, a fused
+        G2P+P2G per substep but the last, one G2P, and 6 kernels per sort (at
+        the start and every sort_every substeps)."""
+        if self.n_substeps == 0:
+            return 0
+        sorts = -(-self.n_substeps // self.sort_every) if self.sort_every > 0 else 0
+        return 1 + 2 * self.n_substeps + 6 * sorts
 
     def _issue(self):
         self.mpm.rollout(self.state, self.pins, self.ids, self.wind, self.t0, self.n_substeps,
