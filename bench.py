@@ -3,7 +3,7 @@
 Headline workload (one "step"): the flag-like sheet at full size - 400,040
 particles, 128^3 grid, Neo-Hookean E = 5e4, pinned edge, 32^3 x 16 Fourier
 wind field, dt = 5e-5 - advanced by 1000 MLS-MPM substeps with a re-sort of
-the particles by cell every 20 substeps, as one CUDA-graph replay. The metric
+the particles by cell every 15 substeps, as one CUDA-graph replay. The metric
 is MPM particle-substeps per second over all ranks (weak scaling: every rank
 runs its own scene). Further measurements on the same run go into "metrics":
 the MPM forward+adjoint rollout with checkpointing (100k-particle sheet on
@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MPM particle-substeps/s fwd+adj, LBM MLUPS; surrogate vs plain LBM at stated error"
 UNIT = "particle-substeps/s"
 WORKLOAD = "sheet400k_128^3_1000substeps_fwd"
-SORT_EVERY = 20
+SORT_EVERY = 15
 
 
 def parse():

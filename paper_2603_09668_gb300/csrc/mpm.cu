@@ -255,17 +255,24 @@ __global__ void k_rev_p2g(MpmParams P, const float *__restrict__ x, const float 
 
 // ------------------------------------------------------------------ sort --
 
+// Launched with whole warps (blocks of 256 threads): one count atomic per
+// distinct key of a warp (between re-sorts most particles keep their cell, so
+// a warp holds a few keys).
 __global__ void k_sort_keys(MpmParams P, int nb, const float *__restrict__ x, int64_t n,
                             int *__restrict__ keys, int *__restrict__ counts) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int k = cell_key(P, nb, x[p], x[n + p], x[2 * n + p]);
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = p < n;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (!ok) return;
+    const int k = cell_key(P, nb, x[p], x[n + p], x[2 * n + p]);
     keys[p] = k;
-    atomicAdd(&counts[k], 1);
+    const unsigned peers = __match_any_sync(act, k);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[k], __popc(peers));
 }
 
-// Exclusive scan, three phases: per-block scan with block totals, scan of the
-// totals (single block, loops over chunks), add-back.
+// Exclusive scan, three phases: per-block scan of SCAN_ITEMS consecutive
+// elements per thread with block totals, scan of the totals (single block,
+// loops over chunks), add-back.
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &total) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -296,13 +303,53 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &
     return res;
 }
 
+// SCAN_ITEMS elements of one thread: 16-byte pieces when the whole run lies
+// inside the array (data is 16-byte aligned, runs start at multiples of 8).
+__device__ __forceinline__ void scan_load(const int *data, int64_t len, int64_t i0, int (&v)[SCAN_ITEMS]) {
+    if (i0 + SCAN_ITEMS <= len) {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j += 4) {
+            const int4 q = *reinterpret_cast<const int4 *>(data + i0 + j);
+            v[j] = q.x;
+            v[j + 1] = q.y;
+            v[j + 2] = q.z;
+            v[j + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) v[j] = i0 + j < len ? data[i0 + j] : 0;
+    }
+}
+
+__device__ __forceinline__ void scan_store(int *data, int64_t len, int64_t i0, const int (&v)[SCAN_ITEMS]) {
+    if (i0 + SCAN_ITEMS <= len) {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j += 4)
+            *reinterpret_cast<int4 *>(data + i0 + j) = make_int4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j)
+            if (i0 + j < len) data[i0 + j] = v[j];
+    }
+}
+
 __global__ void k_scan_blocks(int *__restrict__ data, int64_t len, int *__restrict__ block_sums) {
     __shared__ int sw[33];
-    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    int v = i < len ? data[i] : 0;
+    const int64_t i0 = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    scan_load(data, len, i0, v);
+    int run = 0;  // exclusive scan of the thread's elements
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const int t = v[j];
+        v[j] = run;
+        run += t;
+    }
     int total;
-    int ex = block_exclusive_scan(v, sw, total);
-    if (i < len) data[i] = ex;
+    const int ex = block_exclusive_scan(run, sw, total);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) v[j] += ex;
+    scan_store(data, len, i0, v);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
@@ -320,16 +367,31 @@ __global__ void k_scan_sums(int *__restrict__ sums, int64_t nblocks) {
 }
 
 __global__ void k_scan_add(int *__restrict__ data, int64_t len, const int *__restrict__ sums) {
-    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    if (i < len) data[i] += sums[blockIdx.x];
+    const int64_t i0 = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const int add = sums[blockIdx.x];
+    int v[SCAN_ITEMS];
+    scan_load(data, len, i0, v);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) v[j] += add;
+    scan_store(data, len, i0, v);
 }
 
+// Launched with whole warps (blocks of 256 threads): the lanes of a warp that
+// share a key take consecutive positions of its range, in lane order, from
+// one offset atomic.
 __global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
                                int *__restrict__ perm) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int pos = atomicAdd(&offsets[keys[p]], 1);
-    perm[pos] = (int)p;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = p < n;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (!ok) return;
+    const int key = keys[p];
+    const unsigned peers = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&offsets[key], __popc(peers));
+    base = __shfl_sync(act, base, leader);
+    perm[base + __popc(peers & ((1u << lane) - 1u))] = (int)p;
 }
 
 __global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *__restrict__ x,
@@ -356,7 +418,11 @@ __global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *
 }
 
 dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cudaStream_t st) {
-    int64_t nblocks = (len + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    int64_t nblocks = (len + SCAN_TILE - 1) / SCAN_TILE;
+    if (((uintptr_t)data & 15) != 0) {
+        set_error("scan data must be 16-byte aligned");
+        return DW_ERR_ARG;
+    }
     if (nblocks > tmp_len) {
         set_error("scan workspace too small");
         return DW_ERR_ARG;

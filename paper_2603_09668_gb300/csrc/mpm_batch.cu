@@ -322,15 +322,19 @@ __global__ void __launch_bounds__(BATCH_ITEM) k_batch_p2g(BatchView A, int L) {
 }
 
 // Sort keys of every scene, offset per scene, counted into counts.
+// One count atomic per distinct key of a warp.
 __global__ void __launch_bounds__(BATCH_ITEM) k_batch_sort_keys(BatchView A, int *__restrict__ keys,
                                                                 int *__restrict__ counts) {
     const int4 item = A.items[blockIdx.x];
-    if ((int)threadIdx.x >= item.z) return;
+    const bool ok = (int)threadIdx.x < item.z;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (!ok) return;
     const BatchScene &S = A.scenes[item.x];
     const int64_t p = (int64_t)item.y + threadIdx.x, n = A.n;
     const int key = S.key_offset + cell_key(S.P, S.nb, A.x[p], A.x[n + p], A.x[2 * n + p]);
     keys[p] = key;
-    atomicAdd(&counts[key], 1);
+    const unsigned peers = __match_any_sync(act, key);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
 }
 
 // ---------------------------------------------------------------- reverse --

@@ -134,6 +134,8 @@ dw_status segment_recompute(MpmHandle *h, const dw_mpm_state *start, float *tape
 
 // particle sort (mpm.cu): counting sort by cell key, keys already counted
 constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 8;                         // consecutive elements per scan thread
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;    // elements per scan block
 __global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
                                int *__restrict__ perm);
 __global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *__restrict__ x,

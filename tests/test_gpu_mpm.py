@@ -320,7 +320,8 @@ def test_rollout_matches_oracle_and_substep_loop(n_sub, sort_every):
 
 def test_rollout_sheet_full_size_positions_within_1e4():
     """The flag-like sheet at full size, 100 substeps through mpm_rollout with
-    re-sorting every 20, against the FP64 oracle on every particle."""
+    re-sorting every 15 (the bench's launch sequence), against the FP64 oracle
+    on every particle."""
     sc = inputs.sheet_scene(n_substeps=100)
     params = sc.params()
     st = inputs.rest_state(sc.x)
@@ -328,7 +329,7 @@ def test_rollout_sheet_full_size_positions_within_1e4():
     s = state_to_dev(st)
     pin = to_dev(sc.pinned)
     ids = torch.arange(sc.n, dtype=torch.int32, device="cuda")
-    mpm.rollout(s, pin, ids, wind_dev(sc.wind, sc.t_total), 0.0, 100, 20)
+    mpm.rollout(s, pin, ids, wind_dev(sc.wind, sc.t_total), 0.0, 100, 15)
     mpm.device_status()
     ref = oracle.mpm_rollout(params, f64(st), sc.wind_tuple(), 0.0, 100, sc.pinned)
     idx = ids.cpu().numpy()
