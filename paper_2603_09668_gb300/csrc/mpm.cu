@@ -272,7 +272,8 @@ __global__ void k_sort_keys(MpmParams P, int nb, const float *__restrict__ x, in
 
 // Exclusive scan, three phases: per-block scan of SCAN_ITEMS consecutive
 // elements per thread with block totals, scan of the totals (single block,
-// loops over chunks), add-back.
+// loops over chunks), add-back; the last two are one launch for at most
+// SCAN_BLOCK blocks.
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &total) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -376,6 +377,21 @@ __global__ void k_scan_add(int *__restrict__ data, int64_t len, const int *__res
     scan_store(data, len, i0, v);
 }
 
+// The add-back for at most SCAN_BLOCK blocks, with the scan of the totals
+// folded in: block b sums the totals of blocks 0 .. b - 1 itself.
+__global__ void k_scan_add_prefix(int *__restrict__ data, int64_t len, const int *__restrict__ sums) {
+    __shared__ int sw[33];
+    const int b = blockIdx.x;
+    int add;
+    block_exclusive_scan((int)threadIdx.x < b ? sums[threadIdx.x] : 0, sw, add);
+    const int64_t i0 = (int64_t)b * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    scan_load(data, len, i0, v);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) v[j] += add;
+    scan_store(data, len, i0, v);
+}
+
 // Launched with whole warps (blocks of 256 threads): the lanes of a warp that
 // share a key take consecutive positions of its range, in lane order, from
 // one offset atomic.
@@ -428,8 +444,12 @@ dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cuda
         return DW_ERR_ARG;
     }
     k_scan_blocks<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, tmp);
-    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(tmp, nblocks);
-    k_scan_add<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, tmp);
+    if (nblocks <= SCAN_BLOCK) {  // one thread per block total: two launches
+        k_scan_add_prefix<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, tmp);
+    } else {
+        k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(tmp, nblocks);
+        k_scan_add<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(data, len, tmp);
+    }
     DW_LAUNCHED("exclusive scan");
     return DW_OK;
 }

@@ -204,17 +204,14 @@ __device__ __forceinline__ void pair_warp(
         }
         cp_async_commit();
     }
-    pdl_wait();
-    pdl_trigger();
-    if (reset_count) *reset_count = 0;
-    const unsigned vmask = __ballot_sync(FULL, v0);
-    if (vmask == 0) return;  // the whole warp lies beyond n
     const int N = P.N;
 
     // ---------------------------------------------------------------- G2P
     float2 vn[3], Cn[9];
     bool g0ok, g1ok;
     {
+        // The stencils and the warp's box depend on x alone, so they are
+        // computed before the dependency wait; the grid is read after it.
         Stencil2 s;
         stencil2(P, xp, s, g0ok, g1ok);
         g0ok = g0ok && v0;
@@ -229,6 +226,11 @@ __device__ __forceinline__ void pair_warp(
         const int ex = hi[0] - lo[0] + 3, ey = hi[1] - lo[1] + 3, ez = hi[2] - lo[2] + 3;
         const bool any = lo[0] <= hi[0];
         const int vol = any ? ex * ey * ez : 0;
+        pdl_wait();
+        pdl_trigger();
+        if (reset_count) *reset_count = 0;
+        const unsigned vmask = __ballot_sync(FULL, v0);
+        if (vmask == 0) return;  // the whole warp lies beyond n
         if (any && vol <= BOX_MAX) {
             // stage the box (lanes stride over its nodes), then read it per particle
             const int exy = ex * ey;

@@ -33,12 +33,17 @@ class Rollout:
     @property
     def kernel_launches(self):
         """Kernels of one run: one P2G, a grid update per substep, a fused
-        G2P+P2G per substep but the last, one G2P, and 6 kernels per sort (at
-        the start and every sort_every substeps)."""
+        G2P+P2G per substep but the last, one G2P, and per sort (at the start
+        and every sort_every substeps) the key, scatter and permute kernels
+        and a scan of the 64 nb^3 cell counters (nb = ceil(n_grid / 4)): two
+        kernels for at most 1024 scan blocks of 8192 counters, else three."""
         if self.n_substeps == 0:
             return 0
         sorts = -(-self.n_substeps // self.sort_every) if self.sort_every > 0 else 0
-        return 1 + 2 * self.n_substeps + 6 * sorts
+        nb = (self.mpm.n_grid + 3) // 4
+        scan_blocks = -(-64 * nb ** 3 // 8192)
+        per_sort = 3 + (2 if scan_blocks <= 1024 else 3)
+        return 1 + 2 * self.n_substeps + per_sort * sorts
 
     def _issue(self):
         self.mpm.rollout(self.state, self.pins, self.ids, self.wind, self.t0, self.n_substeps,
