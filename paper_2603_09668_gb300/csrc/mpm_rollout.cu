@@ -8,8 +8,11 @@
 // zeroed grid of substep k + 1 (P2G) while v and C are still in registers.
 // Per inner substep the particle arrays see one read and one write of x and F
 // (96 B per particle) instead of the four arrays of the unfused kernels.
-// Every `sort_every` substeps the particles are re-sorted by cell; the state
-// is complete (x, v, C, F written) at those boundaries and at the end.
+// Every `sort_every` substeps the particles are re-sorted by cell between two
+// fused launches (the P2G of the next substep has run in the old order; the
+// grid does not depend on the order), moving x, F, pinned and ids: v and C
+// are written only by the G2P of the last substep, where the state is
+// complete.
 #include <limits.h>
 #include <math.h>
 
