@@ -72,6 +72,28 @@ def test_forward_matches_oracle(n):
     s.close()
 
 
+def test_inference_pass_matches_the_layer_kernels_at_64():
+    """At the 128^3 lattice's coarse size (64^3: every CTA owns 13-14 output
+    slices, some across two tiles) the one-launch inference pass equals the
+    per-layer kernels: the same tiles, the same arithmetic."""
+    n = 64
+    p = random_params(seed=11)
+    feats = random_features(n, seed=12)
+    s = B.Surrogate(n)
+    s.set_params(to_dev(p))
+    s.set_features(to_dev(feats))
+    out = torch.empty((n ** 3, 16), device="cuda")
+    s.forward(out)
+    inf = torch.empty_like(out)
+    for _ in range(3):
+        s.forward(inf, keep_activations=False)
+    s.device_status()
+    a, b = inf.cpu().numpy(), out.cpu().numpy()
+    assert np.isfinite(a).all() and np.abs(b).max() > 0
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), np.abs(a - b).max()
+    s.close()
+
+
 def test_backward_matches_oracle():
     n = 16
     p = random_params(seed=3)
