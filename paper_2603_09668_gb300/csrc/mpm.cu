@@ -392,11 +392,19 @@ __global__ void k_scan_add_prefix(int *__restrict__ data, int64_t len, const int
     scan_store(data, len, i0, v);
 }
 
-// Launched with whole warps (blocks of 256 threads): the lanes of a warp that
-// share a key take consecutive positions of its range, in lane order, from
-// one offset atomic.
-__global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
-                               int *__restrict__ perm) {
+// The scatter and the permutation in one pass (launched with whole warps,
+// blocks of 256 threads): particle p, at position pos of its key's range
+// (the lanes of a warp that share a key take consecutive positions in lane
+// order from one offset atomic), moves its rows to pos of the output arrays;
+// ids_out[pos] = ids_in[p] (p without ids_in). v and C may be left out
+// (NULL).
+__global__ void k_sort_move(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
+                            const float *__restrict__ x, const float *__restrict__ v,
+                            const float *__restrict__ C, const float *__restrict__ F,
+                            const uint8_t *__restrict__ pin_in, const int *__restrict__ ids_in,
+                            float *__restrict__ xo, float *__restrict__ vo, float *__restrict__ Co,
+                            float *__restrict__ Fo, uint8_t *__restrict__ pin_out,
+                            int *__restrict__ ids_out) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = p < n;
     const unsigned act = __ballot_sync(0xffffffffu, ok);
@@ -407,30 +415,19 @@ __global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__r
     int base = 0;
     if (lane == leader) base = atomicAdd(&offsets[key], __popc(peers));
     base = __shfl_sync(act, base, leader);
-    perm[base + __popc(peers & ((1u << lane) - 1u))] = (int)p;
-}
-
-__global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *__restrict__ x,
-                          const float *__restrict__ v, const float *__restrict__ C,
-                          const float *__restrict__ F, const uint8_t *__restrict__ pin_in,
-                          const int *__restrict__ ids_in, float *__restrict__ xo,
-                          float *__restrict__ vo, float *__restrict__ Co, float *__restrict__ Fo,
-                          uint8_t *__restrict__ pin_out, int *__restrict__ ids_out) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int q = perm[k];
-    ids_out[k] = ids_in ? ids_in[q] : q;
+    const int64_t k = base + __popc(peers & ((1u << lane) - 1u));
+    ids_out[k] = ids_in ? ids_in[p] : (int)p;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) xo[a * n + k] = x[a * n + q];
+    for (int a = 0; a < 3; ++a) xo[a * n + k] = x[a * n + p];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) Fo[c * n + k] = F[c * n + q];
-    if (v) {  // v and C may be left out (NULL)
+    for (int c = 0; c < 9; ++c) Fo[c * n + k] = F[c * n + p];
+    if (v) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) vo[a * n + k] = v[a * n + q];
+        for (int a = 0; a < 3; ++a) vo[a * n + k] = v[a * n + p];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) Co[c * n + k] = C[c * n + q];
+        for (int c = 0; c < 9; ++c) Co[c * n + k] = C[c * n + p];
     }
-    if (pin_in) pin_out[k] = pin_in[q];
+    if (pin_in) pin_out[k] = pin_in[p];
 }
 
 dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cudaStream_t st) {
@@ -525,7 +522,6 @@ extern "C" dw_status mpm_create(const dw_mpm_desc *desc, dw_mpm *out) {
     DW_ALLOC(h->pscratch, sizeof(float) * 12 * (size_t)cap);
     DW_ALLOC(h->err, sizeof(int));
     DW_ALLOC(h->keys, sizeof(int) * (size_t)cap);
-    DW_ALLOC(h->perm, sizeof(int) * (size_t)cap);
     DW_ALLOC(h->counts, sizeof(int) * (size_t)(h->n_keys + 1));
     DW_ALLOC(h->scan_tmp, sizeof(int) * (size_t)h->scan_tmp_len);
     const size_t nblk = (size_t)h->nb * h->nb * h->nb;
@@ -561,7 +557,6 @@ extern "C" dw_status mpm_destroy(dw_mpm h) {
     cudaFree(h->pscratch);
     cudaFree(h->err);
     cudaFree(h->keys);
-    cudaFree(h->perm);
     cudaFree(h->counts);
     cudaFree(h->scan_tmp);
     cudaFree(h->block_flag);
@@ -835,12 +830,11 @@ dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_stat
     DW_LAUNCHED("k_sort_keys");
     dw_status st = exclusive_scan(h->counts, h->n_keys, h->scan_tmp, h->scan_tmp_len, s);
     if (st != DW_OK) return st;
-    k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, h->perm);
-    DW_LAUNCHED("k_sort_scatter");
-    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in->x, with_vc ? in->v : nullptr,
-                                               with_vc ? in->C : nullptr, in->F, pinned_in, ids_in,
-                                               out->x, out->v, out->C, out->F, pinned_out, ids_out);
-    DW_LAUNCHED("k_permute");
+    k_sort_move<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, in->x,
+                                                 with_vc ? in->v : nullptr, with_vc ? in->C : nullptr,
+                                                 in->F, pinned_in, ids_in, out->x, out->v, out->C,
+                                                 out->F, pinned_out, ids_out);
+    DW_LAUNCHED("k_sort_move");
     return DW_OK;
 }
 

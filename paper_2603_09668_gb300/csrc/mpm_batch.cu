@@ -555,7 +555,7 @@ struct dw_mpm_batch_s {
     int *flags = nullptr, *list = nullptr, *count = nullptr, *err = nullptr;
     unsigned *bar = nullptr;
     float *t0 = nullptr;
-    int *keys = nullptr, *perm = nullptr, *key_counts = nullptr, *scan_tmp = nullptr;
+    int *keys = nullptr, *key_counts = nullptr, *scan_tmp = nullptr;
     int64_t scan_tmp_len = 0;
     float *roll_state = nullptr;
     uint8_t *roll_pinned = nullptr;
@@ -630,12 +630,11 @@ static dw_status batch_sort(dw_mpm_batch h, const dw_mpm_state &in, const dw_mpm
     DW_LAUNCHED("k_batch_sort_keys");
     dw_status st = exclusive_scan(h->key_counts, h->total_keys, h->scan_tmp, h->scan_tmp_len, s);
     if (st != DW_OK) return st;
-    k_sort_scatter<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->key_counts, h->perm);
-    DW_LAUNCHED("k_sort_scatter");
-    k_permute<<<grid_for(n, 256), 256, 0, s>>>(h->perm, n, in.x, with_vc ? in.v : nullptr,
-                                               with_vc ? in.C : nullptr, in.F, pin_in, ids_in,
-                                               out.x, out.v, out.C, out.F, pin_out, ids_out);
-    DW_LAUNCHED("k_permute");
+    k_sort_move<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->key_counts, in.x,
+                                                 with_vc ? in.v : nullptr, with_vc ? in.C : nullptr,
+                                                 in.F, pin_in, ids_in, out.x, out.v, out.C, out.F,
+                                                 pin_out, ids_out);
+    DW_LAUNCHED("k_sort_move");
     return DW_OK;
 }
 
@@ -876,7 +875,6 @@ extern "C" dw_status mpm_batch_create(const dw_mpm_scene *scenes, int32_t n_scen
     DW_ALLOC(h->bar, sizeof(unsigned) * 2);
     DW_ALLOC(h->t0, sizeof(float));
     DW_ALLOC(h->keys, sizeof(int) * (size_t)n);
-    DW_ALLOC(h->perm, sizeof(int) * (size_t)n);
     DW_ALLOC(h->key_counts, sizeof(int) * (size_t)(total_keys + 1));
     DW_ALLOC(h->scan_tmp, sizeof(int) * (size_t)h->scan_tmp_len);
     DW_ALLOC(h->roll_state, sizeof(float) * 24 * (size_t)n);
@@ -939,7 +937,6 @@ extern "C" dw_status mpm_batch_destroy(dw_mpm_batch h) {
     cudaFree(h->bar);
     cudaFree(h->t0);
     cudaFree(h->keys);
-    cudaFree(h->perm);
     cudaFree(h->key_counts);
     cudaFree(h->scan_tmp);
     cudaFree(h->roll_state);

@@ -42,7 +42,6 @@ struct MpmHandle {
     int nb = 0;                  // 4^3 blocks per axis
     int64_t n_keys = 0;
     int *keys = nullptr;         // [max_particles]
-    int *perm = nullptr;         // [max_particles]
     int *counts = nullptr;       // [n_keys + 1]
     int *scan_tmp = nullptr;     // block sums for the exclusive scan
     int64_t scan_tmp_len = 0;
@@ -136,14 +135,13 @@ dw_status segment_recompute(MpmHandle *h, const dw_mpm_state *start, float *tape
 constexpr int SCAN_BLOCK = 1024;
 constexpr int SCAN_ITEMS = 8;                         // consecutive elements per scan thread
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;    // elements per scan block
-__global__ void k_sort_scatter(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
-                               int *__restrict__ perm);
-__global__ void k_permute(const int *__restrict__ perm, int64_t n, const float *__restrict__ x,
-                          const float *__restrict__ v, const float *__restrict__ C,
-                          const float *__restrict__ F, const uint8_t *__restrict__ pin_in,
-                          const int *__restrict__ ids_in, float *__restrict__ xo,
-                          float *__restrict__ vo, float *__restrict__ Co, float *__restrict__ Fo,
-                          uint8_t *__restrict__ pin_out, int *__restrict__ ids_out);
+__global__ void k_sort_move(const int *__restrict__ keys, int64_t n, int *__restrict__ offsets,
+                            const float *__restrict__ x, const float *__restrict__ v,
+                            const float *__restrict__ C, const float *__restrict__ F,
+                            const uint8_t *__restrict__ pin_in, const int *__restrict__ ids_in,
+                            float *__restrict__ xo, float *__restrict__ vo, float *__restrict__ Co,
+                            float *__restrict__ Fo, uint8_t *__restrict__ pin_out,
+                            int *__restrict__ ids_out);
 // In-place exclusive prefix sum of data[0, len); tmp holds at least
 // len / SCAN_BLOCK + 1 ints.
 dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cudaStream_t st);

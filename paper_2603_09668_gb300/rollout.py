@@ -34,7 +34,7 @@ class Rollout:
     def kernel_launches(self):
         """Kernels of one run: one P2G, a grid update per substep, a fused
         G2P+P2G per substep but the last, one G2P, and per sort (at the start
-        and every sort_every substeps) the key, scatter and permute kernels
+        and every sort_every substeps) the key and the scatter-move kernels
         and a scan of the 64 nb^3 cell counters (nb = ceil(n_grid / 4)): two
         kernels for at most 1024 scan blocks of 8192 counters, else three."""
         if self.n_substeps == 0:
@@ -42,7 +42,7 @@ class Rollout:
         sorts = -(-self.n_substeps // self.sort_every) if self.sort_every > 0 else 0
         nb = (self.mpm.n_grid + 3) // 4
         scan_blocks = -(-64 * nb ** 3 // 8192)
-        per_sort = 3 + (2 if scan_blocks <= 1024 else 3)
+        per_sort = 2 + (2 if scan_blocks <= 1024 else 3)
         return 1 + 2 * self.n_substeps + per_sort * sorts
 
     def _issue(self):
