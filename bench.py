@@ -335,7 +335,7 @@ ALGO_FLOP_PER_PS = 1991
 # dram__bytes_write.sum of the 5th launch of `bench.py --substeps 40 --steps 1
 # --warmup 1 --no-extras --no-cpu-baseline`); valid only for the kernel
 # sources it was taken on (hash of the files below), else reported as null.
-G2P2G_TRAFFIC = {"sha16": "d0d3c9ce2d01e491", "bytes": 20.10e6, "particles": 400040}
+G2P2G_TRAFFIC = {"sha16": "fcdfa04c31865798", "bytes": 20.10e6, "particles": 400040}
 G2P2G_SOURCES = ("mpm_rollout.cu", "mpm_pair_warp.cuh", "mpm_pair.cuh", "mpm_p2g.cuh",
                  "mpm_math.cuh")
 

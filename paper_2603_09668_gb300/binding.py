@@ -639,6 +639,7 @@ class MPM:
                  E=1e4, nu=0.3, p_mass=1.0, p_vol=1.0, max_particles=0, p2g_mode=P2G_AUTO):
         self.n_grid, self.dt = n_grid, dt
         self.E, self.nu = E, nu
+        self.p2g_mode = p2g_mode
         self.h = mpm_create(n_grid, dt, gravity, bc_band, material, E, nu, p_mass, p_vol,
                             max_particles, p2g_mode)
 

@@ -821,13 +821,16 @@ namespace dw {
 
 dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_state *out,
                          const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
-                         int32_t *ids_out, cudaStream_t s, bool with_vc) {
+                         int32_t *ids_out, cudaStream_t s, bool with_vc, bool keys_ready,
+                         bool clear_after) {
     int64_t n = in->n;
     if (n == 0) return DW_OK;
     ProfScope ps(h, DW_K_SORT, s);
-    DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
-    k_sort_keys<<<grid_for(n, 256), 256, 0, s>>>(h->P, h->nb, in->x, n, h->keys, h->counts);
-    DW_LAUNCHED("k_sort_keys");
+    if (!keys_ready) {
+        DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
+        k_sort_keys<<<grid_for(n, 256), 256, 0, s>>>(h->P, h->nb, in->x, n, h->keys, h->counts);
+        DW_LAUNCHED("k_sort_keys");
+    }
     dw_status st = exclusive_scan(h->counts, h->n_keys, h->scan_tmp, h->scan_tmp_len, s);
     if (st != DW_OK) return st;
     k_sort_move<<<grid_for(n, 256), 256, 0, s>>>(h->keys, n, h->counts, in->x,
@@ -835,6 +838,7 @@ dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_stat
                                                  in->F, pinned_in, ids_in, out->x, out->v, out->C,
                                                  out->F, pinned_out, ids_out);
     DW_LAUNCHED("k_sort_move");
+    if (clear_after) DW_CUDA(cudaMemsetAsync(h->counts, 0, sizeof(int) * (size_t)(h->n_keys + 1), s));
     return DW_OK;
 }
 

@@ -150,10 +150,14 @@ dw_status exclusive_scan(int *data, int64_t len, int *tmp, int64_t tmp_len, cuda
 dw_status validate_desc(const dw_mpm_desc *desc);
 dw_status check_state(const MpmHandle *h, const dw_mpm_state *s, const char *name);
 // with_vc = false leaves v and C of `out` unwritten (a rollout between fused
-// launches, where v and C are not kept).
+// launches, where v and C are not kept). keys_ready: h->keys and h->counts
+// already hold the keys of `in` and their counts (the fused launch before
+// the sort wrote them). clear_after: the counts are cleared at the end, for
+// a fused launch that counts the next sort's keys.
 dw_status sort_particles(MpmHandle *h, const dw_mpm_state *in, const dw_mpm_state *out,
                          const uint8_t *pinned_in, uint8_t *pinned_out, const int32_t *ids_in,
-                         int32_t *ids_out, cudaStream_t s, bool with_vc = true);
+                         int32_t *ids_out, cudaStream_t s, bool with_vc = true,
+                         bool keys_ready = false, bool clear_after = false);
 
 }  // namespace dw
 

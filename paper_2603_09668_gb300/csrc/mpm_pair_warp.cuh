@@ -5,6 +5,7 @@
 
 #include <limits.h>
 
+#include "mpm_grid.cuh"
 #include "mpm_pair.cuh"
 
 namespace dw {
@@ -160,9 +161,12 @@ __device__ __forceinline__ void g2p_direct(const MpmParams &P, const pr::Stencil
 }
 
 // Output arrays of a substep that writes its whole output state elsewhere
-// (the recompute of a reverse segment: state k in, state k + 1 out).
+// (the recompute of a reverse segment: state k in, state k + 1 out), and the
+// next sort's key and count arrays (the substep before a re-sort).
 struct PairOut {
-    float *x, *v, *C, *F;
+    float *x = nullptr, *v = nullptr, *C = nullptr, *F = nullptr;
+    int *keys = nullptr;    // [n] cell key of each updated particle (KEYS)
+    int *counts = nullptr;  // [keys] particles per key, added to (KEYS)
 };
 
 // The substep body for one warp: particles wq .. min(wq + 64, wend) - 1 of
@@ -170,7 +174,10 @@ struct PairOut {
 // (warp-uniform). reset_count, when not NULL, is cleared after the
 // dependency wait (the active list the grid update has consumed). With OUT
 // the updated x, v, C and F go to `out` (x and F are not updated in place).
-template <int MAT, bool STORE_VC, bool VEC, bool OUT = false>
+// With KEYS the substep also writes the sort key (cell_key) of every updated
+// particle to out.keys and counts it in out.counts (one atomic per distinct
+// key of a warp and particle slot), the first pass of the re-sort after it.
+template <int MAT, bool STORE_VC, bool VEC, bool OUT = false, bool KEYS = false>
 __device__ __forceinline__ void pair_warp(
     const MpmParams &P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
     float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
@@ -314,6 +321,21 @@ __device__ __forceinline__ void pair_warp(
     Stencil2 t;
     bool p0ok, p1ok;
     stencil2(P, xp, t, p0ok, p1ok);
+    if (KEYS) {
+        const int kk0 = cell_key(P, ab_next.nb, xp[0].x, xp[1].x, xp[2].x);
+        const int kk1 = cell_key(P, ab_next.nb, xp[0].y, xp[1].y, xp[2].y);
+        const unsigned m0 = __ballot_sync(FULL, v0), m1 = __ballot_sync(FULL, v1);
+        if (v0) {
+            out.keys[q] = kk0;
+            const unsigned peers = __match_any_sync(m0, kk0);
+            if (lane == __ffs(peers) - 1) atomicAdd(&out.counts[kk0], __popc(peers));
+        }
+        if (v1) {
+            out.keys[q + 1] = kk1;
+            const unsigned peers = __match_any_sync(m1, kk1);
+            if (lane == __ffs(peers) - 1) atomicAdd(&out.counts[kk1], __popc(peers));
+        }
+    }
     if ((v0 && !p0ok) || (v1 && !p1ok)) atomicOr(err, ERRBIT_DOMAIN);
     p0ok = p0ok && v0;
     p1ok = p1ok && v1;

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(P2G_WARP_THREADS, 10) k_g2p2g(
 // k_g2p2g_pair: the body of k_g2p2g with two particles per thread on paired
 // FP32 instructions (pair_warp, mpm_pair_warp.cuh).
 // With OUT the output state goes to `out` (the recompute of a reverse segment).
-template <int MAT, bool STORE_VC, bool VEC, bool OUT = false>
+template <int MAT, bool STORE_VC, bool VEC, bool OUT = false, bool KEYS = false>
 __global__ void __launch_bounds__(PAIR_THREADS, PAIR_MIN_CTAS) k_g2p2g_pair(
     MpmParams P, float *__restrict__ x, float *__restrict__ v, float *__restrict__ C,
     float *__restrict__ F, const uint8_t *__restrict__ pinned, const float4 *__restrict__ grid_v,
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, PAIR_MIN_CTAS) k_g2p2g_pair(
     __shared__ PairWarpSmem smem[PAIR_WARPS];
     const int wid = threadIdx.x >> 5;
     const int64_t wq = ((int64_t)blockIdx.x * PAIR_THREADS + wid * 32) * 2;  // the warp's first particle
-    pair_warp<MAT, STORE_VC, VEC, OUT>(P, x, v, C, F, pinned, grid_v, grid_next, n, wq, n, err,
+    pair_warp<MAT, STORE_VC, VEC, OUT, KEYS>(P, x, v, C, F, pinned, grid_v, grid_next, n, wq, n, err,
                                        ab_next,
                                        blockIdx.x == 0 && threadIdx.x == 0 ? reset_count : nullptr,
                                        smem[wid], out);
@@ -205,15 +205,18 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
     const bool pair = h->desc.p2g_mode == DW_P2G_AUTO || h->desc.p2g_mode == DW_P2G_PAIR;
     const unsigned pair_grid = grid_for(n, 2 * PAIR_THREADS);
     int L = 0;  // active list consumed by the next grid update
-    auto resort = [&](bool with_vc) {
-        dw_status r = sort_particles(h, &cur, &oth, cur_pin, oth_pin, cur_ids, oth_ids, s, with_vc);
+    // the fused launch before a re-sort computes and counts the sort keys
+    // (paired kernel; the counts are cleared by the sort before)
+    auto resort = [&](bool with_vc, bool keys_ready) {
+        dw_status r = sort_particles(h, &cur, &oth, cur_pin, oth_pin, cur_ids, oth_ids, s, with_vc,
+                                     keys_ready, pair);
         std::swap(cur, oth);
         std::swap(cur_pin, oth_pin);
         std::swap(cur_ids, oth_ids);
         return r;
     };
     if (sort_every > 0) {
-        st = resort(true);  // the input state's v and C feed the first P2G
+        st = resort(true, false);  // the input state's v and C feed the first P2G
         if (st != DW_OK) return st;
     }
     {
@@ -244,15 +247,25 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
                 // multiple of 4, 16-byte aligned arrays)
                 const bool pair_vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cur.x) |
                                                         reinterpret_cast<uintptr_t>(cur.F)) % 16 == 0);
-                auto kern = h->P.material == DW_NEOHOOKEAN
-                                ? (pair_vec ? k_g2p2g_pair<DW_NEOHOOKEAN, false, true>
-                                            : k_g2p2g_pair<DW_NEOHOOKEAN, false, false>)
-                                : (pair_vec ? k_g2p2g_pair<DW_FIXED_COROTATED, false, true>
-                                            : k_g2p2g_pair<DW_FIXED_COROTATED, false, false>);
+                const bool keys = sort_every > 0 && (k + 1) % sort_every == 0;
+                const bool nh = h->P.material == DW_NEOHOOKEAN;
+                auto kern = keys ? (nh ? (pair_vec ? k_g2p2g_pair<DW_NEOHOOKEAN, false, true, false, true>
+                                                   : k_g2p2g_pair<DW_NEOHOOKEAN, false, false, false, true>)
+                                       : (pair_vec ? k_g2p2g_pair<DW_FIXED_COROTATED, false, true, false, true>
+                                                   : k_g2p2g_pair<DW_FIXED_COROTATED, false, false, false, true>))
+                                 : (nh ? (pair_vec ? k_g2p2g_pair<DW_NEOHOOKEAN, false, true>
+                                                   : k_g2p2g_pair<DW_NEOHOOKEAN, false, false>)
+                                       : (pair_vec ? k_g2p2g_pair<DW_FIXED_COROTATED, false, true>
+                                                   : k_g2p2g_pair<DW_FIXED_COROTATED, false, false>));
+                PairOut po{};
+                if (keys) {
+                    po.keys = h->keys;
+                    po.counts = h->counts;
+                }
                 DW_CUDA(launch_pdl(kern, pair_grid, PAIR_THREADS, s, h->P, cur.x, cur.v, cur.C,
                                    cur.F, (const uint8_t *)cur_pin, (const float4 *)h->grid_v,
                                    h->grid_mp, n, h->err, active_blocks(h, 1 - L),
-                                   h->block_count + L, PairOut{}));
+                                   h->block_count + L, po));
             } else {
                 DW_CUDA(launch_pdl(k_g2p2g<false>, pgrid, P2G_WARP_THREADS, s, h->P, cur.x,
                                    cur.v, cur.C, cur.F, (const uint8_t *)cur_pin,
@@ -266,7 +279,7 @@ extern "C" dw_status mpm_rollout(dw_mpm h, const dw_mpm_state *state, uint8_t *p
         // the sorted order serves the G2P of k + 1 and every P2G after it.
         // v and C are not kept between fused launches, so none is lost.
         if (sort_every > 0 && (k + 1) % sort_every == 0) {
-            st = resort(false);
+            st = resort(false, pair);
             if (st != DW_OK) return st;
         }
     }

@@ -34,16 +34,20 @@ class Rollout:
     def kernel_launches(self):
         """Kernels of one run: one P2G, a grid update per substep, a fused
         G2P+P2G per substep but the last, one G2P, and per sort (at the start
-        and every sort_every substeps) the key and the scatter-move kernels
-        and a scan of the 64 nb^3 cell counters (nb = ceil(n_grid / 4)): two
-        kernels for at most 1024 scan blocks of 8192 counters, else three."""
+        and every sort_every substeps) a scan of the 64 nb^3 cell counters
+        (nb = ceil(n_grid / 4): two kernels for at most 1024 scan blocks of
+        8192 counters, else three) and the scatter-move kernel, plus the key
+        kernel for the first sort (and for every sort with the one-particle
+        fused kernel; the paired one counts the keys itself)."""
         if self.n_substeps == 0:
             return 0
         sorts = -(-self.n_substeps // self.sort_every) if self.sort_every > 0 else 0
         nb = (self.mpm.n_grid + 3) // 4
         scan_blocks = -(-64 * nb ** 3 // 8192)
-        per_sort = 2 + (2 if scan_blocks <= 1024 else 3)
-        return 1 + 2 * self.n_substeps + per_sort * sorts
+        per_sort = 1 + (2 if scan_blocks <= 1024 else 3)
+        paired = getattr(self.mpm, "p2g_mode", B.P2G_AUTO) in (B.P2G_AUTO, B.P2G_PAIR)
+        key_kernels = min(sorts, 1) if paired else sorts
+        return 1 + 2 * self.n_substeps + per_sort * sorts + key_kernels
 
     def _issue(self):
         self.mpm.rollout(self.state, self.pins, self.ids, self.wind, self.t0, self.n_substeps,
