@@ -158,3 +158,28 @@ def test_state_checkpoint_header_is_read_without_a_gpu(tmp_path, libpath):
         B.mpm_state_peek(str(bad))
     with pytest.raises(B.DiffWindError, match="DW_ERR_IO"):
         B.mpm_state_peek(str(tmp_path / "missing.dwst"))
+
+
+def test_rollout_launch_count_follows_the_launch_sequence():
+    """The kernel count the bench reports (`gpu_launches`) for one rollout:
+    one P2G, a grid update per substep, a fused launch per substep but the
+    last, one G2P, per sort the scan (two kernels up to 1024 scan blocks of
+    8192 counters, else three) and the scatter-move, and the key kernel for
+    the first sort only when the paired fused kernel counts the later keys."""
+    from types import SimpleNamespace
+
+    from paper_2603_09668_gb300 import binding as B
+    from paper_2603_09668_gb300.rollout import Rollout
+
+    def count(n_grid, n_sub, sort_every, mode=B.P2G_AUTO):
+        mpm = SimpleNamespace(n_grid=n_grid, p2g_mode=mode)
+        return Rollout(mpm, 8, None, n_sub, sort_every=sort_every, device="cpu").kernel_launches
+
+    # 128^3: 64 * 32^3 counters = 256 scan blocks; 67 sorts in 1000 substeps
+    assert count(128, 1000, 15) == 1 + 2000 + 67 * 3 + 1
+    assert count(128, 1000, 0) == 1 + 2000
+    assert count(128, 30, 15) == 1 + 60 + 2 * 3 + 1  # sorts at substeps 0 and 15
+    # the one-particle fused kernel leaves every sort its key kernel
+    assert count(128, 1000, 15, B.P2G_WARP) == 1 + 2000 + 67 * 4
+    # 512^3: 64 * 128^3 counters = 16384 scan blocks, a three-kernel scan
+    assert count(512, 100, 50) == 1 + 200 + 2 * 4 + 1
